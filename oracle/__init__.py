@@ -1,0 +1,257 @@
+"""CPU oracle for the differentiable Gaussian rasterizer — TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
+package.  The product path (``paper_2601_17354_gb300``) never imports, links or runs it.
+
+The arithmetic lives in ``pgs_oracle.cpp`` (plain C++17, FP64 values, fp32 decisions with a
+prescribed operation order), compiled by :func:`build` with ``-ffp-contract=off`` into
+``oracle/_build/liboracle.so``.  This module only marshals numpy arrays into that library.
+
+Parity status of each function (what pins it, besides agreeing with the GPU path):
+  project / render / render_pixels  closed-form single and stacked Gaussians, sum(w)+T = 1,
+                                    Eq. 7 back-to-front cross-check
+  keys                              brute-force per-tile lists, hand-checked tiny case
+  backward / backward_subset        FP64 central finite differences, two derivations agree
+  sh basis                          orthonormality by quadrature, addition theorem, zonal values
+  det_expf                          FP64 exp within 2 ulp
+  adam                              torch.optim.Adam (float64), closed-form first step
+  l1                                closed forms
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pgs_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (g++, -O2, -ffp-contract=off).  Returns the library path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+    if fresh and not force:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OCam(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("view", C.c_float * 12),
+                ("near_z", C.c_float), ("bg", C.c_float * 3)]
+
+
+class OGauss(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad_", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            P = C.c_void_p
+            L.oracle_det_expf.restype = C.c_float
+            L.oracle_det_expf.argtypes = [C.c_float]
+            L.oracle_sh_basis.argtypes = [P, P, P]
+            L.oracle_param_count.restype = C.c_int
+            L.oracle_param_count.argtypes = [C.c_int]
+            L.oracle_project.argtypes = [P, P, C.c_int] + [P] * 10
+            L.oracle_keys.restype = C.c_int64
+            L.oracle_keys.argtypes = [P, P, C.c_int, C.c_int64, P, P, P]
+            L.oracle_render.argtypes = [P, P, C.c_int, P, P, P, P, P, P]
+            L.oracle_render_pixels.argtypes = [P, P, C.c_int, C.c_int64, P, P, P, P, P]
+            L.oracle_render_eq7.argtypes = [P, P, C.c_int, P]
+            L.oracle_backward.argtypes = [P, P, C.c_int, P, C.c_int, P, P]
+            L.oracle_backward_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, P, P]
+            L.oracle_chain.argtypes = [P, P, C.c_int, P, P]
+            L.oracle_gaussian_flags.argtypes = [P, P, C.c_int, P]
+            L.oracle_l1.argtypes = [C.c_int64, P, P, P, P, P]
+            L.oracle_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int64]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _Inputs:
+    """Keeps the contiguous float32 copies alive while the C structs point at them."""
+
+    def __init__(self, g, cam):
+        self.arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in g.arrays()]
+        m, ls, q, lg, sh = self.arrs
+        self.g = OGauss(g.n, g.sh_degree, 0, _ptr(m).value, _ptr(ls).value, _ptr(q).value,
+                        _ptr(lg).value, _ptr(sh).value)
+        self.cam = OCam(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy),
+                        float(cam.cx), float(cam.cy),
+                        (C.c_float * 12)(*np.asarray(cam.viewmat, np.float32).reshape(-1).tolist()),
+                        float(cam.near), (C.c_float * 3)(*[float(b) for b in cam.bg]))
+
+    @property
+    def gp(self):
+        return C.byref(self.g)
+
+    @property
+    def cp(self):
+        return C.byref(self.cam)
+
+
+def tiles(cam, tile: int = 16):
+    return (cam.width + tile - 1) // tile, (cam.height + tile - 1) // tile
+
+
+def param_count(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def det_expf(x) -> np.ndarray:
+    L = lib()
+    x = np.asarray(x, np.float32).reshape(-1)
+    return np.array([L.oracle_det_expf(float(v)) for v in x], np.float32)
+
+
+def sh_basis(direction):
+    """Y [16] and dY/d(x,y,z) [16][3] of the degree-3 real SH at a unit direction."""
+    d = np.ascontiguousarray(direction, np.float64)
+    y = np.zeros(16)
+    dy = np.zeros((16, 3))
+    lib().oracle_sh_basis(_ptr(d), _ptr(y), _ptr(dy))
+    return y, dy
+
+
+def project(g, cam, tile: int = 16) -> dict:
+    inp = _Inputs(g, cam)
+    n = g.n
+    out = dict(visible=np.zeros(n, np.int32), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), depth=np.zeros(n, np.float32),
+               uv=np.zeros((n, 2), np.float32), cov2d=np.zeros((n, 3), np.float32),
+               mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n),
+               rgb=np.zeros((n, 3)))
+    lib().oracle_project(inp.gp, inp.cp, tile, *[_ptr(out[k]) for k in
+                         ["visible", "radius", "rect", "depth", "uv", "cov2d", "mean2d", "conic",
+                          "opacity", "rgb"]])
+    return out
+
+
+def keys(g, cam, tile: int = 16):
+    """(keys uint64 [P], values uint32 [P], ranges uint32 [tiles][2])."""
+    inp = _Inputs(g, cam)
+    L = lib()
+    P = L.oracle_keys(inp.gp, inp.cp, tile, 0, None, None, None)
+    k = np.zeros(max(P, 1), np.uint64)
+    v = np.zeros(max(P, 1), np.uint32)
+    tx, ty = tiles(cam, tile)
+    r = np.zeros((tx * ty, 2), np.uint32)
+    L.oracle_keys(inp.gp, inp.cp, tile, P, _ptr(k), _ptr(v), _ptr(r))
+    return k[:P], v[:P], r
+
+
+def render(g, cam, tile: int = 16) -> dict:
+    inp = _Inputs(g, cam)
+    H, W = cam.height, cam.width
+    out = dict(image=np.zeros((3, H, W)), T=np.zeros((H, W)), last=np.zeros((H, W), np.int32),
+               flag=np.zeros((H, W), np.uint8), evals=np.zeros((H, W), np.int64),
+               ncomp=np.zeros((H, W), np.int32))
+    lib().oracle_render(inp.gp, inp.cp, tile, _ptr(out["image"]), _ptr(out["T"]),
+                        _ptr(out["last"]), _ptr(out["flag"]), _ptr(out["evals"]),
+                        _ptr(out["ncomp"]))
+    return out
+
+
+def render_pixels(g, cam, pix_xy, tile: int = 16) -> dict:
+    inp = _Inputs(g, cam)
+    pix = np.ascontiguousarray(pix_xy, np.int32).reshape(-1, 2)
+    m = pix.shape[0]
+    out = dict(rgb=np.zeros((m, 3)), T=np.zeros(m), last=np.zeros(m, np.int32),
+               flag=np.zeros(m, np.uint8))
+    lib().oracle_render_pixels(inp.gp, inp.cp, tile, m, _ptr(pix), _ptr(out["rgb"]),
+                               _ptr(out["T"]), _ptr(out["last"]), _ptr(out["flag"]))
+    return out
+
+
+def render_eq7(g, cam, tile: int = 16) -> np.ndarray:
+    inp = _Inputs(g, cam)
+    img = np.zeros((3, cam.height, cam.width))
+    lib().oracle_render_eq7(inp.gp, inp.cp, tile, _ptr(img))
+    return img
+
+
+def split_grads(flat: np.ndarray, n: int, sh_degree: int) -> dict:
+    """Planar [P*N] parameter gradients -> named arrays."""
+    K = (sh_degree + 1) ** 2
+    return dict(means=flat[:3 * n].reshape(3, n), log_scales=flat[3 * n:6 * n].reshape(3, n),
+                quats=flat[6 * n:10 * n].reshape(4, n), opacity_logits=flat[10 * n:11 * n],
+                sh=flat[11 * n:].reshape(3, K, n))
+
+
+def backward(g, cam, dL_dimage, tile: int = 16, mode: int = 0):
+    """(grad2d [N][9], named parameter gradients) for an upstream gradient [3][H][W]."""
+    inp = _Inputs(g, cam)
+    d = np.ascontiguousarray(dL_dimage, np.float64)
+    g2 = np.zeros((g.n, 9))
+    flat = np.zeros(param_count(g.sh_degree) * g.n)
+    lib().oracle_backward(inp.gp, inp.cp, tile, _ptr(d), mode, _ptr(g2), _ptr(flat))
+    return g2, split_grads(flat, g.n, g.sh_degree)
+
+
+def backward_subset(g, cam, dL_dimage, sel, tile: int = 16):
+    """(grad2d [S][9], grads [S][11 + 3K]) for the selected canonical indices."""
+    inp = _Inputs(g, cam)
+    d = np.ascontiguousarray(dL_dimage, np.float64)
+    sel = np.ascontiguousarray(sel, np.int64)
+    g2 = np.zeros((len(sel), 9))
+    gp = np.zeros((len(sel), param_count(g.sh_degree)))
+    lib().oracle_backward_subset(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), _ptr(g2),
+                                 _ptr(gp))
+    return g2, gp
+
+
+def chain(g, cam, grad2d, tile: int = 16) -> dict:
+    inp = _Inputs(g, cam)
+    g2 = np.ascontiguousarray(grad2d, np.float64)
+    flat = np.zeros(param_count(g.sh_degree) * g.n)
+    lib().oracle_chain(inp.gp, inp.cp, tile, _ptr(g2), _ptr(flat))
+    return split_grads(flat, g.n, g.sh_degree)
+
+
+def gaussian_flags(g, cam, tile: int = 16) -> np.ndarray:
+    inp = _Inputs(g, cam)
+    f = np.zeros(g.n, np.uint8)
+    lib().oracle_gaussian_flags(inp.gp, inp.cp, tile, _ptr(f))
+    return f
+
+
+def l1(img, gt):
+    a = np.ascontiguousarray(img, np.float64).reshape(-1)
+    b = np.ascontiguousarray(gt, np.float64).reshape(-1)
+    grad = np.zeros_like(a)
+    loss = C.c_double()
+    sse = C.c_double()
+    lib().oracle_l1(a.size, _ptr(a), _ptr(b), _ptr(grad), C.byref(loss), C.byref(sse))
+    return loss.value, grad.reshape(np.shape(img)), sse.value
+
+
+def adam(p, g, m, v, lr, t, b1=0.9, b2=0.999, eps=1e-15):
+    """One Adam step in place on float64 arrays."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().oracle_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, t)
