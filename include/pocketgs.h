@@ -1,0 +1,150 @@
+/*
+ * pocketgs.h — C ABI of libpocketgs.so, a GB300 (sm_103a) differentiable tile-based Gaussian
+ * rasterizer: the training hot path of PocketGS (arXiv 2601.17354), operator T of Sec. III,
+ *     T : (Theta_0, {I_t, T_t}) -> Theta*,
+ * exposed as the three calls of one optimisation iteration: render (Sec. III-C, Eq. 7),
+ * backward (Eq. 8 and the index-mapped scatter of Eq. 10) and step (Adam with moments aligned to
+ * the canonical parameter buffer, Sec. III-C "Index-Mapped Gradient Scattering").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All tensor pointers are DEVICE pointers owned by the caller and borrowed for the call.
+ *    Parameters are fp32, planar structure-of-arrays ("[k][n]" = k rows of n floats):
+ *        means [3][n], log_scales [3][n], quats [4][n] (w, x, y, z; need not be unit),
+ *        opacity_logits [n], sh [3][K][n] with K = (sh_degree + 1)^2 (channel-major).
+ *    Rows need no particular alignment; 16-byte aligned rows with n % 4 == 0 take the
+ *    vectorised path of pgs_step.
+ *  - Images are [3][H][W] fp32 planar, row-major; pixel (x, y) covers [x, x+1) x [y, y+1).
+ *  - Cameras are pinhole with OpenCV axes (x right, y down, z forward); viewmat is the
+ *    row-major 3x4 world-to-camera matrix [R | t].
+ *  - Every call enqueues work on the context's CUDA stream and returns without synchronising,
+ *    except pgs_status, pgs_read_buffer and pgs_reserve (which may allocate).
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ *  - Return value: PGS_OK (0) or a negative PGS_ERR_* code.  No C++ exception crosses the ABI.
+ *    Errors detected on the device (pair capacity overflow, non-finite parameters) are recorded
+ *    in the context's device status word and reported by the next pgs_status call.
+ */
+#ifndef POCKETGS_H
+#define POCKETGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PGS_OK 0
+#define PGS_ERR_INVALID_ARG (-1) /* null pointer, bad size, unsupported tile or degree */
+#define PGS_ERR_NO_RENDER (-2)   /* pgs_backward without a preceding pgs_render */
+#define PGS_ERR_CAPACITY (-3)    /* more (tile, Gaussian) pairs than pair_capacity */
+#define PGS_ERR_NONFINITE (-4)   /* a parameter of a projected Gaussian was NaN or inf */
+#define PGS_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define PGS_ERR_OOM (-7)         /* device allocation failed */
+
+typedef struct pgs_ctx pgs_ctx;
+
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12]; /* row-major 3x4 world -> camera [R | t] */
+    float near_z;      /* Gaussians with camera depth z <= near_z are culled */
+    float bg[3];       /* background colour composited behind the last Gaussian */
+} pgs_camera;
+
+typedef struct {
+    int64_t n;
+    int32_t sh_degree; /* 0..3 */
+    int32_t pad_;
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logits;
+    float* sh;
+} pgs_gaussians;
+
+typedef struct {
+    int32_t tile;          /* screen tile edge in pixels: 16 (the only supported value) */
+    int32_t reserved_;
+    int64_t pair_capacity; /* (tile, Gaussian) pairs the context holds; 0 = grow on demand */
+    float adam_b1, adam_b2, adam_eps;
+    /* learning rates of the parameter groups: means, log_scales, quats, opacity_logits,
+       sh degree-0 coefficients, sh higher coefficients */
+    float lr[6];
+} pgs_config;
+
+/* Create a context that enqueues on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+   The context owns all scratch memory (projected Gaussians, keys, tile ranges, per-pixel final
+   transmittance and last-contributor index, screen-space gradients, status word).
+   *out receives the context; on error *out is NULL. */
+int pgs_create(pgs_ctx** out, const pgs_config* cfg, void* cuda_stream);
+
+/* Free the context and its scratch.  Synchronises the context's stream first.  NULL is a no-op. */
+void pgs_destroy(pgs_ctx* ctx);
+
+/* Make sure the scratch covers n Gaussians, a width x height image and pair_capacity pairs,
+   allocating if needed (this synchronises the device).  Calls whose sizes fit the reservation
+   never allocate, so a sequence of them can be captured in a CUDA graph. */
+int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t pair_capacity);
+
+/* Forward pass, Eq. 7 front to back: project and cull every Gaussian (EWA projection, SH colour),
+   emit (tile | depth, canonical index) pairs, sort them (the permutation pi of Eq. 10), find each
+   tile's range, alpha-composite each pixel over its tile's depth-ordered list
+   (alpha = min(0.99, o G); skip alpha < 1/255; stop before a Gaussian that would take the
+   transmittance below 1e-4), and write image_out [3][H][W] = colour + T_final * bg.
+   The context keeps, for pgs_backward, the projected Gaussians, the sorted pairs, the tile
+   ranges, T_final [H][W] and last [H][W] (1 + list position of the last composited entry).
+   If the pair count exceeds the capacity the image is undefined and pgs_status reports
+   PGS_ERR_CAPACITY with the count needed; with pair_capacity = 0 the context instead reads the
+   count back (one synchronisation) and grows before compositing. */
+int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out);
+
+/* L1 photometric loss of Sec. IV's training loop (the paper names no loss): for n = 3 H W values,
+   dL_dimage[k] = sign(image[k] - target[k]) / n (sign(0) = 0) and, on the device,
+   loss_out[0] = mean |image - target|, loss_out[1] = sum (image - target)^2 (for PSNR).
+   loss_out is a device pointer to 2 floats. */
+int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,
+                float* loss_out);
+
+/* Backward of the last pgs_render on this context for the upstream gradient dL_dimage [3][H][W]:
+   per pixel, re-traverse its list back to front from `last`, rebuilding the transmittance from
+   T_final (T_i = T_{i+1} / (1 - alpha_i)) and the colour behind each entry with Eq. 7, apply
+   Eq. 8 for dL/dc and dL/dalpha, reduce over the pixels of a tile and scatter to the canonical
+   index (Eq. 10); then chain to every parameter.  Gradients are ADDED to grads (same layout as
+   the parameters; the caller zeroes them, pgs_step does so after reading them).  The parameter
+   values must be those of the last render. */
+int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads);
+
+/* One Adam step over all parameter groups in one launch (Kingma & Ba 2015, bias-corrected, step
+   number t >= 1, the context's b1, b2, eps and per-group learning rates):
+   m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2; p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps);
+   then g = 0.  params, grads, m and v share n and sh_degree. */
+int pgs_step(pgs_ctx* ctx, pgs_gaussians* params, pgs_gaussians* grads, pgs_gaussians* m,
+             pgs_gaussians* v, int64_t t);
+
+/* Synchronise the context's stream, return the first error recorded on the device since the
+   last call (PGS_OK if none) and clear it.  *pairs_needed (optional) receives the pair count of
+   the last render. */
+int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
+
+/* Internal buffers of the last render/backward, copied to `dst` (host or device) for inspection.
+   which: PGS_BUF_KEYS (uint64 [P], sorted), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
+   (uint32 [tiles][2]), PGS_BUF_T_FINAL (float [H][W]), PGS_BUF_LAST (uint32 [H][W]),
+   PGS_BUF_GRAD2D (float [9][n]: du, dv, d conic a, b, c, d opacity, d r, g, b),
+   PGS_BUF_TILES_TOUCHED (uint32 [n]).  Copies min(max_bytes, size) bytes, stores the full size in
+   *bytes, synchronises. */
+#define PGS_BUF_KEYS 0
+#define PGS_BUF_VALUES 1
+#define PGS_BUF_RANGES 2
+#define PGS_BUF_T_FINAL 3
+#define PGS_BUF_LAST 4
+#define PGS_BUF_GRAD2D 5
+#define PGS_BUF_TILES_TOUCHED 6
+int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64_t* bytes);
+
+/* Static description of an error code. */
+const char* pgs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POCKETGS_H */

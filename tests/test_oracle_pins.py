@@ -170,6 +170,26 @@ def test_stacked_gaussians_order_clamp_skip_and_stop():
     assert abs(out["T"][py, px] - T) < 1e-15
 
 
+def test_equal_depths_composite_in_canonical_order():
+    """Two Gaussians at exactly the same depth: the lower canonical index is in front."""
+    cam = axis_camera()
+    cols = np.array([[0.9, 0.1, 0.1], [0.1, 0.1, 0.9]])
+    lg = math.log(0.6 / 0.4)
+
+    def img(order):
+        g = make_gaussians([[0.0, 0.0], [0.0, 0.0], [4.0, 4.0]], [[math.log(0.06)] * 2] * 3,
+                           [[1.0] * 2, [0.0] * 2, [0.0] * 2, [0.0] * 2], [lg, lg],
+                           dc_for(cols[order]).T.reshape(3, 1, 2), 0)
+        return oracle.render(g, cam)["image"][:, 31, 31]
+
+    o = 1.0 / (1.0 + math.exp(-float(np.float32(lg))))
+    s = math.exp(float(np.float32(math.log(0.06))))
+    a = o * math.exp(-0.5 * 0.5 / ((cam.fx * s / 4.0) ** 2 + 0.3))
+    c = Y0 * dc_for(cols).astype(np.float32).astype(np.float64) + 0.5
+    assert np.allclose(img([0, 1]), a * c[0] + a * (1 - a) * c[1], atol=1e-13)
+    assert np.allclose(img([1, 0]), a * c[1] + a * (1 - a) * c[0], atol=1e-13)
+
+
 def test_alpha_clamp_at_099():
     cam = axis_camera()
     g = make_gaussians([[0.0], [0.0], [4.0]], [[math.log(0.5)]] * 3, [[1.0], [0], [0], [0]], [8.0],
@@ -341,6 +361,7 @@ def test_canonical_permutation_equivariance():
 @pytest.mark.parametrize("dims", [(128, 128), (100, 75)])
 def test_keys_and_ranges_match_brute_force(dims):
     g, cam, _ = S.tiny_scene(4, n=1500, width=dims[0], height=dims[1])
+    g.means[2, 1::7] = g.means[2, 0:-1:7][: len(g.means[2, 1::7])]  # exact depth ties
     keys, vals, ranges = oracle.keys(g, cam)
     p = oracle.project(g, cam)
     TX, TY = oracle.tiles(cam)
@@ -397,6 +418,7 @@ def _fd_scene():
     sh = np.zeros((3, 16, n))
     sh[:, 0] = dc_for(rng.uniform(0.2, 0.8, size=(3, n)))
     sh[:, 1:] = rng.normal(0, 0.08, size=(3, 15, n))
+    sh[0, 0, 2] = dc_for(-0.3)  # red of Gaussian 2 is clamped at 0: zero gradient through it
     return make_gaussians(means, ls, rng.normal(size=(4, n)), logits, sh, 3), cam
 
 
