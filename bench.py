@@ -1,0 +1,365 @@
+"""Training-step throughput of the GB300 rasterizer on the 500k-Gaussian, 1920x1080, SH3 workload.
+
+One step = render (project, bin, sort, composite) -> L1 loss -> backward (composite backward,
+projection backward) -> fused Adam, on one view, parameters and Adam state resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one independent replica per GPU (the path has no exchange step
+on one scene and one view; replicas only).  --impl reference times the CPU oracle (a plain FP64
+restatement of the method) on bounded crops of the same workload.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "train iters/sec (fwd+bwd+Adam) at 500k Gaussians 1080p; ms per stage; % roofline"
+UNIT = "it/s"
+N_GAUSS = 500_000
+WIDTH, HEIGHT, FOCAL = 1920, 1080, 1500.0
+SH_DEGREE = 3
+SEED = 3
+N_VIEWS = 8
+WORKLOAD = "surface scene, 500k Gaussians SH3, 1920x1080 fx=1500, L1 loss + Adam, one view per step"
+CROP = 256
+
+# per-unit algorithmic work (see the design notes: roofline per stage)
+BYTES_PER_GAUSS_PROJECT = 4 * (3 + 3 + 4 + 1 + 3 * (SH_DEGREE + 1) ** 2) + 64
+BYTES_PER_GAUSS_ADAM = 4 * 8 * (11 + 3 * (SH_DEGREE + 1) ** 2)
+BYTES_PER_GAUSS_PROJECT_BWD = 4 * (3 * (11 + 3 * (SH_DEGREE + 1) ** 2) + 9)
+FLOPS_ALPHA = 16        # one alpha evaluation of a (pixel, entry)
+FLOPS_FWD_COMP = 10     # compositing of an entry that passes the alpha test
+FLOPS_BWD_COMP = 38     # Eq. 8 + chain to the nine screen-space gradients of a composited entry
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload():
+    from paper_2601_17354_gb300 import synthetic as S
+    sc = S.surface_scene(SEED, N_GAUSS, SH_DEGREE, WIDTH, HEIGHT, FOCAL, n_cameras=64)
+    views = sc.train_views()[:N_VIEWS]
+    return sc, [sc.cameras[v] for v in views]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 6]
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[3 + k]})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][1]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[2]) for r in rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    # 128 FP32 lanes per SM, one fused multiply-add (2 flops) per lane per clock
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_step_seconds(sc, cam, crops, rng_seed=0):
+    """Oracle forward + backward on `crops` tile-aligned 256x256 crops of `cam` and one Adam step
+    over all parameters, extrapolated to one full-frame training step.  Returns (seconds per
+    full step, CPU seconds spent, description)."""
+    import oracle
+    from paper_2601_17354_gb300 import synthetic as S
+    g = sc.init
+    t0 = time.perf_counter()
+    oracle.project(g, cam)
+    t_proj = time.perf_counter() - t0
+    pix_time = 0.0
+    rng = np.random.default_rng(rng_seed)
+    TXc, TYc = (WIDTH - CROP) // 16, (HEIGHT - CROP) // 16
+    for c in range(crops):
+        x0 = 16 * int(rng.integers(TXc // 4, 3 * TXc // 4))
+        y0 = 16 * int(rng.integers(TYc // 4, 3 * TYc // 4))
+        cc = cam.crop(x0, y0, CROP, CROP)
+        t = time.perf_counter()
+        r = oracle.render(g, cc)
+        target = S.random_image(c, CROP, CROP, 0.0, 1.0)
+        _, grad, _ = oracle.l1(r["image"], target)
+        oracle.backward(g, cc, grad)
+        pix_time += time.perf_counter() - t - 2 * t_proj
+    rows = 11 + 3 * (SH_DEGREE + 1) ** 2
+    p = np.zeros(rows * g.n)
+    gr = np.random.default_rng(1).normal(size=p.size)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    t = time.perf_counter()
+    oracle.adam(p, gr, m, v, 1e-3, 1)
+    t_adam = time.perf_counter() - t
+    scale = (WIDTH * HEIGHT) / (CROP * CROP)
+    full = 2 * t_proj + (pix_time / crops) * scale + t_adam
+    spent = time.perf_counter() - t0
+    desc = (f"oracle forward+backward on {crops} tile-aligned {CROP}x{CROP} crops of one view "
+            f"(projection of all {N_GAUSS} Gaussians timed separately) + one FP64 Adam step over "
+            f"all parameters; per-pixel time scaled by {WIDTH}x{HEIGHT}/{CROP}^2")
+    return full, spent, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc, cams = make_workload()
+    for _ in range(args.warmup):
+        oracle_step_seconds(sc, cams[0], 1)
+    times = []
+    spent = 0.0
+    desc = ""
+    for k in range(args.steps):
+        full, s, desc = oracle_step_seconds(sc, cams[k % len(cams)], 1, rng_seed=k)
+        times.append(full)
+        spent += s
+    t = float(np.mean(times))
+    val = 1.0 / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS,
+                                        "width": WIDTH, "height": HEIGHT, "sh_degree": SH_DEGREE},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2601_17354_gb300 import _lib as L
+    from paper_2601_17354_gb300 import rasterizer as R
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    sc, cams = make_workload()
+    # ground-truth targets: the hidden GT Gaussians rendered by this renderer (data, not a check)
+    gt_rast = R.Rasterizer()
+    gt_buf = R.GaussianBuffer.from_arrays(sc.gt)
+    targets = [gt_rast.render(gt_buf, c).clone() for c in cams]
+    L.check(gt_rast.status()[0], "gt render")
+    # pair capacity: measured on the trainable start over the bench views, with headroom
+    probe = R.Rasterizer()
+    init = R.GaussianBuffer.from_arrays(sc.init)
+    pmax = 0
+    for c in cams:
+        probe.render(init, c)
+        pmax = max(pmax, probe.check_status())
+    del probe, gt_rast, gt_buf
+    rast = R.Rasterizer(pair_capacity=int(pmax * 1.5) + 4096)
+    rast.reserve(N_GAUSS, WIDTH, HEIGHT, int(pmax * 1.5) + 4096)
+    params = init.clone()
+    tr = R.Trainer(params, rast)
+    stream = rast.stream
+
+    def step(k):
+        tr.step(cams[k % len(cams)], targets[k % len(targets)])
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    L.check(rast.status()[0], "warm-up")
+    # per-pixel evaluation counts of one view, for the compositing rooflines
+    rast.render(params, cams[0])
+    last = rast.read_buffer(L.PGS_BUF_LAST).astype(np.int64)
+    ncomp = rast.read_buffer(L.PGS_BUF_NCOMP).astype(np.int64)
+    e_eval, e_comp = int(last.sum()), int(ncomp.sum())
+
+    # ---------------- timed region (device) ----------------
+    rast.stage_times()  # reset
+    rast.profile(True)
+    launches0 = rast.launch_count()
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = rast.launch_count() - launches0
+    rast.profile(False)
+    stages = rast.stage_times()
+    code, pairs = rast.status()
+    L.check(code, "timed region")
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    host_targets = [t.cpu().pin_memory() for t in targets]
+    dev_target = torch.empty_like(targets[0])
+    loss_host = torch.zeros(2, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        dev_target.copy_(host_targets[k % len(host_targets)], non_blocking=True)
+        loss = tr.step(cams[k % len(cams)], dev_target)
+        loss_host.copy_(loss, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(targets[0].numel() * 4),
+           "d2h_bytes_per_step": int(loss_host.numel() * 4)}
+
+    # ---------------- rooflines ----------------
+    peaks, src = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    stage_ms = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in stages.items()}
+    n_vis = int(np.count_nonzero(rast.read_buffer(L.PGS_BUF_TILES_TOUCHED)))
+    roof = {}
+    hbm = float(peaks["hbm_gbs"])
+    for k, t in stage_ms.items():
+        if t <= 0:
+            continue
+        if k == "project":
+            roof[k] = ("hbm", N_GAUSS * BYTES_PER_GAUSS_PROJECT / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "adam":
+            roof[k] = ("hbm", N_GAUSS * BYTES_PER_GAUSS_ADAM / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "project_bwd":
+            roof[k] = ("hbm", n_vis * BYTES_PER_GAUSS_PROJECT_BWD / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "loss":
+            roof[k] = ("hbm", 3 * WIDTH * HEIGHT * 12 / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "composite_fwd":
+            fl = e_eval * FLOPS_ALPHA + e_comp * FLOPS_FWD_COMP
+            roof[k] = ("alu", fl / (t * 1e-3) / 1e12, fp32_peak_tflops(sm_count, mhz), "TFLOP/s")
+        elif k == "composite_bwd":
+            fl = e_eval * FLOPS_ALPHA + e_comp * FLOPS_BWD_COMP
+            roof[k] = ("alu", fl / (t * 1e-3) / 1e12, fp32_peak_tflops(sm_count, mhz), "TFLOP/s")
+        elif k == "sort":
+            passes = math.ceil((32 + math.ceil(math.log2((WIDTH // 16 + 1) * (HEIGHT // 16 + 1)))) / 8)
+            roof[k] = ("hbm", pairs * 24 / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "bin":
+            roof[k] = ("hbm", (pairs * 12 + N_GAUSS * 16) / (t * 1e-3) / 1e9, hbm, "GB/s")
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    b, a, pk, u = roof[dom]
+    roofline = {"kernel": dom, "bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk,
+                "traffic": None, "peak_source": f"{src}" if b == "hbm" else
+                f"{sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                   "sh_degree": SH_DEGREE, "views": len(cams), "pairs": int(pairs),
+                   "l2": "inputs larger than L2 (parameters + Adam state + gradients 472 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "roofline": roofline,
+        "stage_roofline": {k: {"bound": v[0], "achieved": round(v[1], 2), "peak": round(v[2], 1),
+                               "unit": v[3], "frac": round(v[1] / v[2], 4)} for k, v in roof.items()},
+        "evaluations": {"alpha": e_eval, "composited": e_comp},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full, spent, desc = oracle_step_seconds(sc, cams[0], 5)
+        out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": desc, "cpu_seconds": round(spent, 1)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

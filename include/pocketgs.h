@@ -130,7 +130,8 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
    which: PGS_BUF_KEYS (uint64 [P], sorted), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
    (uint32 [tiles][2]), PGS_BUF_T_FINAL (float [H][W]), PGS_BUF_LAST (uint32 [H][W]),
    PGS_BUF_GRAD2D (float [9][n]: du, dv, d conic a, b, c, d opacity, d r, g, b),
-   PGS_BUF_TILES_TOUCHED (uint32 [n]).  Copies min(max_bytes, size) bytes, stores the full size in
+   PGS_BUF_TILES_TOUCHED (uint32 [n]), PGS_BUF_NCOMP (uint32 [H][W], entries composited per
+   pixel).  Copies min(max_bytes, size) bytes, stores the full size in
    *bytes, synchronises. */
 #define PGS_BUF_KEYS 0
 #define PGS_BUF_VALUES 1
@@ -139,7 +140,30 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
 #define PGS_BUF_LAST 4
 #define PGS_BUF_GRAD2D 5
 #define PGS_BUF_TILES_TOUCHED 6
+#define PGS_BUF_NCOMP 7
 int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64_t* bytes);
+
+/* Per-stage device time accounting.  pgs_profile(ctx, 1) makes every later call record CUDA
+   events on the context's stream at its stage boundaries; pgs_stage_times synchronises, writes
+   the total milliseconds and the number of timed executions of each stage since the previous
+   read into ms[PGS_NUM_STAGES] and counts[PGS_NUM_STAGES], and resets the accumulators.
+   Stages: projection (K1), binning = scan + key emission (K2, K3), sort = radix sort + tile
+   ranges (K4, K5), compositing forward (K6), loss (K7), compositing backward (K8), projection
+   backward (K9), Adam (K10).  pgs_profile(ctx, 0) stops recording. */
+#define PGS_STAGE_PROJECT 0
+#define PGS_STAGE_BIN 1
+#define PGS_STAGE_SORT 2
+#define PGS_STAGE_COMPOSITE_FWD 3
+#define PGS_STAGE_LOSS 4
+#define PGS_STAGE_COMPOSITE_BWD 5
+#define PGS_STAGE_PROJECT_BWD 6
+#define PGS_STAGE_ADAM 7
+#define PGS_NUM_STAGES 8
+int pgs_profile(pgs_ctx* ctx, int enable);
+int pgs_stage_times(pgs_ctx* ctx, double* ms, int64_t* counts);
+
+/* Number of kernels this context has launched since it was created (host-side count). */
+int64_t pgs_launch_count(const pgs_ctx* ctx);
 
 /* Static description of an error code. */
 const char* pgs_strerror(int code);

@@ -1,0 +1,111 @@
+"""ctypes binding of libpocketgs.so (the C ABI declared in include/pocketgs.h).
+
+Argument marshalling only: every step of the rasterizer runs in the library's CUDA kernels.
+Loading fails loudly if the library cannot be built or found; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+PGS_OK = 0
+PGS_ERR_INVALID_ARG = -1
+PGS_ERR_NO_RENDER = -2
+PGS_ERR_CAPACITY = -3
+PGS_ERR_NONFINITE = -4
+PGS_ERR_CUDA = -6
+PGS_ERR_OOM = -7
+
+PGS_BUF_KEYS = 0
+PGS_BUF_VALUES = 1
+PGS_BUF_RANGES = 2
+PGS_BUF_T_FINAL = 3
+PGS_BUF_LAST = 4
+PGS_BUF_GRAD2D = 5
+PGS_BUF_TILES_TOUCHED = 6
+PGS_BUF_NCOMP = 7
+
+PGS_STAGES = ["project", "bin", "sort", "composite_fwd", "loss", "composite_bwd", "project_bwd",
+              "adam"]
+
+EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_l1",
+            "pgs_backward", "pgs_step", "pgs_status", "pgs_read_buffer", "pgs_strerror",
+            "pgs_profile", "pgs_stage_times", "pgs_launch_count"]
+
+
+class PgsCamera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("viewmat", C.c_float * 12),
+                ("near_z", C.c_float), ("bg", C.c_float * 3)]
+
+
+class PgsGaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad_", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class PgsConfig(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("reserved_", C.c_int32), ("pair_capacity", C.c_int64),
+                ("adam_b1", C.c_float), ("adam_b2", C.c_float), ("adam_eps", C.c_float),
+                ("lr", C.c_float * 6)]
+
+
+class PgsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().pgs_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libpocketgs.so")
+
+
+def lib():
+    """Load libpocketgs.so, building it with nvcc first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            path = _build.build()
+            L = C.CDLL(path)
+            P, I, I64 = C.c_void_p, C.c_int, C.c_int64
+            L.pgs_create.argtypes = [C.POINTER(P), C.POINTER(PgsConfig), P]
+            L.pgs_create.restype = I
+            L.pgs_destroy.argtypes = [P]
+            L.pgs_destroy.restype = None
+            L.pgs_reserve.argtypes = [P, I64, C.c_int32, C.c_int32, I64]
+            L.pgs_reserve.restype = I
+            L.pgs_render.argtypes = [P, C.POINTER(PgsGaussians), C.POINTER(PgsCamera), P]
+            L.pgs_render.restype = I
+            L.pgs_loss_l1.argtypes = [P, P, P, I64, P, P]
+            L.pgs_loss_l1.restype = I
+            L.pgs_backward.argtypes = [P, P, C.POINTER(PgsGaussians)]
+            L.pgs_backward.restype = I
+            L.pgs_step.argtypes = [P] + [C.POINTER(PgsGaussians)] * 4 + [I64]
+            L.pgs_step.restype = I
+            L.pgs_status.argtypes = [P, C.POINTER(I64)]
+            L.pgs_status.restype = I
+            L.pgs_read_buffer.argtypes = [P, I, P, I64, C.POINTER(I64)]
+            L.pgs_read_buffer.restype = I
+            L.pgs_profile.argtypes = [P, I]
+            L.pgs_profile.restype = I
+            L.pgs_stage_times.argtypes = [P, P, P]
+            L.pgs_stage_times.restype = I
+            L.pgs_launch_count.argtypes = [P]
+            L.pgs_launch_count.restype = I64
+            L.pgs_strerror.argtypes = [I]
+            L.pgs_strerror.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def check(code: int, where: str) -> None:
+    if code != PGS_OK:
+        raise PgsError(code, where)

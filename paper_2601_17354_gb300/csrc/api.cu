@@ -1,0 +1,397 @@
+// C ABI of libpocketgs: context, scratch arenas, and the render / loss / backward / step calls.
+//
+// Scratch lives in two device arenas owned by the context: one sized by (Gaussians, pixels,
+// tiles) and one by the pair capacity, so growing the pair buffers never disturbs projected
+// Gaussians of the render in flight.  Buffers are carved at 256-byte alignment.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pgs_internal.cuh"
+
+using namespace pgs;
+
+struct pgs_ctx {
+    pgs_config cfg;
+    cudaStream_t stream = nullptr;
+    Scratch sc;
+    void* arena_g = nullptr;
+    void* arena_p = nullptr;
+    int64_t cap_n = -1, cap_pixels = -1, cap_tiles = -1, cap_pairs = 0;
+    bool grow_pairs = false;
+    // last render
+    bool has_render = false;
+    int64_t n = 0;
+    int TX = 0, TY = 0, buf = 0;
+    pgs_camera cam{};
+    pgs_gaussians params{};
+    // instrumentation
+    int64_t launches = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;       // pool, used in order
+    size_t next_event = 0;
+    struct Span { int stage; size_t a, b; };
+    std::vector<Span> spans;
+};
+
+namespace {
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += align256(sizeof(T) * (count ? count : 1));
+        return p;
+    }
+};
+
+// Layout of the (Gaussians, pixels, tiles) arena; with base == nullptr only measures.
+size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles) {
+    Carver c{base};
+    const int64_t nb = (n + kProjBlock - 1) / kProjBlock;
+    sc.xyo = c.take<float4>(n);
+    sc.conic = c.take<float4>(n);
+    sc.rgb = c.take<float4>(n);
+    sc.depth_bits = c.take<uint32_t>(n);
+    sc.rect = c.take<uint2>(n);
+    sc.touched = c.take<uint32_t>(n);
+    sc.block_sums = c.take<uint32_t>(nb);
+    sc.block_offsets = c.take<unsigned long long>(nb);
+    sc.grad2d = c.take<float>(9 * n);
+    sc.ranges = c.take<uint2>(tiles);
+    sc.T_final = c.take<float>(pixels);
+    sc.last = c.take<uint32_t>(pixels);
+    sc.ncomp = c.take<uint32_t>(pixels);
+    sc.status = c.take<int32_t>(1);
+    sc.pair_count = c.take<unsigned long long>(1);
+    sc.sort_blocks = c.take<uint32_t>(1);
+    sc.digit_totals = c.take<uint32_t>(kMaxPasses * kRadix);
+    sc.loss_partials = c.take<float>(2 * kLossBlocks);
+    sc.loss_ticket = c.take<uint32_t>(1);
+    return c.off;
+}
+
+size_t carve_p(Scratch& sc, char* base, int64_t pairs) {
+    Carver c{base};
+    const int64_t sb = (pairs + kSortTile - 1) / kSortTile;
+    sc.keys[0] = c.take<unsigned long long>(pairs);
+    sc.keys[1] = c.take<unsigned long long>(pairs);
+    sc.vals[0] = c.take<uint32_t>(pairs);
+    sc.vals[1] = c.take<uint32_t>(pairs);
+    sc.sort_hist = c.take<uint32_t>((size_t)kRadix * (sb ? sb : 1));
+    return c.off;
+}
+
+constexpr size_t kEventPool = 8192;
+
+// Record one event on the stream if profiling; returns its pool index or SIZE_MAX.
+size_t mark(pgs_ctx* ctx) {
+    if (!ctx->profiling) return SIZE_MAX;
+    if (ctx->events.empty()) {
+        ctx->events.resize(kEventPool);
+        for (auto& e : ctx->events) cudaEventCreate(&e);
+    }
+    if (ctx->next_event >= ctx->events.size()) return SIZE_MAX;
+    const size_t i = ctx->next_event++;
+    cudaEventRecord(ctx->events[i], ctx->stream);
+    return i;
+}
+
+void span(pgs_ctx* ctx, int stage, size_t a, size_t b) {
+    if (a != SIZE_MAX && b != SIZE_MAX) ctx->spans.push_back({stage, a, b});
+}
+
+int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return PGS_OK;
+    if (e == cudaErrorMemoryAllocation) return PGS_ERR_OOM;
+    return PGS_ERR_CUDA;
+}
+
+int reserve_g(pgs_ctx* ctx, int64_t n, int64_t pixels, int64_t tiles) {
+    if (n <= ctx->cap_n && pixels <= ctx->cap_pixels && tiles <= ctx->cap_tiles) return PGS_OK;
+    n = n > ctx->cap_n ? n : ctx->cap_n;
+    pixels = pixels > ctx->cap_pixels ? pixels : ctx->cap_pixels;
+    tiles = tiles > ctx->cap_tiles ? tiles : ctx->cap_tiles;
+    Scratch tmp = ctx->sc;
+    const size_t bytes = carve_g(tmp, nullptr, n, pixels, tiles);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (ctx->arena_g) cudaFree(ctx->arena_g);
+    ctx->arena_g = nullptr;
+    ctx->cap_n = ctx->cap_pixels = ctx->cap_tiles = -1;
+    e = cudaMalloc(&ctx->arena_g, bytes);
+    if (e != cudaSuccess) {
+        ctx->arena_g = nullptr;
+        return cuda_err(e);
+    }
+    carve_g(ctx->sc, static_cast<char*>(ctx->arena_g), n, pixels, tiles);
+    e = cudaMemsetAsync(ctx->arena_g, 0, bytes, ctx->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    ctx->cap_n = n;
+    ctx->cap_pixels = pixels;
+    ctx->cap_tiles = tiles;
+    ctx->has_render = false;
+    return PGS_OK;
+}
+
+int reserve_p(pgs_ctx* ctx, int64_t pairs) {
+    if (pairs <= ctx->cap_pairs) return PGS_OK;
+    Scratch tmp = ctx->sc;
+    const size_t bytes = carve_p(tmp, nullptr, pairs);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (ctx->arena_p) cudaFree(ctx->arena_p);
+    ctx->arena_p = nullptr;
+    ctx->cap_pairs = 0;
+    e = cudaMalloc(&ctx->arena_p, bytes);
+    if (e != cudaSuccess) {
+        ctx->arena_p = nullptr;
+        return cuda_err(e);
+    }
+    carve_p(ctx->sc, static_cast<char*>(ctx->arena_p), pairs);
+    ctx->cap_pairs = pairs;
+    ctx->has_render = false;
+    return PGS_OK;
+}
+
+bool valid_gaussians(const pgs_gaussians* g) {
+    if (!g || g->n < 0 || g->n >= (int64_t(1) << 32) || g->sh_degree < 0 || g->sh_degree > 3) return false;
+    if (g->n == 0) return true;
+    return g->means && g->log_scales && g->quats && g->opacity_logits && g->sh;
+}
+
+bool valid_camera(const pgs_camera* c) {
+    if (!c || c->width <= 0 || c->height <= 0) return false;
+    if (c->width > 65535 * kTile || c->height > 65535 * kTile) return false;
+    return c->fx > 0.f && c->fy > 0.f && c->near_z > 0.f;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pgs_strerror(int code) {
+    switch (code) {
+        case PGS_OK: return "ok";
+        case PGS_ERR_INVALID_ARG: return "invalid argument";
+        case PGS_ERR_NO_RENDER: return "backward without a preceding render on this context";
+        case PGS_ERR_CAPACITY: return "more (tile, Gaussian) pairs than the pair capacity";
+        case PGS_ERR_NONFINITE: return "non-finite parameter of a Gaussian";
+        case PGS_ERR_CUDA: return "CUDA runtime error";
+        case PGS_ERR_OOM: return "device allocation failed";
+        default: return "unknown error";
+    }
+}
+
+int pgs_create(pgs_ctx** out, const pgs_config* cfg, void* cuda_stream) {
+    if (!out) return PGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg || cfg->tile != kTile || cfg->pair_capacity < 0) return PGS_ERR_INVALID_ARG;
+    pgs_ctx* ctx = new (std::nothrow) pgs_ctx();
+    if (!ctx) return PGS_ERR_OOM;
+    ctx->cfg = *cfg;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->grow_pairs = cfg->pair_capacity == 0;
+    int rc = reserve_g(ctx, 1, 1, 1);
+    if (rc == PGS_OK) rc = reserve_p(ctx, cfg->pair_capacity > 0 ? cfg->pair_capacity : (1 << 20));
+    if (rc != PGS_OK) {
+        pgs_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return PGS_OK;
+}
+
+void pgs_destroy(pgs_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->events) cudaEventDestroy(e);
+    if (ctx->arena_g) cudaFree(ctx->arena_g);
+    if (ctx->arena_p) cudaFree(ctx->arena_p);
+    delete ctx;
+}
+
+int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t pair_capacity) {
+    if (!ctx || n < 0 || width < 0 || height < 0 || pair_capacity < 0) return PGS_ERR_INVALID_ARG;
+    const int64_t TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    int rc = reserve_g(ctx, n, (int64_t)width * height, TX * TY);
+    if (rc == PGS_OK) rc = reserve_p(ctx, pair_capacity);
+    return rc;
+}
+
+int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out) {
+    if (!ctx || !valid_gaussians(params) || !valid_camera(cam) || !image_out) return PGS_ERR_INVALID_ARG;
+    const int TX = (cam->width + kTile - 1) / kTile, TY = (cam->height + kTile - 1) / kTile;
+    const int64_t tiles = (int64_t)TX * TY, pixels = (int64_t)cam->width * cam->height;
+    int rc = reserve_g(ctx, params->n, pixels, tiles);
+    if (rc != PGS_OK) return rc;
+    cudaStream_t s = ctx->stream;
+    ctx->has_render = false;
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_project_fwd(*params, *cam, TX, TY, ctx->sc, s);
+    const size_t e1 = mark(ctx);
+    ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, ctx->sc, s);
+    if (ctx->grow_pairs) {
+        unsigned long long P = 0;
+        cudaError_t e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_err(e);
+        if ((int64_t)P > ctx->cap_pairs) {
+            // grow with headroom, clear the overflow flag, and emit again
+            rc = reserve_p(ctx, (int64_t)(P + P / 4 + 1024));
+            if (rc != PGS_OK) return rc;
+            int32_t st = 0;
+            e = cudaMemcpyAsync(&st, ctx->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_err(e);
+            st &= ~kStatusCapacity;
+            e = cudaMemcpyAsync(ctx->sc.status, &st, sizeof(st), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_err(e);
+            ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, ctx->sc, s);
+        }
+    }
+    const size_t e2 = mark(ctx);
+    ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
+    const size_t e3 = mark(ctx);
+    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, ctx->sc, image_out, s);
+    const size_t e4 = mark(ctx);
+    span(ctx, PGS_STAGE_PROJECT, e0, e1);
+    span(ctx, PGS_STAGE_BIN, e1, e2);
+    span(ctx, PGS_STAGE_SORT, e2, e3);
+    span(ctx, PGS_STAGE_COMPOSITE_FWD, e3, e4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e);
+    ctx->has_render = true;
+    ctx->n = params->n;
+    ctx->TX = TX;
+    ctx->TY = TY;
+    ctx->cam = *cam;
+    ctx->params = *params;
+    return PGS_OK;
+}
+
+int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,
+                float* loss_out) {
+    if (!ctx || !image || !target || !dL_dimage || !loss_out || n <= 0) return PGS_ERR_INVALID_ARG;
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_loss_l1(image, target, n, dL_dimage, loss_out, ctx->sc, ctx->stream);
+    span(ctx, PGS_STAGE_LOSS, e0, mark(ctx));
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
+    if (!ctx || !dL_dimage || !valid_gaussians(grads)) return PGS_ERR_INVALID_ARG;
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    if (grads->n != ctx->n || grads->sh_degree != ctx->params.sh_degree) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = ctx->stream;
+    if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s);
+    const size_t e1 = mark(ctx);
+    ctx->launches += launch_project_bwd(ctx->params, ctx->cam, ctx->sc, *grads, s);
+    const size_t e2 = mark(ctx);
+    span(ctx, PGS_STAGE_COMPOSITE_BWD, e0, e1);
+    span(ctx, PGS_STAGE_PROJECT_BWD, e1, e2);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_step(pgs_ctx* ctx, pgs_gaussians* params, pgs_gaussians* grads, pgs_gaussians* m,
+             pgs_gaussians* v, int64_t t) {
+    if (!ctx || !valid_gaussians(params) || !valid_gaussians(grads) || !valid_gaussians(m) ||
+        !valid_gaussians(v) || t < 1)
+        return PGS_ERR_INVALID_ARG;
+    const pgs_gaussians* all[3] = {grads, m, v};
+    for (auto* q : all)
+        if (q->n != params->n || q->sh_degree != params->sh_degree) return PGS_ERR_INVALID_ARG;
+    if (params->n == 0) return PGS_OK;
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_adam(*params, *grads, *m, *v, ctx->cfg.lr, ctx->cfg.adam_b1,
+                                 ctx->cfg.adam_b2, ctx->cfg.adam_eps, t, ctx->stream);
+    span(ctx, PGS_STAGE_ADAM, e0, mark(ctx));
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
+    if (!ctx) return PGS_ERR_INVALID_ARG;
+    int32_t st = 0;
+    unsigned long long P = 0;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(&st, ctx->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sc.status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (pairs_needed) *pairs_needed = (int64_t)P;
+    if (st & kStatusCapacity) return PGS_ERR_CAPACITY;
+    if (st & kStatusNonfinite) return PGS_ERR_NONFINITE;
+    return PGS_OK;
+}
+
+int pgs_profile(pgs_ctx* ctx, int enable) {
+    if (!ctx) return PGS_ERR_INVALID_ARG;
+    ctx->profiling = enable != 0;
+    return PGS_OK;
+}
+
+int pgs_stage_times(pgs_ctx* ctx, double* ms, int64_t* counts) {
+    if (!ctx || !ms || !counts) return PGS_ERR_INVALID_ARG;
+    for (int k = 0; k < PGS_NUM_STAGES; ++k) {
+        ms[k] = 0.0;
+        counts[k] = 0;
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    for (const auto& sp : ctx->spans) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ctx->events[sp.a], ctx->events[sp.b]);
+        if (e != cudaSuccess) return cuda_err(e);
+        ms[sp.stage] += t;
+        counts[sp.stage] += 1;
+    }
+    ctx->spans.clear();
+    ctx->next_event = 0;
+    return PGS_OK;
+}
+
+int64_t pgs_launch_count(const pgs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64_t* bytes) {
+    if (!ctx || max_bytes < 0) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = ctx->stream;
+    unsigned long long P = 0;
+    cudaError_t e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    const int64_t kept = (int64_t)P < ctx->cap_pairs ? (int64_t)P : ctx->cap_pairs;
+    const int64_t pixels = (int64_t)ctx->cam.width * ctx->cam.height;
+    const void* src = nullptr;
+    int64_t size = 0;
+    switch (which) {
+        case PGS_BUF_KEYS: src = ctx->sc.keys[ctx->buf]; size = 8 * kept; break;
+        case PGS_BUF_VALUES: src = ctx->sc.vals[ctx->buf]; size = 4 * kept; break;
+        case PGS_BUF_RANGES: src = ctx->sc.ranges; size = 8 * (int64_t)ctx->TX * ctx->TY; break;
+        case PGS_BUF_T_FINAL: src = ctx->sc.T_final; size = 4 * pixels; break;
+        case PGS_BUF_LAST: src = ctx->sc.last; size = 4 * pixels; break;
+        case PGS_BUF_GRAD2D: src = ctx->sc.grad2d; size = 36 * ctx->n; break;
+        case PGS_BUF_TILES_TOUCHED: src = ctx->sc.touched; size = 4 * ctx->n; break;
+        case PGS_BUF_NCOMP: src = ctx->sc.ncomp; size = 4 * pixels; break;
+        default: return PGS_ERR_INVALID_ARG;
+    }
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    if (bytes) *bytes = size;
+    const int64_t cp = size < max_bytes ? size : max_bytes;
+    if (cp > 0 && dst) {
+        e = cudaMemcpyAsync(dst, src, (size_t)cp, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    return PGS_OK;
+}
+
+}  // extern "C"

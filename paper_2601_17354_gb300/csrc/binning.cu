@@ -1,0 +1,347 @@
+// K2 scan, K3 key emission, K4 radix sort, K5 tile ranges.
+//
+// The sorted (tile | depth) keys carry the canonical index as their value: this is the
+// permutation pi of Eq. 10 ("a GPU sort yields a permutation mapping sorted index i to canonical
+// index pi(i)").  Parameters are never reordered; the compositing kernels gather by pi and the
+// backward scatters gradients to pi (index-mapped gradient scattering).
+//
+// key = (tile << 32) | float bits of the camera depth (depth > near > 0, so the bits order like
+// the depths); equal keys keep emission order (canonical order), so the sort is the stable sort
+// of the pairs.  The number of pairs is known only on the device: every kernel reads it from the
+// context's pair counter, and pairs beyond the capacity are not written (the status word records
+// the overflow), so no host synchronisation sits between projection and compositing.
+//
+// The radix sort is least-significant-digit first, 8-bit digits, over the bits that can be
+// non-zero (32 depth bits + ceil(log2 tiles) tile bits).  Each pass: per-CTA digit histogram,
+// per-digit scan across CTAs (digit totals come from one up-front histogram of all passes),
+// and a stable scatter that ranks keys inside a CTA with warp match-any (no inter-CTA waiting).
+#include "pgs_internal.cuh"
+
+namespace pgs {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+static_assert(kSortThreads == kRadix, "one thread per digit in the sort kernels");
+
+// ---------------------------------------------------------------------------------------------
+// K2: exclusive scan of the per-CTA tile counts -> pair offsets, total pair count, capacity check
+// ---------------------------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int idx = base + threadIdx.x;
+        unsigned long long v = idx < nb ? sc.block_sums[idx] : 0ull;
+        unsigned long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+            unsigned long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            s_warp[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        if (idx < nb) sc.block_offsets[idx] = carry + s_warp[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long P = s_carry;
+        *sc.pair_count = P;
+        const unsigned long long kept = P < (unsigned long long)capacity ? P : (unsigned long long)capacity;
+        *sc.sort_blocks = (uint32_t)((kept + kSortTile - 1) / kSortTile);
+        if (P > (unsigned long long)capacity) atomicOr(sc.status, kStatusCapacity);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K3: emit the pairs of one CTA's Gaussians, one output pair per thread step (load-balanced by a
+// binary search over the CTA's scanned counts), Gaussians in canonical order, tiles row-major
+// inside each rectangle.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kProjBlock)
+k_emit(int64_t n, int TX, int64_t capacity, Scratch sc) {
+    __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of counts
+    __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock], s_depth[kProjBlock];
+    __shared__ uint32_t s_warp[kProjBlock / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
+    uint32_t cnt = 0;
+    if (i < n) cnt = sc.touched[i];
+    if (cnt) {
+        const uint2 r = sc.rect[i];
+        s_x0[t] = r.x & 0xffffu;
+        s_y0[t] = r.x >> 16;
+        s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
+        s_depth[t] = sc.depth_bits[i];
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kProjBlock / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, wi, o);
+            if (lane >= o) wi += v;
+        }
+        if (lane < kProjBlock / 32) s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    s_end[t] = incl + s_warp[warp];
+    __syncthreads();
+    const uint32_t total = s_end[kProjBlock - 1];
+    const unsigned long long base = sc.block_offsets[blockIdx.x];
+    for (uint32_t k = t; k < total; k += kProjBlock) {
+        // first j with s_end[j] > k
+        int lo = 0, hi = kProjBlock - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_end[mid] > k) hi = mid;
+            else lo = mid + 1;
+        }
+        const uint32_t local = k - (lo ? s_end[lo - 1] : 0u);  // pair index inside Gaussian lo
+        const uint32_t w = s_w[lo];
+        const uint32_t dy = local / w, dx = local - dy * w;
+        const uint32_t tile = (s_y0[lo] + dy) * (uint32_t)TX + s_x0[lo] + dx;
+        const unsigned long long pos = base + k;
+        if (pos < (unsigned long long)capacity) {
+            sc.keys[0][pos] = ((unsigned long long)tile << 32) | s_depth[lo];
+            sc.vals[0][pos] = (uint32_t)((int64_t)blockIdx.x * kProjBlock + lo);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K4: radix sort
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t kept_pairs(const Scratch& sc, int64_t capacity) {
+    const unsigned long long P = *sc.pair_count;
+    return P < (unsigned long long)capacity ? P : (unsigned long long)capacity;
+}
+
+// digit totals of every pass in one read of the keys
+__global__ void __launch_bounds__(kSortThreads)
+k_digit_totals(int64_t capacity, int passes, const unsigned long long* __restrict__ keys, Scratch sc) {
+    __shared__ uint32_t h[kMaxPasses][kRadix];
+    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const uint64_t P = kept_pairs(sc, capacity);
+    for (uint64_t k = (uint64_t)blockIdx.x * kSortThreads + threadIdx.x; k < P;
+         k += (uint64_t)gridDim.x * kSortThreads) {
+        const unsigned long long key = keys[k];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < passes * kRadix; k += kSortThreads) {
+        const uint32_t v = (&h[0][0])[k];
+        if (v) atomicAdd(&sc.digit_totals[k], v);
+    }
+}
+
+// per-CTA histogram of one digit
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_hist(int64_t capacity, int shift, int sb_max, const unsigned long long* __restrict__ keys, Scratch sc) {
+    const uint32_t nblk = *sc.sort_blocks;
+    if (blockIdx.x >= nblk) return;
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;  // kSortThreads == kRadix
+    __syncthreads();
+    const uint64_t P = kept_pairs(sc, capacity);
+    const uint64_t begin = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t end = begin + kSortTile < P ? begin + kSortTile : P;
+    for (uint64_t k = begin + threadIdx.x; k < end; k += kSortThreads)
+        atomicAdd(&h[(keys[k] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x] = h[threadIdx.x];
+}
+
+// one CTA per digit: exclusive scan of that digit's per-CTA counts, offset by the total of all
+// smaller digits; in place (counts -> scatter offsets)
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_rowscan(int pass, int sb_max, Scratch sc) {
+    const int d = blockIdx.x;
+    const uint32_t nblk = *sc.sort_blocks;
+    __shared__ uint32_t s_warp[kSortThreads / 32];
+    __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        // total of digits < d
+        const uint32_t* tot = sc.digit_totals + pass * kRadix;
+        uint32_t acc = 0;
+        for (int k = lane; k < d; k += 32) acc += tot[k];
+        acc = __reduce_add_sync(kFull, acc);
+        if (lane == 0) s_carry = acc;
+    }
+    __syncthreads();
+    uint32_t* row = sc.sort_hist + (size_t)d * sb_max;
+    for (uint32_t base = 0; base < nblk; base += kSortThreads) {
+        const uint32_t idx = base + threadIdx.x;
+        const uint32_t v = idx < nblk ? row[idx] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < kSortThreads / 32 ? s_warp[lane] : 0u;
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < kSortThreads / 32) s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        if (idx < nblk) row[idx] = carry + s_warp[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == kSortThreads - 1) s_carry = carry + s_warp[warp] + incl;
+        __syncthreads();
+    }
+}
+
+// stable scatter of one CTA's keys by one digit
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kWarpItems = kSortTile / kSortWarps;  // contiguous keys per warp
+constexpr int kRounds = kWarpItems / 32;            // == kSortItems
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long* __restrict__ kin,
+               const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
+               uint32_t* __restrict__ vout, Scratch sc) {
+    const uint32_t nblk = *sc.sort_blocks;
+    if (blockIdx.x >= nblk) return;
+    __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
+    __shared__ uint32_t s_off[kRadix];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
+    s_off[threadIdx.x] = sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x];
+    __syncthreads();
+    const uint64_t P = kept_pairs(sc, capacity);
+    const uint64_t wbase = (uint64_t)blockIdx.x * kSortTile + (uint64_t)warp * kWarpItems;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long key[kRounds];
+    uint32_t val[kRounds];
+    uint32_t rank[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        const bool valid = idx < P;
+        key[r] = valid ? kin[idx] : 0ull;
+        val[r] = valid ? vin[idx] : 0u;
+        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : 0x100u + lane;
+        const unsigned peers = __match_any_sync(kFull, d);
+        uint32_t before = 0;
+        if (valid) before = s_wh[warp][d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s_wh[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {   // warp prefixes per digit (thread = digit)
+        const int d = threadIdx.x;
+        uint32_t acc = s_off[d];
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = s_wh[w][d];
+            s_wh[w][d] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        if (idx < P) {
+            const uint32_t d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
+            const uint32_t dst = s_wh[warp][d] + rank[r];
+            kout[dst] = key[r];
+            vout[dst] = val[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K5: tile ranges [first, last + 1) from the sorted keys (ranges pre-zeroed)
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_ranges(int64_t capacity, const unsigned long long* __restrict__ keys, Scratch sc) {
+    const uint64_t P = kept_pairs(sc, capacity);
+    for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256) {
+        const uint32_t t = (uint32_t)(keys[k] >> 32);
+        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) sc.ranges[t].x = (uint32_t)k;
+        if (k == P - 1 || (uint32_t)(keys[k + 1] >> 32) != t) sc.ranges[t].y = (uint32_t)(k + 1);
+    }
+}
+
+}  // namespace
+
+int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cudaStream_t s) {
+    const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
+    k_scan_blocks<<<1, kScanThreads, 0, s>>>(nb, capacity, sc);
+    if (nb == 0) return 1;
+    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, sc);
+    return 2;
+}
+
+int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* out_buf) {
+    int tile_bits = 0;
+    while ((1ll << tile_bits) < (long long)tiles) ++tile_bits;
+    const int passes = (32 + tile_bits + kRadixBits - 1) / kRadixBits;
+    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
+    const int grid_stride_blocks = 152 * 8;
+    int buf = 0, launched = 0;
+    if (sb_max > 0) {
+        cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
+        k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, passes, sc.keys[0], sc);
+        launched += 1 + 3 * passes;
+        for (int p = 0; p < passes; ++p) {
+            const int shift = p * kRadixBits;
+            k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
+            k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
+            k_sort_scatter<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
+                                                           sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
+            buf ^= 1;
+        }
+    }
+    cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
+    if (sb_max > 0) {
+        k_ranges<<<grid_stride_blocks, 256, 0, s>>>(capacity, sc.keys[buf], sc);
+        ++launched;
+    }
+    *out_buf = buf;
+    return launched;
+}
+
+}  // namespace pgs

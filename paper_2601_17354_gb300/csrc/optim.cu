@@ -1,0 +1,178 @@
+// K7 L1 loss and K10 fused Adam.
+//
+// Adam (Kingma & Ba 2015) runs over every parameter group of the canonical buffer in one launch,
+// in canonical order, so the moments stay aligned with their parameters (Sec. III-C, "keeping
+// Adam states aligned with their parameters without CPU intervention"); it also zeroes the
+// gradients it consumed.
+#include "pgs_internal.cuh"
+
+namespace pgs {
+namespace {
+
+constexpr int kThreads = 256;
+
+// mean |x - y| and sum (x - y)^2 over n values, gradient sign(x - y) / n.  Partial sums per
+// CTA; the last CTA to finish (ticket counter) adds them in a fixed order, so the result does
+// not depend on scheduling.  No CTA waits for another.
+__global__ void __launch_bounds__(kThreads)
+k_loss_l1(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
+          float* __restrict__ grad, float* __restrict__ out, float* partials, uint32_t* ticket) {
+    const float inv_n = 1.0f / (float)n;
+    float l1 = 0.f, l2 = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
+        const float d = x[k] - y[k];
+        l1 += fabsf(d);
+        l2 = fmaf(d, d, l2);
+        grad[k] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+    }
+    __shared__ float s1[kThreads / 32], s2[kThreads / 32];
+    __shared__ bool s_last;
+    for (int o = 16; o > 0; o >>= 1) {
+        l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+        l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s1[threadIdx.x >> 5] = l1;
+        s2[threadIdx.x >> 5] = l2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            a += s1[w];
+            b += s2[w];
+        }
+        partials[blockIdx.x] = a;
+        partials[gridDim.x + blockIdx.x] = b;
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) {
+            a += (double)((volatile float*)partials)[k];
+            b += (double)((volatile float*)partials)[gridDim.x + k];
+        }
+        out[0] = (float)(a / (double)n);
+        out[1] = (float)b;
+        *ticket = 0;
+    }
+}
+
+struct AdamArgs {
+    float* p[5];
+    float* g[5];
+    float* m[5];
+    float* v[5];
+    float lr[6];
+    int64_t n;
+    int K;
+    float b1, b2, eps, bc1, bc2;
+};
+
+// row r of the (11 + 3K) x n parameter matrix -> group, row inside the group, learning rate
+__device__ __forceinline__ void row_of(const AdamArgs& a, int r, int& grp, int& sub, float& lr) {
+    if (r < 3) { grp = 0; sub = r; lr = a.lr[0]; }
+    else if (r < 6) { grp = 1; sub = r - 3; lr = a.lr[1]; }
+    else if (r < 10) { grp = 2; sub = r - 6; lr = a.lr[2]; }
+    else if (r == 10) { grp = 3; sub = 0; lr = a.lr[3]; }
+    else { grp = 4; sub = r - 11; lr = (sub % a.K) == 0 ? a.lr[4] : a.lr[5]; }
+}
+
+__device__ __forceinline__ void adam1(float& p, float& g, float& m, float& v, float lr,
+                                      const AdamArgs& a) {
+    m = a.b1 * m + (1.0f - a.b1) * g;
+    v = a.b2 * v + (1.0f - a.b2) * g * g;
+    const float mh = m / a.bc1, vh = v / a.bc2;
+    p -= lr * mh / (sqrtf(vh) + a.eps);
+    g = 0.0f;
+}
+
+// grid.y = row, grid.x x 4 threads' worth of float4 per row
+__global__ void __launch_bounds__(kThreads) k_adam_vec4(AdamArgs a) {
+    int grp, sub;
+    float lr;
+    row_of(a, blockIdx.y, grp, sub, lr);
+    const int64_t off = (int64_t)sub * a.n;
+    float4* P = reinterpret_cast<float4*>(a.p[grp] + off);
+    float4* Gd = reinterpret_cast<float4*>(a.g[grp] + off);
+    float4* M = reinterpret_cast<float4*>(a.m[grp] + off);
+    float4* V = reinterpret_cast<float4*>(a.v[grp] + off);
+    const int64_t n4 = a.n >> 2;
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n4; k += (int64_t)gridDim.x * kThreads) {
+        float4 p = P[k], g = Gd[k], m = M[k], v = V[k];
+        adam1(p.x, g.x, m.x, v.x, lr, a);
+        adam1(p.y, g.y, m.y, v.y, lr, a);
+        adam1(p.z, g.z, m.z, v.z, lr, a);
+        adam1(p.w, g.w, m.w, v.w, lr, a);
+        P[k] = p;
+        M[k] = m;
+        V[k] = v;
+        Gd[k] = g;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_adam_scalar(AdamArgs a) {
+    int grp, sub;
+    float lr;
+    row_of(a, blockIdx.y, grp, sub, lr);
+    const int64_t off = (int64_t)sub * a.n;
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < a.n; k += (int64_t)gridDim.x * kThreads) {
+        float p = a.p[grp][off + k], g = a.g[grp][off + k], m = a.m[grp][off + k], v = a.v[grp][off + k];
+        adam1(p, g, m, v, lr, a);
+        a.p[grp][off + k] = p;
+        a.m[grp][off + k] = m;
+        a.v[grp][off + k] = v;
+        a.g[grp][off + k] = g;
+    }
+}
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+}  // namespace
+
+int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
+                    float* loss_out, const Scratch& sc, cudaStream_t s) {
+    int blocks = (int)((n + kThreads * 8 - 1) / (kThreads * 8));
+    blocks = blocks < 1 ? 1 : (blocks > kLossBlocks ? kLossBlocks : blocks);
+    k_loss_l1<<<blocks, kThreads, 0, s>>>(image, target, n, grad, loss_out, sc.loss_partials,
+                                          sc.loss_ticket);
+    return 1;
+}
+
+int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussians& v,
+                 const float lr[6], float b1, float b2, float eps, int64_t t, cudaStream_t s) {
+    AdamArgs a;
+    pgs_gaussians* src[4] = {&p, &g, &m, &v};
+    float** dst[4] = {a.p, a.g, a.m, a.v};
+    bool vec = (p.n % 4) == 0;
+    for (int q = 0; q < 4; ++q) {
+        float* ptrs[5] = {src[q]->means, src[q]->log_scales, src[q]->quats, src[q]->opacity_logits, src[q]->sh};
+        for (int k = 0; k < 5; ++k) {
+            dst[q][k] = ptrs[k];
+            vec = vec && aligned16(ptrs[k]);
+        }
+    }
+    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    a.n = p.n;
+    a.K = sh_coeffs(p.sh_degree);
+    a.b1 = b1;
+    a.b2 = b2;
+    a.eps = eps;
+    a.bc1 = (float)(1.0 - pow((double)b1, (double)t));
+    a.bc2 = (float)(1.0 - pow((double)b2, (double)t));
+    const int rows = param_rows(p.sh_degree);
+    const int64_t work = vec ? (p.n >> 2) : p.n;
+    int64_t bx = (work + kThreads - 1) / kThreads;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    const dim3 grid((unsigned)bx, (unsigned)rows);
+    if (vec) k_adam_vec4<<<grid, kThreads, 0, s>>>(a);
+    else k_adam_scalar<<<grid, kThreads, 0, s>>>(a);
+    return 1;
+}
+
+}  // namespace pgs

@@ -1,0 +1,93 @@
+// Internal declarations of libpocketgs: the context, its device scratch, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pocketgs.h"
+
+namespace pgs {
+
+constexpr int kTile = 16;            // screen tile edge (pixels); one 16x16 tile per CTA
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kernels
+constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
+constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort CTA
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
+
+// device status word bits
+constexpr int32_t kStatusCapacity = 1;
+constexpr int32_t kStatusNonfinite = 2;
+
+// Per-Gaussian projected record read by the compositing kernels (gathered by canonical index).
+//   xyo   = (u, v, opacity, unused)   screen-space mean and opacity
+//   conic = (a, b, c, unused)         inverse 2-D covariance; power = -(a dx^2 + c dy^2)/2 - b dx dy
+//   rgb   = (r, g, b, unused)         view-dependent colour after the clamp at 0
+
+struct Scratch {
+    // per Gaussian
+    float4* xyo = nullptr;
+    float4* conic = nullptr;
+    float4* rgb = nullptr;
+    uint32_t* depth_bits = nullptr;
+    uint2* rect = nullptr;  // (x0 | y0 << 16, x1 | y1 << 16), tiles, half-open
+    uint32_t* touched = nullptr;
+    uint32_t* block_sums = nullptr;
+    unsigned long long* block_offsets = nullptr;
+    float* grad2d = nullptr;  // [9][n]
+    // per tile / pixel
+    uint2* ranges = nullptr;
+    float* T_final = nullptr;
+    uint32_t* last = nullptr;
+    uint32_t* ncomp = nullptr;  // entries composited per pixel
+    // small words
+    int32_t* status = nullptr;
+    unsigned long long* pair_count = nullptr;
+    uint32_t* sort_blocks = nullptr;  // sort CTAs with work in the current render
+    uint32_t* digit_totals = nullptr; // [kMaxPasses][kRadix]
+    float* loss_partials = nullptr;   // [2][kLossBlocks]
+    uint32_t* loss_ticket = nullptr;
+    // per pair (separate allocation, grows independently)
+    unsigned long long* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* sort_hist = nullptr;  // [kRadix][sort_blocks_max]
+};
+
+constexpr int kLossBlocks = 1024;
+
+// ---------------------------------------------------------------------------------------------
+// launchers (all asynchronous on `s`); each returns the number of kernels it launched
+// ---------------------------------------------------------------------------------------------
+
+// K1: project + cull + SH colour; writes the projected record, depth bits, tile rectangle,
+// tiles touched and the per-CTA sum of tiles touched.
+int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY,
+                        const Scratch& sc, cudaStream_t s);
+// K9: chain screen-space gradients (grad2d) to the parameters, added into grads.
+int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+                        pgs_gaussians& grads, cudaStream_t s);
+
+// K2/K3: scan of the per-CTA sums, pair count + capacity check, and key emission.
+int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cudaStream_t s);
+// K4/K5: radix sort of the pairs (returns which ping-pong buffer holds the result) and ranges.
+int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
+
+// K6/K8: compositing forward and backward (sorted values in buffer `buf`).
+int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, const Scratch& sc,
+                          float* image, cudaStream_t s);
+int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+                          const Scratch& sc, const float* dL_dimage, cudaStream_t s);
+
+// K7: L1 loss; K10: fused Adam over all parameter groups.
+int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
+                    float* loss_out, const Scratch& sc, cudaStream_t s);
+int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussians& v,
+                 const float lr[6], float b1, float b2, float eps, int64_t t, cudaStream_t s);
+
+__host__ __device__ inline int sh_coeffs(int degree) { return (degree + 1) * (degree + 1); }
+__host__ __device__ inline int param_rows(int degree) { return 11 + 3 * sh_coeffs(degree); }
+
+}  // namespace pgs

@@ -1,0 +1,453 @@
+// K1 project_fwd and K9 project_bwd: one thread per Gaussian over the planar SoA parameters.
+//
+// The canonical parameter buffer (mu, Sigma, c, alpha) of Fig. 2 / Sec. III-C is read in place;
+// nothing is reordered (the sorted view exists only as the key/value pairs, Eq. 10).
+//
+// Decision quantities (camera depth, screen position, 2-D covariance, radius, tile rectangle)
+// follow a prescribed fp32 operation order with every operation an explicit correctly rounded
+// intrinsic, and this file is compiled with --fmad=false, so the keys are reproducible bit for
+// bit by any IEEE implementation of the same sequence.  Value quantities (conic, opacity,
+// colour) and the backward use ordinary fp32 arithmetic.
+//
+// Readings of what the paper leaves open: pinhole + first-order (EWA) projection of the 3-D
+// covariance with a 0.3 px^2 dilation; cull at z <= near; Jacobian evaluated at x/z, y/z clamped
+// to +-1.3 tan(half field of view) with zero gradient through the clamp; radius
+// ceil(3 sqrt(lambda_max)); colour from real orthonormal spherical harmonics (no Condon-Shortley
+// phase) of the direction camera -> mean, + 0.5, clamped at 0.
+#include "pgs_internal.cuh"
+
+namespace pgs {
+namespace {
+
+// exp in fp32 by Cody-Waite reduction + degree-7 Taylor polynomial (Horner with fma) and an
+// exact power-of-two scale: k = rint(x log2 e), r = x - k ln2 (ln2 as hi + lo), exp = p(r) 2^k.
+// Bit-reproducible (every step is a correctly rounded IEEE operation); within 2 ulp of exp.
+__device__ __forceinline__ float det_expf(float x) {
+    if (x != x) return x;
+    x = fminf(fmaxf(x, -87.0f), 88.0f);
+    const float k = rintf(__fmul_rn(x, 0x1.715476p+0f));
+    float r = __fmaf_rn(-k, 0x1.62e4p-1f, x);
+    r = __fmaf_rn(-k, 0x1.7f7d1cp-20f, r);
+    float p = 0x1.a01a02p-13f;
+    p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);
+    p = __fmaf_rn(p, r, 0x1.111112p-7f);
+    p = __fmaf_rn(p, r, 0x1.555556p-5f);
+    p = __fmaf_rn(p, r, 0x1.555556p-3f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const float scale = __int_as_float(((int)k + 127) << 23);
+    return __fmul_rn(p, scale);
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) {
+    return fminf(fmaxf(x, lo), hi);
+}
+
+// fp32 state shared by the forward and the backward of one Gaussian.
+struct Geo {
+    float xc, yc, zc, tx, ty;
+    float u, v;
+    float qn, w, x, y, z;  // quaternion norm and unit quaternion
+    float R[3][3], s[3], M[3][3], Sig[3][3];
+    float cxh, cyh;
+    bool xclamp, yclamp;
+    float j00, j02, j11, j12;
+    float T[2][3];
+    float cov_a, cov_b, cov_c, det;
+};
+
+// The prescribed decision sequence.  Returns false if the Gaussian is culled before a rectangle
+// exists (behind the near plane, degenerate quaternion or covariance, non-finite position).
+__device__ __forceinline__ bool geometry(const float mu[3], const float ls[3], const float q[4],
+                                         const pgs_camera& cam, Geo& G) {
+    const float* V = cam.viewmat;
+    G.xc = __fmaf_rn(V[0], mu[0], __fmaf_rn(V[1], mu[1], __fmaf_rn(V[2], mu[2], V[3])));
+    G.yc = __fmaf_rn(V[4], mu[0], __fmaf_rn(V[5], mu[1], __fmaf_rn(V[6], mu[2], V[7])));
+    G.zc = __fmaf_rn(V[8], mu[0], __fmaf_rn(V[9], mu[1], __fmaf_rn(V[10], mu[2], V[11])));
+    if (!(G.zc > cam.near_z)) return false;
+    G.tx = __fdiv_rn(G.xc, G.zc);
+    G.ty = __fdiv_rn(G.yc, G.zc);
+    G.u = __fmaf_rn(cam.fx, G.tx, cam.cx);
+    G.v = __fmaf_rn(cam.fy, G.ty, cam.cy);
+    if (!isfinite(G.u) || !isfinite(G.v)) return false;
+
+    const float n2 = __fmaf_rn(q[0], q[0], __fmaf_rn(q[1], q[1], __fmaf_rn(q[2], q[2], __fmul_rn(q[3], q[3]))));
+    if (!(n2 > 0.0f) || !isfinite(n2)) return false;
+    G.qn = __fsqrt_rn(n2);
+    G.w = __fdiv_rn(q[0], G.qn);
+    G.x = __fdiv_rn(q[1], G.qn);
+    G.y = __fdiv_rn(q[2], G.qn);
+    G.z = __fdiv_rn(q[3], G.qn);
+    const float xx = __fmul_rn(G.x, G.x), yy = __fmul_rn(G.y, G.y), zz = __fmul_rn(G.z, G.z);
+    const float xy = __fmul_rn(G.x, G.y), xz = __fmul_rn(G.x, G.z), yz = __fmul_rn(G.y, G.z);
+    const float wx = __fmul_rn(G.w, G.x), wy = __fmul_rn(G.w, G.y), wz = __fmul_rn(G.w, G.z);
+    G.R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    G.R[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    G.R[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    G.R[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    G.R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    G.R[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    G.R[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    G.R[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    G.R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G.s[k] = det_expf(ls[k]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) G.M[a][k] = __fmul_rn(G.R[a][k], G.s[k]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) {
+            G.Sig[a][b] = __fmaf_rn(G.M[a][0], G.M[b][0],
+                                    __fmaf_rn(G.M[a][1], G.M[b][1], __fmul_rn(G.M[a][2], G.M[b][2])));
+            G.Sig[b][a] = G.Sig[a][b];
+        }
+    const float limx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)cam.width), cam.fx));
+    const float limy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)cam.height), cam.fy));
+    G.xclamp = G.tx < -limx || G.tx > limx;
+    G.yclamp = G.ty < -limy || G.ty > limy;
+    G.cxh = clampf(G.tx, -limx, limx);
+    G.cyh = clampf(G.ty, -limy, limy);
+    G.j00 = __fdiv_rn(cam.fx, G.zc);
+    G.j02 = -__fdiv_rn(__fmul_rn(cam.fx, G.cxh), G.zc);
+    G.j11 = __fdiv_rn(cam.fy, G.zc);
+    G.j12 = -__fdiv_rn(__fmul_rn(cam.fy, G.cyh), G.zc);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        G.T[0][k] = __fmaf_rn(G.j00, V[k], __fmul_rn(G.j02, V[8 + k]));
+        G.T[1][k] = __fmaf_rn(G.j11, V[4 + k], __fmul_rn(G.j12, V[8 + k]));
+    }
+    float A[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            A[a][k] = __fmaf_rn(G.T[a][0], G.Sig[0][k],
+                                __fmaf_rn(G.T[a][1], G.Sig[1][k], __fmul_rn(G.T[a][2], G.Sig[2][k])));
+    G.cov_a = __fadd_rn(__fmaf_rn(A[0][0], G.T[0][0], __fmaf_rn(A[0][1], G.T[0][1], __fmul_rn(A[0][2], G.T[0][2]))), 0.3f);
+    G.cov_b = __fmaf_rn(A[0][0], G.T[1][0], __fmaf_rn(A[0][1], G.T[1][1], __fmul_rn(A[0][2], G.T[1][2])));
+    G.cov_c = __fadd_rn(__fmaf_rn(A[1][0], G.T[1][0], __fmaf_rn(A[1][1], G.T[1][1], __fmul_rn(A[1][2], G.T[1][2]))), 0.3f);
+    G.det = __fsub_rn(__fmul_rn(G.cov_a, G.cov_c), __fmul_rn(G.cov_b, G.cov_b));
+    if (!(G.det > 0.0f) || !isfinite(G.det)) return false;
+    return true;
+}
+
+// Real orthonormal SH, k = l^2 + l + m.  Constants: 1/(2 sqrt(pi)), sqrt(3/(4 pi)),
+// sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4, sqrt(105/pi)/2,
+// sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float K0 = 0.28209479177387814f;
+constexpr float K1 = 0.4886025119029199f;
+constexpr float K2A = 1.0925484305920792f;
+constexpr float K2B = 0.31539156525252005f;
+constexpr float K2C = 0.5462742152960396f;
+constexpr float K3A = 0.5900435899266435f;
+constexpr float K3B = 2.890611442640554f;
+constexpr float K3C = 0.4570457994644658f;
+constexpr float K3D = 0.3731763325901154f;
+constexpr float K3E = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_eval(int K, float x, float y, float z, float Y[16]) {
+    Y[0] = K0;
+    if (K > 1) {
+        Y[1] = K1 * y;
+        Y[2] = K1 * z;
+        Y[3] = K1 * x;
+    }
+    if (K > 4) {
+        Y[4] = K2A * x * y;
+        Y[5] = K2A * y * z;
+        Y[6] = K2B * (3.0f * z * z - 1.0f);
+        Y[7] = K2A * x * z;
+        Y[8] = K2C * (x * x - y * y);
+    }
+    if (K > 9) {
+        Y[9] = K3A * y * (3.0f * x * x - y * y);
+        Y[10] = K3B * x * y * z;
+        Y[11] = K3C * y * (5.0f * z * z - 1.0f);
+        Y[12] = K3D * z * (5.0f * z * z - 3.0f);
+        Y[13] = K3C * x * (5.0f * z * z - 1.0f);
+        Y[14] = K3E * z * (x * x - y * y);
+        Y[15] = K3A * x * (x * x - 3.0f * y * y);
+    }
+}
+
+// d/d(x, y, z) of sum_k w_k Y_k (Cartesian polynomial forms above).
+__device__ __forceinline__ void sh_grad(int K, float x, float y, float z, const float w[16],
+                                        float d[3]) {
+    d[0] = d[1] = d[2] = 0.0f;
+    if (K > 1) {
+        d[0] += K1 * w[3];
+        d[1] += K1 * w[1];
+        d[2] += K1 * w[2];
+    }
+    if (K > 4) {
+        d[0] += K2A * (w[4] * y + w[7] * z) + K2C * w[8] * 2.0f * x;
+        d[1] += K2A * (w[4] * x + w[5] * z) - K2C * w[8] * 2.0f * y;
+        d[2] += K2A * (w[5] * y + w[7] * x) + K2B * w[6] * 6.0f * z;
+    }
+    if (K > 9) {
+        const float a = 5.0f * z * z - 1.0f;
+        d[0] += K3A * w[9] * 6.0f * x * y + K3B * w[10] * y * z + K3C * w[13] * a +
+                K3E * w[14] * 2.0f * x * z + K3A * w[15] * 3.0f * (x * x - y * y);
+        d[1] += K3A * w[9] * 3.0f * (x * x - y * y) + K3B * w[10] * x * z + K3C * w[11] * a -
+                K3E * w[14] * 2.0f * y * z - K3A * w[15] * 6.0f * x * y;
+        d[2] += K3B * w[10] * x * y + K3C * w[11] * 10.0f * y * z + K3D * w[12] * (15.0f * z * z - 3.0f) +
+                K3C * w[13] * 10.0f * x * z + K3E * w[14] * (x * x - y * y);
+    }
+}
+
+__device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3]) {
+    const float* V = cam.viewmat;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = -(V[k] * V[3] + V[4 + k] * V[7] + V[8 + k] * V[11]);
+}
+
+__global__ void __launch_bounds__(kProjBlock)
+k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
+    const int64_t n = g.n;
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    uint32_t count = 0;
+    if (i < n) {
+        const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
+        const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
+        const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
+        const float logit = g.opacity_logits[i];
+        bool finite = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(ls[0]) &&
+                      isfinite(ls[1]) && isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) &&
+                      isfinite(q[2]) && isfinite(q[3]) && isfinite(logit);
+        Geo G;
+        bool vis = finite && geometry(mu, ls, q, cam, G);
+        uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        if (vis) {
+            const float mid = __fmul_rn(0.5f, __fadd_rn(G.cov_a, G.cov_c));
+            const float disc = fmaxf(0.1f, __fsub_rn(__fmul_rn(mid, mid), G.det));
+            const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
+            const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
+            vis = isfinite(rad);
+            if (vis) {
+                const float tf = (float)kTile;
+                x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rad), tf)), 0.0f, (float)TX);
+                x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rad), tf)), 1.0f), 0.0f, (float)TX);
+                y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, rad), tf)), 0.0f, (float)TY);
+                y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, rad), tf)), 1.0f), 0.0f, (float)TY);
+                count = (x1 - x0) * (y1 - y0);
+            }
+        }
+        if (count > 0) {
+            // value path: conic, opacity, colour
+            const float inv_det = 1.0f / G.det;
+            const float opacity = 1.0f / (1.0f + expf(-logit));
+            float cc[3];
+            camera_centre(cam, cc);
+            float d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+            const float inv_len = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            d[0] *= inv_len;
+            d[1] *= inv_len;
+            d[2] *= inv_len;
+            const int K = sh_coeffs(g.sh_degree);
+            float Y[16];
+            sh_eval(K, d[0], d[1], d[2], Y);
+            float rgb[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = 0.5f;
+                for (int k = 0; k < K; ++k) acc += g.sh[((int64_t)c * K + k) * n + i] * Y[k];
+                rgb[c] = fmaxf(acc, 0.0f);
+            }
+            if (!isfinite(rgb[0]) || !isfinite(rgb[1]) || !isfinite(rgb[2])) {
+                count = 0;
+                finite = false;
+            } else {
+                sc.xyo[i] = make_float4(G.u, G.v, opacity, 0.0f);
+                sc.conic[i] = make_float4(G.cov_c * inv_det, -G.cov_b * inv_det, G.cov_a * inv_det, 0.0f);
+                sc.rgb[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+                sc.depth_bits[i] = __float_as_uint(G.zc);
+                sc.rect[i] = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+            }
+        }
+        if (!finite) atomicOr(sc.status, kStatusNonfinite);
+        sc.touched[i] = count;
+    }
+    // CTA total of tiles touched, for the scan
+    uint32_t warp_sum = __reduce_add_sync(0xffffffffu, count);
+    __shared__ uint32_t s_part[kProjBlock / 32];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = warp_sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < kProjBlock / 32 ? s_part[threadIdx.x] : 0u;
+        v = __reduce_add_sync(0xffffffffu, v);
+        if (threadIdx.x == 0) sc.block_sums[blockIdx.x] = v;
+    }
+}
+
+// Backward of one Gaussian: screen-space gradient (du, dv, d conic, d opacity, d rgb) ->
+// parameters.  Matrix form: H = -Q Gq Q (Q the conic matrix, Gq its gradient with the
+// off-diagonal halved), dSigma = T^T H T, dT = 2 H T Sigma, dM = 2 dSigma M.
+__global__ void __launch_bounds__(kProjBlock)
+k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
+    const int64_t n = g.n;
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    if (i >= n || sc.touched[i] == 0) return;
+    const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
+    const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
+    const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
+    Geo G;
+    geometry(mu, ls, q, cam, G);
+    float gr[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gr[k] = sc.grad2d[k * n + i];
+    const float* V = cam.viewmat;
+
+    // colour -> SH coefficients and view direction
+    float cc[3];
+    camera_centre(cam, cc);
+    float d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+    const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float inv_len = 1.0f / dist;
+    d[0] *= inv_len;
+    d[1] *= inv_len;
+    d[2] *= inv_len;
+    const int K = sh_coeffs(g.sh_degree);
+    float Y[16];
+    sh_eval(K, d[0], d[1], d[2], Y);
+    float wsum[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) wsum[k] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.5f;
+        float coef[16];
+        for (int k = 0; k < K; ++k) {
+            coef[k] = g.sh[((int64_t)c * K + k) * n + i];
+            acc += coef[k] * Y[k];
+        }
+        const float gc = acc < 0.0f ? 0.0f : gr[6 + c];  // zero gradient through the clamp
+        for (int k = 0; k < K; ++k) {
+            out.sh[((int64_t)c * K + k) * n + i] += gc * Y[k];
+            wsum[k] += gc * coef[k];
+        }
+    }
+    float ddir[3];
+    sh_grad(K, d[0], d[1], d[2], wsum, ddir);
+    const float dd = ddir[0] * d[0] + ddir[1] * d[1] + ddir[2] * d[2];
+    float dmu[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dmu[k] = (ddir[k] - d[k] * dd) * inv_len;
+
+    // opacity logit
+    const float o = 1.0f / (1.0f + expf(-g.opacity_logits[i]));
+    out.opacity_logits[i] += gr[5] * o * (1.0f - o);
+
+    // conic -> 2-D covariance
+    const float inv_det = 1.0f / G.det;
+    const float qa = G.cov_c * inv_det, qb = -G.cov_b * inv_det, qc = G.cov_a * inv_det;
+    const float ga = gr[2], gb = 0.5f * gr[3], gcn = gr[4];
+    const float P00 = qa * ga + qb * gb, P01 = qa * gb + qb * gcn;
+    const float P10 = qb * ga + qc * gb, P11 = qb * gb + qc * gcn;
+    const float H00 = -(P00 * qa + P01 * qb);
+    const float H01 = -0.5f * ((P00 * qb + P01 * qc) + (P10 * qa + P11 * qb));
+    const float H11 = -(P10 * qb + P11 * qc);
+    const float H[2][2] = {{H00, H01}, {H01, H11}};
+
+    // dSigma = T^T H T ; dT = 2 H T Sigma
+    float HT[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) HT[a][k] = H[a][0] * G.T[0][k] + H[a][1] * G.T[1][k];
+    float dSig[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dSig[m][k] = G.T[0][m] * HT[0][k] + G.T[1][m] * HT[1][k];
+    float dT[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dT[a][k] = 2.0f * (HT[a][0] * G.Sig[0][k] + HT[a][1] * G.Sig[1][k] + HT[a][2] * G.Sig[2][k]);
+    // T = J W
+    float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dJ00 += dT[0][k] * V[k];
+        dJ02 += dT[0][k] * V[8 + k];
+        dJ11 += dT[1][k] * V[4 + k];
+        dJ12 += dT[1][k] * V[8 + k];
+    }
+    const float z = G.zc, iz = 1.0f / z, iz2 = iz * iz;
+    float dpc[3] = {0.f, 0.f, 0.f};
+    dpc[2] += -cam.fx * iz2 * dJ00 + cam.fx * G.cxh * iz2 * dJ02 - cam.fy * iz2 * dJ11 +
+              cam.fy * G.cyh * iz2 * dJ12;
+    const float dcxh = -cam.fx * iz * dJ02, dcyh = -cam.fy * iz * dJ12;
+    if (!G.xclamp) {
+        dpc[0] += dcxh * iz;
+        dpc[2] -= dcxh * G.xc * iz2;
+    }
+    if (!G.yclamp) {
+        dpc[1] += dcyh * iz;
+        dpc[2] -= dcyh * G.yc * iz2;
+    }
+    dpc[0] += gr[0] * cam.fx * iz;
+    dpc[2] -= gr[0] * cam.fx * G.xc * iz2;
+    dpc[1] += gr[1] * cam.fy * iz;
+    dpc[2] -= gr[1] * cam.fy * G.yc * iz2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dmu[k] += dpc[0] * V[k] + dpc[1] * V[4 + k] + dpc[2] * V[8 + k];
+
+    // Sigma = M M^T, M = R diag(s)
+    float dR[3][3], dls[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float ds = 0.f;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float dM = 2.0f * (dSig[p][0] * G.M[0][k] + dSig[p][1] * G.M[1][k] + dSig[p][2] * G.M[2][k]);
+            dR[p][k] = dM * G.s[k];
+            ds += dM * G.R[p][k];
+        }
+        dls[k] = ds * G.s[k];
+    }
+    const float w = G.w, x = G.x, y = G.y, zq = G.z;
+    const float dw = 2.f * (-zq * dR[0][1] + y * dR[0][2] + zq * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    const float dx = 2.f * (y * dR[0][1] + zq * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                            zq * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+    const float dy = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + zq * dR[1][2] -
+                            w * dR[2][0] + zq * dR[2][1] - 2.f * y * dR[2][2]);
+    const float dz = 2.f * (-2.f * zq * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] -
+                            2.f * zq * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float dot = dw * w + dx * x + dy * y + dz * zq;
+    const float iq = 1.0f / G.qn;
+    out.quats[i] += (dw - w * dot) * iq;
+    out.quats[n + i] += (dx - x * dot) * iq;
+    out.quats[2 * n + i] += (dy - y * dot) * iq;
+    out.quats[3 * n + i] += (dz - zq * dot) * iq;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        out.log_scales[k * n + i] += dls[k];
+        out.means[k * n + i] += dmu[k];
+    }
+}
+
+}  // namespace
+
+int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY,
+                       const Scratch& sc, cudaStream_t s) {
+    const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
+    if (blocks == 0) return 0;
+    k_project_fwd<<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc);
+    return 1;
+}
+
+int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+                       pgs_gaussians& grads, cudaStream_t s) {
+    const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
+    if (blocks == 0) return 0;
+    k_project_bwd<<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads);
+    return 1;
+}
+
+}  // namespace pgs

@@ -1,0 +1,233 @@
+"""Python face of the rasterizer: parameter buffers, a context, and the render / loss /
+backward / step calls of one training iteration (operator T of Sec. III,
+T : (Theta_0, {I_t, T_t}) -> Theta*).
+
+PyTorch supplies device memory and the CUDA stream; every computation runs in libpocketgs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+# Learning rates of the parameter groups (the paper states none): means 1.6e-4 x scene extent 2,
+# log-scales 5e-3, rotations 1e-3, opacity logits 2.5e-2, SH DC 2.5e-3, higher SH 1.25e-4.
+DEFAULT_LR = (3.2e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)
+
+
+def rows_of(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+class GaussianBuffer:
+    """One contiguous fp32 device buffer [11 + 3K][n] holding the planar groups
+    means [3][n], log_scales [3][n], quats [4][n], opacity_logits [n], sh [3][K][n]."""
+
+    def __init__(self, n: int, sh_degree: int, device="cuda", data: torch.Tensor | None = None):
+        self.n = int(n)
+        self.sh_degree = int(sh_degree)
+        K = (sh_degree + 1) ** 2
+        rows = rows_of(sh_degree)
+        if data is None:
+            data = torch.zeros((rows, self.n), dtype=torch.float32, device=device)
+        assert data.shape == (rows, self.n) and data.dtype == torch.float32 and data.is_contiguous()
+        self.data = data
+        self.means = data[0:3]
+        self.log_scales = data[3:6]
+        self.quats = data[6:10]
+        self.opacity_logits = data[10]
+        self.sh = data[11:].view(3, K, self.n)
+        self._struct = None
+
+    @classmethod
+    def from_arrays(cls, g, device="cuda") -> "GaussianBuffer":
+        """From any object with numpy/torch attributes means, log_scales, quats, opacity_logits,
+        sh and sh_degree (e.g. synthetic.Gaussians)."""
+        n = int(np.asarray(g.means).shape[1]) if not torch.is_tensor(g.means) else g.means.shape[1]
+        buf = cls(n, g.sh_degree, device)
+        for name in GROUPS:
+            src = getattr(g, name)
+            t = src if torch.is_tensor(src) else torch.from_numpy(np.ascontiguousarray(src, np.float32))
+            getattr(buf, name).copy_(t.to(device).view_as(getattr(buf, name)))
+        return buf
+
+    def zeros_like(self) -> "GaussianBuffer":
+        return GaussianBuffer(self.n, self.sh_degree, self.data.device)
+
+    def clone(self) -> "GaussianBuffer":
+        return GaussianBuffer(self.n, self.sh_degree, self.data.device, self.data.clone())
+
+    def struct(self) -> L.PgsGaussians:
+        if self._struct is None:
+            self._struct = L.PgsGaussians(self.n, self.sh_degree, 0, *[
+                getattr(self, k).data_ptr() for k in GROUPS])
+        return self._struct
+
+    def numpy(self) -> dict:
+        return {k: getattr(self, k).detach().cpu().numpy() for k in GROUPS}
+
+
+def tensors_struct(n, sh_degree, means, log_scales, quats, opacity_logits, sh) -> L.PgsGaussians:
+    """Struct over separate contiguous fp32 CUDA tensors (autograd path)."""
+    ts = (means, log_scales, quats, opacity_logits, sh)
+    for t in ts:
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("parameters must be contiguous float32 CUDA tensors")
+    return L.PgsGaussians(n, sh_degree, 0, *[t.data_ptr() for t in ts])
+
+
+def camera_struct(cam) -> L.PgsCamera:
+    vm = np.asarray(cam.viewmat, np.float32).reshape(-1)
+    bg = getattr(cam, "bg", (0.0, 0.0, 0.0))
+    return L.PgsCamera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy),
+                       float(cam.cx), float(cam.cy), (C.c_float * 12)(*vm.tolist()),
+                       float(getattr(cam, "near", 0.2)), (C.c_float * 3)(*[float(b) for b in bg]))
+
+
+@dataclass
+class AdamConfig:
+    lr: tuple = DEFAULT_LR
+    b1: float = 0.9
+    b2: float = 0.999
+    eps: float = 1e-15
+
+
+class Rasterizer:
+    """A libpocketgs context bound to one CUDA stream (default: the current torch stream)."""
+
+    def __init__(self, pair_capacity: int = 0, adam: AdamConfig | None = None,
+                 stream: torch.cuda.Stream | None = None, device="cuda"):
+        self._lib = L.lib()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        adam = adam or AdamConfig()
+        cfg = L.PgsConfig(16, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
+                          (C.c_float * 6)(*adam.lr))
+        self._ctx = C.c_void_p()
+        L.check(self._lib.pgs_create(C.byref(self._ctx), C.byref(cfg),
+                                     C.c_void_p(self.stream.cuda_stream)), "pgs_create")
+        self.render_id = 0
+        self._last_shape = None
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.pgs_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------------------------- calls
+    def reserve(self, n: int, width: int, height: int, pair_capacity: int):
+        L.check(self._lib.pgs_reserve(self._ctx, int(n), int(width), int(height),
+                                      int(pair_capacity)), "pgs_reserve")
+
+    def render_struct(self, g: L.PgsGaussians, cam, out: torch.Tensor | None = None) -> torch.Tensor:
+        cs = cam if isinstance(cam, L.PgsCamera) else camera_struct(cam)
+        if out is None:
+            out = torch.empty((3, cs.height, cs.width), dtype=torch.float32, device=self.device)
+        L.check(self._lib.pgs_render(self._ctx, C.byref(g), C.byref(cs), C.c_void_p(out.data_ptr())),
+                "pgs_render")
+        self.render_id += 1
+        self._last_shape = (cs.height, cs.width)
+        return out
+
+    def render(self, params: GaussianBuffer, cam, out: torch.Tensor | None = None) -> torch.Tensor:
+        return self.render_struct(params.struct(), cam, out)
+
+    def loss_l1(self, image: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
+                out: torch.Tensor | None = None):
+        """(dL/dimage, device tensor [l1, sse])."""
+        assert image.is_contiguous() and target.is_contiguous() and image.numel() == target.numel()
+        grad = torch.empty_like(image) if grad is None else grad
+        out = torch.empty(2, dtype=torch.float32, device=self.device) if out is None else out
+        L.check(self._lib.pgs_loss_l1(self._ctx, C.c_void_p(image.data_ptr()),
+                                      C.c_void_p(target.data_ptr()), image.numel(),
+                                      C.c_void_p(grad.data_ptr()), C.c_void_p(out.data_ptr())),
+                "pgs_loss_l1")
+        return grad, out
+
+    def backward_struct(self, dL_dimage: torch.Tensor, grads: L.PgsGaussians):
+        assert dL_dimage.is_contiguous() and dL_dimage.dtype == torch.float32
+        L.check(self._lib.pgs_backward(self._ctx, C.c_void_p(dL_dimage.data_ptr()), C.byref(grads)),
+                "pgs_backward")
+
+    def backward(self, dL_dimage: torch.Tensor, grads: GaussianBuffer):
+        self.backward_struct(dL_dimage, grads.struct())
+
+    def step(self, params: GaussianBuffer, grads: GaussianBuffer, m: GaussianBuffer,
+             v: GaussianBuffer, t: int):
+        L.check(self._lib.pgs_step(self._ctx, C.byref(params.struct()), C.byref(grads.struct()),
+                                   C.byref(m.struct()), C.byref(v.struct()), int(t)), "pgs_step")
+
+    def status(self):
+        """(code, pairs of the last render); synchronises."""
+        pairs = C.c_int64()
+        code = self._lib.pgs_status(self._ctx, C.byref(pairs))
+        return code, pairs.value
+
+    def check_status(self):
+        code, pairs = self.status()
+        L.check(code, "device status")
+        return pairs
+
+    def profile(self, enable: bool = True):
+        L.check(self._lib.pgs_profile(self._ctx, int(bool(enable))), "pgs_profile")
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, count)} since the last read; synchronises."""
+        ms = np.zeros(len(L.PGS_STAGES), np.float64)
+        cnt = np.zeros(len(L.PGS_STAGES), np.int64)
+        L.check(self._lib.pgs_stage_times(self._ctx, ms.ctypes.data_as(C.c_void_p),
+                                          cnt.ctypes.data_as(C.c_void_p)), "pgs_stage_times")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(L.PGS_STAGES)}
+
+    def launch_count(self) -> int:
+        return int(self._lib.pgs_launch_count(self._ctx))
+
+    def read_buffer(self, which: int) -> np.ndarray:
+        size = C.c_int64()
+        L.check(self._lib.pgs_read_buffer(self._ctx, which, None, 0, C.byref(size)), "pgs_read_buffer")
+        dtype = {L.PGS_BUF_KEYS: np.uint64, L.PGS_BUF_T_FINAL: np.float32,
+                 L.PGS_BUF_GRAD2D: np.float32}.get(which, np.uint32)
+        out = np.zeros(size.value // np.dtype(dtype).itemsize, dtype)
+        L.check(self._lib.pgs_read_buffer(self._ctx, which, out.ctypes.data_as(C.c_void_p),
+                                          size.value, C.byref(size)), "pgs_read_buffer")
+        return out
+
+
+class Trainer:
+    """Plain training iteration on one view: render -> L1 -> backward -> Adam (Sec. IV, 500
+    iterations, one view per iteration)."""
+
+    def __init__(self, params: GaussianBuffer, rasterizer: Rasterizer | None = None,
+                 adam: AdamConfig | None = None):
+        self.params = params
+        self.r = rasterizer or Rasterizer(adam=adam)
+        self.grads = params.zeros_like()
+        self.m = params.zeros_like()
+        self.v = params.zeros_like()
+        self.t = 0
+        self.image = None
+        self.dl = None
+        self.loss = torch.zeros(2, dtype=torch.float32, device=params.data.device)
+
+    def step(self, cam, target: torch.Tensor) -> torch.Tensor:
+        self.image = self.r.render(self.params, cam, self.image if self.image is not None and
+                                   self.image.shape[1:] == (cam.height, cam.width) else None)
+        if self.dl is None or self.dl.shape != self.image.shape:
+            self.dl = torch.empty_like(self.image)
+        self.r.loss_l1(self.image, target, self.dl, self.loss)
+        self.r.backward(self.dl, self.grads)
+        self.t += 1
+        self.r.step(self.params, self.grads, self.m, self.v, self.t)
+        return self.loss

@@ -1,0 +1,235 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI, against the CPU oracle on
+the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_17354_gb300 import synthetic as S
+from tests._parity import compare_forward, compare_grads, rel_l2, IMAGE_TOL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2601_17354_gb300 import rasterizer
+    return rasterizer
+
+
+def render_gpu(R, g, cam, rast=None):
+    rast = rast or R.Rasterizer()
+    buf = R.GaussianBuffer.from_arrays(g)
+    img = rast.render(buf, cam)
+    torch.cuda.synchronize()
+    code, pairs = rast.status()
+    from paper_2601_17354_gb300 import _lib as L
+    T = rast.read_buffer(L.PGS_BUF_T_FINAL).reshape(cam.height, cam.width)
+    last = rast.read_buffer(L.PGS_BUF_LAST).reshape(cam.height, cam.width)
+    return rast, buf, img.cpu().numpy(), T, last, code, pairs
+
+
+def check_keys(rast, g, cam):
+    from paper_2601_17354_gb300 import _lib as L
+    k, v, r = oracle.keys(g, cam)
+    gk = rast.read_buffer(L.PGS_BUF_KEYS)
+    gv = rast.read_buffer(L.PGS_BUF_VALUES)
+    gr = rast.read_buffer(L.PGS_BUF_RANGES).reshape(-1, 2)
+    assert len(gk) == len(k)
+    assert np.array_equal(gk, k), f"{np.sum(gk != k)} keys differ"
+    assert np.array_equal(gv, v)
+    assert np.array_equal(gr, r)
+    return len(k)
+
+
+SCENES = {
+    "tiny_2k_128": lambda: S.tiny_scene(0)[:2],
+    "ragged_100x75": lambda: S.tiny_scene(1, n=1500, width=100, height=75)[:2],
+    "dense_20k_64": lambda: S.tiny_scene(2, n=20000, width=64, height=64, focal=60.0)[:2],
+    "surface_sh3_200x120": lambda: (lambda sc: (sc.gt, sc.cameras[3]))(
+        S.surface_scene(3, 20000, 3, 200, 120, 160.0, n_cameras=8)),
+}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_forward_keys_and_image(R, name):
+    g, cam = SCENES[name]()
+    rast, _, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0
+    P = check_keys(rast, g, cam)
+    assert pairs == P
+    ora = oracle.render(g, cam)
+    compare_forward(img, T, last, ora)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_backward_grads(R, name):
+    g, cam = SCENES[name]()
+    cam.bg = (0.1, 0.3, 0.2)
+    rast, buf, img, T, last, code, _ = render_gpu(R, g, cam)
+    ora = oracle.render(g, cam)
+    dL = S.random_image(11, cam.width, cam.height)
+    dL[:, ora["flag"] != 0] = 0.0
+    grads = buf.zeros_like()
+    rast.backward(torch.from_numpy(dL).cuda(), grads)
+    torch.cuda.synchronize()
+    o2, og = oracle.backward(g, cam, dL)
+    keep = oracle.gaussian_flags(g, cam) == 0
+    from paper_2601_17354_gb300 import _lib as L
+    g2 = rast.read_buffer(L.PGS_BUF_GRAD2D).reshape(9, g.n)
+    for k in range(9):
+        assert rel_l2(g2[k, keep], o2[keep, k]) < 1e-3, k
+    compare_grads(grads.numpy(), og, keep)
+
+
+def test_backward_accumulates(R):
+    g, cam = SCENES["tiny_2k_128"]()
+    rast, buf, *_ = render_gpu(R, g, cam)
+    dL = torch.from_numpy(S.random_image(4, cam.width, cam.height)).cuda()
+    g1 = buf.zeros_like()
+    rast.backward(dL, g1)
+    g2 = buf.zeros_like()
+    rast.backward(dL, g2)
+    rast.backward(dL, g2)
+    torch.cuda.synchronize()
+    assert torch.allclose(g2.data, 2 * g1.data, rtol=1e-5, atol=1e-9)
+
+
+# ----------------------------------------------------------------------------------------------
+# edge cases
+# ----------------------------------------------------------------------------------------------
+
+def test_empty_scene(R):
+    g, cam = SCENES["tiny_2k_128"]()
+    g = g.subset(np.arange(0))
+    cam.bg = (0.25, 0.5, 0.75)
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0 and pairs == 0
+    assert np.allclose(img, np.array(cam.bg, np.float32)[:, None, None])
+    assert np.all(T == 1.0) and np.all(last == 0)
+
+
+def test_all_culled_behind_camera(R):
+    g, cam = SCENES["tiny_2k_128"]()
+    g.means[2] = -5.0
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0 and pairs == 0
+    assert np.all(img == 0.0) and np.all(T == 1.0)
+    grads = buf.zeros_like()
+    rast.backward(torch.ones(3, cam.height, cam.width, device="cuda"), grads)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(grads.data) == 0
+
+
+def test_single_gaussian_covering_every_tile(R):
+    g, cam = SCENES["ragged_100x75"]()
+    g = g.subset([0])
+    g.means[:, 0] = [0.0, 0.0, 0.0]
+    g.log_scales[:, 0] = 0.0
+    g.opacity_logits[0] = 0.5
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    TX, TY = oracle.tiles(cam)
+    assert pairs == TX * TY
+    check_keys(rast, g, cam)
+    compare_forward(img, T, last, oracle.render(g, cam))
+
+
+def test_one_pixel_image(R):
+    g, cam = SCENES["tiny_2k_128"]()
+    cam1 = S.Camera(1, 1, cam.fx, cam.fy, 0.5, 0.5, cam.viewmat)
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam1)
+    assert code == 0
+    check_keys(rast, g, cam1)
+    compare_forward(img, T, last, oracle.render(g, cam1))
+
+
+def test_equal_depth_ties_are_stable(R):
+    g, cam = SCENES["tiny_2k_128"]()
+    g.means[2, 1::5] = g.means[2, 0:-1:5][: len(g.means[2, 1::5])]
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    check_keys(rast, g, cam)
+    compare_forward(img, T, last, oracle.render(g, cam))
+
+
+def test_nonfinite_parameter_is_reported_and_culled(R):
+    from paper_2601_17354_gb300 import _lib as L
+    g, cam = SCENES["tiny_2k_128"]()
+    g.means[0, 17] = np.nan
+    g.log_scales[1, 99] = np.inf
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == L.PGS_ERR_NONFINITE
+    assert np.all(np.isfinite(img))
+    touched = rast.read_buffer(L.PGS_BUF_TILES_TOUCHED)
+    assert touched[17] == 0 and touched[99] == 0
+    assert rast.status()[0] == 0  # cleared by the read
+
+
+def test_capacity_overflow_is_reported_then_fits(R):
+    from paper_2601_17354_gb300 import _lib as L
+    g, cam = SCENES["tiny_2k_128"]()
+    P = len(oracle.keys(g, cam)[0])
+    small = R.Rasterizer(pair_capacity=P - 1)
+    small.render(R.GaussianBuffer.from_arrays(g), cam)
+    code, pairs = small.status()
+    assert code == L.PGS_ERR_CAPACITY and pairs == P
+    exact = R.Rasterizer(pair_capacity=P)
+    _, _, img, T, last, code, pairs = render_gpu(R, g, cam, exact)
+    assert code == 0 and pairs == P
+    compare_forward(img, T, last, oracle.render(g, cam))
+
+
+def test_backward_without_render_is_an_error(R):
+    from paper_2601_17354_gb300 import _lib as L
+    rast = R.Rasterizer()
+    buf = R.GaussianBuffer(10, 0)
+    with pytest.raises(L.PgsError) as e:
+        rast.backward(torch.zeros(3, 4, 4, device="cuda"), buf)
+    assert e.value.code == L.PGS_ERR_NO_RENDER
+
+
+# ----------------------------------------------------------------------------------------------
+# loss and optimizer
+# ----------------------------------------------------------------------------------------------
+
+def test_l1_loss_matches_oracle(R):
+    rng = np.random.default_rng(0)
+    img = rng.uniform(0, 1, size=(3, 77, 131)).astype(np.float32)
+    gt = rng.uniform(0, 1, size=(3, 77, 131)).astype(np.float32)
+    gt[0, 3, 4] = img[0, 3, 4]  # a zero difference: sign(0) = 0
+    rast = R.Rasterizer()
+    grad, out = rast.loss_l1(torch.from_numpy(img).cuda(), torch.from_numpy(gt).cuda())
+    loss, ograd, sse = oracle.l1(img.astype(np.float64), gt.astype(np.float64))
+    out = out.cpu().numpy()
+    assert abs(out[0] - loss) <= 1e-6 * loss
+    assert abs(out[1] - sse) <= 1e-5 * sse
+    assert np.allclose(grad.cpu().numpy(), ograd, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("n,degree", [(1000, 3), (1001, 1), (7, 0)])
+def test_adam_matches_oracle(R, n, degree):
+    rng = np.random.default_rng(n)
+    rows = R.rows_of(degree)
+    p0 = rng.normal(size=(rows, n)).astype(np.float32)
+    rast = R.Rasterizer()
+    P = R.GaussianBuffer(n, degree, data=torch.from_numpy(p0.copy()).cuda())
+    G, M, V = P.zeros_like(), P.zeros_like(), P.zeros_like()
+    lr = np.array(R.DEFAULT_LR)
+    K = (degree + 1) ** 2
+    row_lr = np.concatenate([[lr[0]] * 3, [lr[1]] * 3, [lr[2]] * 4, [lr[3]],
+                             [lr[4] if k % K == 0 else lr[5] for k in range(3 * K)]])
+    po, mo, vo = p0.astype(np.float64), np.zeros((rows, n)), np.zeros((rows, n))
+    for t in range(1, 6):
+        gk = (rng.normal(size=(rows, n)) * 10.0 ** rng.uniform(-4, 0)).astype(np.float32)
+        G.data.copy_(torch.from_numpy(gk))
+        rast.step(P, G, M, V, t)
+        for r in range(rows):
+            pr, mr, vr = po[r].copy(), mo[r].copy(), vo[r].copy()
+            oracle.adam(pr, gk[r].astype(np.float64), mr, vr, row_lr[r], t)
+            po[r], mo[r], vo[r] = pr, mr, vr
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(G.data) == 0
+    assert np.allclose(P.data.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+    assert np.allclose(M.data.cpu().numpy(), mo, rtol=1e-4, atol=1e-9)
+    assert np.allclose(V.data.cpu().numpy(), vo, rtol=1e-4, atol=1e-12)
