@@ -40,6 +40,7 @@ extern "C" {
 #define PGS_ERR_NONFINITE (-4)   /* a parameter of a projected Gaussian was NaN or inf */
 #define PGS_ERR_CUDA (-6)        /* a CUDA runtime call failed */
 #define PGS_ERR_OOM (-7)         /* device allocation failed */
+#define PGS_ERR_INTERNAL (-8)    /* a device-side consistency check failed (access skipped) */
 
 typedef struct pgs_ctx pgs_ctx;
 

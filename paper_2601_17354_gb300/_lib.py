@@ -20,6 +20,7 @@ PGS_ERR_CAPACITY = -3
 PGS_ERR_NONFINITE = -4
 PGS_ERR_CUDA = -6
 PGS_ERR_OOM = -7
+PGS_ERR_INTERNAL = -8
 
 PGS_BUF_KEYS = 0
 PGS_BUF_VALUES = 1

@@ -184,6 +184,7 @@ const char* pgs_strerror(int code) {
         case PGS_ERR_NONFINITE: return "non-finite parameter of a Gaussian";
         case PGS_ERR_CUDA: return "CUDA runtime error";
         case PGS_ERR_OOM: return "device allocation failed";
+        case PGS_ERR_INTERNAL: return "device-side consistency check failed";
         default: return "unknown error";
     }
 }
@@ -259,7 +260,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     const size_t e2 = mark(ctx);
     ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
     const size_t e3 = mark(ctx);
-    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, ctx->sc, image_out, s);
+    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, params->n, ctx->sc, image_out, s);
     const size_t e4 = mark(ctx);
     span(ctx, PGS_STAGE_PROJECT, e0, e1);
     span(ctx, PGS_STAGE_BIN, e1, e2);
@@ -328,6 +329,7 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(e);
     if (pairs_needed) *pairs_needed = (int64_t)P;
+    if (st & kStatusInternal) return PGS_ERR_INTERNAL;
     if (st & kStatusCapacity) return PGS_ERR_CAPACITY;
     if (st & kStatusNonfinite) return PGS_ERR_NONFINITE;
     return PGS_OK;

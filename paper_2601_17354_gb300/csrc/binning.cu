@@ -286,8 +286,12 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
         if (idx < P) {
             const uint32_t d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
             const uint32_t dst = s_wh[warp][d] + rank[r];
-            kout[dst] = key[r];
-            vout[dst] = val[r];
+            if (dst < P) {
+                kout[dst] = key[r];
+                vout[dst] = val[r];
+            } else {
+                atomicOr(sc.status, kStatusInternal);
+            }
         }
     }
 }
@@ -296,10 +300,14 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
 // K5: tile ranges [first, last + 1) from the sorted keys (ranges pre-zeroed)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_ranges(int64_t capacity, const unsigned long long* __restrict__ keys, Scratch sc) {
+k_ranges(int64_t capacity, uint32_t tiles, const unsigned long long* __restrict__ keys, Scratch sc) {
     const uint64_t P = kept_pairs(sc, capacity);
     for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256) {
         const uint32_t t = (uint32_t)(keys[k] >> 32);
+        if (t >= tiles) {
+            atomicOr(sc.status, kStatusInternal);
+            continue;
+        }
         if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) sc.ranges[t].x = (uint32_t)k;
         if (k == P - 1 || (uint32_t)(keys[k + 1] >> 32) != t) sc.ranges[t].y = (uint32_t)(k + 1);
     }
@@ -337,7 +345,7 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
     }
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (sb_max > 0) {
-        k_ranges<<<grid_stride_blocks, 256, 0, s>>>(capacity, sc.keys[buf], sc);
+        k_ranges<<<grid_stride_blocks, 256, 0, s>>>(capacity, (uint32_t)tiles, sc.keys[buf], sc);
         ++launched;
     }
     *out_buf = buf;

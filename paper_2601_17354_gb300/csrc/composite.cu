@@ -38,8 +38,8 @@ __device__ __forceinline__ float entry_alpha(float dx, float dy, float4 con, flo
 }
 
 __global__ void __launch_bounds__(kTilePixels)
-k_composite_fwd(int W, int H, int TX, float3 bg, const uint32_t* __restrict__ vals, Scratch sc,
-                float* __restrict__ image) {
+k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
+                Scratch sc, float* __restrict__ image) {
     __shared__ float4 s_xyo[kBatch];
     __shared__ float4 s_con[kBatch];
     __shared__ float4 s_rgb[kBatch];
@@ -56,7 +56,11 @@ k_composite_fwd(int W, int H, int TX, float3 bg, const uint32_t* __restrict__ va
         if (__syncthreads_count(done) == kTilePixels) break;
         const uint32_t k = base + threadIdx.x;
         if (k < range.y) {
-            const uint32_t id = vals[k];
+            uint32_t id = vals[k];
+            if (id >= n) {
+                atomicOr(sc.status, kStatusInternal);
+                id = 0;
+            }
             s_xyo[threadIdx.x] = sc.xyo[id];
             s_con[threadIdx.x] = sc.conic[id];
             s_rgb[threadIdx.x] = sc.rgb[id];
@@ -160,7 +164,11 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
         const int cnt = (int)(end - start);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            const uint32_t id = vals[range.x + start + threadIdx.x];
+            uint32_t id = vals[range.x + start + threadIdx.x];
+            if (id >= n) {
+                atomicOr(sc.status, kStatusInternal);
+                id = 0;
+            }
             s_id[threadIdx.x] = id;
             s_xyo[threadIdx.x] = sc.xyo[id];
             s_con[threadIdx.x] = sc.conic[id];
@@ -216,10 +224,10 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
 
 }  // namespace
 
-int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, const Scratch& sc,
-                          float* image, cudaStream_t s) {
+int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+                         const Scratch& sc, float* image, cudaStream_t s) {
     k_composite_fwd<<<TX * TY, kTilePixels, 0, s>>>(cam.width, cam.height, TX,
-                                                     make_float3(cam.bg[0], cam.bg[1], cam.bg[2]),
+                                                     make_float3(cam.bg[0], cam.bg[1], cam.bg[2]), n,
                                                      sc.vals[buf], sc, image);
     return 1;
 }

@@ -50,14 +50,26 @@ k_loss_l1(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (unsigned k = 0; k < gridDim.x; ++k) {
-            a += (double)((volatile float*)partials)[k];
-            b += (double)((volatile float*)partials)[gridDim.x + k];
+    // last CTA: fixed-order sum of the partials (strided per thread, then a fixed tree)
+    __shared__ double d1[kThreads], d2[kThreads];
+    double a = 0.0, b = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += kThreads) {
+        a += (double)__ldcg(partials + k);
+        b += (double)__ldcg(partials + gridDim.x + k);
+    }
+    d1[threadIdx.x] = a;
+    d2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            d1[threadIdx.x] += d1[threadIdx.x + w];
+            d2[threadIdx.x] += d2[threadIdx.x + w];
         }
-        out[0] = (float)(a / (double)n);
-        out[1] = (float)b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = (float)(d1[0] / (double)n);
+        out[1] = (float)d2[0];
         *ticket = 0;
     }
 }

@@ -21,6 +21,7 @@ constexpr int kMaxPasses = 8;
 // device status word bits
 constexpr int32_t kStatusCapacity = 1;
 constexpr int32_t kStatusNonfinite = 2;
+constexpr int32_t kStatusInternal = 4;  // an index failed its bounds check; the access was skipped
 
 // Per-Gaussian projected record read by the compositing kernels (gathered by canonical index).
 //   xyo   = (u, v, opacity, unused)   screen-space mean and opacity
@@ -76,8 +77,8 @@ int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cud
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
-int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, const Scratch& sc,
-                          float* image, cudaStream_t s);
+int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+                         const Scratch& sc, float* image, cudaStream_t s);
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
                           const Scratch& sc, const float* dL_dimage, cudaStream_t s);
 

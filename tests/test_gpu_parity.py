@@ -94,7 +94,9 @@ def test_backward_accumulates(R):
     rast.backward(dL, g2)
     rast.backward(dL, g2)
     torch.cuda.synchronize()
-    assert torch.allclose(g2.data, 2 * g1.data, rtol=1e-5, atol=1e-9)
+    # float atomics add in a scheduling-dependent order: equal up to rounding
+    assert rel_l2(g2.data.cpu().numpy(), 2 * g1.data.cpu().numpy()) < 1e-5
+    assert torch.count_nonzero(g1.data) > 0
 
 
 # ----------------------------------------------------------------------------------------------
@@ -231,5 +233,7 @@ def test_adam_matches_oracle(R, n, degree):
     torch.cuda.synchronize()
     assert torch.count_nonzero(G.data) == 0
     assert np.allclose(P.data.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
-    assert np.allclose(M.data.cpu().numpy(), mo, rtol=1e-4, atol=1e-9)
-    assert np.allclose(V.data.cpu().numpy(), vo, rtol=1e-4, atol=1e-12)
+    # fp32 moments against FP64: m can cancel towards zero, so the absolute floor scales with m
+    mg = M.data.cpu().numpy()
+    assert np.all(np.abs(mg - mo) <= 1e-5 * np.abs(mo) + 1e-6 * np.abs(mo).max())
+    assert np.allclose(V.data.cpu().numpy(), vo, rtol=1e-5, atol=1e-6 * vo.max())
