@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="short run for a profiler: one capacity probe, random targets, --steps "
+                         "steps, few launches before them; prints no bench line")
     return ap.parse_args()
 
 
@@ -356,9 +359,31 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile(args):
+    import torch
+    from paper_2601_17354_gb300 import rasterizer as R
+    torch.cuda.set_device(0)
+    sc, cams = make_workload()
+    params = R.GaussianBuffer.from_arrays(sc.init)
+    probe = R.Rasterizer()
+    probe.render(params, cams[0])
+    cap = int(probe.check_status() * 1.5) + 4096
+    del probe
+    rast = R.Rasterizer(pair_capacity=cap)
+    tr = R.Trainer(params, rast)
+    target = torch.rand(3, HEIGHT, WIDTH, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    for k in range(args.steps):
+        tr.step(cams[0], target)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": True, "steps": args.steps, "status": rast.status()[0],
+                      "launches": rast.launch_count()}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_run:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
