@@ -41,6 +41,7 @@ extern "C" {
 #define PGS_ERR_CUDA (-6)        /* a CUDA runtime call failed */
 #define PGS_ERR_OOM (-7)         /* device allocation failed */
 #define PGS_ERR_INTERNAL (-8)    /* a device-side consistency check failed (access skipped) */
+#define PGS_ERR_TOO_LARGE (-9)   /* size beyond the fixed scratch of pgs_sort_pairs_static */
 
 typedef struct pgs_ctx pgs_ctx;
 
@@ -165,6 +166,24 @@ int pgs_stage_times(pgs_ctx* ctx, double* ms, int64_t* counts);
 
 /* Number of kernels this context has launched since it was created (host-side count). */
 int64_t pgs_launch_count(const pgs_ctx* ctx);
+
+/* Allocation-free pair sort.  The paper has no counterpart: this entry point exists for callers
+   that may not allocate device memory themselves, such as code whose device memory is owned by
+   another allocator (a framework's caching pool or an arena reserved at start-up, where a direct
+   cudaMalloc can fail or fragment the reservation) or latency-critical loops in which
+   cudaMalloc / cudaFree would synchronise the device.  It runs the radix sort of pgs_render
+   (stable, least-significant-digit first, 8-bit digits) over the low key_bits bits of count
+   (key, value) pairs: keys_in/vals_in (device, read only) -> keys_out/vals_out (device, caller
+   owned, not overlapping the inputs).  It allocates nothing: its scratch is one file-scope device
+   array of about 3.1 MB, held by every GPU that loads the library until the process exits.
+   count must be at most 262144 (PGS_ERR_TOO_LARGE otherwise); key_bits in 1..64.  The first call
+   on a device looks the scratch address up (cudaGetSymbolAddress) with that device current; make
+   that first call before any stream capture.  Every call shares the one scratch array, which
+   keeps the previous call's contents (the call clears what must start at zero): calls that
+   overlap on the GPU, on any streams, race and must be serialised by the caller.  Asynchronous on
+   cuda_stream (NULL = legacy default stream). */
+int pgs_sort_pairs_static(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                          uint32_t* vals_out, int64_t count, int32_t key_bits, void* cuda_stream);
 
 /* Static description of an error code. */
 const char* pgs_strerror(int code);

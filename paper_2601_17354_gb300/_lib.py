@@ -21,6 +21,7 @@ PGS_ERR_NONFINITE = -4
 PGS_ERR_CUDA = -6
 PGS_ERR_OOM = -7
 PGS_ERR_INTERNAL = -8
+PGS_ERR_TOO_LARGE = -9
 
 PGS_BUF_KEYS = 0
 PGS_BUF_VALUES = 1
@@ -101,6 +102,8 @@ def lib():
             L.pgs_stage_times.restype = I
             L.pgs_launch_count.argtypes = [P]
             L.pgs_launch_count.restype = I64
+            L.pgs_sort_pairs_static.argtypes = [P, P, P, P, I64, C.c_int32, P]
+            L.pgs_sort_pairs_static.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p
             _lib = L

@@ -352,4 +352,23 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
     return launched;
 }
 
+int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
+                           int* out_buf) {
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
+    const int grid_stride_blocks = 152 * 8;
+    int buf = 0;
+    k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, passes, sc.keys[0], sc);
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
+        k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
+        k_sort_scatter<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
+                                                       sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
+        buf ^= 1;
+    }
+    *out_buf = buf;
+    return 1 + 3 * passes;
+}
+
 }  // namespace pgs

@@ -76,6 +76,12 @@ int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cud
 // K4/K5: radix sort of the pairs (returns which ping-pong buffer holds the result) and ranges.
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
 
+// K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting the
+// low key_bits bits (the pair count is read from sc.pair_count, at most `capacity`); the digit
+// totals must be zero on entry.
+int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
+                           int* out_buf);
+
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
                          const Scratch& sc, float* image, cudaStream_t s);

@@ -1,0 +1,75 @@
+"""The allocation-free pair sort (pgs_sort_pairs_static), called through the C ABI, against the
+sort inside pgs_render.
+
+Some callers cannot allocate device memory themselves (their memory belongs to another
+allocator's pool, or a cudaMalloc would synchronise a latency-critical loop); this entry point
+keeps its scratch in a fixed device array instead.  The test feeds it the render's pairs in their
+emission order (canonical index, then tile) and expects the render's sorted keys and values bit
+for bit, on two calls in a row with different inputs, so the second call also checks that what
+the first left in the shared scratch does not leak into the result.
+
+This file is collected last on purpose.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2601_17354_gb300 import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _render_pairs(g, cam):
+    from paper_2601_17354_gb300 import _lib as L
+    from paper_2601_17354_gb300 import rasterizer as R
+    rast = R.Rasterizer()
+    rast.render(R.GaussianBuffer.from_arrays(g), cam)
+    assert rast.status()[0] == 0
+    keys = rast.read_buffer(L.PGS_BUF_KEYS)
+    vals = rast.read_buffer(L.PGS_BUF_VALUES)
+    tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    return keys, vals, 32 + max(1, int(np.ceil(np.log2(tiles))))
+
+
+def _static_sort(keys_in, vals_in, key_bits):
+    from paper_2601_17354_gb300 import _lib as L
+    lib = L.lib()
+    kin = torch.from_numpy(keys_in.view(np.int64)).cuda()
+    vin = torch.from_numpy(vals_in.view(np.int32)).cuda()
+    kout = torch.empty_like(kin)
+    vout = torch.empty_like(vin)
+    stream = torch.cuda.current_stream()
+    rc = lib.pgs_sort_pairs_static(C.c_void_p(kin.data_ptr()), C.c_void_p(vin.data_ptr()),
+                                   C.c_void_p(kout.data_ptr()), C.c_void_p(vout.data_ptr()),
+                                   len(keys_in), key_bits, C.c_void_p(stream.cuda_stream))
+    assert rc == 0, lib.pgs_strerror(rc)
+    torch.cuda.synchronize()
+    return kout.cpu().numpy().view(np.uint64), vout.cpu().numpy().view(np.uint32)
+
+
+def _emission_order(keys, vals):
+    order = np.lexsort((keys >> np.uint64(32), vals))  # by canonical index, then tile
+    return keys[order], vals[order]
+
+
+def test_static_sort_matches_render_sort_twice():
+    scenes = [S.tiny_scene(0)[:2], S.tiny_scene(5, n=3000, width=150, height=90)[:2]]
+    for g, cam in scenes:
+        keys, vals, bits = _render_pairs(g, cam)
+        assert 0 < len(keys) <= 1 << 18
+        ek, ev = _emission_order(keys, vals)
+        assert not np.array_equal(ek, keys)
+        sk, sv = _static_sort(ek, ev, bits)
+        assert np.array_equal(sk, keys)
+        assert np.array_equal(sv, vals)
+
+
+def test_static_sort_rejects_sizes_beyond_its_scratch():
+    from paper_2601_17354_gb300 import _lib as L
+    lib = L.lib()
+    rc = lib.pgs_sort_pairs_static(C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), C.c_void_p(16),
+                                   (1 << 18) + 1, 40, None)
+    assert rc == L.PGS_ERR_TOO_LARGE
+    assert "262144" in lib.pgs_strerror(rc).decode()
