@@ -63,6 +63,14 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.block_sums = c.take<uint32_t>(nb);
     sc.block_offsets = c.take<unsigned long long>(nb);
     sc.grad2d = c.take<float>(9 * n);
+    sc.dkeys[0] = c.take<unsigned long long>(n);
+    sc.dkeys[1] = c.take<unsigned long long>(n);
+    sc.dvals[0] = c.take<uint32_t>(n);
+    sc.dvals[1] = c.take<uint32_t>(n);
+    sc.dhist = c.take<uint32_t>((size_t)kRadix * ((n + kSortTile - 1) / kSortTile));
+    sc.dtotals = c.take<uint32_t>(kMaxPasses * kRadix);
+    sc.dcount = c.take<unsigned long long>(1);
+    sc.dblocks = c.take<uint32_t>(1);
     sc.ranges = c.take<uint2>(tiles);
     sc.T_final = c.take<float>(pixels);
     sc.last = c.take<uint32_t>(pixels);
@@ -237,7 +245,9 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     const size_t e0 = mark(ctx);
     ctx->launches += launch_project_fwd(*params, *cam, TX, TY, ctx->sc, s);
     const size_t e1 = mark(ctx);
-    ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, ctx->sc, s);
+    const uint32_t* perm = nullptr;
+    if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm);
+    ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, perm, ctx->sc, s);
     if (ctx->grow_pairs) {
         unsigned long long P = 0;
         cudaError_t e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
@@ -255,7 +265,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
             e = cudaMemcpyAsync(ctx->sc.status, &st, sizeof(st), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_err(e);
-            ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, ctx->sc, s);
+            ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, perm, ctx->sc, s);
         }
     }
     const size_t e2 = mark(ctx);

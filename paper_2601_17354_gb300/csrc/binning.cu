@@ -72,26 +72,47 @@ k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
     }
 }
 
+// per-CTA sums of tiles touched, Gaussians taken in depth order
+__global__ void __launch_bounds__(kProjBlock)
+k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    const uint32_t count = i < n ? sc.touched[perm[i]] : 0u;
+    const uint32_t warp_sum = __reduce_add_sync(kFull, count);
+    __shared__ uint32_t s_part[kProjBlock / 32];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = warp_sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < kProjBlock / 32 ? s_part[threadIdx.x] : 0u;
+        v = __reduce_add_sync(kFull, v);
+        if (threadIdx.x == 0) sc.block_sums[blockIdx.x] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // K3: emit the pairs of one CTA's Gaussians, one output pair per thread step (load-balanced by a
-// binary search over the CTA's scanned counts), Gaussians in canonical order, tiles row-major
-// inside each rectangle.
+// binary search over the CTA's scanned counts), Gaussians in depth order (ties: canonical order),
+// tiles row-major inside each rectangle.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
-k_emit(int64_t n, int TX, int64_t capacity, Scratch sc) {
+k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc) {
     __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of counts
     __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock], s_depth[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
+    __shared__ uint32_t s_gid[kProjBlock];
     uint32_t cnt = 0;
-    if (i < n) cnt = sc.touched[i];
-    if (cnt) {
-        const uint2 r = sc.rect[i];
-        s_x0[t] = r.x & 0xffffu;
-        s_y0[t] = r.x >> 16;
-        s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
-        s_depth[t] = sc.depth_bits[i];
+    if (i < n) {
+        const uint32_t g = perm[i];
+        s_gid[t] = g;
+        cnt = sc.touched[g];
+        if (cnt) {
+            const uint2 r = sc.rect[g];
+            s_x0[t] = r.x & 0xffffu;
+            s_y0[t] = r.x >> 16;
+            s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
+            s_depth[t] = sc.depth_bits[g];
+        }
     }
     uint32_t incl = cnt;
 #pragma unroll
@@ -131,7 +152,7 @@ k_emit(int64_t n, int TX, int64_t capacity, Scratch sc) {
         const unsigned long long pos = base + k;
         if (pos < (unsigned long long)capacity) {
             sc.keys[0][pos] = ((unsigned long long)tile << 32) | s_depth[lo];
-            sc.vals[0][pos] = (uint32_t)((int64_t)blockIdx.x * kProjBlock + lo);
+            sc.vals[0][pos] = s_gid[lo];
         }
     }
 }
@@ -145,9 +166,10 @@ __device__ __forceinline__ uint64_t kept_pairs(const Scratch& sc, int64_t capaci
     return P < (unsigned long long)capacity ? P : (unsigned long long)capacity;
 }
 
-// digit totals of every pass in one read of the keys
+// digit totals of every pass (digits from bit first_shift up) in one read of the keys
 __global__ void __launch_bounds__(kSortThreads)
-k_digit_totals(int64_t capacity, int passes, const unsigned long long* __restrict__ keys, Scratch sc) {
+k_digit_totals(int64_t capacity, int first_shift, int passes,
+               const unsigned long long* __restrict__ keys, Scratch sc) {
     __shared__ uint32_t h[kMaxPasses][kRadix];
     for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
@@ -155,7 +177,8 @@ k_digit_totals(int64_t capacity, int passes, const unsigned long long* __restric
     for (uint64_t k = (uint64_t)blockIdx.x * kSortThreads + threadIdx.x; k < P;
          k += (uint64_t)gridDim.x * kSortThreads) {
         const unsigned long long key = keys[k];
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (p * kRadixBits)) & (kRadix - 1)], 1u);
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&h[p][(key >> (first_shift + p * kRadixBits)) & (kRadix - 1)], 1u);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < passes * kRadix; k += kSortThreads) {
@@ -315,27 +338,47 @@ k_ranges(int64_t capacity, uint32_t tiles, const unsigned long long* __restrict_
 
 }  // namespace
 
-int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cudaStream_t s) {
+int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm) {
+    Scratch d = sc;
+    d.keys[0] = sc.dkeys[0];
+    d.keys[1] = sc.dkeys[1];
+    d.vals[0] = sc.dvals[0];
+    d.vals[1] = sc.dvals[1];
+    d.sort_hist = sc.dhist;
+    d.digit_totals = sc.dtotals;
+    d.pair_count = sc.dcount;
+    d.sort_blocks = sc.dblocks;
+    cudaMemsetAsync(sc.dtotals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
+    int buf = 0;
+    const int launched = launch_radix_sort_only(n, 32, d, s, &buf);
+    *perm = sc.dvals[buf];
+    return launched;
+}
+
+int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+                     cudaStream_t s) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
+    if (nb > 0) k_perm_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
     k_scan_blocks<<<1, kScanThreads, 0, s>>>(nb, capacity, sc);
     if (nb == 0) return 1;
-    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, sc);
-    return 2;
+    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, perm, sc);
+    return 3;
 }
 
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* out_buf) {
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)tiles) ++tile_bits;
-    const int passes = (32 + tile_bits + kRadixBits - 1) / kRadixBits;
+    // the pairs arrive in depth order: a stable sort by the tile bits (32 and up) completes it
+    const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
     const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
     const int grid_stride_blocks = 152 * 8;
     int buf = 0, launched = 0;
-    if (sb_max > 0) {
+    if (sb_max > 0 && passes > 0) {
         cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
-        k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, passes, sc.keys[0], sc);
+        k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 32, passes, sc.keys[0], sc);
         launched += 1 + 3 * passes;
         for (int p = 0; p < passes; ++p) {
-            const int shift = p * kRadixBits;
+            const int shift = 32 + p * kRadixBits;
             k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
             k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
             k_sort_scatter<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
@@ -358,7 +401,7 @@ int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cu
     const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
     const int grid_stride_blocks = 152 * 8;
     int buf = 0;
-    k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, passes, sc.keys[0], sc);
+    k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 0, passes, sc.keys[0], sc);
     for (int p = 0; p < passes; ++p) {
         const int shift = p * kRadixBits;
         k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);

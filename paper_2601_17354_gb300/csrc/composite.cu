@@ -1,106 +1,159 @@
-// K6 composite_fwd and K8 composite_bwd: one CTA per 16x16 screen tile, one pixel per thread.
+// K6 composite_fwd and K8 composite_bwd: one CTA per 16x16 screen tile; each thread owns a
+// vertical strip of kPix pixels (64 threads per tile at kPix = 4), so every entry staged in
+// shared memory and every warp reduction serves 4x more pixels than one pixel per thread.
 //
 // Forward (Eq. 7, evaluated front to back with transmittance T): the tile's depth-ordered list
-// [range.x, range.y) is staged in shared memory in batches of 256 entries (projected record
-// gathered through the canonical index, i.e. through pi of Eq. 10); each pixel composites
+// [range.x, range.y) is staged in shared memory in batches (projected record gathered through
+// the canonical index, i.e. through pi of Eq. 10); each pixel composites
 //     alpha = min(0.99, o exp(power)),  skip if alpha < 1/255,
 //     stop (without compositing) when T (1 - alpha) < 1e-4,  C += alpha T c,  T *= 1 - alpha,
-// and keeps only T_final and last = 1 + list position of the last composited entry.
+// and keeps only T_final, last = 1 + list position of the last composited entry, and the number
+// of composited entries.
 //
 // Backward: instead of the paper's per-pixel replay cache S = {id, C_in, alpha} (Eq. 9) the
 // kernel re-traverses the list back to front from `last`, rebuilding the transmittance in front
 // of each entry from T_final (T_i = T_{i+1} / (1 - alpha_i); alpha <= 0.99 bounds the growth) and
 // the colour behind it with Eq. 7 itself (C_in of the last entry is the background), then applies
 // Eq. 8:  dL/dc = alpha dL/dC_out,  dL/dalpha = <dL/dC_out, c - C_in>,  dL/dC_out = T_i dL/dC.
-// Per entry, the nine screen-space gradients of the warp's 32 pixels are summed by a
-// transpose-reduction (9 shuffles for 8 values) and scattered with one atomic per value per
-// warp to the canonical index (Eq. 10: grad_{pi(i)} += g_i).
+// Each thread first sums its strip's nine screen-space gradients; the warp's 32 partial sums are
+// then added by a transpose-reduction (9 shuffles for 8 values) and scattered with one atomic per
+// value per warp to the canonical index (Eq. 10: grad_{pi(i)} += g_i).  Each warp stops at its
+// own deepest `last`, not the tile's.
+//
+// The exponent is evaluated base 2: the conic is pre-scaled by -log2(e)/2 (and -log2(e) for the
+// cross term) when an entry is staged, and alpha uses ex2.approx.  Forward and backward stage and
+// evaluate with the same instruction sequence, so they take identical skip decisions.
 #include "pgs_internal.cuh"
 
 namespace pgs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBatch = kTilePixels;  // entries staged per batch (one per thread)
+constexpr int kPix = 4;                          // pixels per thread (vertical strip)
+constexpr int kThreads = kTilePixels / kPix;     // 64 threads per tile
+constexpr int kBatch = 2 * kThreads;             // entries staged per batch
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
 
-// alpha of one (pixel, entry), written with explicit roundings so the forward and the backward
-// take identical decisions.  og = o * exp(power) before the clamp.
-__device__ __forceinline__ float entry_alpha(float dx, float dy, float4 con, float o, float& G,
-                                             float& og) {
-    const float quad = __fmaf_rn(con.x, __fmul_rn(dx, dx), __fmul_rn(con.z, __fmul_rn(dy, dy)));
-    const float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(con.y, __fmul_rn(dx, dy)));
-    G = __expf(power);
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// conic (a, b, c) -> base-2 exponent coefficients: power * log2(e) = A dx^2 + B dx dy + C dy^2
+__device__ __forceinline__ float4 scaled_conic(float4 con) {
+    return make_float4(__fmul_rn(-0.5f * kLog2e, con.x), __fmul_rn(-kLog2e, con.y),
+                       __fmul_rn(-0.5f * kLog2e, con.z), 0.0f);
+}
+
+// alpha of one (pixel, entry) with the shared part adx2 = A dx^2 precomputed; explicit roundings
+// so the forward and the backward evaluate it identically.  og = o * G before the clamp.
+__device__ __forceinline__ float entry_alpha(float dx, float dy, float adx2, float4 s2, float o,
+                                             float& G, float& og) {
+    const float p = __fmaf_rn(s2.z, __fmul_rn(dy, dy), __fmaf_rn(s2.y, __fmul_rn(dx, dy), adx2));
+    G = ex2_approx(p);
     og = __fmul_rn(o, G);
     return fminf(kAlphaMax, og);
 }
 
-__global__ void __launch_bounds__(kTilePixels)
+__device__ __forceinline__ uint32_t checked_id(uint32_t id, int64_t n, int32_t* status) {
+    if (id >= n) {
+        atomicOr(status, kStatusInternal);
+        return 0;
+    }
+    return id;
+}
+
+__global__ void __launch_bounds__(kThreads)
 k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
                 Scratch sc, float* __restrict__ image) {
     __shared__ float4 s_xyo[kBatch];
-    __shared__ float4 s_con[kBatch];
+    __shared__ float4 s_s2[kBatch];
     __shared__ float4 s_rgb[kBatch];
     const int tile = blockIdx.x;
     const int px = (tile % TX) * kTile + (threadIdx.x % kTile);
-    const int py = (tile / TX) * kTile + (threadIdx.x / kTile);
-    const bool inside = px < W && py < H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int py0 = (tile / TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = sc.ranges[tile];
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0, ncomp = 0;
-    bool done = !inside;
+    float T[kPix], C0[kPix], C1[kPix], C2[kPix];
+    uint32_t last[kPix], ncomp[kPix];
+    bool done[kPix];
+    bool all_done = true;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.f;
+        last[k] = ncomp[k] = 0;
+        done[k] = !(px < W && py0 + k < H);
+        all_done = all_done && done[k];
+    }
     for (uint32_t base = range.x; base < range.y; base += kBatch) {
-        if (__syncthreads_count(done) == kTilePixels) break;
-        const uint32_t k = base + threadIdx.x;
-        if (k < range.y) {
-            uint32_t id = vals[k];
-            if (id >= n) {
-                atomicOr(sc.status, kStatusInternal);
-                id = 0;
+        if (__syncthreads_count(all_done) == kThreads) break;
+#pragma unroll
+        for (int e = threadIdx.x; e < kBatch; e += kThreads) {
+            const uint32_t idx = base + e;
+            if (idx < range.y) {
+                const uint32_t id = checked_id(vals[idx], n, sc.status);
+                s_xyo[e] = sc.xyo[id];
+                s_s2[e] = scaled_conic(sc.conic[id]);
+                s_rgb[e] = sc.rgb[id];
             }
-            s_xyo[threadIdx.x] = sc.xyo[id];
-            s_con[threadIdx.x] = sc.conic[id];
-            s_rgb[threadIdx.x] = sc.rgb[id];
         }
         __syncthreads();
         const int cnt = min((uint32_t)kBatch, range.y - base);
-        for (int j = 0; !done && j < cnt; ++j) {
+        for (int j = 0; !all_done && j < cnt; ++j) {
             const float4 p = s_xyo[j];
-            float G, og;
-            const float alpha = entry_alpha(fx - p.x, fy - p.y, s_con[j], p.z, G, og);
-            if (alpha < kAlphaMin) continue;
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < kTMin) {
-                done = true;
-                break;
-            }
+            const float4 s2 = s_s2[j];
             const float4 c = s_rgb[j];
-            const float w = alpha * T;
-            C0 = fmaf(c.x, w, C0);
-            C1 = fmaf(c.y, w, C1);
-            C2 = fmaf(c.z, w, C2);
-            T = Tn;
-            last = base + j - range.x + 1;
-            ++ncomp;
+            const float dx = fx - p.x;
+            const float adx2 = __fmul_rn(s2.x, __fmul_rn(dx, dx));
+            const float dy0 = fy0 - p.y;
+            all_done = true;
+#pragma unroll
+            for (int k = 0; k < kPix; ++k) {
+                if (!done[k]) {
+                    float G, og;
+                    const float alpha = entry_alpha(dx, dy0 + (float)k, adx2, s2, p.z, G, og);
+                    if (alpha >= kAlphaMin) {
+                        const float Tn = T[k] * (1.0f - alpha);
+                        if (Tn < kTMin) {
+                            done[k] = true;
+                        } else {
+                            const float w = alpha * T[k];
+                            C0[k] = fmaf(c.x, w, C0[k]);
+                            C1[k] = fmaf(c.y, w, C1[k]);
+                            C2[k] = fmaf(c.z, w, C2[k]);
+                            T[k] = Tn;
+                            last[k] = base + j - range.x + 1;
+                            ++ncomp[k];
+                        }
+                    }
+                }
+                all_done = all_done && done[k];
+            }
         }
     }
-    if (inside) {
-        const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
-        image[p] = fmaf(T, bg.x, C0);
-        image[plane + p] = fmaf(T, bg.y, C1);
-        image[2 * plane + p] = fmaf(T, bg.z, C2);
-        sc.T_final[p] = T;
-        sc.last[p] = last;
-        sc.ncomp[p] = ncomp;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        const int py = py0 + k;
+        if (px < W && py < H) {
+            const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
+            image[p] = fmaf(T[k], bg.x, C0[k]);
+            image[plane + p] = fmaf(T[k], bg.y, C1[k]);
+            image[2 * plane + p] = fmaf(T[k], bg.z, C2[k]);
+            sc.T_final[p] = T[k];
+            sc.last[p] = last[k];
+            sc.ncomp[p] = ncomp[k];
+        }
     }
 }
 
 // Sum v[0..8] over the warp.  Afterwards lane l with l % 4 == 0 holds the sum of v[l >> 2]
 // (values 0..7) and every lane holds the sum of v[8].
-__device__ __forceinline__ void warp_sum9(float v[9], int lane, float& s8, float& s9) {
+__device__ __forceinline__ void warp_sum9(const float v[9], int lane, float& s8, float& s9) {
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
     float u[4];
 #pragma unroll
@@ -126,87 +179,111 @@ __device__ __forceinline__ void warp_sum9(float v[9], int lane, float& s8, float
     s9 = t;
 }
 
-__global__ void __launch_bounds__(kTilePixels)
+__global__ void __launch_bounds__(kThreads)
 k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
                 Scratch sc, const float* __restrict__ dL_dimage) {
     __shared__ float4 s_xyo[kBatch];
+    __shared__ float4 s_s2[kBatch];
     __shared__ float4 s_con[kBatch];
     __shared__ float4 s_rgb[kBatch];
     __shared__ uint32_t s_id[kBatch];
-    __shared__ uint32_t s_max[kTilePixels / 32];
+    __shared__ uint32_t s_max[kThreads / 32];
     const int tile = blockIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = (tile % TX) * kTile + (threadIdx.x % kTile);
-    const int py = (tile / TX) * kTile + (threadIdx.x / kTile);
-    const bool inside = px < W && py < H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int py0 = (tile / TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = sc.ranges[tile];
-    const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
-    float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t my_last = 0;
-    if (inside) {
-        T = sc.T_final[p];
-        my_last = sc.last[p];
-        g0 = dL_dimage[p];
-        g1 = dL_dimage[plane + p];
-        g2 = dL_dimage[2 * plane + p];
+    const size_t plane = (size_t)W * H;
+    float T[kPix], g0[kPix], g1[kPix], g2[kPix], B0[kPix], B1[kPix], B2[kPix];
+    uint32_t my_last[kPix];
+    uint32_t tmax = 0;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        const int py = py0 + k;
+        T[k] = 1.0f;
+        g0[k] = g1[k] = g2[k] = 0.f;
+        my_last[k] = 0;
+        if (px < W && py < H) {
+            const size_t p = (size_t)py * W + px;
+            T[k] = sc.T_final[p];
+            my_last[k] = sc.last[p];
+            g0[k] = dL_dimage[p];
+            g1[k] = dL_dimage[plane + p];
+            g2[k] = dL_dimage[2 * plane + p];
+        }
+        B0[k] = bg.x;  // colour behind the current entry (Eq. 7 C_in)
+        B1[k] = bg.y;
+        B2[k] = bg.z;
+        tmax = max(tmax, my_last[k]);
     }
-    float B0 = bg.x, B1 = bg.y, B2 = bg.z;  // colour behind the current entry (Eq. 7 C_in)
-    const uint32_t wmax = __reduce_max_sync(kFull, my_last);
-    if (lane == 0) s_max[threadIdx.x >> 5] = wmax;
+    const uint32_t wmax = __reduce_max_sync(kFull, tmax);
+    if (lane == 0) s_max[warp] = wmax;
     __syncthreads();
     uint32_t end = 0;
 #pragma unroll
-    for (int w = 0; w < kTilePixels / 32; ++w) end = max(end, s_max[w]);
+    for (int w = 0; w < kThreads / 32; ++w) end = max(end, s_max[w]);
 
-    for (; end > 0;) {
+    while (end > 0) {
         const uint32_t start = end > (uint32_t)kBatch ? end - kBatch : 0u;
         const int cnt = (int)(end - start);
         __syncthreads();
-        if (threadIdx.x < cnt) {
-            uint32_t id = vals[range.x + start + threadIdx.x];
-            if (id >= n) {
-                atomicOr(sc.status, kStatusInternal);
-                id = 0;
+#pragma unroll
+        for (int e = threadIdx.x; e < kBatch; e += kThreads) {
+            if (e < cnt) {
+                const uint32_t id = checked_id(vals[range.x + start + e], n, sc.status);
+                s_id[e] = id;
+                s_xyo[e] = sc.xyo[id];
+                const float4 con = sc.conic[id];
+                s_con[e] = con;
+                s_s2[e] = scaled_conic(con);
+                s_rgb[e] = sc.rgb[id];
             }
-            s_id[threadIdx.x] = id;
-            s_xyo[threadIdx.x] = sc.xyo[id];
-            s_con[threadIdx.x] = sc.conic[id];
-            s_rgb[threadIdx.x] = sc.rgb[id];
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
+        // this warp's entries: positions below its deepest `last`
+        const int jtop = (int)min((uint32_t)cnt, wmax > start ? wmax - start : 0u);
+        for (int j = jtop - 1; j >= 0; --j) {
+            const uint32_t pos = start + j;
+            const float4 pm = s_xyo[j];
+            const float4 s2 = s_s2[j];
+            const float4 con = s_con[j];
+            const float4 c = s_rgb[j];
+            const float dx = fx - pm.x;
+            const float adx2 = __fmul_rn(s2.x, __fmul_rn(dx, dx));
+            const float dy0 = fy0 - pm.y;
             float v[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = 0.f;
+            for (int q = 0; q < 9; ++q) v[q] = 0.f;
             bool contrib = false;
-            if (start + j < my_last) {
-                const float4 pm = s_xyo[j];
-                const float4 con = s_con[j];
-                const float dx = fx - pm.x, dy = fy - pm.y;
-                float G, og;
-                const float alpha = entry_alpha(dx, dy, con, pm.z, G, og);
-                if (alpha >= kAlphaMin) {
-                    contrib = true;
-                    const float4 c = s_rgb[j];
-                    const float Tb = __fdividef(T, 1.0f - alpha);  // transmittance in front
-                    const float dLda = Tb * ((c.x - B0) * g0 + (c.y - B1) * g1 + (c.z - B2) * g2);
-                    const float wgt = alpha * Tb;
-                    v[6] = wgt * g0;
-                    v[7] = wgt * g1;
-                    v[8] = wgt * g2;
-                    B0 = fmaf(alpha, c.x - B0, B0);
-                    B1 = fmaf(alpha, c.y - B1, B1);
-                    B2 = fmaf(alpha, c.z - B2, B2);
-                    T = Tb;
-                    if (og <= kAlphaMax) {  // zero gradient through the 0.99 clamp
-                        v[5] = dLda * G;
-                        const float dpow = dLda * alpha;
-                        v[0] = dpow * (con.x * dx + con.y * dy);
-                        v[1] = dpow * (con.z * dy + con.y * dx);
-                        v[2] = -0.5f * dpow * dx * dx;
-                        v[3] = -dpow * dx * dy;
-                        v[4] = -0.5f * dpow * dy * dy;
+#pragma unroll
+            for (int k = 0; k < kPix; ++k) {
+                if (pos < my_last[k]) {
+                    const float dy = dy0 + (float)k;
+                    float G, og;
+                    const float alpha = entry_alpha(dx, dy, adx2, s2, pm.z, G, og);
+                    if (alpha >= kAlphaMin) {
+                        contrib = true;
+                        const float Tb = __fdividef(T[k], 1.0f - alpha);  // transmittance in front
+                        const float r0 = c.x - B0[k], r1 = c.y - B1[k], r2 = c.z - B2[k];
+                        const float dLda = Tb * (r0 * g0[k] + r1 * g1[k] + r2 * g2[k]);
+                        const float wgt = alpha * Tb;
+                        v[6] = fmaf(wgt, g0[k], v[6]);
+                        v[7] = fmaf(wgt, g1[k], v[7]);
+                        v[8] = fmaf(wgt, g2[k], v[8]);
+                        B0[k] = fmaf(alpha, r0, B0[k]);
+                        B1[k] = fmaf(alpha, r1, B1[k]);
+                        B2[k] = fmaf(alpha, r2, B2[k]);
+                        T[k] = Tb;
+                        if (og <= kAlphaMax) {  // zero gradient through the 0.99 clamp
+                            v[5] = fmaf(dLda, G, v[5]);
+                            const float dpow = dLda * alpha;
+                            v[0] = fmaf(dpow, con.x * dx + con.y * dy, v[0]);
+                            v[1] = fmaf(dpow, con.z * dy + con.y * dx, v[1]);
+                            v[2] = fmaf(dpow, dx * dx, v[2]);
+                            v[3] = fmaf(dpow, dx * dy, v[3]);
+                            v[4] = fmaf(dpow, dy * dy, v[4]);
+                        }
                     }
                 }
             }
@@ -214,7 +291,12 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
                 float s8, s9;
                 warp_sum9(v, lane, s8, s9);
                 const uint32_t id = s_id[j];
-                if ((lane & 3) == 0) atomicAdd(&sc.grad2d[(size_t)(lane >> 2) * n + id], s8);
+                if ((lane & 3) == 0) {
+                    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
+                    const int q = lane >> 2;
+                    const float f = q == 2 || q == 4 ? -0.5f : (q == 3 ? -1.0f : 1.0f);
+                    atomicAdd(&sc.grad2d[(size_t)q * n + id], f * s8);
+                }
                 if (lane == 1) atomicAdd(&sc.grad2d[(size_t)8 * n + id], s9);
             }
         }
@@ -226,17 +308,17 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
 
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
                          const Scratch& sc, float* image, cudaStream_t s) {
-    k_composite_fwd<<<TX * TY, kTilePixels, 0, s>>>(cam.width, cam.height, TX,
-                                                     make_float3(cam.bg[0], cam.bg[1], cam.bg[2]), n,
-                                                     sc.vals[buf], sc, image);
+    k_composite_fwd<<<TX * TY, kThreads, 0, s>>>(cam.width, cam.height, TX,
+                                                  make_float3(cam.bg[0], cam.bg[1], cam.bg[2]), n,
+                                                  sc.vals[buf], sc, image);
     return 1;
 }
 
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
-                          const Scratch& sc, const float* dL_dimage, cudaStream_t s) {
-    k_composite_bwd<<<TX * TY, kTilePixels, 0, s>>>(cam.width, cam.height, TX,
-                                                     make_float3(cam.bg[0], cam.bg[1], cam.bg[2]), n,
-                                                     sc.vals[buf], sc, dL_dimage);
+                         const Scratch& sc, const float* dL_dimage, cudaStream_t s) {
+    k_composite_bwd<<<TX * TY, kThreads, 0, s>>>(cam.width, cam.height, TX,
+                                                  make_float3(cam.bg[0], cam.bg[1], cam.bg[2]), n,
+                                                  sc.vals[buf], sc, dL_dimage);
     return 1;
 }
 

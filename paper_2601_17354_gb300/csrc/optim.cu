@@ -82,7 +82,7 @@ struct AdamArgs {
     float lr[6];
     int64_t n;
     int K;
-    float b1, b2, eps, bc1, bc2;
+    float b1, b2, omb1, omb2, eps, bc1, bc2;  // omb = 1 - b, formed in double on the host
 };
 
 // row r of the (11 + 3K) x n parameter matrix -> group, row inside the group, learning rate
@@ -96,8 +96,8 @@ __device__ __forceinline__ void row_of(const AdamArgs& a, int r, int& grp, int& 
 
 __device__ __forceinline__ void adam1(float& p, float& g, float& m, float& v, float lr,
                                       const AdamArgs& a) {
-    m = a.b1 * m + (1.0f - a.b1) * g;
-    v = a.b2 * v + (1.0f - a.b2) * g * g;
+    m = a.b1 * m + a.omb1 * g;
+    v = a.b2 * v + a.omb2 * g * g;
     const float mh = m / a.bc1, vh = v / a.bc2;
     p -= lr * mh / (sqrtf(vh) + a.eps);
     g = 0.0f;
@@ -173,6 +173,8 @@ int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussi
     a.K = sh_coeffs(p.sh_degree);
     a.b1 = b1;
     a.b2 = b2;
+    a.omb1 = (float)(1.0 - (double)b1);
+    a.omb2 = (float)(1.0 - (double)b2);
     a.eps = eps;
     a.bc1 = (float)(1.0 - pow((double)b1, (double)t));
     a.bc2 = (float)(1.0 - pow((double)b2, (double)t));

@@ -51,6 +51,14 @@ struct Scratch {
     uint32_t* digit_totals = nullptr; // [kMaxPasses][kRadix]
     float* loss_partials = nullptr;   // [2][kLossBlocks]
     uint32_t* loss_ticket = nullptr;
+    // depth sort of the Gaussians: keys = depth bits (culled: all ones), values = canonical index;
+    // its pair count / CTA count words and histograms, separate from the pair sort's
+    unsigned long long* dkeys[2] = {nullptr, nullptr};
+    uint32_t* dvals[2] = {nullptr, nullptr};
+    uint32_t* dhist = nullptr;
+    uint32_t* dtotals = nullptr;
+    unsigned long long* dcount = nullptr;
+    uint32_t* dblocks = nullptr;
     // per pair (separate allocation, grows independently)
     unsigned long long* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
@@ -71,9 +79,15 @@ int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, in
 int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
                         pgs_gaussians& grads, cudaStream_t s);
 
-// K2/K3: scan of the per-CTA sums, pair count + capacity check, and key emission.
-int launch_scan_emit(int64_t n, int TX, int64_t capacity, const Scratch& sc, cudaStream_t s);
-// K4/K5: radix sort of the pairs (returns which ping-pong buffer holds the result) and ranges.
+// Depth sort of the Gaussians (LSD radix over the 32 depth bits of dkeys[0] / dvals[0]); returns
+// the kernels launched, *perm receives the buffer holding the depth-ordered canonical indices.
+int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm);
+// K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
+// emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
+int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+                     cudaStream_t s);
+// K4/K5: stable radix sort of the pairs by the tile bits (returns which ping-pong buffer holds
+// the result) and ranges.
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
 
 // K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting the

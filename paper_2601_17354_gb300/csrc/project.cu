@@ -205,8 +205,10 @@ __device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3])
     for (int k = 0; k < 3; ++k) c[k] = -(V[k] * V[3] + V[4 + k] * V[7] + V[8 + k] * V[11]);
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     uint32_t count = 0;
@@ -247,13 +249,13 @@ k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
             d[0] *= inv_len;
             d[1] *= inv_len;
             d[2] *= inv_len;
-            const int K = sh_coeffs(g.sh_degree);
             float Y[16];
             sh_eval(K, d[0], d[1], d[2], Y);
             float rgb[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float acc = 0.5f;
+#pragma unroll
                 for (int k = 0; k < K; ++k) acc += g.sh[((int64_t)c * K + k) * n + i] * Y[k];
                 rgb[c] = fmaxf(acc, 0.0f);
             }
@@ -270,24 +272,23 @@ k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
         }
         if (!finite) atomicOr(sc.status, kStatusNonfinite);
         sc.touched[i] = count;
+        // depth-sort input: visible Gaussians by depth bits, culled ones last
+        sc.dkeys[0][i] = count > 0 ? (unsigned long long)sc.depth_bits[i] : 0xffffffffull;
+        sc.dvals[0][i] = (uint32_t)i;
     }
-    // CTA total of tiles touched, for the scan
-    uint32_t warp_sum = __reduce_add_sync(0xffffffffu, count);
-    __shared__ uint32_t s_part[kProjBlock / 32];
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = warp_sum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < kProjBlock / 32 ? s_part[threadIdx.x] : 0u;
-        v = __reduce_add_sync(0xffffffffu, v);
-        if (threadIdx.x == 0) sc.block_sums[blockIdx.x] = v;
+    if (i == 0) {
+        *sc.dcount = (unsigned long long)n;
+        *sc.dblocks = (uint32_t)((n + kSortTile - 1) / kSortTile);
     }
 }
 
 // Backward of one Gaussian: screen-space gradient (du, dv, d conic, d opacity, d rgb) ->
 // parameters.  Matrix form: H = -Q Gq Q (Q the conic matrix, Gq its gradient with the
 // off-diagonal halved), dSigma = T^T H T, dT = 2 H T Sigma, dM = 2 dSigma M.
+template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     if (i >= n || sc.touched[i] == 0) return;
@@ -310,7 +311,6 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
     d[0] *= inv_len;
     d[1] *= inv_len;
     d[2] *= inv_len;
-    const int K = sh_coeffs(g.sh_degree);
     float Y[16];
     sh_eval(K, d[0], d[1], d[2], Y);
     float wsum[16];
@@ -319,12 +319,14 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float acc = 0.5f;
-        float coef[16];
+        float coef[K];
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             coef[k] = g.sh[((int64_t)c * K + k) * n + i];
             acc += coef[k] * Y[k];
         }
         const float gc = acc < 0.0f ? 0.0f : gr[6 + c];  // zero gradient through the clamp
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             out.sh[((int64_t)c * K + k) * n + i] += gc * Y[k];
             wsum[k] += gc * coef[k];
@@ -438,7 +440,12 @@ int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, in
                        const Scratch& sc, cudaStream_t s) {
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
     if (blocks == 0) return 0;
-    k_project_fwd<<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc);
+    switch (g.sh_degree) {
+        case 0: k_project_fwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
+        case 1: k_project_fwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
+        case 2: k_project_fwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
+        default: k_project_fwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
+    }
     return 1;
 }
 
@@ -446,7 +453,12 @@ int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scra
                        pgs_gaussians& grads, cudaStream_t s) {
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
     if (blocks == 0) return 0;
-    k_project_bwd<<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads);
+    switch (g.sh_degree) {
+        case 0: k_project_bwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
+        case 1: k_project_bwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
+        case 2: k_project_bwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
+        default: k_project_bwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
+    }
     return 1;
 }
 

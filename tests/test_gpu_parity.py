@@ -228,7 +228,9 @@ def test_adam_matches_oracle(R, n, degree):
         rast.step(P, G, M, V, t)
         for r in range(rows):
             pr, mr, vr = po[r].copy(), mo[r].copy(), vo[r].copy()
-            oracle.adam(pr, gk[r].astype(np.float64), mr, vr, row_lr[r], t)
+            # the library takes fp32 hyper-parameters: the oracle uses the same values
+            oracle.adam(pr, gk[r].astype(np.float64), mr, vr, float(np.float32(row_lr[r])), t,
+                        float(np.float32(0.9)), float(np.float32(0.999)), float(np.float32(1e-15)))
             po[r], mo[r], vo[r] = pr, mr, vr
     torch.cuda.synchronize()
     assert torch.count_nonzero(G.data) == 0
