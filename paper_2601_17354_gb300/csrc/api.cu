@@ -72,6 +72,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.dcount = c.take<unsigned long long>(1);
     sc.dblocks = c.take<uint32_t>(1);
     sc.ranges = c.take<uint2>(tiles);
+    sc.tile_order = c.take<uint32_t>(tiles);
     sc.T_final = c.take<float>(pixels);
     sc.last = c.take<uint32_t>(pixels);
     sc.ncomp = c.take<uint32_t>(pixels);
@@ -270,6 +271,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     }
     const size_t e2 = mark(ctx);
     ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
+    ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
     ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, params->n, ctx->sc, image_out, s);
     const size_t e4 = mark(ctx);

@@ -336,7 +336,51 @@ k_ranges(int64_t capacity, uint32_t tiles, const unsigned long long* __restrict_
     }
 }
 
+// One CTA: counting sort of the tiles into 64 half-octave buckets of their list length,
+// heaviest bucket first.  Only the schedule depends on it, never a result.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 64;
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch sc) {
+    __shared__ uint32_t hist[kOrderBuckets], cursor[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    auto slot_of = [&](int t) {
+        const uint2 r = sc.ranges[t];
+        const uint32_t len = r.y - r.x;
+        int b = 0;
+        if (len) {
+            const int l = 31 - __clz(len);
+            b = 2 * l + (l > 0 ? (int)((len >> (l - 1)) & 1u) : 0) + 1;
+        }
+        return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+    };
+    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) atomicAdd(&hist[slot_of(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        uint32_t a = hist[2 * lane], b = hist[2 * lane + 1];
+        uint32_t s = a + b, incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t excl = incl - s;
+        cursor[2 * lane] = excl;
+        cursor[2 * lane + 1] = excl + a;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += kOrderThreads)
+        sc.tile_order[atomicAdd(&cursor[slot_of(t)], 1u)] = (uint32_t)t;
+}
+
 }  // namespace
+
+int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
+    k_tile_order<<<1, kOrderThreads, 0, s>>>(tiles, sc);
+    return 1;
+}
 
 int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm) {
     Scratch d = sc;

@@ -41,6 +41,7 @@ struct Scratch {
     float* grad2d = nullptr;  // [9][n]
     // per tile / pixel
     uint2* ranges = nullptr;
+    uint32_t* tile_order = nullptr;  // tiles by decreasing list length (compositing schedule)
     float* T_final = nullptr;
     uint32_t* last = nullptr;
     uint32_t* ncomp = nullptr;  // entries composited per pixel
@@ -95,6 +96,10 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
 // totals must be zero on entry.
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf);
+
+// Order the tiles by decreasing list length (half-octave buckets), so the compositing grids
+// start the heaviest tiles first.
+int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
