@@ -41,6 +41,7 @@ CROP = 256
 BYTES_PER_GAUSS_PROJECT = 4 * (3 + 3 + 4 + 1 + 3 * (SH_DEGREE + 1) ** 2) + 64
 BYTES_PER_GAUSS_ADAM = 4 * 8 * (11 + 3 * (SH_DEGREE + 1) ** 2)
 BYTES_PER_GAUSS_PROJECT_BWD = 4 * (3 * (11 + 3 * (SH_DEGREE + 1) ** 2) + 9)
+BYTES_PER_GAUSS_BWD_ADAM = 4 * (6 * (11 + 3 * (SH_DEGREE + 1) ** 2) + 9)
 FLOPS_ALPHA = 16        # one alpha evaluation of a (pixel, entry)
 FLOPS_FWD_COMP = 10     # compositing of an entry that passes the alpha test
 FLOPS_BWD_COMP = 38     # Eq. 8 + chain to the nine screen-space gradients of a composited entry
@@ -311,6 +312,8 @@ def run_ours(args):
             roof[k] = ("hbm", N_GAUSS * BYTES_PER_GAUSS_PROJECT / (t * 1e-3) / 1e9, hbm, "GB/s")
         elif k == "adam":
             roof[k] = ("hbm", N_GAUSS * BYTES_PER_GAUSS_ADAM / (t * 1e-3) / 1e9, hbm, "GB/s")
+        elif k == "project_bwd_adam":
+            roof[k] = ("hbm", N_GAUSS * BYTES_PER_GAUSS_BWD_ADAM / (t * 1e-3) / 1e9, hbm, "GB/s")
         elif k == "project_bwd":
             roof[k] = ("hbm", n_vis * BYTES_PER_GAUSS_PROJECT_BWD / (t * 1e-3) / 1e9, hbm, "GB/s")
         elif k == "loss":

@@ -123,6 +123,14 @@ int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads);
 int pgs_step(pgs_ctx* ctx, pgs_gaussians* params, pgs_gaussians* grads, pgs_gaussians* m,
              pgs_gaussians* v, int64_t t);
 
+/* pgs_backward followed by pgs_step for one view, fused: the compositing backward runs as in
+   pgs_backward, then one kernel chains each Gaussian's screen-space gradient to its parameters
+   and applies the Adam update of pgs_step directly (culled Gaussians with a zero gradient), so
+   the parameter gradient is never written to memory.  Equivalent to pgs_backward into zeroed
+   gradients followed by pgs_step; params must be those of the last render. */
+int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* params,
+                      pgs_gaussians* m, pgs_gaussians* v, int64_t t);
+
 /* Synchronise the context's stream, return the first error recorded on the device since the
    last call (PGS_OK if none) and clear it.  *pairs_needed (optional) receives the pair count of
    the last render. */
@@ -151,7 +159,8 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
    read into ms[PGS_NUM_STAGES] and counts[PGS_NUM_STAGES], and resets the accumulators.
    Stages: projection (K1), binning = scan + key emission (K2, K3), sort = radix sort + tile
    ranges (K4, K5), compositing forward (K6), loss (K7), compositing backward (K8), projection
-   backward (K9), Adam (K10).  pgs_profile(ctx, 0) stops recording. */
+   backward (K9), Adam (K10), fused projection backward + Adam (pgs_backward_step).
+   pgs_profile(ctx, 0) stops recording. */
 #define PGS_STAGE_PROJECT 0
 #define PGS_STAGE_BIN 1
 #define PGS_STAGE_SORT 2
@@ -160,7 +169,8 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
 #define PGS_STAGE_COMPOSITE_BWD 5
 #define PGS_STAGE_PROJECT_BWD 6
 #define PGS_STAGE_ADAM 7
-#define PGS_NUM_STAGES 8
+#define PGS_STAGE_PROJECT_BWD_ADAM 8
+#define PGS_NUM_STAGES 9
 int pgs_profile(pgs_ctx* ctx, int enable);
 int pgs_stage_times(pgs_ctx* ctx, double* ms, int64_t* counts);
 

@@ -33,11 +33,11 @@ PGS_BUF_TILES_TOUCHED = 6
 PGS_BUF_NCOMP = 7
 
 PGS_STAGES = ["project", "bin", "sort", "composite_fwd", "loss", "composite_bwd", "project_bwd",
-              "adam"]
+              "adam", "project_bwd_adam"]
 
 EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_l1",
             "pgs_backward", "pgs_step", "pgs_status", "pgs_read_buffer", "pgs_strerror",
-            "pgs_profile", "pgs_stage_times", "pgs_launch_count"]
+            "pgs_profile", "pgs_stage_times", "pgs_launch_count", "pgs_backward_step"]
 
 
 class PgsCamera(C.Structure):
@@ -91,6 +91,8 @@ def lib():
             L.pgs_backward.argtypes = [P, P, C.POINTER(PgsGaussians)]
             L.pgs_backward.restype = I
             L.pgs_step.argtypes = [P] + [C.POINTER(PgsGaussians)] * 4 + [I64]
+            L.pgs_backward_step.argtypes = [P, P] + [C.POINTER(PgsGaussians)] * 3 + [I64]
+            L.pgs_backward_step.restype = I
             L.pgs_step.restype = I
             L.pgs_status.argtypes = [P, C.POINTER(I64)]
             L.pgs_status.restype = I

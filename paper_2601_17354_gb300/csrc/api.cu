@@ -331,6 +331,29 @@ int pgs_step(pgs_ctx* ctx, pgs_gaussians* params, pgs_gaussians* grads, pgs_gaus
     return cuda_err(cudaGetLastError());
 }
 
+int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* params,
+                      pgs_gaussians* m, pgs_gaussians* v, int64_t t) {
+    if (!ctx || !dL_dimage || !valid_gaussians(params) || !valid_gaussians(m) ||
+        !valid_gaussians(v) || t < 1)
+        return PGS_ERR_INVALID_ARG;
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    const pgs_gaussians* all[3] = {params, m, v};
+    for (auto* q : all)
+        if (q->n != ctx->n || q->sh_degree != ctx->params.sh_degree) return PGS_ERR_INVALID_ARG;
+    if (params->means != ctx->params.means) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = ctx->stream;
+    if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s);
+    const size_t e1 = mark(ctx);
+    ctx->launches += launch_project_bwd_adam(*params, ctx->cam, ctx->sc, *m, *v, ctx->cfg.lr,
+                                             ctx->cfg.adam_b1, ctx->cfg.adam_b2, ctx->cfg.adam_eps, t, s);
+    const size_t e2 = mark(ctx);
+    span(ctx, PGS_STAGE_COMPOSITE_BWD, e0, e1);
+    span(ctx, PGS_STAGE_PROJECT_BWD_ADAM, e1, e2);
+    return cuda_err(cudaGetLastError());
+}
+
 int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
     if (!ctx) return PGS_ERR_INVALID_ARG;
     int32_t st = 0;

@@ -253,10 +253,14 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
     }
 }
 
-// stable scatter of one CTA's keys by one digit
+// stable scatter of one CTA's keys by one digit: rank each key among the CTA's keys of its
+// digit (warp match-any per 32 consecutive keys, warp prefixes per digit), reorder the CTA's
+// keys by digit in shared memory, then write each digit's run to its global offset, so the
+// global writes are contiguous runs instead of one scattered store per key.
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kWarpItems = kSortTile / kSortWarps;  // contiguous keys per warp
 constexpr int kRounds = kWarpItems / 32;            // == kSortItems
+constexpr size_t kScatterSmem = sizeof(unsigned long long) * kSortTile + sizeof(uint32_t) * kSortTile;
 
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long* __restrict__ kin,
@@ -264,18 +268,24 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
                uint32_t* __restrict__ vout, Scratch sc) {
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(s_dyn);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(unsigned long long) * kSortTile);
     __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
-    __shared__ uint32_t s_off[kRadix];
+    __shared__ uint32_t s_gofs[kRadix];            // global offset of this CTA's run of digit d
+    __shared__ uint32_t s_bstart[kRadix];          // start of digit d inside the CTA's reordering
+    __shared__ uint32_t s_part[kSortWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
-    s_off[threadIdx.x] = sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x];
+    s_gofs[threadIdx.x] = sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x];
     __syncthreads();
     const uint64_t P = kept_pairs(sc, capacity);
-    const uint64_t wbase = (uint64_t)blockIdx.x * kSortTile + (uint64_t)warp * kWarpItems;
+    const uint64_t cbase = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t wbase = cbase + (uint64_t)warp * kWarpItems;
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long key[kRounds];
     uint32_t val[kRounds];
-    uint32_t rank[kRounds];
+    uint32_t dr[kRounds];  // digit | warp-local rank << 8
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
@@ -283,38 +293,63 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
         key[r] = valid ? kin[idx] : 0ull;
         val[r] = valid ? vin[idx] : 0u;
         const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : 0x100u + lane;
-        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = 0;
         if (valid) before = s_wh[warp][d];
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) s_wh[warp][d] = before + __popc(peers);
         __syncwarp();
-        rank[r] = before + __popc(peers & lt);
+        dr[r] = valid ? (d | ((before + __popc(peers & lt)) << 8)) : 0xffffffffu;
     }
     __syncthreads();
-    {   // warp prefixes per digit (thread = digit)
+    {   // thread = digit: warp prefixes and the CTA total of the digit
         const int d = threadIdx.x;
-        uint32_t acc = s_off[d];
+        uint32_t acc = 0;
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
             const uint32_t c = s_wh[w][d];
             s_wh[w][d] = acc;
             acc += c;
         }
+        // exclusive scan of the digit totals across the CTA
+        uint32_t incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_part[warp] = incl;
+        __syncthreads();
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
+        s_bstart[d] = wpre + incl - acc;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
-        if (idx < P) {
-            const uint32_t d = (uint32_t)((key[r] >> shift) & (kRadix - 1));
-            const uint32_t dst = s_wh[warp][d] + rank[r];
-            if (dst < P) {
-                kout[dst] = key[r];
-                vout[dst] = val[r];
+        if (dr[r] != 0xffffffffu) {
+            const uint32_t d = dr[r] & 0xffu;
+            const uint32_t pos = s_bstart[d] + s_wh[warp][d] + (dr[r] >> 8);
+            if (pos < (uint32_t)kSortTile) {
+                s_keys[pos] = key[r];
+                s_vals[pos] = val[r];
             } else {
                 atomicOr(sc.status, kStatusInternal);
             }
+        }
+    }
+    __syncthreads();
+    const uint32_t count = (uint32_t)min((uint64_t)kSortTile, P - cbase);
+    for (uint32_t p = threadIdx.x; p < count; p += kSortThreads) {
+        const unsigned long long k = s_keys[p];
+        const uint32_t d = (uint32_t)((k >> shift) & (kRadix - 1));
+        const uint64_t dst = (uint64_t)s_gofs[d] + (p - s_bstart[d]);
+        if (dst < P) {
+            kout[dst] = k;
+            vout[dst] = s_vals[p];
+        } else {
+            atomicOr(sc.status, kStatusInternal);
         }
     }
 }
@@ -377,6 +412,15 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch
 
 }  // namespace
 
+// the scatter reorders a whole CTA tile of pairs in dynamic shared memory (48 KB)
+void enable_scatter_smem() {
+    static bool done = [] {
+        cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        return true;
+    }();
+    (void)done;
+}
+
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
     k_tile_order<<<1, kOrderThreads, 0, s>>>(tiles, sc);
     return 1;
@@ -417,6 +461,7 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
     const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
     const int grid_stride_blocks = 152 * 8;
     int buf = 0, launched = 0;
+    enable_scatter_smem();
     if (sb_max > 0 && passes > 0) {
         cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
         k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 32, passes, sc.keys[0], sc);
@@ -425,7 +470,7 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
             const int shift = 32 + p * kRadixBits;
             k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
             k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-            k_sort_scatter<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
+            k_sort_scatter<<<sb_max, kSortThreads, kScatterSmem, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
                                                            sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
             buf ^= 1;
         }
@@ -445,12 +490,13 @@ int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cu
     const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
     const int grid_stride_blocks = 152 * 8;
     int buf = 0;
+    enable_scatter_smem();
     k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 0, passes, sc.keys[0], sc);
     for (int p = 0; p < passes; ++p) {
         const int shift = p * kRadixBits;
         k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
         k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-        k_sort_scatter<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
+        k_sort_scatter<<<sb_max, kSortThreads, kScatterSmem, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
                                                        sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }

@@ -109,21 +109,41 @@ __global__ void __launch_bounds__(kThreads) k_adam_vec4(AdamArgs a) {
     float lr;
     row_of(a, blockIdx.y, grp, sub, lr);
     const int64_t off = (int64_t)sub * a.n;
-    float4* P = reinterpret_cast<float4*>(a.p[grp] + off);
-    float4* Gd = reinterpret_cast<float4*>(a.g[grp] + off);
-    float4* M = reinterpret_cast<float4*>(a.m[grp] + off);
-    float4* V = reinterpret_cast<float4*>(a.v[grp] + off);
+    float4* __restrict__ P = reinterpret_cast<float4*>(a.p[grp] + off);
+    float4* __restrict__ Gd = reinterpret_cast<float4*>(a.g[grp] + off);
+    float4* __restrict__ M = reinterpret_cast<float4*>(a.m[grp] + off);
+    float4* __restrict__ V = reinterpret_cast<float4*>(a.v[grp] + off);
     const int64_t n4 = a.n >> 2;
-    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n4; k += (int64_t)gridDim.x * kThreads) {
-        float4 p = P[k], g = Gd[k], m = M[k], v = V[k];
-        adam1(p.x, g.x, m.x, v.x, lr, a);
-        adam1(p.y, g.y, m.y, v.y, lr, a);
-        adam1(p.z, g.z, m.z, v.z, lr, a);
-        adam1(p.w, g.w, m.w, v.w, lr, a);
-        P[k] = p;
-        M[k] = m;
-        V[k] = v;
-        Gd[k] = g;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    // two float4 of each array in flight per thread per iteration
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n4; k += 2 * stride) {
+        const bool two = k + stride < n4;
+        float4 p0 = P[k], g0 = Gd[k], m0 = M[k], v0 = V[k];
+        float4 p1, g1, m1, v1;
+        if (two) {
+            p1 = P[k + stride];
+            g1 = Gd[k + stride];
+            m1 = M[k + stride];
+            v1 = V[k + stride];
+        }
+        adam1(p0.x, g0.x, m0.x, v0.x, lr, a);
+        adam1(p0.y, g0.y, m0.y, v0.y, lr, a);
+        adam1(p0.z, g0.z, m0.z, v0.z, lr, a);
+        adam1(p0.w, g0.w, m0.w, v0.w, lr, a);
+        P[k] = p0;
+        M[k] = m0;
+        V[k] = v0;
+        Gd[k] = g0;
+        if (two) {
+            adam1(p1.x, g1.x, m1.x, v1.x, lr, a);
+            adam1(p1.y, g1.y, m1.y, v1.y, lr, a);
+            adam1(p1.z, g1.z, m1.z, v1.z, lr, a);
+            adam1(p1.w, g1.w, m1.w, v1.w, lr, a);
+            P[k + stride] = p1;
+            M[k + stride] = m1;
+            V[k + stride] = v1;
+            Gd[k + stride] = g1;
+        }
     }
 }
 

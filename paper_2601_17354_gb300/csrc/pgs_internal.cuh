@@ -83,6 +83,12 @@ int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scra
 // Depth sort of the Gaussians (LSD radix over the 32 depth bits of dkeys[0] / dvals[0]); returns
 // the kernels launched, *perm receives the buffer holding the depth-ordered canonical indices.
 int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm);
+// K9 + K10 fused: chain the screen-space gradients to the parameters and apply one Adam step to
+// every Gaussian (culled ones with a zero gradient) without storing the gradient.
+int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+                            pgs_gaussians& m, pgs_gaussians& v, const float lr[6], float b1,
+                            float b2, float eps, int64_t t, cudaStream_t s);
+
 // K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
 // emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
 int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,

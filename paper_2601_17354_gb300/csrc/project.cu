@@ -285,13 +285,17 @@ k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
 // Backward of one Gaussian: screen-space gradient (du, dv, d conic, d opacity, d rgb) ->
 // parameters.  Matrix form: H = -Q Gq Q (Q the conic matrix, Gq its gradient with the
 // off-diagonal halved), dSigma = T^T H T, dT = 2 H T Sigma, dM = 2 dSigma M.
+struct GradParts {
+    float dmu[3], dls[3], dq[4], dlogit;
+    float gc[3];  // colour gradient after the clamp; d sh[c][k] = gc[c] Y[k]
+    float Y[16];
+};
+
 template <int DEG>
-__global__ void __launch_bounds__(kProjBlock)
-k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
+__device__ __forceinline__ void chain(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+                                      int64_t i, GradParts& out) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
-    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    if (i >= n || sc.touched[i] == 0) return;
     const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
     const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
     const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
@@ -311,7 +315,7 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
     d[0] *= inv_len;
     d[1] *= inv_len;
     d[2] *= inv_len;
-    float Y[16];
+    float* Y = out.Y;
     sh_eval(K, d[0], d[1], d[2], Y);
     float wsum[16];
 #pragma unroll
@@ -326,11 +330,9 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
             acc += coef[k] * Y[k];
         }
         const float gc = acc < 0.0f ? 0.0f : gr[6 + c];  // zero gradient through the clamp
+        out.gc[c] = gc;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            out.sh[((int64_t)c * K + k) * n + i] += gc * Y[k];
-            wsum[k] += gc * coef[k];
-        }
+        for (int k = 0; k < K; ++k) wsum[k] += gc * coef[k];
     }
     float ddir[3];
     sh_grad(K, d[0], d[1], d[2], wsum, ddir);
@@ -341,7 +343,7 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
 
     // opacity logit
     const float o = 1.0f / (1.0f + expf(-g.opacity_logits[i]));
-    out.opacity_logits[i] += gr[5] * o * (1.0f - o);
+    out.dlogit = gr[5] * o * (1.0f - o);
 
     // conic -> 2-D covariance
     const float inv_det = 1.0f / G.det;
@@ -423,14 +425,130 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
                             2.f * zq * dR[1][1] + y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
     const float dot = dw * w + dx * x + dy * y + dz * zq;
     const float iq = 1.0f / G.qn;
-    out.quats[i] += (dw - w * dot) * iq;
-    out.quats[n + i] += (dx - x * dot) * iq;
-    out.quats[2 * n + i] += (dy - y * dot) * iq;
-    out.quats[3 * n + i] += (dz - zq * dot) * iq;
+    out.dq[0] = (dw - w * dot) * iq;
+    out.dq[1] = (dx - x * dot) * iq;
+    out.dq[2] = (dy - y * dot) * iq;
+    out.dq[3] = (dz - zq * dot) * iq;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        out.log_scales[k * n + i] += dls[k];
-        out.means[k * n + i] += dmu[k];
+        out.dls[k] = dls[k];
+        out.dmu[k] = dmu[k];
+    }
+}
+
+// Parameter row r of the (11 + 3K) x n matrix: its group (0 means, 1 log-scales, 2 quaternions,
+// 3 opacity logits, 4 SH) and its row inside the group.
+__device__ __forceinline__ constexpr int row_group(int r) {
+    return r < 3 ? 0 : (r < 6 ? 1 : (r < 10 ? 2 : (r == 10 ? 3 : 4)));
+}
+__device__ __forceinline__ constexpr int row_sub(int r) {
+    return r < 3 ? r : (r < 6 ? r - 3 : (r < 10 ? r - 6 : (r == 10 ? 0 : r - 11)));
+}
+
+struct Rows {
+    float* __restrict__ g[5];
+};
+
+__device__ __forceinline__ Rows rows_of(const pgs_gaussians& q) {
+    return Rows{{q.means, q.log_scales, q.quats, q.opacity_logits, q.sh}};
+}
+
+// gradient of parameter row r of one Gaussian (rows 11.. are SH coefficients: gc[c] Y[k])
+template <int DEG>
+__device__ __forceinline__ float grad_row(const GradParts& gp, int r) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    if (r < 3) return gp.dmu[r];
+    if (r < 6) return gp.dls[r - 3];
+    if (r < 10) return gp.dq[r - 6];
+    if (r == 10) return gp.dlogit;
+    return gp.gc[(r - 11) / K] * gp.Y[(r - 11) % K];
+}
+
+__device__ __forceinline__ void zero_parts(GradParts& gp) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gp.dmu[k] = gp.dls[k] = gp.gc[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gp.dq[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gp.Y[k] = 0.f;
+    gp.dlogit = 0.f;
+}
+
+constexpr int kChunk = 8;  // parameter rows whose loads are issued together
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, 2)
+k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
+    constexpr int ROWS = 11 + 3 * (DEG + 1) * (DEG + 1);
+    const int64_t n = g.n;
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    if (i >= n || sc.touched[i] == 0) return;
+    GradParts gp;
+    chain<DEG>(g, cam, sc, i, gp);
+    const Rows O = rows_of(out);
+#pragma unroll
+    for (int r0 = 0; r0 < ROWS; r0 += kChunk) {
+        float acc[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+            if (r0 + j < ROWS) acc[j] = O.g[row_group(r0 + j)][(int64_t)row_sub(r0 + j) * n + i];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+            if (r0 + j < ROWS)
+                O.g[row_group(r0 + j)][(int64_t)row_sub(r0 + j) * n + i] = acc[j] + grad_row<DEG>(gp, r0 + j);
+    }
+}
+
+// Fused projection backward + Adam for one training step on one view: the parameter gradient of
+// each Gaussian (zero for culled ones) is consumed in registers by the Adam update of its 11 + 3K
+// parameters, so it never round-trips through memory.
+struct AdamStep {
+    float lr[6];
+    float b1, b2, omb1, omb2, eps, bc1, bc2;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, 2)
+k_project_bwd_adam(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians m, pgs_gaussians v,
+                   AdamStep a) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROWS = 11 + 3 * K;
+    const int64_t n = g.n;
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    if (i >= n) return;
+    GradParts gp;
+    if (sc.touched[i] != 0) chain<DEG>(g, cam, sc, i, gp);
+    else zero_parts(gp);
+    const Rows Pp = rows_of(g), Mm = rows_of(m), Vv = rows_of(v);
+#pragma unroll
+    for (int r0 = 0; r0 < ROWS; r0 += kChunk) {
+        float pp[kChunk], mm[kChunk], vv[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            if (r0 + j < ROWS) {
+                const int gi = row_group(r0 + j);
+                const int64_t idx = (int64_t)row_sub(r0 + j) * n + i;
+                pp[j] = Pp.g[gi][idx];
+                mm[j] = Mm.g[gi][idx];
+                vv[j] = Vv.g[gi][idx];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            const int r = r0 + j;
+            if (r < ROWS) {
+                const int gi = row_group(r);
+                const float lr = gi < 4 ? a.lr[gi] : (row_sub(r) % K == 0 ? a.lr[4] : a.lr[5]);
+                const float gr = grad_row<DEG>(gp, r);
+                mm[j] = a.b1 * mm[j] + a.omb1 * gr;
+                vv[j] = a.b2 * vv[j] + a.omb2 * gr * gr;
+                pp[j] -= lr * (mm[j] / a.bc1) / (sqrtf(vv[j] / a.bc2) + a.eps);
+                const int64_t idx = (int64_t)row_sub(r) * n + i;
+                Pp.g[gi][idx] = pp[j];
+                Mm.g[gi][idx] = mm[j];
+                Vv.g[gi][idx] = vv[j];
+            }
+        }
     }
 }
 
@@ -458,6 +576,29 @@ int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scra
         case 1: k_project_bwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
         case 2: k_project_bwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
         default: k_project_bwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, grads); break;
+    }
+    return 1;
+}
+
+int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+                            pgs_gaussians& m, pgs_gaussians& v, const float lr[6], float b1,
+                            float b2, float eps, int64_t t, cudaStream_t s) {
+    const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
+    if (blocks == 0) return 0;
+    AdamStep a;
+    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    a.b1 = b1;
+    a.b2 = b2;
+    a.omb1 = (float)(1.0 - (double)b1);
+    a.omb2 = (float)(1.0 - (double)b2);
+    a.eps = eps;
+    a.bc1 = (float)(1.0 - pow((double)b1, (double)t));
+    a.bc2 = (float)(1.0 - pow((double)b2, (double)t));
+    switch (g.sh_degree) {
+        case 0: k_project_bwd_adam<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
+        case 1: k_project_bwd_adam<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
+        case 2: k_project_bwd_adam<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
+        default: k_project_bwd_adam<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
     }
     return 1;
 }

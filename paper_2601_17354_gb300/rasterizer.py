@@ -169,6 +169,14 @@ class Rasterizer:
         L.check(self._lib.pgs_step(self._ctx, C.byref(params.struct()), C.byref(grads.struct()),
                                    C.byref(m.struct()), C.byref(v.struct()), int(t)), "pgs_step")
 
+    def backward_step(self, dL_dimage: torch.Tensor, params: GaussianBuffer, m: GaussianBuffer,
+                      v: GaussianBuffer, t: int):
+        """Backward of the last render fused with one Adam step (no gradient buffer)."""
+        assert dL_dimage.is_contiguous() and dL_dimage.dtype == torch.float32
+        L.check(self._lib.pgs_backward_step(self._ctx, C.c_void_p(dL_dimage.data_ptr()),
+                                            C.byref(params.struct()), C.byref(m.struct()),
+                                            C.byref(v.struct()), int(t)), "pgs_backward_step")
+
     def status(self):
         """(code, pairs of the last render); synchronises."""
         pairs = C.c_int64()
@@ -210,10 +218,11 @@ class Trainer:
     iterations, one view per iteration)."""
 
     def __init__(self, params: GaussianBuffer, rasterizer: Rasterizer | None = None,
-                 adam: AdamConfig | None = None):
+                 adam: AdamConfig | None = None, fused: bool = True):
         self.params = params
         self.r = rasterizer or Rasterizer(adam=adam)
-        self.grads = params.zeros_like()
+        self.fused = fused
+        self.grads = None if fused else params.zeros_like()
         self.m = params.zeros_like()
         self.v = params.zeros_like()
         self.t = 0
@@ -227,7 +236,10 @@ class Trainer:
         if self.dl is None or self.dl.shape != self.image.shape:
             self.dl = torch.empty_like(self.image)
         self.r.loss_l1(self.image, target, self.dl, self.loss)
-        self.r.backward(self.dl, self.grads)
         self.t += 1
-        self.r.step(self.params, self.grads, self.m, self.v, self.t)
+        if self.fused:
+            self.r.backward_step(self.dl, self.params, self.m, self.v, self.t)
+        else:
+            self.r.backward(self.dl, self.grads)
+            self.r.step(self.params, self.grads, self.m, self.v, self.t)
         return self.loss

@@ -84,6 +84,37 @@ def test_backward_grads(R, name):
     compare_grads(grads.numpy(), og, keep)
 
 
+def test_fused_backward_step_matches_oracle_and_separate_calls(R):
+    """pgs_backward_step == pgs_backward + pgs_step; its first-step moment m = (1 - b1) g
+    exposes the in-register parameter gradient, checked against the oracle."""
+    g, cam = SCENES["surface_sh3_200x120"]()
+    cam.bg = (0.1, 0.3, 0.2)
+    ora = oracle.render(g, cam)
+    dL = S.random_image(12, cam.width, cam.height)
+    dL[:, ora["flag"] != 0] = 0.0
+    dLt = torch.from_numpy(dL).cuda()
+    ra, rb = R.Rasterizer(), R.Rasterizer()
+    pa, pb = R.GaussianBuffer.from_arrays(g), R.GaussianBuffer.from_arrays(g)
+    ga, ma, va = pa.zeros_like(), pa.zeros_like(), pa.zeros_like()
+    mb, vb = pb.zeros_like(), pb.zeros_like()
+    ra.render(pa, cam)
+    ra.backward(dLt, ga)
+    ra.step(pa, ga, ma, va, 1)
+    rb.render(pb, cam)
+    rb.backward_step(dLt, pb, mb, vb, 1)
+    torch.cuda.synchronize()
+    assert rb.status()[0] == 0
+    assert rel_l2(mb.data.cpu().numpy(), ma.data.cpu().numpy()) < 1e-5
+    assert rel_l2(vb.data.cpu().numpy(), va.data.cpu().numpy()) < 1e-5
+    # t = 1: the step is lr * g / (|g| + eps), so parameters agree wherever g is not at noise level
+    dp = np.abs(pb.data.cpu().numpy() - pa.data.cpu().numpy())
+    assert np.mean(dp > 1e-6) < 1e-3
+    _, og = oracle.backward(g, cam, dL)
+    keep = oracle.gaussian_flags(g, cam) == 0
+    grads = {k: v / (1 - np.float32(0.9)) for k, v in mb.numpy().items()}
+    compare_grads(grads, og, keep)
+
+
 def test_backward_accumulates(R):
     g, cam = SCENES["tiny_2k_128"]()
     rast, buf, *_ = render_gpu(R, g, cam)
