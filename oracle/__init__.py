@@ -12,6 +12,8 @@ Parity status of each function (what pins it, besides agreeing with the GPU path
                                     Eq. 7 back-to-front cross-check
   keys                              brute-force per-tile lists, hand-checked tiny case
   backward / backward_subset        FP64 central finite differences, two derivations agree
+  fd_subset                         agrees with the analytic backward on small scenes (and is
+                                    itself plain central differencing of the render)
   sh basis                          orthonormality by quadrature, addition theorem, zonal values
   det_expf                          FP64 exp within 2 ulp
   adam                              torch.optim.Adam (float64), closed-form first step
@@ -81,6 +83,7 @@ def lib():
             L.oracle_backward.argtypes = [P, P, C.c_int, P, C.c_int, P, P]
             L.oracle_backward_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, P, P]
             L.oracle_chain.argtypes = [P, P, C.c_int, P, P]
+            L.oracle_fd_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, C.c_double, P]
             L.oracle_gaussian_flags.argtypes = [P, P, C.c_int, P]
             L.oracle_l1.argtypes = [C.c_int64, P, P, P, P, P]
             L.oracle_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
@@ -223,6 +226,17 @@ def backward_subset(g, cam, dL_dimage, sel, tile: int = 16):
     lib().oracle_backward_subset(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), _ptr(g2),
                                  _ptr(gp))
     return g2, gp
+
+
+def fd_subset(g, cam, dL_dimage, sel, h_rel: float = 2.0 ** -12, tile: int = 16):
+    """FP64 central differences [S][11 + 3K] of sum(dL_dimage * image) for the selected
+    Gaussians; NaN where a perturbation changed a decision."""
+    inp = _Inputs(g, cam)
+    d = np.ascontiguousarray(dL_dimage, np.float64)
+    sel = np.ascontiguousarray(sel, np.int64)
+    out = np.zeros((len(sel), param_count(g.sh_degree)))
+    lib().oracle_fd_subset(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), h_rel, _ptr(out))
+    return out
 
 
 def chain(g, cam, grad2d, tile: int = 16) -> dict:

@@ -851,6 +851,111 @@ void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
     }
 }
 
+// FP64 central finite differences of L = sum_p <w_p, C_p> (w = dL_dimage [3][H][W]) with respect
+// to every parameter of the selected Gaussians.  Each perturbed evaluation changes one parameter
+// of one Gaussian by +-h (h = h_rel * max(1, |theta|), applied to the fp32 parameter), recomputes
+// that Gaussian alone, and re-composites the pixels of its tile rectangle (no other pixel
+// depends on it).  A coordinate whose perturbation changes a decision - the rectangle, the depth
+// order inside a tile, or any pixel's (last, composited count, evaluated count) - is reported as
+// NaN.  out [nsel][11 + 3K] in the per-Gaussian layout of oracle_backward_subset.
+void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
+                      int64_t nsel, const int64_t* sel, double h_rel, double* out) {
+    Scene sc(*G, *cam, tile);
+    const int W = cam->width, H = cam->height;
+    const int K = (G->sh_degree + 1) * (G->sh_degree + 1);
+    const int PC = param_count(G->sh_degree);
+    const int64_t n = G->n;
+    for (int64_t s = 0; s < nsel; ++s) {
+        const int64_t gi = sel[s];
+        const Decision d0 = sc.dec[gi];
+        const Value v0 = sc.val[gi];
+        // one-Gaussian parameter copy
+        float prm[59];
+        for (int k = 0; k < 3; ++k) prm[k] = G->means[k * n + gi];
+        for (int k = 0; k < 3; ++k) prm[3 + k] = G->log_scales[k * n + gi];
+        for (int k = 0; k < 4; ++k) prm[6 + k] = G->quats[k * n + gi];
+        prm[10] = G->logits[gi];
+        for (int k = 0; k < 3 * K; ++k) prm[11 + k] = G->sh[(int64_t)k * n + gi];
+        auto one = [&](const float* q) {
+            ogauss_t g1;
+            g1.n = 1;
+            g1.sh_degree = G->sh_degree;
+            g1.pad_ = 0;
+            static thread_local float buf[59];
+            for (int k = 0; k < PC; ++k) buf[k] = q[k];
+            g1.means = buf;
+            g1.log_scales = buf + 3;
+            g1.quats = buf + 6;
+            g1.logits = buf + 10;
+            g1.sh = buf + 11;
+            // planar [k][1] layout of a single Gaussian is the packed vector itself
+            return g1;
+        };
+        // pixels of the rectangle (clipped to the image), with their base signatures
+        std::vector<std::pair<int, int>> pix;
+        if (d0.visible)
+            for (int py = d0.y0 * tile; py < std::min(H, d0.y1 * tile); ++py)
+                for (int px = d0.x0 * tile; px < std::min(W, d0.x1 * tile); ++px) pix.emplace_back(px, py);
+        std::vector<int64_t> sig0;
+        for (auto& pp : pix) {
+            const PixelResult r = composite(sc, pp.first, pp.second, false);
+            sig0.push_back(((int64_t)r.last << 40) ^ ((int64_t)r.ncomp << 20) ^ r.evals);
+        }
+        auto loss_with = [&](const float* q, bool& ok) {
+            ogauss_t g1 = one(q);
+            const Decision d = decide(g1, *cam, tile, 0);
+            ok = d.visible == d0.visible && d.x0 == d0.x0 && d.x1 == d0.x1 && d.y0 == d0.y0 && d.y1 == d0.y1;
+            if (!ok) return 0.0;
+            // depth order inside every tile of the rectangle must be unchanged
+            const uint32_t b0 = fbits(d0.zc), b1 = fbits(d.zc);
+            if (b0 != b1)
+                for (int ty = d.y0; ty < d.y1 && ok; ++ty)
+                    for (int tx = d.x0; tx < d.x1 && ok; ++tx)
+                        for (int64_t o : sc.lists[(size_t)ty * sc.TX + tx]) {
+                            if (o == gi) continue;
+                            const uint32_t bo = fbits(sc.dec[o].zc);
+                            const uint32_t lo = std::min(b0, b1), hi = std::max(b0, b1);
+                            if (bo >= lo && bo <= hi) {
+                                ok = false;
+                                break;
+                            }
+                        }
+            if (!ok) return 0.0;
+            sc.dec[gi] = d;
+            sc.val[gi] = evaluate(g1, *cam, 0);
+            double L = 0.0;
+            for (size_t k = 0; k < pix.size() && ok; ++k) {
+                const int px = pix[k].first, py = pix[k].second;
+                const PixelResult r = composite(sc, px, py, false);
+                if ((((int64_t)r.last << 40) ^ ((int64_t)r.ncomp << 20) ^ r.evals) != sig0[k]) ok = false;
+                const size_t p = (size_t)py * W + px;
+                for (int c = 0; c < 3; ++c) L += dL_dimage[(size_t)c * W * H + p] * r.C[c];
+            }
+            sc.dec[gi] = d0;
+            sc.val[gi] = v0;
+            return L;
+        };
+        for (int k = 0; k < PC; ++k) {
+            double& o = out[s * PC + k];
+            if (!d0.visible) {
+                o = 0.0;
+                continue;
+            }
+            const float x = prm[k];
+            const double h = h_rel * std::max(1.0, std::fabs((double)x));
+            float qp[59], qm[59];
+            std::memcpy(qp, prm, sizeof(float) * PC);
+            std::memcpy(qm, prm, sizeof(float) * PC);
+            qp[k] = (float)((double)x + h);
+            qm[k] = (float)((double)x - h);
+            bool okp = false, okm = false;
+            const double Lp = loss_with(qp, okp);
+            const double Lm = loss_with(qm, okm);
+            o = (okp && okm) ? (Lp - Lm) / ((double)qp[k] - (double)qm[k]) : std::nan("");
+        }
+    }
+}
+
 // Chain given screen-space gradients grad2d [N][9] to parameters (planar layout, overwritten).
 void oracle_chain(const ogauss_t* G, const ocam_t* cam, int tile, const double* grad2d,
                   double* grads) {

@@ -1,0 +1,170 @@
+"""The differentiable path at scale: RasterizeFn (torch.autograd.Function, recompute backward
+with no per-pixel lists) against the oracle and FP64 finite differences, and the full 500k
+Gaussian / 1920x1080 / SH3 workload in the launch configuration the benchmark times (bit-exact
+keys and ranges, sampled pixels, sampled Gaussians' gradients)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_17354_gb300 import synthetic as S
+from tests._parity import compare_grads, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2601_17354_gb300 import _lib, autograd, rasterizer
+    return rasterizer, autograd, _lib
+
+
+@pytest.fixture(scope="module")
+def big_scene():
+    sc = S.surface_scene(3, 500_000, 3, 1920, 1080, 1500.0, n_cameras=64)
+    return sc.init, sc.cameras[sc.train_views()[0]]
+
+
+def leaf_tensors(g):
+    return [torch.tensor(np.ascontiguousarray(getattr(g, k)), device="cuda", requires_grad=True)
+            for k in GROUPS]
+
+
+def autograd_grads(mods, g, cam, w):
+    R, A, _ = mods
+    rast = R.Rasterizer()
+    ts = leaf_tensors(g)
+    img = A.rasterize(rast, cam, *ts, sh_degree=g.sh_degree)
+    (img * torch.from_numpy(w).cuda()).sum().backward()
+    return img.detach().cpu().numpy(), {k: t.grad.cpu().numpy() for k, t in zip(GROUPS, ts)}
+
+
+def per_gaussian(grads, sel):
+    """[S][11 + 3K] in the oracle's per-Gaussian layout."""
+    K = grads["sh"].shape[1]
+    return np.concatenate([grads["means"][:, sel].T, grads["log_scales"][:, sel].T,
+                           grads["quats"][:, sel].T, grads["opacity_logits"][sel][:, None],
+                           grads["sh"][:, :, sel].reshape(3 * K, -1).T], 1)
+
+
+def group_slices(K):
+    return {"means": slice(0, 3), "log_scales": slice(3, 6), "quats": slice(6, 10),
+            "opacity_logits": slice(10, 11), "sh": slice(11, 11 + 3 * K)}
+
+
+def test_autograd_matches_oracle_tiny(mods):
+    g, cam, _ = S.tiny_scene(0)
+    ora = oracle.render(g, cam)
+    w = S.random_image(21, cam.width, cam.height)
+    w[:, ora["flag"] != 0] = 0
+    img, grads = autograd_grads(mods, g, cam, w)
+    assert np.all((np.abs(img - ora["image"]).max(axis=0) <= 1e-4) | (ora["flag"] != 0))
+    _, og = oracle.backward(g, cam, w)
+    keep = oracle.gaussian_flags(g, cam) == 0
+    compare_grads(grads, og, keep)
+
+
+def test_autograd_recomputes_after_an_interleaved_render(mods):
+    R, A, _ = mods
+    g, cam, _ = S.tiny_scene(1)
+    other = S.Camera(cam.width, cam.height, cam.fx, cam.fy, cam.cx + 9, cam.cy - 5, cam.viewmat)
+    w = torch.from_numpy(S.random_image(5, cam.width, cam.height)).cuda()
+    rast = R.Rasterizer()
+    ts = leaf_tensors(g)
+    img_a = A.rasterize(rast, cam, *ts, sh_degree=0)
+    img_b = A.rasterize(rast, other, *ts, sh_degree=0)  # overwrites the context's state
+    (img_a * w).sum().backward()
+    inter = [t.grad.clone() for t in ts]
+    ref = leaf_tensors(g)
+    (A.rasterize(R.Rasterizer(), cam, *ref, sh_degree=0) * w).sum().backward()
+    for a, b in zip(inter, ref):
+        assert rel_l2(a.cpu().numpy(), b.grad.cpu().numpy()) < 1e-5
+    assert img_b.shape == img_a.shape
+
+
+def _crop(cam):
+    # tile-aligned 256x256 window near the image centre: tile membership is unchanged
+    return cam.crop(16 * 52, 16 * 26, 256, 256)
+
+
+def test_crop_of_full_scene_autograd_vs_oracle(mods, big_scene):
+    g, cam = big_scene
+    crop = _crop(cam)
+    ora = oracle.render(g, crop)
+    w = S.random_image(31, 256, 256)
+    w[:, ora["flag"] != 0] = 0
+    img, grads = autograd_grads(mods, g, crop, w)
+    R, _, L = mods
+    _, og = oracle.backward(g, crop, w)
+    keep = (oracle.gaussian_flags(g, crop) == 0) & (np.abs(og["opacity_logits"]) > 0)
+    assert keep.sum() > 10_000
+    compare_grads(grads, og, keep)
+
+
+def test_fd_64_gaussians_of_full_scene(mods, big_scene):
+    g, cam = big_scene
+    crop = _crop(cam)
+    ora = oracle.render(g, crop)
+    w = S.random_image(41, 256, 256)
+    w[:, ora["flag"] != 0] = 0
+    _, grads = autograd_grads(mods, g, crop, w)
+    vis = np.nonzero((oracle.project(g, crop)["visible"] == 1) & (oracle.gaussian_flags(g, crop) == 0))[0]
+    sel = np.random.default_rng(7).choice(vis, 64, replace=False)
+    fd = oracle.fd_subset(g, crop, w, sel)
+    got = per_gaussian(grads, sel)
+    ok = np.isfinite(fd)
+    assert ok.mean() > 0.9
+    K = (g.sh_degree + 1) ** 2
+    for name, sl in group_slices(K).items():
+        a, b = got[:, sl], fd[:, sl]
+        m = ok[:, sl]
+        if np.abs(b[m]).max() == 0:
+            continue
+        assert rel_l2(a[m], b[m]) < 1e-3, name
+
+
+def test_full_size_keys_pixels_and_sampled_gradients(mods, big_scene):
+    """The benchmark's workload in its launch configuration (fixed pair capacity, fused
+    training-step kernels use the same render and compositing backward)."""
+    R, _, L = mods
+    g, cam = big_scene
+    k, v, r = oracle.keys(g, cam)
+    rast = R.Rasterizer(pair_capacity=int(len(k) * 1.5))
+    buf = R.GaussianBuffer.from_arrays(g)
+    img = rast.render(buf, cam).cpu().numpy()
+    assert rast.status() == (0, len(k))
+    assert np.array_equal(rast.read_buffer(L.PGS_BUF_KEYS), k)
+    assert np.array_equal(rast.read_buffer(L.PGS_BUF_VALUES), v)
+    assert np.array_equal(rast.read_buffer(L.PGS_BUF_RANGES).reshape(-1, 2), r)
+    rng = np.random.default_rng(3)
+    pix = np.stack([rng.integers(0, cam.width, 3000), rng.integers(0, cam.height, 3000)], 1)
+    op = oracle.render_pixels(g, cam, pix)
+    got = img[:, pix[:, 1], pix[:, 0]].T
+    diff = np.abs(got - op["rgb"]).max(axis=1)
+    assert np.all((diff <= 1e-4) | (op["flag"] != 0))
+    # gradients of 64 sampled Gaussians under a full-frame upstream gradient
+    vis = np.nonzero(oracle.gaussian_flags(g, cam) == 0)[0]
+    p = oracle.project(g, cam)
+    vis = vis[p["visible"][vis] == 1]
+    sel = rng.choice(vis, 64, replace=False)
+    w = S.random_image(51, cam.width, cam.height)
+    rect_pix = set()
+    for i in sel:
+        x0, y0, x1, y1 = p["rect"][i]
+        for yy in range(16 * y0, min(cam.height, 16 * y1)):
+            for xx in range(16 * x0, min(cam.width, 16 * x1)):
+                rect_pix.add((xx, yy))
+    rp = np.array(sorted(rect_pix), np.int32)
+    fl = oracle.render_pixels(g, cam, rp)["flag"]
+    bad = rp[fl != 0]
+    w[:, bad[:, 1], bad[:, 0]] = 0
+    grads = buf.zeros_like()
+    rast.backward(torch.from_numpy(w).cuda(), grads)
+    torch.cuda.synchronize()
+    _, og = oracle.backward_subset(g, cam, w, sel)
+    got = per_gaussian(grads.numpy(), sel)
+    K = (g.sh_degree + 1) ** 2
+    for name, sl in group_slices(K).items():
+        assert rel_l2(got[:, sl], og[:, sl]) < 1e-3, name

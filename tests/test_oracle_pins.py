@@ -515,3 +515,20 @@ def test_adam_first_step_is_signed_learning_rate():
     m, v = np.zeros(3), np.zeros(3)
     oracle.adam(p, g, m, v, 0.1, 1)
     assert np.allclose(p, [0.9, -1.9, 0.4], atol=1e-9)
+
+
+def test_fd_subset_matches_analytic_backward():
+    """The subset finite-difference routine (used at full scale on the GPU machine) agrees with the
+    analytic gradient on a small SH-degree-1 scene."""
+    sc = S.surface_scene(9, 3000, 1, 160, 120, 140.0, n_cameras=4)
+    g, cam = sc.gt, sc.cameras[1]
+    w = S.random_image(3, cam.width, cam.height)
+    sel = np.random.default_rng(2).choice(np.nonzero(oracle.project(g, cam)["visible"])[0], 12,
+                                          replace=False)
+    fd = oracle.fd_subset(g, cam, w, sel)
+    _, an = oracle.backward_subset(g, cam, w, sel)
+    ok = np.isfinite(fd)
+    assert ok.mean() > 0.9
+    scale = np.abs(an).max(axis=1, keepdims=True)
+    err = np.abs(fd - an) / (scale + 1e-30)
+    assert np.max(err[ok]) < 1e-4
