@@ -195,6 +195,60 @@ int64_t pgs_launch_count(const pgs_ctx* ctx);
 int pgs_sort_pairs_static(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                           uint32_t* vals_out, int64_t count, int32_t key_bits, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------------
+   Batched training: many views of many scenes (uneven Gaussian counts and resolutions) in one
+   step.  All renders of a step share one projection launch, one depth sort, one pair sort, one
+   persistent compositing launch forward and one backward (CTAs take tiles of every render,
+   heaviest first, from a device work counter), one loss launch and one fused backward + Adam
+   launch that sums each Gaussian's gradient over its scene's views.  The step can be captured
+   in a CUDA graph and replayed; the Adam step counter lives on the device.
+   --------------------------------------------------------------------------------------------- */
+typedef struct pgs_batch pgs_batch;
+
+typedef struct {
+    int32_t scene; /* index into the scene arrays of pgs_batch_create */
+    int32_t pad_;
+    pgs_camera cam;
+    float* image;        /* device [3][H][W]: the render */
+    const float* target; /* device [3][H][W]: the view's ground truth */
+    float* dL_dimage;    /* device [3][H][W]: written by the step's L1 loss */
+} pgs_render_desc;
+
+/* Plan a batch: n_scenes parameter sets with Adam moments m, v (same layout; all scenes share one
+   sh_degree) and n_renders renders ordered scene by scene.  pair_capacity 0 = measure the pairs of
+   the parameters as given and keep 25 % headroom (synchronises).  All buffers stay owned by the
+   caller and must outlive the batch. */
+int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
+                     const pgs_gaussians* params, const pgs_gaussians* m, const pgs_gaussians* v,
+                     int32_t n_renders, const pgs_render_desc* renders, int64_t pair_capacity,
+                     void* cuda_stream);
+void pgs_batch_destroy(pgs_batch* b);
+/* One training step of every render (render, L1, backward, Adam with t = previous t + 1): replays
+   the captured graph if there is one, else enqueues the kernels. */
+int pgs_batch_step(pgs_batch* b);
+/* Capture one step into a CUDA graph (nothing runs during capture); later steps replay it. */
+int pgs_batch_capture(pgs_batch* b);
+/* Per render: losses[2 r] = mean |image - target| and losses[2 r + 1] = sum of squared errors of
+   the last step (host array of 2 n_renders doubles; synchronises). */
+int pgs_batch_losses(pgs_batch* b, double* losses);
+/* As pgs_status, for the batch (pairs = pairs of the last step). */
+int pgs_batch_status(pgs_batch* b, int64_t* pairs);
+int64_t pgs_batch_launch_count(const pgs_batch* b);
+
+/* Compositing kernel variant (pixels per thread 1, 2, 4; entries staged per batch 64, 128, 256)
+   of a context or a batch.  Changing a batch's variant drops its captured graph. */
+int pgs_set_variant(pgs_ctx* ctx, int32_t pixels_per_thread, int32_t depth);
+int pgs_batch_set_variant(pgs_batch* b, int32_t pixels_per_thread, int32_t depth);
+/* Autotuner measurement: runs the render part of a step once, then times the forward + backward
+   compositing of every variant (reps repetitions, CUDA events on the batch's stream) and writes
+   ms[9] in the order (1,64) (1,128) (1,256) (2,64) ... (4,256).  Parameters are not changed.
+   The caller picks and sets the variant (the library's Python layer caches the choice per GPU
+   and workload class). */
+int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms);
+/* The same measurement for a context, on its last render: the timed forwards write `image`
+   ([3][H][W] scratch) and the backwards use dL_dimage [3][H][W]. */
+int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms);
+
 /* Static description of an error code. */
 const char* pgs_strerror(int code);
 

@@ -37,7 +37,12 @@ PGS_STAGES = ["project", "bin", "sort", "composite_fwd", "loss", "composite_bwd"
 
 EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_l1",
             "pgs_backward", "pgs_step", "pgs_status", "pgs_read_buffer", "pgs_strerror",
-            "pgs_profile", "pgs_stage_times", "pgs_launch_count", "pgs_backward_step"]
+            "pgs_profile", "pgs_stage_times", "pgs_launch_count", "pgs_backward_step",
+            "pgs_batch_create", "pgs_batch_destroy", "pgs_batch_step", "pgs_batch_capture",
+            "pgs_batch_losses", "pgs_batch_status", "pgs_batch_launch_count", "pgs_set_variant",
+            "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants"]
+
+VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
 
 class PgsCamera(C.Structure):
@@ -50,6 +55,11 @@ class PgsGaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("pad_", C.c_int32),
                 ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class PgsRenderDesc(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("pad_", C.c_int32), ("cam", PgsCamera), ("image", C.c_void_p),
+                ("target", C.c_void_p), ("dL_dimage", C.c_void_p)]
 
 
 class PgsConfig(C.Structure):
@@ -106,6 +116,30 @@ def lib():
             L.pgs_launch_count.restype = I64
             L.pgs_sort_pairs_static.argtypes = [P, P, P, P, I64, C.c_int32, P]
             L.pgs_sort_pairs_static.restype = I
+            L.pgs_batch_create.argtypes = [C.POINTER(P), C.POINTER(PgsConfig), C.c_int32,
+                                           C.POINTER(PgsGaussians), C.POINTER(PgsGaussians),
+                                           C.POINTER(PgsGaussians), C.c_int32,
+                                           C.POINTER(PgsRenderDesc), I64, P]
+            L.pgs_batch_create.restype = I
+            L.pgs_batch_destroy.argtypes = [P]
+            L.pgs_batch_destroy.restype = None
+            for name in ("pgs_batch_step", "pgs_batch_capture"):
+                getattr(L, name).argtypes = [P]
+                getattr(L, name).restype = I
+            L.pgs_batch_losses.argtypes = [P, P]
+            L.pgs_batch_losses.restype = I
+            L.pgs_batch_status.argtypes = [P, C.POINTER(I64)]
+            L.pgs_batch_status.restype = I
+            L.pgs_batch_launch_count.argtypes = [P]
+            L.pgs_batch_launch_count.restype = I64
+            L.pgs_set_variant.argtypes = [P, C.c_int32, C.c_int32]
+            L.pgs_set_variant.restype = I
+            L.pgs_batch_set_variant.argtypes = [P, C.c_int32, C.c_int32]
+            L.pgs_batch_set_variant.restype = I
+            L.pgs_batch_time_variants.argtypes = [P, C.c_int32, P]
+            L.pgs_batch_time_variants.restype = I
+            L.pgs_time_variants.argtypes = [P, P, P, C.c_int32, P]
+            L.pgs_time_variants.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p
             _lib = L

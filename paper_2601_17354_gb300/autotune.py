@@ -1,0 +1,83 @@
+"""Autotuner of the compositing kernels: picks the pixels-per-thread strip (1, 2, 4) and the
+number of list entries staged in shared memory per batch (64, 128, 256) by timing every variant's
+forward + backward on the caller's own workload, and caches the choice in a JSON file keyed by
+GPU and workload class (resolution class and Gaussian count), so later runs skip the timing."""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pocketgs_gb300", "autotune.json")
+
+
+def _cache_path(path: str | None) -> str:
+    return path or os.environ.get("PGS_AUTOTUNE_CACHE", DEFAULT_CACHE)
+
+
+def _load(path: str) -> dict:
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path: str, key: str, entry: dict) -> None:
+    data = _load(path)
+    data[key] = entry
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def resolution_class(width: int, height: int) -> str:
+    return f"{width}x{height}"
+
+
+def workload_key(kind: str, resolutions, n_gaussians: int, sh_degree: int) -> str:
+    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    res = "+".join(sorted(set(resolutions)))
+    return f"{gpu}|{kind}|{res}|N~2^{round(math.log2(max(n_gaussians, 1)))}|sh{sh_degree}"
+
+
+def pick(timings: dict) -> tuple:
+    return min(timings, key=lambda v: timings[v])
+
+
+def tune_rasterizer(rast, params, cam, dL_dimage: torch.Tensor, cache: str | None = None,
+                    reps: int = 3, force: bool = False) -> tuple:
+    """Choose and set the variant for single-view training of `params` through `cam`."""
+    path = _cache_path(cache)
+    key = workload_key("single", [resolution_class(cam.width, cam.height)], params.n, params.sh_degree)
+    entry = None if force else _load(path).get(key)
+    if entry is None:
+        rast.render(params, cam)
+        t = rast.time_variants(dL_dimage, reps)
+        best = pick(t)
+        entry = {"pixels": best[0], "depth": best[1],
+                 "ms": {f"{p}x{d}": ms for (p, d), ms in t.items()}}
+        _store(path, key, entry)
+    rast.set_variant(entry["pixels"], entry["depth"])
+    return entry["pixels"], entry["depth"]
+
+
+def tune_batch(bt, cache: str | None = None, reps: int = 3, force: bool = False) -> tuple:
+    """Choose and set the variant of a BatchTrainer's persistent compositing launches."""
+    path = _cache_path(cache)
+    res = [resolution_class(c.width, c.height) for _, c, _ in bt.views]
+    n = sum(s.n for s in bt.scenes)
+    key = workload_key(f"batch{len(bt.views)}", res, n, bt.scenes[0].sh_degree)
+    entry = None if force else _load(path).get(key)
+    if entry is None:
+        t = bt.time_variants(reps)
+        best = pick(t)
+        entry = {"pixels": best[0], "depth": best[1],
+                 "ms": {f"{p}x{d}": ms for (p, d), ms in t.items()}}
+        _store(path, key, entry)
+    bt.set_variant(entry["pixels"], entry["depth"])
+    return entry["pixels"], entry["depth"]

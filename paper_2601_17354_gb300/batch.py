@@ -1,0 +1,105 @@
+"""Batched training over many views of many scenes: one planned batch per set of (scene, view,
+target) renders, one training step = render + L1 + backward + Adam of every render, optionally
+captured once in a CUDA graph and replayed.  Thin marshalling over pgs_batch_* of the C ABI."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .rasterizer import AdamConfig, GaussianBuffer, camera_struct
+
+
+class BatchTrainer:
+    """scenes: GaussianBuffers (one SH degree); views: (scene index, camera, target [3][H][W])
+    tuples, given scene by scene."""
+
+    def __init__(self, scenes: list, views: list, adam: AdamConfig | None = None,
+                 pair_capacity: int = 0, stream: torch.cuda.Stream | None = None):
+        self._lib = L.lib()
+        adam = adam or AdamConfig()
+        self.scenes = scenes
+        self.m = [s.zeros_like() for s in scenes]
+        self.v = [s.zeros_like() for s in scenes]
+        order = [s for s, _, _ in views]
+        if order != sorted(order):
+            raise ValueError("views must be given scene by scene")
+        self.views = views
+        dev = scenes[0].data.device
+        self.images = [torch.zeros((3, c.height, c.width), dtype=torch.float32, device=dev)
+                       for _, c, _ in views]
+        self.dls = [torch.zeros_like(im) for im in self.images]
+        self.targets = [t.contiguous() for _, _, t in views]
+        # a stream of its own: the legacy default stream cannot be captured in a graph; every
+        # call is ordered after the caller's current stream and before its later work
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.stream.wait_stream(torch.cuda.current_stream(dev))
+        S, R = len(scenes), len(views)
+        P = (L.PgsGaussians * S)(*[s.struct() for s in scenes])
+        M = (L.PgsGaussians * S)(*[s.struct() for s in self.m])
+        V = (L.PgsGaussians * S)(*[s.struct() for s in self.v])
+        D = (L.PgsRenderDesc * R)(*[
+            L.PgsRenderDesc(int(s), 0, camera_struct(c), self.images[k].data_ptr(),
+                            self.targets[k].data_ptr(), self.dls[k].data_ptr())
+            for k, (s, c, _) in enumerate(views)])
+        cfg = L.PgsConfig(16, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
+                          (C.c_float * 6)(*adam.lr))
+        self._b = C.c_void_p()
+        L.check(self._lib.pgs_batch_create(C.byref(self._b), C.byref(cfg), S, P, M, V, R, D,
+                                           int(pair_capacity), C.c_void_p(self.stream.cuda_stream)),
+                "pgs_batch_create")
+        self.captured = False
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.pgs_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _enter(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.stream.device))
+
+    def _leave(self):
+        torch.cuda.current_stream(self.stream.device).wait_stream(self.stream)
+
+    def step(self):
+        self._enter()
+        L.check(self._lib.pgs_batch_step(self._b), "pgs_batch_step")
+        self._leave()
+
+    def capture(self):
+        self._enter()
+        L.check(self._lib.pgs_batch_capture(self._b), "pgs_batch_capture")
+        self.captured = True
+
+    def losses(self) -> np.ndarray:
+        out = np.zeros((len(self.views), 2))
+        L.check(self._lib.pgs_batch_losses(self._b, out.ctypes.data_as(C.c_void_p)), "pgs_batch_losses")
+        return out
+
+    def status(self):
+        pairs = C.c_int64()
+        code = self._lib.pgs_batch_status(self._b, C.byref(pairs))
+        return code, pairs.value
+
+    def launch_count(self) -> int:
+        return int(self._lib.pgs_batch_launch_count(self._b))
+
+    def set_variant(self, pixels_per_thread: int, depth: int):
+        L.check(self._lib.pgs_batch_set_variant(self._b, int(pixels_per_thread), int(depth)),
+                "pgs_batch_set_variant")
+        self.captured = False
+
+    def time_variants(self, reps: int = 3) -> dict:
+        self._enter()
+        ms = np.zeros(len(L.VARIANTS), np.float32)
+        L.check(self._lib.pgs_batch_time_variants(self._b, int(reps), ms.ctypes.data_as(C.c_void_p)),
+                "pgs_batch_time_variants")
+        return {v: float(t) for v, t in zip(L.VARIANTS, ms)}

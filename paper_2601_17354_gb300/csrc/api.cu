@@ -26,6 +26,7 @@ struct pgs_ctx {
     int TX = 0, TY = 0, buf = 0;
     pgs_camera cam{};
     pgs_gaussians params{};
+    CompositeVariant variant = default_variant();
     // instrumentation
     int64_t launches = 0;
     bool profiling = false;
@@ -273,7 +274,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
     ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
-    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, params->n, ctx->sc, image_out, s);
+    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
     const size_t e4 = mark(ctx);
     span(ctx, PGS_STAGE_PROJECT, e0, e1);
     span(ctx, PGS_STAGE_BIN, e1, e2);
@@ -306,7 +307,7 @@ int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd(ctx->params, ctx->cam, ctx->sc, *grads, s);
     const size_t e2 = mark(ctx);
@@ -344,7 +345,7 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd_adam(*params, ctx->cam, ctx->sc, *m, *v, ctx->cfg.lr,
                                              ctx->cfg.adam_b1, ctx->cfg.adam_b2, ctx->cfg.adam_eps, t, s);
@@ -399,6 +400,46 @@ int pgs_stage_times(pgs_ctx* ctx, double* ms, int64_t* counts) {
 
 int64_t pgs_launch_count(const pgs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int pgs_set_variant(pgs_ctx* ctx, int32_t pixels_per_thread, int32_t depth) {
+    const CompositeVariant v{pixels_per_thread, depth};
+    if (!ctx || !valid_variant(v)) return PGS_ERR_INVALID_ARG;
+    ctx->variant = v;
+    return PGS_OK;
+}
+
+int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms) {
+    if (!ctx || !image || !dL_dimage || !ms || reps < 1) return PGS_ERR_INVALID_ARG;
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int P[3] = {1, 2, 4}, D[3] = {64, 128, 256};
+    int idx = 0;
+    cudaError_t err = cudaSuccess;
+    for (int pi = 0; pi < 3; ++pi)
+        for (int di = 0; di < 3; ++di, ++idx) {
+            const CompositeVariant v{P[pi], D[di]};
+            float best = 1e30f;
+            for (int rep = 0; rep < reps + 1; ++rep) {
+                cudaEventRecord(e0, s);
+                launch_composite_fwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, image, s, v);
+                launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, v);
+                cudaEventRecord(e1, s);
+                err = cudaEventSynchronize(e1);
+                if (err != cudaSuccess) break;
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < best) best = t;
+            }
+            ms[idx] = best;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing overwrote the screen-space gradients: the next backward recomputes them
+    return err == cudaSuccess ? PGS_OK : cuda_err(err);
+}
+
 int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64_t* bytes) {
     if (!ctx || max_bytes < 0) return PGS_ERR_INVALID_ARG;
     cudaStream_t s = ctx->stream;
@@ -430,6 +471,324 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
         if (e != cudaSuccess) return cuda_err(e);
     }
     return PGS_OK;
+}
+
+}  // extern "C"
+
+// ================================================================================================
+// batch
+// ================================================================================================
+struct pgs_batch {
+    pgs_config cfg;
+    cudaStream_t stream = nullptr;
+    int S = 0, R = 0, deg = 0;
+    std::vector<SceneDesc> scenes;
+    std::vector<RenderDesc> renders;
+    int64_t items = 0, gauss = 0, tiles = 0, pixels = 0, values = 0, cap_pairs = 0;
+    Scratch sc;
+    void* arena_g = nullptr;
+    void* arena_p = nullptr;
+    void* arena_t = nullptr;  // tables, losses, counters
+    SceneDesc* d_scenes = nullptr;
+    RenderDesc* d_renders = nullptr;
+    double* d_losses = nullptr;
+    uint32_t* d_work = nullptr;  // forward and backward work counters
+    int64_t* d_step = nullptr;
+    int buf = 0;
+    CompositeVariant variant = default_variant();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    int64_t launches_per_step = 0;  // kernels in the captured graph
+};
+
+namespace {
+
+void drop_graph(pgs_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// the render part of a step: projection .. tile order (returns kernels launched)
+int64_t enqueue_render(pgs_batch* b) {
+    cudaStream_t s = b->stream;
+    int64_t k = 0;
+    k += launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
+    const uint32_t* perm = nullptr;
+    if (b->items > 0) k += launch_depth_sort(b->items, b->sc, s, &perm);
+    k += launch_scan_emit(b->items, 0, b->cap_pairs, perm, b->sc, s, b->d_renders, b->R);
+    k += launch_sort_ranges(b->cap_pairs, (int)b->tiles, b->sc, s, &b->buf);
+    k += launch_tile_order((int)b->tiles, b->sc, s);
+    return k;
+}
+
+int64_t enqueue_step(pgs_batch* b) {
+    cudaStream_t s = b->stream;
+    int64_t k = launch_step_tick(b->d_step, s);
+    k += enqueue_render(b);
+    cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
+    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work,
+                                false, s, b->variant);
+    cudaMemsetAsync(b->d_losses, 0, sizeof(double) * 2 * b->R, s);
+    k += launch_loss_batch(b->d_renders, b->R, b->values, b->d_losses, s);
+    cudaMemsetAsync(b->sc.grad2d, 0, sizeof(float) * 9 * (size_t)b->items, s);
+    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work + 1,
+                                true, s, b->variant);
+    k += launch_bwd_adam_batch(b->d_renders, b->d_scenes, b->S, b->deg, b->gauss, b->items, b->sc,
+                               b->cfg.lr, b->cfg.adam_b1, b->cfg.adam_b2, b->cfg.adam_eps, b->d_step, s);
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
+                     const pgs_gaussians* params, const pgs_gaussians* m, const pgs_gaussians* v,
+                     int32_t n_renders, const pgs_render_desc* renders, int64_t pair_capacity,
+                     void* cuda_stream) {
+    if (!out) return PGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg || cfg->tile != kTile || n_scenes < 1 || n_renders < 1 || !params || !m || !v ||
+        !renders || pair_capacity < 0)
+        return PGS_ERR_INVALID_ARG;
+    const int deg = params[0].sh_degree;
+    for (int k = 0; k < n_scenes; ++k) {
+        if (!valid_gaussians(&params[k]) || !valid_gaussians(&m[k]) || !valid_gaussians(&v[k]))
+            return PGS_ERR_INVALID_ARG;
+        if (params[k].sh_degree != deg || m[k].n != params[k].n || v[k].n != params[k].n ||
+            m[k].sh_degree != deg || v[k].sh_degree != deg)
+            return PGS_ERR_INVALID_ARG;
+    }
+    for (int r = 0; r < n_renders; ++r) {
+        const pgs_render_desc& d = renders[r];
+        if (d.scene < 0 || d.scene >= n_scenes || !valid_camera(&d.cam) || !d.image || !d.target ||
+            !d.dL_dimage)
+            return PGS_ERR_INVALID_ARG;
+        if (r > 0 && d.scene < renders[r - 1].scene) return PGS_ERR_INVALID_ARG;  // scene by scene
+    }
+    pgs_batch* b = new (std::nothrow) pgs_batch();
+    if (!b) return PGS_ERR_OOM;
+    b->cfg = *cfg;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->S = n_scenes;
+    b->R = n_renders;
+    b->deg = deg;
+    b->scenes.resize(n_scenes);
+    for (int k = 0; k < n_scenes; ++k) {
+        SceneDesc& sd = b->scenes[k];
+        sd.params = params[k];
+        sd.m = m[k];
+        sd.v = v[k];
+        sd.first_render = 0;
+        sd.n_renders = 0;
+        sd.gauss_base = b->gauss;
+        b->gauss += params[k].n;
+    }
+    b->renders.resize(n_renders);
+    for (int r = 0; r < n_renders; ++r) {
+        const pgs_render_desc& d = renders[r];
+        RenderDesc& rd = b->renders[r];
+        std::memset(&rd, 0, sizeof(rd));
+        rd.cam = d.cam;
+        rd.scene = d.scene;
+        rd.TX = (d.cam.width + kTile - 1) / kTile;
+        rd.TY = (d.cam.height + kTile - 1) / kTile;
+        rd.item_base = b->items;
+        rd.n = params[d.scene].n;
+        rd.tile_base = b->tiles;
+        rd.pixel_base = b->pixels;
+        rd.value_base = b->values;
+        rd.image = d.image;
+        rd.target = d.target;
+        rd.dL = d.dL_dimage;
+        b->items += rd.n;
+        b->tiles += (int64_t)rd.TX * rd.TY;
+        b->pixels += (int64_t)d.cam.width * d.cam.height;
+        b->values += 3ll * d.cam.width * d.cam.height;
+        SceneDesc& sd = b->scenes[d.scene];
+        if (sd.n_renders == 0) sd.first_render = r;
+        sd.n_renders++;
+    }
+    auto fail = [&](int rc) {
+        pgs_batch_destroy(b);
+        return rc;
+    };
+    if (b->items >= (int64_t(1) << 32) || b->tiles >= (int64_t(1) << 32)) return fail(PGS_ERR_INVALID_ARG);
+    // arenas
+    Scratch tmp;
+    const size_t gbytes = carve_g(tmp, nullptr, b->items, b->pixels, b->tiles);
+    cudaError_t e = cudaMalloc(&b->arena_g, gbytes);
+    if (e != cudaSuccess) return fail(cuda_err(e));
+    carve_g(b->sc, static_cast<char*>(b->arena_g), b->items, b->pixels, b->tiles);
+    const size_t tbytes = align256(sizeof(SceneDesc) * n_scenes) + align256(sizeof(RenderDesc) * n_renders) +
+                          align256(sizeof(double) * 2 * n_renders) + 256 + 256;
+    e = cudaMalloc(&b->arena_t, tbytes);
+    if (e != cudaSuccess) return fail(cuda_err(e));
+    {
+        Carver c{static_cast<char*>(b->arena_t)};
+        b->d_scenes = c.take<SceneDesc>(n_scenes);
+        b->d_renders = c.take<RenderDesc>(n_renders);
+        b->d_losses = c.take<double>(2 * n_renders);
+        b->d_work = c.take<uint32_t>(2);
+        b->d_step = c.take<int64_t>(1);
+    }
+    cudaStream_t s = b->stream;
+    e = cudaMemsetAsync(b->arena_g, 0, gbytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->arena_t, 0, tbytes, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_scenes, b->scenes.data(), sizeof(SceneDesc) * n_scenes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_renders, b->renders.data(), sizeof(RenderDesc) * n_renders, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_err(e));
+    // pair capacity: measured on the parameters as given when not specified
+    int64_t cap = pair_capacity;
+    if (cap == 0) {
+        launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
+        const uint32_t* perm = nullptr;
+        launch_depth_sort(b->items, b->sc, s, &perm);
+        launch_scan_emit(b->items, 0, 0, perm, b->sc, s, b->d_renders, b->R);
+        unsigned long long P = 0;
+        int32_t zero = 0;
+        e = cudaMemcpyAsync(&P, b->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->sc.status, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(cuda_err(e));
+        cap = (int64_t)(P + P / 4 + 4096);
+    }
+    const size_t pbytes = carve_p(tmp, nullptr, cap);
+    e = cudaMalloc(&b->arena_p, pbytes);
+    if (e != cudaSuccess) return fail(cuda_err(e));
+    carve_p(b->sc, static_cast<char*>(b->arena_p), cap);
+    b->cap_pairs = cap;
+    *out = b;
+    return PGS_OK;
+}
+
+void pgs_batch_destroy(pgs_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->arena_g) cudaFree(b->arena_g);
+    if (b->arena_p) cudaFree(b->arena_p);
+    if (b->arena_t) cudaFree(b->arena_t);
+    delete b;
+}
+
+int pgs_batch_step(pgs_batch* b) {
+    if (!b) return PGS_ERR_INVALID_ARG;
+    if (b->exec) {
+        const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return cuda_err(e);
+        b->launches += b->launches_per_step;
+        return PGS_OK;
+    }
+    b->launches += enqueue_step(b);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_batch_capture(pgs_batch* b) {
+    if (!b) return PGS_ERR_INVALID_ARG;
+    drop_graph(b);
+    // relaxed: one-time launch-configuration queries of the kernels may run during the capture
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // do not leave the failure for an unrelated later check
+        return cuda_err(e);
+    }
+    b->launches_per_step = enqueue_step(b);
+    e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        return cuda_err(e);
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(b);
+        return cuda_err(e);
+    }
+    return PGS_OK;
+}
+
+int pgs_batch_losses(pgs_batch* b, double* losses) {
+    if (!b || !losses) return PGS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(losses, b->d_losses, sizeof(double) * 2 * b->R, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    for (int r = 0; r < b->R; ++r)
+        losses[2 * r] /= 3.0 * b->renders[r].cam.width * b->renders[r].cam.height;
+    return PGS_OK;
+}
+
+int pgs_batch_status(pgs_batch* b, int64_t* pairs) {
+    if (!b) return PGS_ERR_INVALID_ARG;
+    int32_t st = 0;
+    unsigned long long P = 0;
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaMemcpyAsync(&st, b->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&P, b->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sc.status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (pairs) *pairs = (int64_t)P;
+    if (st & kStatusInternal) return PGS_ERR_INTERNAL;
+    if (st & kStatusCapacity) return PGS_ERR_CAPACITY;
+    if (st & kStatusNonfinite) return PGS_ERR_NONFINITE;
+    return PGS_OK;
+}
+
+int64_t pgs_batch_launch_count(const pgs_batch* b) { return b ? b->launches : 0; }
+
+int pgs_batch_set_variant(pgs_batch* b, int32_t pixels_per_thread, int32_t depth) {
+    const CompositeVariant v{pixels_per_thread, depth};
+    if (!b || !valid_variant(v)) return PGS_ERR_INVALID_ARG;
+    if (v.pix != b->variant.pix || v.depth != b->variant.depth) drop_graph(b);
+    b->variant = v;
+    return PGS_OK;
+}
+
+int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms) {
+    if (!b || !ms || reps < 1) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream;
+    enqueue_render(b);
+    // a render's forward composite also writes the images the loss needs: run one of each
+    cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
+    launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work, false, s, b->variant);
+    cudaMemsetAsync(b->d_losses, 0, sizeof(double) * 2 * b->R, s);
+    launch_loss_batch(b->d_renders, b->R, b->values, b->d_losses, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int P[3] = {1, 2, 4}, D[3] = {64, 128, 256};
+    int idx = 0;
+    cudaError_t err = cudaSuccess;
+    for (int pi = 0; pi < 3; ++pi)
+        for (int di = 0; di < 3; ++di, ++idx) {
+            const CompositeVariant v{P[pi], D[di]};
+            float best = 1e30f;
+            for (int rep = 0; rep < reps + 1; ++rep) {  // first repetition warms up
+                cudaEventRecord(e0, s);
+                cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
+                launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work, false, s, v);
+                cudaMemsetAsync(b->sc.grad2d, 0, sizeof(float) * 9 * (size_t)b->items, s);
+                launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work + 1, true, s, v);
+                cudaEventRecord(e1, s);
+                err = cudaEventSynchronize(e1);
+                if (err != cudaSuccess) break;
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < best) best = t;
+            }
+            ms[idx] = best;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err == cudaSuccess ? PGS_OK : cuda_err(err);
 }
 
 }  // extern "C"

@@ -94,9 +94,11 @@ k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
 // tiles row-major inside each rectangle.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
-k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc) {
+k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
+       const RenderDesc* __restrict__ renders, int R) {
     __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of counts
     __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock], s_depth[kProjBlock];
+    __shared__ uint32_t s_tx[kProjBlock], s_tbase[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
@@ -112,6 +114,18 @@ k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, S
             s_y0[t] = r.x >> 16;
             s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
             s_depth[t] = sc.depth_bits[g];
+            s_tx[t] = (uint32_t)TX;
+            s_tbase[t] = 0;
+            if (renders) {  // batch: item g belongs to the last render whose first item is <= g
+                int lo = 0, hi = R - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (renders[mid].item_base <= (int64_t)g) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_tx[t] = (uint32_t)renders[lo].TX;
+                s_tbase[t] = (uint32_t)renders[lo].tile_base;
+            }
         }
     }
     uint32_t incl = cnt;
@@ -148,7 +162,7 @@ k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, S
         const uint32_t local = k - (lo ? s_end[lo - 1] : 0u);  // pair index inside Gaussian lo
         const uint32_t w = s_w[lo];
         const uint32_t dy = local / w, dx = local - dy * w;
-        const uint32_t tile = (s_y0[lo] + dy) * (uint32_t)TX + s_x0[lo] + dx;
+        const uint32_t tile = s_tbase[lo] + (s_y0[lo] + dy) * s_tx[lo] + s_x0[lo] + dx;
         const unsigned long long pos = base + k;
         if (pos < (unsigned long long)capacity) {
             sc.keys[0][pos] = ((unsigned long long)tile << 32) | s_depth[lo];
@@ -444,12 +458,12 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
 }
 
 int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s) {
+                     cudaStream_t s, const RenderDesc* renders, int R) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
     if (nb > 0) k_perm_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
     k_scan_blocks<<<1, kScanThreads, 0, s>>>(nb, capacity, sc);
     if (nb == 0) return 1;
-    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, perm, sc);
+    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, perm, sc, renders, R);
     return 3;
 }
 

@@ -25,6 +25,7 @@
 // cross term) when an entry is staged, and alpha uses ex2.approx.  Forward and backward stage and
 // evaluate with the same instruction sequence, so they take identical skip decisions.
 #include <cstdlib>
+#include <type_traits>
 
 #include "pgs_internal.cuh"
 
@@ -67,20 +68,40 @@ __device__ __forceinline__ uint32_t checked_id(uint32_t id, int64_t n, int32_t* 
     return id;
 }
 
-template <int kPix>  // pixels per thread (vertical strip)
-__global__ void __launch_bounds__(kTilePixels / kPix)
-k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
-                Scratch sc, float* __restrict__ image) {
+// Where one tile reads and writes.
+struct TileJob {
+    int W, H, TX;  // image of the render
+    int tile;      // tile index inside the render
+    float3 bg;
+    uint2 range;   // [first, last) in the sorted pairs
+    float* image;  // [3][H][W] (forward)
+    const float* dL;  // [3][H][W] (backward)
+    float* T_final;
+    uint32_t* last;
+    uint32_t* ncomp;
+};
+
+template <int kDepth>
+struct FwdSmem {
+    float4 xyo[kDepth], s2[kDepth], rgb[kDepth];
+};
+
+// One tile of the forward.  kPix: pixels per thread (vertical strip); kDepth: entries staged per
+// batch.  Every thread of the CTA calls it with the same job.
+template <int kPix, int kDepth>
+__device__ __forceinline__ void fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                         const Scratch& sc, FwdSmem<kDepth>& S) {
     constexpr int kThreads = kTilePixels / kPix;
-    constexpr int kBatch = 2 * kThreads;  // entries staged per batch
-    __shared__ float4 s_xyo[kBatch];
-    __shared__ float4 s_s2[kBatch];
-    __shared__ float4 s_rgb[kBatch];
-    const int tile = (int)sc.tile_order[blockIdx.x];
-    const int px = (tile % TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (tile / TX) * kTile + (threadIdx.x / kTile) * kPix;
+    constexpr int kBatch = kDepth;
+    float4* s_xyo = S.xyo;
+    float4* s_s2 = S.s2;
+    float4* s_rgb = S.rgb;
+    const int W = J.W, H = J.H;
+    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
+    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
-    const uint2 range = sc.ranges[tile];
+    const uint2 range = J.range;
+    const float3 bg = J.bg;
     float T[kPix], C0[kPix], C1[kPix], C2[kPix];
     uint32_t last[kPix], ncomp[kPix];
     bool done[kPix];
@@ -144,12 +165,12 @@ k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
         const int py = py0 + k;
         if (px < W && py < H) {
             const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
-            image[p] = fmaf(T[k], bg.x, C0[k]);
-            image[plane + p] = fmaf(T[k], bg.y, C1[k]);
-            image[2 * plane + p] = fmaf(T[k], bg.z, C2[k]);
-            sc.T_final[p] = T[k];
-            sc.last[p] = last[k];
-            sc.ncomp[p] = ncomp[k];
+            J.image[p] = fmaf(T[k], bg.x, C0[k]);
+            J.image[plane + p] = fmaf(T[k], bg.y, C1[k]);
+            J.image[2 * plane + p] = fmaf(T[k], bg.z, C2[k]);
+            J.T_final[p] = T[k];
+            J.last[p] = last[k];
+            J.ncomp[p] = ncomp[k];
         }
     }
 }
@@ -182,24 +203,32 @@ __device__ __forceinline__ void warp_sum9(const float v[9], int lane, float& s8,
     s9 = t;
 }
 
-template <int kPix>
-__global__ void __launch_bounds__(kTilePixels / kPix)
-k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
-                Scratch sc, const float* __restrict__ dL_dimage) {
+template <int kDepth>
+struct BwdSmem {
+    float4 xyo[kDepth], s2[kDepth], con[kDepth], rgb[kDepth];
+    uint32_t id[kDepth];
+    uint32_t wmax[kTilePixels / 32];
+};
+
+template <int kPix, int kDepth>
+__device__ __forceinline__ void bwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                         const Scratch& sc, BwdSmem<kDepth>& S) {
     constexpr int kThreads = kTilePixels / kPix;
-    constexpr int kBatch = 2 * kThreads;
-    __shared__ float4 s_xyo[kBatch];
-    __shared__ float4 s_s2[kBatch];
-    __shared__ float4 s_con[kBatch];
-    __shared__ float4 s_rgb[kBatch];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint32_t s_max[kThreads / 32];
-    const int tile = (int)sc.tile_order[blockIdx.x];
+    constexpr int kBatch = kDepth;
+    float4* s_xyo = S.xyo;
+    float4* s_s2 = S.s2;
+    float4* s_con = S.con;
+    float4* s_rgb = S.rgb;
+    uint32_t* s_id = S.id;
+    uint32_t* s_max = S.wmax;
+    const int W = J.W, H = J.H;
+    const float3 bg = J.bg;
+    const float* __restrict__ dL_dimage = J.dL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = (tile % TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (tile / TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
+    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
-    const uint2 range = sc.ranges[tile];
+    const uint2 range = J.range;
     const size_t plane = (size_t)W * H;
     float T[kPix], g0[kPix], g1[kPix], g2[kPix], B0[kPix], B1[kPix], B2[kPix];
     uint32_t my_last[kPix];
@@ -212,8 +241,8 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
         my_last[k] = 0;
         if (px < W && py < H) {
             const size_t p = (size_t)py * W + px;
-            T[k] = sc.T_final[p];
-            my_last[k] = sc.last[p];
+            T[k] = J.T_final[p];
+            my_last[k] = J.last[p];
             g0[k] = dL_dimage[p];
             g1[k] = dL_dimage[plane + p];
             g2[k] = dL_dimage[2 * plane + p];
@@ -310,39 +339,170 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     }
 }
 
+
+__device__ __forceinline__ int render_of_tile(const RenderDesc* __restrict__ renders, int R, int64_t gt) {
+    int lo = 0, hi = R - 1;  // last render whose tile_base <= gt
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (renders[mid].tile_base <= gt) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ TileJob batch_job(const RenderDesc& rd, int64_t gt, const Scratch& sc) {
+    TileJob J;
+    J.W = rd.cam.width;
+    J.H = rd.cam.height;
+    J.TX = rd.TX;
+    J.tile = (int)(gt - rd.tile_base);
+    J.bg = make_float3(rd.cam.bg[0], rd.cam.bg[1], rd.cam.bg[2]);
+    J.range = sc.ranges[gt];
+    J.image = rd.image;
+    J.dL = rd.dL;
+    J.T_final = sc.T_final + rd.pixel_base;
+    J.last = sc.last + rd.pixel_base;
+    J.ncomp = sc.ncomp + rd.pixel_base;
+    return J;
+}
+
+template <int kPix, int kDepth>
+__global__ void __launch_bounds__(kTilePixels / kPix)
+k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
+                Scratch sc, float* __restrict__ image) {
+    __shared__ FwdSmem<kDepth> S;
+    TileJob J;
+    J.W = W;
+    J.H = H;
+    J.TX = TX;
+    J.tile = (int)sc.tile_order[blockIdx.x];
+    J.bg = bg;
+    J.range = sc.ranges[J.tile];
+    J.image = image;
+    J.dL = nullptr;
+    J.T_final = sc.T_final;
+    J.last = sc.last;
+    J.ncomp = sc.ncomp;
+    fwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+}
+
+template <int kPix, int kDepth>
+__global__ void __launch_bounds__(kTilePixels / kPix)
+k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
+                Scratch sc, const float* __restrict__ dL_dimage) {
+    __shared__ BwdSmem<kDepth> S;
+    TileJob J;
+    J.W = W;
+    J.H = H;
+    J.TX = TX;
+    J.tile = (int)sc.tile_order[blockIdx.x];
+    J.bg = bg;
+    J.range = sc.ranges[J.tile];
+    J.image = nullptr;
+    J.dL = dL_dimage;
+    J.T_final = sc.T_final;
+    J.last = sc.last;
+    J.ncomp = sc.ncomp;
+    bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+}
+
+// Batched compositing: persistent CTAs take global tiles, heaviest first, from a device work
+// counter (an atomic ticket; no CTA ever waits for another) until every tile of every render
+// is done.
+template <int kPix, int kDepth, bool kBackward>
+__global__ void __launch_bounds__(kTilePixels / kPix)
+k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_tiles, int64_t n,
+                  const uint32_t* __restrict__ vals, Scratch sc, uint32_t* __restrict__ work) {
+    __shared__ typename std::conditional<kBackward, BwdSmem<kDepth>, FwdSmem<kDepth>>::type S;
+    __shared__ int64_t s_job;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_job = (int64_t)atomicAdd(work, 1u);
+        __syncthreads();
+        const int64_t job = s_job;
+        if (job >= total_tiles) break;
+        const int64_t gt = sc.tile_order[job];
+        const TileJob J = batch_job(renders[render_of_tile(renders, R, gt)], gt, sc);
+        if constexpr (kBackward) bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+        else fwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+    }
+}
+
 }  // namespace
 
-// pixels per thread of the compositing kernels (1, 2 or 4; default 2, measured fastest on the
-// 500k-Gaussian 1080p workload), overridable with PGS_COMPOSITE_PIXELS (read once per process)
-int composite_pixels() {
-    static int v = [] {
-        const char* e = getenv("PGS_COMPOSITE_PIXELS");
-        const int p = e ? atoi(e) : 2;
-        return (p == 1 || p == 4) ? p : 2;
+// pixels per thread (1, 2, 4) and staging depth (64, 128, 256 entries) of the compositing
+// kernels; default (2, 256), the autotuner's choice on the 500k-Gaussian 1080p workload.
+// PGS_COMPOSITE_PIXELS / PGS_COMPOSITE_DEPTH override the default (read once per process).
+CompositeVariant default_variant() {
+    static CompositeVariant v = [] {
+        CompositeVariant c{2, 256};
+        if (const char* e = getenv("PGS_COMPOSITE_PIXELS")) c.pix = atoi(e);
+        if (const char* e = getenv("PGS_COMPOSITE_DEPTH")) c.depth = atoi(e);
+        if (!valid_variant(c)) c = CompositeVariant{2, 256};
+        return c;
     }();
     return v;
 }
 
+bool valid_variant(CompositeVariant v) {
+    return (v.pix == 1 || v.pix == 2 || v.pix == 4) && (v.depth == 64 || v.depth == 128 || v.depth == 256);
+}
+
+#define PGS_VARIANTS(X) X(1, 64) X(1, 128) X(1, 256) X(2, 64) X(2, 128) X(2, 256) X(4, 64) X(4, 128) X(4, 256)
+
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
-                         const Scratch& sc, float* image, cudaStream_t s) {
+                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
-    switch (composite_pixels()) {
-        case 1: k_composite_fwd<1><<<TX * TY, kTilePixels, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, image); break;
-        case 2: k_composite_fwd<2><<<TX * TY, kTilePixels / 2, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, image); break;
-        default: k_composite_fwd<4><<<TX * TY, kTilePixels / 4, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, image); break;
+#define X(P, D)                                                                                   \
+    if (v.pix == P && v.depth == D) {                                                             \
+        k_composite_fwd<P, D><<<TX * TY, kTilePixels / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+                                                                  sc.vals[buf], sc, image);      \
+        return 1;                                                                                 \
     }
-    return 1;
+    PGS_VARIANTS(X)
+#undef X
+    return 0;
 }
 
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
-                         const Scratch& sc, const float* dL_dimage, cudaStream_t s) {
+                         const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
-    switch (composite_pixels()) {
-        case 1: k_composite_bwd<1><<<TX * TY, kTilePixels, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, dL_dimage); break;
-        case 2: k_composite_bwd<2><<<TX * TY, kTilePixels / 2, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, dL_dimage); break;
-        default: k_composite_bwd<4><<<TX * TY, kTilePixels / 4, 0, s>>>(cam.width, cam.height, TX, bg, n, sc.vals[buf], sc, dL_dimage); break;
+#define X(P, D)                                                                                   \
+    if (v.pix == P && v.depth == D) {                                                             \
+        k_composite_bwd<P, D><<<TX * TY, kTilePixels / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+                                                                  sc.vals[buf], sc, dL_dimage);  \
+        return 1;                                                                                 \
     }
+    PGS_VARIANTS(X)
+#undef X
+    return 0;
+}
+
+template <int P, int D, bool B>
+static int launch_batch_variant(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
+                                int64_t n, const Scratch& sc, uint32_t* work, cudaStream_t s) {
+    static int grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_batch<P, D, B>, kTilePixels / P, 0);
+        return sms * (per_sm > 0 ? per_sm : 1);
+    }();
+    k_composite_batch<P, D, B><<<grid, kTilePixels / P, 0, s>>>(renders, R, total_tiles, n,
+                                                               sc.vals[buf], sc, work);
     return 1;
+}
+
+int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
+                           int64_t n, const Scratch& sc, uint32_t* work, bool backward,
+                           cudaStream_t s, CompositeVariant v) {
+#define X(P, D)                                                                                   \
+    if (v.pix == P && v.depth == D)                                                               \
+        return backward ? launch_batch_variant<P, D, true>(renders, R, total_tiles, buf, n, sc, work, s) \
+                        : launch_batch_variant<P, D, false>(renders, R, total_tiles, buf, n, sc, work, s);
+    PGS_VARIANTS(X)
+#undef X
+    return 0;
 }
 
 }  // namespace pgs

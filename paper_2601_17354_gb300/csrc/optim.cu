@@ -164,6 +164,59 @@ __global__ void __launch_bounds__(kThreads) k_adam_scalar(AdamArgs a) {
 
 bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
 
+// Batched L1: one pass over every render's image values (renders' values are numbered
+// consecutively); gradient sign / (3 H W) of the value's render; per-render sums of |d| and d^2
+// accumulated in double (losses[2 r], losses[2 r + 1], zeroed by the caller).  Each CTA covers
+// a contiguous chunk, so a thread's values change render rarely and it flushes per change.
+constexpr int kLossChunk = kThreads * 16;
+
+__global__ void __launch_bounds__(kThreads)
+k_loss_batch(const RenderDesc* __restrict__ renders, int R, int64_t values, double* __restrict__ losses) {
+    const int64_t begin = (int64_t)blockIdx.x * kLossChunk;
+    const int64_t end = begin + kLossChunk < values ? begin + kLossChunk : values;
+    int r = -1;
+    double l1 = 0.0, l2 = 0.0;
+    int64_t rend = -1;
+    const float* img = nullptr;
+    const float* tgt = nullptr;
+    float* grad = nullptr;
+    float inv_n = 0.f;
+    int64_t vbase = 0;
+    for (int64_t e = begin + threadIdx.x; e < end; e += kThreads) {
+        if (e >= rend) {
+            if (r >= 0) {
+                atomicAdd(&losses[2 * r], l1);
+                atomicAdd(&losses[2 * r + 1], l2);
+            }
+            int lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (renders[mid].value_base <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            r = lo;
+            const RenderDesc& rd = renders[r];
+            const int64_t nv = 3ll * rd.cam.width * rd.cam.height;
+            vbase = rd.value_base;
+            rend = vbase + nv;
+            img = rd.image;
+            tgt = rd.target;
+            grad = rd.dL;
+            inv_n = 1.0f / (float)nv;
+            l1 = l2 = 0.0;
+        }
+        const int64_t q = e - vbase;
+        const float d = img[q] - tgt[q];
+        l1 += fabsf(d);
+        l2 += (double)d * d;
+        grad[q] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+    }
+    if (r >= 0) {
+        atomicAdd(&losses[2 * r], l1);
+        atomicAdd(&losses[2 * r + 1], l2);
+    }
+}
+
 }  // namespace
 
 int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
@@ -206,6 +259,13 @@ int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussi
     const dim3 grid((unsigned)bx, (unsigned)rows);
     if (vec) k_adam_vec4<<<grid, kThreads, 0, s>>>(a);
     else k_adam_scalar<<<grid, kThreads, 0, s>>>(a);
+    return 1;
+}
+
+int launch_loss_batch(const RenderDesc* renders, int R, int64_t values, double* losses, cudaStream_t s) {
+    const int64_t blocks = (values + kLossChunk - 1) / kLossChunk;
+    if (blocks == 0) return 0;
+    k_loss_batch<<<(unsigned)blocks, kThreads, 0, s>>>(renders, R, values, losses);
     return 1;
 }
 

@@ -68,6 +68,38 @@ struct Scratch {
 
 constexpr int kLossBlocks = 1024;
 
+// One render of a batch (device table): its camera, its scene, where its projected Gaussians
+// ("items"), tiles and pixels start in the batch-wide arrays, and its image buffers.
+struct RenderDesc {
+    pgs_camera cam;
+    int32_t scene;
+    int32_t TX, TY;
+    int32_t pad_;
+    int64_t item_base;   // first item: item j of the render = Gaussian j - item_base of the scene
+    int64_t n;           // Gaussians of the scene
+    int64_t tile_base;   // first batch-wide tile
+    int64_t pixel_base;  // first pixel of the batch-wide per-pixel planes
+    int64_t value_base;  // first value of the batch-wide image buffers (3 H W per render)
+    float* image;        // [3][H][W]
+    const float* target; // [3][H][W]
+    float* dL;           // [3][H][W]
+};
+
+// One scene of a batch (device table): parameters and Adam moments, and its renders
+// [first_render, first_render + n_renders) (renders are stored scene by scene).
+struct SceneDesc {
+    pgs_gaussians params, m, v;
+    int32_t first_render, n_renders;
+    int64_t gauss_base;  // first Gaussian of the scene in the batch-wide Gaussian numbering
+};
+
+// Compositing kernel variant: pixels per thread and entries staged per batch.
+struct CompositeVariant {
+    int pix, depth;
+};
+bool valid_variant(CompositeVariant v);
+CompositeVariant default_variant();
+
 // ---------------------------------------------------------------------------------------------
 // launchers (all asynchronous on `s`); each returns the number of kernels it launched
 // ---------------------------------------------------------------------------------------------
@@ -89,10 +121,19 @@ int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const
                             pgs_gaussians& m, pgs_gaussians& v, const float lr[6], float b1,
                             float b2, float eps, int64_t t, cudaStream_t s);
 
+// Batched variants (render / scene tables in device memory; see RenderDesc, SceneDesc).
+int launch_project_fwd_batch(const RenderDesc* renders, int R, const SceneDesc* scenes, int deg,
+                             int64_t items, const Scratch& sc, cudaStream_t s);
+int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, int S, int deg,
+                          int64_t gauss_total, int64_t items, const Scratch& sc, const float lr[6],
+                          float b1, float b2, float eps, const int64_t* step, cudaStream_t s);
+int launch_step_tick(int64_t* step, cudaStream_t s);
+int launch_loss_batch(const RenderDesc* renders, int R, int64_t values, double* losses, cudaStream_t s);
+
 // K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
 // emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
 int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s);
+                     cudaStream_t s, const RenderDesc* renders = nullptr, int R = 0);
 // K4/K5: stable radix sort of the pairs by the tile bits (returns which ping-pong buffer holds
 // the result) and ranges.
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
@@ -109,9 +150,14 @@ int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
-                         const Scratch& sc, float* image, cudaStream_t s);
+                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v);
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
-                          const Scratch& sc, const float* dL_dimage, cudaStream_t s);
+                         const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v);
+// Batched compositing over every tile of every render in one persistent launch; `work` is a
+// zeroed device counter.
+int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
+                           int64_t n, const Scratch& sc, uint32_t* work, bool backward,
+                           cudaStream_t s, CompositeVariant v);
 
 // K7: L1 loss; K10: fused Adam over all parameter groups.
 int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,

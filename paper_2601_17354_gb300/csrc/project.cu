@@ -205,80 +205,113 @@ __device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3])
     for (int k = 0; k < 3; ++k) c[k] = -(V[k] * V[3] + V[4 + k] * V[7] + V[8 + k] * V[11]);
 }
 
+// Project Gaussian i of g through cam (tile grid TX x TY) and write its record at item j.
+template <int DEG>
+__device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
+                                             int TX, int TY, int64_t j, const Scratch& sc) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t n = g.n;
+    uint32_t count = 0;
+    const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
+    const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
+    const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
+    const float logit = g.opacity_logits[i];
+    bool finite = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(ls[0]) &&
+                  isfinite(ls[1]) && isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) &&
+                  isfinite(q[2]) && isfinite(q[3]) && isfinite(logit);
+    Geo G;
+    bool vis = finite && geometry(mu, ls, q, cam, G);
+    uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (vis) {
+        const float mid = __fmul_rn(0.5f, __fadd_rn(G.cov_a, G.cov_c));
+        const float disc = fmaxf(0.1f, __fsub_rn(__fmul_rn(mid, mid), G.det));
+        const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
+        const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
+        vis = isfinite(rad);
+        if (vis) {
+            const float tf = (float)kTile;
+            x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rad), tf)), 0.0f, (float)TX);
+            x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rad), tf)), 1.0f), 0.0f, (float)TX);
+            y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, rad), tf)), 0.0f, (float)TY);
+            y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, rad), tf)), 1.0f), 0.0f, (float)TY);
+            count = (x1 - x0) * (y1 - y0);
+        }
+    }
+    if (count > 0) {
+        // value path: conic, opacity, colour
+        const float inv_det = 1.0f / G.det;
+        const float opacity = 1.0f / (1.0f + expf(-logit));
+        float cc[3];
+        camera_centre(cam, cc);
+        float d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+        const float inv_len = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        d[0] *= inv_len;
+        d[1] *= inv_len;
+        d[2] *= inv_len;
+        float Y[16];
+        sh_eval(K, d[0], d[1], d[2], Y);
+        float rgb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc += g.sh[((int64_t)c * K + k) * n + i] * Y[k];
+            rgb[c] = fmaxf(acc, 0.0f);
+        }
+        if (!isfinite(rgb[0]) || !isfinite(rgb[1]) || !isfinite(rgb[2])) {
+            count = 0;
+            finite = false;
+        } else {
+            sc.xyo[j] = make_float4(G.u, G.v, opacity, 0.0f);
+            sc.conic[j] = make_float4(G.cov_c * inv_det, -G.cov_b * inv_det, G.cov_a * inv_det, 0.0f);
+            sc.rgb[j] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+            sc.depth_bits[j] = __float_as_uint(G.zc);
+            sc.rect[j] = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+        }
+    }
+    if (!finite) atomicOr(sc.status, kStatusNonfinite);
+    sc.touched[j] = count;
+    // depth-sort input: visible Gaussians by depth bits, culled ones last
+    sc.dkeys[0][j] = count > 0 ? (unsigned long long)sc.depth_bits[j] : 0xffffffffull;
+    sc.dvals[0][j] = (uint32_t)j;
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    uint32_t count = 0;
-    if (i < n) {
-        const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
-        const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
-        const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
-        const float logit = g.opacity_logits[i];
-        bool finite = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(ls[0]) &&
-                      isfinite(ls[1]) && isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) &&
-                      isfinite(q[2]) && isfinite(q[3]) && isfinite(logit);
-        Geo G;
-        bool vis = finite && geometry(mu, ls, q, cam, G);
-        uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-        if (vis) {
-            const float mid = __fmul_rn(0.5f, __fadd_rn(G.cov_a, G.cov_c));
-            const float disc = fmaxf(0.1f, __fsub_rn(__fmul_rn(mid, mid), G.det));
-            const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
-            const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
-            vis = isfinite(rad);
-            if (vis) {
-                const float tf = (float)kTile;
-                x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rad), tf)), 0.0f, (float)TX);
-                x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rad), tf)), 1.0f), 0.0f, (float)TX);
-                y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, rad), tf)), 0.0f, (float)TY);
-                y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, rad), tf)), 1.0f), 0.0f, (float)TY);
-                count = (x1 - x0) * (y1 - y0);
-            }
-        }
-        if (count > 0) {
-            // value path: conic, opacity, colour
-            const float inv_det = 1.0f / G.det;
-            const float opacity = 1.0f / (1.0f + expf(-logit));
-            float cc[3];
-            camera_centre(cam, cc);
-            float d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
-            const float inv_len = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            d[0] *= inv_len;
-            d[1] *= inv_len;
-            d[2] *= inv_len;
-            float Y[16];
-            sh_eval(K, d[0], d[1], d[2], Y);
-            float rgb[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float acc = 0.5f;
-#pragma unroll
-                for (int k = 0; k < K; ++k) acc += g.sh[((int64_t)c * K + k) * n + i] * Y[k];
-                rgb[c] = fmaxf(acc, 0.0f);
-            }
-            if (!isfinite(rgb[0]) || !isfinite(rgb[1]) || !isfinite(rgb[2])) {
-                count = 0;
-                finite = false;
-            } else {
-                sc.xyo[i] = make_float4(G.u, G.v, opacity, 0.0f);
-                sc.conic[i] = make_float4(G.cov_c * inv_det, -G.cov_b * inv_det, G.cov_a * inv_det, 0.0f);
-                sc.rgb[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
-                sc.depth_bits[i] = __float_as_uint(G.zc);
-                sc.rect[i] = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
-            }
-        }
-        if (!finite) atomicOr(sc.status, kStatusNonfinite);
-        sc.touched[i] = count;
-        // depth-sort input: visible Gaussians by depth bits, culled ones last
-        sc.dkeys[0][i] = count > 0 ? (unsigned long long)sc.depth_bits[i] : 0xffffffffull;
-        sc.dvals[0][i] = (uint32_t)i;
-    }
+    if (i < n) project_item<DEG>(g, i, cam, TX, TY, i, sc);
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
         *sc.dblocks = (uint32_t)((n + kSortTile - 1) / kSortTile);
+    }
+}
+
+// last render whose first item is <= j
+__device__ __forceinline__ int render_of_item(const RenderDesc* __restrict__ renders, int R, int64_t j) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (renders[mid].item_base <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched projection: item j = (render r, Gaussian j - item_base of r's scene).
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock)
+k_project_fwd_batch(const RenderDesc* __restrict__ renders, int R, const SceneDesc* __restrict__ scenes,
+                    int64_t items, Scratch sc) {
+    const int64_t j = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    if (j < items) {
+        const RenderDesc& rd = renders[render_of_item(renders, R, j)];
+        project_item<DEG>(scenes[rd.scene].params, j - rd.item_base, rd.cam, rd.TX, rd.TY, j, sc);
+    }
+    if (j == 0) {
+        *sc.dcount = (unsigned long long)items;
+        *sc.dblocks = (uint32_t)((items + kSortTile - 1) / kSortTile);
     }
 }
 
@@ -292,7 +325,8 @@ struct GradParts {
 };
 
 template <int DEG>
-__device__ __forceinline__ void chain(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
+__device__ __forceinline__ void chain(const pgs_gaussians& g, const pgs_camera& cam,
+                                      const float* __restrict__ grad2d, int64_t gstride, int64_t gidx,
                                       int64_t i, GradParts& out) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
@@ -303,7 +337,7 @@ __device__ __forceinline__ void chain(const pgs_gaussians& g, const pgs_camera& 
     geometry(mu, ls, q, cam, G);
     float gr[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) gr[k] = sc.grad2d[k * n + i];
+    for (int k = 0; k < 9; ++k) gr[k] = grad2d[k * gstride + gidx];
     const float* V = cam.viewmat;
 
     // colour -> SH coefficients and view direction
@@ -484,7 +518,7 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     if (i >= n || sc.touched[i] == 0) return;
     GradParts gp;
-    chain<DEG>(g, cam, sc, i, gp);
+    chain<DEG>(g, cam, sc.grad2d, n, i, i, gp);
     const Rows O = rows_of(out);
 #pragma unroll
     for (int r0 = 0; r0 < ROWS; r0 += kChunk) {
@@ -517,7 +551,7 @@ k_project_bwd_adam(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians m,
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     if (i >= n) return;
     GradParts gp;
-    if (sc.touched[i] != 0) chain<DEG>(g, cam, sc, i, gp);
+    if (sc.touched[i] != 0) chain<DEG>(g, cam, sc.grad2d, n, i, i, gp);
     else zero_parts(gp);
     const Rows Pp = rows_of(g), Mm = rows_of(m), Vv = rows_of(v);
 #pragma unroll
@@ -547,6 +581,92 @@ k_project_bwd_adam(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians m,
                 Pp.g[gi][idx] = pp[j];
                 Mm.g[gi][idx] = mm[j];
                 Vv.g[gi][idx] = vv[j];
+            }
+        }
+    }
+}
+
+// Adam bias corrections for step t read from the device (so a captured step graph advances it).
+struct AdamDev {
+    float lr[6];
+    float b1, b2, omb1, omb2, eps;
+};
+
+__global__ void k_step_tick(int64_t* step) { *step += 1; }
+
+__device__ __forceinline__ int scene_of(const SceneDesc* __restrict__ scenes, int S, int64_t k) {
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scenes[mid].gauss_base <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched backward + Adam: one thread per Gaussian of every scene.  The Gaussian's parameter
+// gradient is summed over the scene's renders (views) in shared memory, row by row, and then
+// consumed by the Adam update of the scene's parameters.
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, 2)
+k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __restrict__ scenes, int S,
+                 int64_t gauss_total, int64_t items, Scratch sc, AdamDev a, const int64_t* __restrict__ step) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROWS = 11 + 3 * K;
+    extern __shared__ float s_acc[];  // [ROWS][kProjBlock]
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+        const double t = (double)*step;
+        s_bc[0] = (float)(1.0 - pow((double)a.b1, t));
+        s_bc[1] = (float)(1.0 - pow((double)a.b2, t));
+    }
+    const int64_t k = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    float* acc = s_acc + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] = 0.f;
+    __syncthreads();
+    const float bc1 = s_bc[0], bc2 = s_bc[1];
+    if (k >= gauss_total) return;
+    const SceneDesc& sd = scenes[scene_of(scenes, S, k)];
+    const int64_t i = k - sd.gauss_base;
+    const int64_t n = sd.params.n;
+    for (int rr = 0; rr < sd.n_renders; ++rr) {
+        const RenderDesc& rd = renders[sd.first_render + rr];
+        const int64_t j = rd.item_base + i;
+        if (sc.touched[j] == 0) continue;
+        GradParts gp;
+        chain<DEG>(sd.params, rd.cam, sc.grad2d, items, j, i, gp);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] += grad_row<DEG>(gp, r);
+    }
+    const Rows Pp = rows_of(sd.params), Mm = rows_of(sd.m), Vv = rows_of(sd.v);
+#pragma unroll
+    for (int r0 = 0; r0 < ROWS; r0 += kChunk) {
+        float pp[kChunk], mm[kChunk], vv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            if (r0 + q < ROWS) {
+                const int gi = row_group(r0 + q);
+                const int64_t idx = (int64_t)row_sub(r0 + q) * n + i;
+                pp[q] = Pp.g[gi][idx];
+                mm[q] = Mm.g[gi][idx];
+                vv[q] = Vv.g[gi][idx];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int r = r0 + q;
+            if (r < ROWS) {
+                const int gi = row_group(r);
+                const float lr = gi < 4 ? a.lr[gi] : (row_sub(r) % K == 0 ? a.lr[4] : a.lr[5]);
+                const float gr = acc[r * kProjBlock];
+                mm[q] = a.b1 * mm[q] + a.omb1 * gr;
+                vv[q] = a.b2 * vv[q] + a.omb2 * gr * gr;
+                pp[q] -= lr * (mm[q] / bc1) / (sqrtf(vv[q] / bc2) + a.eps);
+                const int64_t idx = (int64_t)row_sub(r) * n + i;
+                Pp.g[gi][idx] = pp[q];
+                Mm.g[gi][idx] = mm[q];
+                Vv.g[gi][idx] = vv[q];
             }
         }
     }
@@ -601,6 +721,60 @@ int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const
         default: k_project_bwd_adam<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
     }
     return 1;
+}
+
+int launch_project_fwd_batch(const RenderDesc* renders, int R, const SceneDesc* scenes, int deg,
+                             int64_t items, const Scratch& sc, cudaStream_t s) {
+    const int64_t blocks = (items + kProjBlock - 1) / kProjBlock;
+    if (blocks == 0) return 0;
+    switch (deg) {
+        case 0: k_project_fwd_batch<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(renders, R, scenes, items, sc); break;
+        case 1: k_project_fwd_batch<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(renders, R, scenes, items, sc); break;
+        case 2: k_project_fwd_batch<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(renders, R, scenes, items, sc); break;
+        default: k_project_fwd_batch<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(renders, R, scenes, items, sc); break;
+    }
+    return 1;
+}
+
+int launch_step_tick(int64_t* step, cudaStream_t s) {
+    k_step_tick<<<1, 1, 0, s>>>(step);
+    return 1;
+}
+
+template <int DEG>
+static int launch_bwd_adam_batch_deg(const RenderDesc* renders, const SceneDesc* scenes, int S,
+                                     int64_t gauss_total, int64_t items, const Scratch& sc,
+                                     const AdamDev& a, const int64_t* step, cudaStream_t s) {
+    constexpr int ROWS = 11 + 3 * (DEG + 1) * (DEG + 1);
+    const size_t smem = sizeof(float) * ROWS * kProjBlock;
+    static bool attr = [&] {
+        cudaFuncSetAttribute(k_bwd_adam_batch<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return true;
+    }();
+    (void)attr;
+    const int64_t blocks = (gauss_total + kProjBlock - 1) / kProjBlock;
+    k_bwd_adam_batch<DEG><<<(unsigned)blocks, kProjBlock, smem, s>>>(renders, scenes, S, gauss_total,
+                                                                     items, sc, a, step);
+    return 1;
+}
+
+int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, int S, int deg,
+                          int64_t gauss_total, int64_t items, const Scratch& sc, const float lr[6],
+                          float b1, float b2, float eps, const int64_t* step, cudaStream_t s) {
+    if (gauss_total == 0) return 0;
+    AdamDev a;
+    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    a.b1 = b1;
+    a.b2 = b2;
+    a.omb1 = (float)(1.0 - (double)b1);
+    a.omb2 = (float)(1.0 - (double)b2);
+    a.eps = eps;
+    switch (deg) {
+        case 0: return launch_bwd_adam_batch_deg<0>(renders, scenes, S, gauss_total, items, sc, a, step, s);
+        case 1: return launch_bwd_adam_batch_deg<1>(renders, scenes, S, gauss_total, items, sc, a, step, s);
+        case 2: return launch_bwd_adam_batch_deg<2>(renders, scenes, S, gauss_total, items, sc, a, step, s);
+        default: return launch_bwd_adam_batch_deg<3>(renders, scenes, S, gauss_total, items, sc, a, step, s);
+    }
 }
 
 }  // namespace pgs

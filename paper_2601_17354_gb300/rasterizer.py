@@ -199,6 +199,18 @@ class Rasterizer:
                                           cnt.ctypes.data_as(C.c_void_p)), "pgs_stage_times")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(L.PGS_STAGES)}
 
+    def set_variant(self, pixels_per_thread: int, depth: int):
+        L.check(self._lib.pgs_set_variant(self._ctx, int(pixels_per_thread), int(depth)), "pgs_set_variant")
+
+    def time_variants(self, dL_dimage: torch.Tensor, reps: int = 3) -> dict:
+        """{(pixels per thread, depth): ms} of forward + backward compositing on the last render."""
+        ms = np.zeros(len(L.VARIANTS), np.float32)
+        scratch = torch.empty_like(dL_dimage)
+        L.check(self._lib.pgs_time_variants(self._ctx, C.c_void_p(scratch.data_ptr()),
+                                            C.c_void_p(dL_dimage.data_ptr()), int(reps),
+                                            ms.ctypes.data_as(C.c_void_p)), "pgs_time_variants")
+        return {v: float(t) for v, t in zip(L.VARIANTS, ms)}
+
     def launch_count(self) -> int:
         return int(self._lib.pgs_launch_count(self._ctx))
 

@@ -1,0 +1,136 @@
+"""Batched training (many views of uneven scenes in one persistent launch, CUDA graph, autotuner)
+against the single-view path, which the oracle parity tests pin."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_17354_gb300 import synthetic as S
+from tests._parity import compare_forward, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2601_17354_gb300 import _lib, autotune, batch, rasterizer
+    return rasterizer, batch, autotune, _lib
+
+
+def small_batch(seed=0):
+    """Three scenes with uneven Gaussian counts and resolutions, two views each."""
+    specs = [(4000, 160, 120, 140.0), (9000, 96, 64, 80.0), (2500, 130, 100, 120.0)]
+    scenes, views = [], []
+    for s, (n, w, h, f) in enumerate(specs):
+        sc = S.surface_scene(seed * 10 + s, n, 1, w, h, f, n_cameras=4)
+        scenes.append(sc)
+        for v in (0, 2):
+            views.append((s, sc.cameras[v], S.random_image(100 * s + v, w, h, 0.0, 1.0)))
+    return scenes, views
+
+
+def make_trainer(mods, scenes, views, **kw):
+    R, B, _, _ = mods
+    bufs = [R.GaussianBuffer.from_arrays(sc.init) for sc in scenes]
+    tv = [(s, c, torch.from_numpy(t).cuda()) for s, c, t in views]
+    return B.BatchTrainer(bufs, tv, **kw), bufs
+
+
+def test_batch_step_matches_single_view_calls(mods):
+    R, B, _, L = mods
+    scenes, views = small_batch()
+    bt, bufs = make_trainer(mods, scenes, views)
+    bt.step()
+    torch.cuda.synchronize()
+    assert bt.status()[0] == 0
+    losses = bt.losses()
+    # single-view reference: per scene, accumulate the gradients of its views, then one Adam step
+    rast = R.Rasterizer()
+    for s, sc in enumerate(scenes):
+        p = R.GaussianBuffer.from_arrays(sc.init)
+        g, m, v = p.zeros_like(), p.zeros_like(), p.zeros_like()
+        for k, (vs, cam, tgt) in enumerate(views):
+            if vs != s:
+                continue
+            img = rast.render(p, cam)
+            assert torch.equal(img, bt.images[k]), f"render {k} differs"
+            dl, loss = rast.loss_l1(img, torch.from_numpy(tgt).cuda())
+            assert abs(float(loss[0]) - losses[k, 0]) <= 1e-6 * losses[k, 0]
+            rast.backward(dl, g)
+        rast.step(p, g, m, v, 1)
+        torch.cuda.synchronize()
+        assert rel_l2(bt.m[s].data.cpu().numpy(), m.data.cpu().numpy()) < 1e-5
+        assert rel_l2(bt.v[s].data.cpu().numpy(), v.data.cpu().numpy()) < 1e-5
+        dp = np.abs(bufs[s].data.cpu().numpy() - p.data.cpu().numpy())
+        assert np.mean(dp > 1e-6) < 2e-3
+
+
+def test_batch_render_matches_oracle(mods):
+    scenes, views = small_batch(1)
+    bt, _ = make_trainer(mods, scenes, views)
+    bt.step()
+    torch.cuda.synchronize()
+    s, cam, _ = views[2]
+    ora = oracle.render(scenes[s].init, cam)
+    img = bt.images[2].cpu().numpy()
+    bad = (np.abs(img - ora["image"]).max(axis=0) > 1e-4) & (ora["flag"] == 0)
+    assert not bad.any()
+
+
+def test_graph_replay_equals_eager_steps(mods):
+    scenes, views = small_batch(2)
+    a, pa = make_trainer(mods, scenes, views)
+    b, pb = make_trainer(mods, scenes, views)
+    b.capture()
+    for _ in range(3):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert a.status()[0] == 0 and b.status()[0] == 0
+    assert b.launch_count() > 0
+    for x, y in zip(pa, pb):
+        assert rel_l2(y.data.cpu().numpy(), x.data.cpu().numpy()) < 1e-4
+    for k in range(len(views)):
+        assert rel_l2(b.images[k].cpu().numpy(), a.images[k].cpu().numpy()) < 1e-4
+
+
+def test_all_variants_render_identically(mods):
+    R, B, _, L = mods
+    scenes, views = small_batch(3)
+    ref = None
+    for pix, depth in L.VARIANTS:
+        bt, _ = make_trainer(mods, scenes, views)
+        bt.set_variant(pix, depth)
+        bt.step()
+        torch.cuda.synchronize()
+        imgs = [im.cpu().numpy() for im in bt.images]
+        if ref is None:
+            ref = imgs
+        else:
+            for a, b in zip(imgs, ref):
+                assert np.array_equal(a, b), (pix, depth)
+
+
+def test_autotuner_times_picks_and_caches(mods, tmp_path):
+    R, B, A, L = mods
+    scenes, views = small_batch(4)
+    bt, _ = make_trainer(mods, scenes, views)
+    cache = str(tmp_path / "tune.json")
+    choice = A.tune_batch(bt, cache=cache, reps=1)
+    assert choice in L.VARIANTS
+    import json
+    data = json.load(open(cache))
+    (entry,) = data.values()
+    assert (entry["pixels"], entry["depth"]) == choice and len(entry["ms"]) == 9
+    bt2, _ = make_trainer(mods, scenes, views)
+    assert A.tune_batch(bt2, cache=cache) == choice
+    bt2.capture()
+    bt2.step()
+    torch.cuda.synchronize()
+    assert bt2.status()[0] == 0
+    # single-view tuning on one render
+    rast = R.Rasterizer()
+    p = R.GaussianBuffer.from_arrays(scenes[0].init)
+    cam = views[0][1]
+    dl = torch.from_numpy(S.random_image(1, cam.width, cam.height)).cuda()
+    assert A.tune_rasterizer(rast, p, cam, dl, cache=cache, reps=1) in L.VARIANTS
