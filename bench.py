@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 16-scene x 4-view measurement")
+    ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: one capacity probe, random targets, --steps "
                          "steps, few launches before them; prints no bench line")
@@ -211,6 +214,55 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
+BATCH_SCENES, BATCH_VIEWS = 16, 4
+
+
+def run_batched(steps: int, warmup: int) -> dict:
+    """16 surface scenes with log-uniform 20k-300k Gaussians and resolutions from {640x480,
+    960x720, 1280x720}, 4 views each: every step renders, differentiates and updates all 64
+    renders in one captured CUDA graph (one persistent compositing launch each way)."""
+    import torch
+    from paper_2601_17354_gb300 import autotune as A
+    from paper_2601_17354_gb300 import batch as B
+    from paper_2601_17354_gb300 import rasterizer as R
+    from paper_2601_17354_gb300 import synthetic as S
+    scenes = S.batched_scenes(11, BATCH_SCENES, BATCH_VIEWS, sh_degree=SH_DEGREE)
+    rast = R.Rasterizer()
+    bufs, views = [], []
+    for s, sc in enumerate(scenes):
+        gt = R.GaussianBuffer.from_arrays(sc.gt)
+        for c in sc.cameras:
+            views.append((s, c, rast.render(gt, c).clone()))
+        bufs.append(R.GaussianBuffer.from_arrays(sc.init))
+    del rast
+    bt = B.BatchTrainer(bufs, views)
+    variant = A.tune_batch(bt)
+    bt.capture()
+    for _ in range(warmup):
+        bt.step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = bt.launch_count()
+    ev0.record(bt.stream)
+    for _ in range(steps):
+        bt.step()
+    ev1.record(bt.stream)
+    torch.cuda.synchronize()
+    code, pairs = bt.status()
+    if code != 0:
+        raise RuntimeError(f"batched step status {code}")
+    ms = ev0.elapsed_time(ev1) / steps
+    losses = bt.losses()
+    return {"workload": f"{BATCH_SCENES} surface scenes x {BATCH_VIEWS} views, Gaussians "
+                        f"log-uniform 20k-300k (total {sum(b.n for b in bufs)}), SH{SH_DEGREE}, "
+                        f"resolutions {sorted({f'{c.width}x{c.height}' for _, c, _ in views})}",
+            "steps_per_s": 1000.0 / ms, "renders_per_s": len(views) * 1000.0 / ms,
+            "ms_per_step": ms, "renders": len(views), "steps": steps, "pairs": int(pairs),
+            "cuda_graph": True, "variant": {"pixels_per_thread": variant[0], "depth": variant[1]},
+            "gpu_launches": int(bt.launch_count() - launches0),
+            "mean_l1": float(losses[:, 0].mean())}
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -243,6 +295,8 @@ def run_ours(args):
     rast = R.Rasterizer(pair_capacity=int(pmax * 1.5) + 4096)
     rast.reserve(N_GAUSS, WIDTH, HEIGHT, int(pmax * 1.5) + 4096)
     params = init.clone()
+    from paper_2601_17354_gb300 import autotune as A
+    tuned = A.tune_rasterizer(rast, params, cams[0], torch.ones(3, HEIGHT, WIDTH, device="cuda") * 1e-6)
     tr = R.Trainer(params, rast)
     stream = rast.stream
 
@@ -351,7 +405,10 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
+        "variant": {"pixels_per_thread": tuned[0], "depth": tuned[1]},
     }
+    if not args.no_batched:
+        out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",
