@@ -18,6 +18,11 @@ Parity status of each function (what pins it, besides agreeing with the GPU path
   det_expf                          FP64 exp within 2 ulp
   adam                              torch.optim.Adam (float64), closed-form first step
   l1                                closed forms
+  knn                               scipy cKDTree (library routine)
+  eig3                              numpy.linalg.eigh (library routine)
+  pca_init / features               closed forms on planes, tilted planes and spheres
+  mlp_forward / mlp_backward        torch float64 autograd of the same network (library routine)
+  init_loss                         torch float64 autograd (library routine)
 """
 from __future__ import annotations
 
@@ -30,6 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pgs_oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "init_oracle.cpp")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
@@ -39,12 +45,13 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle (g++, -O2, -ffp-contract=off).  Returns the library path."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    fresh = os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+    fresh = os.path.exists(_LIB_PATH) and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f)
+                                              for f in _SRCS)
     if fresh and not force:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC]
+           "-o", tmp, *_SRCS]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -86,6 +93,14 @@ def lib():
             L.oracle_fd_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, C.c_double, P]
             L.oracle_gaussian_flags.argtypes = [P, P, C.c_int, P]
             L.oracle_l1.argtypes = [C.c_int64, P, P, P, P, P]
+            L.oracle_knn.argtypes = [C.c_int64, P, C.c_int, P]
+            L.oracle_eig3.argtypes = [P, P, P]
+            L.oracle_pca_init.argtypes = [C.c_int64, P, P, C.c_int, C.c_double, P, P, P]
+            L.oracle_features.argtypes = [C.c_int64, P, P, C.c_int, P, P]
+            L.oracle_mlp_forward.argtypes = [C.c_int64] + [P] * 7 + [C.c_int, P]
+            L.oracle_init_loss.argtypes = [C.c_int64, P, P, P]
+            L.oracle_init_loss.restype = C.c_double
+            L.oracle_mlp_backward.argtypes = [C.c_int64] + [P] * 7 + [P, C.c_int] + [P] * 6
             L.oracle_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int64]
             _lib = L
@@ -269,3 +284,75 @@ def adam(p, g, m, v, lr, t, b1=0.9, b2=0.999, eps=1e-15):
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().oracle_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, t)
+
+
+# ------------------------------------------------------------------------------------------------
+# initializer path (operator I, Sec. III-B) and its learned stand-in
+# ------------------------------------------------------------------------------------------------
+
+def knn(points, k: int) -> np.ndarray:
+    """points [3][n] float32 -> neighbour indices [n][k] (self excluded), by (fp32 d^2, index)."""
+    P = np.ascontiguousarray(points, np.float32)
+    n = P.shape[1]
+    nb = np.zeros((n, k), np.int32)
+    lib().oracle_knn(n, _ptr(P), k, _ptr(nb))
+    return nb
+
+
+def eig3(A):
+    A = np.ascontiguousarray(A, np.float64).reshape(9)
+    w = np.zeros(3)
+    V = np.zeros(9)
+    lib().oracle_eig3(_ptr(A), _ptr(w), _ptr(V))
+    return w, V.reshape(3, 3)
+
+
+def pca_init(points, nb, r_normal: float = 0.1) -> dict:
+    P = np.ascontiguousarray(points, np.float32)
+    nb = np.ascontiguousarray(nb, np.int32)
+    n = P.shape[1]
+    ls, q, lg = np.zeros((3, n)), np.zeros((4, n)), np.zeros(n)
+    lib().oracle_pca_init(n, _ptr(P), _ptr(nb), nb.shape[1], r_normal, _ptr(ls), _ptr(q), _ptr(lg))
+    return dict(log_scales=ls, quats=q, opacity_logits=lg)
+
+
+def features(points, nb):
+    """(features [n][16], eigenframe quaternions [4][n])."""
+    P = np.ascontiguousarray(points, np.float32)
+    nb = np.ascontiguousarray(nb, np.int32)
+    n = P.shape[1]
+    f = np.zeros((n, 16))
+    fq = np.zeros((4, n))
+    lib().oracle_features(n, _ptr(P), _ptr(nb), nb.shape[1], _ptr(f), _ptr(fq))
+    return f, fq
+
+
+def _w(ws):
+    return [np.ascontiguousarray(w, np.float32) for w in ws]
+
+
+def mlp_forward(x, weights, mode: int = 1) -> np.ndarray:
+    """weights = (W1 [64][16], b1, W2 [64][64], b2, W3 [8][64], b3); x [n][16]."""
+    x = np.ascontiguousarray(x, np.float32)
+    W = _w(weights)
+    out = np.zeros((x.shape[0], 8))
+    lib().oracle_mlp_forward(x.shape[0], _ptr(x), *[_ptr(w) for w in W], mode, _ptr(out))
+    return out
+
+
+def init_loss(y, t):
+    y = np.ascontiguousarray(y, np.float64)
+    t = np.ascontiguousarray(t, np.float32)
+    dy = np.zeros_like(y)
+    L = lib().oracle_init_loss(y.shape[0], _ptr(y), _ptr(t), _ptr(dy))
+    return L, dy
+
+
+def mlp_backward(x, weights, dy, mode: int = 1):
+    x = np.ascontiguousarray(x, np.float32)
+    W = _w(weights)
+    dy = np.ascontiguousarray(dy, np.float64)
+    grads = [np.zeros(w.shape) for w in W]
+    lib().oracle_mlp_backward(x.shape[0], _ptr(x), *[_ptr(w) for w in W], _ptr(dy), mode,
+                              *[_ptr(g) for g in grads])
+    return grads
