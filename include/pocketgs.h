@@ -249,6 +249,63 @@ int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms);
    ([3][H][W] scratch) and the backwards use dL_dimage [3][H][W]. */
 int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms);
 
+/* ---------------------------------------------------------------------------------------------
+   Initialization (operator I of Sec. III-B) and its learned stand-in.
+   --------------------------------------------------------------------------------------------- */
+typedef struct pgs_init pgs_init;
+
+/* A context for the initializer kernels on `cuda_stream`; owns the kNN grid scratch. */
+int pgs_init_create(pgs_init** out, void* cuda_stream);
+void pgs_init_destroy(pgs_init* ctx);
+
+/* The k (3, 16 or 32) nearest other points of each of n points [3][n] (device fp32): nb [n][k]
+   (device int32), ascending by squared distance d2 = fma(dx,dx, fma(dy,dy, dz*dz)) in fp32 with
+   ties by index; exact (uniform grid, search widened until provably complete).  -1 pads when
+   n - 1 < k.  Synchronises once (bounding box). */
+int pgs_knn(pgs_init* ctx, const float* points, int64_t n, int32_t k, int32_t* nb);
+
+/* From 32-neighbour lists nb [n][32]: the paper's initializer (Eq. 5 normal from 16 neighbours,
+   Eq. 6 scale from 3, normal scale r_normal * s_t, z axis onto the normal, opacity logit(0.1),
+   means = points, SH = 0) written into `init`; the 16 features of the learned initializer
+   (eigenvalues / sum ascending, eigenvectors smallest first, mean offset / mean distance,
+   -3 log mean distance) as features [n][16] fp32 and features_bf16 [n][16]; the eigenframe
+   quaternion frame_q [4][n] (x largest, z smallest eigenvector).  All device pointers. */
+int pgs_features_init(pgs_init* ctx, const float* points, int64_t n, const int32_t* nb32,
+                      float r_normal, float* features, void* features_bf16, float* frame_q,
+                      pgs_gaussians* init);
+
+/* MLP 16-64-64-8 (GELU): master = FP32 parameters [W1 64x16 | b1 64 | W2 64x64 | b2 64 |
+   W3 8x64 | b3 8] (row-major [out][in]), W1/W2/W3 = their BF16 copies used by the kernels. */
+typedef struct {
+    float* master;
+    void* W1;
+    void* W2;
+    void* W3;
+} pgs_mlp;
+int pgs_mlp_param_count(void);
+/* refresh the BF16 copies from the master parameters */
+int pgs_mlp_pack(pgs_init* ctx, const pgs_mlp* w);
+/* out [n][8] fp32 = MLP(x) for x [n][16] bf16 */
+int pgs_mlp_forward(pgs_init* ctx, const pgs_mlp* w, const void* x_bf16, int64_t n, float* out);
+/* adds d(loss)/d(parameters) to grad [param_count] and the summed per-point loss to *loss_sum
+   (device double); loss = mean over points of |y0..2 - t0..2|^2 + (1 - <y3..6/|y3..6|, t3..6>^2)
+   + (y7 - t7)^2, targets [n][8] fp32 with unit quaternions in t3..6 */
+int pgs_mlp_grad(pgs_init* ctx, const pgs_mlp* w, const void* x_bf16, const float* targets,
+                 int64_t n, float* grad, double* loss_sum);
+/* Adam step t on the master parameters (b1 0.9, b2 0.999, eps 1e-8), BF16 copies refreshed,
+   grad zeroed */
+int pgs_mlp_adam(pgs_init* ctx, pgs_mlp* w, float* grad, float* m, float* v, float lr, int64_t t);
+
+/* Learned initial parameters from MLP outputs y [n][8] (device): log-scales y0..2, rotation
+   frame_q (x) normalise(y3..6), opacity logit y7 written into `out` (log_scales, quats,
+   opacity_logits; means and SH are left to the caller); points whose output is not finite keep
+   the paper's initializer `pca` and are counted in *fallbacks (device uint32, added to). */
+int pgs_apply_mlp(pgs_init* ctx, const float* y, const float* frame_q, const pgs_gaussians* pca,
+                  pgs_gaussians* out, uint32_t* fallbacks);
+/* Training targets t [n][8] from converged Gaussians: log-scales, conj(frame_q) (x) normalise(q),
+   opacity logit. */
+int pgs_make_targets(pgs_init* ctx, const float* frame_q, const pgs_gaussians* converged, float* t);
+
 /* Static description of an error code. */
 const char* pgs_strerror(int code);
 

@@ -101,6 +101,8 @@ def lib():
             L.oracle_init_loss.argtypes = [C.c_int64, P, P, P]
             L.oracle_init_loss.restype = C.c_double
             L.oracle_mlp_backward.argtypes = [C.c_int64] + [P] * 7 + [P, C.c_int] + [P] * 6
+            L.oracle_apply_mlp.argtypes = [C.c_int64, P, P, P, P, P]
+            L.oracle_make_targets.argtypes = [C.c_int64, P, P, P, P, P]
             L.oracle_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
                                       C.c_double, C.c_int64]
             _lib = L
@@ -356,3 +358,23 @@ def mlp_backward(x, weights, dy, mode: int = 1):
     lib().oracle_mlp_backward(x.shape[0], _ptr(x), *[_ptr(w) for w in W], _ptr(dy), mode,
                               *[_ptr(g) for g in grads])
     return grads
+
+
+def apply_mlp(y, frame_q) -> dict:
+    y = np.ascontiguousarray(y, np.float64)
+    fq = np.ascontiguousarray(frame_q, np.float64)
+    n = y.shape[0]
+    out = dict(log_scales=np.zeros((3, n)), quats=np.zeros((4, n)), opacity_logits=np.zeros(n))
+    lib().oracle_apply_mlp(n, _ptr(y), _ptr(fq), _ptr(out["log_scales"]), _ptr(out["quats"]),
+                           _ptr(out["opacity_logits"]))
+    return out
+
+
+def make_targets(frame_q, log_scales, quats, logits) -> np.ndarray:
+    fq = np.ascontiguousarray(frame_q, np.float64)
+    ls = np.ascontiguousarray(log_scales, np.float64)
+    q = np.ascontiguousarray(quats, np.float64)
+    lg = np.ascontiguousarray(logits, np.float64)
+    t = np.zeros((fq.shape[1], 8))
+    lib().oracle_make_targets(fq.shape[1], _ptr(fq), _ptr(ls), _ptr(q), _ptr(lg), _ptr(t))
+    return t

@@ -374,4 +374,44 @@ void oracle_mlp_backward(int64_t n, const float* x, const float* W1, const float
     }
 }
 
+static void qmul(const double a[4], const double b[4], double o[4]) {
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// Learned parameters from MLP outputs y [n][8]: log-scales y0..2, quaternion frame_q (x)
+// normalise(y3..6), logit y7 (log_scales [3][n], quats [4][n], logits [n]).
+void oracle_apply_mlp(int64_t n, const double* y, const double* frame_q, double* log_scales,
+                      double* quats, double* logits) {
+    for (int64_t i = 0; i < n; ++i) {
+        const double* a = y + i * 8;
+        const double qn = std::sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5] + a[6] * a[6]);
+        const double ql[4] = {a[3] / qn, a[4] / qn, a[5] / qn, a[6] / qn};
+        const double qf[4] = {frame_q[i], frame_q[n + i], frame_q[2 * n + i], frame_q[3 * n + i]};
+        double q[4];
+        qmul(qf, ql, q);
+        for (int k = 0; k < 3; ++k) log_scales[k * n + i] = a[k];
+        for (int k = 0; k < 4; ++k) quats[k * n + i] = q[k];
+        logits[i] = a[7];
+    }
+}
+
+// Targets [n][8]: log-scales, conj(frame_q) (x) normalise(q), logit of converged Gaussians.
+void oracle_make_targets(int64_t n, const double* frame_q, const double* log_scales,
+                         const double* quats, const double* logits, double* t) {
+    for (int64_t i = 0; i < n; ++i) {
+        double q[4] = {quats[i], quats[n + i], quats[2 * n + i], quats[3 * n + i]};
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int k = 0; k < 4; ++k) q[k] /= qn;
+        const double qc[4] = {frame_q[i], -frame_q[n + i], -frame_q[2 * n + i], -frame_q[3 * n + i]};
+        double ql[4];
+        qmul(qc, q, ql);
+        for (int k = 0; k < 3; ++k) t[i * 8 + k] = log_scales[k * n + i];
+        for (int k = 0; k < 4; ++k) t[i * 8 + 3 + k] = ql[k];
+        t[i * 8 + 7] = logits[i];
+    }
+}
+
 }  // extern "C"

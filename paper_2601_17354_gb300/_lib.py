@@ -40,7 +40,10 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_profile", "pgs_stage_times", "pgs_launch_count", "pgs_backward_step",
             "pgs_batch_create", "pgs_batch_destroy", "pgs_batch_step", "pgs_batch_capture",
             "pgs_batch_losses", "pgs_batch_status", "pgs_batch_launch_count", "pgs_set_variant",
-            "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants"]
+            "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants",
+            "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
+            "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
+            "pgs_apply_mlp", "pgs_make_targets"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -60,6 +63,10 @@ class PgsGaussians(C.Structure):
 class PgsRenderDesc(C.Structure):
     _fields_ = [("scene", C.c_int32), ("pad_", C.c_int32), ("cam", PgsCamera), ("image", C.c_void_p),
                 ("target", C.c_void_p), ("dL_dimage", C.c_void_p)]
+
+
+class PgsMlp(C.Structure):
+    _fields_ = [("master", C.c_void_p), ("W1", C.c_void_p), ("W2", C.c_void_p), ("W3", C.c_void_p)]
 
 
 class PgsConfig(C.Structure):
@@ -140,6 +147,28 @@ def lib():
             L.pgs_batch_time_variants.restype = I
             L.pgs_time_variants.argtypes = [P, P, P, C.c_int32, P]
             L.pgs_time_variants.restype = I
+            L.pgs_init_create.argtypes = [C.POINTER(P), P]
+            L.pgs_init_create.restype = I
+            L.pgs_init_destroy.argtypes = [P]
+            L.pgs_init_destroy.restype = None
+            L.pgs_knn.argtypes = [P, P, I64, C.c_int32, P]
+            L.pgs_knn.restype = I
+            L.pgs_features_init.argtypes = [P, P, I64, P, C.c_float, P, P, P, C.POINTER(PgsGaussians)]
+            L.pgs_features_init.restype = I
+            L.pgs_mlp_param_count.argtypes = []
+            L.pgs_mlp_param_count.restype = I
+            L.pgs_mlp_pack.argtypes = [P, C.POINTER(PgsMlp)]
+            L.pgs_mlp_pack.restype = I
+            L.pgs_mlp_forward.argtypes = [P, C.POINTER(PgsMlp), P, I64, P]
+            L.pgs_mlp_forward.restype = I
+            L.pgs_mlp_grad.argtypes = [P, C.POINTER(PgsMlp), P, P, I64, P, P]
+            L.pgs_mlp_grad.restype = I
+            L.pgs_mlp_adam.argtypes = [P, C.POINTER(PgsMlp), P, P, P, C.c_float, I64]
+            L.pgs_mlp_adam.restype = I
+            L.pgs_apply_mlp.argtypes = [P, P, P, C.POINTER(PgsGaussians), C.POINTER(PgsGaussians), P]
+            L.pgs_apply_mlp.restype = I
+            L.pgs_make_targets.argtypes = [P, P, C.POINTER(PgsGaussians), P]
+            L.pgs_make_targets.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p
             _lib = L

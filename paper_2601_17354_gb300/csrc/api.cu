@@ -792,3 +792,118 @@ int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms) {
 }
 
 }  // extern "C"
+
+// ================================================================================================
+// initializer
+// ================================================================================================
+struct pgs_init {
+    cudaStream_t stream = nullptr;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int* bbox = nullptr;
+};
+
+extern "C" {
+
+int pgs_init_create(pgs_init** out, void* cuda_stream) {
+    if (!out) return PGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    pgs_init* c = new (std::nothrow) pgs_init();
+    if (!c) return PGS_ERR_OOM;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = cudaMalloc(&c->bbox, 6 * sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_err(e);
+    }
+    *out = c;
+    return PGS_OK;
+}
+
+void pgs_init_destroy(pgs_init* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->bbox) cudaFree(c->bbox);
+    delete c;
+}
+
+int pgs_knn(pgs_init* c, const float* points, int64_t n, int32_t k, int32_t* nb) {
+    if (!c || !points || !nb || n < 0 || n >= (int64_t(1) << 31) || (k != 3 && k != 16 && k != 32))
+        return PGS_ERR_INVALID_ARG;
+    if (n == 0) return PGS_OK;
+    cudaStream_t s = c->stream;
+    launch_bbox(n, points, c->bbox, s);
+    int enc[6];
+    cudaError_t e = cudaMemcpyAsync(enc, c->bbox, sizeof(enc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    float bb[6];
+    decode_bbox(enc, bb);
+    // scratch for up to ~4 points per cell on average (the grid coarsens to fit)
+    const size_t want = knn_scratch_bytes(n, n / 2 + 1024);
+    if (c->scratch_bytes < want) {
+        e = cudaStreamSynchronize(s);
+        if (c->scratch) cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+        e = cudaMalloc(&c->scratch, want);
+        if (e != cudaSuccess) return cuda_err(e);
+        c->scratch_bytes = want;
+    }
+    launch_knn(n, points, k, nb, c->scratch, c->scratch_bytes, bb, s);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_features_init(pgs_init* c, const float* points, int64_t n, const int32_t* nb32, float r_normal,
+                      float* features, void* features_bf16, float* frame_q, pgs_gaussians* init) {
+    if (!c || !points || !nb32 || !features || !features_bf16 || !frame_q || !valid_gaussians(init) ||
+        init->n != n || n < 33)
+        return PGS_ERR_INVALID_ARG;
+    launch_features_init(n, points, nb32, r_normal, features, features_bf16, frame_q, *init, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_mlp_param_count(void) { return mlp_param_count(); }
+
+int pgs_mlp_pack(pgs_init* c, const pgs_mlp* w) {
+    if (!c || !w || !w->master || !w->W1 || !w->W2 || !w->W3) return PGS_ERR_INVALID_ARG;
+    launch_mlp_pack(w->master, w->W1, w->W2, w->W3, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_mlp_forward(pgs_init* c, const pgs_mlp* w, const void* x, int64_t n, float* out) {
+    if (!c || !w || !w->master || !x || !out || n < 0) return PGS_ERR_INVALID_ARG;
+    launch_mlp_forward(x, n, w->master, w->W1, w->W2, w->W3, out, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_mlp_grad(pgs_init* c, const pgs_mlp* w, const void* x, const float* targets, int64_t n,
+                 float* grad, double* loss_sum) {
+    if (!c || !w || !w->master || !x || !targets || !grad || !loss_sum || n < 0) return PGS_ERR_INVALID_ARG;
+    launch_mlp_train(x, targets, n, w->master, w->W1, w->W2, w->W3, grad, loss_sum, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_mlp_adam(pgs_init* c, pgs_mlp* w, float* grad, float* m, float* v, float lr, int64_t t) {
+    if (!c || !w || !w->master || !grad || !m || !v || t < 1) return PGS_ERR_INVALID_ARG;
+    launch_mlp_adam(w->master, grad, m, v, lr, 0.9f, 0.999f, 1e-8f, t, w->W1, w->W2, w->W3, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_apply_mlp(pgs_init* c, const float* y, const float* frame_q, const pgs_gaussians* pca,
+                  pgs_gaussians* out, uint32_t* fallbacks) {
+    if (!c || !y || !frame_q || !valid_gaussians(pca) || !valid_gaussians(out) || !fallbacks ||
+        pca->n != out->n)
+        return PGS_ERR_INVALID_ARG;
+    launch_apply_mlp(out->n, y, frame_q, *pca, *out, fallbacks, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+int pgs_make_targets(pgs_init* c, const float* frame_q, const pgs_gaussians* conv, float* t) {
+    if (!c || !frame_q || !valid_gaussians(conv) || !t) return PGS_ERR_INVALID_ARG;
+    launch_make_targets(conv->n, frame_q, *conv, t, c->stream);
+    return cuda_err(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -130,6 +130,26 @@ int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, in
 int launch_step_tick(int64_t* step, cudaStream_t s);
 int launch_loss_batch(const RenderDesc* renders, int R, int64_t values, double* losses, cudaStream_t s);
 
+// Initializer path (K13 kNN, K14 features + paper initializer, K15 MLP).
+size_t knn_scratch_bytes(int64_t n, int64_t cells);
+int launch_bbox(int64_t n, const float* P, int* bbox_dev, cudaStream_t s);
+void decode_bbox(const int* enc, float* out);
+int launch_knn(int64_t n, const float* P, int k, int32_t* nb, void* scratch, size_t scratch_bytes,
+               const float* host_bbox, cudaStream_t s);
+int launch_features_init(int64_t n, const float* P, const int32_t* nb, float r_normal, float* feats,
+                         void* feats_bf16, float* frame_q, pgs_gaussians& init, cudaStream_t s);
+int launch_apply_mlp(int64_t n, const float* y, const float* frame_q, const pgs_gaussians& pca,
+                     pgs_gaussians& out, uint32_t* fallbacks, cudaStream_t s);
+int launch_make_targets(int64_t n, const float* frame_q, const pgs_gaussians& conv, float* t, cudaStream_t s);
+int mlp_param_count();
+int launch_mlp_forward(const void* x, int64_t n, const float* master, const void* W1, const void* W2,
+                       const void* W3, float* out, cudaStream_t s);
+int launch_mlp_train(const void* x, const float* target, int64_t n, const float* master, const void* W1,
+                     const void* W2, const void* W3, float* grad, double* loss_sum, cudaStream_t s);
+int launch_mlp_adam(float* master, float* grad, float* m, float* v, float lr, float b1, float b2,
+                    float eps, int64_t t, void* W1, void* W2, void* W3, cudaStream_t s);
+int launch_mlp_pack(const float* master, void* W1, void* W2, void* W3, cudaStream_t s);
+
 // K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
 // emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
 int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,

@@ -138,3 +138,26 @@ def test_mlp_bf16_mode_is_close_to_exact():
     gb = oracle.mlp_backward(x, W, dy, mode=0)
     for u, v in zip(ga, gb):
         assert np.linalg.norm(u - v) / np.linalg.norm(v) < 3e-2
+
+
+def test_frame_composition_matches_scipy_and_round_trips():
+    """Learned rotation = eigenframe (x) predicted local rotation (rotation composition, checked
+    with scipy's Rotation), and targets built from a converged rotation map back to it."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    rng = np.random.default_rng(6)
+    n = 40
+    fq = rng.normal(size=(4, n))
+    fq /= np.linalg.norm(fq, axis=0)
+    y = rng.normal(size=(n, 8))
+    out = oracle.apply_mlp(y, fq)
+    for i in range(n):
+        Rf = Rot.from_quat([fq[1, i], fq[2, i], fq[3, i], fq[0, i]])
+        Rl = Rot.from_quat([y[i, 4], y[i, 5], y[i, 6], y[i, 3]])
+        want = (Rf * Rl).as_matrix()
+        q = out["quats"][:, i]
+        got = Rot.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        assert np.allclose(got, want, atol=1e-12)
+    t = oracle.make_targets(fq, out["log_scales"], out["quats"], out["opacity_logits"])
+    back = oracle.apply_mlp(t, fq)
+    assert np.allclose(np.abs(np.sum(back["quats"] * out["quats"], axis=0)), 1.0, atol=1e-12)
+    assert np.allclose(back["log_scales"], out["log_scales"]) and np.allclose(back["opacity_logits"], out["opacity_logits"])
