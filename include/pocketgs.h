@@ -227,6 +227,11 @@ void pgs_batch_destroy(pgs_batch* b);
    the captured graph if there is one, else enqueues the kernels. */
 int pgs_batch_step(pgs_batch* b);
 /* Capture one step into a CUDA graph (nothing runs during capture); later steps replay it. */
+/* Point every render at a new view before the next step (cameras[n_renders], targets[n_renders]
+   device pointers): each render keeps its scene and image size (width and height must match);
+   the render table is updated in device memory on the batch's stream, so a captured graph picks
+   the new views up at its next replay. */
+int pgs_batch_set_views(pgs_batch* b, const pgs_camera* cameras, const float* const* targets);
 int pgs_batch_capture(pgs_batch* b);
 /* Per render: losses[2 r] = mean |image - target| and losses[2 r + 1] = sum of squared errors of
    the last step (host array of 2 n_renders doubles; synchronises). */

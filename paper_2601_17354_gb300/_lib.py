@@ -43,7 +43,7 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants",
             "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
-            "pgs_apply_mlp", "pgs_make_targets"]
+            "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -133,6 +133,8 @@ def lib():
             for name in ("pgs_batch_step", "pgs_batch_capture"):
                 getattr(L, name).argtypes = [P]
                 getattr(L, name).restype = I
+            L.pgs_batch_set_views.argtypes = [P, C.POINTER(PgsCamera), C.POINTER(C.c_void_p)]
+            L.pgs_batch_set_views.restype = I
             L.pgs_batch_losses.argtypes = [P, P]
             L.pgs_batch_losses.restype = I
             L.pgs_batch_status.argtypes = [P, C.POINTER(I64)]

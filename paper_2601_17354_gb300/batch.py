@@ -79,6 +79,16 @@ class BatchTrainer:
         L.check(self._lib.pgs_batch_capture(self._b), "pgs_batch_capture")
         self.captured = True
 
+    def set_views(self, views: list):
+        """New (camera, target) per render slot, same sizes; applies from the next step."""
+        if len(views) != len(self.views):
+            raise ValueError("one (camera, target) per render")
+        cams = (L.PgsCamera * len(views))(*[camera_struct(c) for c, _ in views])
+        self._keep = [t.contiguous() for _, t in views]
+        ptrs = (C.c_void_p * len(views))(*[t.data_ptr() for t in self._keep])
+        self._enter()
+        L.check(self._lib.pgs_batch_set_views(self._b, cams, ptrs), "pgs_batch_set_views")
+
     def losses(self) -> np.ndarray:
         out = np.zeros((len(self.views), 2))
         L.check(self._lib.pgs_batch_losses(self._b, out.ctypes.data_as(C.c_void_p)), "pgs_batch_losses")

@@ -690,6 +690,23 @@ int pgs_batch_step(pgs_batch* b) {
     return cuda_err(cudaGetLastError());
 }
 
+int pgs_batch_set_views(pgs_batch* b, const pgs_camera* cameras, const float* const* targets) {
+    if (!b || !cameras || !targets) return PGS_ERR_INVALID_ARG;
+    for (int r = 0; r < b->R; ++r) {
+        const RenderDesc& rd = b->renders[r];
+        if (!valid_camera(&cameras[r]) || cameras[r].width != rd.cam.width ||
+            cameras[r].height != rd.cam.height || !targets[r])
+            return PGS_ERR_INVALID_ARG;
+    }
+    for (int r = 0; r < b->R; ++r) {
+        b->renders[r].cam = cameras[r];
+        b->renders[r].target = targets[r];
+    }
+    const cudaError_t e = cudaMemcpyAsync(b->d_renders, b->renders.data(), sizeof(RenderDesc) * b->R,
+                                          cudaMemcpyHostToDevice, b->stream);
+    return cuda_err(e);
+}
+
 int pgs_batch_capture(pgs_batch* b) {
     if (!b) return PGS_ERR_INVALID_ARG;
     drop_graph(b);

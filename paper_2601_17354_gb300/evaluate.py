@@ -1,0 +1,257 @@
+"""Training and evaluation drivers on synthetic surface scenes: the plain method (paper
+initializer + one view per iteration), the learned initializer fitted on converged Gaussians of
+plain runs, and held-out-view PSNR at fixed iteration budgets."""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import synthetic as S
+from .initializer import Initializer, LearnedInit, PointInit
+from .rasterizer import GaussianBuffer, Rasterizer, Trainer
+
+
+@dataclass
+class SceneData:
+    scene: S.SurfaceScene
+    points: torch.Tensor              # [3][n] trainable start positions
+    targets: dict                     # view index -> [3][H][W] ground-truth render
+    pi: PointInit | None = None
+
+
+def make_scene(seed: int, n: int, width: int, height: int, focal: float, n_cameras: int = 64,
+               sh_degree: int = 3) -> SceneData:
+    sc = S.surface_scene(seed, n, sh_degree, width, height, focal, n_cameras=n_cameras)
+    rast = Rasterizer()
+    gt = GaussianBuffer.from_arrays(sc.gt)
+    targets = {v: rast.render(gt, sc.cameras[v]).clone() for v in range(len(sc.cameras))}
+    torch.cuda.synchronize()
+    return SceneData(sc, torch.from_numpy(np.ascontiguousarray(sc.init.means)).cuda(), targets)
+
+
+def with_colour(params: GaussianBuffer) -> GaussianBuffer:
+    """Initial colour: grey (all SH coefficients 0)."""
+    params.sh.zero_()
+    return params
+
+
+def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
+    mse = torch.mean((img.clamp(0, 1) - ref.clamp(0, 1)) ** 2).item()
+    return float("inf") if mse == 0 else -10.0 * math.log10(mse)
+
+
+def eval_psnr(rast: Rasterizer, params: GaussianBuffer, sd: SceneData) -> float:
+    vals = [psnr(rast.render(params, sd.scene.cameras[v]), sd.targets[v]) for v in sd.scene.test_views()]
+    return float(np.mean(vals))
+
+
+def train_plain(params: GaussianBuffer, sd: SceneData, iters: int, checkpoints=(), seed: int = 0,
+                rast: Rasterizer | None = None):
+    """Plain training: Adam, L1, one view per iteration from a seeded permutation of the training
+    views, reshuffled every epoch.  Returns ({iteration: held-out PSNR}, GPU seconds of training)."""
+    rast = rast or Rasterizer()
+    tr = Trainer(params, rast)
+    views = sd.scene.train_views()
+    rng = np.random.default_rng(seed)
+    order = []
+    out = {}
+    gpu_ms = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eval_rast = Rasterizer()
+    e0.record()
+    for it in range(1, iters + 1):
+        if not order:
+            order = list(rng.permutation(views))
+        v = order.pop()
+        tr.step(sd.scene.cameras[v], sd.targets[v])
+        if it in checkpoints:
+            e1.record()
+            torch.cuda.synchronize()
+            gpu_ms += e0.elapsed_time(e1)
+            out[it] = eval_psnr(eval_rast, params, sd)
+            e0.record()
+    e1.record()
+    torch.cuda.synchronize()
+    gpu_ms += e0.elapsed_time(e1)
+    code, _ = rast.status()
+    if code != 0:
+        raise RuntimeError(f"training status {code}")
+    return out, gpu_ms / 1000.0
+
+
+@dataclass
+class InitComparison:
+    budgets: tuple
+    paper: list = field(default_factory=list)    # per eval scene {budget: PSNR}
+    learned: list = field(default_factory=list)
+    fit_history: list = field(default_factory=list)
+    fallbacks: int = 0
+    seconds: dict = field(default_factory=dict)
+
+    def mean(self, which: str) -> dict:
+        rows = getattr(self, which)
+        return {b: float(np.mean([r[b] for r in rows])) for b in self.budgets}
+
+
+def compare_initializers(train_seeds, eval_seeds, n: int, width: int, height: int, focal: float,
+                         budgets=(100, 250, 500), converge_iters: int = 500, fit_steps: int = 600,
+                         n_cameras: int = 64, sh_degree: int = 3) -> InitComparison:
+    """Fit the learned initializer on converged Gaussians of plain runs on the training scenes,
+    then compare it with the paper's initializer on the held-out views of the evaluation scenes."""
+    t0 = time.time()
+    init = Initializer()
+    feats, targs = [], []
+    for seed in train_seeds:
+        sd = make_scene(seed, n, width, height, focal, n_cameras, sh_degree)
+        pi = init.paper_init(sd.points, sh_degree)
+        params = with_colour(pi.paper.clone())
+        train_plain(params, sd, converge_iters, seed=seed)
+        feats.append(pi.features_bf16)
+        targs.append(init.make_targets(pi, params))
+    t1 = time.time()
+    li = LearnedInit(init, seed=1)
+    li.fit(feats, targs, steps=fit_steps)
+    res = InitComparison(tuple(budgets), fit_history=list(li.history))
+    t2 = time.time()
+    for seed in eval_seeds:
+        sd = make_scene(seed, n, width, height, focal, n_cameras, sh_degree)
+        pi = init.paper_init(sd.points, sh_degree)
+        paper = with_colour(pi.paper.clone())
+        p, _ = train_plain(paper, sd, max(budgets), checkpoints=budgets, seed=seed)
+        learned, fb = li.infer(pi)
+        learned = with_colour(learned)
+        q, _ = train_plain(learned, sd, max(budgets), checkpoints=budgets, seed=seed)
+        res.paper.append(p)
+        res.learned.append(q)
+        res.fallbacks += fb
+    res.seconds = {"converge_runs": t1 - t0, "fit": t2 - t1, "eval": time.time() - t2}
+    return res
+
+
+def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_iters: int = 500,
+                   views_per_step: int = 4, learned: LearnedInit | None = None, check_every: int = 10,
+                   max_steps: int = 500, n_cameras: int = 64, sh_degree: int = 3) -> dict:
+    """GPU seconds for the plain form (paper initializer, one view per iteration, each scene on its
+    own for plain_iters iterations) against the batched form (every scene in one captured batch,
+    views_per_step views of each scene per step, learned initializer when given) to reach, for
+    every scene, the plain form's held-out PSNR.  Evaluation renders are not counted."""
+    from .batch import BatchTrainer
+    init = learned.init if learned is not None else Initializer()
+    scenes = [make_scene(s, n, width, height, focal, n_cameras, sh_degree) for s in seeds]
+    plain_psnr, plain_s = [], 0.0
+    for k, sd in enumerate(scenes):
+        sd.pi = init.paper_init(sd.points, sh_degree)
+        params = with_colour(sd.pi.paper.clone())
+        out, secs = train_plain(params, sd, plain_iters, checkpoints=(plain_iters,), seed=seeds[k])
+        plain_psnr.append(out[plain_iters])
+        plain_s += secs
+    starts = []
+    fallbacks = 0
+    for sd in scenes:
+        if learned is not None:
+            p, fb = learned.infer(sd.pi)
+            fallbacks += fb
+        else:
+            p = sd.pi.paper.clone()
+        starts.append(with_colour(p))
+    rng = np.random.default_rng(0)
+    orders = [[] for _ in scenes]
+
+    def next_views():
+        out = []
+        for k, sd in enumerate(scenes):
+            for _ in range(views_per_step):
+                if not orders[k]:
+                    orders[k] = list(rng.permutation(sd.scene.train_views()))
+                v = orders[k].pop()
+                out.append((k, sd.scene.cameras[v], sd.targets[v]))
+        return out
+
+    first = next_views()
+    bt = BatchTrainer(starts, first)
+    bt.capture()
+    eval_rast = Rasterizer()
+    reached = [None] * len(scenes)
+    batched_s = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step = 0
+    while step < max_steps and any(r is None for r in reached):
+        e0.record(bt.stream)
+        for _ in range(check_every):
+            if step > 0:
+                bt.set_views([(c, t) for _, c, t in next_views()])
+            bt.step()
+            step += 1
+        e1.record(bt.stream)
+        torch.cuda.synchronize()
+        batched_s += e0.elapsed_time(e1) / 1000.0
+        for k, sd in enumerate(scenes):
+            if reached[k] is None and eval_psnr(eval_rast, starts[k], sd) >= plain_psnr[k]:
+                reached[k] = (step, batched_s)
+    code, _ = bt.status()
+    if code != 0:
+        raise RuntimeError(f"batched status {code}")
+    done = all(r is not None for r in reached)
+    return {"plain_psnr": plain_psnr, "plain_gpu_s": plain_s, "batched_gpu_s": batched_s,
+            "steps": step, "reached": reached, "all_reached": done, "fallbacks": fallbacks,
+            "ratio": batched_s / plain_s if done else None}
+
+
+def main(argv=None):
+    """Learned-initializer experiment at the 32-scene x 200k-point scale (1280x720, fx = 1000):
+    fit on 28 scenes' converged Gaussians, compare with the paper's initializer on 4 held-out
+    scenes at 100/250/500 iterations, then time the batched learned-init form to the plain form's
+    500-iteration PSNR.  Prints one JSON line."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scenes", type=int, default=32)
+    ap.add_argument("--held-out", type=int, default=4)
+    ap.add_argument("--points", type=int, default=200_000)
+    ap.add_argument("--width", type=int, default=1280)
+    ap.add_argument("--height", type=int, default=720)
+    ap.add_argument("--focal", type=float, default=1000.0)
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    train = list(range(1000, 1000 + args.scenes - args.held_out))
+    held = list(range(2000, 2000 + args.held_out))
+    init = Initializer()
+    feats, targs = [], []
+    for seed in train:
+        sd = make_scene(seed, args.points, args.width, args.height, args.focal)
+        pi = init.paper_init(sd.points, 3)
+        p = with_colour(pi.paper.clone())
+        train_plain(p, sd, 500, seed=seed)
+        feats.append(pi.features_bf16)
+        targs.append(init.make_targets(pi, p))
+        del sd
+    li = LearnedInit(init, seed=1)
+    li.fit(feats, targs, steps=1000)
+    paper_rows, learned_rows = [], []
+    for seed in held:
+        sd = make_scene(seed, args.points, args.width, args.height, args.focal)
+        pi = init.paper_init(sd.points, 3)
+        a, _ = train_plain(with_colour(pi.paper.clone()), sd, 500, checkpoints=(100, 250, 500), seed=seed)
+        lp, _ = li.infer(pi)
+        b, _ = train_plain(with_colour(lp), sd, 500, checkpoints=(100, 250, 500), seed=seed)
+        paper_rows.append(a)
+        learned_rows.append(b)
+    mean = lambda rows: {k: float(np.mean([r[k] for r in rows])) for k in (100, 250, 500)}
+    tt = time_to_target(held, args.points, args.width, args.height, args.focal, views_per_step=1,
+                        learned=li)
+    print(json.dumps({"experiment": "learned initializer", "train_scenes": len(train),
+                      "held_out_scenes": len(held), "points": args.points,
+                      "resolution": f"{args.width}x{args.height}",
+                      "psnr_paper_init": mean(paper_rows), "psnr_learned_init": mean(learned_rows),
+                      "fit_loss": li.history[-1][1],
+                      "time_to_plain_psnr": {k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps",
+                                                                "all_reached", "ratio")},
+                      "wall_s": time.time() - t0}))
+
+
+if __name__ == "__main__":
+    main()
