@@ -223,16 +223,25 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
                      int32_t n_renders, const pgs_render_desc* renders, int64_t pair_capacity,
                      void* cuda_stream);
 void pgs_batch_destroy(pgs_batch* b);
-/* One training step of every render (render, L1, backward, Adam with t = previous t + 1): replays
-   the captured graph if there is one, else enqueues the kernels. */
+/* One training step of every render (render, L1, backward, Adam with t = completed steps + 1):
+   replays the captured graph if there is one, else enqueues the kernels.  A step whose pairs
+   overflow the capacity changes no parameter, moment or step count (its Adam launch and its step
+   count read the device's overflow flag), and neither do the steps after it until
+   pgs_batch_status has reported PGS_ERR_CAPACITY (with the pairs needed) and cleared the flag;
+   pgs_batch_reserve then grows the capacity. */
 int pgs_batch_step(pgs_batch* b);
 /* Capture one step into a CUDA graph (nothing runs during capture); later steps replay it. */
+int pgs_batch_capture(pgs_batch* b);
 /* Point every render at a new view before the next step (cameras[n_renders], targets[n_renders]
    device pointers): each render keeps its scene and image size (width and height must match);
    the render table is updated in device memory on the batch's stream, so a captured graph picks
    the new views up at its next replay. */
 int pgs_batch_set_views(pgs_batch* b, const pgs_camera* cameras, const float* const* targets);
-int pgs_batch_capture(pgs_batch* b);
+/* Grow the pair capacity to at least pair_capacity (synchronises; smaller values do nothing).  A
+   captured graph is captured again over the new buffers. */
+int pgs_batch_reserve(pgs_batch* b, int64_t pair_capacity);
+/* Completed training steps: the device step counter (synchronises). */
+int pgs_batch_steps(pgs_batch* b, int64_t* steps);
 /* Per render: losses[2 r] = mean |image - target| and losses[2 r + 1] = sum of squared errors of
    the last step (host array of 2 n_renders doubles; synchronises). */
 int pgs_batch_losses(pgs_batch* b, double* losses);

@@ -43,7 +43,8 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants",
             "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
-            "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views"]
+            "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views", "pgs_batch_reserve",
+            "pgs_batch_steps"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -135,6 +136,10 @@ def lib():
                 getattr(L, name).restype = I
             L.pgs_batch_set_views.argtypes = [P, C.POINTER(PgsCamera), C.POINTER(C.c_void_p)]
             L.pgs_batch_set_views.restype = I
+            L.pgs_batch_reserve.argtypes = [P, C.c_int64]
+            L.pgs_batch_reserve.restype = I
+            L.pgs_batch_steps.argtypes = [P, C.POINTER(C.c_int64)]
+            L.pgs_batch_steps.restype = I
             L.pgs_batch_losses.argtypes = [P, P]
             L.pgs_batch_losses.restype = I
             L.pgs_batch_status.argtypes = [P, C.POINTER(I64)]

@@ -89,6 +89,27 @@ class BatchTrainer:
         self._enter()
         L.check(self._lib.pgs_batch_set_views(self._b, cams, ptrs), "pgs_batch_set_views")
 
+    def reserve(self, pair_capacity: int):
+        """Grow the pair capacity (a captured graph is captured again)."""
+        self._enter()
+        L.check(self._lib.pgs_batch_reserve(self._b, int(pair_capacity)), "pgs_batch_reserve")
+
+    def steps(self) -> int:
+        """Completed steps (steps after a pair overflow do not count)."""
+        t = C.c_int64()
+        L.check(self._lib.pgs_batch_steps(self._b, C.byref(t)), "pgs_batch_steps")
+        return t.value
+
+    def check(self) -> int:
+        """Read the status; after a pair overflow grow the capacity to the pairs needed + 25 %.
+        Returns the completed steps."""
+        code, pairs = self.status()
+        if code == L.PGS_ERR_CAPACITY:
+            self.reserve(pairs + pairs // 4 + 4096)
+        elif code != 0:
+            L.check(code, "batched step")
+        return self.steps()
+
     def losses(self) -> np.ndarray:
         out = np.zeros((len(self.views), 2))
         L.check(self._lib.pgs_batch_losses(self._b, out.ctypes.data_as(C.c_void_p)), "pgs_batch_losses")

@@ -526,8 +526,7 @@ int64_t enqueue_render(pgs_batch* b) {
 
 int64_t enqueue_step(pgs_batch* b) {
     cudaStream_t s = b->stream;
-    int64_t k = launch_step_tick(b->d_step, s);
-    k += enqueue_render(b);
+    int64_t k = enqueue_render(b);
     cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
     k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work,
                                 false, s, b->variant);
@@ -538,6 +537,7 @@ int64_t enqueue_step(pgs_batch* b) {
                                 true, s, b->variant);
     k += launch_bwd_adam_batch(b->d_renders, b->d_scenes, b->S, b->deg, b->gauss, b->items, b->sc,
                                b->cfg.lr, b->cfg.adam_b1, b->cfg.adam_b2, b->cfg.adam_eps, b->d_step, s);
+    k += launch_step_tick(b->d_step, b->sc.status, s);
     return k;
 }
 
@@ -730,6 +730,35 @@ int pgs_batch_capture(pgs_batch* b) {
         return cuda_err(e);
     }
     return PGS_OK;
+}
+
+int pgs_batch_reserve(pgs_batch* b, int64_t pair_capacity) {
+    if (!b || pair_capacity < 0) return PGS_ERR_INVALID_ARG;
+    if (pair_capacity <= b->cap_pairs) return PGS_OK;
+    const bool recapture = b->exec != nullptr;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    drop_graph(b);  // the graph holds the old pair buffers
+    Scratch tmp;
+    const size_t bytes = carve_p(tmp, nullptr, pair_capacity);
+    if (b->arena_p) cudaFree(b->arena_p);
+    b->arena_p = nullptr;
+    b->cap_pairs = 0;
+    e = cudaMalloc(&b->arena_p, bytes);
+    if (e != cudaSuccess) {
+        b->arena_p = nullptr;
+        return cuda_err(e);
+    }
+    carve_p(b->sc, static_cast<char*>(b->arena_p), pair_capacity);
+    b->cap_pairs = pair_capacity;
+    return recapture ? pgs_batch_capture(b) : PGS_OK;
+}
+
+int pgs_batch_steps(pgs_batch* b, int64_t* steps) {
+    if (!b || !steps) return PGS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(steps, b->d_step, sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return cuda_err(e);
 }
 
 int pgs_batch_losses(pgs_batch* b, double* losses) {

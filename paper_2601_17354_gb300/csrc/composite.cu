@@ -406,25 +406,28 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
 }
 
-// Batched compositing: persistent CTAs take global tiles, heaviest first, from a device work
-// counter (an atomic ticket; no CTA ever waits for another) until every tile of every render
-// is done.
+// Batched compositing: persistent CTAs take global tiles, heaviest first, until every tile of
+// every render is done.  A CTA's first job is its own index, so the first (heaviest) round is
+// spread over the SMs in launch order as a one-tile-per-CTA grid would be; later jobs come from a
+// device work counter (an atomic ticket offset by the grid size; no CTA ever waits for another).
+// Taking the first round from the ticket too let the heaviest tiles gather on a few SMs (the
+// CTAs of one SM reach the ticket together) and left the other SMs idle at the end.
 template <int kPix, int kDepth, bool kBackward>
 __global__ void __launch_bounds__(kTilePixels / kPix)
 k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_tiles, int64_t n,
                   const uint32_t* __restrict__ vals, Scratch sc, uint32_t* __restrict__ work) {
     __shared__ typename std::conditional<kBackward, BwdSmem<kDepth>, FwdSmem<kDepth>>::type S;
     __shared__ int64_t s_job;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_job = (int64_t)atomicAdd(work, 1u);
-        __syncthreads();
-        const int64_t job = s_job;
-        if (job >= total_tiles) break;
+    int64_t job = blockIdx.x;
+    while (job < total_tiles) {
         const int64_t gt = sc.tile_order[job];
         const TileJob J = batch_job(renders[render_of_tile(renders, R, gt)], gt, sc);
         if constexpr (kBackward) bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
         else fwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+        __syncthreads();
+        if (threadIdx.x == 0) s_job = (int64_t)atomicAdd(work, 1u) + gridDim.x;
+        __syncthreads();
+        job = s_job;
     }
 }
 
@@ -488,8 +491,10 @@ static int launch_batch_variant(const RenderDesc* renders, int R, int64_t total_
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_batch<P, D, B>, kTilePixels / P, 0);
         return sms * (per_sm > 0 ? per_sm : 1);
     }();
-    k_composite_batch<P, D, B><<<grid, kTilePixels / P, 0, s>>>(renders, R, total_tiles, n,
-                                                               sc.vals[buf], sc, work);
+    const int64_t g = grid < total_tiles ? grid : total_tiles;  // every CTA has a first job
+    if (g < 1) return 0;
+    k_composite_batch<P, D, B><<<(unsigned)g, kTilePixels / P, 0, s>>>(renders, R, total_tiles, n,
+                                                                      sc.vals[buf], sc, work);
     return 1;
 }
 

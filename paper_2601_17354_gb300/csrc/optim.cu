@@ -166,54 +166,59 @@ bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u
 
 // Batched L1: one pass over every render's image values (renders' values are numbered
 // consecutively); gradient sign / (3 H W) of the value's render; per-render sums of |d| and d^2
-// accumulated in double (losses[2 r], losses[2 r + 1], zeroed by the caller).  Each CTA covers
-// a contiguous chunk, so a thread's values change render rarely and it flushes per change.
+// (losses[2 r], losses[2 r + 1], zeroed by the caller).  Each CTA covers a contiguous chunk and
+// walks the render segments inside it (usually one, two at a render boundary): per segment the
+// threads' float partials are reduced across the CTA and added with one double atomic per sum,
+// so a render receives about 3 H W / 4096 atomics.
 constexpr int kLossChunk = kThreads * 16;
+
+__device__ __forceinline__ double block_sum(double x, double* s_red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();  // s_red is free again
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
+    return t;
+}
 
 __global__ void __launch_bounds__(kThreads)
 k_loss_batch(const RenderDesc* __restrict__ renders, int R, int64_t values, double* __restrict__ losses) {
+    __shared__ double s_red[kThreads / 32];
     const int64_t begin = (int64_t)blockIdx.x * kLossChunk;
     const int64_t end = begin + kLossChunk < values ? begin + kLossChunk : values;
-    int r = -1;
-    double l1 = 0.0, l2 = 0.0;
-    int64_t rend = -1;
-    const float* img = nullptr;
-    const float* tgt = nullptr;
-    float* grad = nullptr;
-    float inv_n = 0.f;
-    int64_t vbase = 0;
-    for (int64_t e = begin + threadIdx.x; e < end; e += kThreads) {
-        if (e >= rend) {
-            if (r >= 0) {
-                atomicAdd(&losses[2 * r], l1);
-                atomicAdd(&losses[2 * r + 1], l2);
-            }
-            int lo = 0, hi = R - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (renders[mid].value_base <= e) lo = mid;
-                else hi = mid - 1;
-            }
-            r = lo;
-            const RenderDesc& rd = renders[r];
-            const int64_t nv = 3ll * rd.cam.width * rd.cam.height;
-            vbase = rd.value_base;
-            rend = vbase + nv;
-            img = rd.image;
-            tgt = rd.target;
-            grad = rd.dL;
-            inv_n = 1.0f / (float)nv;
-            l1 = l2 = 0.0;
-        }
-        const int64_t q = e - vbase;
-        const float d = img[q] - tgt[q];
-        l1 += fabsf(d);
-        l2 += (double)d * d;
-        grad[q] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+    int lo = 0, hi = R - 1;  // last render whose values start at or before `begin`
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (renders[mid].value_base <= begin) lo = mid;
+        else hi = mid - 1;
     }
-    if (r >= 0) {
-        atomicAdd(&losses[2 * r], l1);
-        atomicAdd(&losses[2 * r + 1], l2);
+    for (int r = lo; r < R; ++r) {
+        const RenderDesc& rd = renders[r];
+        const int64_t vbase = rd.value_base;
+        if (vbase >= end) break;
+        const int64_t nv = 3ll * rd.cam.width * rd.cam.height;
+        const int64_t a = begin > vbase ? begin - vbase : 0;
+        const int64_t b = end - vbase < nv ? end - vbase : nv;
+        if (a >= b) continue;
+        const float* __restrict__ img = rd.image;
+        const float* __restrict__ tgt = rd.target;
+        float* __restrict__ grad = rd.dL;
+        const float inv_n = 1.0f / (float)nv;
+        float l1 = 0.f, l2 = 0.f;
+        for (int64_t q = a + threadIdx.x; q < b; q += kThreads) {
+            const float d = img[q] - tgt[q];
+            l1 += fabsf(d);
+            l2 = fmaf(d, d, l2);
+            grad[q] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+        }
+        const double t1 = block_sum((double)l1, s_red);
+        const double t2 = block_sum((double)l2, s_red);
+        if (threadIdx.x == 0) {
+            atomicAdd(&losses[2 * r], t1);
+            atomicAdd(&losses[2 * r + 1], t2);
+        }
     }
 }
 

@@ -127,7 +127,7 @@ int launch_project_fwd_batch(const RenderDesc* renders, int R, const SceneDesc* 
 int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, int S, int deg,
                           int64_t gauss_total, int64_t items, const Scratch& sc, const float lr[6],
                           float b1, float b2, float eps, const int64_t* step, cudaStream_t s);
-int launch_step_tick(int64_t* step, cudaStream_t s);
+int launch_step_tick(int64_t* step, const int32_t* status, cudaStream_t s);
 int launch_loss_batch(const RenderDesc* renders, int R, int64_t values, double* losses, cudaStream_t s);
 
 // Initializer path (K13 kNN, K14 features + paper initializer, K15 MLP).

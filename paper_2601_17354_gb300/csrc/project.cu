@@ -592,7 +592,11 @@ struct AdamDev {
     float b1, b2, omb1, omb2, eps;
 };
 
-__global__ void k_step_tick(int64_t* step) { *step += 1; }
+// Counts a completed step; a step whose pairs overflowed the capacity did no Adam update and is
+// not counted.
+__global__ void k_step_tick(int64_t* step, const int32_t* status) {
+    if ((*status & kStatusCapacity) == 0) *step += 1;
+}
 
 __device__ __forceinline__ int scene_of(const SceneDesc* __restrict__ scenes, int S, int64_t k) {
     int lo = 0, hi = S - 1;
@@ -606,7 +610,8 @@ __device__ __forceinline__ int scene_of(const SceneDesc* __restrict__ scenes, in
 
 // Batched backward + Adam: one thread per Gaussian of every scene.  The Gaussian's parameter
 // gradient is summed over the scene's renders (views) in shared memory, row by row, and then
-// consumed by the Adam update of the scene's parameters.
+// consumed by the Adam update (step t = completed steps + 1) of the scene's parameters.  When the
+// step's pairs overflowed the capacity (the renders are incomplete) nothing is written.
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock, 2)
 k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __restrict__ scenes, int S,
@@ -615,10 +620,12 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
     constexpr int ROWS = 11 + 3 * K;
     extern __shared__ float s_acc[];  // [ROWS][kProjBlock]
     __shared__ float s_bc[2];
+    __shared__ int s_skip;
     if (threadIdx.x == 0) {
-        const double t = (double)*step;
+        const double t = (double)(*step + 1);
         s_bc[0] = (float)(1.0 - pow((double)a.b1, t));
         s_bc[1] = (float)(1.0 - pow((double)a.b2, t));
+        s_skip = (*sc.status & kStatusCapacity) != 0;
     }
     const int64_t k = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     float* acc = s_acc + threadIdx.x;
@@ -626,7 +633,7 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
     for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] = 0.f;
     __syncthreads();
     const float bc1 = s_bc[0], bc2 = s_bc[1];
-    if (k >= gauss_total) return;
+    if (k >= gauss_total || s_skip) return;
     const SceneDesc& sd = scenes[scene_of(scenes, S, k)];
     const int64_t i = k - sd.gauss_base;
     const int64_t n = sd.params.n;
@@ -736,8 +743,8 @@ int launch_project_fwd_batch(const RenderDesc* renders, int R, const SceneDesc* 
     return 1;
 }
 
-int launch_step_tick(int64_t* step, cudaStream_t s) {
-    k_step_tick<<<1, 1, 0, s>>>(step);
+int launch_step_tick(int64_t* step, const int32_t* status, cudaStream_t s) {
+    k_step_tick<<<1, 1, 0, s>>>(step, status);
     return 1;
 }
 

@@ -11,8 +11,9 @@ import numpy as np
 import torch
 
 from . import synthetic as S
+from .autotune import tune_batch, tune_rasterizer
 from .initializer import Initializer, LearnedInit, PointInit
-from .rasterizer import GaussianBuffer, Rasterizer, Trainer
+from .rasterizer import DEFAULT_LR, AdamConfig, GaussianBuffer, Rasterizer, Trainer
 
 
 @dataclass
@@ -49,11 +50,36 @@ def eval_psnr(rast: Rasterizer, params: GaussianBuffer, sd: SceneData) -> float:
     return float(np.mean(vals))
 
 
+def pair_capacity(params: GaussianBuffer, sd: SceneData, views: int = 8, headroom: float = 2.0) -> int:
+    """A fixed pair capacity for training: the most pairs over the first training views of the
+    starting parameters, times the headroom (the pairs grow as the Gaussians train)."""
+    probe = Rasterizer()
+    most = 0
+    for v in sd.scene.train_views()[:views]:
+        probe.render(params, sd.scene.cameras[v])
+        most = max(most, probe.status()[1])
+    probe.close()
+    return int(most * headroom) + 4096
+
+
+def tuned_rasterizer(params: GaussianBuffer, sd: SceneData) -> Rasterizer:
+    """A rasterizer for training `params` on `sd`: fixed pair capacity, compositing variant chosen
+    by the autotuner on the first training view."""
+    rast = Rasterizer(pair_capacity=pair_capacity(params, sd))
+    v = sd.scene.train_views()[0]
+    img = rast.render(params, sd.scene.cameras[v])
+    dl, _ = rast.loss_l1(img, sd.targets[v])
+    tune_rasterizer(rast, params, sd.scene.cameras[v], dl.clone())
+    return rast
+
+
 def train_plain(params: GaussianBuffer, sd: SceneData, iters: int, checkpoints=(), seed: int = 0,
                 rast: Rasterizer | None = None):
     """Plain training: Adam, L1, one view per iteration from a seeded permutation of the training
-    views, reshuffled every epoch.  Returns ({iteration: held-out PSNR}, GPU seconds of training)."""
-    rast = rast or Rasterizer()
+    views, reshuffled every epoch.  Returns ({iteration: held-out PSNR}, GPU seconds of training).
+    The rasterizer has a fixed pair capacity, so no iteration waits on the host (an overflow is
+    reported at the end), and the autotuner's compositing variant."""
+    rast = rast or tuned_rasterizer(params, sd)
     tr = Trainer(params, rast)
     views = sd.scene.train_views()
     rng = np.random.default_rng(seed)
@@ -91,6 +117,7 @@ class InitComparison:
     fit_history: list = field(default_factory=list)
     fallbacks: int = 0
     seconds: dict = field(default_factory=dict)
+    learned_init: LearnedInit | None = None
 
     def mean(self, which: str) -> dict:
         rows = getattr(self, which)
@@ -99,7 +126,7 @@ class InitComparison:
 
 def compare_initializers(train_seeds, eval_seeds, n: int, width: int, height: int, focal: float,
                          budgets=(100, 250, 500), converge_iters: int = 500, fit_steps: int = 600,
-                         n_cameras: int = 64, sh_degree: int = 3) -> InitComparison:
+                         n_cameras: int = 64, sh_degree: int = 3, keep_learned: bool = False) -> InitComparison:
     """Fit the learned initializer on converged Gaussians of plain runs on the training scenes,
     then compare it with the paper's initializer on the held-out views of the evaluation scenes."""
     t0 = time.time()
@@ -129,16 +156,29 @@ def compare_initializers(train_seeds, eval_seeds, n: int, width: int, height: in
         res.learned.append(q)
         res.fallbacks += fb
     res.seconds = {"converge_runs": t1 - t0, "fit": t2 - t1, "eval": time.time() - t2}
+    if keep_learned:
+        res.learned_init = li
     return res
+
+
+def batched_adam(views_per_step: int) -> AdamConfig:
+    """Adam settings for a step that averages the gradients of `views_per_step` views of a scene:
+    the square-root learning-rate rule and momentum decay per view (beta ** views_per_step) of
+    the batch-size scaling study for Gaussian splatting by Zhao et al. (2024), so that one step
+    stands in for that many single-view iterations."""
+    return AdamConfig(lr=tuple(l * math.sqrt(views_per_step) for l in DEFAULT_LR),
+                      b1=0.9 ** views_per_step, b2=0.999 ** views_per_step)
 
 
 def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_iters: int = 500,
                    views_per_step: int = 4, learned: LearnedInit | None = None, check_every: int = 10,
-                   max_steps: int = 500, n_cameras: int = 64, sh_degree: int = 3) -> dict:
+                   max_steps: int = 500, n_cameras: int = 64, sh_degree: int = 3,
+                   adam=None) -> dict:
     """GPU seconds for the plain form (paper initializer, one view per iteration, each scene on its
     own for plain_iters iterations) against the batched form (every scene in one captured batch,
     views_per_step views of each scene per step, learned initializer when given) to reach, for
-    every scene, the plain form's held-out PSNR.  Evaluation renders are not counted."""
+    every scene, the plain form's held-out PSNR.  adam: the batched form's Adam settings (default:
+    the plain form's).  Evaluation renders are not counted."""
     from .batch import BatchTrainer
     init = learned.init if learned is not None else Initializer()
     scenes = [make_scene(s, n, width, height, focal, n_cameras, sh_degree) for s in seeds]
@@ -172,85 +212,71 @@ def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_i
         return out
 
     first = next_views()
-    bt = BatchTrainer(starts, first)
+    bt = BatchTrainer(starts, first, adam=adam)
+    bt.reserve(2 * bt.status()[1] + 4096)
+    tune_batch(bt)
     bt.capture()
     eval_rast = Rasterizer()
     reached = [None] * len(scenes)
     batched_s = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step = 0
+    step, issued = 0, 0
     while step < max_steps and any(r is None for r in reached):
         e0.record(bt.stream)
         for _ in range(check_every):
-            if step > 0:
+            if issued > 0:
                 bt.set_views([(c, t) for _, c, t in next_views()])
             bt.step()
-            step += 1
+            issued += 1
         e1.record(bt.stream)
         torch.cuda.synchronize()
         batched_s += e0.elapsed_time(e1) / 1000.0
+        step = bt.check()  # completed steps; a pair overflow grows the capacity
         for k, sd in enumerate(scenes):
             if reached[k] is None and eval_psnr(eval_rast, starts[k], sd) >= plain_psnr[k]:
                 reached[k] = (step, batched_s)
-    code, _ = bt.status()
-    if code != 0:
-        raise RuntimeError(f"batched status {code}")
     done = all(r is not None for r in reached)
     return {"plain_psnr": plain_psnr, "plain_gpu_s": plain_s, "batched_gpu_s": batched_s,
-            "steps": step, "reached": reached, "all_reached": done, "fallbacks": fallbacks,
+            "steps": step, "issued": issued, "reached": reached, "all_reached": done, "fallbacks": fallbacks,
             "ratio": batched_s / plain_s if done else None}
 
 
 def main(argv=None):
-    """Learned-initializer experiment at the 32-scene x 200k-point scale (1280x720, fx = 1000):
-    fit on 28 scenes' converged Gaussians, compare with the paper's initializer on 4 held-out
-    scenes at 100/250/500 iterations, then time the batched learned-init form to the plain form's
-    500-iteration PSNR.  Prints one JSON line."""
+    """Learned-initializer experiment on 32 surface scenes of 200k points (1280x720, fx = 1000):
+    the network is fitted on the converged Gaussians of plain 500-iteration runs of the training
+    scenes and compared with the paper's initializer on the held-out views of the held-out scenes
+    at 100/250/500 iterations; then the batched learned-init form is timed to the plain form's
+    500-iteration PSNR on the held-out scenes.  Prints one JSON line."""
     import argparse
     import json
     ap = argparse.ArgumentParser()
     ap.add_argument("--scenes", type=int, default=32)
-    ap.add_argument("--held-out", type=int, default=4)
+    ap.add_argument("--held-out", type=int, default=8)
     ap.add_argument("--points", type=int, default=200_000)
     ap.add_argument("--width", type=int, default=1280)
     ap.add_argument("--height", type=int, default=720)
     ap.add_argument("--focal", type=float, default=1000.0)
+    ap.add_argument("--fit-steps", type=int, default=1000)
+    ap.add_argument("--views-per-step", type=int, nargs="+", default=[1, 2])
     args = ap.parse_args(argv)
     t0 = time.time()
     train = list(range(1000, 1000 + args.scenes - args.held_out))
     held = list(range(2000, 2000 + args.held_out))
-    init = Initializer()
-    feats, targs = [], []
-    for seed in train:
-        sd = make_scene(seed, args.points, args.width, args.height, args.focal)
-        pi = init.paper_init(sd.points, 3)
-        p = with_colour(pi.paper.clone())
-        train_plain(p, sd, 500, seed=seed)
-        feats.append(pi.features_bf16)
-        targs.append(init.make_targets(pi, p))
-        del sd
-    li = LearnedInit(init, seed=1)
-    li.fit(feats, targs, steps=1000)
-    paper_rows, learned_rows = [], []
-    for seed in held:
-        sd = make_scene(seed, args.points, args.width, args.height, args.focal)
-        pi = init.paper_init(sd.points, 3)
-        a, _ = train_plain(with_colour(pi.paper.clone()), sd, 500, checkpoints=(100, 250, 500), seed=seed)
-        lp, _ = li.infer(pi)
-        b, _ = train_plain(with_colour(lp), sd, 500, checkpoints=(100, 250, 500), seed=seed)
-        paper_rows.append(a)
-        learned_rows.append(b)
-    mean = lambda rows: {k: float(np.mean([r[k] for r in rows])) for k in (100, 250, 500)}
-    tt = time_to_target(held, args.points, args.width, args.height, args.focal, views_per_step=1,
-                        learned=li)
-    print(json.dumps({"experiment": "learned initializer", "train_scenes": len(train),
-                      "held_out_scenes": len(held), "points": args.points,
-                      "resolution": f"{args.width}x{args.height}",
-                      "psnr_paper_init": mean(paper_rows), "psnr_learned_init": mean(learned_rows),
-                      "fit_loss": li.history[-1][1],
-                      "time_to_plain_psnr": {k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps",
-                                                                "all_reached", "ratio")},
-                      "wall_s": time.time() - t0}))
+    res = compare_initializers(train, held, args.points, args.width, args.height, args.focal,
+                               fit_steps=args.fit_steps, keep_learned=True)
+    out = {"experiment": "learned initializer", "train_scenes": len(train), "held_out_scenes": len(held),
+           "points": args.points, "resolution": f"{args.width}x{args.height}",
+           "psnr_paper_init": res.mean("paper"), "psnr_learned_init": res.mean("learned"),
+           "fit_loss": res.fit_history[-1][1], "fallbacks": res.fallbacks, "time_to_plain_psnr": []}
+    for vps in args.views_per_step:
+        for learned in (res.learned_init, None):
+            tt = time_to_target(held, args.points, args.width, args.height, args.focal, views_per_step=vps,
+                                learned=learned, adam=batched_adam(vps) if vps > 1 else None)
+            out["time_to_plain_psnr"].append(
+                {"views_per_step": vps, "learned": learned is not None,
+                 **{k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps", "all_reached", "ratio")}})
+    out["wall_s"] = time.time() - t0
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -134,3 +134,33 @@ def test_autotuner_times_picks_and_caches(mods, tmp_path):
     cam = views[0][1]
     dl = torch.from_numpy(S.random_image(1, cam.width, cam.height)).cuda()
     assert A.tune_rasterizer(rast, p, cam, dl, cache=cache, reps=1) in L.VARIANTS
+
+
+def test_pair_overflow_skips_the_step_then_grows(mods):
+    """A captured step whose pairs overflow the capacity leaves parameters, moments and the step
+    count untouched; after the status is read and the capacity grown, the graph is captured again
+    and steps proceed as in a batch planned with room from the start."""
+    R, B, _, L = mods
+    scenes, views = small_batch(5)
+    a, pa = make_trainer(mods, scenes, views)           # measured capacity
+    b, pb = make_trainer(mods, scenes, views, pair_capacity=512)
+    before = [p.data.clone() for p in pb]
+    b.capture()
+    for _ in range(2):
+        b.step()
+    torch.cuda.synchronize()
+    code, pairs = b.status()
+    assert code == L.PGS_ERR_CAPACITY and pairs > 512
+    assert b.steps() == 0
+    for x, y in zip(before, pb):
+        assert torch.equal(x, y.data)
+    for m in b.m + b.v:
+        assert not m.data.any()
+    b.reserve(pairs + pairs // 4)
+    for _ in range(2):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert b.check() == 2 and a.check() == 2
+    for x, y in zip(pa, pb):
+        assert rel_l2(y.data.cpu().numpy(), x.data.cpu().numpy()) < 1e-4
