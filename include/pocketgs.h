@@ -310,15 +310,18 @@ int pgs_mlp_grad(pgs_init* ctx, const pgs_mlp* w, const void* x_bf16, const floa
    grad zeroed */
 int pgs_mlp_adam(pgs_init* ctx, pgs_mlp* w, float* grad, float* m, float* v, float lr, int64_t t);
 
-/* Learned initial parameters from MLP outputs y [n][8] (device): log-scales y0..2, rotation
-   frame_q (x) normalise(y3..6), opacity logit y7 written into `out` (log_scales, quats,
-   opacity_logits; means and SH are left to the caller); points whose output is not finite keep
-   the paper's initializer `pca` and are counted in *fallbacks (device uint32, added to). */
-int pgs_apply_mlp(pgs_init* ctx, const float* y, const float* frame_q, const pgs_gaussians* pca,
-                  pgs_gaussians* out, uint32_t* fallbacks);
-/* Training targets t [n][8] from converged Gaussians: log-scales, conj(frame_q) (x) normalise(q),
-   opacity logit. */
-int pgs_make_targets(pgs_init* ctx, const float* frame_q, const pgs_gaussians* converged, float* t);
+/* Learned initial parameters from MLP outputs y [n][8] (device), as corrections of the paper's
+   initializer `pca` of the same point (operator I, Eq. 5-6): log-scales pca + y0..2, rotation
+   normalise(pca q) (x) normalise(y3..6), opacity logit pca + y7, written into `out` (log_scales,
+   quats, opacity_logits; means and SH are left to the caller).  Points whose output is not finite
+   (or whose y3..6 is zero) keep the paper's initializer and are counted in *fallbacks (device
+   uint32, added to). */
+int pgs_apply_mlp(pgs_init* ctx, const float* y, const pgs_gaussians* pca, pgs_gaussians* out,
+                  uint32_t* fallbacks);
+/* Training targets t [n][8] (device fp32) of converged Gaussians relative to the paper's
+   initializer `pca` of the same points: log-scale differences, conj(normalise(pca q)) (x)
+   normalise(q), opacity-logit difference.  pca and converged have the same n. */
+int pgs_make_targets(pgs_init* ctx, const pgs_gaussians* pca, const pgs_gaussians* converged, float* t);
 
 /* Static description of an error code. */
 const char* pgs_strerror(int code);

@@ -360,21 +360,28 @@ def mlp_backward(x, weights, dy, mode: int = 1):
     return grads
 
 
-def apply_mlp(y, frame_q) -> dict:
+def _base(g):
+    return (np.ascontiguousarray(g["log_scales"], np.float64), np.ascontiguousarray(g["quats"], np.float64),
+            np.ascontiguousarray(g["opacity_logits"], np.float64))
+
+
+def apply_mlp(y, base) -> dict:
+    """Learned parameters: MLP outputs y [n][8] applied as corrections of `base` (the paper's
+    initializer: log_scales [3][n], quats [4][n], opacity_logits [n])."""
     y = np.ascontiguousarray(y, np.float64)
-    fq = np.ascontiguousarray(frame_q, np.float64)
+    bl, bq, bo = _base(base)
     n = y.shape[0]
     out = dict(log_scales=np.zeros((3, n)), quats=np.zeros((4, n)), opacity_logits=np.zeros(n))
-    lib().oracle_apply_mlp(n, _ptr(y), _ptr(fq), _ptr(out["log_scales"]), _ptr(out["quats"]),
-                           _ptr(out["opacity_logits"]))
+    lib().oracle_apply_mlp(n, _ptr(y), _ptr(bl), _ptr(bq), _ptr(bo), _ptr(out["log_scales"]),
+                           _ptr(out["quats"]), _ptr(out["opacity_logits"]))
     return out
 
 
-def make_targets(frame_q, log_scales, quats, logits) -> np.ndarray:
-    fq = np.ascontiguousarray(frame_q, np.float64)
-    ls = np.ascontiguousarray(log_scales, np.float64)
-    q = np.ascontiguousarray(quats, np.float64)
-    lg = np.ascontiguousarray(logits, np.float64)
-    t = np.zeros((fq.shape[1], 8))
-    lib().oracle_make_targets(fq.shape[1], _ptr(fq), _ptr(ls), _ptr(q), _ptr(lg), _ptr(t))
+def make_targets(base, converged) -> np.ndarray:
+    """Targets [n][8] of `converged` relative to `base` (dicts as in apply_mlp)."""
+    bl, bq, bo = _base(base)
+    cl, cq, co = _base(converged)
+    n = bq.shape[1]
+    t = np.zeros((n, 8))
+    lib().oracle_make_targets(n, _ptr(bl), _ptr(bq), _ptr(bo), _ptr(cl), _ptr(cq), _ptr(co), _ptr(t))
     return t

@@ -381,36 +381,42 @@ static void qmul(const double a[4], const double b[4], double o[4]) {
     o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
 }
 
-// Learned parameters from MLP outputs y [n][8]: log-scales y0..2, quaternion frame_q (x)
-// normalise(y3..6), logit y7 (log_scales [3][n], quats [4][n], logits [n]).
-void oracle_apply_mlp(int64_t n, const double* y, const double* frame_q, double* log_scales,
-                      double* quats, double* logits) {
+// Learned parameters from MLP outputs y [n][8], as corrections of the paper's initializer of the
+// same point (base: log-scales [3][n], quaternions [4][n], logits [n]): log-scales base + y0..2,
+// rotation normalise(base q) (x) normalise(y3..6), logit base + y7.
+void oracle_apply_mlp(int64_t n, const double* y, const double* base_ls, const double* base_q,
+                      const double* base_logit, double* log_scales, double* quats, double* logits) {
     for (int64_t i = 0; i < n; ++i) {
         const double* a = y + i * 8;
         const double qn = std::sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5] + a[6] * a[6]);
         const double ql[4] = {a[3] / qn, a[4] / qn, a[5] / qn, a[6] / qn};
-        const double qf[4] = {frame_q[i], frame_q[n + i], frame_q[2 * n + i], frame_q[3 * n + i]};
+        double qb[4] = {base_q[i], base_q[n + i], base_q[2 * n + i], base_q[3 * n + i]};
+        const double bn = std::sqrt(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+        for (int k = 0; k < 4; ++k) qb[k] /= bn;
         double q[4];
-        qmul(qf, ql, q);
-        for (int k = 0; k < 3; ++k) log_scales[k * n + i] = a[k];
+        qmul(qb, ql, q);
+        for (int k = 0; k < 3; ++k) log_scales[k * n + i] = base_ls[k * n + i] + a[k];
         for (int k = 0; k < 4; ++k) quats[k * n + i] = q[k];
-        logits[i] = a[7];
+        logits[i] = base_logit[i] + a[7];
     }
 }
 
-// Targets [n][8]: log-scales, conj(frame_q) (x) normalise(q), logit of converged Gaussians.
-void oracle_make_targets(int64_t n, const double* frame_q, const double* log_scales,
-                         const double* quats, const double* logits, double* t) {
+// Targets [n][8] of converged Gaussians relative to the paper's initializer of the same point:
+// log-scale differences, conj(normalise(base q)) (x) normalise(q), logit difference.
+void oracle_make_targets(int64_t n, const double* base_ls, const double* base_q, const double* base_logit,
+                         const double* log_scales, const double* quats, const double* logits, double* t) {
     for (int64_t i = 0; i < n; ++i) {
         double q[4] = {quats[i], quats[n + i], quats[2 * n + i], quats[3 * n + i]};
         const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         for (int k = 0; k < 4; ++k) q[k] /= qn;
-        const double qc[4] = {frame_q[i], -frame_q[n + i], -frame_q[2 * n + i], -frame_q[3 * n + i]};
+        double qb[4] = {base_q[i], base_q[n + i], base_q[2 * n + i], base_q[3 * n + i]};
+        const double bn = std::sqrt(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+        const double qc[4] = {qb[0] / bn, -qb[1] / bn, -qb[2] / bn, -qb[3] / bn};
         double ql[4];
         qmul(qc, q, ql);
-        for (int k = 0; k < 3; ++k) t[i * 8 + k] = log_scales[k * n + i];
+        for (int k = 0; k < 3; ++k) t[i * 8 + k] = log_scales[k * n + i] - base_ls[k * n + i];
         for (int k = 0; k < 4; ++k) t[i * 8 + 3 + k] = ql[k];
-        t[i * 8 + 7] = logits[i];
+        t[i * 8 + 7] = logits[i] - base_logit[i];
     }
 }
 

@@ -172,9 +172,9 @@ def lib():
             L.pgs_mlp_grad.restype = I
             L.pgs_mlp_adam.argtypes = [P, C.POINTER(PgsMlp), P, P, P, C.c_float, I64]
             L.pgs_mlp_adam.restype = I
-            L.pgs_apply_mlp.argtypes = [P, P, P, C.POINTER(PgsGaussians), C.POINTER(PgsGaussians), P]
+            L.pgs_apply_mlp.argtypes = [P, P, C.POINTER(PgsGaussians), C.POINTER(PgsGaussians), P]
             L.pgs_apply_mlp.restype = I
-            L.pgs_make_targets.argtypes = [P, P, C.POINTER(PgsGaussians), P]
+            L.pgs_make_targets.argtypes = [P, C.POINTER(PgsGaussians), C.POINTER(PgsGaussians), P]
             L.pgs_make_targets.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p

@@ -937,18 +937,18 @@ int pgs_mlp_adam(pgs_init* c, pgs_mlp* w, float* grad, float* m, float* v, float
     return cuda_err(cudaGetLastError());
 }
 
-int pgs_apply_mlp(pgs_init* c, const float* y, const float* frame_q, const pgs_gaussians* pca,
-                  pgs_gaussians* out, uint32_t* fallbacks) {
-    if (!c || !y || !frame_q || !valid_gaussians(pca) || !valid_gaussians(out) || !fallbacks ||
-        pca->n != out->n)
+int pgs_apply_mlp(pgs_init* c, const float* y, const pgs_gaussians* pca, pgs_gaussians* out,
+                  uint32_t* fallbacks) {
+    if (!c || !y || !valid_gaussians(pca) || !valid_gaussians(out) || !fallbacks || pca->n != out->n)
         return PGS_ERR_INVALID_ARG;
-    launch_apply_mlp(out->n, y, frame_q, *pca, *out, fallbacks, c->stream);
+    launch_apply_mlp(out->n, y, *pca, *out, fallbacks, c->stream);
     return cuda_err(cudaGetLastError());
 }
 
-int pgs_make_targets(pgs_init* c, const float* frame_q, const pgs_gaussians* conv, float* t) {
-    if (!c || !frame_q || !valid_gaussians(conv) || !t) return PGS_ERR_INVALID_ARG;
-    launch_make_targets(conv->n, frame_q, *conv, t, c->stream);
+int pgs_make_targets(pgs_init* c, const pgs_gaussians* pca, const pgs_gaussians* conv, float* t) {
+    if (!c || !valid_gaussians(pca) || !valid_gaussians(conv) || !t || pca->n != conv->n)
+        return PGS_ERR_INVALID_ARG;
+    launch_make_targets(conv->n, *pca, *conv, t, c->stream);
     return cuda_err(cudaGetLastError());
 }
 

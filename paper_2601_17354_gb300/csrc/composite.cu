@@ -89,7 +89,7 @@ struct FwdSmem {
 // One tile of the forward.  kPix: pixels per thread (vertical strip); kDepth: entries staged per
 // batch.  Every thread of the CTA calls it with the same job.
 template <int kPix, int kDepth>
-__device__ __forceinline__ void fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+__device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, FwdSmem<kDepth>& S) {
     constexpr int kThreads = kTilePixels / kPix;
     constexpr int kBatch = kDepth;
@@ -211,7 +211,7 @@ struct BwdSmem {
 };
 
 template <int kPix, int kDepth>
-__device__ __forceinline__ void bwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+__device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, BwdSmem<kDepth>& S) {
     constexpr int kThreads = kTilePixels / kPix;
     constexpr int kBatch = kDepth;
@@ -337,6 +337,333 @@ __device__ __forceinline__ void bwd_tile(const TileJob& J, int64_t n, const uint
         }
         end = start;
     }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Paired-pixel tiles (kPix = 2, 4): a thread's strip is processed two pixels at a time with the
+// packed fp32 instructions of sm_100+ (add/sub/mul/fma .rn .f32x2).  Every packed lane rounds
+// exactly as the scalar instruction does, so the alpha, skip and stop decisions and the forward
+// image are bit-identical to the one-pixel tiles; per pixel the work is branch-free (a pixel that
+// does not composite an entry contributes alpha = 0, which leaves T, C and the colour behind
+// unchanged), and the pair shares one branch.
+struct F2 {
+    unsigned long long r;
+};
+__device__ __forceinline__ F2 f2(float a, float b) {
+    F2 o;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
+    return o;
+}
+__device__ __forceinline__ F2 f2(float a) { return f2(a, a); }
+__device__ __forceinline__ float2 un(F2 a) {
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(a.r));
+    return o;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+    return d;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+    return d;
+}
+
+// alpha of the pixel pair (dy, dy + 1) below one entry: the packed form of entry_alpha
+__device__ __forceinline__ void pair_alpha(F2 dy, F2 DX, F2 ADX2, F2 S2Y, F2 S2Z, F2 O, float2& G,
+                                           float2& og, float2& alpha) {
+    const float2 p = un(fma2(S2Z, mul2(dy, dy), fma2(S2Y, mul2(DX, dy), ADX2)));
+    G = make_float2(ex2_approx(p.x), ex2_approx(p.y));
+    og = un(mul2(O, f2(G.x, G.y)));
+    alpha = make_float2(fminf(kAlphaMax, og.x), fminf(kAlphaMax, og.y));
+}
+
+template <int kPix, int kDepth>
+__device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                               const Scratch& sc, FwdSmem<kDepth>& S) {
+    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kBatch = kDepth;
+    constexpr int NP = kPix / 2;
+    float4* s_xyo = S.xyo;
+    float4* s_s2 = S.s2;
+    float4* s_rgb = S.rgb;
+    const int W = J.W, H = J.H;
+    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
+    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
+    const uint2 range = J.range;
+    const float3 bg = J.bg;
+    F2 T[NP], C0[NP], C1[NP], C2[NP];
+    uint32_t last[kPix], ncomp[kPix];
+    bool done[kPix];
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        T[q] = f2(1.0f);
+        C0[q] = C1[q] = C2[q] = f2(0.0f);
+    }
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        last[k] = ncomp[k] = 0;
+        done[k] = !(px < W && py0 + k < H);
+        all_done = all_done && done[k];
+    }
+    for (uint32_t base = range.x; base < range.y; base += kBatch) {
+        if (__syncthreads_count(all_done) == kThreads) break;
+#pragma unroll
+        for (int e = threadIdx.x; e < kBatch; e += kThreads) {
+            const uint32_t idx = base + e;
+            if (idx < range.y) {
+                const uint32_t id = checked_id(vals[idx], n, sc.status);
+                s_xyo[e] = sc.xyo[id];
+                s_s2[e] = scaled_conic(sc.conic[id]);
+                s_rgb[e] = sc.rgb[id];
+            }
+        }
+        __syncthreads();
+        const int cnt = min((uint32_t)kBatch, range.y - base);
+        for (int j = 0; !all_done && j < cnt; ++j) {
+            const float4 p = s_xyo[j];
+            const float4 s2 = s_s2[j];
+            const float dx = fx - p.x;
+            const F2 DX = f2(dx), ADX2 = f2(__fmul_rn(s2.x, __fmul_rn(dx, dx)));
+            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(p.z);
+            const F2 DY0 = f2(fy0 - p.y);
+            const uint32_t pos = base + j - range.x + 1;
+            all_done = true;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const int k0 = 2 * q, k1 = 2 * q + 1;
+                const F2 dy = add2(DY0, f2((float)k0, (float)k1));
+                float2 G, og, a;
+                pair_alpha(dy, DX, ADX2, S2Y, S2Z, O, G, og, a);
+                const bool p0 = !done[k0] && a.x >= kAlphaMin, p1 = !done[k1] && a.y >= kAlphaMin;
+                if (p0 || p1) {
+                    const float2 tv = un(T[q]);
+                    const float2 tn = un(mul2(T[q], sub2(f2(1.0f), f2(a.x, a.y))));
+                    const bool s0 = p0 && tn.x < kTMin, s1 = p1 && tn.y < kTMin;  // stop, not composited
+                    const bool c0 = p0 && !s0, c1 = p1 && !s1;
+                    done[k0] = done[k0] || s0;
+                    done[k1] = done[k1] || s1;
+                    const F2 w = mul2(f2(c0 ? a.x : 0.0f, c1 ? a.y : 0.0f), T[q]);
+                    const float4 c = s_rgb[j];
+                    C0[q] = fma2(f2(c.x), w, C0[q]);
+                    C1[q] = fma2(f2(c.y), w, C1[q]);
+                    C2[q] = fma2(f2(c.z), w, C2[q]);
+                    T[q] = f2(c0 ? tn.x : tv.x, c1 ? tn.y : tv.y);
+                    last[k0] = c0 ? pos : last[k0];
+                    last[k1] = c1 ? pos : last[k1];
+                    ncomp[k0] += c0;
+                    ncomp[k1] += c1;
+                }
+                all_done = all_done && done[k0] && done[k1];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const float2 t = un(T[q]), c0 = un(C0[q]), c1 = un(C1[q]), c2 = un(C2[q]);
+        const float tk[2] = {t.x, t.y}, r[2] = {c0.x, c0.y}, g[2] = {c1.x, c1.y}, b[2] = {c2.x, c2.y};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * q + h;
+            const int py = py0 + k;
+            if (px < W && py < H) {
+                const size_t pp = (size_t)py * W + px, plane = (size_t)W * H;
+                J.image[pp] = fmaf(tk[h], bg.x, r[h]);
+                J.image[plane + pp] = fmaf(tk[h], bg.y, g[h]);
+                J.image[2 * plane + pp] = fmaf(tk[h], bg.z, b[h]);
+                J.T_final[pp] = tk[h];
+                J.last[pp] = last[k];
+                J.ncomp[pp] = ncomp[k];
+            }
+        }
+    }
+}
+
+template <int kPix, int kDepth>
+__device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                               const Scratch& sc, BwdSmem<kDepth>& S) {
+    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kBatch = kDepth;
+    constexpr int NP = kPix / 2;
+    float4* s_xyo = S.xyo;
+    float4* s_s2 = S.s2;
+    float4* s_con = S.con;
+    float4* s_rgb = S.rgb;
+    uint32_t* s_id = S.id;
+    uint32_t* s_max = S.wmax;
+    const int W = J.W, H = J.H;
+    const float3 bg = J.bg;
+    const float* __restrict__ dL_dimage = J.dL;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
+    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
+    const uint2 range = J.range;
+    const size_t plane = (size_t)W * H;
+    F2 T[NP], g0[NP], g1[NP], g2[NP], B0[NP], B1[NP], B2[NP];
+    uint32_t my_last[kPix];
+    uint32_t tmax = 0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float t[2] = {1.0f, 1.0f}, a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f}, c[2] = {0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * q + h;
+            const int py = py0 + k;
+            my_last[k] = 0;
+            if (px < W && py < H) {
+                const size_t pp = (size_t)py * W + px;
+                t[h] = J.T_final[pp];
+                my_last[k] = J.last[pp];
+                a[h] = dL_dimage[pp];
+                b[h] = dL_dimage[plane + pp];
+                c[h] = dL_dimage[2 * plane + pp];
+            }
+            tmax = max(tmax, my_last[k]);
+        }
+        T[q] = f2(t[0], t[1]);
+        g0[q] = f2(a[0], a[1]);
+        g1[q] = f2(b[0], b[1]);
+        g2[q] = f2(c[0], c[1]);
+        B0[q] = f2(bg.x);  // colour behind the current entry (Eq. 7 C_in)
+        B1[q] = f2(bg.y);
+        B2[q] = f2(bg.z);
+    }
+    const uint32_t wmax = __reduce_max_sync(kFull, tmax);
+    if (lane == 0) s_max[warp] = wmax;
+    __syncthreads();
+    uint32_t end = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) end = max(end, s_max[w]);
+
+    while (end > 0) {
+        const uint32_t start = end > (uint32_t)kBatch ? end - kBatch : 0u;
+        const int cnt = (int)(end - start);
+        __syncthreads();
+#pragma unroll
+        for (int e = threadIdx.x; e < kBatch; e += kThreads) {
+            if (e < cnt) {
+                const uint32_t id = checked_id(vals[range.x + start + e], n, sc.status);
+                s_id[e] = id;
+                s_xyo[e] = sc.xyo[id];
+                const float4 con = sc.conic[id];
+                s_con[e] = con;
+                s_s2[e] = scaled_conic(con);
+                s_rgb[e] = sc.rgb[id];
+            }
+        }
+        __syncthreads();
+        // this warp's entries: positions below its deepest `last`
+        const int jtop = (int)min((uint32_t)cnt, wmax > start ? wmax - start : 0u);
+        for (int j = jtop - 1; j >= 0; --j) {
+            const uint32_t pos = start + j;
+            const float4 pm = s_xyo[j];
+            const float4 s2 = s_s2[j];
+            const float dx = fx - pm.x;
+            const F2 DX = f2(dx), ADX2 = f2(__fmul_rn(s2.x, __fmul_rn(dx, dx)));
+            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(pm.z);
+            const F2 DY0 = f2(fy0 - pm.y);
+            // per-lane sums over the strip: dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2,
+            // dL/dalpha G, alpha T dL/dC (rgb)
+            F2 acc[9];
+#pragma unroll
+            for (int v = 0; v < 9; ++v) acc[v] = f2(0.0f);
+            bool contrib = false;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const int k0 = 2 * q, k1 = 2 * q + 1;
+                const F2 dy = add2(DY0, f2((float)k0, (float)k1));
+                float2 G, og, a;
+                pair_alpha(dy, DX, ADX2, S2Y, S2Z, O, G, og, a);
+                const bool p0 = pos < my_last[k0] && a.x >= kAlphaMin;
+                const bool p1 = pos < my_last[k1] && a.y >= kAlphaMin;
+                if (p0 || p1) {
+                    contrib = true;
+                    const float4 c = s_rgb[j];
+                    const float e0 = p0 ? a.x : 0.0f, e1 = p1 ? a.y : 0.0f;
+                    const F2 A = f2(e0, e1);
+                    const float2 om = un(sub2(f2(1.0f), A)), tv = un(T[q]);
+                    const F2 Tb = f2(p0 ? __fdividef(tv.x, om.x) : tv.x,
+                                     p1 ? __fdividef(tv.y, om.y) : tv.y);  // transmittance in front
+                    const F2 r0 = sub2(f2(c.x), B0[q]), r1 = sub2(f2(c.y), B1[q]), r2 = sub2(f2(c.z), B2[q]);
+                    const F2 dLda = mul2(Tb, fma2(r2, g2[q], fma2(r1, g1[q], mul2(r0, g0[q]))));
+                    const F2 wgt = mul2(A, Tb);
+                    acc[6] = fma2(wgt, g0[q], acc[6]);
+                    acc[7] = fma2(wgt, g1[q], acc[7]);
+                    acc[8] = fma2(wgt, g2[q], acc[8]);
+                    B0[q] = fma2(A, r0, B0[q]);
+                    B1[q] = fma2(A, r1, B1[q]);
+                    B2[q] = fma2(A, r2, B2[q]);
+                    T[q] = Tb;
+                    // zero gradient through the 0.99 clamp
+                    const bool q0 = p0 && og.x <= kAlphaMax, q1 = p1 && og.y <= kAlphaMax;
+                    acc[5] = fma2(dLda, f2(q0 ? G.x : 0.0f, q1 ? G.y : 0.0f), acc[5]);
+                    const F2 dpow = mul2(dLda, f2(q0 ? a.x : 0.0f, q1 ? a.y : 0.0f));
+                    const F2 dpx = mul2(dpow, DX), dpy = mul2(dpow, dy);
+                    acc[0] = add2(acc[0], dpx);
+                    acc[1] = add2(acc[1], dpy);
+                    acc[2] = fma2(dpx, DX, acc[2]);
+                    acc[3] = fma2(dpx, dy, acc[3]);
+                    acc[4] = fma2(dpy, dy, acc[4]);
+                }
+            }
+            if (__any_sync(kFull, contrib)) {
+                float v[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const float2 h = un(acc[q]);
+                    v[q] = h.x + h.y;
+                }
+                // d power / d mean2D = (a dx + b dy, c dy + b dx) with the conic (a, b, c) of
+                // the entry, from the strip's sums of dpow dx and dpow dy
+                const float4 con = s_con[j];
+                const float m0 = fmaf(con.x, v[0], con.y * v[1]);
+                const float m1 = fmaf(con.z, v[1], con.y * v[0]);
+                v[0] = m0;
+                v[1] = m1;
+                float s8, s9;
+                warp_sum9(v, lane, s8, s9);
+                const uint32_t id = s_id[j];
+                if ((lane & 3) == 0) {
+                    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
+                    const int q = lane >> 2;
+                    const float f = q == 2 || q == 4 ? -0.5f : (q == 3 ? -1.0f : 1.0f);
+                    atomicAdd(&sc.grad2d[(size_t)q * n + id], f * s8);
+                }
+                if (lane == 1) atomicAdd(&sc.grad2d[(size_t)8 * n + id], s9);
+            }
+        }
+        end = start;
+    }
+}
+
+template <int kPix, int kDepth>
+__device__ __forceinline__ void fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                         const Scratch& sc, FwdSmem<kDepth>& S) {
+    if constexpr (kPix == 1) fwd_tile_scalar<kPix, kDepth>(J, n, vals, sc, S);
+    else fwd_tile_pairs<kPix, kDepth>(J, n, vals, sc, S);
+}
+
+template <int kPix, int kDepth>
+__device__ __forceinline__ void bwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                         const Scratch& sc, BwdSmem<kDepth>& S) {
+    if constexpr (kPix == 1) bwd_tile_scalar<kPix, kDepth>(J, n, vals, sc, S);
+    else bwd_tile_pairs<kPix, kDepth>(J, n, vals, sc, S);
 }
 
 

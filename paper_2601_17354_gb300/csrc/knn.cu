@@ -361,11 +361,12 @@ __device__ __forceinline__ void qmul(const float a[4], const float b[4], float o
     o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
 }
 
-// Learned initial parameters: log-scales y0..2, rotation q_frame (x) normalise(y3..6) (the MLP
-// predicts the rotation relative to the point's eigenframe), opacity logit y7; any point whose
-// output is not finite keeps the paper's initializer (fallback).
-__global__ void k_apply_mlp(int64_t n, const float* __restrict__ y, const float* __restrict__ frame_q,
-                            pgs_gaussians pca, pgs_gaussians out, uint32_t* fallbacks) {
+// Learned parameters from MLP outputs y [n][8], as corrections of the paper's initializer `pca`
+// of the same point: log-scales pca + y0..2, rotation normalise(pca q) (x) normalise(y3..6),
+// logit pca + y7.  A point whose outputs are not finite (or whose quaternion is zero) keeps the
+// paper's initializer and is counted in *fallbacks.
+__global__ void k_apply_mlp(int64_t n, const float* __restrict__ y, pgs_gaussians pca, pgs_gaussians out,
+                            uint32_t* fallbacks) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const float* yi = y + i * 8;
@@ -375,12 +376,14 @@ __global__ void k_apply_mlp(int64_t n, const float* __restrict__ y, const float*
     ok = ok && qn > 1e-12f;
     if (ok) {
         const float ql[4] = {yi[3] / qn, yi[4] / qn, yi[5] / qn, yi[6] / qn};
-        const float qf[4] = {frame_q[i], frame_q[n + i], frame_q[2 * n + i], frame_q[3 * n + i]};
+        float qb[4] = {pca.quats[i], pca.quats[n + i], pca.quats[2 * n + i], pca.quats[3 * n + i]};
+        const float bn = sqrtf(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+        for (int k = 0; k < 4; ++k) qb[k] /= bn;
         float q[4];
-        qmul(qf, ql, q);
-        for (int k = 0; k < 3; ++k) out.log_scales[k * n + i] = yi[k];
+        qmul(qb, ql, q);
+        for (int k = 0; k < 3; ++k) out.log_scales[k * n + i] = pca.log_scales[k * n + i] + yi[k];
         for (int k = 0; k < 4; ++k) out.quats[k * n + i] = q[k];
-        out.opacity_logits[i] = yi[7];
+        out.opacity_logits[i] = pca.opacity_logits[i] + yi[7];
     } else {
         for (int k = 0; k < 3; ++k) out.log_scales[k * n + i] = pca.log_scales[k * n + i];
         for (int k = 0; k < 4; ++k) out.quats[k * n + i] = pca.quats[k * n + i];
@@ -389,35 +392,37 @@ __global__ void k_apply_mlp(int64_t n, const float* __restrict__ y, const float*
     }
 }
 
-// Training targets [n][8] from converged Gaussians: log-scales, the rotation relative to the
-// eigenframe conj(q_frame) (x) normalise(q), opacity logit.
-__global__ void k_make_targets(int64_t n, const float* __restrict__ frame_q, pgs_gaussians conv,
-                               float* __restrict__ t) {
+// Training targets [n][8] of converged Gaussians relative to the paper's initializer `pca` of the
+// same point: log-scale differences, conj(normalise(pca q)) (x) normalise(q), logit difference.
+__global__ void k_make_targets(int64_t n, pgs_gaussians pca, pgs_gaussians conv, float* __restrict__ t) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     float q[4] = {conv.quats[i], conv.quats[n + i], conv.quats[2 * n + i], conv.quats[3 * n + i]};
     const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     for (int k = 0; k < 4; ++k) q[k] /= qn;
-    const float qc[4] = {frame_q[i], -frame_q[n + i], -frame_q[2 * n + i], -frame_q[3 * n + i]};
+    float qb[4] = {pca.quats[i], pca.quats[n + i], pca.quats[2 * n + i], pca.quats[3 * n + i]};
+    const float bn = sqrtf(qb[0] * qb[0] + qb[1] * qb[1] + qb[2] * qb[2] + qb[3] * qb[3]);
+    const float qc[4] = {qb[0] / bn, -qb[1] / bn, -qb[2] / bn, -qb[3] / bn};
     float ql[4];
     qmul(qc, q, ql);
-    for (int k = 0; k < 3; ++k) t[i * 8 + k] = conv.log_scales[k * n + i];
+    for (int k = 0; k < 3; ++k) t[i * 8 + k] = conv.log_scales[k * n + i] - pca.log_scales[k * n + i];
     for (int k = 0; k < 4; ++k) t[i * 8 + 3 + k] = ql[k];
-    t[i * 8 + 7] = conv.opacity_logits[i];
+    t[i * 8 + 7] = conv.opacity_logits[i] - pca.opacity_logits[i];
 }
 
 }  // namespace
 
-int launch_apply_mlp(int64_t n, const float* y, const float* frame_q, const pgs_gaussians& pca,
-                     pgs_gaussians& out, uint32_t* fallbacks, cudaStream_t s) {
+int launch_apply_mlp(int64_t n, const float* y, const pgs_gaussians& pca, pgs_gaussians& out,
+                     uint32_t* fallbacks, cudaStream_t s) {
     if (n <= 0) return 0;
-    k_apply_mlp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, y, frame_q, pca, out, fallbacks);
+    k_apply_mlp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, y, pca, out, fallbacks);
     return 1;
 }
 
-int launch_make_targets(int64_t n, const float* frame_q, const pgs_gaussians& conv, float* t, cudaStream_t s) {
+int launch_make_targets(int64_t n, const pgs_gaussians& pca, const pgs_gaussians& conv, float* t,
+                        cudaStream_t s) {
     if (n <= 0) return 0;
-    k_make_targets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, frame_q, conv, t);
+    k_make_targets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pca, conv, t);
     return 1;
 }
 

@@ -138,9 +138,10 @@ int launch_knn(int64_t n, const float* P, int k, int32_t* nb, void* scratch, siz
                const float* host_bbox, cudaStream_t s);
 int launch_features_init(int64_t n, const float* P, const int32_t* nb, float r_normal, float* feats,
                          void* feats_bf16, float* frame_q, pgs_gaussians& init, cudaStream_t s);
-int launch_apply_mlp(int64_t n, const float* y, const float* frame_q, const pgs_gaussians& pca,
-                     pgs_gaussians& out, uint32_t* fallbacks, cudaStream_t s);
-int launch_make_targets(int64_t n, const float* frame_q, const pgs_gaussians& conv, float* t, cudaStream_t s);
+int launch_apply_mlp(int64_t n, const float* y, const pgs_gaussians& pca, pgs_gaussians& out,
+                     uint32_t* fallbacks, cudaStream_t s);
+int launch_make_targets(int64_t n, const pgs_gaussians& pca, const pgs_gaussians& conv, float* t,
+                        cudaStream_t s);
 int mlp_param_count();
 int launch_mlp_forward(const void* x, int64_t n, const float* master, const void* W1, const void* W2,
                        const void* W3, float* out, cudaStream_t s);

@@ -3,8 +3,10 @@
 Initializer.paper_init: kNN -> Eq. 5 normal (16 neighbours) and Eq. 6 tangential scale
 (3 neighbours) -> thin disc Gaussians (the paper's initializer, also the learned path's fallback).
 LearnedInit: a 16-64-64-8 GELU MLP (BF16 weights and activations, FP32 accumulation, FP32 master
-weights with Adam) mapping 32-neighbour features to log-scales, rotation (relative to the point's
-eigenframe) and opacity logit; trained on converged Gaussians produced by the plain method.
+weights with Adam) mapping 32-neighbour features to log-scales, rotation and opacity logit, each
+expressed as a correction of the paper's initializer of the same point (log-scale and logit
+offsets, rotation composed after the seeded one), so the network learns what training changes in
+the seeding; trained on converged Gaussians produced by the plain method.
 All arithmetic runs in libpocketgs kernels; this module marshals tensors.
 """
 from __future__ import annotations
@@ -76,17 +78,16 @@ class Initializer:
 
     def make_targets(self, pi: PointInit, converged: GaussianBuffer) -> torch.Tensor:
         t = torch.empty((converged.n, 8), dtype=torch.float32, device=self.device)
-        L.check(self._lib.pgs_make_targets(self._c, _p(pi.frame_q), C.byref(converged.struct()), _p(t)),
-                "pgs_make_targets")
+        L.check(self._lib.pgs_make_targets(self._c, C.byref(pi.paper.struct()), C.byref(converged.struct()),
+                                           _p(t)), "pgs_make_targets")
         return t
 
     def apply(self, pi: PointInit, y: torch.Tensor) -> tuple:
         """Learned initial parameters from MLP outputs y [n][8]; (GaussianBuffer, fallbacks)."""
         out = pi.paper.clone()
         fb = torch.zeros(1, dtype=torch.int32, device=self.device)
-        L.check(self._lib.pgs_apply_mlp(self._c, _p(y.contiguous()), _p(pi.frame_q),
-                                        C.byref(pi.paper.struct()), C.byref(out.struct()), _p(fb)),
-                "pgs_apply_mlp")
+        L.check(self._lib.pgs_apply_mlp(self._c, _p(y.contiguous()), C.byref(pi.paper.struct()),
+                                        C.byref(out.struct()), _p(fb)), "pgs_apply_mlp")
         return out, int(fb.item())
 
 

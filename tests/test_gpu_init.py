@@ -107,8 +107,8 @@ def test_apply_and_targets_match_oracle(I):
     y[5, 2] = np.nan  # falls back to the paper's initializer
     out, fallbacks = init.apply(pi, torch.from_numpy(y).cuda())
     assert fallbacks == 1
-    fq = pi.frame_q.cpu().numpy().astype(np.float64)
-    o = oracle.apply_mlp(y.astype(np.float64), fq)
+    base = pi.paper.numpy()
+    o = oracle.apply_mlp(y.astype(np.float64), base)
     g = out.numpy()
     keep = np.ones(3000, bool)
     keep[5] = False
@@ -116,7 +116,7 @@ def test_apply_and_targets_match_oracle(I):
     assert np.allclose(g["log_scales"][:, keep], o["log_scales"][:, keep])
     assert np.allclose(g["quats"][:, 5], pi.paper.quats[:, 5].cpu().numpy())
     t = init.make_targets(pi, out).cpu().numpy()
-    ot = oracle.make_targets(fq, g["log_scales"], g["quats"], g["opacity_logits"])
+    ot = oracle.make_targets(base, g)
     assert np.allclose(t, ot, atol=1e-5)
 
 
@@ -124,11 +124,11 @@ def test_training_reduces_the_loss(I):
     init = I.Initializer()
     P = surface_points(5, 20000)
     pi = init.paper_init(torch.from_numpy(P).cuda(), sh_degree=0)
-    # targets: a smooth function of the point's own statistics (scale from density, rotation of
-    # the eigenframe itself, opacity from planarity)
+    # targets: a smooth function of the point's own statistics (scale offset from density, the
+    # seeded rotation itself, opacity offset from planarity)
     f = pi.features
     t = torch.zeros((f.shape[0], 8), device="cuda")
-    t[:, 0:3] = (-f[:, 15:16] / 3.0) - 1.0
+    t[:, 0:3] = 0.1 * (f[:, 15:16] - f[:, 15].mean())
     t[:, 3] = 1.0
     t[:, 7] = 2.0 * f[:, 0] - 0.5
     li = I.LearnedInit(init, seed=3)

@@ -140,24 +140,33 @@ def test_mlp_bf16_mode_is_close_to_exact():
         assert np.linalg.norm(u - v) / np.linalg.norm(v) < 3e-2
 
 
-def test_frame_composition_matches_scipy_and_round_trips():
-    """Learned rotation = eigenframe (x) predicted local rotation (rotation composition, checked
-    with scipy's Rotation), and targets built from a converged rotation map back to it."""
+def test_residual_composition_matches_scipy_and_round_trips():
+    """Learned parameters = the paper's seeding corrected by the network: rotation = seeded
+    rotation (x) predicted rotation (composition checked with scipy's Rotation), log-scales and
+    logit offset; zero offsets with the identity rotation give the seeding back, and targets built
+    from any converged Gaussians map back to them."""
     Rot = pytest.importorskip("scipy.spatial.transform").Rotation
     rng = np.random.default_rng(6)
     n = 40
-    fq = rng.normal(size=(4, n))
-    fq /= np.linalg.norm(fq, axis=0)
+    bq = rng.normal(size=(4, n))
+    bq /= np.linalg.norm(bq, axis=0)
+    base = dict(log_scales=rng.normal(-4, 0.3, (3, n)), quats=bq, opacity_logits=rng.normal(-2, 0.1, n))
     y = rng.normal(size=(n, 8))
-    out = oracle.apply_mlp(y, fq)
+    out = oracle.apply_mlp(y, base)
     for i in range(n):
-        Rf = Rot.from_quat([fq[1, i], fq[2, i], fq[3, i], fq[0, i]])
+        Rb = Rot.from_quat([bq[1, i], bq[2, i], bq[3, i], bq[0, i]])
         Rl = Rot.from_quat([y[i, 4], y[i, 5], y[i, 6], y[i, 3]])
-        want = (Rf * Rl).as_matrix()
+        want = (Rb * Rl).as_matrix()
         q = out["quats"][:, i]
         got = Rot.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
         assert np.allclose(got, want, atol=1e-12)
-    t = oracle.make_targets(fq, out["log_scales"], out["quats"], out["opacity_logits"])
-    back = oracle.apply_mlp(t, fq)
+    assert np.allclose(out["log_scales"], base["log_scales"] + y[:, 0:3].T)
+    assert np.allclose(out["opacity_logits"], base["opacity_logits"] + y[:, 7])
+    ident = np.zeros((n, 8))
+    ident[:, 3] = 2.5  # any positive multiple of the identity rotation
+    same = oracle.apply_mlp(ident, base)
+    assert np.allclose(same["quats"], bq, atol=1e-15) and np.array_equal(same["log_scales"], base["log_scales"])
+    t = oracle.make_targets(base, out)
+    back = oracle.apply_mlp(t, base)
     assert np.allclose(np.abs(np.sum(back["quats"] * out["quats"], axis=0)), 1.0, atol=1e-12)
     assert np.allclose(back["log_scales"], out["log_scales"]) and np.allclose(back["opacity_logits"], out["opacity_logits"])
