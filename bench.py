@@ -46,6 +46,26 @@ FLOPS_ALPHA = 16        # one alpha evaluation of a (pixel, entry)
 FLOPS_FWD_COMP = 10     # compositing of an entry that passes the alpha test
 FLOPS_BWD_COMP = 38     # Eq. 8 + chain to the nine screen-space gradients of a composited entry
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel on this workload, with a
+# digest of the sources it was taken on: reported only while those sources are unchanged.
+NCU_TRAFFIC = {
+    "composite_bwd": (88_407_808 + 3_389_952, "60a0bc4555796ea0",
+                      ("paper_2601_17354_gb300/csrc/composite.cu", "paper_2601_17354_gb300/csrc/pgs_internal.cuh")),
+}
+
+
+def ncu_traffic(kernel: str):
+    import hashlib
+    entry = NCU_TRAFFIC.get(kernel)
+    if entry is None:
+        return None
+    nbytes, digest, files = entry
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest()[:16] == digest else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -55,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched 16-scene x 4-view measurement")
+                    help="skip the batched 16-scene x 4-view and initializer measurements")
     ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: one capacity probe, random targets, --steps "
@@ -263,6 +283,53 @@ def run_batched(steps: int, warmup: int) -> dict:
             "mean_l1": float(losses[:, 0].mean())}
 
 
+def run_initializer(reps: int = 5) -> dict:
+    """The learned initializer's kernels at the 32-scene x 200k-point scale: 32-nearest-neighbour
+    search + features + the paper's seeding for one 200k-point scene, MLP inference over the
+    6.4 M feature rows of 32 scenes, and one training step (gradient over a 65,536-row batch +
+    Adam).  Tensor-core roofline of the MLP: 2 (16*64 + 64*64 + 64*8) flops per row forward."""
+    import torch
+    from paper_2601_17354_gb300 import initializer as I
+    from paper_2601_17354_gb300 import synthetic as S
+    rng = np.random.default_rng(5)
+    pts = torch.from_numpy(np.ascontiguousarray(
+        S.sample_surface_points(rng, S.random_surfaces(rng), 200_000).astype(np.float32))).cuda()
+    init = I.Initializer()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(k):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    holder = {}
+    ms_init = timed(lambda: holder.__setitem__("pi", init.paper_init(pts, 3)), reps)
+    x = holder["pi"].features_bf16.repeat(32, 1).contiguous()          # 6.4 M rows
+    mlp = I.MLP(init, seed=1)
+    ms_fwd = timed(lambda: mlp.forward(x), reps)
+    xb, tb = x[:65536].contiguous(), torch.zeros(65536, 8, device="cuda")
+    tb[:, 3] = 1.0
+
+    def train_step():
+        mlp.accumulate_grad(xb, tb)
+        mlp.adam(1e-3)
+    ms_train = timed(train_step, reps)
+    peaks, _ = measured_peaks()
+    flops = 2 * (16 * 64 + 64 * 64 + 64 * 8)
+    fwd_tflops = x.shape[0] * flops / (ms_fwd * 1e-3) / 1e12
+    return {"points": int(pts.shape[1]), "knn_features_seed_ms": ms_init,
+            "mlp_forward": {"rows": int(x.shape[0]), "ms": ms_fwd, "rows_per_s": x.shape[0] / (ms_fwd * 1e-3),
+                            "tflops": fwd_tflops, "bf16_peak_tflops": float(peaks["bf16_tflops"]),
+                            "frac": fwd_tflops / float(peaks["bf16_tflops"]),
+                            "hbm_gbs": x.shape[0] * (32 + 32) / (ms_fwd * 1e-3) / 1e9},
+            "mlp_train_step": {"rows": 65536, "ms": ms_train}}
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -386,7 +453,7 @@ def run_ours(args):
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     b, a, pk, u = roof[dom]
     roofline = {"kernel": dom, "bound": b, "achieved": a, "peak": pk, "unit": u, "frac": a / pk,
-                "traffic": None, "peak_source": f"{src}" if b == "hbm" else
+                "traffic": ncu_traffic(dom), "peak_source": f"{src}" if b == "hbm" else
                 f"{sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src} max clock)"}
 
     out = {
@@ -409,6 +476,7 @@ def run_ours(args):
     }
     if not args.no_batched:
         out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))
+        out["initializer"] = run_initializer()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",
