@@ -82,7 +82,7 @@ struct AdamArgs {
     float lr[6];
     int64_t n;
     int K;
-    float b1, b2, omb1, omb2, eps, bc1, bc2;  // omb = 1 - b, formed in double on the host
+    float b1, b2, omb1, omb2, eps, isb;  // omb = 1 - b, isb = 1 / sqrt(1 - b2^t), in double on the host
 };
 
 // row r of the (11 + 3K) x n parameter matrix -> group, row inside the group, learning rate
@@ -94,12 +94,10 @@ __device__ __forceinline__ void row_of(const AdamArgs& a, int r, int& grp, int& 
     else { grp = 4; sub = r - 11; lr = (sub % a.K) == 0 ? a.lr[4] : a.lr[5]; }
 }
 
+// lr: the row's learning rate already divided by 1 - b1^t
 __device__ __forceinline__ void adam1(float& p, float& g, float& m, float& v, float lr,
                                       const AdamArgs& a) {
-    m = a.b1 * m + a.omb1 * g;
-    v = a.b2 * v + a.omb2 * g * g;
-    const float mh = m / a.bc1, vh = v / a.bc2;
-    p -= lr * mh / (sqrtf(vh) + a.eps);
+    adam_update(p, m, v, g, a.b1, a.b2, a.omb1, a.omb2, lr, a.isb, a.eps);
     g = 0.0f;
 }
 
@@ -246,7 +244,8 @@ int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussi
             vec = vec && aligned16(ptrs[k]);
         }
     }
-    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    const double bc1 = 1.0 - pow((double)b1, (double)t), bc2 = 1.0 - pow((double)b2, (double)t);
+    for (int k = 0; k < 6; ++k) a.lr[k] = (float)((double)lr[k] / bc1);
     a.n = p.n;
     a.K = sh_coeffs(p.sh_degree);
     a.b1 = b1;
@@ -254,8 +253,7 @@ int launch_adam(pgs_gaussians& p, pgs_gaussians& g, pgs_gaussians& m, pgs_gaussi
     a.omb1 = (float)(1.0 - (double)b1);
     a.omb2 = (float)(1.0 - (double)b2);
     a.eps = eps;
-    a.bc1 = (float)(1.0 - pow((double)b1, (double)t));
-    a.bc2 = (float)(1.0 - pow((double)b2, (double)t));
+    a.isb = (float)(1.0 / sqrt(bc2));
     const int rows = param_rows(p.sh_degree);
     const int64_t work = vec ? (p.n >> 2) : p.n;
     int64_t bx = (work + kThreads - 1) / kThreads;

@@ -93,6 +93,24 @@ struct SceneDesc {
     int64_t gauss_base;  // first Gaussian of the scene in the batch-wide Gaussian numbering
 };
 
+// One Adam update (Kingma & Ba 2015) of parameter p with gradient g.  The bias corrections are
+// folded into two per-step constants formed in double: lr_hat = lr / (1 - b1^t) and
+// isb = 1 / sqrt(1 - b2^t), so p -= lr_hat m / (sqrt(v) isb + eps), which is algebraically the
+// textbook lr m^ / (sqrt(v^) + eps).  The square root and the reciprocal use the approximate
+// special-function instructions (relative error about 2^-22, far below the step's own scale);
+// every other operation is an explicitly rounded fp32 multiply or fma, so the update is the same
+// in every translation unit whatever its contraction flags.
+__device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float b1, float b2,
+                                            float omb1, float omb2, float lr_hat, float isb, float eps) {
+    m = __fmaf_rn(b1, m, __fmul_rn(omb1, g));
+    v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(omb2, g), g));
+    float s, r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(v));
+    const float den = __fmaf_rn(s, isb, eps);
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(den));
+    p = __fmaf_rn(-lr_hat, __fmul_rn(m, r), p);
+}
+
 // Compositing kernel variant: pixels per thread and entries staged per batch.
 struct CompositeVariant {
     int pix, depth;

@@ -537,8 +537,8 @@ k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
 // each Gaussian (zero for culled ones) is consumed in registers by the Adam update of its 11 + 3K
 // parameters, so it never round-trips through memory.
 struct AdamStep {
-    float lr[6];
-    float b1, b2, omb1, omb2, eps, bc1, bc2;
+    float lr[6];  // learning rates already divided by 1 - b1^t
+    float b1, b2, omb1, omb2, eps, isb;  // isb = 1 / sqrt(1 - b2^t)
 };
 
 template <int DEG>
@@ -573,10 +573,8 @@ k_project_bwd_adam(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians m,
             if (r < ROWS) {
                 const int gi = row_group(r);
                 const float lr = gi < 4 ? a.lr[gi] : (row_sub(r) % K == 0 ? a.lr[4] : a.lr[5]);
-                const float gr = grad_row<DEG>(gp, r);
-                mm[j] = a.b1 * mm[j] + a.omb1 * gr;
-                vv[j] = a.b2 * vv[j] + a.omb2 * gr * gr;
-                pp[j] -= lr * (mm[j] / a.bc1) / (sqrtf(vv[j] / a.bc2) + a.eps);
+                adam_update(pp[j], mm[j], vv[j], grad_row<DEG>(gp, r), a.b1, a.b2, a.omb1, a.omb2, lr,
+                            a.isb, a.eps);
                 const int64_t idx = (int64_t)row_sub(r) * n + i;
                 Pp.g[gi][idx] = pp[j];
                 Mm.g[gi][idx] = mm[j];
@@ -619,12 +617,13 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int ROWS = 11 + 3 * K;
     extern __shared__ float s_acc[];  // [ROWS][kProjBlock]
-    __shared__ float s_bc[2];
+    __shared__ float s_lr[6], s_isb;
     __shared__ int s_skip;
     if (threadIdx.x == 0) {
         const double t = (double)(*step + 1);
-        s_bc[0] = (float)(1.0 - pow((double)a.b1, t));
-        s_bc[1] = (float)(1.0 - pow((double)a.b2, t));
+        const double bc1 = 1.0 - pow((double)a.b1, t), bc2 = 1.0 - pow((double)a.b2, t);
+        for (int q = 0; q < 6; ++q) s_lr[q] = (float)((double)a.lr[q] / bc1);
+        s_isb = (float)(1.0 / sqrt(bc2));
         s_skip = (*sc.status & kStatusCapacity) != 0;
     }
     const int64_t k = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
@@ -632,7 +631,7 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] = 0.f;
     __syncthreads();
-    const float bc1 = s_bc[0], bc2 = s_bc[1];
+    const float isb = s_isb;
     if (k >= gauss_total || s_skip) return;
     const SceneDesc& sd = scenes[scene_of(scenes, S, k)];
     const int64_t i = k - sd.gauss_base;
@@ -665,11 +664,9 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
             const int r = r0 + q;
             if (r < ROWS) {
                 const int gi = row_group(r);
-                const float lr = gi < 4 ? a.lr[gi] : (row_sub(r) % K == 0 ? a.lr[4] : a.lr[5]);
-                const float gr = acc[r * kProjBlock];
-                mm[q] = a.b1 * mm[q] + a.omb1 * gr;
-                vv[q] = a.b2 * vv[q] + a.omb2 * gr * gr;
-                pp[q] -= lr * (mm[q] / bc1) / (sqrtf(vv[q] / bc2) + a.eps);
+                const float lr = gi < 4 ? s_lr[gi] : (row_sub(r) % K == 0 ? s_lr[4] : s_lr[5]);
+                adam_update(pp[q], mm[q], vv[q], acc[r * kProjBlock], a.b1, a.b2, a.omb1, a.omb2, lr, isb,
+                            a.eps);
                 const int64_t idx = (int64_t)row_sub(r) * n + i;
                 Pp.g[gi][idx] = pp[q];
                 Mm.g[gi][idx] = mm[q];
@@ -713,14 +710,14 @@ int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
     if (blocks == 0) return 0;
     AdamStep a;
-    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    const double bc1 = 1.0 - pow((double)b1, (double)t), bc2 = 1.0 - pow((double)b2, (double)t);
+    for (int k = 0; k < 6; ++k) a.lr[k] = (float)((double)lr[k] / bc1);
     a.b1 = b1;
     a.b2 = b2;
     a.omb1 = (float)(1.0 - (double)b1);
     a.omb2 = (float)(1.0 - (double)b2);
     a.eps = eps;
-    a.bc1 = (float)(1.0 - pow((double)b1, (double)t));
-    a.bc2 = (float)(1.0 - pow((double)b2, (double)t));
+    a.isb = (float)(1.0 / sqrt(bc2));
     switch (g.sh_degree) {
         case 0: k_project_bwd_adam<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
         case 1: k_project_bwd_adam<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, sc, m, v, a); break;
