@@ -137,7 +137,8 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
 int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
 
 /* Internal buffers of the last render/backward, copied to `dst` (host or device) for inspection.
-   which: PGS_BUF_KEYS (uint64 [P], sorted), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
+   which: PGS_BUF_KEYS (uint64 [P], sorted keys (tile << 32) | depth bits, assembled from the
+   sorted tile ids and the Gaussians' depths), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
    (uint32 [tiles][2]), PGS_BUF_T_FINAL (float [H][W]), PGS_BUF_LAST (uint32 [H][W]),
    PGS_BUF_GRAD2D (float [9][n]: du, dv, d conic a, b, c, d opacity, d r, g, b),
    PGS_BUF_TILES_TOUCHED (uint32 [n]), PGS_BUF_NCOMP (uint32 [H][W], entries composited per

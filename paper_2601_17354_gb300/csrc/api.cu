@@ -452,7 +452,7 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
     const void* src = nullptr;
     int64_t size = 0;
     switch (which) {
-        case PGS_BUF_KEYS: src = ctx->sc.keys[ctx->buf]; size = 8 * kept; break;
+        case PGS_BUF_KEYS: src = ctx->sc.keys[ctx->buf ^ 1]; size = 8 * kept; break;
         case PGS_BUF_VALUES: src = ctx->sc.vals[ctx->buf]; size = 4 * kept; break;
         case PGS_BUF_RANGES: src = ctx->sc.ranges; size = 8 * (int64_t)ctx->TX * ctx->TY; break;
         case PGS_BUF_T_FINAL: src = ctx->sc.T_final; size = 4 * pixels; break;
@@ -463,6 +463,9 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
         default: return PGS_ERR_INVALID_ARG;
     }
     if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    // the sorted pair buffer holds tile ids: join each pair's depth bits into the free ping-pong
+    // key buffer (the backward reads only the values and ranges)
+    if (which == PGS_BUF_KEYS) launch_join_keys(ctx->cap_pairs, ctx->buf, ctx->sc, s);
     if (bytes) *bytes = size;
     const int64_t cp = size < max_bytes ? size : max_bytes;
     if (cp > 0 && dst) {

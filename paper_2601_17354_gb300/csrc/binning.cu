@@ -7,12 +7,16 @@
 //
 // key = (tile << 32) | float bits of the camera depth (depth > near > 0, so the bits order like
 // the depths); equal keys keep emission order (canonical order), so the sort is the stable sort
-// of the pairs.  The number of pairs is known only on the device: every kernel reads it from the
+// of the pairs.  The Gaussians are first sorted by depth (32-bit depth keys) and the pairs are
+// emitted in that order, so the pair sort only has to order the 32-bit tile part stably: the
+// pair buffers hold tile ids (uint32), and the full 64-bit key of a sorted pair is
+// (tile << 32) | depth bits of its Gaussian.  The number of pairs is known only on the device: every kernel reads it from the
 // context's pair counter, and pairs beyond the capacity are not written (the status word records
 // the overflow), so no host synchronisation sits between projection and compositing.
 //
 // The radix sort is least-significant-digit first, 8-bit digits, over the bits that can be
-// non-zero (32 depth bits + ceil(log2 tiles) tile bits).  Each pass: per-CTA digit histogram,
+// non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; 64-bit
+// keys for the allocation-free entry point).  Each pass: per-CTA digit histogram,
 // per-digit scan across CTAs (digit totals come from one up-front histogram of all passes),
 // and a stable scatter that ranks keys inside a CTA with warp match-any (no inter-CTA waiting).
 #include "pgs_internal.cuh"
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(kProjBlock)
 k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
        const RenderDesc* __restrict__ renders, int R) {
     __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of counts
-    __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock], s_depth[kProjBlock];
+    __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock];
     __shared__ uint32_t s_tx[kProjBlock], s_tbase[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -113,7 +117,6 @@ k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, S
             s_x0[t] = r.x & 0xffffu;
             s_y0[t] = r.x >> 16;
             s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
-            s_depth[t] = sc.depth_bits[g];
             s_tx[t] = (uint32_t)TX;
             s_tbase[t] = 0;
             if (renders) {  // batch: item g belongs to the last render whose first item is <= g
@@ -165,7 +168,7 @@ k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, S
         const uint32_t tile = s_tbase[lo] + (s_y0[lo] + dy) * s_tx[lo] + s_x0[lo] + dx;
         const unsigned long long pos = base + k;
         if (pos < (unsigned long long)capacity) {
-            sc.keys[0][pos] = ((unsigned long long)tile << 32) | s_depth[lo];
+            reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
             sc.vals[0][pos] = s_gid[lo];
         }
     }
@@ -181,9 +184,9 @@ __device__ __forceinline__ uint64_t kept_pairs(const Scratch& sc, int64_t capaci
 }
 
 // digit totals of every pass (digits from bit first_shift up) in one read of the keys
+template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
-k_digit_totals(int64_t capacity, int first_shift, int passes,
-               const unsigned long long* __restrict__ keys, Scratch sc) {
+k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __restrict__ keys, Scratch sc) {
     __shared__ uint32_t h[kMaxPasses][kRadix];
     for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
@@ -202,8 +205,9 @@ k_digit_totals(int64_t capacity, int first_shift, int passes,
 }
 
 // per-CTA histogram of one digit
+template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_hist(int64_t capacity, int shift, int sb_max, const unsigned long long* __restrict__ keys, Scratch sc) {
+k_sort_hist(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ keys, Scratch sc) {
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
     __shared__ uint32_t h[kRadix];
@@ -213,7 +217,7 @@ k_sort_hist(int64_t capacity, int shift, int sb_max, const unsigned long long* _
     const uint64_t begin = (uint64_t)blockIdx.x * kSortTile;
     const uint64_t end = begin + kSortTile < P ? begin + kSortTile : P;
     for (uint64_t k = begin + threadIdx.x; k < end; k += kSortThreads)
-        atomicAdd(&h[(keys[k] >> shift) & (kRadix - 1)], 1u);
+        atomicAdd(&h[(uint32_t)(keys[k] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
     sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x] = h[threadIdx.x];
 }
@@ -274,17 +278,19 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kWarpItems = kSortTile / kSortWarps;  // contiguous keys per warp
 constexpr int kRounds = kWarpItems / 32;            // == kSortItems
-constexpr size_t kScatterSmem = sizeof(unsigned long long) * kSortTile + sizeof(uint32_t) * kSortTile;
+template <typename KeyT>
+constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSortTile; }
 
+template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long* __restrict__ kin,
-               const uint32_t* __restrict__ vin, unsigned long long* __restrict__ kout,
-               uint32_t* __restrict__ vout, Scratch sc) {
+k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ kin,
+               const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
+               Scratch sc) {
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(s_dyn);
-    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(unsigned long long) * kSortTile);
+    KeyT* s_keys = reinterpret_cast<KeyT*>(s_dyn);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KeyT) * kSortTile);
     __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_gofs[kRadix];            // global offset of this CTA's run of digit d
     __shared__ uint32_t s_bstart[kRadix];          // start of digit d inside the CTA's reordering
@@ -297,14 +303,14 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
     const uint64_t cbase = (uint64_t)blockIdx.x * kSortTile;
     const uint64_t wbase = cbase + (uint64_t)warp * kWarpItems;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long key[kRounds];
+    KeyT key[kRounds];
     uint32_t val[kRounds];
     uint32_t dr[kRounds];  // digit | warp-local rank << 8
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         const bool valid = idx < P;
-        key[r] = valid ? kin[idx] : 0ull;
+        key[r] = valid ? kin[idx] : (KeyT)0;
         val[r] = valid ? vin[idx] : 0u;
         const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : 0x100u + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -356,8 +362,8 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
     __syncthreads();
     const uint32_t count = (uint32_t)min((uint64_t)kSortTile, P - cbase);
     for (uint32_t p = threadIdx.x; p < count; p += kSortThreads) {
-        const unsigned long long k = s_keys[p];
-        const uint32_t d = (uint32_t)((k >> shift) & (kRadix - 1));
+        const KeyT k = s_keys[p];
+        const uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
         const uint64_t dst = (uint64_t)s_gofs[d] + (p - s_bstart[d]);
         if (dst < P) {
             kout[dst] = k;
@@ -372,17 +378,26 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const unsigned long long
 // K5: tile ranges [first, last + 1) from the sorted keys (ranges pre-zeroed)
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_ranges(int64_t capacity, uint32_t tiles, const unsigned long long* __restrict__ keys, Scratch sc) {
+k_ranges(int64_t capacity, uint32_t tiles, const uint32_t* __restrict__ keys, Scratch sc) {
     const uint64_t P = kept_pairs(sc, capacity);
     for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256) {
-        const uint32_t t = (uint32_t)(keys[k] >> 32);
+        const uint32_t t = keys[k];
         if (t >= tiles) {
             atomicOr(sc.status, kStatusInternal);
             continue;
         }
-        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != t) sc.ranges[t].x = (uint32_t)k;
-        if (k == P - 1 || (uint32_t)(keys[k + 1] >> 32) != t) sc.ranges[t].y = (uint32_t)(k + 1);
+        if (k == 0 || keys[k - 1] != t) sc.ranges[t].x = (uint32_t)k;
+        if (k == P - 1 || keys[k + 1] != t) sc.ranges[t].y = (uint32_t)(k + 1);
     }
+}
+
+// the full keys of the sorted pairs, (tile << 32) | depth bits of the pair's Gaussian
+__global__ void __launch_bounds__(256)
+k_join_keys(int64_t capacity, const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
+            unsigned long long* __restrict__ out, Scratch sc) {
+    const uint64_t P = kept_pairs(sc, capacity);
+    for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256)
+        out[k] = ((unsigned long long)tiles[k] << 32) | sc.depth_bits[vals[k]];
 }
 
 // One CTA: counting sort of the tiles into 64 half-octave buckets of their list length,
@@ -426,13 +441,42 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch
 
 }  // namespace
 
-// the scatter reorders a whole CTA tile of pairs in dynamic shared memory (48 KB)
+// the scatter reorders a whole CTA tile of pairs in dynamic shared memory (32 KB with 32-bit
+// keys, 48 KB with 64-bit keys)
 void enable_scatter_smem() {
     static bool done = [] {
-        cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem);
+        cudaFuncSetAttribute(k_sort_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<uint32_t>());
+        cudaFuncSetAttribute(k_sort_scatter<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<unsigned long long>());
         return true;
     }();
     (void)done;
+}
+
+// LSD passes over the keys in keys[0] / keys[1] (viewed as KeyT) starting at bit first_shift;
+// returns the launches and leaves the sorted buffer's index in *out_buf
+template <typename KeyT>
+int sort_passes(int64_t capacity, int first_shift, int passes, const Scratch& sc, cudaStream_t s, int* out_buf) {
+    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
+    const int grid_stride_blocks = 152 * 8;
+    int buf = 0;
+    *out_buf = 0;
+    if (sb_max <= 0 || passes <= 0) return 0;
+    enable_scatter_smem();
+    KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
+    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
+    k_digit_totals<KeyT><<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, k[0], sc);
+    for (int p = 0; p < passes; ++p) {
+        const int shift = first_shift + p * kRadixBits;
+        k_sort_hist<KeyT><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, k[buf], sc);
+        k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
+        k_sort_scatter<KeyT><<<sb_max, kSortThreads, scatter_smem<KeyT>(), s>>>(
+            capacity, shift, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
+        buf ^= 1;
+    }
+    *out_buf = buf;
+    return 1 + 3 * passes;
 }
 
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
@@ -450,9 +494,8 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     d.digit_totals = sc.dtotals;
     d.pair_count = sc.dcount;
     d.sort_blocks = sc.dblocks;
-    cudaMemsetAsync(sc.dtotals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
     int buf = 0;
-    const int launched = launch_radix_sort_only(n, 32, d, s, &buf);
+    const int launched = sort_passes<uint32_t>(n, 0, 32 / kRadixBits, d, s, &buf);
     *perm = sc.dvals[buf];
     return launched;
 }
@@ -470,52 +513,30 @@ int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, 
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* out_buf) {
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)tiles) ++tile_bits;
-    // the pairs arrive in depth order: a stable sort by the tile bits (32 and up) completes it
+    // the pairs arrive in depth order: a stable sort of their 32-bit tile keys completes it
     const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
-    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
-    const int grid_stride_blocks = 152 * 8;
-    int buf = 0, launched = 0;
-    enable_scatter_smem();
-    if (sb_max > 0 && passes > 0) {
-        cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
-        k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 32, passes, sc.keys[0], sc);
-        launched += 1 + 3 * passes;
-        for (int p = 0; p < passes; ++p) {
-            const int shift = 32 + p * kRadixBits;
-            k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
-            k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-            k_sort_scatter<<<sb_max, kSortThreads, kScatterSmem, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
-                                                           sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
-            buf ^= 1;
-        }
-    }
+    int buf = 0;
+    int launched = sort_passes<uint32_t>(capacity, 0, passes, sc, s, &buf);
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
-    if (sb_max > 0) {
-        k_ranges<<<grid_stride_blocks, 256, 0, s>>>(capacity, (uint32_t)tiles, sc.keys[buf], sc);
+    if (capacity > 0) {
+        k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)tiles, reinterpret_cast<const uint32_t*>(sc.keys[buf]), sc);
         ++launched;
     }
     *out_buf = buf;
     return launched;
 }
 
+int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t s) {
+    if (capacity <= 0) return 0;
+    k_join_keys<<<152 * 8, 256, 0, s>>>(capacity, reinterpret_cast<const uint32_t*>(sc.keys[buf]),
+                                         sc.vals[buf], sc.keys[buf ^ 1], sc);
+    return 1;
+}
+
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf) {
-    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
-    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
-    const int grid_stride_blocks = 152 * 8;
-    int buf = 0;
-    enable_scatter_smem();
-    k_digit_totals<<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, 0, passes, sc.keys[0], sc);
-    for (int p = 0; p < passes; ++p) {
-        const int shift = p * kRadixBits;
-        k_sort_hist<<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, sc.keys[buf], sc);
-        k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-        k_sort_scatter<<<sb_max, kSortThreads, kScatterSmem, s>>>(capacity, shift, sb_max, sc.keys[buf], sc.vals[buf],
-                                                       sc.keys[buf ^ 1], sc.vals[buf ^ 1], sc);
-        buf ^= 1;
-    }
-    *out_buf = buf;
-    return 1 + 3 * passes;
+    return sort_passes<unsigned long long>(capacity, 0, (key_bits + kRadixBits - 1) / kRadixBits, sc, s,
+                                           out_buf);
 }
 
 }  // namespace pgs

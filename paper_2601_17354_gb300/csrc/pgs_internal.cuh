@@ -176,6 +176,8 @@ int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, 
 // K4/K5: stable radix sort of the pairs by the tile bits (returns which ping-pong buffer holds
 // the result) and ranges.
 int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
+// the sorted pairs' full 64-bit keys (tile << 32 | depth bits) into keys[buf ^ 1]
+int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t s);
 
 // K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting the
 // low key_bits bits (the pair count is read from sc.pair_count, at most `capacity`); the digit

@@ -272,7 +272,7 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
     if (!finite) atomicOr(sc.status, kStatusNonfinite);
     sc.touched[j] = count;
     // depth-sort input: visible Gaussians by depth bits, culled ones last
-    sc.dkeys[0][j] = count > 0 ? (unsigned long long)sc.depth_bits[j] : 0xffffffffull;
+    reinterpret_cast<uint32_t*>(sc.dkeys[0])[j] = count > 0 ? sc.depth_bits[j] : 0xffffffffu;
     sc.dvals[0][j] = (uint32_t)j;
 }
 
