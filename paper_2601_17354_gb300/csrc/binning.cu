@@ -18,7 +18,7 @@
 // non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; 64-bit
 // keys for the allocation-free entry point).  Each pass: per-CTA digit histogram,
 // per-digit scan across CTAs (digit totals come from one up-front histogram of all passes),
-// and a stable scatter that ranks keys inside a CTA with warp match-any (no inter-CTA waiting).
+// and a stable scatter that ranks keys inside a CTA with warp ballots (no inter-CTA waiting).
 #include "pgs_internal.cuh"
 
 namespace pgs {
@@ -272,7 +272,8 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
 }
 
 // stable scatter of one CTA's keys by one digit: rank each key among the CTA's keys of its
-// digit (warp match-any per 32 consecutive keys, warp prefixes per digit), reorder the CTA's
+// digit (per 32 consecutive keys the lanes of equal digit from one ballot per digit bit, warp
+// prefixes per digit), reorder the CTA's
 // keys by digit in shared memory, then write each digit's run to its global offset, so the
 // global writes are contiguous runs instead of one scattered store per key.
 constexpr int kSortWarps = kSortThreads / 32;
@@ -312,8 +313,16 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
         const bool valid = idx < P;
         key[r] = valid ? kin[idx] : (KeyT)0;
         val[r] = valid ? vin[idx] : 0u;
-        const uint32_t d = valid ? (uint32_t)((key[r] >> shift) & (kRadix - 1)) : 0x100u + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRadix - 1) : 0u;
+        // lanes holding the same digit: one ballot per digit bit (and one for validity)
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         uint32_t before = 0;
         if (valid) before = s_wh[warp][d];
         __syncwarp();
