@@ -255,3 +255,32 @@ class Trainer:
             self.r.backward(self.dl, self.grads)
             self.r.step(self.params, self.grads, self.m, self.v, self.t)
         return self.loss
+
+
+class ImageFeed:
+    """Host images (pinned) fed to training steps through `depth` device buffers that a copy
+    stream of their own fills ahead of use, so the host-to-device copy of the next view overlaps
+    the current step on the copy engine.  put(k, host) queues image k into slot k % depth (after
+    the step that last used the slot); take(k, stream) orders `stream` after that copy and returns
+    the device image; release(k, stream) marks the slot free once `stream`'s queued work is done."""
+
+    def __init__(self, shape, device="cuda", depth: int = 2):
+        self.bufs = [torch.empty(shape, dtype=torch.float32, device=device) for _ in range(depth)]
+        self.copy_stream = torch.cuda.Stream(torch.device(device))
+        self.ready = [torch.cuda.Event() for _ in range(depth)]
+        self.free = [torch.cuda.Event() for _ in range(depth)]
+
+    def put(self, k: int, host: torch.Tensor):
+        s = k % len(self.bufs)
+        self.copy_stream.wait_event(self.free[s])
+        with torch.cuda.stream(self.copy_stream):
+            self.bufs[s].copy_(host, non_blocking=True)
+        self.ready[s].record(self.copy_stream)
+
+    def take(self, k: int, stream: torch.cuda.Stream) -> torch.Tensor:
+        s = k % len(self.bufs)
+        stream.wait_event(self.ready[s])
+        return self.bufs[s]
+
+    def release(self, k: int, stream: torch.cuda.Stream):
+        self.free[k % len(self.bufs)].record(stream)
