@@ -65,7 +65,7 @@ typedef struct {
 } pgs_gaussians;
 
 typedef struct {
-    int32_t tile;          /* screen tile edge in pixels: 16 (the only supported value) */
+    int32_t tile;          /* screen tile edge T in pixels: 8, 16 or 32 (fixed for the context) */
     int32_t reserved_;
     int64_t pair_capacity; /* (tile, Gaussian) pairs the context holds; 0 = grow on demand */
     float adam_b1, adam_b2, adam_eps;
@@ -251,15 +251,22 @@ int pgs_batch_status(pgs_batch* b, int64_t* pairs);
 int64_t pgs_batch_launch_count(const pgs_batch* b);
 
 /* Compositing kernel variant (pixels per thread 1, 2, 4; entries staged per batch 64, 128, 256)
-   of a context or a batch.  Changing a batch's variant drops its captured graph. */
+   of a context or a batch.  A tile of T x T pixels is one CTA of T * T / pixels_per_thread
+   threads: T = 8 takes 1 or 2 pixels per thread, T = 16 takes 1, 2 or 4, T = 32 takes 2 or 4
+   (PGS_ERR_INVALID_ARG otherwise).  Changing a batch's variant drops its captured graph. */
 int pgs_set_variant(pgs_ctx* ctx, int32_t pixels_per_thread, int32_t depth);
 int pgs_batch_set_variant(pgs_batch* b, int32_t pixels_per_thread, int32_t depth);
 /* Autotuner measurement: runs the render part of a step once, then times the forward + backward
    compositing of every variant (reps repetitions, CUDA events on the batch's stream) and writes
-   ms[9] in the order (1,64) (1,128) (1,256) (2,64) ... (4,256).  Parameters are not changed.
+   ms[9] in the order (1,64) (1,128) (1,256) (2,64) ... (4,256); a strip the tile edge does not
+   take (4 pixels at T = 8, 1 pixel at T = 32) gets -1.  Parameters are not changed.
    The caller picks and sets the variant (the library's Python layer caches the choice per GPU
    and workload class). */
 int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms);
+/* Autotuner measurement of the render part of a step (projection, depth sort, key emission, pair
+   sort, ranges, tile order: the part that depends on the tile edge besides the compositing):
+   best of reps timed runs after one warm-up, *ms (host).  Parameters are not changed. */
+int pgs_batch_time_render(pgs_batch* b, int32_t reps, float* ms);
 /* The same measurement for a context, on its last render: the timed forwards write `image`
    ([3][H][W] scratch) and the backwards use dL_dimage [3][H][W]. */
 int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms);

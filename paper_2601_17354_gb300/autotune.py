@@ -1,7 +1,8 @@
-"""Autotuner of the compositing kernels: picks the pixels-per-thread strip (1, 2, 4) and the
-number of list entries staged in shared memory per batch (64, 128, 256) by timing every variant's
-forward + backward on the caller's own workload, and caches the choice in a JSON file keyed by
-GPU and workload class (resolution class and Gaussian count), so later runs skip the timing."""
+"""Autotuner of the rasterizer: picks the screen tile edge (8, 16, 32 pixels), the pixels-per-thread
+strip (1, 2, 4) and the number of list entries staged in shared memory per batch (64, 128, 256) by
+timing them on the caller's own workload (every variant's forward + backward compositing, and per
+tile edge the render part of the step), and caches the choices in a JSON file keyed by GPU and
+workload class (batch shape, resolution class, Gaussian count), so later runs skip the timing."""
 from __future__ import annotations
 
 import json
@@ -53,7 +54,8 @@ def tune_rasterizer(rast, params, cam, dL_dimage: torch.Tensor, cache: str | Non
                     reps: int = 3, force: bool = False) -> tuple:
     """Choose and set the variant for single-view training of `params` through `cam`."""
     path = _cache_path(cache)
-    key = workload_key("single", [resolution_class(cam.width, cam.height)], params.n, params.sh_degree)
+    key = workload_key(f"single-T{rast.tile}", [resolution_class(cam.width, cam.height)], params.n,
+                       params.sh_degree)
     entry = None if force else _load(path).get(key)
     if entry is None:
         rast.render(params, cam)
@@ -71,7 +73,7 @@ def tune_batch(bt, cache: str | None = None, reps: int = 3, force: bool = False)
     path = _cache_path(cache)
     res = [resolution_class(c.width, c.height) for _, c, _ in bt.views]
     n = sum(s.n for s in bt.scenes)
-    key = workload_key(f"batch{len(bt.views)}", res, n, bt.scenes[0].sh_degree)
+    key = workload_key(f"batch{len(bt.views)}-T{bt.tile}", res, n, bt.scenes[0].sh_degree)
     entry = None if force else _load(path).get(key)
     if entry is None:
         t = bt.time_variants(reps)
@@ -81,3 +83,44 @@ def tune_batch(bt, cache: str | None = None, reps: int = 3, force: bool = False)
         _store(path, key, entry)
     bt.set_variant(entry["pixels"], entry["depth"])
     return entry["pixels"], entry["depth"]
+
+
+def tune_batch_tile(scenes: list, views: list, adam=None, tiles=(8, 16, 32), cache: str | None = None,
+                    reps: int = 3, force: bool = False, pair_headroom: float = 1.0):
+    """A BatchTrainer for (scenes, views) with the tile edge and compositing variant that minimise
+    the render part of a step plus the forward + backward compositing, each timed on this workload
+    (parameters are not changed).  pair_headroom > 1 grows the pair capacity over the measured
+    count.  Returns (trainer, tile, (pixels_per_thread, depth))."""
+    from .batch import BatchTrainer
+    path = _cache_path(cache)
+    res = [resolution_class(c.width, c.height) for _, c, _ in views]
+    n = sum(s.n for s in scenes)
+    key = workload_key(f"batch{len(views)}-tile", res, n, scenes[0].sh_degree)
+    entry = None if force else _load(path).get(key)
+
+    def build(T):
+        bt = BatchTrainer(scenes, views, adam=adam, tile=T)
+        if pair_headroom > 1.0:
+            bt.reserve(int(pair_headroom * bt.status()[1]) + 4096)
+        return bt
+
+    if entry is not None and int(entry["tile"]) in tiles:
+        bt = build(int(entry["tile"]))
+        return bt, bt.tile, tune_batch(bt, cache=cache, reps=reps)
+    best, costs = None, {}
+    for T in tiles:
+        bt = build(T)
+        variant = tune_batch(bt, cache=cache, reps=reps, force=force)
+        timed = _load(path).get(workload_key(f"batch{len(views)}-T{T}", res, n, scenes[0].sh_degree), {})
+        comp = timed.get("ms", {}).get(f"{variant[0]}x{variant[1]}")
+        if comp is None:
+            comp = bt.time_variants(reps)[variant]
+        costs[T] = bt.time_render(reps) + comp
+        if best is None or costs[T] < costs[best[0]]:
+            if best is not None:
+                best[1].close()
+            best = (T, bt, variant)
+        else:
+            bt.close()
+    _store(path, key, {"tile": best[0], "ms": {str(t): c for t, c in costs.items()}})
+    return best[1], best[0], best[2]

@@ -17,7 +17,7 @@ class BatchTrainer:
     tuples, given scene by scene."""
 
     def __init__(self, scenes: list, views: list, adam: AdamConfig | None = None,
-                 pair_capacity: int = 0, stream: torch.cuda.Stream | None = None):
+                 pair_capacity: int = 0, stream: torch.cuda.Stream | None = None, tile: int = 16):
         self._lib = L.lib()
         adam = adam or AdamConfig()
         self.scenes = scenes
@@ -44,7 +44,9 @@ class BatchTrainer:
             L.PgsRenderDesc(int(s), 0, camera_struct(c), self.images[k].data_ptr(),
                             self.targets[k].data_ptr(), self.dls[k].data_ptr())
             for k, (s, c, _) in enumerate(views)])
-        cfg = L.PgsConfig(16, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
+        self.tile = int(tile)  # screen tile edge: 8, 16 or 32
+        self.adam = adam
+        cfg = L.PgsConfig(self.tile, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
                           (C.c_float * 6)(*adam.lr))
         self._b = C.c_void_p()
         L.check(self._lib.pgs_batch_create(C.byref(self._b), C.byref(cfg), S, P, M, V, R, D,
@@ -128,9 +130,16 @@ class BatchTrainer:
                 "pgs_batch_set_variant")
         self.captured = False
 
+    def time_render(self, reps: int = 3) -> float:
+        """ms of the render part of a step (projection .. tile order) on the current parameters."""
+        self._enter()
+        ms = C.c_float()
+        L.check(self._lib.pgs_batch_time_render(self._b, int(reps), C.byref(ms)), "pgs_batch_time_render")
+        return float(ms.value)
+
     def time_variants(self, reps: int = 3) -> dict:
         self._enter()
         ms = np.zeros(len(L.VARIANTS), np.float32)
         L.check(self._lib.pgs_batch_time_variants(self._b, int(reps), ms.ctypes.data_as(C.c_void_p)),
                 "pgs_batch_time_variants")
-        return {v: float(t) for v, t in zip(L.VARIANTS, ms)}
+        return {v: float(t) for v, t in zip(L.VARIANTS, ms) if t >= 0}  # -1: not for this tile edge

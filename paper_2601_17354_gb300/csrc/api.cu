@@ -24,6 +24,7 @@ struct pgs_ctx {
     bool has_render = false;
     int64_t n = 0;
     int TX = 0, TY = 0, buf = 0;
+    int tile = kTileDefault;  // tile edge T, fixed at creation
     pgs_camera cam{};
     pgs_gaussians params{};
     CompositeVariant variant = default_variant();
@@ -177,7 +178,7 @@ bool valid_gaussians(const pgs_gaussians* g) {
 
 bool valid_camera(const pgs_camera* c) {
     if (!c || c->width <= 0 || c->height <= 0) return false;
-    if (c->width > 65535 * kTile || c->height > 65535 * kTile) return false;
+    if (c->width > 65535 * 8 || c->height > 65535 * 8) return false;  // tile coordinates fit 16 bits
     return c->fx > 0.f && c->fy > 0.f && c->near_z > 0.f;
 }
 
@@ -203,10 +204,11 @@ const char* pgs_strerror(int code) {
 int pgs_create(pgs_ctx** out, const pgs_config* cfg, void* cuda_stream) {
     if (!out) return PGS_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!cfg || cfg->tile != kTile || cfg->pair_capacity < 0) return PGS_ERR_INVALID_ARG;
+    if (!cfg || !valid_tile(cfg->tile) || cfg->pair_capacity < 0) return PGS_ERR_INVALID_ARG;
     pgs_ctx* ctx = new (std::nothrow) pgs_ctx();
     if (!ctx) return PGS_ERR_OOM;
     ctx->cfg = *cfg;
+    ctx->tile = cfg->tile;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     ctx->grow_pairs = cfg->pair_capacity == 0;
     int rc = reserve_g(ctx, 1, 1, 1);
@@ -230,7 +232,7 @@ void pgs_destroy(pgs_ctx* ctx) {
 
 int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t pair_capacity) {
     if (!ctx || n < 0 || width < 0 || height < 0 || pair_capacity < 0) return PGS_ERR_INVALID_ARG;
-    const int64_t TX = (width + kTile - 1) / kTile, TY = (height + kTile - 1) / kTile;
+    const int64_t T = ctx->tile, TX = (width + T - 1) / T, TY = (height + T - 1) / T;
     int rc = reserve_g(ctx, n, (int64_t)width * height, TX * TY);
     if (rc == PGS_OK) rc = reserve_p(ctx, pair_capacity);
     return rc;
@@ -238,14 +240,14 @@ int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t 
 
 int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out) {
     if (!ctx || !valid_gaussians(params) || !valid_camera(cam) || !image_out) return PGS_ERR_INVALID_ARG;
-    const int TX = (cam->width + kTile - 1) / kTile, TY = (cam->height + kTile - 1) / kTile;
+    const int T = ctx->tile, TX = (cam->width + T - 1) / T, TY = (cam->height + T - 1) / T;
     const int64_t tiles = (int64_t)TX * TY, pixels = (int64_t)cam->width * cam->height;
     int rc = reserve_g(ctx, params->n, pixels, tiles);
     if (rc != PGS_OK) return rc;
     cudaStream_t s = ctx->stream;
     ctx->has_render = false;
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_project_fwd(*params, *cam, TX, TY, ctx->sc, s);
+    ctx->launches += launch_project_fwd(*params, *cam, TX, TY, T, ctx->sc, s);
     const size_t e1 = mark(ctx);
     const uint32_t* perm = nullptr;
     if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm);
@@ -274,7 +276,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
     ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
-    ctx->launches += launch_composite_fwd(*cam, TX, TY, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
+    ctx->launches += launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
     const size_t e4 = mark(ctx);
     span(ctx, PGS_STAGE_PROJECT, e0, e1);
     span(ctx, PGS_STAGE_BIN, e1, e2);
@@ -307,7 +309,7 @@ int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd(ctx->params, ctx->cam, ctx->sc, *grads, s);
     const size_t e2 = mark(ctx);
@@ -345,7 +347,7 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
+    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd_adam(*params, ctx->cam, ctx->sc, *m, *v, ctx->cfg.lr,
                                              ctx->cfg.adam_b1, ctx->cfg.adam_b2, ctx->cfg.adam_eps, t, s);
@@ -402,7 +404,7 @@ int64_t pgs_launch_count(const pgs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int pgs_set_variant(pgs_ctx* ctx, int32_t pixels_per_thread, int32_t depth) {
     const CompositeVariant v{pixels_per_thread, depth};
-    if (!ctx || !valid_variant(v)) return PGS_ERR_INVALID_ARG;
+    if (!ctx || !valid_variant(v, ctx->tile)) return PGS_ERR_INVALID_ARG;
     ctx->variant = v;
     return PGS_OK;
 }
@@ -420,11 +422,15 @@ int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_
     for (int pi = 0; pi < 3; ++pi)
         for (int di = 0; di < 3; ++di, ++idx) {
             const CompositeVariant v{P[pi], D[di]};
+            if (!valid_variant(v, ctx->tile)) {  // no such strip for this tile edge
+                ms[idx] = -1.0f;
+                continue;
+            }
             float best = 1e30f;
             for (int rep = 0; rep < reps + 1; ++rep) {
                 cudaEventRecord(e0, s);
-                launch_composite_fwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, image, s, v);
-                launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, v);
+                launch_composite_fwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, image, s, v);
+                launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, v);
                 cudaEventRecord(e1, s);
                 err = cudaEventSynchronize(e1);
                 if (err != cudaSuccess) break;
@@ -531,12 +537,12 @@ int64_t enqueue_step(pgs_batch* b) {
     cudaStream_t s = b->stream;
     int64_t k = enqueue_render(b);
     cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
-    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work,
+    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc, b->d_work,
                                 false, s, b->variant);
     cudaMemsetAsync(b->d_losses, 0, sizeof(double) * 2 * b->R, s);
     k += launch_loss_batch(b->d_renders, b->R, b->values, b->d_losses, s);
     cudaMemsetAsync(b->sc.grad2d, 0, sizeof(float) * 9 * (size_t)b->items, s);
-    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work + 1,
+    k += launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc, b->d_work + 1,
                                 true, s, b->variant);
     k += launch_bwd_adam_batch(b->d_renders, b->d_scenes, b->S, b->deg, b->gauss, b->items, b->sc,
                                b->cfg.lr, b->cfg.adam_b1, b->cfg.adam_b2, b->cfg.adam_eps, b->d_step, s);
@@ -554,7 +560,7 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
                      void* cuda_stream) {
     if (!out) return PGS_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!cfg || cfg->tile != kTile || n_scenes < 1 || n_renders < 1 || !params || !m || !v ||
+    if (!cfg || !valid_tile(cfg->tile) || n_scenes < 1 || n_renders < 1 || !params || !m || !v ||
         !renders || pair_capacity < 0)
         return PGS_ERR_INVALID_ARG;
     const int deg = params[0].sh_degree;
@@ -597,8 +603,9 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         std::memset(&rd, 0, sizeof(rd));
         rd.cam = d.cam;
         rd.scene = d.scene;
-        rd.TX = (d.cam.width + kTile - 1) / kTile;
-        rd.TY = (d.cam.height + kTile - 1) / kTile;
+        rd.tile = cfg->tile;
+        rd.TX = (d.cam.width + cfg->tile - 1) / cfg->tile;
+        rd.TY = (d.cam.height + cfg->tile - 1) / cfg->tile;
         rd.item_base = b->items;
         rd.n = params[d.scene].n;
         rd.tile_base = b->tiles;
@@ -795,10 +802,34 @@ int64_t pgs_batch_launch_count(const pgs_batch* b) { return b ? b->launches : 0;
 
 int pgs_batch_set_variant(pgs_batch* b, int32_t pixels_per_thread, int32_t depth) {
     const CompositeVariant v{pixels_per_thread, depth};
-    if (!b || !valid_variant(v)) return PGS_ERR_INVALID_ARG;
+    if (!b || !valid_variant(v, b->cfg.tile)) return PGS_ERR_INVALID_ARG;
     if (v.pix != b->variant.pix || v.depth != b->variant.depth) drop_graph(b);
     b->variant = v;
     return PGS_OK;
+}
+
+int pgs_batch_time_render(pgs_batch* b, int32_t reps, float* ms) {
+    if (!b || !ms || reps < 1) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < reps + 1; ++rep) {  // first repetition warms up
+        cudaEventRecord(e0, s);
+        enqueue_render(b);
+        cudaEventRecord(e1, s);
+        err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0 && t < best) best = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return err == cudaSuccess ? PGS_OK : cuda_err(err);
 }
 
 int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms) {
@@ -807,7 +838,7 @@ int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms) {
     enqueue_render(b);
     // a render's forward composite also writes the images the loss needs: run one of each
     cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
-    launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work, false, s, b->variant);
+    launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc, b->d_work, false, s, b->variant);
     cudaMemsetAsync(b->d_losses, 0, sizeof(double) * 2 * b->R, s);
     launch_loss_batch(b->d_renders, b->R, b->values, b->d_losses, s);
     cudaEvent_t e0, e1;
@@ -819,13 +850,17 @@ int pgs_batch_time_variants(pgs_batch* b, int32_t reps, float* ms) {
     for (int pi = 0; pi < 3; ++pi)
         for (int di = 0; di < 3; ++di, ++idx) {
             const CompositeVariant v{P[pi], D[di]};
+            if (!valid_variant(v, b->cfg.tile)) {  // no such strip for this tile edge
+                ms[idx] = -1.0f;
+                continue;
+            }
             float best = 1e30f;
             for (int rep = 0; rep < reps + 1; ++rep) {  // first repetition warms up
                 cudaEventRecord(e0, s);
                 cudaMemsetAsync(b->d_work, 0, 2 * sizeof(uint32_t), s);
-                launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work, false, s, v);
+                launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc, b->d_work, false, s, v);
                 cudaMemsetAsync(b->sc.grad2d, 0, sizeof(float) * 9 * (size_t)b->items, s);
-                launch_composite_batch(b->d_renders, b->R, b->tiles, b->buf, b->items, b->sc, b->d_work + 1, true, s, v);
+                launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc, b->d_work + 1, true, s, v);
                 cudaEventRecord(e1, s);
                 err = cudaEventSynchronize(e1);
                 if (err != cudaSuccess) break;

@@ -88,17 +88,17 @@ struct FwdSmem {
 
 // One tile of the forward.  kPix: pixels per thread (vertical strip); kDepth: entries staged per
 // batch.  Every thread of the CTA calls it with the same job.
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, FwdSmem<kDepth>& S) {
-    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     float4* s_xyo = S.xyo;
     float4* s_s2 = S.s2;
     float4* s_rgb = S.rgb;
     const int W = J.W, H = J.H;
-    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
+    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = J.range;
     const float3 bg = J.bg;
@@ -207,13 +207,13 @@ template <int kDepth>
 struct BwdSmem {
     float4 xyo[kDepth], s2[kDepth], con[kDepth], rgb[kDepth];
     uint32_t id[kDepth];
-    uint32_t wmax[kTilePixels / 32];
+    uint32_t wmax[32];  // per warp (at most 32 warps per CTA)
 };
 
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, BwdSmem<kDepth>& S) {
-    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     float4* s_xyo = S.xyo;
     float4* s_s2 = S.s2;
@@ -225,8 +225,8 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
     const float3 bg = J.bg;
     const float* __restrict__ dL_dimage = J.dL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
+    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
+    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = J.range;
     const size_t plane = (size_t)W * H;
@@ -343,8 +343,9 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
 // ---------------------------------------------------------------------------------------------
 // Paired-pixel tiles (kPix = 2, 4): a thread's strip is processed two pixels at a time with the
 // packed fp32 instructions of sm_100+ (add/sub/mul/fma .rn .f32x2).  Every packed lane rounds
-// exactly as the scalar instruction does, so the alpha, skip and stop decisions and the forward
-// image are bit-identical to the one-pixel tiles; per pixel the work is branch-free (a pixel that
+// exactly as the scalar instruction does and takes the same operands (dx = column - x,
+// dy = row - y per pixel), so the alpha, skip and stop decisions and the forward image are
+// bit-identical to the one-pixel tiles; per pixel the work is branch-free (a pixel that
 // does not composite an entry contributes alpha = 0, which leaves T, C and the colour behind
 // unchanged), and the pair shares one branch.
 struct F2 {
@@ -391,19 +392,22 @@ __device__ __forceinline__ void pair_alpha(F2 dy, F2 DX, F2 ADX2, F2 S2Y, F2 S2Z
     alpha = make_float2(fminf(kAlphaMax, og.x), fminf(kAlphaMax, og.y));
 }
 
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                                const Scratch& sc, FwdSmem<kDepth>& S) {
-    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     constexpr int NP = kPix / 2;
     float4* s_xyo = S.xyo;
     float4* s_s2 = S.s2;
     float4* s_rgb = S.rgb;
     const int W = J.W, H = J.H;
-    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
-    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
+    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
+    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    const float fx = (float)px + 0.5f;
+    F2 FY[NP];  // pixel-centre rows of the pairs: dy = row - y exactly as the one-pixel strips
+#pragma unroll
+    for (int q = 0; q < NP; ++q) FY[q] = f2((float)(py0 + 2 * q) + 0.5f, (float)(py0 + 2 * q + 1) + 0.5f);
     const uint2 range = J.range;
     const float3 bg = J.bg;
     F2 T[NP], C0[NP], C1[NP], C2[NP];
@@ -440,14 +444,13 @@ __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, cons
             const float4 s2 = s_s2[j];
             const float dx = fx - p.x;
             const F2 DX = f2(dx), ADX2 = f2(__fmul_rn(s2.x, __fmul_rn(dx, dx)));
-            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(p.z);
-            const F2 DY0 = f2(fy0 - p.y);
+            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(p.z), Y = f2(p.y);
             const uint32_t pos = base + j - range.x + 1;
             all_done = true;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const int k0 = 2 * q, k1 = 2 * q + 1;
-                const F2 dy = add2(DY0, f2((float)k0, (float)k1));
+                const F2 dy = sub2(FY[q], Y);
                 float2 G, og, a;
                 pair_alpha(dy, DX, ADX2, S2Y, S2Z, O, G, og, a);
                 const bool p0 = !done[k0] && a.x >= kAlphaMin, p1 = !done[k1] && a.y >= kAlphaMin;
@@ -494,10 +497,10 @@ __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, cons
     }
 }
 
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                                const Scratch& sc, BwdSmem<kDepth>& S) {
-    constexpr int kThreads = kTilePixels / kPix;
+    constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     constexpr int NP = kPix / 2;
     float4* s_xyo = S.xyo;
@@ -510,9 +513,12 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
     const float3 bg = J.bg;
     const float* __restrict__ dL_dimage = J.dL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = (J.tile % J.TX) * kTile + (threadIdx.x % kTile);
-    const int py0 = (J.tile / J.TX) * kTile + (threadIdx.x / kTile) * kPix;
-    const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
+    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
+    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    const float fx = (float)px + 0.5f;
+    F2 FY[NP];  // pixel-centre rows of the pairs (as in the forward)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) FY[q] = f2((float)(py0 + 2 * q) + 0.5f, (float)(py0 + 2 * q + 1) + 0.5f);
     const uint2 range = J.range;
     const size_t plane = (size_t)W * H;
     F2 T[NP], g0[NP], g1[NP], g2[NP], B0[NP], B1[NP], B2[NP];
@@ -576,8 +582,7 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
             const float4 s2 = s_s2[j];
             const float dx = fx - pm.x;
             const F2 DX = f2(dx), ADX2 = f2(__fmul_rn(s2.x, __fmul_rn(dx, dx)));
-            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(pm.z);
-            const F2 DY0 = f2(fy0 - pm.y);
+            const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(pm.z), Y = f2(pm.y);
             // per-lane sums over the strip: dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2,
             // dL/dalpha G, alpha T dL/dC (rgb)
             F2 acc[9];
@@ -587,7 +592,7 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const int k0 = 2 * q, k1 = 2 * q + 1;
-                const F2 dy = add2(DY0, f2((float)k0, (float)k1));
+                const F2 dy = sub2(FY[q], Y);
                 float2 G, og, a;
                 pair_alpha(dy, DX, ADX2, S2Y, S2Z, O, G, og, a);
                 const bool p0 = pos < my_last[k0] && a.x >= kAlphaMin;
@@ -652,18 +657,18 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
     }
 }
 
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, FwdSmem<kDepth>& S) {
-    if constexpr (kPix == 1) fwd_tile_scalar<kPix, kDepth>(J, n, vals, sc, S);
-    else fwd_tile_pairs<kPix, kDepth>(J, n, vals, sc, S);
+    if constexpr (kPix == 1) fwd_tile_scalar<kT, kPix, kDepth>(J, n, vals, sc, S);
+    else fwd_tile_pairs<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
-template <int kPix, int kDepth>
+template <int kT, int kPix, int kDepth>
 __device__ __forceinline__ void bwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, BwdSmem<kDepth>& S) {
-    if constexpr (kPix == 1) bwd_tile_scalar<kPix, kDepth>(J, n, vals, sc, S);
-    else bwd_tile_pairs<kPix, kDepth>(J, n, vals, sc, S);
+    if constexpr (kPix == 1) bwd_tile_scalar<kT, kPix, kDepth>(J, n, vals, sc, S);
+    else bwd_tile_pairs<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
 
@@ -693,8 +698,8 @@ __device__ __forceinline__ TileJob batch_job(const RenderDesc& rd, int64_t gt, c
     return J;
 }
 
-template <int kPix, int kDepth>
-__global__ void __launch_bounds__(kTilePixels / kPix)
+template <int kT, int kPix, int kDepth>
+__global__ void __launch_bounds__(kT * kT / kPix)
 k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
                 Scratch sc, float* __restrict__ image) {
     __shared__ FwdSmem<kDepth> S;
@@ -710,11 +715,11 @@ k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     J.T_final = sc.T_final;
     J.last = sc.last;
     J.ncomp = sc.ncomp;
-    fwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+    fwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
-template <int kPix, int kDepth>
-__global__ void __launch_bounds__(kTilePixels / kPix)
+template <int kT, int kPix, int kDepth>
+__global__ void __launch_bounds__(kT * kT / kPix)
 k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
                 Scratch sc, const float* __restrict__ dL_dimage) {
     __shared__ BwdSmem<kDepth> S;
@@ -730,7 +735,7 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     J.T_final = sc.T_final;
     J.last = sc.last;
     J.ncomp = sc.ncomp;
-    bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+    bwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
 // Batched compositing: persistent CTAs take global tiles, heaviest first, until every tile of
@@ -739,8 +744,8 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
 // device work counter (an atomic ticket offset by the grid size; no CTA ever waits for another).
 // Taking the first round from the ticket too let the heaviest tiles gather on a few SMs (the
 // CTAs of one SM reach the ticket together) and left the other SMs idle at the end.
-template <int kPix, int kDepth, bool kBackward>
-__global__ void __launch_bounds__(kTilePixels / kPix)
+template <int kT, int kPix, int kDepth, bool kBackward>
+__global__ void __launch_bounds__(kT * kT / kPix)
 k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_tiles, int64_t n,
                   const uint32_t* __restrict__ vals, Scratch sc, uint32_t* __restrict__ work) {
     __shared__ typename std::conditional<kBackward, BwdSmem<kDepth>, FwdSmem<kDepth>>::type S;
@@ -749,8 +754,8 @@ k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_t
     while (job < total_tiles) {
         const int64_t gt = sc.tile_order[job];
         const TileJob J = batch_job(renders[render_of_tile(renders, R, gt)], gt, sc);
-        if constexpr (kBackward) bwd_tile<kPix, kDepth>(J, n, vals, sc, S);
-        else fwd_tile<kPix, kDepth>(J, n, vals, sc, S);
+        if constexpr (kBackward) bwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
+        else fwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
         __syncthreads();
         if (threadIdx.x == 0) s_job = (int64_t)atomicAdd(work, 1u) + gridDim.x;
         __syncthreads();
@@ -760,32 +765,44 @@ k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_t
 
 }  // namespace
 
-// pixels per thread (1, 2, 4) and staging depth (64, 128, 256 entries) of the compositing
-// kernels; default (2, 256), the autotuner's choice on the 500k-Gaussian 1080p workload.
+// pixels per thread and staging depth (64, 128, 256 entries) of the compositing kernels; default
+// (2, 256), the autotuner's choice on the 500k-Gaussian 1080p workload, valid for every tile edge.
 // PGS_COMPOSITE_PIXELS / PGS_COMPOSITE_DEPTH override the default (read once per process).
 CompositeVariant default_variant() {
     static CompositeVariant v = [] {
         CompositeVariant c{2, 256};
         if (const char* e = getenv("PGS_COMPOSITE_PIXELS")) c.pix = atoi(e);
         if (const char* e = getenv("PGS_COMPOSITE_DEPTH")) c.depth = atoi(e);
-        if (!valid_variant(c)) c = CompositeVariant{2, 256};
+        if (!valid_variant(c, kTileDefault) || !valid_variant(c, 8) || !valid_variant(c, 32))
+            c = CompositeVariant{2, 256};
         return c;
     }();
     return v;
 }
 
-bool valid_variant(CompositeVariant v) {
-    return (v.pix == 1 || v.pix == 2 || v.pix == 4) && (v.depth == 64 || v.depth == 128 || v.depth == 256);
+// Strips per tile edge: T = 8 takes 1 or 2 pixels per thread (64 or 32 threads per tile), T = 16
+// takes 1, 2 or 4 (256, 128, 64 threads), T = 32 takes 2 or 4 (512, 256 threads), so every CTA
+// is whole warps.
+bool valid_variant(CompositeVariant v, int T) {
+    const bool depth = v.depth == 64 || v.depth == 128 || v.depth == 256;
+    if (T == 8) return depth && (v.pix == 1 || v.pix == 2);
+    if (T == 16) return depth && (v.pix == 1 || v.pix == 2 || v.pix == 4);
+    if (T == 32) return depth && (v.pix == 2 || v.pix == 4);
+    return false;
 }
 
-#define PGS_VARIANTS(X) X(1, 64) X(1, 128) X(1, 256) X(2, 64) X(2, 128) X(2, 256) X(4, 64) X(4, 128) X(4, 256)
+#define PGS_VARIANTS(X)                                                                           \
+    X(8, 1, 64) X(8, 1, 128) X(8, 1, 256) X(8, 2, 64) X(8, 2, 128) X(8, 2, 256)                   \
+    X(16, 1, 64) X(16, 1, 128) X(16, 1, 256) X(16, 2, 64) X(16, 2, 128) X(16, 2, 256)             \
+    X(16, 4, 64) X(16, 4, 128) X(16, 4, 256)                                                      \
+    X(32, 2, 64) X(32, 2, 128) X(32, 2, 256) X(32, 4, 64) X(32, 4, 128) X(32, 4, 256)
 
-int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
-#define X(P, D)                                                                                   \
-    if (v.pix == P && v.depth == D) {                                                             \
-        k_composite_fwd<P, D><<<TX * TY, kTilePixels / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+#define X(TT, P, D)                                                                               \
+    if (T == TT && v.pix == P && v.depth == D) {                                                  \
+        k_composite_fwd<TT, P, D><<<TX * TY, TT * TT / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
                                                                   sc.vals[buf], sc, image);      \
         return 1;                                                                                 \
     }
@@ -794,12 +811,12 @@ int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t
     return 0;
 }
 
-int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
-#define X(P, D)                                                                                   \
-    if (v.pix == P && v.depth == D) {                                                             \
-        k_composite_bwd<P, D><<<TX * TY, kTilePixels / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+#define X(TT, P, D)                                                                               \
+    if (T == TT && v.pix == P && v.depth == D) {                                                  \
+        k_composite_bwd<TT, P, D><<<TX * TY, TT * TT / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
                                                                   sc.vals[buf], sc, dL_dimage);  \
         return 1;                                                                                 \
     }
@@ -808,30 +825,30 @@ int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t
     return 0;
 }
 
-template <int P, int D, bool B>
+template <int TT, int P, int D, bool B>
 static int launch_batch_variant(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
                                 int64_t n, const Scratch& sc, uint32_t* work, cudaStream_t s) {
     static int grid = [] {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_batch<P, D, B>, kTilePixels / P, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite_batch<TT, P, D, B>, TT * TT / P, 0);
         return sms * (per_sm > 0 ? per_sm : 1);
     }();
     const int64_t g = grid < total_tiles ? grid : total_tiles;  // every CTA has a first job
     if (g < 1) return 0;
-    k_composite_batch<P, D, B><<<(unsigned)g, kTilePixels / P, 0, s>>>(renders, R, total_tiles, n,
-                                                                      sc.vals[buf], sc, work);
+    k_composite_batch<TT, P, D, B><<<(unsigned)g, TT * TT / P, 0, s>>>(renders, R, total_tiles, n,
+                                                                       sc.vals[buf], sc, work);
     return 1;
 }
 
-int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
+int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int T, int buf,
                            int64_t n, const Scratch& sc, uint32_t* work, bool backward,
                            cudaStream_t s, CompositeVariant v) {
-#define X(P, D)                                                                                   \
-    if (v.pix == P && v.depth == D)                                                               \
-        return backward ? launch_batch_variant<P, D, true>(renders, R, total_tiles, buf, n, sc, work, s) \
-                        : launch_batch_variant<P, D, false>(renders, R, total_tiles, buf, n, sc, work, s);
+#define X(TT, P, D)                                                                               \
+    if (T == TT && v.pix == P && v.depth == D)                                                    \
+        return backward ? launch_batch_variant<TT, P, D, true>(renders, R, total_tiles, buf, n, sc, work, s) \
+                        : launch_batch_variant<TT, P, D, false>(renders, R, total_tiles, buf, n, sc, work, s);
     PGS_VARIANTS(X)
 #undef X
     return 0;

@@ -8,8 +8,9 @@
 
 namespace pgs {
 
-constexpr int kTile = 16;            // screen tile edge (pixels); one 16x16 tile per CTA
-constexpr int kTilePixels = kTile * kTile;
+// screen tile edge T (pixels): 8, 16 (the default) or 32, one tile per compositing CTA
+constexpr int kTileDefault = 16;
+inline bool valid_tile(int T) { return T == 8 || T == 16 || T == 32; }
 constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kernels
 constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
 constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels
@@ -74,7 +75,7 @@ struct RenderDesc {
     pgs_camera cam;
     int32_t scene;
     int32_t TX, TY;
-    int32_t pad_;
+    int32_t tile;        // tile edge T
     int64_t item_base;   // first item: item j of the render = Gaussian j - item_base of the scene
     int64_t n;           // Gaussians of the scene
     int64_t tile_base;   // first batch-wide tile
@@ -115,7 +116,7 @@ __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float 
 struct CompositeVariant {
     int pix, depth;
 };
-bool valid_variant(CompositeVariant v);
+bool valid_variant(CompositeVariant v, int T);
 CompositeVariant default_variant();
 
 // ---------------------------------------------------------------------------------------------
@@ -124,7 +125,7 @@ CompositeVariant default_variant();
 
 // K1: project + cull + SH colour; writes the projected record, depth bits, tile rectangle,
 // tiles touched and the per-CTA sum of tiles touched.
-int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY,
+int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY, int T,
                         const Scratch& sc, cudaStream_t s);
 // K9: chain screen-space gradients (grad2d) to the parameters, added into grads.
 int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
@@ -190,13 +191,13 @@ int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cu
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
-int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v);
-int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int buf, int64_t n,
+int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v);
 // Batched compositing over every tile of every render in one persistent launch; `work` is a
 // zeroed device counter.
-int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int buf,
+int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int T, int buf,
                            int64_t n, const Scratch& sc, uint32_t* work, bool backward,
                            cudaStream_t s, CompositeVariant v);
 

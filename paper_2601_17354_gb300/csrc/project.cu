@@ -205,10 +205,11 @@ __device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3])
     for (int k = 0; k < 3; ++k) c[k] = -(V[k] * V[3] + V[4 + k] * V[7] + V[8 + k] * V[11]);
 }
 
-// Project Gaussian i of g through cam (tile grid TX x TY) and write its record at item j.
+// Project Gaussian i of g through cam (tiles of T x T pixels, grid TX x TY) and write its record at
+// item j.
 template <int DEG>
 __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
-                                             int TX, int TY, int64_t j, const Scratch& sc) {
+                                             int TX, int TY, int T, int64_t j, const Scratch& sc) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     uint32_t count = 0;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
         const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
         vis = isfinite(rad);
         if (vis) {
-            const float tf = (float)kTile;
+            const float tf = (float)T;  // a power of two: the division is an exact scaling
             x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rad), tf)), 0.0f, (float)TX);
             x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rad), tf)), 1.0f), 0.0f, (float)TX);
             y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, rad), tf)), 0.0f, (float)TY);
@@ -278,10 +279,10 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
 
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
-k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, Scratch sc) {
+k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc) {
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    if (i < n) project_item<DEG>(g, i, cam, TX, TY, i, sc);
+    if (i < n) project_item<DEG>(g, i, cam, TX, TY, T, i, sc);
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
         *sc.dblocks = (uint32_t)((n + kSortTile - 1) / kSortTile);
@@ -307,7 +308,7 @@ k_project_fwd_batch(const RenderDesc* __restrict__ renders, int R, const SceneDe
     const int64_t j = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     if (j < items) {
         const RenderDesc& rd = renders[render_of_item(renders, R, j)];
-        project_item<DEG>(scenes[rd.scene].params, j - rd.item_base, rd.cam, rd.TX, rd.TY, j, sc);
+        project_item<DEG>(scenes[rd.scene].params, j - rd.item_base, rd.cam, rd.TX, rd.TY, rd.tile, j, sc);
     }
     if (j == 0) {
         *sc.dcount = (unsigned long long)items;
@@ -678,15 +679,15 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
 
 }  // namespace
 
-int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY,
+int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY, int T,
                        const Scratch& sc, cudaStream_t s) {
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
     if (blocks == 0) return 0;
     switch (g.sh_degree) {
-        case 0: k_project_fwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
-        case 1: k_project_fwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
-        case 2: k_project_fwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
-        default: k_project_fwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, sc); break;
+        case 0: k_project_fwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
+        case 1: k_project_fwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
+        case 2: k_project_fwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
+        default: k_project_fwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
     }
     return 1;
 }

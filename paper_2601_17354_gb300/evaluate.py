@@ -258,6 +258,7 @@ def main(argv=None):
     ap.add_argument("--focal", type=float, default=1000.0)
     ap.add_argument("--fit-steps", type=int, default=1000)
     ap.add_argument("--views-per-step", type=int, nargs="+", default=[1, 2])
+    ap.add_argument("--check-every", type=int, default=5, help="batched steps between PSNR checks")
     args = ap.parse_args(argv)
     t0 = time.time()
     train = list(range(1000, 1000 + args.scenes - args.held_out))
@@ -271,7 +272,8 @@ def main(argv=None):
     for vps in args.views_per_step:
         for learned in (res.learned_init, None):
             tt = time_to_target(held, args.points, args.width, args.height, args.focal, views_per_step=vps,
-                                learned=learned, adam=batched_adam(vps) if vps > 1 else None)
+                                learned=learned, adam=batched_adam(vps) if vps > 1 else None,
+                                check_every=args.check_every)
             out["time_to_plain_psnr"].append(
                 {"views_per_step": vps, "learned": learned is not None,
                  **{k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps", "all_reached", "ratio")}})

@@ -102,12 +102,13 @@ class Rasterizer:
     """A libpocketgs context bound to one CUDA stream (default: the current torch stream)."""
 
     def __init__(self, pair_capacity: int = 0, adam: AdamConfig | None = None,
-                 stream: torch.cuda.Stream | None = None, device="cuda"):
+                 stream: torch.cuda.Stream | None = None, device="cuda", tile: int = 16):
         self._lib = L.lib()
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.tile = int(tile)  # screen tile edge: 8, 16 or 32
         adam = adam or AdamConfig()
-        cfg = L.PgsConfig(16, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
+        cfg = L.PgsConfig(self.tile, 0, int(pair_capacity), adam.b1, adam.b2, adam.eps,
                           (C.c_float * 6)(*adam.lr))
         self._ctx = C.c_void_p()
         L.check(self._lib.pgs_create(C.byref(self._ctx), C.byref(cfg),
@@ -209,7 +210,7 @@ class Rasterizer:
         L.check(self._lib.pgs_time_variants(self._ctx, C.c_void_p(scratch.data_ptr()),
                                             C.c_void_p(dL_dimage.data_ptr()), int(reps),
                                             ms.ctypes.data_as(C.c_void_p)), "pgs_time_variants")
-        return {v: float(t) for v, t in zip(L.VARIANTS, ms)}
+        return {v: float(t) for v, t in zip(L.VARIANTS, ms) if t >= 0}  # -1: not for this tile edge
 
     def launch_count(self) -> int:
         return int(self._lib.pgs_launch_count(self._ctx))

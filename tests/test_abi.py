@@ -43,8 +43,9 @@ def test_invalid_arguments_are_rejected_on_the_host():
     from paper_2601_17354_gb300 import _lib
     L = _lib.lib()
     out = ctypes.c_void_p(123)
-    cfg = _lib.PgsConfig(8, 0, 0, 0.9, 0.999, 1e-15, (ctypes.c_float * 6)(*[1e-3] * 6))
-    assert L.pgs_create(ctypes.byref(out), ctypes.byref(cfg), None) == _lib.PGS_ERR_INVALID_ARG
+    for tile in (12, 64, 0):  # tile edges other than 8, 16, 32 are refused before any CUDA call
+        cfg = _lib.PgsConfig(tile, 0, 0, 0.9, 0.999, 1e-15, (ctypes.c_float * 6)(*[1e-3] * 6))
+        assert L.pgs_create(ctypes.byref(out), ctypes.byref(cfg), None) == _lib.PGS_ERR_INVALID_ARG
     assert out.value is None
     assert L.pgs_render(None, None, None, None) == _lib.PGS_ERR_INVALID_ARG
     assert L.pgs_status(None, None) == _lib.PGS_ERR_INVALID_ARG

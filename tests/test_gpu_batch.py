@@ -164,3 +164,31 @@ def test_pair_overflow_skips_the_step_then_grows(mods):
     assert b.check() == 2 and a.check() == 2
     for x, y in zip(pa, pb):
         assert rel_l2(y.data.cpu().numpy(), x.data.cpu().numpy()) < 1e-4
+
+
+def test_tile_edge_8_batch_matches_single_view_and_tuner_picks_an_edge(mods, tmp_path):
+    """A batch planned with 8x8 tiles renders like single-view contexts with 8x8 tiles, and the
+    tile autotuner returns a trainer with the edge and variant it timed fastest (and caches)."""
+    R, B, A, L = mods
+    scenes, views = small_batch(6)
+    bt, bufs = make_trainer(mods, scenes, views, tile=8)
+    bt.step()
+    torch.cuda.synchronize()
+    assert bt.status()[0] == 0
+    rast = R.Rasterizer(tile=8)
+    for k, (s, cam, _) in enumerate(views):
+        img = rast.render(R.GaussianBuffer.from_arrays(scenes[s].init), cam)
+        assert torch.equal(img, bt.images[k]), k
+    assert bt.time_render(1) > 0
+    cache = str(tmp_path / "tile.json")
+    bufs2 = [R.GaussianBuffer.from_arrays(sc.init) for sc in scenes]
+    tv = [(s, c, torch.from_numpy(t).cuda()) for s, c, t in views]
+    tuned, tile, variant = A.tune_batch_tile(bufs2, tv, cache=cache, reps=1)
+    assert tile in (8, 16, 32) and tuned.tile == tile and variant in L.VARIANTS
+    import json
+    entry = [v for k, v in json.load(open(cache)).items() if "-tile" in k][0]
+    assert entry["tile"] == tile and set(entry["ms"]) == {"8", "16", "32"}
+    tuned.capture()
+    tuned.step()
+    torch.cuda.synchronize()
+    assert tuned.status()[0] == 0
