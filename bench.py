@@ -255,8 +255,7 @@ def run_batched(steps: int, warmup: int) -> dict:
             views.append((s, c, rast.render(gt, c).clone()))
         bufs.append(R.GaussianBuffer.from_arrays(sc.init))
     del rast
-    bt = B.BatchTrainer(bufs, views)
-    variant = A.tune_batch(bt)
+    bt, tile, variant = A.tune_batch_tile(bufs, views)
     bt.capture()
     for _ in range(warmup):
         bt.step()
@@ -278,7 +277,8 @@ def run_batched(steps: int, warmup: int) -> dict:
                         f"resolutions {sorted({f'{c.width}x{c.height}' for _, c, _ in views})}",
             "steps_per_s": 1000.0 / ms, "renders_per_s": len(views) * 1000.0 / ms,
             "ms_per_step": ms, "renders": len(views), "steps": steps, "pairs": int(pairs),
-            "cuda_graph": True, "variant": {"pixels_per_thread": variant[0], "depth": variant[1]},
+            "cuda_graph": True,
+            "variant": {"tile": tile, "pixels_per_thread": variant[0], "depth": variant[1]},
             "gpu_launches": int(bt.launch_count() - launches0),
             "mean_l1": float(losses[:, 0].mean())}
 
@@ -351,19 +351,23 @@ def run_ours(args):
     gt_buf = R.GaussianBuffer.from_arrays(sc.gt)
     targets = [gt_rast.render(gt_buf, c).clone() for c in cams]
     L.check(gt_rast.status()[0], "gt render")
-    # pair capacity: measured on the trainable start over the bench views, with headroom
-    probe = R.Rasterizer()
     init = R.GaussianBuffer.from_arrays(sc.init)
+    del gt_rast, gt_buf
+    # tile edge and compositing variant: the autotuner's choice on this workload
+    from paper_2601_17354_gb300 import autotune as A
+    cand, tile, tuned = A.tune_rasterizer_tile(init, cams[0], torch.ones(3, HEIGHT, WIDTH, device="cuda") * 1e-6)
+    cand.close()
+    # pair capacity: measured on the trainable start over the bench views, with headroom
+    probe = R.Rasterizer(tile=tile)
     pmax = 0
     for c in cams:
         probe.render(init, c)
         pmax = max(pmax, probe.check_status())
-    del probe, gt_rast, gt_buf
-    rast = R.Rasterizer(pair_capacity=int(pmax * 1.5) + 4096)
+    del probe
+    rast = R.Rasterizer(pair_capacity=int(pmax * 1.5) + 4096, tile=tile)
     rast.reserve(N_GAUSS, WIDTH, HEIGHT, int(pmax * 1.5) + 4096)
+    rast.set_variant(*tuned)
     params = init.clone()
-    from paper_2601_17354_gb300 import autotune as A
-    tuned = A.tune_rasterizer(rast, params, cams[0], torch.ones(3, HEIGHT, WIDTH, device="cuda") * 1e-6)
     tr = R.Trainer(params, rast)
     stream = rast.stream
 
@@ -480,7 +484,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "variant": {"pixels_per_thread": tuned[0], "depth": tuned[1]},
+        "variant": {"tile": tile, "pixels_per_thread": tuned[0], "depth": tuned[1]},
     }
     if not args.no_batched:
         out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))

@@ -68,6 +68,49 @@ def tune_rasterizer(rast, params, cam, dL_dimage: torch.Tensor, cache: str | Non
     return entry["pixels"], entry["depth"]
 
 
+def tune_rasterizer_tile(params, cam, dL_dimage: torch.Tensor, adam=None, tiles=(8, 16, 32),
+                         cache: str | None = None, reps: int = 3, force: bool = False):
+    """The tile edge and compositing variant that minimise render + forward and backward
+    compositing time for single-view training of `params` through `cam`, each timed on this
+    workload (the candidates grow their pair buffers on demand).  Returns (rasterizer with that
+    edge and variant, tile, (pixels_per_thread, depth))."""
+    from .rasterizer import Rasterizer
+    path = _cache_path(cache)
+    key = workload_key("single-tile", [resolution_class(cam.width, cam.height)], params.n, params.sh_degree)
+    entry = None if force else _load(path).get(key)
+
+    def build(T):
+        return Rasterizer(adam=adam, tile=T)
+
+    if entry is not None and int(entry["tile"]) in tiles:
+        rast = build(int(entry["tile"]))
+        return rast, rast.tile, tune_rasterizer(rast, params, cam, dL_dimage, cache=cache, reps=reps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best, costs = None, {}
+    for T in tiles:
+        rast = build(T)
+        variant = tune_rasterizer(rast, params, cam, dL_dimage, cache=cache, reps=reps, force=force)
+        timed = _load(path).get(workload_key(f"single-T{T}", [resolution_class(cam.width, cam.height)],
+                                             params.n, params.sh_degree), {})
+        comp = timed.get("ms", {}).get(f"{variant[0]}x{variant[1]}", 0.0)
+        render = []
+        for _ in range(reps + 1):
+            ev0.record(rast.stream)
+            rast.render(params, cam)
+            ev1.record(rast.stream)
+            ev1.synchronize()
+            render.append(ev0.elapsed_time(ev1))
+        costs[T] = min(render[1:]) + comp  # the render includes one forward composite
+        if best is None or costs[T] < costs[best[0]]:
+            if best is not None:
+                best[1].close()
+            best = (T, rast, variant)
+        else:
+            rast.close()
+    _store(path, key, {"tile": best[0], "ms": {str(t): c for t, c in costs.items()}})
+    return best[1], best[0], best[2]
+
+
 def tune_batch(bt, cache: str | None = None, reps: int = 3, force: bool = False) -> tuple:
     """Choose and set the variant of a BatchTrainer's persistent compositing launches."""
     path = _cache_path(cache)

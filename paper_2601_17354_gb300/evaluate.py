@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import synthetic as S
-from .autotune import tune_batch, tune_rasterizer
+from .autotune import tune_batch_tile, tune_rasterizer_tile
 from .initializer import Initializer, LearnedInit, PointInit
 from .rasterizer import DEFAULT_LR, AdamConfig, GaussianBuffer, Rasterizer, Trainer
 
@@ -50,10 +50,11 @@ def eval_psnr(rast: Rasterizer, params: GaussianBuffer, sd: SceneData) -> float:
     return float(np.mean(vals))
 
 
-def pair_capacity(params: GaussianBuffer, sd: SceneData, views: int = 8, headroom: float = 2.0) -> int:
+def pair_capacity(params: GaussianBuffer, sd: SceneData, views: int = 8, headroom: float = 2.0,
+                  tile: int = 16) -> int:
     """A fixed pair capacity for training: the most pairs over the first training views of the
     starting parameters, times the headroom (the pairs grow as the Gaussians train)."""
-    probe = Rasterizer()
+    probe = Rasterizer(tile=tile)
     most = 0
     for v in sd.scene.train_views()[:views]:
         probe.render(params, sd.scene.cameras[v])
@@ -63,13 +64,17 @@ def pair_capacity(params: GaussianBuffer, sd: SceneData, views: int = 8, headroo
 
 
 def tuned_rasterizer(params: GaussianBuffer, sd: SceneData) -> Rasterizer:
-    """A rasterizer for training `params` on `sd`: fixed pair capacity, compositing variant chosen
-    by the autotuner on the first training view."""
-    rast = Rasterizer(pair_capacity=pair_capacity(params, sd))
+    """A rasterizer for training `params` on `sd`: tile edge and compositing variant chosen by the
+    autotuner on the first training view, fixed pair capacity for that edge."""
     v = sd.scene.train_views()[0]
-    img = rast.render(params, sd.scene.cameras[v])
-    dl, _ = rast.loss_l1(img, sd.targets[v])
-    tune_rasterizer(rast, params, sd.scene.cameras[v], dl.clone())
+    probe = Rasterizer()
+    img = probe.render(params, sd.scene.cameras[v])
+    dl, _ = probe.loss_l1(img, sd.targets[v])
+    tuned, tile, variant = tune_rasterizer_tile(params, sd.scene.cameras[v], dl.clone())
+    tuned.close()
+    probe.close()
+    rast = Rasterizer(pair_capacity=pair_capacity(params, sd, tile=tile), tile=tile)
+    rast.set_variant(*variant)
     return rast
 
 
@@ -179,7 +184,6 @@ def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_i
     views_per_step views of each scene per step, learned initializer when given) to reach, for
     every scene, the plain form's held-out PSNR.  adam: the batched form's Adam settings (default:
     the plain form's).  Evaluation renders are not counted."""
-    from .batch import BatchTrainer
     init = learned.init if learned is not None else Initializer()
     scenes = [make_scene(s, n, width, height, focal, n_cameras, sh_degree) for s in seeds]
     plain_psnr, plain_s = [], 0.0
@@ -212,9 +216,7 @@ def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_i
         return out
 
     first = next_views()
-    bt = BatchTrainer(starts, first, adam=adam)
-    bt.reserve(2 * bt.status()[1] + 4096)
-    tune_batch(bt)
+    bt, _, _ = tune_batch_tile(starts, first, adam=adam, pair_headroom=2.0)
     bt.capture()
     eval_rast = Rasterizer()
     reached = [None] * len(scenes)
