@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched 16-scene x 4-view and initializer measurements")
+                    help="skip the batched 16-scene x 4-view, initializer and replay-cache measurements")
     ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: one capacity probe, random targets, --steps "
@@ -330,6 +330,51 @@ def run_initializer(reps: int = 5) -> dict:
             "mlp_train_step": {"rows": 65536, "ms": ms_train}}
 
 
+def run_replay(params, cams, targets, tile: int, reps: int = 20, k_max: int = 256) -> dict:
+    """The paper's replay-cache backward (Eq. 9) against the recompute backward on the bench
+    workload: ms of render + L1 + fused backward/Adam per step and of the two compositing stages,
+    recompute at the same one-pixel strip as the replay kernels and at the tuned strip."""
+    import torch
+    from paper_2601_17354_gb300 import _lib as L
+    from paper_2601_17354_gb300 import rasterizer as R
+    out = {"k_max": k_max, "steps": reps}
+    for name, variant, cache in (("recompute_1x256", (1, 256), 0), ("replay_1x256", (1, 256), k_max)):
+        p = params.clone()
+        probe = R.Rasterizer(tile=tile)
+        probe.render(p, cams[0])
+        cap = int(probe.check_status() * 1.5) + 4096
+        probe.close()
+        rast = R.Rasterizer(pair_capacity=cap, tile=tile)
+        rast.set_variant(*variant)
+        rast.set_replay_cache(cache)
+        tr = R.Trainer(p, rast)
+        for k in range(3):
+            tr.step(cams[k % len(cams)], targets[k % len(targets)])
+        torch.cuda.synchronize()
+        rast.stage_times()
+        rast.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(rast.stream)
+        for k in range(reps):
+            tr.step(cams[k % len(cams)], targets[k % len(targets)])
+        ev1.record(rast.stream)
+        torch.cuda.synchronize()
+        rast.profile(False)
+        st = rast.stage_times()
+        L.check(rast.status()[0], name)
+        entry = {"ms_per_step": ev0.elapsed_time(ev1) / reps,
+                 "composite_fwd_ms": st["composite_fwd"][0] / max(st["composite_fwd"][1], 1),
+                 "composite_bwd_ms": st["composite_bwd"][0] / max(st["composite_bwd"][1], 1)}
+        if cache:
+            ncomp = rast.read_buffer(L.PGS_BUF_NCOMP)
+            entry["cache_bytes"] = int(ncomp.size * (16 * k_max + 4))
+            entry["pixels_over_k_max"] = float(np.mean(ncomp > k_max))
+            entry["composited_entries"] = int(ncomp.sum())
+        out[name] = entry
+        rast.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -489,6 +534,7 @@ def run_ours(args):
     if not args.no_batched:
         out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))
         out["initializer"] = run_initializer()
+        out["replay_cache"] = run_replay(init, cams, targets, tile)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",

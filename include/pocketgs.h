@@ -136,6 +136,18 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
    the last render. */
 int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
 
+/* The paper's replay cache (Sec. III-C, Eq. 9: the per-pixel record S of the forward, with its
+   count reset every render) instead of the recompute backward.  k_max > 0: from the next render
+   on, the forward records for every pixel its first k_max composited entries as 16-byte records
+   {list position, alpha, transmittance in front} ([pixel][k_max], context-owned, allocated at
+   that render; synchronises) and the backward replays them instead of re-evaluating alpha and
+   dividing out the transmittance; pixels that composited more than k_max entries are recomputed
+   (the paper's overflow case).  Compositing then runs one pixel per thread with 256 entries
+   staged per batch (the variant setting is not used).  k_max = 0 (the default) returns to the
+   recompute backward.  Changing the setting invalidates the last render (PGS_ERR_NO_RENDER until
+   the next).  k_max at most 4096. */
+int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max);
+
 /* Internal buffers of the last render/backward, copied to `dst` (host or device) for inspection.
    which: PGS_BUF_KEYS (uint64 [P], sorted keys (tile << 32) | depth bits, assembled from the
    sorted tile ids and the Gaussians' depths), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES

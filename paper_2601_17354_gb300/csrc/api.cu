@@ -25,6 +25,13 @@ struct pgs_ctx {
     int64_t n = 0;
     int TX = 0, TY = 0, buf = 0;
     int tile = kTileDefault;  // tile edge T, fixed at creation
+    // replay cache (pgs_set_replay_cache): K entries per pixel, off when 0
+    int replay_k = 0;
+    bool recorded = false;     // the last render recorded the cache
+    void* arena_c = nullptr;
+    int64_t cap_c = 0;         // pixels x K the cache arena holds
+    float4* c_rec = nullptr;
+    uint32_t* c_count = nullptr;
     pgs_camera cam{};
     pgs_gaussians params{};
     CompositeVariant variant = default_variant();
@@ -170,6 +177,29 @@ int reserve_p(pgs_ctx* ctx, int64_t pairs) {
     return PGS_OK;
 }
 
+// replay cache arena for `pixels` pixels of K entries (16-byte records) plus a count per pixel
+int reserve_c(pgs_ctx* ctx, int64_t pixels) {
+    const int64_t K = ctx->replay_k;
+    if (pixels * K <= ctx->cap_c && ctx->arena_c) return PGS_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (ctx->arena_c) cudaFree(ctx->arena_c);
+    ctx->arena_c = nullptr;
+    ctx->cap_c = 0;
+    const size_t entries = (size_t)(pixels * K);
+    const size_t bytes = align256(16 * entries) + align256(4 * (size_t)pixels);
+    e = cudaMalloc(&ctx->arena_c, bytes);
+    if (e != cudaSuccess) {
+        ctx->arena_c = nullptr;
+        return cuda_err(e);
+    }
+    Carver c{static_cast<char*>(ctx->arena_c)};
+    ctx->c_rec = c.take<float4>(entries);
+    ctx->c_count = c.take<uint32_t>((size_t)pixels);
+    ctx->cap_c = pixels * K;
+    return PGS_OK;
+}
+
 bool valid_gaussians(const pgs_gaussians* g) {
     if (!g || g->n < 0 || g->n >= (int64_t(1) << 32) || g->sh_degree < 0 || g->sh_degree > 3) return false;
     if (g->n == 0) return true;
@@ -227,6 +257,7 @@ void pgs_destroy(pgs_ctx* ctx) {
     for (auto& e : ctx->events) cudaEventDestroy(e);
     if (ctx->arena_g) cudaFree(ctx->arena_g);
     if (ctx->arena_p) cudaFree(ctx->arena_p);
+    if (ctx->arena_c) cudaFree(ctx->arena_c);
     delete ctx;
 }
 
@@ -276,7 +307,16 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
     ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
-    ctx->launches += launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
+    ctx->recorded = false;
+    if (ctx->replay_k > 0) {
+        rc = reserve_c(ctx, pixels);
+        if (rc != PGS_OK) return rc;
+        ctx->launches += launch_composite_replay(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, nullptr,
+                                                 ctx->c_rec, ctx->c_count, ctx->replay_k, false, s);
+        ctx->recorded = true;
+    } else {
+        ctx->launches += launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
+    }
     const size_t e4 = mark(ctx);
     span(ctx, PGS_STAGE_PROJECT, e0, e1);
     span(ctx, PGS_STAGE_BIN, e1, e2);
@@ -302,6 +342,30 @@ int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n
     return cuda_err(cudaGetLastError());
 }
 
+// the backward compositing of the last render: replayed from the cache when it recorded one
+static int composite_backward(pgs_ctx* ctx, const float* dL_dimage) {
+    if (ctx->recorded)
+        return launch_composite_replay(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, nullptr,
+                                       dL_dimage, ctx->c_rec, ctx->c_count, ctx->replay_k, true, ctx->stream);
+    return launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage,
+                                ctx->stream, ctx->variant);
+}
+
+int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max) {
+    if (!ctx || k_max < 0 || k_max > 4096) return PGS_ERR_INVALID_ARG;
+    if (k_max != ctx->replay_k) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_err(e);
+        if (ctx->arena_c) cudaFree(ctx->arena_c);
+        ctx->arena_c = nullptr;
+        ctx->cap_c = 0;
+        ctx->replay_k = k_max;
+        ctx->recorded = false;
+        ctx->has_render = false;  // the next backward needs a render made with this setting
+    }
+    return PGS_OK;
+}
+
 int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
     if (!ctx || !dL_dimage || !valid_gaussians(grads)) return PGS_ERR_INVALID_ARG;
     if (!ctx->has_render) return PGS_ERR_NO_RENDER;
@@ -309,7 +373,7 @@ int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
+    ctx->launches += composite_backward(ctx, dL_dimage);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd(ctx->params, ctx->cam, ctx->sc, *grads, s);
     const size_t e2 = mark(ctx);
@@ -347,7 +411,7 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
     cudaStream_t s = ctx->stream;
     if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, ctx->variant);
+    ctx->launches += composite_backward(ctx, dL_dimage);
     const size_t e1 = mark(ctx);
     ctx->launches += launch_project_bwd_adam(*params, ctx->cam, ctx->sc, *m, *v, ctx->cfg.lr,
                                              ctx->cfg.adam_b1, ctx->cfg.adam_b2, ctx->cfg.adam_eps, t, s);

@@ -81,6 +81,19 @@ struct TileJob {
     uint32_t* ncomp;
 };
 
+// Replay cache of the paper's training operator (the per-pixel record S = {id, C_in, alpha} of
+// Eq. 9 with a per-pixel count reset every render), in front-to-back form: for each pixel the
+// first K composited entries as one 16-byte record {list position | clamp flag << 31, alpha,
+// T in front of the entry, unused}, [pixel][K] (one vector store per recorded entry), and the
+// count (K + 1 when the pixel composited more than K entries: its backward falls back to
+// recomputing).  The colour behind an entry (Eq. 7's C_in) is rebuilt back to front in the
+// backward, as in the recompute path.
+struct ReplayCache {
+    float4* rec = nullptr;
+    uint32_t* count = nullptr;
+    int K = 0;
+};
+
 template <int kDepth>
 struct FwdSmem {
     float4 xyo[kDepth], s2[kDepth], rgb[kDepth];
@@ -88,9 +101,10 @@ struct FwdSmem {
 
 // One tile of the forward.  kPix: pixels per thread (vertical strip); kDepth: entries staged per
 // batch.  Every thread of the CTA calls it with the same job.
-template <int kT, int kPix, int kDepth>
+template <int kT, int kPix, int kDepth, bool kRecord = false>
 __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
-                                         const Scratch& sc, FwdSmem<kDepth>& S) {
+                                         const Scratch& sc, FwdSmem<kDepth>& S, ReplayCache rc = {}) {
+    static_assert(!kRecord || kPix == 1, "the replay cache records one pixel per thread");
     constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     float4* s_xyo = S.xyo;
@@ -146,6 +160,13 @@ __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, con
                         if (Tn < kTMin) {
                             done[k] = true;
                         } else {
+                            if constexpr (kRecord) {
+                                if (ncomp[k] < (uint32_t)rc.K) {
+                                    const uint32_t word = (base + j - range.x) | (og > kAlphaMax ? 0x80000000u : 0u);
+                                    rc.rec[((size_t)(py0 + k) * W + px) * rc.K + ncomp[k]] =
+                                        make_float4(__uint_as_float(word), alpha, T[k], 0.0f);
+                                }
+                            }
                             const float w = alpha * T[k];
                             C0[k] = fmaf(c.x, w, C0[k]);
                             C1[k] = fmaf(c.y, w, C1[k]);
@@ -171,6 +192,7 @@ __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, con
             J.T_final[p] = T[k];
             J.last[p] = last[k];
             J.ncomp[p] = ncomp[k];
+            if constexpr (kRecord) rc.count[p] = ncomp[k] > (uint32_t)rc.K ? (uint32_t)rc.K + 1 : ncomp[k];
         }
     }
 }
@@ -210,9 +232,38 @@ struct BwdSmem {
     uint32_t wmax[32];  // per warp (at most 32 warps per CTA)
 };
 
-template <int kT, int kPix, int kDepth>
+// Eq. 8 for one composited (pixel, entry): the colour behind B is updated by Eq. 7, T becomes
+// the transmittance in front Tb, and the strip's partial sums v gain the nine screen-space
+// gradient terms (mean and conic only when alpha was not clamped at 0.99).
+__device__ __forceinline__ void eq8_accumulate(float alpha, float Tb, float G, bool unclamped, float dx,
+                                               float dy, float4 c, float4 con, float g0, float g1,
+                                               float g2, float& B0, float& B1, float& B2, float& T,
+                                               float v[9]) {
+    const float r0 = c.x - B0, r1 = c.y - B1, r2 = c.z - B2;
+    const float dLda = Tb * (r0 * g0 + r1 * g1 + r2 * g2);
+    const float wgt = alpha * Tb;
+    v[6] = fmaf(wgt, g0, v[6]);
+    v[7] = fmaf(wgt, g1, v[7]);
+    v[8] = fmaf(wgt, g2, v[8]);
+    B0 = fmaf(alpha, r0, B0);
+    B1 = fmaf(alpha, r1, B1);
+    B2 = fmaf(alpha, r2, B2);
+    T = Tb;
+    if (unclamped) {  // zero gradient through the 0.99 clamp
+        v[5] = fmaf(dLda, G, v[5]);
+        const float dpow = dLda * alpha;
+        v[0] = fmaf(dpow, con.x * dx + con.y * dy, v[0]);
+        v[1] = fmaf(dpow, con.z * dy + con.y * dx, v[1]);
+        v[2] = fmaf(dpow, dx * dx, v[2]);
+        v[3] = fmaf(dpow, dx * dy, v[3]);
+        v[4] = fmaf(dpow, dy * dy, v[4]);
+    }
+}
+
+template <int kT, int kPix, int kDepth, bool kReplay = false>
 __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
-                                         const Scratch& sc, BwdSmem<kDepth>& S) {
+                                         const Scratch& sc, BwdSmem<kDepth>& S, ReplayCache rc = {}) {
+    static_assert(!kReplay || kPix == 1, "the replay cache holds one pixel per thread");
     constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     float4* s_xyo = S.xyo;
@@ -233,12 +284,21 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
     float T[kPix], g0[kPix], g1[kPix], g2[kPix], B0[kPix], B1[kPix], B2[kPix];
     uint32_t my_last[kPix];
     uint32_t tmax = 0;
+    // replay state (kReplay): the pixel's next cached record from the back
+    bool replay[kPix];
+    int ci[kPix];
+    float4 cr[kPix];
+    size_t cbase[kPix];
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
         const int py = py0 + k;
         T[k] = 1.0f;
         g0[k] = g1[k] = g2[k] = 0.f;
         my_last[k] = 0;
+        replay[k] = false;
+        ci[k] = -1;
+        cr[k] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+        cbase[k] = 0;
         if (px < W && py < H) {
             const size_t p = (size_t)py * W + px;
             T[k] = J.T_final[p];
@@ -246,6 +306,15 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
             g0[k] = dL_dimage[p];
             g1[k] = dL_dimage[plane + p];
             g2[k] = dL_dimage[2 * plane + p];
+            if constexpr (kReplay) {
+                const uint32_t count = rc.count[p];
+                replay[k] = count <= (uint32_t)rc.K;
+                cbase[k] = p * rc.K;
+                if (replay[k]) {
+                    ci[k] = (int)count - 1;
+                    if (ci[k] >= 0) cr[k] = rc.rec[cbase[k] + ci[k]];
+                }
+            }
         }
         B0[k] = bg.x;  // colour behind the current entry (Eq. 7 C_in)
         B1[k] = bg.y;
@@ -293,32 +362,26 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < kPix; ++k) {
-                if (pos < my_last[k]) {
-                    const float dy = dy0 + (float)k;
+                const float dy = dy0 + (float)k;
+                if (kReplay && replay[k]) {
+                    // cached entry at this position: alpha and T in front from the forward
+                    const uint32_t word = __float_as_uint(cr[k].x);
+                    if (ci[k] >= 0 && (word & 0x7fffffffu) == pos) {
+                        const float alpha = cr[k].y;
+                        contrib = true;
+                        eq8_accumulate(alpha, cr[k].z, __fdividef(alpha, pm.z), (word >> 31) == 0u, dx, dy, c,
+                                       con, g0[k], g1[k], g2[k], B0[k], B1[k], B2[k], T[k], v);
+                        --ci[k];
+                        if (ci[k] >= 0) cr[k] = rc.rec[cbase[k] + ci[k]];
+                    }
+                } else if (pos < my_last[k]) {
                     float G, og;
                     const float alpha = entry_alpha(dx, dy, adx2, s2, pm.z, G, og);
                     if (alpha >= kAlphaMin) {
                         contrib = true;
                         const float Tb = __fdividef(T[k], 1.0f - alpha);  // transmittance in front
-                        const float r0 = c.x - B0[k], r1 = c.y - B1[k], r2 = c.z - B2[k];
-                        const float dLda = Tb * (r0 * g0[k] + r1 * g1[k] + r2 * g2[k]);
-                        const float wgt = alpha * Tb;
-                        v[6] = fmaf(wgt, g0[k], v[6]);
-                        v[7] = fmaf(wgt, g1[k], v[7]);
-                        v[8] = fmaf(wgt, g2[k], v[8]);
-                        B0[k] = fmaf(alpha, r0, B0[k]);
-                        B1[k] = fmaf(alpha, r1, B1[k]);
-                        B2[k] = fmaf(alpha, r2, B2[k]);
-                        T[k] = Tb;
-                        if (og <= kAlphaMax) {  // zero gradient through the 0.99 clamp
-                            v[5] = fmaf(dLda, G, v[5]);
-                            const float dpow = dLda * alpha;
-                            v[0] = fmaf(dpow, con.x * dx + con.y * dy, v[0]);
-                            v[1] = fmaf(dpow, con.z * dy + con.y * dx, v[1]);
-                            v[2] = fmaf(dpow, dx * dx, v[2]);
-                            v[3] = fmaf(dpow, dx * dy, v[3]);
-                            v[4] = fmaf(dpow, dy * dy, v[4]);
-                        }
+                        eq8_accumulate(alpha, Tb, G, og <= kAlphaMax, dx, dy, c, con, g0[k], g1[k], g2[k],
+                                       B0[k], B1[k], B2[k], T[k], v);
                     }
                 }
             }
@@ -738,6 +801,47 @@ k_composite_bwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     bwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
+// Replay-cache forward and backward (one pixel per thread, 256 entries staged per batch).
+template <int kT>
+__global__ void __launch_bounds__(kT * kT)
+k_composite_fwd_record(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
+                       Scratch sc, float* __restrict__ image, ReplayCache rc) {
+    __shared__ FwdSmem<256> S;
+    TileJob J;
+    J.W = W;
+    J.H = H;
+    J.TX = TX;
+    J.tile = (int)sc.tile_order[blockIdx.x];
+    J.bg = bg;
+    J.range = sc.ranges[J.tile];
+    J.image = image;
+    J.dL = nullptr;
+    J.T_final = sc.T_final;
+    J.last = sc.last;
+    J.ncomp = sc.ncomp;
+    fwd_tile_scalar<kT, 1, 256, true>(J, n, vals, sc, S, rc);
+}
+
+template <int kT>
+__global__ void __launch_bounds__(kT * kT)
+k_composite_bwd_replay(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
+                       Scratch sc, const float* __restrict__ dL_dimage, ReplayCache rc) {
+    __shared__ BwdSmem<256> S;
+    TileJob J;
+    J.W = W;
+    J.H = H;
+    J.TX = TX;
+    J.tile = (int)sc.tile_order[blockIdx.x];
+    J.bg = bg;
+    J.range = sc.ranges[J.tile];
+    J.image = nullptr;
+    J.dL = dL_dimage;
+    J.T_final = sc.T_final;
+    J.last = sc.last;
+    J.ncomp = sc.ncomp;
+    bwd_tile_scalar<kT, 1, 256, true>(J, n, vals, sc, S, rc);
+}
+
 // Batched compositing: persistent CTAs take global tiles, heaviest first, until every tile of
 // every render is done.  A CTA's first job is its own index, so the first (heaviest) round is
 // spread over the SMs in launch order as a one-tile-per-CTA grid would be; later jobs come from a
@@ -821,6 +925,30 @@ int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, 
         return 1;                                                                                 \
     }
     PGS_VARIANTS(X)
+#undef X
+    return 0;
+}
+
+int launch_composite_replay(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
+                            const Scratch& sc, float* image, const float* dL_dimage, float4* rec,
+                            uint32_t* count, int K, bool backward, cudaStream_t s) {
+    const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
+    ReplayCache rc;
+    rc.rec = rec;
+    rc.count = count;
+    rc.K = K;
+    const unsigned grid = (unsigned)(TX * TY);
+#define X(TT)                                                                                     \
+    if (T == TT) {                                                                                \
+        if (backward)                                                                             \
+            k_composite_bwd_replay<TT><<<grid, TT * TT, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+                                                               sc.vals[buf], sc, dL_dimage, rc);  \
+        else                                                                                      \
+            k_composite_fwd_record<TT><<<grid, TT * TT, 0, s>>>(cam.width, cam.height, TX, bg, n, \
+                                                               sc.vals[buf], sc, image, rc);      \
+        return 1;                                                                                 \
+    }
+    X(8) X(16) X(32)
 #undef X
     return 0;
 }

@@ -195,6 +195,13 @@ int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, 
                          const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v);
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v);
+// Replay-cache compositing (one pixel per thread): the forward records, per pixel, the first K
+// composited entries as 16-byte records {position | clamp << 31, alpha, T in front, unused}
+// into rec [pixels][K] and their count (K + 1 on overflow); the backward replays them
+// (recomputing overflowed pixels).
+int launch_composite_replay(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
+                            const Scratch& sc, float* image, const float* dL_dimage, float4* rec,
+                            uint32_t* count, int K, bool backward, cudaStream_t s);
 // Batched compositing over every tile of every render in one persistent launch; `work` is a
 // zeroed device counter.
 int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int T, int buf,

@@ -200,6 +200,11 @@ class Rasterizer:
                                           cnt.ctypes.data_as(C.c_void_p)), "pgs_stage_times")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(L.PGS_STAGES)}
 
+    def set_replay_cache(self, k_max: int):
+        """The paper's per-pixel replay cache (k_max entries per pixel) instead of the recompute
+        backward from the next render on; 0 turns it off."""
+        L.check(self._lib.pgs_set_replay_cache(self._ctx, int(k_max)), "pgs_set_replay_cache")
+
     def set_variant(self, pixels_per_thread: int, depth: int):
         L.check(self._lib.pgs_set_variant(self._ctx, int(pixels_per_thread), int(depth)), "pgs_set_variant")
 
