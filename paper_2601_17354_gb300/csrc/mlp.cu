@@ -77,9 +77,25 @@ __device__ __forceinline__ void frag_b_t(uint32_t b[2], const __nv_bfloat16* S, 
     ldsm_x2_t(b, S + (size_t)(k0 + ((l >> 3) & 1) * 8 + (l & 7)) * ld + n0);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// 1 + erf(x) by the rational approximation 7.1.26 of Abramowitz & Stegun (Handbook of
+// Mathematical Functions, 1964): for x >= 0, erf(x) = 1 - (a1 s + a2 s^2 + ... + a5 s^5) e^{-x^2}
+// with s = 1 / (1 + p x) and |error| <= 1.5e-7, far below the BF16 rounding of the activations.
+// Evaluated as q = polynomial * e^{-x^2}, 1 + erf(x) = 2 - q for x >= 0 and q for x < 0 (the
+// odd symmetry), so the left tail keeps its relative accuracy instead of cancelling.
+__device__ __forceinline__ float one_plus_erf(float x) {
+    const float ax = fabsf(x);
+    const float s = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float poly = fmaf(1.061405429f, s, -1.453152027f);
+    poly = fmaf(poly, s, 1.421413741f);
+    poly = fmaf(poly, s, -0.284496736f);
+    poly = fmaf(poly, s, 0.254829592f);
+    const float q = poly * s * __expf(-ax * ax);
+    return x >= 0.0f ? 2.0f - q : q;
+}
+// GELU in the erf form, z Phi(z), and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * one_plus_erf(z * 0.70710678118654752f); }
 __device__ __forceinline__ float gelu_d(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+    return 0.5f * one_plus_erf(z * 0.70710678118654752f) + z * __expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
 struct Smem {
@@ -172,25 +188,95 @@ __device__ void warp_forward(Smem& S, const __nv_bfloat16* __restrict__ x, int64
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(32 * kWarps)
+// Inference: activations never leave registers.  The f32 accumulator fragment of a 16 x 8
+// product tile (rows g, g + 8; columns 2t, 2t + 1 of lane (g, t)) is, after bias and GELU and
+// packing column pairs to bf16x2, exactly the A fragment of the next layer's 16 x 16 k-tile (the
+// k-tile of columns 16 kk.. is made of n-tiles 2 kk and 2 kk + 1), so each warp carries its 16
+// points through the three layers with no shared-memory round trip; only the weights are staged.
+struct WeightSmem {
+    __nv_bfloat16 W1[kHid * LD16], W2[kHid * LD64], W3[16 * LD64];  // W3 rows 8..15 zero
+    float b1[kHid], b2[kHid], b3[kOut];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// bias + GELU of the eight 16 x 8 accumulator tiles C[j] of a 64-wide layer, packed into the
+// four A fragments of the next layer
+__device__ __forceinline__ void activate(const float C[8][4], const float* __restrict__ bias, int t,
+                                         uint32_t A[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        A[kk][0] = pack_bf16(gelu(C[2 * kk][0] + bias[c0]), gelu(C[2 * kk][1] + bias[c0 + 1]));
+        A[kk][1] = pack_bf16(gelu(C[2 * kk][2] + bias[c0]), gelu(C[2 * kk][3] + bias[c0 + 1]));
+        A[kk][2] = pack_bf16(gelu(C[2 * kk + 1][0] + bias[c1]), gelu(C[2 * kk + 1][1] + bias[c1 + 1]));
+        A[kk][3] = pack_bf16(gelu(C[2 * kk + 1][2] + bias[c1]), gelu(C[2 * kk + 1][3] + bias[c1 + 1]));
+    }
+}
+
+constexpr int kInferWarps = 4;
+
+__global__ void __launch_bounds__(32 * kInferWarps)
 k_mlp_forward(const __nv_bfloat16* __restrict__ x, int64_t n, const __nv_bfloat16* __restrict__ W1,
               const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
               const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3,
               float* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char s_raw[];
-    Smem& S = *reinterpret_cast<Smem*>(s_raw);
-    load_weights(S, W1, W2, W3, b1, b2, b3);
+    __shared__ __align__(16) WeightSmem S;
+    for (int k = threadIdx.x; k < kHid * kIn; k += blockDim.x) S.W1[(k / kIn) * LD16 + k % kIn] = W1[k];
+    for (int k = threadIdx.x; k < kHid * kHid; k += blockDim.x) S.W2[(k / kHid) * LD64 + k % kHid] = W2[k];
+    for (int k = threadIdx.x; k < 16 * kHid; k += blockDim.x)
+        S.W3[(k / kHid) * LD64 + k % kHid] = k < kOut * kHid ? W3[k] : __float2bfloat16_rn(0.f);
+    for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
+        S.b1[k] = b1[k];
+        S.b2[k] = b2[k];
+    }
+    if (threadIdx.x < kOut) S.b3[threadIdx.x] = b3[threadIdx.x];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t p0 = (int64_t)blockIdx.x * kRows; p0 < n; p0 += (int64_t)gridDim.x * kRows) {
-        const int r0 = 16 * warp;
-        warp_forward(S, x, n, p0 + r0, r0);
-        for (int e = lane; e < 16 * kOut; e += 32) {
-            const int row = e / kOut, col = e % kOut;
-            const int64_t p = p0 + r0 + row;
-            if (p < n) out[p * kOut + col] = S.Y[(r0 + row) * kOut + col];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t* __restrict__ xw = reinterpret_cast<const uint32_t*>(x);  // 8 words per point
+    const int64_t slices = (n + 15) / 16;
+    for (int64_t sl = (int64_t)blockIdx.x * kInferWarps + warp; sl < slices;
+         sl += (int64_t)gridDim.x * kInferWarps) {
+        const int64_t p0 = sl * 16, pa = p0 + g, pb = p0 + g + 8;
+        uint32_t a[4];
+        a[0] = pa < n ? xw[pa * 8 + t] : 0u;
+        a[1] = pb < n ? xw[pb * 8 + t] : 0u;
+        a[2] = pa < n ? xw[pa * 8 + t + 4] : 0u;
+        a[3] = pb < n ? xw[pb * 8 + t + 4] : 0u;
+        float C[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            uint32_t b[2];
+            frag_b(b, S.W1, LD16, 8 * j, 0);
+            C[j][0] = C[j][1] = C[j][2] = C[j][3] = 0.f;
+            mma(C[j], a, b);
         }
-        __syncwarp();
+        uint32_t A[4][4];
+        activate(C, S.b1, t, A);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            C[j][0] = C[j][1] = C[j][2] = C[j][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                uint32_t b[2];
+                frag_b(b, S.W2, LD64, 8 * j, 16 * kk);
+                mma(C[j], A[kk], b);
+            }
+        }
+        activate(C, S.b2, t, A);
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t b[2];
+            frag_b(b, S.W3, LD64, 0, 16 * kk);
+            mma(y, A[kk], b);
+        }
+        const int c = 2 * t;
+        if (pa < n) *reinterpret_cast<float2*>(out + pa * kOut + c) = make_float2(y[0] + S.b3[c], y[1] + S.b3[c + 1]);
+        if (pb < n) *reinterpret_cast<float2*>(out + pb * kOut + c) = make_float2(y[2] + S.b3[c], y[3] + S.b3[c + 1]);
     }
 }
 
@@ -416,7 +502,6 @@ int grid_for(int64_t n) {
 
 void enable_smem() {
     static bool done = [] {
-        cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         return true;
     }();
@@ -431,7 +516,16 @@ int launch_mlp_forward(const void* x, int64_t n, const float* master, const void
                        const void* W3, float* out, cudaStream_t s) {
     if (n <= 0) return 0;
     enable_smem();
-    k_mlp_forward<<<grid_for(n), 32 * kWarps, sizeof(Smem), s>>>(
+    static int grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_forward, 32 * kInferWarps, 0);
+        return sms * (per_sm > 0 ? per_sm : 1);
+    }();
+    const int64_t slices = (n + 15) / 16;
+    const int64_t blocks = std::min<int64_t>(grid, (slices + kInferWarps - 1) / kInferWarps);
+    k_mlp_forward<<<(unsigned)blocks, 32 * kInferWarps, 0, s>>>(
         static_cast<const __nv_bfloat16*>(x), n, static_cast<const __nv_bfloat16*>(W1),
         static_cast<const __nv_bfloat16*>(W2), static_cast<const __nv_bfloat16*>(W3), master + ob1,
         master + ob2, master + ob3, out);
