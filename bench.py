@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batched 16-scene x 4-view, initializer and replay-cache measurements")
+                    help="skip the batched 16-scene x 4-view, initializer, replay-cache and D-SSIM measurements")
     ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: one capacity probe, random targets, --steps "
@@ -375,6 +375,53 @@ def run_replay(params, cams, targets, tile: int, reps: int = 20, k_max: int = 25
     return out
 
 
+def run_dssim(params, cams, targets, tile: int, variant, reps: int = 20, lam: float = 0.2) -> dict:
+    """The L1 + D-SSIM loss on the bench workload: the loss kernels alone (HBM roofline over the
+    44 algorithmic bytes per image value: x, y read; three derivative planes written and read
+    back; x, y read again; the gradient written) and a training step that uses it."""
+    import torch
+    from paper_2601_17354_gb300 import _lib as L
+    from paper_2601_17354_gb300 import rasterizer as R
+    p = params.clone()
+    probe = R.Rasterizer(tile=tile)
+    probe.render(p, cams[0])
+    cap = int(probe.check_status() * 1.5) + 4096
+    probe.close()
+    rast = R.Rasterizer(pair_capacity=cap, tile=tile)
+    rast.set_variant(*variant)
+    img = rast.render(p, cams[0]).clone()
+    grad = torch.empty_like(img)
+    out = torch.empty(2, device=img.device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = {}
+    for name, fn in (("l1", lambda: rast.loss_l1(img, targets[0], grad, out)),
+                     ("dssim", lambda: rast.loss_dssim(img, targets[0], lam, grad, out))):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record(rast.stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(rast.stream)
+        torch.cuda.synchronize()
+        times[name] = ev0.elapsed_time(ev1) / reps
+    tr = R.Trainer(p, rast, dssim=lam)
+    for k in range(3):
+        tr.step(cams[k % len(cams)], targets[k % len(targets)])
+    torch.cuda.synchronize()
+    ev0.record(rast.stream)
+    for k in range(reps):
+        tr.step(cams[k % len(cams)], targets[k % len(targets)])
+    ev1.record(rast.stream)
+    torch.cuda.synchronize()
+    L.check(rast.status()[0], "dssim steps")
+    peaks, _ = measured_peaks()
+    gbs = img.numel() * 44 / (times["dssim"] * 1e-3) / 1e9
+    return {"lambda": lam, "loss_ms": times["dssim"], "l1_loss_ms": times["l1"],
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": gbs / float(peaks["hbm_gbs"])},
+            "train_it_per_s": 1000.0 / (ev0.elapsed_time(ev1) / reps), "mean_ssim": float(out[1])}
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -535,6 +582,7 @@ def run_ours(args):
         out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))
         out["initializer"] = run_initializer()
         out["replay_cache"] = run_replay(init, cams, targets, tile)
+        out["dssim"] = run_dssim(init, cams, targets, tile, tuned)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",

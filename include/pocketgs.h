@@ -106,6 +106,14 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
    loss_out is a device pointer to 2 floats. */
 int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,
                 float* loss_out);
+/* L1 + D-SSIM loss (the paper reports SSIM, Sec. IV, and names no training loss): per colour
+   plane of [3][height][width] images, SSIM with the 11 x 11 Gaussian window (sigma 1.5, taps
+   normalised to 1), zero padding, C1 = 0.01^2, C2 = 0.03^2; loss = (1 - lambda) mean|image -
+   target| + lambda (1 - mean SSIM).  Writes dL_dimage (device [3][H][W]) and, on the device,
+   loss_out[0] = the loss, loss_out[1] = mean SSIM (device pointer to 2 floats).  Context-owned
+   scratch of 9 floats per pixel (grown with the image; growing synchronises).  lambda in [0, 1]. */
+int pgs_loss_dssim(pgs_ctx* ctx, const float* image, const float* target, int32_t width, int32_t height,
+                   float lambda, float* dL_dimage, float* loss_out);
 
 /* Backward of the last pgs_render on this context for the upstream gradient dL_dimage [3][H][W]:
    per pixel, re-traverse its list back to front from `last`, rebuilding the transmittance from

@@ -44,7 +44,7 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
             "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views", "pgs_batch_reserve",
-            "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache"]
+            "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -144,6 +144,8 @@ def lib():
             L.pgs_batch_time_render.restype = I
             L.pgs_set_replay_cache.argtypes = [P, I]
             L.pgs_set_replay_cache.restype = I
+            L.pgs_loss_dssim.argtypes = [P, P, P, I, I, C.c_float, P, P]
+            L.pgs_loss_dssim.restype = I
             L.pgs_batch_losses.argtypes = [P, P]
             L.pgs_batch_losses.restype = I
             L.pgs_batch_status.argtypes = [P, C.POINTER(I64)]

@@ -32,6 +32,9 @@ struct pgs_ctx {
     int64_t cap_c = 0;         // pixels x K the cache arena holds
     float4* c_rec = nullptr;
     uint32_t* c_count = nullptr;
+    // D-SSIM scratch: 9 floats per pixel + 2 doubles
+    void* arena_s = nullptr;
+    int64_t cap_s = 0;
     pgs_camera cam{};
     pgs_gaussians params{};
     CompositeVariant variant = default_variant();
@@ -258,6 +261,7 @@ void pgs_destroy(pgs_ctx* ctx) {
     if (ctx->arena_g) cudaFree(ctx->arena_g);
     if (ctx->arena_p) cudaFree(ctx->arena_p);
     if (ctx->arena_c) cudaFree(ctx->arena_c);
+    if (ctx->arena_s) cudaFree(ctx->arena_s);
     delete ctx;
 }
 
@@ -364,6 +368,34 @@ int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max) {
         ctx->has_render = false;  // the next backward needs a render made with this setting
     }
     return PGS_OK;
+}
+
+int pgs_loss_dssim(pgs_ctx* ctx, const float* image, const float* target, int32_t width, int32_t height,
+                   float lambda, float* dL_dimage, float* loss_out) {
+    if (!ctx || !image || !target || !dL_dimage || !loss_out || width <= 0 || height <= 0 ||
+        !(lambda >= 0.f && lambda <= 1.f))
+        return PGS_ERR_INVALID_ARG;
+    const int64_t pixels = (int64_t)width * height;
+    if (pixels > ctx->cap_s) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_err(e);
+        if (ctx->arena_s) cudaFree(ctx->arena_s);
+        ctx->arena_s = nullptr;
+        ctx->cap_s = 0;
+        e = cudaMalloc(&ctx->arena_s, 256 + align256(sizeof(float) * 9 * (size_t)pixels));
+        if (e != cudaSuccess) {
+            ctx->arena_s = nullptr;
+            return cuda_err(e);
+        }
+        ctx->cap_s = pixels;
+    }
+    double* sums = static_cast<double*>(ctx->arena_s);
+    float* dm = reinterpret_cast<float*>(static_cast<char*>(ctx->arena_s) + 256);
+    const size_t e0 = mark(ctx);
+    ctx->launches += launch_loss_dssim(image, target, width, height, lambda, dm, sums, dL_dimage, loss_out,
+                                       ctx->stream);
+    span(ctx, PGS_STAGE_LOSS, e0, mark(ctx));
+    return cuda_err(cudaGetLastError());
 }
 
 int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {

@@ -208,6 +208,10 @@ int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles
                            int64_t n, const Scratch& sc, uint32_t* work, bool backward,
                            cudaStream_t s, CompositeVariant v);
 
+// L1 + D-SSIM loss and gradient of [3][H][W] images; dm = 9 H W floats of scratch, sums = 2
+// doubles of scratch, loss_out = device {loss, mean SSIM}.
+int launch_loss_dssim(const float* image, const float* target, int W, int H, float lam, float* dm,
+                      double* sums, float* grad, float* loss_out, cudaStream_t s);
 // K7: L1 loss; K10: fused Adam over all parameter groups.
 int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
                     float* loss_out, const Scratch& sc, cudaStream_t s);

@@ -157,6 +157,19 @@ class Rasterizer:
                 "pgs_loss_l1")
         return grad, out
 
+    def loss_dssim(self, image: torch.Tensor, target: torch.Tensor, lam: float = 0.2,
+                   grad: torch.Tensor | None = None, out: torch.Tensor | None = None):
+        """(1 - lam) L1 + lam (1 - SSIM) of [3][H][W] images: (dL/dimage, device tensor
+        [loss, mean SSIM])."""
+        assert image.is_contiguous() and target.is_contiguous() and image.shape == target.shape
+        _, H, W = image.shape
+        grad = torch.empty_like(image) if grad is None else grad
+        out = torch.empty(2, dtype=torch.float32, device=self.device) if out is None else out
+        L.check(self._lib.pgs_loss_dssim(self._ctx, C.c_void_p(image.data_ptr()), C.c_void_p(target.data_ptr()),
+                                         int(W), int(H), float(lam), C.c_void_p(grad.data_ptr()),
+                                         C.c_void_p(out.data_ptr())), "pgs_loss_dssim")
+        return grad, out
+
     def backward_struct(self, dL_dimage: torch.Tensor, grads: L.PgsGaussians):
         assert dL_dimage.is_contiguous() and dL_dimage.dtype == torch.float32
         L.check(self._lib.pgs_backward(self._ctx, C.c_void_p(dL_dimage.data_ptr()), C.byref(grads)),
@@ -236,8 +249,10 @@ class Trainer:
     iterations, one view per iteration)."""
 
     def __init__(self, params: GaussianBuffer, rasterizer: Rasterizer | None = None,
-                 adam: AdamConfig | None = None, fused: bool = True):
+                 adam: AdamConfig | None = None, fused: bool = True, dssim: float = 0.0):
+        """dssim: weight lambda of the D-SSIM term ((1 - lambda) L1 + lambda D-SSIM); 0 = L1."""
         self.params = params
+        self.dssim = float(dssim)
         self.r = rasterizer or Rasterizer(adam=adam)
         self.fused = fused
         self.grads = None if fused else params.zeros_like()
@@ -253,7 +268,10 @@ class Trainer:
                                    self.image.shape[1:] == (cam.height, cam.width) else None)
         if self.dl is None or self.dl.shape != self.image.shape:
             self.dl = torch.empty_like(self.image)
-        self.r.loss_l1(self.image, target, self.dl, self.loss)
+        if self.dssim > 0.0:
+            self.r.loss_dssim(self.image, target, self.dssim, self.dl, self.loss)
+        else:
+            self.r.loss_l1(self.image, target, self.dl, self.loss)
         self.t += 1
         if self.fused:
             self.r.backward_step(self.dl, self.params, self.m, self.v, self.t)
