@@ -1020,8 +1020,8 @@ int pgs_knn(pgs_init* c, const float* points, int64_t n, int32_t k, int32_t* nb)
     if (e != cudaSuccess) return cuda_err(e);
     float bb[6];
     decode_bbox(enc, bb);
-    // scratch for up to ~4 points per cell on average (the grid coarsens to fit)
-    const size_t want = knn_scratch_bytes(n, n / 2 + 1024);
+    // scratch for up to 4 cells per point (the grid coarsens to fit)
+    const size_t want = knn_scratch_bytes(n, 4 * n + 1024);
     if (c->scratch_bytes < want) {
         e = cudaStreamSynchronize(s);
         if (c->scratch) cudaFree(c->scratch);

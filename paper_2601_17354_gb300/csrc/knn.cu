@@ -107,17 +107,24 @@ __global__ void __launch_bounds__(1024) k_scan_cells(int64_t m, const uint32_t* 
     if (threadIdx.x == 0) start[m] = s_carry;
 }
 
-__global__ void k_cell_scatter(int64_t n, const uint32_t* __restrict__ cell_of, uint32_t* __restrict__ cursor,
-                               uint32_t* __restrict__ sorted) {
+// points in cell order: their indices and a copy of their positions ([3][n]), so the queries read
+// each cell's candidates contiguously
+__global__ void k_cell_scatter(int64_t n, const float* __restrict__ P, const uint32_t* __restrict__ cell_of,
+                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ sorted,
+                               float* __restrict__ Ps) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
-    sorted[atomicAdd(&cursor[cell_of[i]], 1u)] = (uint32_t)i;
+    const uint32_t s = atomicAdd(&cursor[cell_of[i]], 1u);
+    sorted[s] = (uint32_t)i;
+    Ps[s] = P[i];
+    Ps[n + s] = P[n + i];
+    Ps[2 * n + s] = P[2 * n + i];
 }
 
 template <int K>
 __global__ void __launch_bounds__(128)
 k_knn_query(int64_t n, const float* __restrict__ P, Grid g, const uint32_t* __restrict__ start,
-            const uint32_t* __restrict__ sorted, int32_t* __restrict__ nb) {
+            const uint32_t* __restrict__ sorted, const float* __restrict__ Ps, int32_t* __restrict__ nb) {
     const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
     if (i >= n) return;
     const float qx = P[i], qy = P[n + i], qz = P[2 * n + i];
@@ -147,17 +154,24 @@ k_knn_query(int64_t n, const float* __restrict__ P, Grid g, const uint32_t* __re
                     for (uint32_t s = start[c]; s < start[c + 1]; ++s) {
                         const int32_t j = (int32_t)sorted[s];
                         if (j == i) continue;
-                        const float ex = P[j] - qx, ey = P[n + j] - qy, ez = P[2 * n + j] - qz;
+                        const float ex = Ps[s] - qx, ey = Ps[n + s] - qy, ez = Ps[2 * n + s] - qz;
                         const float d2 = __fmaf_rn(ex, ex, __fmaf_rn(ey, ey, __fmul_rn(ez, ez)));
                         if (d2 < bd[K - 1] || (d2 == bd[K - 1] && j < bi[K - 1])) {
-                            int a = K - 1;
-                            while (a > 0 && (d2 < bd[a - 1] || (d2 == bd[a - 1] && j < bi[a - 1]))) {
-                                bd[a] = bd[a - 1];
-                                bi[a] = bi[a - 1];
-                                --a;
+                            // insertion by a fixed pass of compare-and-swap (static indices keep the
+                            // list in registers): the candidate trades places with every entry it
+                            // precedes, and the last entry falls off
+                            float cd = d2;
+                            int32_t cj = j;
+#pragma unroll
+                            for (int a = 0; a < K; ++a) {
+                                const bool before = cd < bd[a] || (cd == bd[a] && cj < bi[a]);
+                                const float td = bd[a];
+                                const int32_t tj = bi[a];
+                                bd[a] = before ? cd : td;
+                                bi[a] = before ? cj : tj;
+                                cd = before ? td : cd;
+                                cj = before ? tj : cj;
                             }
-                            bd[a] = d2;
-                            bi[a] = j;
                         }
                     }
                 }
@@ -429,7 +443,7 @@ int launch_make_targets(int64_t n, const pgs_gaussians& pca, const pgs_gaussians
 // Scratch of the kNN: bbox (6 floats), cell of each point (n), counts / cursors (cells + 1),
 // starts (cells + 1), sorted indices (n).  Returns the bytes needed for n points and `cells` cells.
 size_t knn_scratch_bytes(int64_t n, int64_t cells) {
-    return 256 + 4 * (size_t)n + 2 * 4 * (size_t)(cells + 1) + 4 * (size_t)n + 4 * 256;
+    return 256 + 4 * (size_t)n + 2 * 4 * (size_t)(cells + 1) + 4 * (size_t)n + 12 * (size_t)n + 5 * 256;
 }
 
 int launch_knn(int64_t n, const float* P, int k, int32_t* nb, void* scratch, size_t scratch_bytes,
@@ -439,7 +453,9 @@ int launch_knn(int64_t n, const float* P, int k, int32_t* nb, void* scratch, siz
     // whatever the density)
     const float ex = fmaxf(host_bbox[3] - host_bbox[0], 1e-6f), ey = fmaxf(host_bbox[4] - host_bbox[1], 1e-6f),
                 ez = fmaxf(host_bbox[5] - host_bbox[2], 1e-6f);
-    float h = 1.5f * cbrtf(ex * ey * ez / (float)n);
+    // a fine grid (about 2.4 cells per point over the bounding box): surface points fill few
+    // cells densely, and fewer candidates per cell beat fewer, fuller cells
+    float h = 0.75f * cbrtf(ex * ey * ez / (float)n);
     Grid g;
     for (int d = 0; d < 3; ++d) g.lo[d] = host_bbox[d];
     int64_t cells = 0;
@@ -457,17 +473,19 @@ int launch_knn(int64_t n, const float* P, int k, int32_t* nb, void* scratch, siz
     uint32_t* counts = cell_of + n;
     uint32_t* start = counts + (cells + 1);
     uint32_t* sorted = start + (cells + 1);
+    float* Ps = reinterpret_cast<float*>(base + ((256 + 4 * (size_t)n + 2 * 4 * (size_t)(cells + 1) +
+                                                   4 * (size_t)n + 255) & ~(size_t)255));
     cudaMemsetAsync(counts, 0, 4 * (size_t)(cells + 1), s);
     const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
     k_cell_count<<<blocks, kThreads, 0, s>>>(n, P, g, cell_of, counts);
     k_scan_cells<<<1, 1024, 0, s>>>(cells, counts, start);
     cudaMemcpyAsync(counts, start, 4 * (size_t)cells, cudaMemcpyDeviceToDevice, s);
-    k_cell_scatter<<<blocks, kThreads, 0, s>>>(n, cell_of, counts, sorted);
+    k_cell_scatter<<<blocks, kThreads, 0, s>>>(n, P, cell_of, counts, sorted, Ps);
     const unsigned qb = (unsigned)((n + 127) / 128);
     switch (k) {
-        case 3: k_knn_query<3><<<qb, 128, 0, s>>>(n, P, g, start, sorted, nb); break;
-        case 16: k_knn_query<16><<<qb, 128, 0, s>>>(n, P, g, start, sorted, nb); break;
-        default: k_knn_query<32><<<qb, 128, 0, s>>>(n, P, g, start, sorted, nb); break;
+        case 3: k_knn_query<3><<<qb, 128, 0, s>>>(n, P, g, start, sorted, Ps, nb); break;
+        case 16: k_knn_query<16><<<qb, 128, 0, s>>>(n, P, g, start, sorted, Ps, nb); break;
+        default: k_knn_query<32><<<qb, 128, 0, s>>>(n, P, g, start, sorted, Ps, nb); break;
     }
     return 4;
 }
