@@ -264,3 +264,48 @@ def batched_scenes(seed: int, n_scenes: int = 16, views_per_scene: int = 4,
                            n_cameras=views_per_scene)
         out.append(sc)
     return out
+
+
+@dataclass
+class BAProblem:
+    """Bundle-adjustment inputs drawn for the geometry prior (Sec. III-A): ground-truth ring cameras
+    and surface points, their perturbed starting values, and per (camera, point) pixel noise.
+    Which pairs are observed and where (the projection) is left to the caller."""
+    K: tuple                 # (fx, fy, cx, cy)
+    width: int
+    height: int
+    R_gt: np.ndarray         # [C][3][3] world -> camera rotations
+    t_gt: np.ndarray         # [C][3]
+    P_gt: np.ndarray         # [n][3]
+    R_init: np.ndarray       # [C][3][3] = small random rotation @ R_gt (camera 0 exact)
+    t_init: np.ndarray       # [C][3]
+    P_init: np.ndarray       # [n][3]
+    noise: np.ndarray        # [C][n][2] pixel noise, sigma `pixel_sigma`
+    pixel_sigma: float
+
+
+def _small_rotation(rng: np.random.Generator, max_deg: float) -> np.ndarray:
+    """Rotation matrix of a random unit quaternion within about max_deg of the identity."""
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    half = 0.5 * np.deg2rad(rng.uniform(0.0, max_deg))
+    w, (x, y, z) = np.cos(half), np.sin(half) * axis
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def ba_problem(seed: int, n_cams: int = 32, n_points: int = 20000, width: int = 1280, height: int = 720,
+               focal: float = 1000.0, rot_deg: float = 0.5, trans: float = 0.02, point: float = 0.01,
+               pixel_sigma: float = 0.5) -> BAProblem:
+    rng = np.random.default_rng(seed)
+    cams = ring_cameras(rng, n_cams, width, height, focal)
+    R = np.array([c.viewmat[:, :3] for c in cams], np.float64)
+    t = np.array([c.viewmat[:, 3] for c in cams], np.float64)
+    P = sample_surface_points(rng, random_surfaces(rng), n_points).T.astype(np.float64)
+    Rp = np.array([R[i] if i == 0 else _small_rotation(rng, rot_deg) @ R[i] for i in range(n_cams)])
+    tp = t + np.vstack([np.zeros(3), rng.normal(0.0, trans, (n_cams - 1, 3))])
+    Pp = P + rng.normal(0.0, point, P.shape)
+    noise = rng.normal(0.0, pixel_sigma, (n_cams, n_points, 2))
+    return BAProblem((focal, focal, width / 2.0, height / 2.0), width, height, R, t, P, Rp, tp, Pp,
+                     noise, pixel_sigma)
