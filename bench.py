@@ -422,6 +422,62 @@ def run_dssim(params, cams, targets, tile: int, variant, reps: int = 20, lam: fl
             "train_it_per_s": 1000.0 / (ev0.elapsed_time(ev1) / reps), "mean_ssim": float(out[1])}
 
 
+def ba_observations(p, Rg, tg, Pg):
+    """Observations of the synthetic bundle-adjustment problem, made on the GPU: every (camera,
+    point) pair projected, kept when in front of the camera (z > 0.2), inside the image and inside
+    the point's feature track, points with fewer than two views dropped, pixel noise added,
+    ordered by point then camera."""
+    import torch
+    from paper_2601_17354_gb300 import ba as B
+    C, n = len(p.R_gt), len(p.P_gt)
+    dev = Rg.device
+    cams = torch.arange(C, dtype=torch.int32, device=dev).repeat_interleave(n)
+    pts = torch.arange(n, dtype=torch.int32, device=dev).repeat(C)
+    uv, z = B.BundleAdjuster(C, n, 0).project(Rg, tg, Pg, cams, pts, p.K)
+    ci, pj = cams.long(), pts.long()
+    ts = torch.from_numpy(p.track_start).to(dev)[pj]
+    tl = torch.from_numpy(p.track_len).to(dev)[pj]
+    ok = ((z > 0.2) & (uv[:, 0] >= 0) & (uv[:, 0] < p.width) & (uv[:, 1] >= 0) & (uv[:, 1] < p.height)
+          & ((ci - ts) % C < tl))
+    ok &= torch.bincount(pj[ok], minlength=n)[pj] >= 2
+    uv = uv + torch.from_numpy(p.noise.reshape(C * n, 2).astype("float32")).to(dev)
+    c, q, u = cams[ok], pts[ok], uv[ok]
+    order = torch.argsort(q.long() * C + c.long())
+    return c[order].contiguous(), q[order].contiguous(), u[order].contiguous()
+
+
+def run_ba(reps: int = 10, iters: int = 10) -> dict:
+    """Bundle adjustment of the geometry prior (Sec. III-A) on a synthetic 32-keyframe, 20k-point
+    problem with feature tracks of 2-12 consecutive keyframes: device time of each stage of one
+    Levenberg-Marquardt iteration (median of reps) and a full solve from the perturbed start
+    (host round trip per iteration included)."""
+    import numpy as np
+    import torch
+    from paper_2601_17354_gb300 import ba as B
+    from paper_2601_17354_gb300 import synthetic as S
+    C, n = 32, 20000
+    p = S.ba_problem(7, C, n)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    cam, pt, uv = ba_observations(p, f(p.R_gt), f(p.t_gt), f(p.P_gt))
+    m = int(cam.numel())
+    ba = B.BundleAdjuster(C, n, m)
+    R0, t0, P0 = f(p.R_init), f(p.t_init), f(p.P_init)
+    rows = [ba.stage_times(R0, t0, P0, cam, pt, uv, p.K, 0.5, 2.0, 1e-4) for _ in range(reps + 2)][2:]
+    stages = {k: float(np.median([r[k] for r in rows])) for k in B.BundleAdjuster.STAGES}
+    R, t, P = R0.clone(), t0.clone(), P0.clone()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ba.stream)
+    costs, acc = ba.solve(R, t, P, cam, pt, uv, p.K, 0.5, 2.0, iters=iters, lam0=1e-4)
+    ev1.record(ba.stream)
+    torch.cuda.synchronize()
+    ms_iter = ev0.elapsed_time(ev1) / iters
+    return {"workload": f"{C} keyframes, {n} points, {m} observations (tracks of 2-12 keyframes)",
+            "stage_ms": stages, "iteration_ms_device": sum(stages.values()),
+            "solve_ms_per_iteration": ms_iter, "observations_per_s": m / (ms_iter * 1e-3),
+            "cost_initial": float(costs[0]), "cost_final": float(costs[-1]), "accepted": acc, "iterations": iters}
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -583,6 +639,7 @@ def run_ours(args):
         out["initializer"] = run_initializer()
         out["replay_cache"] = run_replay(init, cams, targets, tile)
         out["dssim"] = run_dssim(init, cams, targets, tile, tuned)
+        out["bundle_adjustment"] = run_ba()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -42,6 +42,7 @@ extern "C" {
 #define PGS_ERR_OOM (-7)         /* device allocation failed */
 #define PGS_ERR_INTERNAL (-8)    /* a device-side consistency check failed (access skipped) */
 #define PGS_ERR_TOO_LARGE (-9)   /* size beyond the fixed scratch of pgs_sort_pairs_static */
+#define PGS_ERR_NOT_PD (-10)     /* bundle adjustment: damped reduced system not positive definite */
 
 typedef struct pgs_ctx pgs_ctx;
 
@@ -350,6 +351,56 @@ int pgs_apply_mlp(pgs_init* ctx, const float* y, const pgs_gaussians* pca, pgs_g
    initializer `pca` of the same points: log-scale differences, conj(normalise(pca q)) (x)
    normalise(q), opacity-logit difference.  pca and converged have the same n. */
 int pgs_make_targets(pgs_init* ctx, const pgs_gaussians* pca, const pgs_gaussians* converged, float* t);
+
+/* ------------------------------------------------------------------------------------------
+   Bundle adjustment of the geometry prior (Sec. III-A): Levenberg-Marquardt on the robust
+   reprojection objective (Eq. 2), each step solved through the reduced camera system (Eq. 3):
+   the point blocks are inverted independently (3 x 3 each), folded into a dense 6C x 6C camera
+   system (Schur complement), which is solved by Cholesky (FP64), and the point steps follow by
+   back-substitution.
+     camera i: world-to-camera rotation R_i (row-major 3 x 3) and translation t_i, x = R_i P + t_i;
+     observation o of point pt[o] in camera cam[o] at pixel uv[o]; intrinsics K = (fx, fy, cx, cy);
+     residual r = pi(x) - uv, whitened norm e = |r| / sigma; Huber: rho = e^2 (e <= delta) or
+     2 delta e - delta^2, solved by reweighting (weight 1 or delta / e);
+     step: R_i <- exp([omega_i]x) R_i, t_i <- t_i + v_i, P_j <- P_j + d_j; damping
+     H + lambda diag(H);
+     gauge: camera 0 fixed, and of camera 1's translation the component along which its baseline
+     to camera 0, in camera 1's frame, is largest (computed from the state at the call's start).
+   Layout (all device, FP32 unless said): R [C][9], t [C][3], P [n][3], cam / pt [m] int32 with
+   pt non-decreasing (observations grouped by point), uv [m][2]; K is a host array of 4 floats.
+   Observations behind their camera (z <= 1e-6) carry no weight.  Errors: PGS_ERR_INVALID_ARG
+   for a null pointer, bad size, a cam or pt index out of range or pt not sorted (checked on the
+   device before any other work); PGS_ERR_NOT_PD when the damped reduced system is not positive
+   definite.
+   ------------------------------------------------------------------------------------------ */
+typedef struct pgs_ba pgs_ba;
+/* Buffers for C cameras (2..256), n points and m observations, work on `cuda_stream`. */
+int pgs_ba_create(pgs_ba** out, int32_t n_cams, int64_t n_points, int64_t n_obs, void* cuda_stream);
+void pgs_ba_destroy(pgs_ba* ba);
+/* uv [count][2] and depth z [count] of the given (cam, pt) pairs (device); z is not checked, a
+   pair with an index out of range gets NaN. */
+int pgs_ba_project(pgs_ba* ba, const float* R, const float* t, const float* P, const int32_t* cam,
+                   const int32_t* pt, int64_t count, const float* K, float* uv, float* z);
+/* One damped step at `lambda` from the given state, not applied: dcam [C][6] (omega, v; zero for
+   fixed parameters) and dP [n][3] (device), and the robust cost of the state (*cost, host). */
+int pgs_ba_step(pgs_ba* ba, const float* R, const float* t, const float* P, const int32_t* cam,
+                const int32_t* pt, const float* uv, const float* K, float sigma, float huber_delta,
+                float lambda, float* dcam, float* dP, double* cost);
+/* `iters` Levenberg-Marquardt trials from lambda0, R, t, P updated in place: a trial whose
+   robust cost is lower is taken and lambda divided by 10, else lambda multiplied by 10 and the
+   linearization reused.  costs [iters + 1] (host) receives the cost after each trial (costs[0]
+   initial), *accepted (host) the number taken.  Synchronises once per trial. */
+int pgs_ba_solve(pgs_ba* ba, float* R, float* t, float* P, const int32_t* cam, const int32_t* pt,
+                 const float* uv, const float* K, float sigma, float huber_delta, int32_t iters,
+                 float lambda0, double* costs, int32_t* accepted);
+
+/* Device times (ms) of the stages of one iteration from the given state (nothing applied):
+   ms[0] point linearization (H_pp, b_p, H_tp), ms[1] camera blocks (H_tt, b_t), ms[2] point
+   inverses and E, ms[3] reduced-system blocks, ms[4] reduced-system solve, ms[5]
+   back-substitution and candidate poses, ms[6] candidate cost.  Synchronises. */
+int pgs_ba_stage_times(pgs_ba* ba, const float* R, const float* t, const float* P, const int32_t* cam,
+                       const int32_t* pt, const float* uv, const float* K, float sigma, float huber_delta,
+                       float lambda, float* ms);
 
 /* Static description of an error code. */
 const char* pgs_strerror(int code);

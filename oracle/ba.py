@@ -16,9 +16,13 @@ path).  Plain FP64 numpy, written from the definitions:
   (numpy.linalg.solve) — the plain definition that the GPU's Schur complement (Eq. 3) reaches
   exactly up to rounding.
 
+normal_residual evaluates the same normal equations matrix-free (a check of a proposed step that
+runs at any problem size).
+
 Parity status: analytic Jacobians pinned by central differences; a step from exact observations
 at the solution is zero; Levenberg-Marquardt from perturbed poses and points on noise-free
-observations drives the reprojection error to zero.
+observations drives the reprojection error to zero; the matrix-free residual vanishes at the dense
+solution and equals H step - b of the dense equations for an arbitrary step.
 """
 from __future__ import annotations
 
@@ -101,9 +105,11 @@ def cost_terms(R, t, P, obs, K, sigma, delta):
     return r, e, w, rho
 
 
-def lm_step(R, t, P, obs, K, sigma, delta, lam, axis):
-    """One damped Gauss-Newton step by the dense normal equations.  Returns (dcam [C][6] with zeros
-    for fixed parameters, dP [n][3], cost before)."""
+def normal_equations(R, t, P, obs, K, sigma, delta, lam, axis):
+    """The damped normal equations over the free parameters (cameras first, then points):
+    (H + lam diag(H), b, H's diagonal, camera index [C][6], number of free camera parameters,
+    robust cost).  Each observation adds its 2 x 9 Jacobian's block W J^T J at its parameters'
+    indices (the same sum as over the full Jacobian, without its zero columns)."""
     cams, pts, uv = obs
     C, n = len(R), len(P)
     ci, nc = free_layout(C, n, axis)
@@ -114,18 +120,25 @@ def lm_step(R, t, P, obs, K, sigma, delta, lam, axis):
     for i in np.unique(cams):
         sel = np.nonzero(cams == i)[0]
         Jc, Jp = jacobians(R[i], t[i], P[pts[sel]], K)
+        free = [d for d in range(6) if ci[i, d] >= 0]
         for q, m in enumerate(sel):
-            J = np.zeros((2, N))
-            for d in range(6):
-                if ci[i, d] >= 0:
-                    J[:, ci[i, d]] = Jc[q, :, d]
             j = pts[m]
-            J[:, nc + 3 * j:nc + 3 * j + 3] = Jp[q]
+            idx = np.array([ci[i, d] for d in free] + [nc + 3 * j + c for c in range(3)])
+            J = np.concatenate([Jc[q][:, free], Jp[q]], axis=1)
             Wm = w[m] / (sigma * sigma)
-            H += Wm * J.T @ J
-            b -= Wm * J.T @ r[m]
-    Hd = H + lam * np.diag(np.diag(H))
-    unseen = np.diag(H) == 0.0  # a parameter no observation touches stays where it is
+            H[np.ix_(idx, idx)] += Wm * J.T @ J
+            b[idx] -= Wm * J.T @ r[m]
+    diag = np.diag(H).copy()
+    Hd = H + lam * np.diag(diag)
+    return Hd, b, diag, ci, nc, float(rho.sum())
+
+
+def lm_step(R, t, P, obs, K, sigma, delta, lam, axis):
+    """One damped Gauss-Newton step by the dense normal equations.  Returns (dcam [C][6] with zeros
+    for fixed parameters, dP [n][3], cost before)."""
+    C, n = len(R), len(P)
+    Hd, b, diag, ci, nc, cost = normal_equations(R, t, P, obs, K, sigma, delta, lam, axis)
+    unseen = diag == 0.0  # a parameter no observation touches stays where it is
     Hd[unseen, unseen] = 1.0
     delta_x = np.linalg.solve(Hd, b)
     dcam = np.zeros((C, 6))
@@ -134,7 +147,44 @@ def lm_step(R, t, P, obs, K, sigma, delta, lam, axis):
             if ci[i, d] >= 0:
                 dcam[i, d] = delta_x[ci[i, d]]
     dP = delta_x[nc:].reshape(n, 3)
-    return dcam, dP, float(rho.sum())
+    return dcam, dP, cost
+
+
+def normal_residual(R, t, P, obs, K, sigma, delta, lam, axis, dcam, dP):
+    """For a proposed step (dcam, dP): the residual (H + lam diag H) step - b of the normal
+    equations row by row, and per row the scale (|H| + lam diag H) |step| + |b| (|H| taken over
+    the Jacobians' absolute values, an upper bound), without forming H, so it runs at any size.
+    Returns (res_cam [C][6], scale_cam [C][6], res_pt [n][3], scale_pt [n][3]); fixed camera
+    parameters get zeros."""
+    cams, pts, uv = obs
+    C, n = len(R), len(P)
+    ci, _ = free_layout(C, n, axis)
+    free = ci >= 0
+    dc = np.where(free, dcam, 0.0)
+    r, e, w, rho = cost_terms(R, t, P, obs, K, sigma, delta)
+    Wm = w / (sigma * sigma)
+    hc, sc, dgc, bc = (np.zeros((C, 6)) for _ in range(4))
+    hp, sp, dgp, bpt = (np.zeros((n, 3)) for _ in range(4))
+    for i in np.unique(cams):
+        sel = np.nonzero(cams == i)[0]
+        Jc, Jp = jacobians(R[i], t[i], P[pts[sel]], K)
+        Jc = Jc * free[i][None, None, :]
+        wq = Wm[sel][:, None]
+        Jd = np.einsum("kad,d->ka", Jc, dc[i]) + np.einsum("kad,kd->ka", Jp, dP[pts[sel]])
+        Ja = np.einsum("kad,d->ka", np.abs(Jc), np.abs(dc[i])) + np.einsum("kad,kd->ka", np.abs(Jp), np.abs(dP[pts[sel]]))
+        hc[i] += np.einsum("kad,ka->d", Jc, wq * Jd)
+        sc[i] += np.einsum("kad,ka->d", np.abs(Jc), wq * Ja)
+        dgc[i] += np.einsum("kad,kad->d", Jc, Jc * wq[:, :, None])
+        bc[i] -= np.einsum("kad,ka->d", Jc, wq * r[sel])
+        np.add.at(hp, pts[sel], np.einsum("kad,ka->kd", Jp, wq * Jd))
+        np.add.at(sp, pts[sel], np.einsum("kad,ka->kd", np.abs(Jp), wq * Ja))
+        np.add.at(dgp, pts[sel], np.einsum("kad,kad->kd", Jp, Jp * wq[:, :, None]))
+        np.add.at(bpt, pts[sel], -np.einsum("kad,ka->kd", Jp, wq * r[sel]))
+    res_c = np.where(free, hc + lam * dgc * dc - bc, 0.0)
+    scale_c = np.where(free, sc + lam * dgc * np.abs(dc) + np.abs(bc), 0.0)
+    res_p = hp + lam * dgp * dP - bpt
+    scale_p = sp + lam * dgp * np.abs(dP) + np.abs(bpt)
+    return res_c, scale_c, res_p, scale_p
 
 
 def apply(R, t, P, dcam, dP):

@@ -22,6 +22,7 @@ PGS_ERR_CUDA = -6
 PGS_ERR_OOM = -7
 PGS_ERR_INTERNAL = -8
 PGS_ERR_TOO_LARGE = -9
+PGS_ERR_NOT_PD = -10
 
 PGS_BUF_KEYS = 0
 PGS_BUF_VALUES = 1
@@ -44,7 +45,8 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
             "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views", "pgs_batch_reserve",
-            "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim"]
+            "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim",
+            "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -182,6 +184,20 @@ def lib():
             L.pgs_apply_mlp.restype = I
             L.pgs_make_targets.argtypes = [P, C.POINTER(PgsGaussians), C.POINTER(PgsGaussians), P]
             L.pgs_make_targets.restype = I
+            F, D = C.c_float, C.c_double
+            L.pgs_ba_create.argtypes = [C.POINTER(P), C.c_int32, I64, I64, P]
+            L.pgs_ba_create.restype = I
+            L.pgs_ba_destroy.argtypes = [P]
+            L.pgs_ba_destroy.restype = None
+            L.pgs_ba_project.argtypes = [P, P, P, P, P, P, I64, C.POINTER(F), P, P]
+            L.pgs_ba_project.restype = I
+            L.pgs_ba_step.argtypes = [P, P, P, P, P, P, P, C.POINTER(F), F, F, F, P, P, C.POINTER(D)]
+            L.pgs_ba_step.restype = I
+            L.pgs_ba_solve.argtypes = [P, P, P, P, P, P, P, C.POINTER(F), F, F, C.c_int32, F,
+                                       C.POINTER(D), C.POINTER(C.c_int32)]
+            L.pgs_ba_solve.restype = I
+            L.pgs_ba_stage_times.argtypes = [P, P, P, P, P, P, P, C.POINTER(F), F, F, F, P]
+            L.pgs_ba_stage_times.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p
             _lib = L

@@ -229,6 +229,7 @@ const char* pgs_strerror(int code) {
         case PGS_ERR_CUDA: return "CUDA runtime error";
         case PGS_ERR_OOM: return "device allocation failed";
         case PGS_ERR_INTERNAL: return "device-side consistency check failed";
+        case PGS_ERR_NOT_PD: return "bundle adjustment: damped reduced camera system not positive definite";
         case PGS_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free sort (262144 pairs)";
         default: return "unknown error";
     }

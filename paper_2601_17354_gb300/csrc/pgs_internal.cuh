@@ -212,6 +212,40 @@ int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles
 // doubles of scratch, loss_out = device {loss, mean SSIM}.
 int launch_loss_dssim(const float* image, const float* target, int W, int H, float lam, float* dm,
                       double* sums, float* grad, float* loss_out, cudaStream_t s);
+// Bundle adjustment (Sec. III-A, Eq. 2-3): problem shape and chunking, index check, per-point
+// offsets and camera masks, linearization, one Levenberg-Marquardt trial through the reduced
+// camera system, robust cost, projection.
+struct BaShape {
+    int C = 0;             // cameras
+    int64_t n = 0;         // points
+    int64_t m = 0;         // observations
+    int W = 0;             // 32-bit camera-mask words per point
+    int N = 0;             // 6 C
+    int pairs = 0;         // C (C + 1) / 2 camera pairs
+    int chc = 1, chs = 1;  // chunks of a camera's observations in the camera-block and Schur launches
+    bool blocked = false;  // blocked Cholesky of the full matrix in shared memory (6C <= 224)
+    size_t solve_smem = 0; // shared memory of the solve (0: packed matrix in global scratch)
+};
+BaShape ba_shape(int C, int64_t n, int64_t m);
+int ba_configure_solve();
+int launch_ba_check(int64_t m, int64_t n, int C, const int32_t* cam, const int32_t* pt, int* flag, cudaStream_t s);
+int launch_ba_index(const BaShape& sh, const int32_t* pt, const int32_t* cam, int64_t* start, uint32_t* mask,
+                    int64_t* cam_count, int64_t* cam_start, int64_t* cam_obs, cudaStream_t s);
+int launch_ba_linearize(const BaShape& sh, const float* R, const float* t, const float* P, const int32_t* cam,
+                        const int32_t* pt, const float* uv, const int64_t* start, const int64_t* cam_start,
+                        const int64_t* cam_obs, const float K[4], float sigma, float delta, float* Htp, double* Hpp,
+                        double* bp, double* camp, double* cost, cudaStream_t s, cudaEvent_t* ev = nullptr);
+int launch_ba_trial(const BaShape& sh, const int32_t* pt, const int64_t* start, const uint32_t* mask,
+                    const int64_t* cam_start, const int64_t* cam_obs, const int32_t* cam, const float* Htp,
+                    const double* Hpp, const double* bp, const double* camp, double lam, int fixed_axis, double* Hinv,
+                    double* y, float* E, double* schp, double* rhsp, double* Sfull, double* rhs, float* Aglob,
+                    double* dc, const float* R, const float* t, const float* P, float* Rn, float* tn, float* Pn,
+                    float* dcam, float* dP, int* status, cudaStream_t s, cudaEvent_t* ev = nullptr);
+int launch_ba_cost(const BaShape& sh, const float* R, const float* t, const float* P, const int32_t* cam,
+                   const float* uv, const int64_t* start, const float K[4], float sigma, float delta, double* cost,
+                   cudaStream_t s);
+int launch_ba_project(int64_t m, int64_t n, int C, const float* R, const float* t, const float* P, const int32_t* cam,
+                      const int32_t* pt, const float K[4], float* uv, float* z, cudaStream_t s);
 // K7: L1 loss; K10: fused Adam over all parameter groups.
 int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
                     float* loss_out, const Scratch& sc, cudaStream_t s);

@@ -269,8 +269,10 @@ def batched_scenes(seed: int, n_scenes: int = 16, views_per_scene: int = 4,
 @dataclass
 class BAProblem:
     """Bundle-adjustment inputs drawn for the geometry prior (Sec. III-A): ground-truth ring cameras
-    and surface points, their perturbed starting values, and per (camera, point) pixel noise.
-    Which pairs are observed and where (the projection) is left to the caller."""
+    and surface points, their perturbed starting values, per (camera, point) pixel noise, and per
+    point a feature track over consecutive cameras (start, length), as a tracker following a
+    feature through a keyframe sequence would give.  Which pairs are observed and where (the
+    projection) is left to the caller."""
     K: tuple                 # (fx, fy, cx, cy)
     width: int
     height: int
@@ -282,6 +284,8 @@ class BAProblem:
     P_init: np.ndarray       # [n][3]
     noise: np.ndarray        # [C][n][2] pixel noise, sigma `pixel_sigma`
     pixel_sigma: float
+    track_start: np.ndarray  # [n] first camera of the point's feature track
+    track_len: np.ndarray    # [n] track length in consecutive cameras (2..12)
 
 
 def _small_rotation(rng: np.random.Generator, max_deg: float) -> np.ndarray:
@@ -307,5 +311,7 @@ def ba_problem(seed: int, n_cams: int = 32, n_points: int = 20000, width: int = 
     tp = t + np.vstack([np.zeros(3), rng.normal(0.0, trans, (n_cams - 1, 3))])
     Pp = P + rng.normal(0.0, point, P.shape)
     noise = rng.normal(0.0, pixel_sigma, (n_cams, n_points, 2))
+    track_start = rng.integers(0, n_cams, n_points)
+    track_len = rng.integers(2, 13, n_points)
     return BAProblem((focal, focal, width / 2.0, height / 2.0), width, height, R, t, P, Rp, tp, Pp,
-                     noise, pixel_sigma)
+                     noise, pixel_sigma, track_start, track_len)
