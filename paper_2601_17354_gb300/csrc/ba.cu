@@ -40,6 +40,7 @@ namespace {
 constexpr int kBaThreads = 256;
 constexpr int kPointThreads = 64;  // per-point kernels: ~80 CTAs per 20k points would leave SMs idle
 constexpr int kSolveThreads = 1024;
+constexpr int kBlockedThreads = 512;  // 128 registers a thread: the 32-float rows stay in registers
 constexpr int kMaxN = 6 * 256;
 constexpr int kMaxBlockedN = 224;  // (224 x 225) FP32 = 197 KB of shared memory
 constexpr size_t kMaxSolveSmem = 200 * 1024;  // + 13 KB static: within the 227 KB a CTA may use
@@ -458,9 +459,10 @@ k_ba_assemble(int C, int chc, int chs, const double* __restrict__ camp, const do
 
 // fixed rows (gauge, unobserved) and the Jacobi scale: s_id[i] = 1 / sqrt(S_ii), 0 for a fixed row;
 // s_rhs[i] = rhs_i / sqrt(S_ii) (FP32: the scaled system is what gets factored)
+template <int kThreads>
 __device__ __forceinline__ void scale_rows(int N, int NP, int fixed_axis, const double* __restrict__ S,
                                            const double* __restrict__ rhs, float* s_id, float* s_rhs) {
-    for (int i = threadIdx.x; i < NP; i += kSolveThreads) {
+    for (int i = threadIdx.x; i < NP; i += kThreads) {
         if (i >= N) {
             s_id[i] = 0.f;
             s_rhs[i] = 0.f;
@@ -468,7 +470,7 @@ __device__ __forceinline__ void scale_rows(int N, int NP, int fixed_axis, const 
         }
         const double dg = S[(int64_t)i * N + i];
         const bool fixed = i < 6 || i == 9 + fixed_axis || !(dg > 0.0);
-        const float id = fixed ? 0.f : 1.0f / sqrtf((float)dg);
+        const float id = fixed ? 0.f : rsqrtf((float)dg);
         s_id[i] = id;
         s_rhs[i] = fixed ? 0.f : (float)rhs[i] * id;
     }
@@ -491,7 +493,7 @@ k_ba_solve(int C, const double* __restrict__ S, const double* __restrict__ rhs, 
     const int N = 6 * C;
     float* A = Aglob ? Aglob : s_dyn;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = kSolveThreads / 32;
-    scale_rows(N, N, fixed_axis, S, rhs, s_d, s_rhs);
+    scale_rows<kSolveThreads>(N, N, fixed_axis, S, rhs, s_d, s_rhs);
     __syncthreads();
     for (int i = warp; i < N; i += warps) {
         const int64_t oi = row_off(i, N);
@@ -528,70 +530,113 @@ k_ba_solve(int C, const double* __restrict__ S, const double* __restrict__ rhs, 
 }
 
 // ---- blocked solve (N padded to NP, a multiple of 32, NP <= 224): full lower triangle in shared
-// memory, row stride NP + 1 (column walks hit distinct banks), right-looking by 32-column panels:
-// one warp factors the diagonal block from registers, warps solve the rows below it, all threads
-// update the trailing lower triangle; 3 barriers a panel instead of one a column.
+// memory, row stride NP + 1 (column walks hit distinct banks), Cholesky right-looking by 8-column
+// panels (one warp factors the diagonal block in registers, a thread per
+// row solves the rows below it, 4 x 4 register micro-tiles update the trailing lower triangle; one
+// barrier per column step, whatever its form, cost ~1k cycles here, so the column steps are kept
+// inside a warp), then forward and back substitution by 32-row panels.
 
-__global__ void __launch_bounds__(kSolveThreads)
+constexpr int kPanel = 8;  // factorization panel width: 3 barriers a panel, 8 short column steps in registers
+
+// warp: Cholesky of the kPanel x kPanel diagonal block at B (row stride ld), lane r < kPanel
+// holding row r in registers; rdiag[k] = 1 / L_kk.  The pivot goes through the hardware
+// reciprocal square root (2 ulp): the correctly rounded sqrt and division are multi-instruction
+// sequences, and they sit on the dependent chain of every column.
+__device__ __forceinline__ void factor_diag_block(float* B, int ld, int lane, float* rdiag, int* status) {
+    float a[kPanel];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) a[c] = (lane < kPanel && c <= lane) ? B[lane * ld + c] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kPanel; ++k) {
+        float d = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(d > 0.f)) {
+            if (lane == 0) atomicOr(status, 1);
+            d = 1.f;
+        }
+        const float rs = rsqrtf(d);
+        if (lane == 0) rdiag[k] = rs;
+        a[k] = lane == k ? d * rs : (lane > k ? a[k] * rs : a[k]);
+#pragma unroll
+        for (int c = k + 1; c < kPanel; ++c) {
+            const float lck = __shfl_sync(0xffffffffu, a[k], c);
+            if (lane >= c) a[c] = fmaf(-a[k], lck, a[c]);
+        }
+    }
+    if (lane < kPanel)
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c)
+            if (c <= lane) B[lane * ld + c] = a[c];
+}
+
+__global__ void __launch_bounds__(kBlockedThreads)
 k_ba_solve_blocked(int C, const double* __restrict__ S, const double* __restrict__ rhs, int fixed_axis,
                    double* __restrict__ dc, int* __restrict__ status) {
     extern __shared__ float A[];
     __shared__ float s_rhs[kMaxBlockedN];
     __shared__ float s_id[kMaxBlockedN];  // 1 / sqrt of the diagonal; 0 marks a fixed (or padding) row
+    __shared__ float s_rdiag[kMaxBlockedN];  // 1 / L_kk
     const int N = 6 * C, NP = (N + 31) & ~31, ld = NP + 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = kSolveThreads / 32;
-    scale_rows(N, NP, fixed_axis, S, rhs, s_id, s_rhs);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = kBlockedThreads / 32;
+    scale_rows<kBlockedThreads>(N, NP, fixed_axis, S, rhs, s_id, s_rhs);
     __syncthreads();
     for (int r = warp; r < NP; r += warps)
+#pragma unroll 4
         for (int c = lane; c <= r; c += 32)
             A[r * ld + c] = r < N ? scaled_entry(S, N, r, c, s_id) : (r == c ? 1.f : 0.f);
     __syncthreads();
-    for (int c0 = 0; c0 < NP; c0 += 32) {
-        // diagonal block, thread (warp, lane) = element (row, column) of the block, column by column
-        float* B = A + c0 * ld + c0;
-        for (int k = 0; k < 32; ++k) {
-            __syncthreads();  // the updates of column k - 1, including B_kk, are visible
-            const float d = B[k * ld + k];
-            if (threadIdx.x == 0 && !(d > 0.f)) atomicOr(status, 1);
-            const float piv = sqrtf(d > 0.f ? d : 1.f);
-            if (lane == k && warp > k) B[warp * ld + k] /= piv;
-            __syncthreads();  // column k scaled; every thread has read B_kk
-            if (warp == k && lane == k) B[k * ld + k] = piv;
-            if (lane > k && lane <= warp) B[warp * ld + lane] = fmaf(-B[warp * ld + k], B[lane * ld + k], B[warp * ld + lane]);
-        }
+    for (int c0 = 0; c0 < NP; c0 += kPanel) {
+        if (warp == 0) factor_diag_block(A + c0 * ld + c0, ld, lane, s_rdiag + c0, status);
         __syncthreads();
-        // rows below the panel: x L_pp^T = a, forward substitution column by column
-        const float rd = 1.0f / A[(c0 + lane) * ld + c0 + lane];
-        for (int r = c0 + 32 + warp; r < NP; r += warps) {
-            float x = A[r * ld + c0 + lane];
+        // rows below the panel, thread per row: x L_pp^T = a by forward substitution
+        const int t0 = c0 + kPanel;
+        for (int r = t0 + threadIdx.x; r < NP; r += kBlockedThreads) {
+            float x[kPanel];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                if (lane == k) x *= rd;
-                const float xk = __shfl_sync(0xffffffffu, x, k);
-                if (lane > k) x = fmaf(-A[(c0 + lane) * ld + c0 + k], xk, x);
+            for (int q = 0; q < kPanel; ++q) x[q] = A[r * ld + c0 + q];
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) {
+                const float* Lk = A + (c0 + k) * ld + c0;
+                float v = x[k];
+#pragma unroll
+                for (int q = 0; q < k; ++q) v = fmaf(-Lk[q], x[q], v);
+                x[k] = v * s_rdiag[c0 + k];
             }
-            A[r * ld + c0 + lane] = x;
+#pragma unroll
+            for (int q = 0; q < kPanel; ++q) A[r * ld + c0 + q] = x[q];
         }
         __syncthreads();
-        // trailing lower triangle: A_rc -= sum_q L_rq L_cq over the panel's columns
-        const int t0 = c0 + 32, nt = (NP - t0) >> 5;
-        for (int ti = 0; ti < nt; ++ti)
-            for (int tj = 0; tj <= ti; ++tj) {
-                const int r = t0 + 32 * ti + warp, c = t0 + 32 * tj + lane;
-                if (c > r) continue;
-                const float* Lr = A + r * ld + c0;
-                const float* Lc = A + c * ld + c0;
-                float acc = 0.f;
+        // trailing lower triangle in 4 x 4 micro-tiles: A_rc -= sum_q L_rq L_cq over the panel
+        const int mt = (NP - t0) >> 2;
+        for (int mi = warp; mi < mt; mi += warps)
+            for (int mj = lane; mj <= mi; mj += 32) {
+                const float* Lr = A + (t0 + 4 * mi) * ld + c0;
+                const float* Lc = A + (t0 + 4 * mj) * ld + c0;
+                float acc[4][4] = {};
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc = fmaf(Lr[q], Lc[q], acc);
-                A[r * ld + c] -= acc;
+                for (int q = 0; q < kPanel; ++q) {
+                    float lr[4], lc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        lr[u] = Lr[u * ld + q];
+                        lc[u] = Lc[u * ld + q];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lr[u], lc[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (mi > mj || v <= u) A[(t0 + 4 * mi + u) * ld + t0 + 4 * mj + v] -= acc[u][v];
             }
         __syncthreads();
     }
     // L z = rhs
     for (int c0 = 0; c0 < NP; c0 += 32) {
         if (warp == 0) {
-            const float rd = 1.0f / A[(c0 + lane) * ld + c0 + lane];
+            const float rd = s_rdiag[c0 + lane];
             float z = s_rhs[c0 + lane];
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
@@ -612,7 +657,7 @@ k_ba_solve_blocked(int C, const double* __restrict__ S, const double* __restrict
     // L^T x = z, panels from the last
     for (int c0 = NP - 32; c0 >= 0; c0 -= 32) {
         if (warp == 0) {
-            const float rd = 1.0f / A[(c0 + lane) * ld + c0 + lane];
+            const float rd = s_rdiag[c0 + lane];
             float x = s_rhs[c0 + lane];
 #pragma unroll
             for (int k = 31; k >= 0; --k) {
@@ -630,7 +675,7 @@ k_ba_solve_blocked(int C, const double* __restrict__ S, const double* __restrict
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < N; i += kSolveThreads) dc[i] = (double)s_rhs[i] * s_id[i];
+    for (int i = threadIdx.x; i < N; i += kBlockedThreads) dc[i] = (double)s_rhs[i] * s_id[i];
 }
 
 // Delta_p = H^-1 (b_p - sum H_tp^T Delta_t); candidate points
@@ -827,7 +872,7 @@ int launch_ba_trial(const BaShape& sh, const int32_t* pt, const int64_t* start, 
     k_ba_assemble<<<(unsigned)(((int64_t)sh.N * sh.N + kBaThreads - 1) / kBaThreads), kBaThreads, 0, s>>>(
         sh.C, sh.chc, sh.chs, camp, schp, rhsp, lam, Sfull, rhs);
     if (sh.blocked)
-        k_ba_solve_blocked<<<1, kSolveThreads, sh.solve_smem, s>>>(sh.C, Sfull, rhs, fixed_axis, dc, status);
+        k_ba_solve_blocked<<<1, kBlockedThreads, sh.solve_smem, s>>>(sh.C, Sfull, rhs, fixed_axis, dc, status);
     else
         k_ba_solve<<<1, kSolveThreads, sh.solve_smem, s>>>(sh.C, Sfull, rhs, fixed_axis,
                                                            sh.solve_smem ? nullptr : Aglob, dc, status);
