@@ -315,3 +315,103 @@ def ba_problem(seed: int, n_cams: int = 32, n_points: int = 20000, width: int = 
     track_len = rng.integers(2, 13, n_points)
     return BAProblem((focal, focal, width / 2.0, height / 2.0), width, height, R, t, P, Rp, tp, Pp,
                      noise, pixel_sigma, track_start, track_len)
+
+
+# ------------------------------------------------------------------------------------------------
+# Multi-view stereo inputs: textured analytic surfaces seen by ring keyframes
+# ------------------------------------------------------------------------------------------------
+@dataclass
+class MVSScene:
+    """Keyframe images of textured spheres and squares, their exact depth maps, and sparse surface
+    points standing in for the bundle-adjusted points (Sec. III-A).  The images come from ray
+    casting the analytic surfaces (pixel-centre rays, nearest hit), so they are exact data for
+    both the CUDA path and the oracle and the depth maps are the ground truth."""
+    surfaces: Surfaces
+    cameras: list            # ring keyframes
+    images: list             # [3][H][W] float32 per camera (None where not rendered)
+    depths: list             # [H][W] float64 camera-z of the visible surface, inf on background
+    sparse: np.ndarray       # [n][3] float64 surface points with N(0, 0.005) noise
+
+
+def _hash_cells(ix, iy, iz, salt):
+    """Deterministic pseudo-random values in [0, 1) of integer lattice cells (a multiply-xorshift
+    mix of the three cell indices)."""
+    h = (ix.astype(np.int64) * 73856093) ^ (iy.astype(np.int64) * 19349663) ^ (iz.astype(np.int64) * 83492791)
+    h = (h ^ salt) & 0xFFFFFFFF
+    h = (h * 0x45D9F3B) & 0xFFFFFFFF
+    h = ((h >> 16) ^ h) * 0x45D9F3B & 0xFFFFFFFF
+    h = (h >> 16) ^ h
+    return (h & 0xFFFFFF) / float(1 << 24)
+
+
+def surface_texture(points: np.ndarray, surface_id: np.ndarray, tints: np.ndarray) -> np.ndarray:
+    """RGB [n][3] of surface points: a per-surface tint times two octaves of cell noise (cells of
+    0.02 and 0.05 world units), in [0.15, 1]."""
+    fine = _hash_cells(*np.floor(points / 0.02).T.astype(np.int64), 17)
+    coarse = _hash_cells(*np.floor(points / 0.05).T.astype(np.int64), 29)
+    lum = 0.15 + 0.85 * (0.6 * fine + 0.4 * coarse)
+    return lum[:, None] * tints[surface_id]
+
+
+def cast_surfaces(surf: Surfaces, cam: Camera):
+    """Ray-cast the surfaces through every pixel centre of ``cam``: (hit points [H*W][3], camera-z
+    depth [H*W] (inf on background), surface index [H*W] (-1 on background))."""
+    H, W = cam.height, cam.width
+    R = cam.viewmat[:, :3].astype(np.float64)
+    t = cam.viewmat[:, 3].astype(np.float64)
+    eye = -R.T @ t
+    xs, ys = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    dirs_c = np.stack([(xs - cam.cx) / cam.fx, (ys - cam.cy) / cam.fy, np.ones_like(xs)], axis=-1).reshape(-1, 3)
+    dirs = dirs_c @ R                      # world directions with camera-z component 1
+    best = np.full(H * W, np.inf)
+    sid = np.full(H * W, -1)
+    for k in range(len(surf.sphere_r)):
+        oc = eye - surf.sphere_c[k]
+        a = np.einsum("ij,ij->i", dirs, dirs)
+        b = 2.0 * dirs @ oc
+        c = oc @ oc - surf.sphere_r[k] ** 2
+        disc = b * b - 4 * a * c
+        ok = disc > 0
+        sq = np.sqrt(np.where(ok, disc, 0.0))
+        t0 = (-b - sq) / (2 * a)
+        t1 = (-b + sq) / (2 * a)
+        tt = np.where(t0 > 1e-6, t0, t1)
+        hit = ok & (tt > 1e-6) & (tt < best)
+        best = np.where(hit, tt, best)
+        sid = np.where(hit, k, sid)
+    ns = len(surf.sphere_r)
+    for k in range(len(surf.plane_side)):
+        n = np.cross(surf.plane_u[k], surf.plane_v[k])
+        den = dirs @ n
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tt = ((surf.plane_c[k] - eye) @ n) / den
+        p = eye + tt[:, None] * dirs
+        du = (p - surf.plane_c[k]) @ surf.plane_u[k]
+        dv = (p - surf.plane_c[k]) @ surf.plane_v[k]
+        half = 0.5 * surf.plane_side[k]
+        hit = (np.abs(den) > 1e-12) & (tt > 1e-6) & (np.abs(du) <= half) & (np.abs(dv) <= half) & (tt < best)
+        best = np.where(hit, tt, best)
+        sid = np.where(hit, ns + k, sid)
+    pts = eye + np.where(np.isfinite(best), best, 0.0)[:, None] * dirs
+    return pts, best, sid   # dirs have camera-z 1, so the ray parameter is the camera-z depth
+
+
+def mvs_scene(seed: int, n_cameras: int = 64, width: int = 640, height: int = 360, focal: float = 500.0,
+              n_sparse: int = 20000, views=None) -> MVSScene:
+    """Ring keyframes (as the surface scene, 640 x 360 at fx = 500: the 1280 x 720 keyframes at half
+    resolution) of 8 textured spheres and 4 textured squares; images and depth maps for ``views``
+    (all cameras by default)."""
+    rng = np.random.default_rng(seed)
+    surf = random_surfaces(rng)
+    tints = rng.uniform(0.4, 1.0, size=(len(surf.sphere_r) + len(surf.plane_side), 3))
+    cams = ring_cameras(rng, n_cameras, width, height, focal)
+    sparse = sample_surface_points(rng, surf, n_sparse).T + rng.normal(0.0, 0.005, size=(n_sparse, 3))
+    images, depths = [None] * n_cameras, [None] * n_cameras
+    for i in (range(n_cameras) if views is None else views):
+        pts, depth, sid = cast_surfaces(surf, cams[i])
+        rgb = np.zeros((height * width, 3))
+        hit = sid >= 0
+        rgb[hit] = surface_texture(pts[hit], sid[hit], tints)
+        images[i] = _f32(rgb.reshape(height, width, 3).transpose(2, 0, 1))
+        depths[i] = depth.reshape(height, width)
+    return MVSScene(surf, cams, images, depths, sparse)
