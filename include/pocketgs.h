@@ -402,6 +402,54 @@ int pgs_ba_stage_times(pgs_ba* ba, const float* R, const float* t, const float* 
                        const int32_t* pt, const float* uv, const float* K, float sigma, float huber_delta,
                        float lambda, float* ms);
 
+/* ------------------------------------------------------------------------------------------
+   Single-reference cost-volume MVS of the geometry prior (Sec. III-A): depth range of a target
+   keyframe from the projected sparse points ([0.5 q.05, 1.5 q.95]), its reference keyframe by
+   Eq. 4, census matching over a plane sweep, SGM aggregation, the 0.4 confidence filter, and
+   fusion of the kept depths into world points.
+     luma Y = 0.299 R + 0.587 G + 0.114 B; census: 7 x 7 window, 48 bits in raster order of the
+     neighbours, set when the neighbour is darker, outside neighbours clear; D planes
+     fronto-parallel in the target, uniform in inverse depth, plane 0 the farthest; cost = Hamming
+     distance of the census codes at the target pixel and at the reference pixel its centre maps to
+     through the plane (24 when behind the reference or outside it); SGM: 4 paths, P1 = 8,
+     P2 = 32; a pixel is kept when its best plane is interior and 1 - S1 / S2 >= 0.4, S2 the best
+     aggregated cost two or more planes away; depth refined by the parabola through the best plane
+     and its neighbours, in inverse depth.  Eq. 4: b = distance of the camera centres, b_target =
+     0.1 x the median sparse depth, sigma_b = 0.5 b_target, alpha = angle between the optical
+     axes, alpha_min = 5 degrees; ties go to the lowest index.
+   Images are device [3][H][W] FP32 of the context's size; cameras are pgs_camera (viewmat world ->
+   camera) of that size.  A context holds one target's census codes (u64 [H][W] x 2), cost volume
+   (u8 [H][W][D]) and aggregated cost (u16 [H][W][D]).
+   ------------------------------------------------------------------------------------------ */
+typedef struct pgs_mvs pgs_mvs;
+#define PGS_MVS_CENSUS_TARGET 0    /* u64 [H][W] */
+#define PGS_MVS_CENSUS_REFERENCE 1 /* u64 [H][W] */
+#define PGS_MVS_COST 2             /* u8 [H][W][D] */
+#define PGS_MVS_AGGREGATED 3       /* u16 [H][W][D] */
+#define PGS_MVS_PLANE_MAPS 4       /* FP32 [D][9], row-major 3 x 3 per plane */
+/* Buffers for width x height images and `planes` (3..128) depth hypotheses, work on cuda_stream. */
+int pgs_mvs_create(pgs_mvs** out, int32_t width, int32_t height, int32_t planes, void* cuda_stream);
+void pgs_mvs_destroy(pgs_mvs* mvs);
+/* out[0..2] (host) = d_min, d_max, median sparse depth of the target, from the camera-z of the
+   points [n][3] (device FP32) in front of it (z > 0.2) and inside its image; quantiles interpolate
+   linearly between order statistics.  PGS_ERR_INVALID_ARG when no point qualifies.  Synchronises. */
+int pgs_mvs_depth_range(pgs_mvs* mvs, const pgs_camera* target, const float* points, int64_t n, double* out);
+/* The Eq. 4 reference of keyframe `target` among cams[0..count) (host array, count <= 1024):
+   *ref (host), and the scores (host [count], optional; -inf for the target).  Synchronises. */
+int pgs_mvs_select_reference(pgs_mvs* mvs, const pgs_camera* cams, int32_t count, int32_t target,
+                             double median_depth, double* scores, int32_t* ref);
+/* Depth map of the target (device [H][W] FP32 camera-z, NaN where not kept) between d_min and
+   d_max; *kept (host, optional: synchronises when given) = kept pixels. */
+int pgs_mvs_depth(pgs_mvs* mvs, const pgs_camera* target, const pgs_camera* reference, const float* image_t,
+                  const float* image_r, double d_min, double d_max, float* depth, int64_t* kept);
+/* Copy an internal buffer of the last pgs_mvs_depth (PGS_MVS_*) to device memory dst. */
+int pgs_mvs_read(pgs_mvs* mvs, int32_t what, void* dst, int64_t bytes);
+/* World points (device [capacity][3] FP32) and row-major pixel indices (device int32) of the
+   finite depths of a depth map, in pixel order; *count (host) = how many there are.
+   PGS_ERR_CAPACITY when that exceeds capacity (the first `capacity` are written).  Synchronises. */
+int pgs_mvs_fuse(pgs_mvs* mvs, const pgs_camera* target, const float* depth, float* points, int32_t* pixels,
+                 int64_t capacity, int64_t* count);
+
 /* Static description of an error code. */
 const char* pgs_strerror(int code);
 

@@ -24,6 +24,12 @@ PGS_ERR_INTERNAL = -8
 PGS_ERR_TOO_LARGE = -9
 PGS_ERR_NOT_PD = -10
 
+PGS_MVS_CENSUS_TARGET = 0
+PGS_MVS_CENSUS_REFERENCE = 1
+PGS_MVS_COST = 2
+PGS_MVS_AGGREGATED = 3
+PGS_MVS_PLANE_MAPS = 4
+
 PGS_BUF_KEYS = 0
 PGS_BUF_VALUES = 1
 PGS_BUF_RANGES = 2
@@ -46,7 +52,9 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
             "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views", "pgs_batch_reserve",
             "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim",
-            "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times"]
+            "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times",
+            "pgs_mvs_create", "pgs_mvs_destroy", "pgs_mvs_depth_range", "pgs_mvs_select_reference",
+            "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -198,6 +206,22 @@ def lib():
             L.pgs_ba_solve.restype = I
             L.pgs_ba_stage_times.argtypes = [P, P, P, P, P, P, P, C.POINTER(F), F, F, F, P]
             L.pgs_ba_stage_times.restype = I
+            CamP = C.POINTER(PgsCamera)
+            L.pgs_mvs_create.argtypes = [C.POINTER(P), C.c_int32, C.c_int32, C.c_int32, P]
+            L.pgs_mvs_create.restype = I
+            L.pgs_mvs_destroy.argtypes = [P]
+            L.pgs_mvs_destroy.restype = None
+            L.pgs_mvs_depth_range.argtypes = [P, CamP, P, I64, C.POINTER(D)]
+            L.pgs_mvs_depth_range.restype = I
+            L.pgs_mvs_select_reference.argtypes = [P, CamP, C.c_int32, C.c_int32, D, C.POINTER(D),
+                                                   C.POINTER(C.c_int32)]
+            L.pgs_mvs_select_reference.restype = I
+            L.pgs_mvs_depth.argtypes = [P, CamP, CamP, P, P, D, D, P, C.POINTER(I64)]
+            L.pgs_mvs_depth.restype = I
+            L.pgs_mvs_read.argtypes = [P, C.c_int32, P, I64]
+            L.pgs_mvs_read.restype = I
+            L.pgs_mvs_fuse.argtypes = [P, CamP, P, P, P, I64, C.POINTER(I64)]
+            L.pgs_mvs_fuse.restype = I
             L.pgs_strerror.argtypes = [I]
             L.pgs_strerror.restype = C.c_char_p
             _lib = L

@@ -1,7 +1,7 @@
 """Build libpocketgs.so in-tree for sm_103a (GB300) with nvcc.
 
-Each translation unit compiles in parallel; the decision-path unit (project.cu) is compiled with
---fmad=false so its prescribed fp32 operation order is kept exactly.  Output:
+Each translation unit compiles in parallel; the decision-path units (project.cu, mvs.cu) are
+compiled with --fmad=false so their prescribed floating-point operation order is kept exactly.  Output:
 paper_2601_17354_gb300/_build/libpocketgs.so (git-ignored).
 """
 from __future__ import annotations
@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-PER_FILE = {"project.cu": ["--fmad=false"]}
+PER_FILE = {"project.cu": ["--fmad=false"], "mvs.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

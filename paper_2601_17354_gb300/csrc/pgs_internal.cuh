@@ -246,6 +246,23 @@ int launch_ba_cost(const BaShape& sh, const float* R, const float* t, const floa
                    cudaStream_t s);
 int launch_ba_project(int64_t m, int64_t n, int C, const float* R, const float* t, const float* P, const int32_t* cam,
                       const int32_t* pt, const float K[4], float* uv, float* z, cudaStream_t s);
+// Single-reference MVS (Sec. III-A): census, plane maps + cost volume, SGM, selection, fusion,
+// sparse-depth quantiles, Eq. 4 reference choice.
+int launch_mvs_census(const float* rgb, int W, int H, uint64_t* code, cudaStream_t s);
+int launch_mvs_cost(const pgs_camera& t, const pgs_camera& r, const uint64_t* cen_t, const uint64_t* cen_r, int W,
+                    int H, int D, double inv_far, double step, float* maps, uint8_t* C, cudaStream_t s);
+int launch_mvs_sgm(const uint8_t* C, uint16_t* S, int W, int H, int D, cudaStream_t s);
+int launch_mvs_select(const uint16_t* S, int W, int H, int D, double inv_far, double step, float* depth,
+                      uint8_t* kept, unsigned long long* count, cudaStream_t s);
+int launch_mvs_fuse(const float* depth, int W, int H, const pgs_camera& cam, uint32_t* cta_scratch, int64_t* total,
+                    int64_t capacity, float* points, int32_t* pix, cudaStream_t s);
+int mvs_fuse_ctas(int W, int H);
+int launch_mvs_range(const float* P, int64_t n, const pgs_camera& cam, double* zbuf, unsigned long long* count,
+                     double* out, int* status, cudaStream_t s);
+int launch_mvs_reference(const void* cams_f, int count, int target, double median, double* scores, int* best,
+                         cudaStream_t s);
+size_t mvs_camf_bytes();
+void mvs_pack_cameras(const pgs_camera* cams, int count, void* host_out);
 // K7: L1 loss; K10: fused Adam over all parameter groups.
 int launch_loss_l1(const float* image, const float* target, int64_t n, float* grad,
                     float* loss_out, const Scratch& sc, cudaStream_t s);
