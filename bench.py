@@ -479,6 +479,53 @@ def run_ba(reps: int = 10, iters: int = 10) -> dict:
             "cost_initial": float(costs[0]), "cost_final": float(costs[-1]), "accepted": acc, "iterations": iters}
 
 
+def run_mvs(reps: int = 10, every: int = 4) -> dict:
+    """Single-reference MVS of the geometry prior (Sec. III-A) on 640 x 360 keyframes (the
+    1280 x 720 ring at half resolution) of a textured synthetic scene with 20k sparse points, 64
+    planes: device time of each stage of one target (median of reps), and the whole per-target
+    flow (range, Eq. 4 reference, depth, fusion) over every `every`-th keyframe with the fused
+    cloud's size and its depth error against the ray-cast ground truth."""
+    import numpy as np
+    import torch
+    from paper_2601_17354_gb300 import mvs as V
+    from paper_2601_17354_gb300 import synthetic as S
+    sc = S.mvs_scene(3)
+    cams = sc.cameras
+    W, H, D = cams[0].width, cams[0].height, 64
+    mv = V.MultiViewStereo(W, H, D)
+    images = [torch.from_numpy(im).cuda() for im in sc.images]
+    pts = torch.from_numpy(sc.sparse.astype(np.float32)).cuda()
+    d_min, d_max, med = mv.depth_range(cams[4], pts)
+    ref, _ = mv.select_reference(cams, 4, med)
+    rows = [mv.stage_times(cams[4], cams[ref], images[4], images[ref], d_min, d_max) for _ in range(reps + 2)][2:]
+    stages = {k: float(np.median([r[k] for r in rows])) for k in V.MultiViewStereo.STAGES}
+    targets = list(range(0, len(cams), every))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(mv.stream)
+    clouds, good, total = [], 0, 0
+    depths = []
+    for t in targets:
+        _, _, depth, p, _ = mv.reconstruct(cams, images, t, pts)
+        clouds.append(p)
+        depths.append(depth)
+    ev1.record(mv.stream)
+    torch.cuda.synchronize()
+    for t, depth in zip(targets, depths):
+        g = depth.cpu().numpy()
+        gt = sc.depths[t]
+        fg = np.isfinite(g) & np.isfinite(gt)
+        rel = np.abs(g[fg] - gt[fg]) / gt[fg]
+        good += int((rel < 0.02).sum())
+        total += int(np.isfinite(g).sum())
+    ms_flow = ev0.elapsed_time(ev1)
+    return {"workload": f"{len(targets)} target keyframes of 64, {W}x{H}, {D} planes, 20000 sparse points",
+            "stage_ms": stages, "depth_ms_device": sum(stages.values()),
+            "flow_ms_per_target": ms_flow / len(targets),
+            "fused_points": int(sum(len(c) for c in clouds)),
+            "kept_within_2pct_of_gt": good / max(total, 1)}
+
+
 def run_ours(args):
     import torch
     from paper_2601_17354_gb300 import _lib as L
@@ -641,6 +688,7 @@ def run_ours(args):
         out["replay_cache"] = run_replay(init, cams, targets, tile)
         out["dssim"] = run_dssim(init, cams, targets, tile, tuned)
         out["bundle_adjustment"] = run_ba()
+        out["mvs"] = run_mvs()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         full, spent, desc = oracle_step_seconds(sc, cams[0], 16)
         out["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle",

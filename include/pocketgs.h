@@ -442,6 +442,10 @@ int pgs_mvs_select_reference(pgs_mvs* mvs, const pgs_camera* cams, int32_t count
    d_max; *kept (host, optional: synchronises when given) = kept pixels. */
 int pgs_mvs_depth(pgs_mvs* mvs, const pgs_camera* target, const pgs_camera* reference, const float* image_t,
                   const float* image_r, double d_min, double d_max, float* depth, int64_t* kept);
+/* pgs_mvs_depth with device times (ms): ms[0] census of both images, ms[1] plane maps and cost
+   volume, ms[2] SGM, ms[3] selection.  Synchronises. */
+int pgs_mvs_stage_times(pgs_mvs* mvs, const pgs_camera* target, const pgs_camera* reference, const float* image_t,
+                        const float* image_r, double d_min, double d_max, float* depth, float* ms);
 /* Copy an internal buffer of the last pgs_mvs_depth (PGS_MVS_*) to device memory dst. */
 int pgs_mvs_read(pgs_mvs* mvs, int32_t what, void* dst, int64_t bytes);
 /* World points (device [capacity][3] FP32) and row-major pixel indices (device int32) of the

@@ -54,7 +54,7 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim",
             "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times",
             "pgs_mvs_create", "pgs_mvs_destroy", "pgs_mvs_depth_range", "pgs_mvs_select_reference",
-            "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse"]
+            "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse", "pgs_mvs_stage_times"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -218,6 +218,8 @@ def lib():
             L.pgs_mvs_select_reference.restype = I
             L.pgs_mvs_depth.argtypes = [P, CamP, CamP, P, P, D, D, P, C.POINTER(I64)]
             L.pgs_mvs_depth.restype = I
+            L.pgs_mvs_stage_times.argtypes = [P, CamP, CamP, P, P, D, D, P, P]
+            L.pgs_mvs_stage_times.restype = I
             L.pgs_mvs_read.argtypes = [P, C.c_int32, P, I64]
             L.pgs_mvs_read.restype = I
             L.pgs_mvs_fuse.argtypes = [P, CamP, P, P, P, I64, C.POINTER(I64)]

@@ -14,8 +14,9 @@
 //   the minimum is interior and 5 (S2 - S1) >= 2 S2 (confidence 1 - S1 / S2 >= 0.4); parabola
 //   refinement in inverse depth; kept pixels back-projected in FP64.
 //
-// Layout: census codes [H][W] u64; cost C and aggregated cost S [H][W][D] (u8 / u16), the plane
-// index innermost so a pixel's costs are one contiguous run for every path direction.
+// Layout: census codes [H][W] u64; cost C [H][W][D] u8, the four paths' L [4][H][W][D] u8 and the
+// aggregated cost S [H][W][D] u16, the plane index innermost so a pixel's costs are one contiguous
+// run for every path direction.
 #include <cmath>
 
 #include "pgs_internal.cuh"
@@ -150,85 +151,165 @@ __global__ void k_cost(const uint64_t* __restrict__ cen_t, const uint64_t* __res
     }
 }
 
-// one SGM path, warp per scanline, lane holding planes lane * KPL .. + KPL - 1; dir 0: left to
-// right, 1: right to left, 2: top down, 3: bottom up; S = L (first path) or S += L
+// the four SGM paths in one launch (blockIdx.y = direction: 0 left to right, 1 right to left,
+// 2 top down, 3 bottom up), warp per scanline, lane holding planes lane * KPL .. + KPL - 1; each
+// path writes its own L (<= 48 + P2 = 80, a byte) so the directions run concurrently, and the
+// costs of the next steps are loaded ahead (the walk along a line is the only serial part)
 template <int KPL>
 __global__ void __launch_bounds__(128)
-k_sgm(const uint8_t* __restrict__ C, uint16_t* __restrict__ S, int W, int H, int D, int dir, int first) {
+k_sgm(const uint8_t* __restrict__ C, uint8_t* __restrict__ Lall, int W, int H, int D) {
+    const int dir = blockIdx.y;
     const int line = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const bool horiz = dir < 2;
     const int lines = horiz ? H : W, len = horiz ? W : H;
     if (line >= lines) return;
-    constexpr int kBig = 1 << 20;
-    int L[KPL];
-    for (int s = 0; s < len; ++s) {
+    uint8_t* __restrict__ Lout = Lall + (size_t)dir * W * H * D;
+    constexpr int kBig = 1 << 20, kAhead = 4;
+    auto base_of = [&](int s) {
         const int pos = (dir == 0 || dir == 2) ? s : len - 1 - s;
         const int x = horiz ? pos : line, y = horiz ? line : pos;
-        const size_t base = ((size_t)y * W + x) * D;
-        int c[KPL];
-#pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-            const int k = lane * KPL + j;
-            c[j] = k < D ? (int)C[base + k] : 0;
-        }
-        if (s == 0) {
-#pragma unroll
-            for (int j = 0; j < KPL; ++j) L[j] = lane * KPL + j < D ? c[j] : kBig;
-        } else {
-            int mloc = kBig;
-#pragma unroll
-            for (int j = 0; j < KPL; ++j) mloc = min(mloc, L[j]);
-            const int m = __reduce_min_sync(0xffffffffu, mloc);
-            const int below = __shfl_up_sync(0xffffffffu, L[KPL - 1], 1);   // plane lane*KPL - 1
-            const int above = __shfl_down_sync(0xffffffffu, L[0], 1);       // plane lane*KPL + KPL
-            int nl[KPL];
+        return ((size_t)y * W + x) * D;
+    };
+    auto load = [&](int s, int (&c)[KPL]) {
+        if (s < len) {
+            const size_t b = base_of(s);
 #pragma unroll
             for (int j = 0; j < KPL; ++j) {
                 const int k = lane * KPL + j;
-                const int lm = j > 0 ? L[j - 1] : (lane > 0 ? below : kBig);
-                const int lp = j < KPL - 1 ? L[j + 1] : (lane < 31 ? above : kBig);
-                const int best = min(min(L[j], min(lm, lp) + kP1), m + kP2);
-                nl[j] = k < D ? c[j] + best - m : kBig;
+                c[j] = k < D ? (int)__ldg(C + b + k) : 0;
             }
-#pragma unroll
-            for (int j = 0; j < KPL; ++j) L[j] = nl[j];
         }
+    };
+    int ring[kAhead][KPL];
 #pragma unroll
-        for (int j = 0; j < KPL; ++j) {
-            const int k = lane * KPL + j;
-            if (k < D) S[base + k] = (uint16_t)(first ? L[j] : (int)S[base + k] + L[j]);
+    for (int a = 0; a < kAhead; ++a) load(a, ring[a]);
+    int L[KPL];
+    for (int s0 = 0; s0 < len; s0 += kAhead) {
+#pragma unroll
+        for (int a = 0; a < kAhead; ++a) {
+            const int s = s0 + a;
+            if (s >= len) break;
+            int c[KPL];
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) c[j] = ring[a][j];
+            load(s + kAhead, ring[a]);
+            if (s == 0) {
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) L[j] = lane * KPL + j < D ? c[j] : kBig;
+            } else {
+                int mloc = kBig;
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) mloc = min(mloc, L[j]);
+                const int m = __reduce_min_sync(0xffffffffu, mloc);
+                const int below = __shfl_up_sync(0xffffffffu, L[KPL - 1], 1);   // plane lane*KPL - 1
+                const int above = __shfl_down_sync(0xffffffffu, L[0], 1);       // plane lane*KPL + KPL
+                int nl[KPL];
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) {
+                    const int k = lane * KPL + j;
+                    const int lm = j > 0 ? L[j - 1] : (lane > 0 ? below : kBig);
+                    const int lp = j < KPL - 1 ? L[j + 1] : (lane < 31 ? above : kBig);
+                    const int best = min(min(L[j], min(lm, lp) + kP1), m + kP2);
+                    nl[j] = k < D ? c[j] + best - m : kBig;
+                }
+#pragma unroll
+                for (int j = 0; j < KPL; ++j) L[j] = nl[j];
+            }
+            const size_t b = base_of(s);
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane * KPL + j;
+                if (k < D) Lout[b + k] = (uint8_t)L[j];
+            }
         }
     }
 }
 
-// winner-take-all, confidence, parabola refinement; depth (NaN where not kept) and kept flags
-__global__ void k_select(const uint16_t* __restrict__ S, int W, int H, int D, double inv_far, double step,
-                         float* __restrict__ depth, uint8_t* __restrict__ kept, unsigned long long* __restrict__ count) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)W * H) return;
-    const uint16_t* s = S + (size_t)p * D;
-    int k1 = 0, s1 = s[0];
-    for (int k = 1; k < D; ++k)
-        if (s[k] < s1) {
-            s1 = s[k];
-            k1 = k;
+// S = the sum of the four paths (written out), winner-take-all, confidence, parabola refinement;
+// depth (NaN where not kept) and kept flags.  A warp takes 32 consecutive pixels: for each, lanes
+// over the planes (as in the SGM walk: coalesced loads and stores) find the minimiser, S2 and the
+// neighbours by warp reductions and leave them with lane i for pixel i; then every lane refines its
+// own pixel, so the FP64 refinement runs on full warps (GB300's FP64 pipe costs a warp instruction
+// the same with one lane or thirty-two).
+constexpr int kSelectThreads = 256;
+
+template <int KPL>
+__global__ void __launch_bounds__(kSelectThreads)
+k_select(const uint8_t* __restrict__ Lall, uint16_t* __restrict__ S, int W, int H, int D, double inv_far,
+         double step, float* __restrict__ depth, uint8_t* __restrict__ kept, unsigned long long* __restrict__ count) {
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t n = (int64_t)W * H;
+    const size_t plane = (size_t)n * D;
+    const int64_t chunks = (n + 31) / 32, warps = (int64_t)gridDim.x * (kSelectThreads / 32);
+    constexpr int kBig = 1 << 30;
+    for (int64_t ch = (int64_t)blockIdx.x * (kSelectThreads / 32) + (threadIdx.x >> 5); ch < chunks; ch += warps) {
+        int my_k1 = 0, my_s1 = 0, my_s2 = 0, my_sm = 0, my_sp = 0;
+        for (int i = 0; i < 32; ++i) {
+            const int64_t p = ch * 32 + i;
+            if (p >= n) break;  // warp-uniform
+            int v[KPL];
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane * KPL + j;
+                v[j] = kBig;
+                if (k < D) {
+                    int t = 0;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) t += __ldg(Lall + d * plane + (size_t)p * D + k);
+                    v[j] = t;
+                    S[(size_t)p * D + k] = (uint16_t)t;
+                }
+            }
+            int loc = kBig;
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) loc = min(loc, v[j]);
+            const int s1 = __reduce_min_sync(0xffffffffu, loc);
+            int kloc = kBig;
+#pragma unroll
+            for (int j = KPL - 1; j >= 0; --j)
+                if (v[j] == s1) kloc = lane * KPL + j;
+            const int k1 = __reduce_min_sync(0xffffffffu, kloc);  // first minimiser
+            int far = kBig, mm = 0, mp = 0;
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int k = lane * KPL + j;
+                if (k < D && abs(k - k1) >= 2) far = min(far, v[j]);
+                if (k == k1 - 1) mm = v[j];
+                if (k == k1 + 1) mp = v[j];
+            }
+            const int s2 = __reduce_min_sync(0xffffffffu, far);
+            const int sm = __reduce_add_sync(0xffffffffu, mm), sp = __reduce_add_sync(0xffffffffu, mp);
+            if (lane == i) {
+                my_k1 = k1;
+                my_s1 = s1;
+                my_s2 = s2 == kBig ? s1 : s2;
+                my_sm = sm;
+                my_sp = sp;
+            }
         }
-    int s2 = 1 << 30;
-    for (int k = 0; k < D; ++k)
-        if (abs(k - k1) >= 2) s2 = min(s2, (int)s[k]);
-    if (s2 == (1 << 30)) s2 = s1;
-    const bool keep = k1 > 0 && k1 < D - 1 && s2 > 0 && 5 * (s2 - s1) >= 2 * s2;
-    float out = __int_as_float(0x7fc00000);
-    if (keep) {
-        const int sm = s[k1 - 1], sp = s[k1 + 1];
-        const int den = sm - 2 * s1 + sp;
-        const float delta = den > 0 ? __fdiv_rn((float)(sm - sp), __fmul_rn(2.f, (float)den)) : 0.f;
-        const double inv = dadd(inv_far, dmul(dadd((double)k1, (double)delta), step));
-        out = __double2float_rn(ddiv(1.0, inv));
-        atomicAdd(count, 1ull);
+        const int64_t p = ch * 32 + lane;
+        const bool live = p < n;
+        const bool keep =
+            live && my_k1 > 0 && my_k1 < D - 1 && my_s2 > 0 && 5 * (my_s2 - my_s1) >= 2 * my_s2;
+        float out = __int_as_float(0x7fc00000);
+        if (keep) {
+            const int den = my_sm - 2 * my_s1 + my_sp;
+            const float delta = den > 0 ? __fdiv_rn((float)(my_sm - my_sp), __fmul_rn(2.f, (float)den)) : 0.f;
+            const double inv = dadd(inv_far, dmul(dadd((double)my_k1, (double)delta), step));
+            out = __double2float_rn(ddiv(1.0, inv));
+        }
+        if (live) {
+            depth[p] = out;
+            kept[p] = keep ? 1 : 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && bal) atomicAdd(&s_count, __popc(bal));
     }
-    depth[p] = out;
-    kept[p] = keep ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_count) atomicAdd(count, (unsigned long long)s_count);
 }
 
 // kept-pixel counts per CTA (pixel order), then an exclusive scan in one CTA, then the points
@@ -441,22 +522,26 @@ int launch_mvs_cost(const pgs_camera& t, const pgs_camera& r, const uint64_t* ce
     return 2;
 }
 
-int launch_mvs_sgm(const uint8_t* C, uint16_t* S, int W, int H, int D, cudaStream_t s) {
-    for (int dir = 0; dir < 4; ++dir) {
-        const int lines = dir < 2 ? H : W;
-        const unsigned g = blocks((int64_t)lines * 32, 128);
-        if (D <= 32) k_sgm<1><<<g, 128, 0, s>>>(C, S, W, H, D, dir, dir == 0);
-        else if (D <= 64) k_sgm<2><<<g, 128, 0, s>>>(C, S, W, H, D, dir, dir == 0);
-        else if (D <= 96) k_sgm<3><<<g, 128, 0, s>>>(C, S, W, H, D, dir, dir == 0);
-        else k_sgm<4><<<g, 128, 0, s>>>(C, S, W, H, D, dir, dir == 0);
-    }
-    return 4;
+int launch_mvs_sgm(const uint8_t* C, uint8_t* L, int W, int H, int D, cudaStream_t s) {
+    const int lines = W > H ? W : H;
+    const dim3 g(blocks((int64_t)lines * 32, 128), 4);
+    if (D <= 32) k_sgm<1><<<g, 128, 0, s>>>(C, L, W, H, D);
+    else if (D <= 64) k_sgm<2><<<g, 128, 0, s>>>(C, L, W, H, D);
+    else if (D <= 96) k_sgm<3><<<g, 128, 0, s>>>(C, L, W, H, D);
+    else k_sgm<4><<<g, 128, 0, s>>>(C, L, W, H, D);
+    return 1;
 }
 
-int launch_mvs_select(const uint16_t* S, int W, int H, int D, double inv_far, double step, float* depth,
+int launch_mvs_select(const uint8_t* L, uint16_t* S, int W, int H, int D, double inv_far, double step, float* depth,
                       uint8_t* kept, unsigned long long* count, cudaStream_t s) {
     cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
-    k_select<<<blocks((int64_t)W * H, 256), 256, 0, s>>>(S, W, H, D, inv_far, step, depth, kept, count);
+    const int64_t n = (int64_t)W * H;
+    int64_t g = ((n + 31) / 32 + kSelectThreads / 32 - 1) / (kSelectThreads / 32);
+    if (g > 152 * 8) g = 152 * 8;  // grid-stride: 8 resident CTAs an SM
+    if (D <= 32) k_select<1><<<(unsigned)g, kSelectThreads, 0, s>>>(L, S, W, H, D, inv_far, step, depth, kept, count);
+    else if (D <= 64) k_select<2><<<(unsigned)g, kSelectThreads, 0, s>>>(L, S, W, H, D, inv_far, step, depth, kept, count);
+    else if (D <= 96) k_select<3><<<(unsigned)g, kSelectThreads, 0, s>>>(L, S, W, H, D, inv_far, step, depth, kept, count);
+    else k_select<4><<<(unsigned)g, kSelectThreads, 0, s>>>(L, S, W, H, D, inv_far, step, depth, kept, count);
     return 1;
 }
 

@@ -15,6 +15,7 @@ struct pgs_mvs {
     uint64_t *cen_t = nullptr, *cen_r = nullptr;
     float* maps = nullptr;
     uint8_t* C = nullptr;
+    uint8_t* L = nullptr;  // [4][H][W][D], one SGM path each
     uint16_t* S = nullptr;
     uint8_t* kept = nullptr;
     unsigned long long* count = nullptr;  // [0] kept pixels, [1] sparse depths
@@ -62,9 +63,9 @@ int pgs_mvs_create(pgs_mvs** out, int32_t width, int32_t height, int32_t planes,
     m->H = height;
     m->D = planes;
     const size_t px = (size_t)width * height, D = planes;
-    const size_t sizes[] = {8 * px, 8 * px, 4 * 9 * D, px * D, 2 * px * D, px, 16, 24, 8, 1024 * mvs_camf_bytes(),
-                            8 * 1024, 4 * (size_t)mvs_fuse_ctas(width, height), 8};
-    void** slots[] = {(void**)&m->cen_t, (void**)&m->cen_r, (void**)&m->maps, (void**)&m->C, (void**)&m->S,
+    const size_t sizes[] = {8 * px, 8 * px, 4 * 9 * D, px * D, 4 * px * D, 2 * px * D, px, 16, 24, 8,
+                            1024 * mvs_camf_bytes(), 8 * 1024, 4 * (size_t)mvs_fuse_ctas(width, height), 8};
+    void** slots[] = {(void**)&m->cen_t, (void**)&m->cen_r, (void**)&m->maps, (void**)&m->C, (void**)&m->L, (void**)&m->S,
                       (void**)&m->kept, (void**)&m->count, (void**)&m->range, (void**)&m->status, &m->cams,
                       (void**)&m->scores, (void**)&m->cta, (void**)&m->total};
     constexpr int kSlots = sizeof(sizes) / sizeof(sizes[0]);
@@ -154,8 +155,8 @@ int pgs_mvs_depth(pgs_mvs* m, const pgs_camera* target, const pgs_camera* refere
     launch_mvs_census(image_t, m->W, m->H, m->cen_t, s);
     launch_mvs_census(image_r, m->W, m->H, m->cen_r, s);
     launch_mvs_cost(*target, *reference, m->cen_t, m->cen_r, m->W, m->H, m->D, inv_far, step, m->maps, m->C, s);
-    launch_mvs_sgm(m->C, m->S, m->W, m->H, m->D, s);
-    launch_mvs_select(m->S, m->W, m->H, m->D, inv_far, step, depth, m->kept, m->count, s);
+    launch_mvs_sgm(m->C, m->L, m->W, m->H, m->D, s);
+    launch_mvs_select(m->L, m->S, m->W, m->H, m->D, inv_far, step, depth, m->kept, m->count, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return err(e);
     if (kept) {
@@ -166,6 +167,40 @@ int pgs_mvs_depth(pgs_mvs* m, const pgs_camera* target, const pgs_camera* refere
         *kept = (int64_t)c;
     }
     return PGS_OK;
+}
+
+int pgs_mvs_stage_times(pgs_mvs* m, const pgs_camera* target, const pgs_camera* reference, const float* image_t,
+                        const float* image_r, double d_min, double d_max, float* depth, float* ms) {
+    if (!m || !same_size(m, target) || !same_size(m, reference) || !finite_camera(target) ||
+        !finite_camera(reference) || !image_t || !image_r || !depth || !ms || !(d_min > 0.0) || !(d_max > d_min) ||
+        !std::isfinite(d_max))
+        return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = m->stream;
+    const double inv_far = 1.0 / d_max;
+    const double step = (1.0 / d_min - inv_far) / (m->D - 1);
+    cudaEvent_t ev[5];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 5; ++made) {
+        e = cudaEventCreate(&ev[made]);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) {
+        cudaEventRecord(ev[0], s);
+        launch_mvs_census(image_t, m->W, m->H, m->cen_t, s);
+        launch_mvs_census(image_r, m->W, m->H, m->cen_r, s);
+        cudaEventRecord(ev[1], s);
+        launch_mvs_cost(*target, *reference, m->cen_t, m->cen_r, m->W, m->H, m->D, inv_far, step, m->maps, m->C, s);
+        cudaEventRecord(ev[2], s);
+        launch_mvs_sgm(m->C, m->L, m->W, m->H, m->D, s);
+        cudaEventRecord(ev[3], s);
+        launch_mvs_select(m->L, m->S, m->W, m->H, m->D, inv_far, step, depth, m->kept, m->count, s);
+        cudaEventRecord(ev[4], s);
+        e = cudaEventSynchronize(ev[4]);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    return err(e);
 }
 
 int pgs_mvs_read(pgs_mvs* m, int32_t what, void* dst, int64_t bytes) {

@@ -251,8 +251,8 @@ int launch_ba_project(int64_t m, int64_t n, int C, const float* R, const float* 
 int launch_mvs_census(const float* rgb, int W, int H, uint64_t* code, cudaStream_t s);
 int launch_mvs_cost(const pgs_camera& t, const pgs_camera& r, const uint64_t* cen_t, const uint64_t* cen_r, int W,
                     int H, int D, double inv_far, double step, float* maps, uint8_t* C, cudaStream_t s);
-int launch_mvs_sgm(const uint8_t* C, uint16_t* S, int W, int H, int D, cudaStream_t s);
-int launch_mvs_select(const uint16_t* S, int W, int H, int D, double inv_far, double step, float* depth,
+int launch_mvs_sgm(const uint8_t* C, uint8_t* L, int W, int H, int D, cudaStream_t s);
+int launch_mvs_select(const uint8_t* L, uint16_t* S, int W, int H, int D, double inv_far, double step, float* depth,
                       uint8_t* kept, unsigned long long* count, cudaStream_t s);
 int launch_mvs_fuse(const float* depth, int W, int H, const pgs_camera& cam, uint32_t* cta_scratch, int64_t* total,
                     int64_t capacity, float* points, int32_t* pix, cudaStream_t s);

@@ -82,6 +82,19 @@ class MultiViewStereo:
                                         float(d_max), _p(out), C.byref(kept) if count else None), "pgs_mvs_depth")
         return out, (int(kept.value) if count else None)
 
+    STAGES = ["census", "cost", "sgm", "select"]
+
+    def stage_times(self, cam_t, cam_r, image_t: torch.Tensor, image_r: torch.Tensor, d_min: float, d_max: float):
+        """Device ms of each stage of depth(), keyed by STAGES."""
+        image_t, image_r = self._image(image_t, "image_t"), self._image(image_r, "image_r")
+        out = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+        ct, cr = camera_struct(cam_t), camera_struct(cam_r)
+        ms = (C.c_float * 4)()
+        L.check(self._lib.pgs_mvs_stage_times(self._m, C.byref(ct), C.byref(cr), _p(image_t), _p(image_r),
+                                              float(d_min), float(d_max), _p(out), C.cast(ms, C.c_void_p)),
+                "pgs_mvs_stage_times")
+        return dict(zip(self.STAGES, list(ms)))
+
     def read(self, what: int) -> torch.Tensor:
         shapes = {L.PGS_MVS_CENSUS_TARGET: ((self.H, self.W), torch.int64),
                   L.PGS_MVS_CENSUS_REFERENCE: ((self.H, self.W), torch.int64),
