@@ -424,12 +424,20 @@ k_quantiles(const double* __restrict__ z, const unsigned long long* __restrict__
         for (int e = threadIdx.x; e < kQ * 256; e += blockDim.x) (&s_hist[0][0])[e] = 0u;
         __syncthreads();
         const unsigned long long hmask = shift == 56 ? 0ull : (~0ull << (shift + 8));
-        for (long long i = threadIdx.x; i < m; i += blockDim.x) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(z[i]);
+        // the values cluster, so most lanes of a warp hit the same bin: one atomic per distinct bin
+        // of a warp (lanes grouped by __match_any_sync) instead of one per lane
+        const long long mend = (m + 31) & ~31ll;
+        for (long long i = threadIdx.x; i < mend; i += blockDim.x) {
+            const bool live = i < m;
+            const unsigned long long b = live ? (unsigned long long)__double_as_longlong(z[i]) : 0ull;
             const unsigned d = (unsigned)((b >> shift) & 255ull);
+            const unsigned lane = threadIdx.x & 31;
 #pragma unroll
-            for (int q = 0; q < kQ; ++q)
-                if ((b & hmask) == s_prefix[q]) atomicAdd(&s_hist[q][d], 1u);
+            for (int q = 0; q < kQ; ++q) {
+                const unsigned key = (live && (b & hmask) == s_prefix[q]) ? d : 256u;
+                const unsigned grp = __match_any_sync(0xffffffffu, key);
+                if (key < 256u && lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(&s_hist[q][key], (unsigned)__popc(grp));
+            }
         }
         __syncthreads();
         if (threadIdx.x < kQ) {

@@ -243,6 +243,61 @@ def time_to_target(seeds, n: int, width: int, height: int, focal: float, plain_i
             "ratio": batched_s / plain_s if done else None}
 
 
+def geometry_prior(sc: S.MVSScene, images: list, every: int = 4, planes: int = 64):
+    """The geometry prior of Sec. III-A on a synthetic keyframe ring: single-reference MVS on every
+    `every`-th keyframe (depth range from the sparse points, Eq. 4 reference), fused into one
+    dense cloud [n][3].  images: CUDA [3][H][W] per keyframe."""
+    from .mvs import MultiViewStereo
+    cams = sc.cameras
+    mv = MultiViewStereo(cams[0].width, cams[0].height, planes)
+    sparse = torch.from_numpy(sc.sparse.astype(np.float32)).cuda()
+    clouds = [mv.reconstruct(cams, images, t, sparse)[3] for t in range(0, len(cams), every)]
+    mv.close()
+    return torch.cat(clouds, 0)
+
+
+def train_views_psnr(params: GaussianBuffer, cams: list, images: list, iters: int, seed: int = 0) -> float:
+    """Plain training (Adam, L1, one view per iteration from a seeded permutation of the views
+    i % 8 != 0), then the mean PSNR over the held-out views i % 8 == 0."""
+    rast = Rasterizer()
+    tr = Trainer(params, rast)
+    views = [i for i in range(len(cams)) if i % 8 != 0]
+    rng = np.random.default_rng(seed)
+    order = []
+    for _ in range(iters):
+        if not order:
+            order = list(rng.permutation(views))
+        v = order.pop()
+        tr.step(cams[v], images[v])
+    code, _ = rast.status()
+    if code != 0:
+        raise RuntimeError(f"training status {code}")
+    return float(np.mean([psnr(rast.render(params, cams[v]), images[v]) for v in range(0, len(cams), 8)]))
+
+
+def prior_experiment(seed: int = 3, width: int = 320, height: int = 180, focal: float = 250.0, n_points: int = 60000,
+                     iters: int = 300, sh_degree: int = 0) -> dict:
+    """The G -> I -> T loop on a synthetic keyframe ring: the MVS cloud (subsampled to n_points)
+    seeds the paper's initializer (Eq. 5-6) and trains for `iters` iterations; the same budget
+    from as many points drawn uniformly in the cloud's bounding box is the comparison.  Returns
+    the held-out PSNRs and the cloud size."""
+    sc = S.mvs_scene(seed, width=width, height=height, focal=focal)
+    images = [torch.from_numpy(im).cuda() for im in sc.images]
+    cloud = geometry_prior(sc, images)
+    rng = np.random.default_rng(seed)
+    pick = torch.from_numpy(rng.choice(cloud.shape[0], size=min(n_points, cloud.shape[0]), replace=False)).cuda()
+    pts = cloud[pick].t().contiguous()
+    init = Initializer()
+    out = {"cloud_points": int(cloud.shape[0])}
+    lo, hi = pts.min(dim=1).values.cpu().numpy(), pts.max(dim=1).values.cpu().numpy()
+    box = torch.from_numpy(rng.uniform(lo[:, None], hi[:, None], size=(3, pts.shape[1])).astype(np.float32)).cuda()
+    for name, p in (("mvs_prior", pts), ("bounding_box", box)):
+        params = with_colour(init.paper_init(p, sh_degree).paper)
+        out[name] = train_views_psnr(params, sc.cameras, images, iters)
+    init.close()
+    return out
+
+
 def main(argv=None):
     """Learned-initializer experiment on 32 surface scenes of 200k points (1280x720, fx = 1000):
     the network is fitted on the converged Gaussians of plain 500-iteration runs of the training
