@@ -389,7 +389,7 @@ def run_dssim(params, cams, targets, tile: int, variant, reps: int = 20, lam: fl
     cap = int(probe.check_status() * 1.5) + 4096
     probe.close()
     rast = R.Rasterizer(pair_capacity=cap, tile=tile)
-    rast.set_variant(*variant)
+    variant.apply(rast)
     img = rast.render(p, cams[0]).clone()
     grad = torch.empty_like(img)
     out = torch.empty(2, device=img.device)
@@ -562,7 +562,7 @@ def run_ours(args):
     del probe
     rast = R.Rasterizer(pair_capacity=int(pmax * 1.5) + 4096, tile=tile)
     rast.reserve(N_GAUSS, WIDTH, HEIGHT, int(pmax * 1.5) + 4096)
-    rast.set_variant(*tuned)
+    tuned.apply(rast)
     params = init.clone()
     tr = R.Trainer(params, rast)
     stream = rast.stream
@@ -680,7 +680,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
-        "variant": {"tile": tile, "pixels_per_thread": tuned[0], "depth": tuned[1]},
+        "variant": {"tile": tile, "forward": {"pixels_per_thread": tuned.fwd[0], "depth": tuned.fwd[1]},
+                    "backward": {"pixels_per_thread": tuned.bwd[0], "depth": tuned.bwd[1]}},
     }
     if not args.no_batched:
         out["batched"] = run_batched(args.batched_steps, max(3, args.warmup))

@@ -291,6 +291,11 @@ int pgs_batch_time_render(pgs_batch* b, int32_t reps, float* ms);
 /* The same measurement for a context, on its last render: the timed forwards write `image`
    ([3][H][W] scratch) and the backwards use dL_dimage [3][H][W]. */
 int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms);
+/* Separate compositing variants for the forward and the backward (pgs_set_variant sets both). */
+int pgs_set_variants(pgs_ctx* ctx, int32_t fwd_pixels, int32_t fwd_depth, int32_t bwd_pixels, int32_t bwd_depth);
+/* As pgs_time_variants, with the forward (ms_fwd [9]) and backward (ms_bwd [9]) times apart. */
+int pgs_time_variants_split(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms_fwd,
+                            float* ms_bwd);
 
 /* ---------------------------------------------------------------------------------------------
    Initialization (operator I of Sec. III-B) and its learned stand-in.

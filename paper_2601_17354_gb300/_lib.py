@@ -48,6 +48,7 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_batch_create", "pgs_batch_destroy", "pgs_batch_step", "pgs_batch_capture",
             "pgs_batch_losses", "pgs_batch_status", "pgs_batch_launch_count", "pgs_set_variant",
             "pgs_batch_set_variant", "pgs_batch_time_variants", "pgs_time_variants",
+            "pgs_set_variants", "pgs_time_variants_split",
             "pgs_init_create", "pgs_init_destroy", "pgs_knn", "pgs_features_init",
             "pgs_mlp_param_count", "pgs_mlp_pack", "pgs_mlp_forward", "pgs_mlp_grad", "pgs_mlp_adam",
             "pgs_apply_mlp", "pgs_make_targets", "pgs_batch_set_views", "pgs_batch_reserve",
@@ -170,6 +171,10 @@ def lib():
             L.pgs_batch_time_variants.restype = I
             L.pgs_time_variants.argtypes = [P, P, P, C.c_int32, P]
             L.pgs_time_variants.restype = I
+            L.pgs_set_variants.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+            L.pgs_set_variants.restype = I
+            L.pgs_time_variants_split.argtypes = [P, P, P, C.c_int32, P, P]
+            L.pgs_time_variants_split.restype = I
             L.pgs_init_create.argtypes = [C.POINTER(P), P]
             L.pgs_init_create.restype = I
             L.pgs_init_destroy.argtypes = [P]

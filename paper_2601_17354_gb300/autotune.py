@@ -8,6 +8,7 @@ from __future__ import annotations
 import json
 import math
 import os
+from dataclasses import dataclass
 
 import torch
 
@@ -50,30 +51,45 @@ def pick(timings: dict) -> tuple:
     return min(timings, key=lambda v: timings[v])
 
 
+@dataclass(frozen=True)
+class Variants:
+    """The compositing variants (pixels per thread, staging depth) of the forward and the backward
+    of single-view training, each the fastest for its own kernel."""
+    fwd: tuple
+    bwd: tuple
+    ms: float = 0.0  # forward + backward compositing time at this choice
+
+    def apply(self, rast):
+        rast.set_variants(self.fwd, self.bwd)
+
+
 def tune_rasterizer(rast, params, cam, dL_dimage: torch.Tensor, cache: str | None = None,
-                    reps: int = 3, force: bool = False) -> tuple:
-    """Choose and set the variant for single-view training of `params` through `cam`."""
+                    reps: int = 3, force: bool = False) -> Variants:
+    """Choose and set the forward and backward variants for single-view training of `params`
+    through `cam` (each kernel timed on its own)."""
     path = _cache_path(cache)
     key = workload_key(f"single-T{rast.tile}", [resolution_class(cam.width, cam.height)], params.n,
                        params.sh_degree)
     entry = None if force else _load(path).get(key)
-    if entry is None:
+    if entry is None or "fwd" not in entry:
         rast.render(params, cam)
-        t = rast.time_variants(dL_dimage, reps)
-        best = pick(t)
-        entry = {"pixels": best[0], "depth": best[1],
-                 "ms": {f"{p}x{d}": ms for (p, d), ms in t.items()}}
+        tf, tb = rast.time_variants_split(dL_dimage, reps)
+        f, b = pick(tf), pick(tb)
+        entry = {"fwd": list(f), "bwd": list(b), "ms": tf[f] + tb[b],
+                 "ms_fwd": {f"{p}x{d}": ms for (p, d), ms in tf.items()},
+                 "ms_bwd": {f"{p}x{d}": ms for (p, d), ms in tb.items()}}
         _store(path, key, entry)
-    rast.set_variant(entry["pixels"], entry["depth"])
-    return entry["pixels"], entry["depth"]
+    v = Variants(tuple(entry["fwd"]), tuple(entry["bwd"]), float(entry["ms"]))
+    v.apply(rast)
+    return v
 
 
 def tune_rasterizer_tile(params, cam, dL_dimage: torch.Tensor, adam=None, tiles=(8, 16, 32),
                          cache: str | None = None, reps: int = 3, force: bool = False):
-    """The tile edge and compositing variant that minimise render + forward and backward
+    """The tile edge and compositing variants that minimise render + forward and backward
     compositing time for single-view training of `params` through `cam`, each timed on this
     workload (the candidates grow their pair buffers on demand).  Returns (rasterizer with that
-    edge and variant, tile, (pixels_per_thread, depth))."""
+    edge and those variants, tile, Variants)."""
     from .rasterizer import Rasterizer
     path = _cache_path(cache)
     key = workload_key("single-tile", [resolution_class(cam.width, cam.height)], params.n, params.sh_degree)
@@ -90,9 +106,7 @@ def tune_rasterizer_tile(params, cam, dL_dimage: torch.Tensor, adam=None, tiles=
     for T in tiles:
         rast = build(T)
         variant = tune_rasterizer(rast, params, cam, dL_dimage, cache=cache, reps=reps, force=force)
-        timed = _load(path).get(workload_key(f"single-T{T}", [resolution_class(cam.width, cam.height)],
-                                             params.n, params.sh_degree), {})
-        comp = timed.get("ms", {}).get(f"{variant[0]}x{variant[1]}", 0.0)
+        comp = variant.ms
         render = []
         for _ in range(reps + 1):
             ev0.record(rast.stream)

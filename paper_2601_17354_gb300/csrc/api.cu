@@ -37,7 +37,8 @@ struct pgs_ctx {
     int64_t cap_s = 0;
     pgs_camera cam{};
     pgs_gaussians params{};
-    CompositeVariant variant = default_variant();
+    CompositeVariant variant = default_variant();       // forward compositing
+    CompositeVariant variant_bwd = default_variant();   // backward compositing
     // instrumentation
     int64_t launches = 0;
     bool profiling = false;
@@ -353,7 +354,7 @@ static int composite_backward(pgs_ctx* ctx, const float* dL_dimage) {
         return launch_composite_replay(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, nullptr,
                                        dL_dimage, ctx->c_rec, ctx->c_count, ctx->replay_k, true, ctx->stream);
     return launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage,
-                                ctx->stream, ctx->variant);
+                                ctx->stream, ctx->variant_bwd);
 }
 
 int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max) {
@@ -503,7 +504,58 @@ int pgs_set_variant(pgs_ctx* ctx, int32_t pixels_per_thread, int32_t depth) {
     const CompositeVariant v{pixels_per_thread, depth};
     if (!ctx || !valid_variant(v, ctx->tile)) return PGS_ERR_INVALID_ARG;
     ctx->variant = v;
+    ctx->variant_bwd = v;
     return PGS_OK;
+}
+
+int pgs_set_variants(pgs_ctx* ctx, int32_t fwd_pixels, int32_t fwd_depth, int32_t bwd_pixels, int32_t bwd_depth) {
+    const CompositeVariant f{fwd_pixels, fwd_depth}, b{bwd_pixels, bwd_depth};
+    if (!ctx || !valid_variant(f, ctx->tile) || !valid_variant(b, ctx->tile)) return PGS_ERR_INVALID_ARG;
+    ctx->variant = f;
+    ctx->variant_bwd = b;
+    return PGS_OK;
+}
+
+int pgs_time_variants_split(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms_fwd,
+                            float* ms_bwd) {
+    if (!ctx || !image || !dL_dimage || !ms_fwd || !ms_bwd || reps < 1) return PGS_ERR_INVALID_ARG;
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t ev[3];
+    for (auto& e : ev) cudaEventCreate(&e);
+    const int P[3] = {1, 2, 4}, D[3] = {64, 128, 256};
+    int idx = 0;
+    cudaError_t err = cudaSuccess;
+    for (int pi = 0; pi < 3 && err == cudaSuccess; ++pi)
+        for (int di = 0; di < 3 && err == cudaSuccess; ++di, ++idx) {
+            const CompositeVariant v{P[pi], D[di]};
+            if (!valid_variant(v, ctx->tile)) {  // no such strip for this tile edge
+                ms_fwd[idx] = ms_bwd[idx] = -1.0f;
+                continue;
+            }
+            float bf = 1e30f, bb = 1e30f;
+            for (int rep = 0; rep < reps + 1; ++rep) {
+                cudaEventRecord(ev[0], s);
+                launch_composite_fwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, image, s, v);
+                cudaEventRecord(ev[1], s);
+                launch_composite_bwd(ctx->cam, ctx->TX, ctx->TY, ctx->tile, ctx->buf, ctx->n, ctx->sc, dL_dimage, s, v);
+                cudaEventRecord(ev[2], s);
+                err = cudaEventSynchronize(ev[2]);
+                if (err != cudaSuccess) break;
+                float tf = 0.f, tb = 0.f;
+                cudaEventElapsedTime(&tf, ev[0], ev[1]);
+                cudaEventElapsedTime(&tb, ev[1], ev[2]);
+                if (rep > 0) {
+                    bf = tf < bf ? tf : bf;
+                    bb = tb < bb ? tb : bb;
+                }
+            }
+            ms_fwd[idx] = bf;
+            ms_bwd[idx] = bb;
+        }
+    for (auto& e : ev) cudaEventDestroy(e);
+    // the timing overwrote the screen-space gradients: the next backward recomputes them
+    return err == cudaSuccess ? PGS_OK : cuda_err(err);
 }
 
 int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_t reps, float* ms) {

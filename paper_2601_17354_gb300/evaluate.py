@@ -74,7 +74,7 @@ def tuned_rasterizer(params: GaussianBuffer, sd: SceneData) -> Rasterizer:
     tuned.close()
     probe.close()
     rast = Rasterizer(pair_capacity=pair_capacity(params, sd, tile=tile), tile=tile)
-    rast.set_variant(*variant)
+    variant.apply(rast)
     return rast
 
 

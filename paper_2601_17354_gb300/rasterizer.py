@@ -230,6 +230,23 @@ class Rasterizer:
                                             ms.ctypes.data_as(C.c_void_p)), "pgs_time_variants")
         return {v: float(t) for v, t in zip(L.VARIANTS, ms) if t >= 0}  # -1: not for this tile edge
 
+    def set_variants(self, fwd: tuple, bwd: tuple):
+        """Compositing variants (pixels per thread, depth) of the forward and of the backward."""
+        L.check(self._lib.pgs_set_variants(self._ctx, int(fwd[0]), int(fwd[1]), int(bwd[0]), int(bwd[1])),
+                "pgs_set_variants")
+
+    def time_variants_split(self, dL_dimage: torch.Tensor, reps: int = 3) -> tuple:
+        """({variant: forward ms}, {variant: backward ms}) of compositing on the last render."""
+        mf = np.zeros(len(L.VARIANTS), np.float32)
+        mb = np.zeros(len(L.VARIANTS), np.float32)
+        scratch = torch.empty_like(dL_dimage)
+        L.check(self._lib.pgs_time_variants_split(self._ctx, C.c_void_p(scratch.data_ptr()),
+                                                  C.c_void_p(dL_dimage.data_ptr()), int(reps),
+                                                  mf.ctypes.data_as(C.c_void_p), mb.ctypes.data_as(C.c_void_p)),
+                "pgs_time_variants_split")
+        keep = [i for i, t in enumerate(mf) if t >= 0]
+        return ({L.VARIANTS[i]: float(mf[i]) for i in keep}, {L.VARIANTS[i]: float(mb[i]) for i in keep})
+
     def launch_count(self) -> int:
         return int(self._lib.pgs_launch_count(self._ctx))
 

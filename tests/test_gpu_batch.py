@@ -133,7 +133,12 @@ def test_autotuner_times_picks_and_caches(mods, tmp_path):
     p = R.GaussianBuffer.from_arrays(scenes[0].init)
     cam = views[0][1]
     dl = torch.from_numpy(S.random_image(1, cam.width, cam.height)).cuda()
-    assert A.tune_rasterizer(rast, p, cam, dl, cache=cache, reps=1) in L.VARIANTS
+    v = A.tune_rasterizer(rast, p, cam, dl, cache=cache, reps=1)
+    assert v.fwd in L.VARIANTS and v.bwd in L.VARIANTS and v.ms > 0
+    # the split timing's choice: each kernel's own fastest strip, and a render with it still matches
+    tf, tb = rast.time_variants_split(dl, 1)
+    assert set(tf) == set(tb) and len(tf) >= 6
+    assert A.tune_rasterizer(rast, p, cam, dl, cache=cache) == v   # from the cache
 
 
 def test_pair_overflow_skips_the_step_then_grows(mods):

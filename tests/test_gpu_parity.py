@@ -114,6 +114,29 @@ def test_backward_grads(R, name):
     compare_grads(grads.numpy(), og, keep)
 
 
+def test_separate_forward_and_backward_variants(R):
+    """A forward strip and a different backward strip on one context: the image is the oracle's
+    and the gradients match it as with one variant."""
+    g, cam = SCENES["surface_sh3_200x120"]()
+    cam.bg = (0.1, 0.3, 0.2)
+    ora = oracle.render(g, cam)
+    dL = S.random_image(13, cam.width, cam.height)
+    dL[:, ora["flag"] != 0] = 0.0
+    keep = oracle.gaussian_flags(g, cam) == 0
+    _, og = oracle.backward(g, cam, dL)
+    for fwd, bwd in (((1, 64), (4, 256)), ((4, 128), (2, 64))):
+        rast = R.Rasterizer()
+        rast.set_variants(fwd, bwd)
+        buf = R.GaussianBuffer.from_arrays(g)
+        img = rast.render(buf, cam).cpu().numpy()
+        ok = ora["flag"] == 0
+        assert np.abs(img[:, ok] - ora["image"][:, ok]).max() <= 1e-4
+        grads = buf.zeros_like()
+        rast.backward(torch.from_numpy(dL).cuda(), grads)
+        torch.cuda.synchronize()
+        compare_grads(grads.numpy(), og, keep)
+
+
 def test_fused_backward_step_matches_oracle_and_separate_calls(R):
     """pgs_backward_step == pgs_backward + pgs_step; its first-step moment m = (1 - b1) g
     exposes the in-register parameter gradient, checked against the oracle."""
