@@ -161,7 +161,7 @@ def sh_basis(direction):
 def project(g, cam, tile: int = 16) -> dict:
     inp = _Inputs(g, cam)
     n = g.n
-    out = dict(visible=np.zeros(n, np.int32), radius=np.zeros(n, np.int32),
+    out = dict(visible=np.zeros(n, np.int32), radius=np.zeros((n, 2), np.int32),
                rect=np.zeros((n, 4), np.int32), depth=np.zeros(n, np.float32),
                uv=np.zeros((n, 2), np.float32), cov2d=np.zeros((n, 3), np.float32),
                mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n),

@@ -20,7 +20,7 @@
 //     parameters (Sec. III-C, gradient scattering paragraph);
 //   * the L1 image loss and its gradient (the paper names no loss).
 //
-// Precision: decision quantities (depth, screen position, 2-D covariance, radius, tile rectangle)
+// Precision: decision quantities (depth, screen position, 2-D covariance, radii, tile rectangle)
 // are computed in fp32 with a prescribed operation order (each +, -, *, / and sqrt correctly
 // rounded, fma fused, compiled with -ffp-contract=off), so that keys are reproducible bit for bit
 // by any IEEE implementation of the same sequence.  Everything else is FP64.
@@ -28,7 +28,7 @@
 // Readings of points the paper leaves open (all listed in the design notes):
 //   projection model = pinhole + first-order (EWA) covariance projection with 0.3 px^2 dilation;
 //   near cull z <= near; Jacobian at x/z, y/z clamped to +-1.3 tan(half FoV) with zero gradient
-//   through the clamp; pixel i covers [i, i+1), centre i + 0.5; radius = ceil(3 sqrt(lambda_max));
+//   through the clamp; pixel i covers [i, i+1), centre i + 0.5; radii ceil(3 sqrt(Sigma_xx)), ceil(3 sqrt(Sigma_yy));
 //   alpha = min(0.99, o exp(power)), skip if alpha < 1/255, stop before compositing when
 //   T (1 - alpha) < 1e-4; colour = real orthonormal SH (no Condon-Shortley phase) + 0.5, clamped
 //   at 0; ties in depth broken by canonical index.
@@ -99,7 +99,7 @@ struct Decision {
     float xc = 0, yc = 0, zc = 0;
     float u = 0, v = 0;
     float cov_a = 0, cov_b = 0, cov_c = 0, det = 0;
-    int32_t radius = 0;
+    int32_t radius_x = 0, radius_y = 0;
     int32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
 };
 
@@ -173,18 +173,18 @@ Decision decide(const ogauss_t& G, const ocam_t& cam, int tile, int64_t i) {
     d.cov_c = std::fma(A[1][0], T[1][0], std::fma(A[1][1], T[1][1], A[1][2] * T[1][2])) + 0.3f;
     d.det = (d.cov_a * d.cov_c) - (d.cov_b * d.cov_b);
     if (!(d.det > 0.0f) || !std::isfinite(d.det)) return d;
-    const float mid = 0.5f * (d.cov_a + d.cov_c);
-    const float disc = std::fmax(0.1f, (mid * mid) - d.det);
-    const float lam = mid + std::sqrt(disc);
-    const float rad = std::ceil(3.0f * std::sqrt(lam));
-    if (!std::isfinite(rad)) return d;
+    // per-axis 3-sigma extents: the bounding box of the 3-sigma ellipse of the 2-D covariance
+    const float rx = std::ceil(3.0f * std::sqrt(d.cov_a));
+    const float ry = std::ceil(3.0f * std::sqrt(d.cov_c));
+    if (!std::isfinite(rx) || !std::isfinite(ry)) return d;
     const float tf = (float)tile;
     const int32_t TX = (cam.width + tile - 1) / tile, TY = (cam.height + tile - 1) / tile;
-    d.x0 = (int32_t)fclampf(std::floor((d.u - rad) / tf), 0.0f, (float)TX);
-    d.x1 = (int32_t)fclampf(std::floor((d.u + rad) / tf) + 1.0f, 0.0f, (float)TX);
-    d.y0 = (int32_t)fclampf(std::floor((d.v - rad) / tf), 0.0f, (float)TY);
-    d.y1 = (int32_t)fclampf(std::floor((d.v + rad) / tf) + 1.0f, 0.0f, (float)TY);
-    d.radius = (int32_t)rad;
+    d.x0 = (int32_t)fclampf(std::floor((d.u - rx) / tf), 0.0f, (float)TX);
+    d.x1 = (int32_t)fclampf(std::floor((d.u + rx) / tf) + 1.0f, 0.0f, (float)TX);
+    d.y0 = (int32_t)fclampf(std::floor((d.v - ry) / tf), 0.0f, (float)TY);
+    d.y1 = (int32_t)fclampf(std::floor((d.v + ry) / tf) + 1.0f, 0.0f, (float)TY);
+    d.radius_x = (int32_t)rx;
+    d.radius_y = (int32_t)ry;
     d.visible = (d.x1 > d.x0) && (d.y1 > d.y0);
     return d;
 }
@@ -656,7 +656,7 @@ void oracle_sh_basis(const double* dir, double* out_y, double* out_dy) {
 
 int oracle_param_count(int sh_degree) { return param_count(sh_degree); }
 
-// Per-Gaussian projection.  Decision outputs (fp32 path): visible, radius, rect [N][4]
+// Per-Gaussian projection.  Decision outputs (fp32 path): visible, radii [N][2] (x, y), rect [N][4]
 // (x0, y0, x1, y1 in tiles, half-open), depth, uv [N][2], cov2d [N][3].  Value outputs (FP64):
 // mean2d [N][2], conic [N][3], opacity [N], rgb [N][3].  Any output pointer may be null.
 void oracle_project(const ogauss_t* G, const ocam_t* cam, int tile, int32_t* visible,
@@ -665,7 +665,10 @@ void oracle_project(const ogauss_t* G, const ocam_t* cam, int tile, int32_t* vis
     for (int64_t i = 0; i < G->n; ++i) {
         const Decision d = decide(*G, *cam, tile, i);
         if (visible) visible[i] = d.visible ? 1 : 0;
-        if (radius) radius[i] = d.visible ? d.radius : 0;
+        if (radius) {
+            radius[2 * i] = d.visible ? d.radius_x : 0;
+            radius[2 * i + 1] = d.visible ? d.radius_y : 0;
+        }
         if (rect) {
             rect[4 * i + 0] = d.visible ? d.x0 : 0;
             rect[4 * i + 1] = d.visible ? d.y0 : 0;

@@ -3,7 +3,7 @@
 // The canonical parameter buffer (mu, Sigma, c, alpha) of Fig. 2 / Sec. III-C is read in place;
 // nothing is reordered (the sorted view exists only as the key/value pairs, Eq. 10).
 //
-// Decision quantities (camera depth, screen position, 2-D covariance, radius, tile rectangle)
+// Decision quantities (camera depth, screen position, 2-D covariance, radii, tile rectangle)
 // follow a prescribed fp32 operation order with every operation an explicit correctly rounded
 // intrinsic, and this file is compiled with --fmad=false, so the keys are reproducible bit for
 // bit by any IEEE implementation of the same sequence.  Value quantities (conic, opacity,
@@ -11,9 +11,10 @@
 //
 // Readings of what the paper leaves open: pinhole + first-order (EWA) projection of the 3-D
 // covariance with a 0.3 px^2 dilation; cull at z <= near; Jacobian evaluated at x/z, y/z clamped
-// to +-1.3 tan(half field of view) with zero gradient through the clamp; radius
-// ceil(3 sqrt(lambda_max)); colour from real orthonormal spherical harmonics (no Condon-Shortley
-// phase) of the direction camera -> mean, + 0.5, clamped at 0.
+// to +-1.3 tan(half field of view) with zero gradient through the clamp; per-axis radii
+// ceil(3 sqrt(Sigma_xx)), ceil(3 sqrt(Sigma_yy)) (the box of the 3-sigma ellipse); colour from
+// real orthonormal spherical harmonics (no Condon-Shortley phase) of the direction camera ->
+// mean, + 0.5, clamped at 0.
 #include "pgs_internal.cuh"
 
 namespace pgs {
@@ -224,17 +225,16 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
     bool vis = finite && geometry(mu, ls, q, cam, G);
     uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     if (vis) {
-        const float mid = __fmul_rn(0.5f, __fadd_rn(G.cov_a, G.cov_c));
-        const float disc = fmaxf(0.1f, __fsub_rn(__fmul_rn(mid, mid), G.det));
-        const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
-        const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
-        vis = isfinite(rad);
+        // per-axis 3-sigma extents: the bounding box of the 3-sigma ellipse of the 2-D covariance
+        const float rx = ceilf(__fmul_rn(3.0f, __fsqrt_rn(G.cov_a)));
+        const float ry = ceilf(__fmul_rn(3.0f, __fsqrt_rn(G.cov_c)));
+        vis = isfinite(rx) && isfinite(ry);
         if (vis) {
             const float tf = (float)T;  // a power of two: the division is an exact scaling
-            x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rad), tf)), 0.0f, (float)TX);
-            x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rad), tf)), 1.0f), 0.0f, (float)TX);
-            y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, rad), tf)), 0.0f, (float)TY);
-            y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, rad), tf)), 1.0f), 0.0f, (float)TY);
+            x0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.u, rx), tf)), 0.0f, (float)TX);
+            x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rx), tf)), 1.0f), 0.0f, (float)TX);
+            y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, ry), tf)), 0.0f, (float)TY);
+            y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, ry), tf)), 1.0f), 0.0f, (float)TY);
             count = (x1 - x0) * (y1 - y0);
         }
     }

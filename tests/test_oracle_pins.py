@@ -104,6 +104,24 @@ def test_sh_gradient_matches_finite_differences():
 # projection and compositing: closed forms (Eq. 7 and its front-to-back form)
 # ------------------------------------------------------------------------------------------------
 
+def test_anisotropic_footprint_rectangle():
+    """An axis-aligned elongated Gaussian facing the camera: the 2-D covariance is
+    diag((f s_x / z)^2 + 0.3, (f s_y / z)^2 + 0.3), the radii are the 3-sigma extents of each axis
+    and the tile rectangle follows from them (a box, not the circle of the largest axis)."""
+    cam = axis_camera()
+    sx, sy, z = 0.12, 0.02, 4.0
+    g = make_gaussians([[0.0], [0.0], [z]], [[math.log(sx)], [math.log(sy)], [math.log(0.01)]],
+                       [[1.0], [0.0], [0.0], [0.0]], [1.0], np.zeros((3, 1, 1)), 0)
+    fx = float(np.float32(cam.fx))
+    sxx = (fx * math.exp(float(np.float32(math.log(sx)))) / z) ** 2 + 0.3
+    syy = (fx * math.exp(float(np.float32(math.log(sy)))) / z) ** 2 + 0.3
+    p = oracle.project(g, cam)
+    rx, ry = (math.ceil(3 * math.sqrt(v)) for v in (sxx, syy))
+    assert list(p["radius"][0]) == [rx, ry] and rx > ry
+    assert list(p["rect"][0]) == [max((32 - rx) // 16, 0), max((32 - ry) // 16, 0),
+                                  min((32 + rx) // 16 + 1, 4), min((32 + ry) // 16 + 1, 4)]
+
+
 def test_single_isotropic_gaussian_closed_form():
     cam = axis_camera()
     sigma, z, o_logit, colour = 0.05, 4.0, 1.5, np.array([0.9, 0.4, 0.2])
@@ -115,9 +133,9 @@ def test_single_isotropic_gaussian_closed_form():
     s2 = (cam.fx * s / z) ** 2 + 0.3
     p = oracle.project(g, cam)
     assert p["visible"][0] == 1
-    # lambda_max = s2 + sqrt(0.1) (the 0.1 floor of the discriminant), radius = ceil(3 sqrt)
-    assert p["radius"][0] == math.ceil(3 * math.sqrt(s2 + math.sqrt(0.1)))
-    r = p["radius"][0]
+    # per-axis 3-sigma extents of the isotropic footprint: ceil(3 sqrt(s2)) on both axes
+    assert list(p["radius"][0]) == [math.ceil(3 * math.sqrt(s2))] * 2
+    r = p["radius"][0][0]
     assert list(p["rect"][0]) == [(32 - r) // 16, (32 - r) // 16, (32 + r) // 16 + 1, (32 + r) // 16 + 1]
     assert np.allclose(p["conic"][0], [1 / s2, 0.0, 1 / s2], rtol=1e-13, atol=1e-15)
     out = oracle.render(g, cam)
