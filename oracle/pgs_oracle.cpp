@@ -28,7 +28,9 @@
 // Readings of points the paper leaves open (all listed in the design notes):
 //   projection model = pinhole + first-order (EWA) covariance projection with 0.3 px^2 dilation;
 //   near cull z <= near; Jacobian at x/z, y/z clamped to +-1.3 tan(half FoV) with zero gradient
-//   through the clamp; pixel i covers [i, i+1), centre i + 0.5; radii ceil(3 sqrt(Sigma_xx)), ceil(3 sqrt(Sigma_yy));
+//   through the clamp; pixel i covers [i, i+1), centre i + 0.5; tile rectangle from the radii
+//   ceil(3 sqrt(Sigma_xx)), ceil(3 sqrt(Sigma_yy)) (the box of the 3-sigma ellipse), and of its
+//   tiles those whose pixel-centre box the 3-sigma ellipse reaches;
 //   alpha = min(0.99, o exp(power)), skip if alpha < 1/255, stop before compositing when
 //   T (1 - alpha) < 1e-4; colour = real orthonormal SH (no Condon-Shortley phase) + 0.5, clamped
 //   at 0; ties in depth broken by canonical index.
@@ -101,9 +103,30 @@ struct Decision {
     float cov_a = 0, cov_b = 0, cov_c = 0, det = 0;
     int32_t radius_x = 0, radius_y = 0;
     int32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    float ca = 0, cb = 0, cc = 0;  // conic (inverse 2-D covariance), fp32 decision path
+    int32_t hits = 0;              // tiles of the rectangle the 3-sigma ellipse reaches
 };
 
 inline float fclampf(float x, float lo, float hi) { return std::fmin(std::fmax(x, lo), hi); }
+
+// Does the 3-sigma ellipse {Q <= 9}, Q(X, Y) = (X - u, Y - v) conic (X - u, Y - v)^T, reach a pixel
+// centre box of tile (tx, ty)?  The minimum of the convex Q over the box is at the clamped centre
+// or on an edge at the clamped line minimum; fp32 in this order, every operation rounded.
+inline bool tile_hit(const Decision& d, int tx, int ty, int tile) {
+    const float xl = (float)(tx * tile) + 0.5f, xh = (float)(tx * tile + tile) - 0.5f;
+    const float yl = (float)(ty * tile) + 0.5f, yh = (float)(ty * tile + tile) - 0.5f;
+    auto Q = [&](float X, float Y) {
+        const float dx = X - d.u, dy = Y - d.v;
+        return (((d.ca * dx) * dx) + (((d.cb + d.cb) * dx) * dy)) + ((d.cc * dy) * dy);
+    };
+    const float sy = d.cb / d.cc, sx = d.cb / d.ca;
+    float best = Q(fclampf(d.u, xl, xh), fclampf(d.v, yl, yh));
+    best = std::fmin(best, Q(xl, fclampf(d.v - sy * (xl - d.u), yl, yh)));
+    best = std::fmin(best, Q(xh, fclampf(d.v - sy * (xh - d.u), yl, yh)));
+    best = std::fmin(best, Q(fclampf(d.u - sx * (yl - d.v), xl, xh), yl));
+    best = std::fmin(best, Q(fclampf(d.u - sx * (yh - d.v), xl, xh), yh));
+    return best <= 9.0f;
+}
 
 // The prescribed fp32 sequence for every quantity that decides membership and order.
 Decision decide(const ogauss_t& G, const ocam_t& cam, int tile, int64_t i) {
@@ -185,7 +208,13 @@ Decision decide(const ogauss_t& G, const ocam_t& cam, int tile, int64_t i) {
     d.y1 = (int32_t)fclampf(std::floor((d.v + ry) / tf) + 1.0f, 0.0f, (float)TY);
     d.radius_x = (int32_t)rx;
     d.radius_y = (int32_t)ry;
-    d.visible = (d.x1 > d.x0) && (d.y1 > d.y0);
+    const float inv = 1.0f / d.det;
+    d.ca = d.cov_c * inv;
+    d.cb = -d.cov_b * inv;
+    d.cc = d.cov_a * inv;
+    for (int ty = d.y0; ty < d.y1; ++ty)
+        for (int tx = d.x0; tx < d.x1; ++tx) d.hits += tile_hit(d, tx, ty, tile);
+    d.visible = d.hits > 0;
     return d;
 }
 
@@ -365,12 +394,14 @@ struct Scene {
             dec[i] = decide(G, cam, tile, i);
             if (dec[i].visible) val[i] = evaluate(G, cam, i);
         }
-        // membership: Gaussian i belongs to the list of every tile inside its rectangle
+        // membership: Gaussian i belongs to the list of every tile of its rectangle that its
+        // 3-sigma ellipse reaches
         lists.assign((size_t)TX * TY, {});
         for (int64_t i = 0; i < G.n; ++i) {
             if (!dec[i].visible) continue;
             for (int ty = dec[i].y0; ty < dec[i].y1; ++ty)
-                for (int tx = dec[i].x0; tx < dec[i].x1; ++tx) lists[(size_t)ty * TX + tx].push_back(i);
+                for (int tx = dec[i].x0; tx < dec[i].x1; ++tx)
+                    if (tile_hit(dec[i], tx, ty, tile)) lists[(size_t)ty * TX + tx].push_back(i);
         }
         for (auto& L : lists)
             std::sort(L.begin(), L.end(), [&](int64_t a, int64_t b) {
@@ -700,7 +731,7 @@ void oracle_project(const ogauss_t* G, const ocam_t* cam, int tile, int32_t* vis
 }
 
 // Keys of every (tile, Gaussian) pair: Gaussians in canonical order, tiles row-major inside each
-// rectangle; key = (tile << 32) | float bits of the depth; value = canonical index.  Stable sort
+// rectangle (those the 3-sigma ellipse reaches); key = (tile << 32) | float bits of the depth; value = canonical index.  Stable sort
 // by key; ranges[2 t], ranges[2 t + 1] = [first, last + 1) of tile t, [0, 0) if empty.
 // Writes at most `capacity` pairs and returns the total pair count.
 int64_t oracle_keys(const ogauss_t* G, const ocam_t* cam, int tile, int64_t capacity,
@@ -712,6 +743,7 @@ int64_t oracle_keys(const ogauss_t* G, const ocam_t* cam, int tile, int64_t capa
         if (!d.visible) continue;
         for (int ty = d.y0; ty < d.y1; ++ty)
             for (int tx = d.x0; tx < d.x1; ++tx) {
+                if (!tile_hit(d, tx, ty, tile)) continue;
                 const uint64_t t = (uint64_t)ty * TX + tx;
                 pairs.emplace_back((t << 32) | fbits(d.zc), (uint32_t)i);
             }
@@ -908,6 +940,8 @@ void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const doub
             ogauss_t g1 = one(q);
             const Decision d = decide(g1, *cam, tile, 0);
             ok = d.visible == d0.visible && d.x0 == d0.x0 && d.x1 == d0.x1 && d.y0 == d0.y0 && d.y1 == d0.y1;
+            for (int ty = d.y0; ty < d.y1 && ok; ++ty)  // the same tiles of the rectangle reached
+                for (int tx = d.x0; tx < d.x1 && ok; ++tx) ok = tile_hit(d, tx, ty, tile) == tile_hit(d0, tx, ty, tile);
             if (!ok) return 0.0;
             // depth order inside every tile of the rectangle must be unchanged
             const uint32_t b0 = fbits(d0.zc), b1 = fbits(d.zc);

@@ -72,6 +72,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.rgb = c.take<float4>(n);
     sc.depth_bits = c.take<uint32_t>(n);
     sc.rect = c.take<uint2>(n);
+    sc.hitmask = c.take<uint32_t>(n);
     sc.touched = c.take<uint32_t>(n);
     sc.block_sums = c.take<uint32_t>(nb);
     sc.block_offsets = c.take<unsigned long long>(nb);
@@ -288,7 +289,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     const size_t e1 = mark(ctx);
     const uint32_t* perm = nullptr;
     if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm);
-    ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, perm, ctx->sc, s);
+    ctx->launches += launch_scan_emit(params->n, TX, T, ctx->cap_pairs, perm, ctx->sc, s);
     if (ctx->grow_pairs) {
         unsigned long long P = 0;
         cudaError_t e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
@@ -306,7 +307,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
             e = cudaMemcpyAsync(ctx->sc.status, &st, sizeof(st), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_err(e);
-            ctx->launches += launch_scan_emit(params->n, TX, ctx->cap_pairs, perm, ctx->sc, s);
+            ctx->launches += launch_scan_emit(params->n, TX, T, ctx->cap_pairs, perm, ctx->sc, s);
         }
     }
     const size_t e2 = mark(ctx);
@@ -676,7 +677,7 @@ int64_t enqueue_render(pgs_batch* b) {
     k += launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
     const uint32_t* perm = nullptr;
     if (b->items > 0) k += launch_depth_sort(b->items, b->sc, s, &perm);
-    k += launch_scan_emit(b->items, 0, b->cap_pairs, perm, b->sc, s, b->d_renders, b->R);
+    k += launch_scan_emit(b->items, 0, b->cfg.tile, b->cap_pairs, perm, b->sc, s, b->d_renders, b->R);
     k += launch_sort_ranges(b->cap_pairs, (int)b->tiles, b->sc, s, &b->buf);
     k += launch_tile_order((int)b->tiles, b->sc, s);
     return k;
@@ -809,7 +810,7 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
         const uint32_t* perm = nullptr;
         launch_depth_sort(b->items, b->sc, s, &perm);
-        launch_scan_emit(b->items, 0, 0, perm, b->sc, s, b->d_renders, b->R);
+        launch_scan_emit(b->items, 0, b->cfg.tile, 0, perm, b->sc, s, b->d_renders, b->R);
         unsigned long long P = 0;
         int32_t zero = 0;
         e = cudaMemcpyAsync(&P, b->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);

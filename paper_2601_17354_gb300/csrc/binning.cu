@@ -98,25 +98,40 @@ k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
 // tiles row-major inside each rectangle.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
-k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
+k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
        const RenderDesc* __restrict__ renders, int R) {
-    __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of counts
+    // the CTA's Gaussians (in depth order) and their rectangles' tiles as one flat candidate list;
+    // candidates whose tile the 3-sigma ellipse reaches are written in order (a CTA-wide ordered
+    // compaction per round), so each Gaussian's pairs stay contiguous, row-major in its rectangle
+    __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of candidate counts (rectangle areas)
     __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock];
     __shared__ uint32_t s_tx[kProjBlock], s_tbase[kProjBlock];
+    __shared__ float s_u[kProjBlock], s_v[kProjBlock], s_ca[kProjBlock], s_cb[kProjBlock], s_cc[kProjBlock];
+    __shared__ float s_sx[kProjBlock], s_sy[kProjBlock];
+    __shared__ uint32_t s_mask[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
+    __shared__ uint32_t s_gid[kProjBlock];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
-    __shared__ uint32_t s_gid[kProjBlock];
     uint32_t cnt = 0;
     if (i < n) {
         const uint32_t g = perm[i];
         s_gid[t] = g;
-        cnt = sc.touched[g];
-        if (cnt) {
+        if (sc.touched[g]) {
             const uint2 r = sc.rect[g];
             s_x0[t] = r.x & 0xffffu;
             s_y0[t] = r.x >> 16;
             s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
+            cnt = s_w[t] * ((r.y >> 16) - (r.x >> 16));
+            const float4 p = sc.xyo[g], q = sc.conic[g];
+            s_u[t] = p.x;
+            s_v[t] = p.y;
+            s_ca[t] = q.x;
+            s_cb[t] = q.y;
+            s_cc[t] = q.z;
+            s_sx[t] = __fdiv_rn(q.y, q.x);
+            s_sy[t] = __fdiv_rn(q.y, q.z);
+            s_mask[t] = sc.hitmask[g];
             s_tx[t] = (uint32_t)TX;
             s_tbase[t] = 0;
             if (renders) {  // batch: item g belongs to the last render whose first item is <= g
@@ -154,23 +169,49 @@ k_emit(int64_t n, int TX, int64_t capacity, const uint32_t* __restrict__ perm, S
     __syncthreads();
     const uint32_t total = s_end[kProjBlock - 1];
     const unsigned long long base = sc.block_offsets[blockIdx.x];
-    for (uint32_t k = t; k < total; k += kProjBlock) {
-        // first j with s_end[j] > k
-        int lo = 0, hi = kProjBlock - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_end[mid] > k) hi = mid;
-            else lo = mid + 1;
+    uint32_t written = 0;
+    for (uint32_t k0 = 0; k0 < total; k0 += kProjBlock) {
+        const uint32_t k = k0 + t;
+        bool hit = false;
+        uint32_t tile = 0, gid = 0;
+        if (k < total) {
+            // first j with s_end[j] > k
+            int lo = 0, hi = kProjBlock - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_end[mid] > k) hi = mid;
+                else lo = mid + 1;
+            }
+            const uint32_t local = k - (lo ? s_end[lo - 1] : 0u);  // candidate inside Gaussian lo
+            const uint32_t w = s_w[lo];
+            const uint32_t dy = local / w, dx = local - dy * w;
+            const uint32_t tx = s_x0[lo] + dx, ty = s_y0[lo] + dy;
+            const uint32_t area = s_end[lo] - (lo ? s_end[lo - 1] : 0u);
+            hit = area <= 32u ? ((s_mask[lo] >> local) & 1u) != 0u
+                              : tile_hit(s_u[lo], s_v[lo], s_ca[lo], s_cb[lo], s_cc[lo], s_sx[lo], s_sy[lo], (int)tx,
+                                         (int)ty, T);
+            tile = s_tbase[lo] + ty * s_tx[lo] + tx;
+            gid = s_gid[lo];
         }
-        const uint32_t local = k - (lo ? s_end[lo - 1] : 0u);  // pair index inside Gaussian lo
-        const uint32_t w = s_w[lo];
-        const uint32_t dy = local / w, dx = local - dy * w;
-        const uint32_t tile = s_tbase[lo] + (s_y0[lo] + dy) * s_tx[lo] + s_x0[lo] + dx;
-        const unsigned long long pos = base + k;
-        if (pos < (unsigned long long)capacity) {
-            reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
-            sc.vals[0][pos] = s_gid[lo];
+        // ordered compaction of this round's hits
+        const unsigned bal = __ballot_sync(kFull, hit);
+        __syncthreads();  // the previous round's s_warp reads are done
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = 0, round = 0;
+#pragma unroll
+        for (int w = 0; w < kProjBlock / 32; ++w) {
+            before += w < warp ? s_warp[w] : 0u;
+            round += s_warp[w];
         }
+        if (hit) {
+            const unsigned long long pos = base + written + before + __popc(bal & ((1u << lane) - 1u));
+            if (pos < (unsigned long long)capacity) {
+                reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
+                sc.vals[0][pos] = gid;
+            }
+        }
+        written += round;
     }
 }
 
@@ -509,13 +550,13 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     return launched;
 }
 
-int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+int launch_scan_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* perm, const Scratch& sc,
                      cudaStream_t s, const RenderDesc* renders, int R) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
     if (nb > 0) k_perm_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
     k_scan_blocks<<<1, kScanThreads, 0, s>>>(nb, capacity, sc);
     if (nb == 0) return 1;
-    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, capacity, perm, sc, renders, R);
+    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, T, capacity, perm, sc, renders, R);
     return 3;
 }
 

@@ -36,6 +36,7 @@ struct Scratch {
     float4* rgb = nullptr;
     uint32_t* depth_bits = nullptr;
     uint2* rect = nullptr;  // (x0 | y0 << 16, x1 | y1 << 16), tiles, half-open
+    uint32_t* hitmask = nullptr;  // rectangles of <= 32 tiles: bit k (row-major in the rectangle) = tile k reached
     uint32_t* touched = nullptr;
     uint32_t* block_sums = nullptr;
     unsigned long long* block_offsets = nullptr;
@@ -172,7 +173,7 @@ int launch_mlp_pack(const float* master, void* W1, void* W2, void* W3, cudaStrea
 
 // K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
 // emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
-int launch_scan_emit(int64_t n, int TX, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+int launch_scan_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* perm, const Scratch& sc,
                      cudaStream_t s, const RenderDesc* renders = nullptr, int R = 0);
 // K4/K5: stable radix sort of the pairs by the tile bits (returns which ping-pong buffer holds
 // the result) and ranges.
@@ -212,6 +213,32 @@ int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles
 // doubles of scratch, loss_out = device {loss, mean SSIM}.
 int launch_loss_dssim(const float* image, const float* target, int W, int H, float lam, float* dm,
                       double* sums, float* grad, float* loss_out, cudaStream_t s);
+// Does the 3-sigma ellipse {Q <= 9} of a projected Gaussian (screen position u, v; conic ca, cb,
+// cc) reach the pixel-centre box of tile (tx, ty) of edge T?  The minimum of the convex Q over the
+// box is at the clamped centre or on an edge at the clamped line minimum.  Part of the prescribed
+// fp32 decision path (membership): every operation an explicit correctly rounded intrinsic, in
+// the order of the oracle's definition.
+__device__ __forceinline__ float hit_q(float X, float Y, float u, float v, float ca, float cb, float cc) {
+    const float dx = __fadd_rn(X, -u), dy = __fadd_rn(Y, -v);
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(ca, dx), dx), __fmul_rn(__fmul_rn(__fadd_rn(cb, cb), dx), dy)),
+                     __fmul_rn(__fmul_rn(cc, dy), dy));
+}
+// (sx, sy) = (cb / ca, cb / cc): the slopes of the line minima, per Gaussian; the test stops at the
+// first candidate within the ellipse (min <= 9 exactly when some candidate is)
+__device__ __forceinline__ bool tile_hit(float u, float v, float ca, float cb, float cc, float sx, float sy, int tx,
+                                         int ty, int T) {
+    const float xl = __fadd_rn((float)(tx * T), 0.5f), xh = __fadd_rn((float)(tx * T + T), -0.5f);
+    const float yl = __fadd_rn((float)(ty * T), 0.5f), yh = __fadd_rn((float)(ty * T + T), -0.5f);
+    if (hit_q(fminf(fmaxf(u, xl), xh), fminf(fmaxf(v, yl), yh), u, v, ca, cb, cc) <= 9.0f) return true;
+    if (hit_q(xl, fminf(fmaxf(__fadd_rn(v, -__fmul_rn(sy, __fadd_rn(xl, -u))), yl), yh), u, v, ca, cb, cc) <= 9.0f)
+        return true;
+    if (hit_q(xh, fminf(fmaxf(__fadd_rn(v, -__fmul_rn(sy, __fadd_rn(xh, -u))), yl), yh), u, v, ca, cb, cc) <= 9.0f)
+        return true;
+    if (hit_q(fminf(fmaxf(__fadd_rn(u, -__fmul_rn(sx, __fadd_rn(yl, -v))), xl), xh), yl, u, v, ca, cb, cc) <= 9.0f)
+        return true;
+    return hit_q(fminf(fmaxf(__fadd_rn(u, -__fmul_rn(sx, __fadd_rn(yh, -v))), xl), xh), yh, u, v, ca, cb, cc) <= 9.0f;
+}
+
 // Bundle adjustment (Sec. III-A, Eq. 2-3): problem shape and chunking, index check, per-point
 // offsets and camera masks, linearization, one Levenberg-Marquardt trial through the reduced
 // camera system, robust cost, projection.

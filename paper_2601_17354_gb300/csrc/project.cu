@@ -224,6 +224,8 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
     Geo G;
     bool vis = finite && geometry(mu, ls, q, cam, G);
     uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    float con_a = 0.f, con_b = 0.f, con_c = 0.f;  // conic, decision path
+    uint32_t hits = 0;                             // reached tiles of a rectangle of <= 32
     if (vis) {
         // per-axis 3-sigma extents: the bounding box of the 3-sigma ellipse of the 2-D covariance
         const float rx = ceilf(__fmul_rn(3.0f, __fsqrt_rn(G.cov_a)));
@@ -235,12 +237,24 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
             x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rx), tf)), 1.0f), 0.0f, (float)TX);
             y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, ry), tf)), 0.0f, (float)TY);
             y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, ry), tf)), 1.0f), 0.0f, (float)TY);
-            count = (x1 - x0) * (y1 - y0);
+            // of the rectangle's tiles, those whose pixel centres the 3-sigma ellipse reaches
+            const float inv = __fdiv_rn(1.0f, G.det);
+            con_a = __fmul_rn(G.cov_c, inv);
+            con_b = __fmul_rn(-G.cov_b, inv);
+            con_c = __fmul_rn(G.cov_a, inv);
+            const float sx = __fdiv_rn(con_b, con_a), sy = __fdiv_rn(con_b, con_c);
+            const bool small = (x1 - x0) * (y1 - y0) <= 32u;
+            uint32_t k = 0;
+            for (uint32_t ty = y0; ty < y1; ++ty)
+                for (uint32_t tx = x0; tx < x1; ++tx, ++k) {
+                    const bool h = tile_hit(G.u, G.v, con_a, con_b, con_c, sx, sy, (int)tx, (int)ty, T);
+                    count += h;
+                    if (small && h) hits |= 1u << k;
+                }
         }
     }
     if (count > 0) {
-        // value path: conic, opacity, colour
-        const float inv_det = 1.0f / G.det;
+        // value path: opacity, colour (the conic is the decision path's)
         const float opacity = 1.0f / (1.0f + expf(-logit));
         float cc[3];
         camera_centre(cam, cc);
@@ -264,10 +278,11 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
             finite = false;
         } else {
             sc.xyo[j] = make_float4(G.u, G.v, opacity, 0.0f);
-            sc.conic[j] = make_float4(G.cov_c * inv_det, -G.cov_b * inv_det, G.cov_a * inv_det, 0.0f);
+            sc.conic[j] = make_float4(con_a, con_b, con_c, 0.0f);
             sc.rgb[j] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
             sc.depth_bits[j] = __float_as_uint(G.zc);
             sc.rect[j] = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+            sc.hitmask[j] = hits;
         }
     }
     if (!finite) atomicOr(sc.status, kStatusNonfinite);

@@ -376,6 +376,63 @@ def test_canonical_permutation_equivariance():
 # keys, sort and tile ranges (the permutation pi of Eq. 10), against brute force
 # ------------------------------------------------------------------------------------------------
 
+def _tile_hit(uv, cov, tx, ty, T=16):
+    """The 3-sigma ellipse / tile rule in numpy float32 (products and sums rounded one by one):
+    the minimum of Q over the tile's pixel-centre box, at the clamped centre or an edge's clamped
+    line minimum, is at most 9."""
+    f = np.float32
+    u, v = f(uv[0]), f(uv[1])
+    a_, b_, c_ = f(cov[0]), f(cov[1]), f(cov[2])
+    det = f(f(a_ * c_) - f(b_ * b_))
+    inv = f(f(1) / det)
+    ca, cb, cc = f(c_ * inv), f(f(-b_) * inv), f(a_ * inv)
+    xl, xh = f(f(tx * T) + f(0.5)), f(f(tx * T + T) - f(0.5))
+    yl, yh = f(f(ty * T) + f(0.5)), f(f(ty * T + T) - f(0.5))
+    clamp = lambda x, lo, hi: min(max(x, lo), hi)
+
+    def Q(X, Y):
+        dx, dy = f(X - u), f(Y - v)
+        return f(f(f(f(ca * dx) * dx) + f(f(f(cb + cb) * dx) * dy)) + f(f(cc * dy) * dy))
+    sy, sx = f(cb / cc), f(cb / ca)
+    best = Q(clamp(u, xl, xh), clamp(v, yl, yh))
+    for X in (xl, xh):
+        best = min(best, Q(X, clamp(f(v - f(sy * f(X - u))), yl, yh)))
+    for Y in (yl, yh):
+        best = min(best, Q(clamp(f(u - f(sx * f(Y - v))), xl, xh), Y))
+    return bool(best <= f(9))
+
+
+def test_tile_membership_is_the_three_sigma_ellipse():
+    """An isotropic footprint (Q = d^2 / s2): a tile of the rectangle is listed exactly when the
+    distance from the centre to its pixel-centre box is at most 3 sqrt(s2) (closed form, cases
+    away from the boundary)."""
+    cam = axis_camera(160, 160, 100.0)
+    dropped = 0
+    for sigma, x in ((0.3, 0.31), (0.25, -0.2), (0.4, 0.02)):
+        g = make_gaussians([[x], [0.13], [4.0]], [[math.log(sigma)]] * 3, [[1.0], [0.0], [0.0], [0.0]],
+                           [1.0], np.zeros((3, 1, 1)), 0)
+        p = oracle.project(g, cam)
+        keys, vals, ranges = oracle.keys(g, cam)
+        TX, TY = oracle.tiles(cam)
+        u, v = p["uv"][0]
+        s2 = float(p["cov2d"][0][0])
+        x0, y0, x1, y1 = p["rect"][0]
+        listed = {int(k >> np.uint64(32)) for k in keys}
+        checked = 0
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                bx = min(max(u, 16 * tx + 0.5), 16 * tx + 15.5)
+                by = min(max(v, 16 * ty + 0.5), 16 * ty + 15.5)
+                q = ((bx - u) ** 2 + (by - v) ** 2) / s2
+                if abs(q - 9) < 1e-3:
+                    continue
+                assert ((ty * TX + tx) in listed) == (q <= 9), (tx, ty, q)
+                checked += 1
+        assert checked >= 4
+        dropped += (x1 - x0) * (y1 - y0) - len(listed)
+    assert dropped > 0   # rectangle corners the ellipse does not reach
+
+
 @pytest.mark.parametrize("dims", [(128, 128), (100, 75)])
 def test_keys_and_ranges_match_brute_force(dims):
     g, cam, _ = S.tiny_scene(4, n=1500, width=dims[0], height=dims[1])
@@ -384,14 +441,17 @@ def test_keys_and_ranges_match_brute_force(dims):
     p = oracle.project(g, cam)
     TX, TY = oracle.tiles(cam)
     depth_bits = p["depth"].view(np.uint32).astype(np.uint64)
-    touched = [(p["rect"][i, 2] - p["rect"][i, 0]) * (p["rect"][i, 3] - p["rect"][i, 1])
-               for i in range(g.n) if p["visible"][i]]
-    assert len(keys) == sum(touched)
+    r = p["rect"]
+    hit = {}
+    for i in range(g.n):
+        if p["visible"][i]:
+            for ty in range(r[i, 1], r[i, 3]):
+                for tx in range(r[i, 0], r[i, 2]):
+                    if _tile_hit(p["uv"][i], p["cov2d"][i], tx, ty):
+                        hit.setdefault(ty * TX + tx, []).append(i)
+    assert len(keys) == sum(len(v) for v in hit.values())
     for t in range(TX * TY):
-        tx, ty = t % TX, t // TX
-        r = p["rect"]
-        ids = np.nonzero((p["visible"] == 1) & (r[:, 0] <= tx) & (tx < r[:, 2]) & (r[:, 1] <= ty)
-                         & (ty < r[:, 3]))[0]
+        ids = np.array(hit.get(t, []), np.int64)
         ids = ids[np.lexsort((ids, depth_bits[ids]))]
         s, e = ranges[t]
         assert np.array_equal(vals[s:e], ids.astype(np.uint32))
@@ -543,10 +603,13 @@ def test_fd_subset_matches_analytic_backward():
     w = S.random_image(3, cam.width, cam.height)
     sel = np.random.default_rng(2).choice(np.nonzero(oracle.project(g, cam)["visible"])[0], 12,
                                           replace=False)
-    fd = oracle.fd_subset(g, cam, w, sel)
     _, an = oracle.backward_subset(g, cam, w, sel)
-    ok = np.isfinite(fd)
-    assert ok.mean() > 0.9
     scale = np.abs(an).max(axis=1, keepdims=True)
-    err = np.abs(fd - an) / (scale + 1e-30)
-    assert np.max(err[ok]) < 1e-4
+    worst = []
+    for h in (2.0 ** -12, 2.0 ** -14):
+        fd = oracle.fd_subset(g, cam, w, sel, h_rel=h)
+        ok = np.isfinite(fd)
+        assert ok.mean() > 0.9
+        worst.append(np.max((np.abs(fd - an) / (scale + 1e-30))[ok]))
+    # central differences: the error is the O(h^2) truncation, 16x smaller at a 4x smaller step
+    assert worst[1] < 1e-4 and worst[0] > 8 * worst[1]
