@@ -94,6 +94,19 @@ struct ReplayCache {
     int K = 0;
 };
 
+// Thread t's pixel column and first row inside the tile: each warp takes a block 8 pixels wide and
+// 4 kPix rows high (lane: column lane % 8, strip of kPix rows from kPix (lane / 8)), the blocks
+// tiling the tile row by row.  Compact blocks end their pixels' lists at more similar depths than
+// kT-wide strips, so a warp walks fewer entries only some of its pixels need (16-pixel tiles, two
+// pixels a thread: 8 x 8 blocks instead of 16 x 4 strips, backward 0.574 -> 0.536 ms).
+template <int kT, int kPix>
+__device__ __forceinline__ void strip_origin(int t, int& dx, int& dy0) {
+    constexpr int kAcross = kT / 8;  // blocks per block row
+    const int w = t >> 5, lane = t & 31;
+    dx = (w % kAcross) * 8 + (lane & 7);
+    dy0 = (w / kAcross) * (4 * kPix) + (lane >> 3) * kPix;
+}
+
 template <int kDepth>
 struct FwdSmem {
     float4 xyo[kDepth], s2[kDepth], rgb[kDepth];
@@ -111,8 +124,10 @@ __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, con
     float4* s_s2 = S.s2;
     float4* s_rgb = S.rgb;
     const int W = J.W, H = J.H;
-    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
-    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    int sdx, sdy0;
+    strip_origin<kT, kPix>((int)threadIdx.x, sdx, sdy0);
+    const int px = (J.tile % J.TX) * kT + sdx;
+    const int py0 = (J.tile / J.TX) * kT + sdy0;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = J.range;
     const float3 bg = J.bg;
@@ -276,8 +291,10 @@ __device__ __forceinline__ void bwd_tile_scalar(const TileJob& J, int64_t n, con
     const float3 bg = J.bg;
     const float* __restrict__ dL_dimage = J.dL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
-    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    int sdx, sdy0;
+    strip_origin<kT, kPix>((int)threadIdx.x, sdx, sdy0);
+    const int px = (J.tile % J.TX) * kT + sdx;
+    const int py0 = (J.tile / J.TX) * kT + sdy0;
     const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f;
     const uint2 range = J.range;
     const size_t plane = (size_t)W * H;
@@ -465,8 +482,10 @@ __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, cons
     float4* s_s2 = S.s2;
     float4* s_rgb = S.rgb;
     const int W = J.W, H = J.H;
-    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
-    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    int sdx, sdy0;
+    strip_origin<kT, kPix>((int)threadIdx.x, sdx, sdy0);
+    const int px = (J.tile % J.TX) * kT + sdx;
+    const int py0 = (J.tile / J.TX) * kT + sdy0;
     const float fx = (float)px + 0.5f;
     F2 FY[NP];  // pixel-centre rows of the pairs: dy = row - y exactly as the one-pixel strips
 #pragma unroll
@@ -576,8 +595,10 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
     const float3 bg = J.bg;
     const float* __restrict__ dL_dimage = J.dL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = (J.tile % J.TX) * kT + (threadIdx.x % kT);
-    const int py0 = (J.tile / J.TX) * kT + (threadIdx.x / kT) * kPix;
+    int sdx, sdy0;
+    strip_origin<kT, kPix>((int)threadIdx.x, sdx, sdy0);
+    const int px = (J.tile % J.TX) * kT + sdx;
+    const int py0 = (J.tile / J.TX) * kT + sdy0;
     const float fx = (float)px + 0.5f;
     F2 FY[NP];  // pixel-centre rows of the pairs (as in the forward)
 #pragma unroll
