@@ -90,7 +90,9 @@ void pgs_destroy(pgs_ctx* ctx);
 int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t pair_capacity);
 
 /* Forward pass, Eq. 7 front to back: project and cull every Gaussian (EWA projection, SH colour),
-   emit (tile | depth, canonical index) pairs, sort them (the permutation pi of Eq. 10), find each
+   emit (tile | depth, canonical index) pairs for the tiles of its footprint (the rectangle of the
+   per-axis 3-sigma extents ceil(3 sqrt(Sigma_xx)), ceil(3 sqrt(Sigma_yy)), and of it the tiles
+   whose pixel centres the 3-sigma ellipse reaches), sort them (the permutation pi of Eq. 10), find each
    tile's range, alpha-composite each pixel over its tile's depth-ordered list
    (alpha = min(0.99, o G); skip alpha < 1/255; stop before a Gaussian that would take the
    transmittance below 1e-4), and write image_out [3][H][W] = colour + T_final * bg.
