@@ -239,6 +239,64 @@ def test_equal_depth_ties_are_stable(R):
     compare_forward(img, T, last, oracle.render(g, cam))
 
 
+def _lengths(g, cam, tile=16):
+    r = oracle.keys(g, cam, tile)[2]
+    return r[:, 1] - r[:, 0]
+
+
+# per-tile list lengths: all short (< 1024 entries), some of 1024 .. 8191, some of 8192 and more
+# (a list longer than the 4096 keys of one radix-sort CTA spans several of them)
+LENGTH_SCENES = {
+    "short": (2000, 128, 150.0, lambda L: L.max() < 1024),
+    "long": (20000, 64, 60.0, lambda L: np.any((L >= 1024) & (L < 8192))),
+    "very_long": (60000, 32, 30.0, lambda L: np.any(L >= 8192)),
+}
+
+
+@pytest.mark.parametrize("name", list(LENGTH_SCENES))
+def test_list_length_classes(R, name):
+    """Short, long and very long tile lists, distinct depths: keys, values and ranges bit-exact."""
+    n, size, focal, covers = LENGTH_SCENES[name]
+    g, cam, _ = S.tiny_scene(11, n=n, width=size, height=size, focal=focal)
+    assert covers(_lengths(g, cam))
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0
+    assert pairs == check_keys(rast, g, cam)
+
+
+@pytest.mark.parametrize("name", list(LENGTH_SCENES))
+def test_long_equal_depth_runs(R, name):
+    """40 % of the Gaussians at one depth (the identity-rotation camera makes their depths equal to
+    the bit): runs of far more than 32 equal keys per tile, ordered by canonical index."""
+    n, size, focal, covers = LENGTH_SCENES[name]
+    g, cam, _ = S.tiny_scene(12, n=n, width=size, height=size, focal=focal)
+    rng = np.random.default_rng(12)
+    g.means[2, rng.random(n) < 0.4] = 0.25
+    k = oracle.keys(g, cam)[0]
+    runs = np.diff(np.flatnonzero(np.diff(np.concatenate([[-1], k.astype(np.int64), [-1]])) != 0))
+    assert runs.max() > 32
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0
+    assert pairs == check_keys(rast, g, cam)
+
+
+def test_short_equal_depth_runs(R):
+    """Triples of nearby Gaussians sharing a depth: runs of 2 and 3 equal keys inside tiles."""
+    g, cam, _ = S.tiny_scene(13, n=2001, width=128, height=128)
+    rng = np.random.default_rng(13)
+    for c in range(3):
+        base = g.means[c, 0::3]
+        g.means[c, 1::3] = base + (0.0 if c == 2 else rng.uniform(-0.02, 0.02, base.shape))
+        g.means[c, 2::3] = base + (0.0 if c == 2 else rng.uniform(-0.02, 0.02, base.shape))
+    k = oracle.keys(g, cam)[0]
+    runs = np.diff(np.flatnonzero(np.diff(np.concatenate([[-1], k.astype(np.int64), [-1]])) != 0))
+    assert runs.max() in (2, 3) and np.sum(runs >= 2) > 100
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
+    assert code == 0
+    assert pairs == check_keys(rast, g, cam)
+    compare_forward(img, T, last, oracle.render(g, cam))
+
+
 def test_nonfinite_parameter_is_reported_and_culled(R):
     from paper_2601_17354_gb300 import _lib as L
     g, cam = SCENES["tiny_2k_128"]()
