@@ -81,8 +81,8 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.dkeys[1] = c.take<unsigned long long>(n);
     sc.dvals[0] = c.take<uint32_t>(n);
     sc.dvals[1] = c.take<uint32_t>(n);
-    sc.dhist = c.take<uint32_t>((size_t)kRadix * ((n + kSortTile - 1) / kSortTile));
-    sc.dtotals = c.take<uint32_t>(kMaxPasses * kRadix);
+    sc.dhist = c.take<uint32_t>((size_t)kRadix * ((n + kDepthTile - 1) / kDepthTile));
+    sc.dtotals = c.take<uint32_t>(kTotalWords);
     sc.dcount = c.take<unsigned long long>(1);
     sc.dblocks = c.take<uint32_t>(1);
     sc.ranges = c.take<uint2>(tiles);
@@ -93,7 +93,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.status = c.take<int32_t>(1);
     sc.pair_count = c.take<unsigned long long>(1);
     sc.sort_blocks = c.take<uint32_t>(1);
-    sc.digit_totals = c.take<uint32_t>(kMaxPasses * kRadix);
+    sc.digit_totals = c.take<uint32_t>(kTotalWords);
     sc.loss_partials = c.take<float>(2 * kLossBlocks);
     sc.loss_ticket = c.take<uint32_t>(1);
     return c.off;

@@ -93,10 +93,12 @@ k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// K3: emit the pairs of one CTA's Gaussians, one output pair per thread step (load-balanced by a
-// binary search over the CTA's scanned counts), Gaussians in depth order (ties: canonical order),
-// tiles row-major inside each rectangle.
+// K3: emit the pairs of one CTA's Gaussians, kEmitPer consecutive candidate tiles per thread and
+// round (load-balanced by a binary search over the CTA's scanned rectangle areas), Gaussians in
+// depth order (ties: canonical order), tiles row-major inside each rectangle.
 // ---------------------------------------------------------------------------------------------
+constexpr int kEmitPer = 4;  // consecutive candidates per thread and round
+
 __global__ void __launch_bounds__(kProjBlock)
 k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
        const RenderDesc* __restrict__ renders, int R) {
@@ -170,33 +172,47 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
     const uint32_t total = s_end[kProjBlock - 1];
     const unsigned long long base = sc.block_offsets[blockIdx.x];
     uint32_t written = 0;
-    for (uint32_t k0 = 0; k0 < total; k0 += kProjBlock) {
-        const uint32_t k = k0 + t;
-        bool hit = false;
-        uint32_t tile = 0, gid = 0;
-        if (k < total) {
-            // first j with s_end[j] > k
-            int lo = 0, hi = kProjBlock - 1;
+    // rounds of kEmitPer x kProjBlock candidates, kEmitPer consecutive ones per thread
+    for (uint32_t k0 = 0; k0 < total; k0 += kProjBlock * kEmitPer) {
+        const uint32_t kb = k0 + (uint32_t)t * kEmitPer;
+        uint32_t bits = 0, tile[kEmitPer], gid[kEmitPer];
+        if (kb < total) {
+            int lo = 0, hi = kProjBlock - 1;  // first j with s_end[j] > kb
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (s_end[mid] > k) hi = mid;
+                if (s_end[mid] > kb) hi = mid;
                 else lo = mid + 1;
             }
-            const uint32_t local = k - (lo ? s_end[lo - 1] : 0u);  // candidate inside Gaussian lo
-            const uint32_t w = s_w[lo];
-            const uint32_t dy = local / w, dx = local - dy * w;
-            const uint32_t tx = s_x0[lo] + dx, ty = s_y0[lo] + dy;
-            const uint32_t area = s_end[lo] - (lo ? s_end[lo - 1] : 0u);
-            hit = area <= 32u ? ((s_mask[lo] >> local) & 1u) != 0u
-                              : tile_hit(s_u[lo], s_v[lo], s_ca[lo], s_cb[lo], s_cc[lo], s_sx[lo], s_sy[lo], (int)tx,
-                                         (int)ty, T);
-            tile = s_tbase[lo] + ty * s_tx[lo] + tx;
-            gid = s_gid[lo];
+#pragma unroll
+            for (int j = 0; j < kEmitPer; ++j) {
+                const uint32_t k = kb + j;
+                tile[j] = gid[j] = 0;
+                if (k >= total) continue;
+                while (s_end[lo] <= k) ++lo;  // the next Gaussian with candidates (s_end[255] > k)
+                const uint32_t start = lo ? s_end[lo - 1] : 0u;
+                const uint32_t local = k - start;  // candidate inside Gaussian lo
+                const uint32_t w = s_w[lo];
+                const uint32_t dy = local / w, dx = local - dy * w;
+                const uint32_t tx = s_x0[lo] + dx, ty = s_y0[lo] + dy;
+                const uint32_t area = s_end[lo] - start;
+                const bool hit = area <= 32u ? ((s_mask[lo] >> local) & 1u) != 0u
+                                             : tile_hit(s_u[lo], s_v[lo], s_ca[lo], s_cb[lo], s_cc[lo], s_sx[lo],
+                                                        s_sy[lo], (int)tx, (int)ty, T);
+                bits |= (uint32_t)hit << j;
+                tile[j] = s_tbase[lo] + ty * s_tx[lo] + tx;
+                gid[j] = s_gid[lo];
+            }
         }
-        // ordered compaction of this round's hits
-        const unsigned bal = __ballot_sync(kFull, hit);
+        // ordered compaction of this round's hits: exclusive scan of the per-thread hit counts
+        const uint32_t c = __popc(bits);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
         __syncthreads();  // the previous round's s_warp reads are done
-        if (lane == 0) s_warp[warp] = __popc(bal);
+        if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
         uint32_t before = 0, round = 0;
 #pragma unroll
@@ -204,11 +220,15 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
             before += w < warp ? s_warp[w] : 0u;
             round += s_warp[w];
         }
-        if (hit) {
-            const unsigned long long pos = base + written + before + __popc(bal & ((1u << lane) - 1u));
-            if (pos < (unsigned long long)capacity) {
-                reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
-                sc.vals[0][pos] = gid;
+        const unsigned long long pos0 = base + written + before + incl - c;
+#pragma unroll
+        for (int j = 0; j < kEmitPer; ++j) {
+            if ((bits >> j) & 1u) {
+                const unsigned long long pos = pos0 + __popc(bits & ((1u << j) - 1u));
+                if (pos < (unsigned long long)capacity) {
+                    reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile[j];
+                    sc.vals[0][pos] = gid[j];
+                }
             }
         }
         written += round;
@@ -224,7 +244,8 @@ __device__ __forceinline__ uint64_t kept_pairs(const Scratch& sc, int64_t capaci
     return P < (unsigned long long)capacity ? P : (unsigned long long)capacity;
 }
 
-// digit totals of every pass (digits from bit first_shift up) in one read of the keys
+// digit totals of every pass (digits from bit first_shift up) in one read of the keys, added into
+// the partial copy of the CTA
 template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
 k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __restrict__ keys, Scratch sc) {
@@ -239,24 +260,26 @@ k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __rest
             atomicAdd(&h[p][(key >> (first_shift + p * kRadixBits)) & (kRadix - 1)], 1u);
     }
     __syncthreads();
+    uint32_t* copy = sc.digit_totals + (blockIdx.x % kTotalCopies) * (kMaxPasses * kRadix);
     for (int k = threadIdx.x; k < passes * kRadix; k += kSortThreads) {
         const uint32_t v = (&h[0][0])[k];
-        if (v) atomicAdd(&sc.digit_totals[k], v);
+        if (v) atomicAdd(&copy[k], v);
     }
 }
 
-// per-CTA histogram of one digit
-template <typename KeyT>
+// per-CTA histogram of one digit (CTA tiles of kSortThreads x kItems keys)
+template <typename KeyT, int kItems>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_hist(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ keys, Scratch sc) {
+    constexpr int kTile = kSortThreads * kItems;
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;  // kSortThreads == kRadix
     __syncthreads();
     const uint64_t P = kept_pairs(sc, capacity);
-    const uint64_t begin = (uint64_t)blockIdx.x * kSortTile;
-    const uint64_t end = begin + kSortTile < P ? begin + kSortTile : P;
+    const uint64_t begin = (uint64_t)blockIdx.x * kTile;
+    const uint64_t end = begin + kTile < P ? begin + kTile : P;
     for (uint64_t k = begin + threadIdx.x; k < end; k += kSortThreads)
         atomicAdd(&h[(uint32_t)(keys[k] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
@@ -264,7 +287,10 @@ k_sort_hist(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ ke
 }
 
 // one CTA per digit: exclusive scan of that digit's per-CTA counts, offset by the total of all
-// smaller digits; in place (counts -> scatter offsets)
+// smaller digits (summed over the partial copies of the totals); in place (counts -> scatter
+// offsets); each thread scans kRowItems consecutive counts per round
+constexpr int kRowItems = 8;
+
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_rowscan(int pass, int sb_max, Scratch sc) {
     const int d = blockIdx.x;
@@ -272,20 +298,33 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
     __shared__ uint32_t s_warp[kSortThreads / 32];
     __shared__ uint32_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 32) {
-        // total of digits < d
-        const uint32_t* tot = sc.digit_totals + pass * kRadix;
+    {   // total of digits < d: thread t sums copy t mod 16 over digits t / 16, t / 16 + 16, ...
+        static_assert(kSortThreads % kTotalCopies == 0, "copies per thread stride");
+        constexpr int kStep = kSortThreads / kTotalCopies;
+        const uint32_t* tot = sc.digit_totals + (threadIdx.x % kTotalCopies) * (kMaxPasses * kRadix) + pass * kRadix;
         uint32_t acc = 0;
-        for (int k = lane; k < d; k += 32) acc += tot[k];
+        for (int k = threadIdx.x / kTotalCopies; k < d; k += kStep) acc += tot[k];
         acc = __reduce_add_sync(kFull, acc);
-        if (lane == 0) s_carry = acc;
+        if (lane == 0) s_warp[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) c += s_warp[w];
+            s_carry = c;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     uint32_t* row = sc.sort_hist + (size_t)d * sb_max;
-    for (uint32_t base = 0; base < nblk; base += kSortThreads) {
-        const uint32_t idx = base + threadIdx.x;
-        const uint32_t v = idx < nblk ? row[idx] : 0u;
-        uint32_t incl = v;
+    for (uint32_t base = 0; base < nblk; base += kSortThreads * kRowItems) {
+        const uint32_t i0 = base + threadIdx.x * kRowItems;
+        uint32_t v[kRowItems], mine = 0;
+#pragma unroll
+        for (int j = 0; j < kRowItems; ++j) {
+            v[j] = i0 + j < nblk ? row[i0 + j] : 0u;
+            mine += v[j];
+        }
+        uint32_t incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, incl, o);
@@ -293,21 +332,20 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
         }
         if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t w = lane < kSortThreads / 32 ? s_warp[lane] : 0u;
-            uint32_t wi = w;
+        uint32_t wpre = 0, total = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, wi, o);
-                if (lane >= o) wi += t;
-            }
-            if (lane < kSortThreads / 32) s_warp[lane] = wi - w;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            wpre += w < warp ? s_warp[w] : 0u;
+            total += s_warp[w];
+        }
+        uint32_t run = s_carry + wpre + incl - mine;
+#pragma unroll
+        for (int j = 0; j < kRowItems; ++j) {
+            if (i0 + j < nblk) row[i0 + j] = run;
+            run += v[j];
         }
         __syncthreads();
-        const uint32_t carry = s_carry;
-        if (idx < nblk) row[idx] = carry + s_warp[warp] + incl - v;
-        __syncthreads();
-        if (threadIdx.x == kSortThreads - 1) s_carry = carry + s_warp[warp] + incl;
+        if (threadIdx.x == 0) s_carry += total;
         __syncthreads();
     }
 }
@@ -318,21 +356,22 @@ k_sort_rowscan(int pass, int sb_max, Scratch sc) {
 // keys by digit in shared memory, then write each digit's run to its global offset, so the
 // global writes are contiguous runs instead of one scattered store per key.
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kWarpItems = kSortTile / kSortWarps;  // contiguous keys per warp
-constexpr int kRounds = kWarpItems / 32;            // == kSortItems
-template <typename KeyT>
-constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSortTile; }
+template <typename KeyT, int kItems>
+constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSortThreads * kItems; }
 
-template <typename KeyT>
+template <typename KeyT, int kItems>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ kin,
                const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
                Scratch sc) {
+    constexpr int kTile = kSortThreads * kItems;        // keys per CTA
+    constexpr int kWarpItems = kTile / kSortWarps;      // contiguous keys per warp
+    constexpr int kRounds = kWarpItems / 32;            // == kItems
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     KeyT* s_keys = reinterpret_cast<KeyT*>(s_dyn);
-    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KeyT) * kSortTile);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KeyT) * kTile);
     __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_gofs[kRadix];            // global offset of this CTA's run of digit d
     __shared__ uint32_t s_bstart[kRadix];          // start of digit d inside the CTA's reordering
@@ -342,7 +381,7 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
     s_gofs[threadIdx.x] = sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x];
     __syncthreads();
     const uint64_t P = kept_pairs(sc, capacity);
-    const uint64_t cbase = (uint64_t)blockIdx.x * kSortTile;
+    const uint64_t cbase = (uint64_t)blockIdx.x * kTile;
     const uint64_t wbase = cbase + (uint64_t)warp * kWarpItems;
     const unsigned lt = (1u << lane) - 1u;
     KeyT key[kRounds];
@@ -401,7 +440,7 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
         if (dr[r] != 0xffffffffu) {
             const uint32_t d = dr[r] & 0xffu;
             const uint32_t pos = s_bstart[d] + s_wh[warp][d] + (dr[r] >> 8);
-            if (pos < (uint32_t)kSortTile) {
+            if (pos < (uint32_t)kTile) {
                 s_keys[pos] = key[r];
                 s_vals[pos] = val[r];
             } else {
@@ -410,7 +449,7 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
         }
     }
     __syncthreads();
-    const uint32_t count = (uint32_t)min((uint64_t)kSortTile, P - cbase);
+    const uint32_t count = (uint32_t)min((uint64_t)kTile, P - cbase);
     for (uint32_t p = threadIdx.x; p < count; p += kSortThreads) {
         const KeyT k = s_keys[p];
         const uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
@@ -430,14 +469,32 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
 __global__ void __launch_bounds__(256)
 k_ranges(int64_t capacity, uint32_t tiles, const uint32_t* __restrict__ keys, Scratch sc) {
     const uint64_t P = kept_pairs(sc, capacity);
-    for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256) {
-        const uint32_t t = keys[k];
-        if (t >= tiles) {
-            atomicOr(sc.status, kStatusInternal);
-            continue;
+    // four consecutive keys per thread step (one 16-byte load), with the neighbours either side
+    for (uint64_t k0 = ((uint64_t)blockIdx.x * 256 + threadIdx.x) * 4; k0 < P; k0 += (uint64_t)gridDim.x * 1024) {
+        uint32_t t[6];
+        t[0] = k0 > 0 ? keys[k0 - 1] : 0xffffffffu;
+        if (k0 + 4 <= P) {
+            const uint4 q = *reinterpret_cast<const uint4*>(keys + k0);
+            t[1] = q.x;
+            t[2] = q.y;
+            t[3] = q.z;
+            t[4] = q.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[1 + j] = k0 + j < P ? keys[k0 + j] : 0xffffffffu;
         }
-        if (k == 0 || keys[k - 1] != t) sc.ranges[t].x = (uint32_t)k;
-        if (k == P - 1 || keys[k + 1] != t) sc.ranges[t].y = (uint32_t)(k + 1);
+        t[5] = k0 + 4 < P ? keys[k0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int j = 1; j <= 4; ++j) {
+            const uint64_t k = k0 + j - 1;
+            if (k >= P) break;
+            if (t[j] >= tiles) {
+                atomicOr(sc.status, kStatusInternal);
+                continue;
+            }
+            if (t[j - 1] != t[j]) sc.ranges[t[j]].x = (uint32_t)k;
+            if (t[j + 1] != t[j]) sc.ranges[t[j]].y = (uint32_t)(k + 1);
+        }
     }
 }
 
@@ -491,37 +548,40 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch
 
 }  // namespace
 
-// the scatter reorders a whole CTA tile of pairs in dynamic shared memory (32 KB with 32-bit
-// keys, 48 KB with 64-bit keys)
+// the scatter reorders a whole CTA tile of keys in dynamic shared memory (32 KB with 4096 32-bit
+// keys, 48 KB with 4096 64-bit keys)
+template <typename KeyT, int kItems>
 void enable_scatter_smem() {
     static bool done = [] {
-        cudaFuncSetAttribute(k_sort_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<uint32_t>());
-        cudaFuncSetAttribute(k_sort_scatter<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<unsigned long long>());
+        cudaFuncSetAttribute(k_sort_scatter<KeyT, kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<KeyT, kItems>());
         return true;
     }();
     (void)done;
 }
 
-// LSD passes over the keys in keys[0] / keys[1] (viewed as KeyT) starting at bit first_shift;
-// returns the launches and leaves the sorted buffer's index in *out_buf
-template <typename KeyT>
+// LSD passes over the keys in keys[0] / keys[1] (viewed as KeyT) starting at bit first_shift, CTA
+// tiles of kSortThreads x kItems keys; returns the launches and leaves the sorted buffer's index
+// in *out_buf
+template <typename KeyT, int kItems>
 int sort_passes(int64_t capacity, int first_shift, int passes, const Scratch& sc, cudaStream_t s, int* out_buf) {
-    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
-    const int grid_stride_blocks = 152 * 8;
+    constexpr int kTile = kSortThreads * kItems;
+    const int sb_max = (int)((capacity + kTile - 1) / kTile);
+    // the totals read every key once: one CTA per 1024 keys, at most 8 per SM
+    const int64_t want = (capacity + 1023) / 1024;
+    const int total_blocks = (int)(want < 152 * 8 ? (want > 0 ? want : 1) : 152 * 8);
     int buf = 0;
     *out_buf = 0;
     if (sb_max <= 0 || passes <= 0) return 0;
-    enable_scatter_smem();
+    enable_scatter_smem<KeyT, kItems>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
-    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kMaxPasses * kRadix, s);
-    k_digit_totals<KeyT><<<grid_stride_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, k[0], sc);
+    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+    k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, k[0], sc);
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
-        k_sort_hist<KeyT><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, k[buf], sc);
+        k_sort_hist<KeyT, kItems><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, k[buf], sc);
         k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-        k_sort_scatter<KeyT><<<sb_max, kSortThreads, scatter_smem<KeyT>(), s>>>(
+        k_sort_scatter<KeyT, kItems><<<sb_max, kSortThreads, scatter_smem<KeyT, kItems>(), s>>>(
             capacity, shift, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }
@@ -545,7 +605,7 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     d.pair_count = sc.dcount;
     d.sort_blocks = sc.dblocks;
     int buf = 0;
-    const int launched = sort_passes<uint32_t>(n, 0, 32 / kRadixBits, d, s, &buf);
+    const int launched = sort_passes<uint32_t, kDepthItems>(n, 0, 32 / kRadixBits, d, s, &buf);
     *perm = sc.dvals[buf];
     return launched;
 }
@@ -566,7 +626,7 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
     // the pairs arrive in depth order: a stable sort of their 32-bit tile keys completes it
     const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
     int buf = 0;
-    int launched = sort_passes<uint32_t>(capacity, 0, passes, sc, s, &buf);
+    int launched = sort_passes<uint32_t, kSortItems>(capacity, 0, passes, sc, s, &buf);
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (capacity > 0) {
         k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)tiles, reinterpret_cast<const uint32_t*>(sc.keys[buf]), sc);
@@ -585,8 +645,8 @@ int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t 
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf) {
-    return sort_passes<unsigned long long>(capacity, 0, (key_bits + kRadixBits - 1) / kRadixBits, sc, s,
-                                           out_buf);
+    return sort_passes<unsigned long long, kSortItems>(capacity, 0, (key_bits + kRadixBits - 1) / kRadixBits, sc,
+                                                       s, out_buf);
 }
 
 }  // namespace pgs

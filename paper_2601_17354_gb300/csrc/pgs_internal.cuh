@@ -13,11 +13,17 @@ constexpr int kTileDefault = 16;
 inline bool valid_tile(int T) { return T == 8 || T == 16 || T == 32; }
 constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kernels
 constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
-constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels
+constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels of the pairs
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort CTA
+constexpr int kDepthItems = 4;       // keys per thread in the depth sort (more, shorter CTAs)
+constexpr int kDepthTile = kSortThreads * kDepthItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
+// the digit totals of a sort are kept as this many partial copies (CTA b adds into copy b mod
+// kTotalCopies), so no counter takes more than a few dozen CTAs' atomics
+constexpr int kTotalCopies = 16;
+constexpr int kTotalWords = kTotalCopies * kMaxPasses * kRadix;
 
 // device status word bits
 constexpr int32_t kStatusCapacity = 1;
@@ -51,7 +57,7 @@ struct Scratch {
     int32_t* status = nullptr;
     unsigned long long* pair_count = nullptr;
     uint32_t* sort_blocks = nullptr;  // sort CTAs with work in the current render
-    uint32_t* digit_totals = nullptr; // [kMaxPasses][kRadix]
+    uint32_t* digit_totals = nullptr; // [kTotalCopies][kMaxPasses][kRadix]
     float* loss_partials = nullptr;   // [2][kLossBlocks]
     uint32_t* loss_ticket = nullptr;
     // depth sort of the Gaussians: keys = depth bits (culled: all ones), values = canonical index;

@@ -300,7 +300,7 @@ k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc
     if (i < n) project_item<DEG>(g, i, cam, TX, TY, T, i, sc);
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
-        *sc.dblocks = (uint32_t)((n + kSortTile - 1) / kSortTile);
+        *sc.dblocks = (uint32_t)((n + kDepthTile - 1) / kDepthTile);
     }
 }
 
@@ -327,7 +327,7 @@ k_project_fwd_batch(const RenderDesc* __restrict__ renders, int R, const SceneDe
     }
     if (j == 0) {
         *sc.dcount = (unsigned long long)items;
-        *sc.dblocks = (uint32_t)((items + kSortTile - 1) / kSortTile);
+        *sc.dblocks = (uint32_t)((items + kDepthTile - 1) / kDepthTile);
     }
 }
 

@@ -22,18 +22,18 @@ constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + sizeof(unsigned long long) * kStaticMaxPairs;
 constexpr size_t kOffHist = kOffVals + sizeof(uint32_t) * kStaticMaxPairs;
 constexpr size_t kOffTotals = kOffHist + sizeof(uint32_t) * kRadix * kStaticSortBlocks;
-constexpr size_t kOffCount = kOffTotals + sizeof(uint32_t) * kMaxPasses * kRadix;
+constexpr size_t kOffCount = kOffTotals + sizeof(uint32_t) * kTotalWords;
 constexpr size_t kOffBlocks = kOffCount + sizeof(unsigned long long);
 constexpr size_t kOffStatus = kOffBlocks + sizeof(uint32_t);
 constexpr size_t kScratchBytes = (kOffStatus + sizeof(int32_t) + 255) & ~size_t(255);
 
-// Held by every GPU that loads the library until the process exits (about 3.1 MB).
+// Held by every GPU that loads the library until the process exits (about 3.2 MB).
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
 // Per-call set-up on the device: pair count, active sort CTAs, cleared totals and status.
 __global__ void k_static_sort_init(unsigned char* base, int64_t count) {
     uint32_t* totals = reinterpret_cast<uint32_t*>(base + kOffTotals);
-    for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += blockDim.x) totals[k] = 0;
+    for (int k = threadIdx.x; k < kTotalWords; k += blockDim.x) totals[k] = 0;
     if (threadIdx.x == 0) {
         *reinterpret_cast<unsigned long long*>(base + kOffCount) = (unsigned long long)count;
         *reinterpret_cast<uint32_t*>(base + kOffBlocks) = (uint32_t)((count + kSortTile - 1) / kSortTile);
