@@ -526,6 +526,21 @@ __device__ __forceinline__ void zero_parts(GradParts& gp) {
 
 constexpr int kChunk = 8;  // parameter rows whose loads are issued together
 
+__device__ __forceinline__ void prefetch_l2(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Start the DRAM reads of one Gaussian's Adam moments (rows of m and v) into L2, so that they
+// overlap the gradient chain instead of following it (the kernel's register use leaves 16 warps
+// per SM, too few to cover the moments' latency by themselves).
+template <int ROWS>
+__device__ __forceinline__ void prefetch_moments(const Rows& Mm, const Rows& Vv, int64_t n, int64_t i) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int64_t idx = (int64_t)row_sub(r) * n + i;
+        prefetch_l2(Mm.g[row_group(r)] + idx);
+        prefetch_l2(Vv.g[row_group(r)] + idx);
+    }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock, 2)
 k_project_bwd(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians out) {
@@ -566,10 +581,11 @@ k_project_bwd_adam(pgs_gaussians g, pgs_camera cam, Scratch sc, pgs_gaussians m,
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     if (i >= n) return;
+    const Rows Pp = rows_of(g), Mm = rows_of(m), Vv = rows_of(v);
+    prefetch_moments<ROWS>(Mm, Vv, n, i);
     GradParts gp;
     if (sc.touched[i] != 0) chain<DEG>(g, cam, sc.grad2d, n, i, i, gp);
     else zero_parts(gp);
-    const Rows Pp = rows_of(g), Mm = rows_of(m), Vv = rows_of(v);
 #pragma unroll
     for (int r0 = 0; r0 < ROWS; r0 += kChunk) {
         float pp[kChunk], mm[kChunk], vv[kChunk];
@@ -652,6 +668,7 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
     const SceneDesc& sd = scenes[scene_of(scenes, S, k)];
     const int64_t i = k - sd.gauss_base;
     const int64_t n = sd.params.n;
+    prefetch_moments<ROWS>(rows_of(sd.m), rows_of(sd.v), n, i);
     for (int rr = 0; rr < sd.n_renders; ++rr) {
         const RenderDesc& rd = renders[sd.first_render + rr];
         const int64_t j = rd.item_base + i;
