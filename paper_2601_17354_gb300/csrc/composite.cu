@@ -240,6 +240,52 @@ __device__ __forceinline__ void warp_sum9(const float v[9], int lane, float& s8,
     s9 = t;
 }
 
+// Sum a[0..8] and b[0..8] (values 0..8 and 9..17) over the warp by one transpose-reduction: at
+// each level (xor 16, 8, 4, 2, 1) a lane keeps the half of its values selected by that lane bit
+// (odd counts padded with a zero) and adds the partner's copy of it, 9 + 5 + 3 + 2 + 1 = 20
+// shuffles.  Afterwards lane l holds the warp sum of value idx, or idx = -1 (a padding slot).
+__device__ __forceinline__ void warp_sum18(const float a[9], const float b[9], int lane, float& s, int& idx) {
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4, b2 = lane & 2, b1 = lane & 1;
+    float x9[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) x9[k] = (b16 ? b[k] : a[k]) + __shfl_xor_sync(kFull, b16 ? a[k] : b[k], 16);
+    float x5[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float lo = x9[k], hi = k + 5 < 9 ? x9[k + 5] : 0.0f;
+        x5[k] = (b8 ? hi : lo) + __shfl_xor_sync(kFull, b8 ? lo : hi, 8);
+    }
+    float x3[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = x5[k], hi = k + 3 < 5 ? x5[k + 3] : 0.0f;
+        x3[k] = (b4 ? hi : lo) + __shfl_xor_sync(kFull, b4 ? lo : hi, 4);
+    }
+    float x2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float lo = x3[k], hi = k + 2 < 3 ? x3[k + 2] : 0.0f;
+        x2[k] = (b2 ? hi : lo) + __shfl_xor_sync(kFull, b2 ? lo : hi, 2);
+    }
+    s = (b1 ? x2[1] : x2[0]) + __shfl_xor_sync(kFull, b1 ? x2[0] : x2[1], 1);
+    const int r2 = (b2 ? 2 : 0) + (b1 ? 1 : 0);  // index in the 3-value level (4 with the pad)
+    const int r4 = (b4 ? 3 : 0) + r2;            // in the 5-value level
+    const int r8 = (b8 ? 5 : 0) + r4;            // in the 9-value level
+    idx = (r2 < 3 && r4 < 5 && r8 < 9) ? (b16 ? 9 : 0) + r8 : -1;
+}
+
+// factor from the summed (dpow dx^2, dpow dx dy, dpow dy^2) to d power / d(a, b, c) =
+// (-dx^2 / 2, -dx dy, -dy^2 / 2); 1 for the other screen-space gradients
+__device__ __forceinline__ float grad_factor(int q) { return q == 2 || q == 4 ? -0.5f : (q == 3 ? -1.0f : 1.0f); }
+
+// One entry's nine warp-summed screen-space gradients added to its canonical index
+__device__ __forceinline__ void scatter9(const float v[9], int lane, uint32_t id, int64_t n, float* grad2d) {
+    float s8, s9;
+    warp_sum9(v, lane, s8, s9);
+    if ((lane & 3) == 0) atomicAdd(&grad2d[(size_t)(lane >> 2) * n + id], grad_factor(lane >> 2) * s8);
+    if (lane == 1) atomicAdd(&grad2d[(size_t)8 * n + id], s9);
+}
+
 template <int kDepth>
 struct BwdSmem {
     float4 xyo[kDepth], s2[kDepth], con[kDepth], rgb[kDepth];
@@ -660,7 +706,10 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
         __syncthreads();
         // this warp's entries: positions below its deepest `last`
         const int jtop = (int)min((uint32_t)cnt, wmax > start ? wmax - start : 0u);
-        for (int j = jtop - 1; j >= 0; --j) {
+        // one entry, back to front: per-lane gradient sums over the strip (dpow-weighted mean
+        // terms already through the conic), the strip's state moved in front of the entry;
+        // returns whether a pixel of the lane composited it
+        auto entry = [&](int j, float (&v)[9]) -> bool {
             const uint32_t pos = start + j;
             const float4 pm = s_xyo[j];
             const float4 s2 = s_s2[j];
@@ -671,7 +720,7 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
             // dL/dalpha G, alpha T dL/dC (rgb)
             F2 acc[9];
 #pragma unroll
-            for (int v = 0; v < 9; ++v) acc[v] = f2(0.0f);
+            for (int q = 0; q < 9; ++q) acc[q] = f2(0.0f);
             bool contrib = false;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -711,30 +760,39 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
                     acc[4] = fma2(dpy, dy, acc[4]);
                 }
             }
-            if (__any_sync(kFull, contrib)) {
-                float v[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const float2 h = un(acc[q]);
-                    v[q] = h.x + h.y;
+            for (int q = 0; q < 9; ++q) {
+                const float2 h = un(acc[q]);
+                v[q] = h.x + h.y;
+            }
+            // d power / d mean2D = (a dx + b dy, c dy + b dx) with the conic (a, b, c) of the
+            // entry, from the strip's sums of dpow dx and dpow dy
+            const float4 con = s_con[j];
+            const float m0 = fmaf(con.x, v[0], con.y * v[1]);
+            const float m1 = fmaf(con.z, v[1], con.y * v[0]);
+            v[0] = m0;
+            v[1] = m1;
+            return contrib;
+        };
+        // entries in pairs: two entries' gradients share one transpose-reduction and one
+        // atomic instruction (an entry no lane composited is not added)
+        for (int j = jtop - 1; j >= 0; j -= 2) {
+            float va[9], vb[9];
+            const bool ca = __any_sync(kFull, entry(j, va));
+            const bool cb = j >= 1 && __any_sync(kFull, entry(j - 1, vb));
+            if (ca && cb) {
+                float s;
+                int idx;
+                warp_sum18(va, vb, lane, s, idx);
+                if (idx >= 0) {
+                    const int q = idx >= 9 ? idx - 9 : idx;
+                    const uint32_t id = s_id[idx >= 9 ? j - 1 : j];
+                    atomicAdd(&sc.grad2d[(size_t)q * n + id], grad_factor(q) * s);
                 }
-                // d power / d mean2D = (a dx + b dy, c dy + b dx) with the conic (a, b, c) of
-                // the entry, from the strip's sums of dpow dx and dpow dy
-                const float4 con = s_con[j];
-                const float m0 = fmaf(con.x, v[0], con.y * v[1]);
-                const float m1 = fmaf(con.z, v[1], con.y * v[0]);
-                v[0] = m0;
-                v[1] = m1;
-                float s8, s9;
-                warp_sum9(v, lane, s8, s9);
-                const uint32_t id = s_id[j];
-                if ((lane & 3) == 0) {
-                    // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
-                    const int q = lane >> 2;
-                    const float f = q == 2 || q == 4 ? -0.5f : (q == 3 ? -1.0f : 1.0f);
-                    atomicAdd(&sc.grad2d[(size_t)q * n + id], f * s8);
-                }
-                if (lane == 1) atomicAdd(&sc.grad2d[(size_t)8 * n + id], s9);
+            } else if (ca) {
+                scatter9(va, lane, s_id[j], n, sc.grad2d);
+            } else if (cb) {
+                scatter9(vb, lane, s_id[j - 1], n, sc.grad2d);
             }
         }
         end = start;
