@@ -17,9 +17,10 @@
 // the colour behind it with Eq. 7 itself (C_in of the last entry is the background), then applies
 // Eq. 8:  dL/dc = alpha dL/dC_out,  dL/dalpha = <dL/dC_out, c - C_in>,  dL/dC_out = T_i dL/dC.
 // Each thread first sums its strip's nine screen-space gradients; the warp's 32 partial sums are
-// then added by a transpose-reduction (9 shuffles for 8 values) and scattered with one atomic per
-// value per warp to the canonical index (Eq. 10: grad_{pi(i)} += g_i).  Each warp stops at its
-// own deepest `last`, not the tile's.
+// then added by a transpose-reduction (9 shuffles for 8 values; in the paired-pixel kernels two
+// consecutive entries share one 18-value reduction) and scattered with one atomic per value per
+// warp to the canonical index (Eq. 10: grad_{pi(i)} += g_i).  Each warp stops at its own deepest
+// `last`, not the tile's.
 //
 // The exponent is evaluated base 2: the conic is pre-scaled by -log2(e)/2 (and -log2(e) for the
 // cross term) when an entry is staged, and alpha uses ex2.approx.  Forward and backward stage and
