@@ -507,10 +507,10 @@ k_join_keys(int64_t capacity, const uint32_t* __restrict__ tiles, const uint32_t
         out[k] = ((unsigned long long)tiles[k] << 32) | sc.depth_bits[vals[k]];
 }
 
-// One CTA: counting sort of the tiles into 64 half-octave buckets of their list length,
+// One CTA: counting sort of the tiles into 128 quarter-octave buckets of their list length,
 // heaviest bucket first.  Only the schedule depends on it, never a result.
 constexpr int kOrderThreads = 1024;
-constexpr int kOrderBuckets = 64;
+constexpr int kOrderBuckets = 128;
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch sc) {
     __shared__ uint32_t hist[kOrderBuckets], cursor[kOrderBuckets];
@@ -519,27 +519,37 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch
     auto slot_of = [&](int t) {
         const uint2 r = sc.ranges[t];
         const uint32_t len = r.y - r.x;
-        int b = 0;
-        if (len) {
+        // lengths 0..3 are their own buckets; from 4 on, 4 (l - 1) + the two bits after the
+        // leading one (l = floor(log2 len)): monotone in the length, at most 123
+        int b = (int)len;
+        if (len >= 4) {
             const int l = 31 - __clz(len);
-            b = 2 * l + (l > 0 ? (int)((len >> (l - 1)) & 1u) : 0) + 1;
+            b = 4 * (l - 1) + (int)((len >> (l - 2)) & 3u);
         }
-        return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+        return kOrderBuckets - 1 - b;
     };
     for (int t = threadIdx.x; t < tiles; t += kOrderThreads) atomicAdd(&hist[slot_of(t)], 1u);
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 32) {  // exclusive scan, 4 buckets per lane
         const int lane = threadIdx.x;
-        uint32_t a = hist[2 * lane], b = hist[2 * lane + 1];
-        uint32_t s = a + b, incl = s;
+        uint32_t h[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            h[k] = hist[4 * lane + k];
+            s += h[k];
+        }
+        uint32_t incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t v = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += v;
         }
-        const uint32_t excl = incl - s;
-        cursor[2 * lane] = excl;
-        cursor[2 * lane + 1] = excl + a;
+        uint32_t run = incl - s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cursor[4 * lane + k] = run;
+            run += h[k];
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tiles; t += kOrderThreads)

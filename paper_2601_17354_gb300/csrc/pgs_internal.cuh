@@ -193,7 +193,7 @@ int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf);
 
-// Order the tiles by decreasing list length (half-octave buckets), so the compositing grids
+// Order the tiles by decreasing list length (quarter-octave buckets), so the compositing grids
 // start the heaviest tiles first.
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
