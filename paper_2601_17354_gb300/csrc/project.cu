@@ -206,25 +206,94 @@ __device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3])
     for (int k = 0; k < 3; ++k) c[k] = -(V[k] * V[3] + V[4 + k] * V[7] + V[8 + k] * V[11]);
 }
 
+// The reach tests of a warp's rectangles, load-balanced: the candidate tiles of the 32 lanes'
+// rectangles are numbered in lane order (row-major inside each rectangle) and evaluated 32 per
+// round, candidate k by lane k mod 32 with its owner's parameters (found by a binary search over
+// the lanes' inclusive counts); a lane's count and bit mask of reached tiles (rectangles of <= 32
+// tiles) come from the round ballots over its own candidates.  Every lane of the warp calls it;
+// the warp's rectangles hold at most 32 x 1024 candidates.
+__device__ __forceinline__ void warp_reach(uint32_t area, uint32_t w, uint32_t x0, uint32_t y0, float u, float v,
+                                           float ca, float cb, float cc, float sx, float sy, int T, uint32_t& count,
+                                           uint32_t& hits) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kAll, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kAll, incl, 31);
+    const uint32_t first = incl - area;  // this lane's first candidate
+    count = 0;
+    hits = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t k = base + lane;
+        int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive count exceeds k
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t im = __shfl_sync(kAll, incl, mid);
+            if (lo < hi) {
+                if (im > k) hi = mid;
+                else lo = mid + 1;
+            }
+        }
+        const uint32_t ofirst = __shfl_sync(kAll, first, lo), ow = __shfl_sync(kAll, w, lo);
+        const uint32_t ox0 = __shfl_sync(kAll, x0, lo), oy0 = __shfl_sync(kAll, y0, lo);
+        const float ou = __shfl_sync(kAll, u, lo), ov = __shfl_sync(kAll, v, lo);
+        const float oca = __shfl_sync(kAll, ca, lo), ocb = __shfl_sync(kAll, cb, lo), occ = __shfl_sync(kAll, cc, lo);
+        const float osx = __shfl_sync(kAll, sx, lo), osy = __shfl_sync(kAll, sy, lo);
+        const int oT = __shfl_sync(kAll, T, lo);
+        bool h = false;
+        if (k < total) {  // then the owner's rectangle is not empty (ow >= 1)
+            const uint32_t local = k - ofirst;
+            const uint32_t dy = local / ow, dx = local - dy * ow;
+            h = tile_hit(ou, ov, oca, ocb, occ, osx, osy, (int)(ox0 + dx), (int)(oy0 + dy), oT);
+        }
+        const uint32_t hb = __ballot_sync(kAll, h);
+        // this lane's candidates in the round: [s0, s1), at lanes s0 - base ..
+        const uint32_t s0 = max(first, base), s1 = min(incl, base + 32u);
+        if (s1 > s0) {
+            const uint32_t nb = s1 - s0;
+            const uint32_t mine = (hb >> (s0 - base)) & (nb == 32u ? kAll : (1u << nb) - 1u);
+            count += __popc(mine);
+            if (area <= 32u) hits |= mine << (s0 - first);
+        }
+    }
+}
+
 // Project Gaussian i of g through cam (tiles of T x T pixels, grid TX x TY) and write its record at
-// item j.
+// item j.  Every lane of the warp calls it (the reach tests are warp-collective); lanes with
+// active == false only take part in them.
 template <int DEG>
 __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
-                                             int TX, int TY, int T, int64_t j, const Scratch& sc) {
+                                             int TX, int TY, int T, int64_t j, const Scratch& sc, bool active) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     uint32_t count = 0;
-    const float mu[3] = {g.means[i], g.means[n + i], g.means[2 * n + i]};
-    const float ls[3] = {g.log_scales[i], g.log_scales[n + i], g.log_scales[2 * n + i]};
-    const float q[4] = {g.quats[i], g.quats[n + i], g.quats[2 * n + i], g.quats[3 * n + i]};
-    const float logit = g.opacity_logits[i];
+    float mu[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, logit = 0.f;
+    if (active) {
+        mu[0] = g.means[i];
+        mu[1] = g.means[n + i];
+        mu[2] = g.means[2 * n + i];
+        ls[0] = g.log_scales[i];
+        ls[1] = g.log_scales[n + i];
+        ls[2] = g.log_scales[2 * n + i];
+        q[0] = g.quats[i];
+        q[1] = g.quats[n + i];
+        q[2] = g.quats[2 * n + i];
+        q[3] = g.quats[3 * n + i];
+        logit = g.opacity_logits[i];
+    }
     bool finite = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(ls[0]) &&
                   isfinite(ls[1]) && isfinite(ls[2]) && isfinite(q[0]) && isfinite(q[1]) &&
                   isfinite(q[2]) && isfinite(q[3]) && isfinite(logit);
     Geo G;
-    bool vis = finite && geometry(mu, ls, q, cam, G);
+    bool vis = active && finite && geometry(mu, ls, q, cam, G);
     uint32_t x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     float con_a = 0.f, con_b = 0.f, con_c = 0.f;  // conic, decision path
+    float sx = 0.f, sy = 0.f;                      // slopes of the reach test's line minima
     uint32_t hits = 0;                             // reached tiles of a rectangle of <= 32
     if (vis) {
         // per-axis 3-sigma extents: the bounding box of the 3-sigma ellipse of the 2-D covariance
@@ -237,22 +306,29 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
             x1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.u, rx), tf)), 1.0f), 0.0f, (float)TX);
             y0 = (uint32_t)clampf(floorf(__fdiv_rn(__fsub_rn(G.v, ry), tf)), 0.0f, (float)TY);
             y1 = (uint32_t)clampf(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(G.v, ry), tf)), 1.0f), 0.0f, (float)TY);
-            // of the rectangle's tiles, those whose pixel centres the 3-sigma ellipse reaches
             const float inv = __fdiv_rn(1.0f, G.det);
             con_a = __fmul_rn(G.cov_c, inv);
             con_b = __fmul_rn(-G.cov_b, inv);
             con_c = __fmul_rn(G.cov_a, inv);
-            const float sx = __fdiv_rn(con_b, con_a), sy = __fdiv_rn(con_b, con_c);
-            const bool small = (x1 - x0) * (y1 - y0) <= 32u;
-            uint32_t k = 0;
-            for (uint32_t ty = y0; ty < y1; ++ty)
-                for (uint32_t tx = x0; tx < x1; ++tx, ++k) {
-                    const bool h = tile_hit(G.u, G.v, con_a, con_b, con_c, sx, sy, (int)tx, (int)ty, T);
-                    count += h;
-                    if (small && h) hits |= 1u << k;
-                }
+            sx = __fdiv_rn(con_b, con_a);
+            sy = __fdiv_rn(con_b, con_c);
         }
     }
+    // of the rectangle's tiles, those whose pixel centres the 3-sigma ellipse reaches
+    const uint32_t rw = vis ? x1 - x0 : 0u, area = vis ? rw * (y1 - y0) : 0u;  // at most 65535^2
+    if (__any_sync(0xffffffffu, area > 1024u)) {
+        // a large rectangle in the warp: each lane walks its own
+        uint32_t k = 0;
+        for (uint32_t ty = y0; ty < y1 && vis; ++ty)
+            for (uint32_t tx = x0; tx < x1; ++tx, ++k) {
+                const bool h = tile_hit(G.u, G.v, con_a, con_b, con_c, sx, sy, (int)tx, (int)ty, T);
+                count += h;
+                if (area <= 32u && h) hits |= 1u << k;
+            }
+    } else {
+        warp_reach(area, rw, x0, y0, vis ? G.u : 0.f, vis ? G.v : 0.f, con_a, con_b, con_c, sx, sy, T, count, hits);
+    }
+    if (!active) return;
     if (count > 0) {
         // value path: opacity, colour (the conic is the decision path's)
         const float opacity = 1.0f / (1.0f + expf(-logit));
@@ -297,7 +373,7 @@ __global__ void __launch_bounds__(kProjBlock)
 k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc) {
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    if (i < n) project_item<DEG>(g, i, cam, TX, TY, T, i, sc);
+    project_item<DEG>(g, i < n ? i : 0, cam, TX, TY, T, i, sc, i < n);
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
         *sc.dblocks = (uint32_t)((n + kDepthTile - 1) / kDepthTile);
@@ -321,10 +397,10 @@ __global__ void __launch_bounds__(kProjBlock)
 k_project_fwd_batch(const RenderDesc* __restrict__ renders, int R, const SceneDesc* __restrict__ scenes,
                     int64_t items, Scratch sc) {
     const int64_t j = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    if (j < items) {
-        const RenderDesc& rd = renders[render_of_item(renders, R, j)];
-        project_item<DEG>(scenes[rd.scene].params, j - rd.item_base, rd.cam, rd.TX, rd.TY, rd.tile, j, sc);
-    }
+    const bool active = j < items;
+    const RenderDesc& rd = renders[active ? render_of_item(renders, R, j) : 0];
+    project_item<DEG>(scenes[rd.scene].params, active ? j - rd.item_base : 0, rd.cam, rd.TX, rd.TY, rd.tile, j, sc,
+                      active);
     if (j == 0) {
         *sc.dcount = (unsigned long long)items;
         *sc.dblocks = (uint32_t)((items + kDepthTile - 1) / kDepthTile);
