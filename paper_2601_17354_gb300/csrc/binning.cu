@@ -93,19 +93,16 @@ k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// K3: emit the pairs of one CTA's Gaussians, kEmitPer consecutive candidate tiles per thread and
-// round (load-balanced by a binary search over the CTA's scanned rectangle areas), Gaussians in
-// depth order (ties: canonical order), tiles row-major inside each rectangle.
+// K3: emit the pairs of one CTA's Gaussians in depth order (ties: canonical order), tiles
+// row-major inside each rectangle.  Each warp walks the candidate tiles of its own 32 Gaussians,
+// 32 per round (candidate k by lane k mod 32; its Gaussian found by a shuffle binary search over
+// the lanes' inclusive rectangle areas), and compacts the reached ones in order with one ballot.
+// A warp's output starts after the pairs of the warps before it, known from the Gaussians'
+// reached-tile counts, so warps never wait for one another inside the walk.
 // ---------------------------------------------------------------------------------------------
-constexpr int kEmitPer = 4;  // consecutive candidates per thread and round
-
 __global__ void __launch_bounds__(kProjBlock)
 k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
        const RenderDesc* __restrict__ renders, int R) {
-    // the CTA's Gaussians (in depth order) and their rectangles' tiles as one flat candidate list;
-    // candidates whose tile the 3-sigma ellipse reaches are written in order (a CTA-wide ordered
-    // compaction per round), so each Gaussian's pairs stay contiguous, row-major in its rectangle
-    __shared__ uint32_t s_end[kProjBlock];  // inclusive prefix of candidate counts (rectangle areas)
     __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock];
     __shared__ uint32_t s_tx[kProjBlock], s_tbase[kProjBlock];
     __shared__ float s_u[kProjBlock], s_v[kProjBlock], s_ca[kProjBlock], s_cb[kProjBlock], s_cc[kProjBlock];
@@ -115,11 +112,12 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
     __shared__ uint32_t s_gid[kProjBlock];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, reached = 0;  // rectangle area, reached tiles
     if (i < n) {
         const uint32_t g = perm[i];
         s_gid[t] = g;
-        if (sc.touched[g]) {
+        reached = sc.touched[g];
+        if (reached) {
             const uint2 r = sc.rect[g];
             s_x0[t] = r.x & 0xffffu;
             s_y0[t] = r.x >> 16;
@@ -154,84 +152,53 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
         const uint32_t v = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += v;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < kProjBlock / 32 ? s_warp[lane] : 0u;
-        uint32_t wi = w;
+    const uint32_t first = incl - cnt;  // this lane's first candidate in the warp's walk
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t wpairs = __reduce_add_sync(kFull, reached);
+    if (lane == 0) s_warp[warp] = wpairs;
+    __syncthreads();  // also publishes the lanes' records in shared memory
+    uint32_t before = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(kFull, wi, o);
-            if (lane >= o) wi += v;
-        }
-        if (lane < kProjBlock / 32) s_warp[lane] = wi - w;
-    }
-    __syncthreads();
-    s_end[t] = incl + s_warp[warp];
-    __syncthreads();
-    const uint32_t total = s_end[kProjBlock - 1];
-    const unsigned long long base = sc.block_offsets[blockIdx.x];
+    for (int w = 0; w < kProjBlock / 32; ++w) before += w < warp ? s_warp[w] : 0u;
+    const unsigned long long out = sc.block_offsets[blockIdx.x] + before;
+    const unsigned lt = (1u << lane) - 1u;
     uint32_t written = 0;
-    // rounds of kEmitPer x kProjBlock candidates, kEmitPer consecutive ones per thread
-    for (uint32_t k0 = 0; k0 < total; k0 += kProjBlock * kEmitPer) {
-        const uint32_t kb = k0 + (uint32_t)t * kEmitPer;
-        uint32_t bits = 0, tile[kEmitPer], gid[kEmitPer];
-        if (kb < total) {
-            int lo = 0, hi = kProjBlock - 1;  // first j with s_end[j] > kb
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_end[mid] > kb) hi = mid;
+    for (uint32_t b = 0; b < total; b += 32) {  // warp-uniform
+        const uint32_t k = b + (uint32_t)lane;
+        int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive area exceeds k
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t im = __shfl_sync(kFull, incl, mid);
+            if (lo < hi) {
+                if (im > k) hi = mid;
                 else lo = mid + 1;
             }
-#pragma unroll
-            for (int j = 0; j < kEmitPer; ++j) {
-                const uint32_t k = kb + j;
-                tile[j] = gid[j] = 0;
-                if (k >= total) continue;
-                while (s_end[lo] <= k) ++lo;  // the next Gaussian with candidates (s_end[255] > k)
-                const uint32_t start = lo ? s_end[lo - 1] : 0u;
-                const uint32_t local = k - start;  // candidate inside Gaussian lo
-                const uint32_t w = s_w[lo];
-                const uint32_t dy = local / w, dx = local - dy * w;
-                const uint32_t tx = s_x0[lo] + dx, ty = s_y0[lo] + dy;
-                const uint32_t area = s_end[lo] - start;
-                const bool hit = area <= 32u ? ((s_mask[lo] >> local) & 1u) != 0u
-                                             : tile_hit(s_u[lo], s_v[lo], s_ca[lo], s_cb[lo], s_cc[lo], s_sx[lo],
-                                                        s_sy[lo], (int)tx, (int)ty, T);
-                bits |= (uint32_t)hit << j;
-                tile[j] = s_tbase[lo] + ty * s_tx[lo] + tx;
-                gid[j] = s_gid[lo];
+        }
+        const uint32_t ofirst = __shfl_sync(kFull, first, lo), oarea = __shfl_sync(kFull, cnt, lo);
+        bool hit = false;
+        uint32_t tile = 0, gid = 0;
+        if (k < total) {  // then the owner's rectangle is not empty
+            const int o = warp * 32 + lo;
+            const uint32_t local = k - ofirst;
+            const uint32_t w = s_w[o];
+            const uint32_t dy = local / w, dx = local - dy * w;
+            const uint32_t tx = s_x0[o] + dx, ty = s_y0[o] + dy;
+            hit = oarea <= 32u ? ((s_mask[o] >> local) & 1u) != 0u
+                               : tile_hit(s_u[o], s_v[o], s_ca[o], s_cb[o], s_cc[o], s_sx[o], s_sy[o], (int)tx,
+                                          (int)ty, T);
+            tile = s_tbase[o] + ty * s_tx[o] + tx;
+            gid = s_gid[o];
+        }
+        const unsigned bal = __ballot_sync(kFull, hit);
+        if (hit) {
+            const unsigned long long pos = out + written + __popc(bal & lt);
+            if (pos < (unsigned long long)capacity) {
+                reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
+                sc.vals[0][pos] = gid;
             }
         }
-        // ordered compaction of this round's hits: exclusive scan of the per-thread hit counts
-        const uint32_t c = __popc(bits);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        __syncthreads();  // the previous round's s_warp reads are done
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        uint32_t before = 0, round = 0;
-#pragma unroll
-        for (int w = 0; w < kProjBlock / 32; ++w) {
-            before += w < warp ? s_warp[w] : 0u;
-            round += s_warp[w];
-        }
-        const unsigned long long pos0 = base + written + before + incl - c;
-#pragma unroll
-        for (int j = 0; j < kEmitPer; ++j) {
-            if ((bits >> j) & 1u) {
-                const unsigned long long pos = pos0 + __popc(bits & ((1u << j) - 1u));
-                if (pos < (unsigned long long)capacity) {
-                    reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile[j];
-                    sc.vals[0][pos] = gid[j];
-                }
-            }
-        }
-        written += round;
+        written += __popc(bal);
     }
 }
 
