@@ -17,7 +17,7 @@
 // the colour behind it with Eq. 7 itself (C_in of the last entry is the background), then applies
 // Eq. 8:  dL/dc = alpha dL/dC_out,  dL/dalpha = <dL/dC_out, c - C_in>,  dL/dC_out = T_i dL/dC.
 // Each thread first sums its strip's nine screen-space gradients; the warp's 32 partial sums are
-// then added by a transpose-reduction (9 shuffles for 8 values; in the paired-pixel kernels two
+// then added by a transpose-reduction (9 shuffles for 8 values; with two pixels per thread two
 // consecutive entries share one 18-value reduction) and scattered with one atomic per value per
 // warp to the canonical index (Eq. 10: grad_{pi(i)} += g_i).  Each warp stops at its own deepest
 // `last`, not the tile's.
@@ -775,6 +775,89 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
             v[1] = m1;
             return contrib;
         };
+        if constexpr (NP > 1) {
+            // four or more pixels per thread: one entry per reduction (pairing the entries
+            // raised the register count and made the batched step 3 % slower)
+            for (int j = jtop - 1; j >= 0; --j) {
+                const uint32_t pos = start + j;
+                const float4 pm = s_xyo[j];
+                const float4 s2 = s_s2[j];
+                const float dx = fx - pm.x;
+                const F2 DX = f2(dx), ADX2 = f2(__fmul_rn(s2.x, __fmul_rn(dx, dx)));
+                const F2 S2Y = f2(s2.y), S2Z = f2(s2.z), O = f2(pm.z), Y = f2(pm.y);
+                // per-lane sums over the strip: dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2,
+                // dL/dalpha G, alpha T dL/dC (rgb)
+                F2 acc[9];
+    #pragma unroll
+                for (int v = 0; v < 9; ++v) acc[v] = f2(0.0f);
+                bool contrib = false;
+    #pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const int k0 = 2 * q, k1 = 2 * q + 1;
+                    const F2 dy = sub2(FY[q], Y);
+                    float2 G, og, a;
+                    pair_alpha(dy, DX, ADX2, S2Y, S2Z, O, G, og, a);
+                    const bool p0 = pos < my_last[k0] && a.x >= kAlphaMin;
+                    const bool p1 = pos < my_last[k1] && a.y >= kAlphaMin;
+                    if (p0 || p1) {
+                        contrib = true;
+                        const float4 c = s_rgb[j];
+                        const float e0 = p0 ? a.x : 0.0f, e1 = p1 ? a.y : 0.0f;
+                        const F2 A = f2(e0, e1);
+                        const float2 om = un(sub2(f2(1.0f), A)), tv = un(T[q]);
+                        const F2 Tb = f2(p0 ? __fdividef(tv.x, om.x) : tv.x,
+                                         p1 ? __fdividef(tv.y, om.y) : tv.y);  // transmittance in front
+                        const F2 r0 = sub2(f2(c.x), B0[q]), r1 = sub2(f2(c.y), B1[q]), r2 = sub2(f2(c.z), B2[q]);
+                        const F2 dLda = mul2(Tb, fma2(r2, g2[q], fma2(r1, g1[q], mul2(r0, g0[q]))));
+                        const F2 wgt = mul2(A, Tb);
+                        acc[6] = fma2(wgt, g0[q], acc[6]);
+                        acc[7] = fma2(wgt, g1[q], acc[7]);
+                        acc[8] = fma2(wgt, g2[q], acc[8]);
+                        B0[q] = fma2(A, r0, B0[q]);
+                        B1[q] = fma2(A, r1, B1[q]);
+                        B2[q] = fma2(A, r2, B2[q]);
+                        T[q] = Tb;
+                        // zero gradient through the 0.99 clamp
+                        const bool q0 = p0 && og.x <= kAlphaMax, q1 = p1 && og.y <= kAlphaMax;
+                        acc[5] = fma2(dLda, f2(q0 ? G.x : 0.0f, q1 ? G.y : 0.0f), acc[5]);
+                        const F2 dpow = mul2(dLda, f2(q0 ? a.x : 0.0f, q1 ? a.y : 0.0f));
+                        const F2 dpx = mul2(dpow, DX), dpy = mul2(dpow, dy);
+                        acc[0] = add2(acc[0], dpx);
+                        acc[1] = add2(acc[1], dpy);
+                        acc[2] = fma2(dpx, DX, acc[2]);
+                        acc[3] = fma2(dpx, dy, acc[3]);
+                        acc[4] = fma2(dpy, dy, acc[4]);
+                    }
+                }
+                if (__any_sync(kFull, contrib)) {
+                    float v[9];
+    #pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const float2 h = un(acc[q]);
+                        v[q] = h.x + h.y;
+                    }
+                    // d power / d mean2D = (a dx + b dy, c dy + b dx) with the conic (a, b, c) of
+                    // the entry, from the strip's sums of dpow dx and dpow dy
+                    const float4 con = s_con[j];
+                    const float m0 = fmaf(con.x, v[0], con.y * v[1]);
+                    const float m1 = fmaf(con.z, v[1], con.y * v[0]);
+                    v[0] = m0;
+                    v[1] = m1;
+                    float s8, s9;
+                    warp_sum9(v, lane, s8, s9);
+                    const uint32_t id = s_id[j];
+                    if ((lane & 3) == 0) {
+                        // d power / d(a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2)
+                        const int q = lane >> 2;
+                        const float f = q == 2 || q == 4 ? -0.5f : (q == 3 ? -1.0f : 1.0f);
+                        atomicAdd(&sc.grad2d[(size_t)q * n + id], f * s8);
+                    }
+                    if (lane == 1) atomicAdd(&sc.grad2d[(size_t)8 * n + id], s9);
+                }
+            }
+            end = start;
+            continue;
+        }
         // entries in pairs: two entries' gradients share one transpose-reduction and one
         // atomic instruction (an entry no lane composited is not added)
         for (int j = jtop - 1; j >= 0; j -= 2) {
