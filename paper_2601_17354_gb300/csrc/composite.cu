@@ -855,28 +855,27 @@ __device__ __forceinline__ void bwd_tile_pairs(const TileJob& J, int64_t n, cons
                     if (lane == 1) atomicAdd(&sc.grad2d[(size_t)8 * n + id], s9);
                 }
             }
-            end = start;
-            continue;
-        }
-        // entries in pairs: two entries' gradients share one transpose-reduction and one
-        // atomic instruction (an entry no lane composited is not added)
-        for (int j = jtop - 1; j >= 0; j -= 2) {
-            float va[9], vb[9];
-            const bool ca = __any_sync(kFull, entry(j, va));
-            const bool cb = j >= 1 && __any_sync(kFull, entry(j - 1, vb));
-            if (ca && cb) {
-                float s;
-                int idx;
-                warp_sum18(va, vb, lane, s, idx);
-                if (idx >= 0) {
-                    const int q = idx >= 9 ? idx - 9 : idx;
-                    const uint32_t id = s_id[idx >= 9 ? j - 1 : j];
-                    atomicAdd(&sc.grad2d[(size_t)q * n + id], grad_factor(q) * s);
+        } else {
+            // entries in pairs: two entries' gradients share one transpose-reduction and one
+            // atomic instruction (an entry no lane composited is not added)
+            for (int j = jtop - 1; j >= 0; j -= 2) {
+                float va[9], vb[9];
+                const bool ca = __any_sync(kFull, entry(j, va));
+                const bool cb = j >= 1 && __any_sync(kFull, entry(j - 1, vb));
+                if (ca && cb) {
+                    float s;
+                    int idx;
+                    warp_sum18(va, vb, lane, s, idx);
+                    if (idx >= 0) {
+                        const int q = idx >= 9 ? idx - 9 : idx;
+                        const uint32_t id = s_id[idx >= 9 ? j - 1 : j];
+                        atomicAdd(&sc.grad2d[(size_t)q * n + id], grad_factor(q) * s);
+                    }
+                } else if (ca) {
+                    scatter9(va, lane, s_id[j], n, sc.grad2d);
+                } else if (cb) {
+                    scatter9(vb, lane, s_id[j - 1], n, sc.grad2d);
                 }
-            } else if (ca) {
-                scatter9(va, lane, s_id[j], n, sc.grad2d);
-            } else if (cb) {
-                scatter9(vb, lane, s_id[j - 1], n, sc.grad2d);
             }
         }
         end = start;
