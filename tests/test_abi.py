@@ -50,3 +50,29 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.pgs_render(None, None, None, None) == _lib.PGS_ERR_INVALID_ARG
     assert L.pgs_status(None, None) == _lib.PGS_ERR_INVALID_ARG
     L.pgs_destroy(None)
+
+
+def declared_arity():
+    """Number of parameters of every function include/pocketgs.h declares."""
+    arity = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            for m in re.finditer(r"\b(pgs_[a-z0-9_]+)\s*\(([^;{)]*)\)\s*;", src):
+                params = " ".join(m.group(2).split())
+                arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_signatures_match_the_header():
+    """The ctypes binding marshals every declared function with as many arguments as the header
+    gives it (a drifted signature would pass garbage through the ABI)."""
+    from paper_2601_17354_gb300 import _lib
+    L = _lib.lib()
+    arity = declared_arity()
+    assert set(arity) == set(declared_functions())
+    wrong = {n: (k, len(getattr(L, n).argtypes or ())) for n, k in arity.items()
+             if getattr(L, n).argtypes is None or len(getattr(L, n).argtypes) != k}
+    assert not wrong, wrong
