@@ -177,6 +177,23 @@ int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max);
 #define PGS_BUF_NCOMP 7
 int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64_t* bytes);
 
+/* Decision trace of the last render (diagnostics and parity tests).  The compositing rules of Eq. 7
+   decide per (pixel, entry) whether the entry is skipped (alpha < 1/255), composited, clamped at
+   alpha = 0.99, or stops the pixel (the transmittance would fall below 1e-4); those integer
+   outcomes are decided in fp32.  For each of npix pixels (x, y pairs, device int32 [npix][2])
+   this walks the pixel's tile list front to back with the forward kernels' own arithmetic and
+   writes, per evaluated entry (list order, at most max_entries recorded per pixel):
+     og   [npix][max_entries] float: o G, the opacity times the Gaussian before the 0.99 clamp;
+     code [npix][max_entries] uint8: 0 skipped, 1 composited, 2 composited clamped, 3 stop
+          (not composited; the walk ends there);
+   and per pixel: count [npix] int32 = entries evaluated (> max_entries: the rest not recorded;
+   -1 for a pixel outside the image), T_final [npix] float, last [npix] uint32 and ncomp [npix]
+   uint32, which equal the render's own T_final, last and composited count of the pixel.
+   All pointers are device memory owned by the caller.  Asynchronous on the context's stream.
+   PGS_ERR_NO_RENDER without a render on this context. */
+int pgs_trace_pixels(pgs_ctx* ctx, const int32_t* pixels, int64_t npix, int32_t max_entries, float* og,
+                     uint8_t* code, int32_t* count, float* T_final, uint32_t* last, uint32_t* ncomp);
+
 /* Per-stage device time accounting.  pgs_profile(ctx, 1) makes every later call record CUDA
    events on the context's stream at its stage boundaries; pgs_stage_times synchronises, writes
    the total milliseconds and the number of timed executions of each stage since the previous

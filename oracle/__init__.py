@@ -5,11 +5,14 @@ package.  The product path (``paper_2601_17354_gb300``) never imports, links or 
 
 The arithmetic lives in ``pgs_oracle.cpp`` (plain C++17, FP64 values, fp32 decisions with a
 prescribed operation order), compiled by :func:`build` with ``-ffp-contract=off`` into
-``oracle/_build/liboracle.so``.  This module only marshals numpy arrays into that library.
+``oracle/_build/liboracle.so``; its per-pixel and per-Gaussian loops run on OpenMP threads
+(:func:`set_threads`), each pixel and each Gaussian computed exactly as in a serial run.  This module only marshals numpy arrays into that library.
 
 Parity status of each function (what pins it, besides agreeing with the GPU path):
   project / render / render_pixels  closed-form single and stacked Gaussians, sum(w)+T = 1,
                                     Eq. 7 back-to-front cross-check
+  render_forced / decisions         its own decisions replayed reproduce render exactly; a
+                                    forced flip is legal only inside the stated error bound
   keys                              brute-force per-tile lists, hand-checked tiny case
   backward / backward_subset        FP64 central finite differences, two derivations agree
   fd_subset                         agrees with the analytic backward on small scenes (and is
@@ -50,8 +53,8 @@ def build(force: bool = False) -> str:
     if fresh and not force:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, *_SRCS]
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-o", tmp, *_SRCS]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +80,10 @@ def lib():
             L = C.CDLL(path)
             P = C.c_void_p
             L.oracle_det_expf.restype = C.c_float
+            L.oracle_decision_bound.restype = C.c_double
+            L.oracle_set_threads.restype = C.c_int
+            L.oracle_set_threads.argtypes = [C.c_int]
+            L.oracle_decision_bound.argtypes = []
             L.oracle_det_expf.argtypes = [C.c_float]
             L.oracle_sh_basis.argtypes = [P, P, P]
             L.oracle_param_count.restype = C.c_int
@@ -86,11 +93,18 @@ def lib():
             L.oracle_keys.argtypes = [P, P, C.c_int, C.c_int64, P, P, P]
             L.oracle_render.argtypes = [P, P, C.c_int, P, P, P, P, P, P]
             L.oracle_render_pixels.argtypes = [P, P, C.c_int, C.c_int64, P, P, P, P, P]
+            L.oracle_render_forced.argtypes = [P, P, C.c_int, C.c_int64, P, P, P] + [P] * 6
+            L.oracle_decisions.argtypes = [P, P, C.c_int, C.c_int64, P, C.c_int64, P, P, P]
+            L.oracle_backward_forced.argtypes = [P, P, C.c_int, P, C.c_int, C.c_int64, P, P, P, P, P]
+            L.oracle_backward_subset_forced.argtypes = [P, P, C.c_int, P, C.c_int64, P, C.c_int64,
+                                                        P, P, P, P, P]
             L.oracle_render_eq7.argtypes = [P, P, C.c_int, P]
             L.oracle_backward.argtypes = [P, P, C.c_int, P, C.c_int, P, P]
             L.oracle_backward_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, P, P]
             L.oracle_chain.argtypes = [P, P, C.c_int, P, P]
             L.oracle_fd_subset.argtypes = [P, P, C.c_int, P, C.c_int64, P, C.c_double, P]
+            L.oracle_fd_subset_forced.argtypes = [P, P, C.c_int, P, C.c_int64, P, C.c_double,
+                                                  C.c_int64, P, P, P, P]
             L.oracle_gaussian_flags.argtypes = [P, P, C.c_int, P]
             L.oracle_l1.argtypes = [C.c_int64, P, P, P, P, P]
             L.oracle_knn.argtypes = [C.c_int64, P, C.c_int, P]
@@ -147,6 +161,18 @@ def det_expf(x) -> np.ndarray:
     L = lib()
     x = np.asarray(x, np.float32).reshape(-1)
     return np.array([L.oracle_det_expf(float(v)) for v in x], np.float32)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (pixel rows, pixels, Gaussians); n <= 0 keeps the
+    current setting.  Returns the count in effect."""
+    return int(lib().oracle_set_threads(int(n)))
+
+
+def decision_bound() -> float:
+    """Relative bound on a compositing kernel's o G against the oracle's decision-side o 2^p
+    (hardware 2^x approximation + fp32 logistic + one rounding)."""
+    return float(lib().oracle_decision_bound())
 
 
 def sh_basis(direction):
@@ -208,6 +234,60 @@ def render_pixels(g, cam, pix_xy, tile: int = 16) -> dict:
     return out
 
 
+class Forced:
+    """Decisions to follow for some pixels: pix [m][2] (x, y) int32, and per pixel the codes of its
+    evaluated list entries (0 skipped, 1 composited, 2 composited clamped at 0.99, 3 stop),
+    concatenated in `codes` (uint8) with pixel k's at codes[off[k]:off[k + 1]]."""
+
+    def __init__(self, pix, off, codes):
+        self.pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+        self.off = np.ascontiguousarray(off, np.int64)
+        self.codes = np.ascontiguousarray(codes, np.uint8)
+        assert self.off.shape == (self.pix.shape[0] + 1,) and self.off[-1] == self.codes.size
+
+    @classmethod
+    def empty(cls):
+        return cls(np.zeros((0, 2), np.int32), np.zeros(1, np.int64), np.zeros(0, np.uint8))
+
+    def __len__(self):
+        return self.pix.shape[0]
+
+    def args(self):
+        b = max(1, self.codes.size)
+        if self.codes.size == 0:
+            self._pad = np.zeros(b, np.uint8)
+            return [len(self), _ptr(self.pix), _ptr(self.off), _ptr(self._pad)]
+        return [len(self), _ptr(self.pix), _ptr(self.off), _ptr(self.codes)]
+
+
+def render_forced(g, cam, forced: Forced, tile: int = 16) -> dict:
+    """Pixels of `forced` composited with its decisions (values FP64): rgb [m][3], T, last, ncomp,
+    flips (codes differing from the oracle's own decisions) and illegal (of those, decisions the
+    oracle did not find within the error bound of their threshold)."""
+    inp = _Inputs(g, cam)
+    m = len(forced)
+    out = dict(rgb=np.zeros((m, 3)), T=np.zeros(m), last=np.zeros(m, np.int32),
+               ncomp=np.zeros(m, np.int32), flips=np.zeros(m, np.int32), illegal=np.zeros(m, np.int32))
+    if m:
+        lib().oracle_render_forced(inp.gp, inp.cp, tile, m, _ptr(forced.pix), _ptr(forced.off),
+                                   _ptr(forced.codes), *[_ptr(out[k]) for k in
+                                                         ("rgb", "T", "last", "ncomp", "flips", "illegal")])
+    return out
+
+
+def decisions(g, cam, pix_xy, max_entries: int, tile: int = 16) -> dict:
+    """The oracle's own decisions entry by entry: og [m][max_entries] (decision-side o 2^p),
+    code [m][max_entries] and count [m] (evaluated entries, -1 beyond max_entries)."""
+    inp = _Inputs(g, cam)
+    pix = np.ascontiguousarray(pix_xy, np.int32).reshape(-1, 2)
+    m = pix.shape[0]
+    out = dict(og=np.zeros((m, max_entries)), code=np.full((m, max_entries), 255, np.uint8),
+               count=np.zeros(m, np.int64))
+    lib().oracle_decisions(inp.gp, inp.cp, tile, m, _ptr(pix), max_entries, _ptr(out["og"]),
+                           _ptr(out["code"]), _ptr(out["count"]))
+    return out
+
+
 def render_eq7(g, cam, tile: int = 16) -> np.ndarray:
     inp = _Inputs(g, cam)
     img = np.zeros((3, cam.height, cam.width))
@@ -223,36 +303,44 @@ def split_grads(flat: np.ndarray, n: int, sh_degree: int) -> dict:
                 sh=flat[11 * n:].reshape(3, K, n))
 
 
-def backward(g, cam, dL_dimage, tile: int = 16, mode: int = 0):
-    """(grad2d [N][9], named parameter gradients) for an upstream gradient [3][H][W]."""
+def backward(g, cam, dL_dimage, tile: int = 16, mode: int = 0, forced: Forced | None = None):
+    """(grad2d [N][9], named parameter gradients) for an upstream gradient [3][H][W]; the pixels of
+    `forced` follow its decisions."""
     inp = _Inputs(g, cam)
     d = np.ascontiguousarray(dL_dimage, np.float64)
     g2 = np.zeros((g.n, 9))
     flat = np.zeros(param_count(g.sh_degree) * g.n)
-    lib().oracle_backward(inp.gp, inp.cp, tile, _ptr(d), mode, _ptr(g2), _ptr(flat))
+    f = forced if forced is not None else Forced.empty()
+    lib().oracle_backward_forced(inp.gp, inp.cp, tile, _ptr(d), mode, *f.args(), _ptr(g2), _ptr(flat))
     return g2, split_grads(flat, g.n, g.sh_degree)
 
 
-def backward_subset(g, cam, dL_dimage, sel, tile: int = 16):
-    """(grad2d [S][9], grads [S][11 + 3K]) for the selected canonical indices."""
+def backward_subset(g, cam, dL_dimage, sel, tile: int = 16, forced: Forced | None = None):
+    """(grad2d [S][9], grads [S][11 + 3K]) for the selected canonical indices; the pixels of
+    `forced` follow its decisions."""
     inp = _Inputs(g, cam)
     d = np.ascontiguousarray(dL_dimage, np.float64)
     sel = np.ascontiguousarray(sel, np.int64)
     g2 = np.zeros((len(sel), 9))
     gp = np.zeros((len(sel), param_count(g.sh_degree)))
-    lib().oracle_backward_subset(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), _ptr(g2),
-                                 _ptr(gp))
+    f = forced if forced is not None else Forced.empty()
+    lib().oracle_backward_subset_forced(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), *f.args(),
+                                        _ptr(g2), _ptr(gp))
     return g2, gp
 
 
-def fd_subset(g, cam, dL_dimage, sel, h_rel: float = 2.0 ** -12, tile: int = 16):
+def fd_subset(g, cam, dL_dimage, sel, h_rel: float = 2.0 ** -12, tile: int = 16,
+              forced: Forced | None = None):
     """FP64 central differences [S][11 + 3K] of sum(dL_dimage * image) for the selected
-    Gaussians; NaN where a perturbation changed a decision."""
+    Gaussians; NaN where a perturbation changed a decision.  The pixels of `forced` keep its
+    decisions."""
     inp = _Inputs(g, cam)
     d = np.ascontiguousarray(dL_dimage, np.float64)
     sel = np.ascontiguousarray(sel, np.int64)
     out = np.zeros((len(sel), param_count(g.sh_degree)))
-    lib().oracle_fd_subset(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), h_rel, _ptr(out))
+    f = forced if forced is not None else Forced.empty()
+    lib().oracle_fd_subset_forced(inp.gp, inp.cp, tile, _ptr(d), len(sel), _ptr(sel), h_rel, *f.args(),
+                                  _ptr(out))
     return out
 
 

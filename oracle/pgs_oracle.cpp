@@ -39,6 +39,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <omp.h>
+#include <unordered_map>
 #include <vector>
 
 extern "C" {
@@ -390,6 +392,7 @@ struct Scene {
         TY = (cam.height + tile - 1) / tile;
         dec.resize(G.n);
         val.resize(G.n);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < G.n; ++i) {
             dec[i] = decide(G, cam, tile, i);
             if (dec[i].visible) val[i] = evaluate(G, cam, i);
@@ -403,8 +406,9 @@ struct Scene {
                 for (int tx = dec[i].x0; tx < dec[i].x1; ++tx)
                     if (tile_hit(dec[i], tx, ty, tile)) lists[(size_t)ty * TX + tx].push_back(i);
         }
-        for (auto& L : lists)
-            std::sort(L.begin(), L.end(), [&](int64_t a, int64_t b) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t t = 0; t < (int64_t)lists.size(); ++t)
+            std::sort(lists[t].begin(), lists[t].end(), [&](int64_t a, int64_t b) {
                 const uint32_t da = fbits(dec[a].zc), db = fbits(dec[b].zc);
                 return da != db ? da < db : a < b;
             });
@@ -414,11 +418,33 @@ struct Scene {
     }
 };
 
-// decision-margin flags for a pixel (set when an fp32 evaluation could legitimately decide
-// differently from this FP64 one)
+// Compositing decisions.  Whether an entry is skipped (alpha < 1/255), clamped (o G > 0.99) or
+// stops the pixel (T (1 - alpha) < 1e-4) is an integer outcome decided in floating point, so the
+// oracle takes it in the kernel's precision, fp32, from the fp32 quantities of the decision path
+// (screen position u, v and conic of decide()), in the compositing kernels' evaluation order:
+//   dx = fl(x + 1/2 - u), dy = fl(y + 1/2 - v);
+//   exponent base 2: A = fl(-log2(e)/2 a), B = fl(-log2(e) b), C = fl(-log2(e)/2 c) (log2(e) in
+//   fp32), p = fma(C, fl(dy dy), fma(B, fl(dx dy), fl(A fl(dx dx))));
+//   og = o 2^p,  alpha = min(0.99f, og),  skip alpha < fl(1/255),  T' = fl(T fl(1 - alpha)),
+//   stop when T' < 1e-4f.
+// Two steps of the kernel are not reproducible bit for bit: its 2^p is a hardware approximation
+// and its opacity goes through the library exp.  The oracle evaluates og from the exact 2^p and
+// the FP64 opacity and carries the kernel's possible deviation as a bound: |og_k / og - 1| <=
+// EPS_OG, and a running relative bound on its fp32 transmittance chain.  A decision whose
+// threshold lies inside that bound is ambiguous: the pixel is flagged (FLAG_*), and a test can
+// replay the kernel's own decisions for it (composite with forced decisions), each forced
+// decision that differs from the oracle's being checked to be an ambiguous one.
+// Values (the composited alpha, colour and transmittance) stay FP64, from the value path.
 enum { FLAG_SKIP = 1, FLAG_STOP = 2, FLAG_CLAMP = 4 };
-constexpr double SKIP_MARGIN = 1e-4, STOP_MARGIN = 1e-3, CLAMP_MARGIN = 1e-4;
-constexpr double ALPHA_MIN = 1.0 / 255.0, ALPHA_MAX = 0.99, T_MIN = 1e-4;
+constexpr double ALPHA_MIN = (double)(1.0f / 255.0f), ALPHA_MAX = (double)0.99f, T_MIN = (double)1e-4f;
+constexpr double U32 = 0x1p-24;                  // unit roundoff of fp32
+constexpr double EPS_EX2 = 0x1p-21;              // hardware 2^x approximation, relative
+constexpr double EPS_OPACITY = 4.0 * 0x1p-23;    // fp32 logistic 1 / (1 + exp(-x)) via the library exp
+constexpr double EPS_OG = EPS_EX2 + EPS_OPACITY + U32;  // the kernel's o G against o 2^p
+constexpr float LOG2E_F = 1.4426950408889634f;
+
+// decision codes of one evaluated list entry (as a kernel trace reports them)
+enum { CODE_SKIP = 0, CODE_COMPOSITE = 1, CODE_CLAMPED = 2, CODE_STOP = 3 };
 
 struct Entry {
     int64_t g;
@@ -434,39 +460,117 @@ struct PixelResult {
     uint8_t flag;
     int64_t evals;   // list entries evaluated (up to and including the stopping one)
     int32_t ncomp;   // entries composited
+    int32_t nclamp;  // composited entries clamped at 0.99
+    int32_t flips;   // forced decisions that differ from the oracle's own
+    int32_t illegal; // ... of which the oracle's own decision was not ambiguous
     std::vector<Entry> used;
 };
 
-PixelResult composite(const Scene& sc, int px, int py, bool keep) {
+// The fp32 exponent p (base 2) of Gaussian g at pixel (px, py), in the kernels' order.
+inline float decision_exponent(const Decision& d, int px, int py) {
+    const float A = (-0.5f * LOG2E_F) * d.ca, B = -LOG2E_F * d.cb, Cc = (-0.5f * LOG2E_F) * d.cc;
+    const float dx = ((float)px + 0.5f) - d.u, dy = ((float)py + 0.5f) - d.v;
+    const float adx2 = A * (dx * dx);
+    return std::fma(Cc, dy * dy, std::fma(B, dx * dy, adx2));
+}
+
+// Composite pixel (px, py) front to back.  keep: record the composited entries (for the
+// backward).  forced / nforced: the decision codes of the first nforced evaluated entries
+// (CODE_*), followed instead of the oracle's own decisions; nullptr = the oracle decides.
+// dtrace (optional): receives (decision-side o 2^p, the code taken) of every evaluated entry.
+PixelResult composite(const Scene& sc, int px, int py, bool keep, const uint8_t* forced = nullptr,
+                      int64_t nforced = 0, std::vector<std::pair<double, uint8_t>>* dtrace = nullptr) {
     PixelResult r{};
     r.C[0] = r.C[1] = r.C[2] = 0.0;
-    double T = 1.0;
+    double T = 1.0;      // FP64 value transmittance
+    float T32 = 1.0f;    // fp32 decision transmittance
+    double dT = 0.0;     // relative bound on |T32 - the kernel's fp32 transmittance| / T32
     const auto& L = sc.list_of(px, py);
     const double cx = px + 0.5, cy = py + 0.5;
     for (size_t k = 0; k < L.size(); ++k) {
         const Value& q = sc.val[L[k]];
+        const Decision& d = sc.dec[L[k]];
         r.evals++;
+        // decision side (fp32 exponent, exact 2^p and FP64 opacity, bounded deviation)
+        const double og_d = q.opacity * std::exp2((double)decision_exponent(d, px, py));
+        const double a_d = std::min(ALPHA_MAX, og_d);
+        const bool skip_o = a_d < ALPHA_MIN;
+        const bool skip_amb = std::fabs(og_d - ALPHA_MIN) <= EPS_OG * og_d;
+        const bool clamp_o = og_d > ALPHA_MAX;
+        const bool clamp_amb = std::fabs(og_d - ALPHA_MAX) <= EPS_OG * og_d;
+        // the kernel's alpha differs from a32 by at most (EPS_OG + U32) alpha (0 when both clamp)
+        const float a32 = (float)a_d;
+        const float Tn32 = T32 * (1.0f - a32);
+        const double e_a = (clamp_o && !clamp_amb) ? 0.0 : (EPS_OG + U32) * a_d / (1.0 - a_d);
+        const double dTn = (1.0 + dT) * (1.0 + e_a) * (1.0 + 4.0 * U32) - 1.0;
+        const bool stop_o = Tn32 < (float)T_MIN;
+        const bool stop_amb = std::fabs((double)Tn32 - T_MIN) <= dTn * (double)Tn32;
+        if (skip_amb) r.flag |= FLAG_SKIP;
+        if (!skip_o && clamp_amb) r.flag |= FLAG_CLAMP;
+        if (!skip_o && stop_amb) r.flag |= FLAG_STOP;
+        const int own = skip_o ? CODE_SKIP : (stop_o ? CODE_STOP : (clamp_o ? CODE_CLAMPED : CODE_COMPOSITE));
+        int code = own;
+        if (forced) {
+            if ((int64_t)k >= nforced) {  // the kernel ended here without a stop: only if the list did
+                r.illegal++;
+                break;
+            }
+            code = forced[k];
+            if (code != own) {
+                r.flips++;
+                const bool skip_f = code == CODE_SKIP, stop_f = code == CODE_STOP, clamp_f = code == CODE_CLAMPED;
+                bool ok = skip_f == skip_o || skip_amb;
+                if (!skip_f) ok = ok && (stop_f == stop_o || stop_amb);
+                if (!skip_f && !stop_f) ok = ok && (clamp_f == clamp_o || clamp_amb);
+                if (!ok) r.illegal++;
+            }
+        }
+        if (dtrace) dtrace->emplace_back(og_d, (uint8_t)code);
+        if (code == CODE_SKIP) continue;
+        if (code == CODE_STOP) break;
+        // composited: FP64 value of the entry on the decided branch
         const double dx = cx - q.u, dy = cy - q.v;
         const double power = -0.5 * (q.conic[0] * dx * dx + q.conic[2] * dy * dy) - q.conic[1] * dx * dy;
         const double Gv = std::exp(power);
-        const double og = q.opacity * Gv;
-        const double alpha = std::min(ALPHA_MAX, og);
-        if (std::fabs(alpha - ALPHA_MIN) < SKIP_MARGIN * ALPHA_MIN) r.flag |= FLAG_SKIP;
-        if (alpha < ALPHA_MIN) continue;
-        if (std::fabs(og - ALPHA_MAX) < CLAMP_MARGIN * ALPHA_MAX) r.flag |= FLAG_CLAMP;
-        const double Tn = T * (1.0 - alpha);
-        if (std::fabs(Tn - T_MIN) < STOP_MARGIN * T_MIN) r.flag |= FLAG_STOP;
-        if (Tn < T_MIN) break;
+        const bool clamped = code == CODE_CLAMPED;
+        const double alpha = clamped ? 0.99 : q.opacity * Gv;  // the clamp's value is 0.99 itself
         for (int c = 0; c < 3; ++c) r.C[c] += q.rgb[c] * alpha * T;
-        if (keep) r.used.push_back(Entry{L[k], alpha, Gv, T, dx, dy, og > ALPHA_MAX});
+        if (keep) r.used.push_back(Entry{L[k], alpha, Gv, T, dx, dy, clamped});
         r.ncomp++;
-        T = Tn;
+        r.nclamp += clamped;
+        T *= 1.0 - alpha;
+        T32 = clamped ? T32 * (1.0f - 0.99f) : Tn32;
+        dT = dTn;
         r.last = (int32_t)(k + 1);
     }
+    if (forced && r.evals < nforced) r.illegal++;  // the kernel evaluated entries the list lacks
     for (int c = 0; c < 3; ++c) r.C[c] += T * (double)sc.cam.bg[c];
     r.T = T;
     return r;
 }
+
+// What a perturbation must leave unchanged for a pixel's value to be a smooth function of it.
+inline int64_t signature(const PixelResult& r) {
+    return ((int64_t)r.last << 40) ^ ((int64_t)r.ncomp << 20) ^ ((int64_t)r.nclamp << 52) ^ r.evals;
+}
+
+// Forced decisions of some pixels (a kernel's own decisions for them): pixel (x, y) -> its codes.
+struct Forced {
+    std::unordered_map<int64_t, std::pair<const uint8_t*, int64_t>> by_pixel;
+    int W = 0;
+    Forced() = default;
+    Forced(int width, int64_t npix, const int32_t* pix, const int64_t* off, const uint8_t* codes) : W(width) {
+        for (int64_t k = 0; k < npix; ++k)
+            by_pixel[(int64_t)pix[2 * k + 1] * W + pix[2 * k]] = {codes + off[k], off[k + 1] - off[k]};
+    }
+    PixelResult composite_at(const Scene& sc, int px, int py, bool keep) const {
+        if (!by_pixel.empty()) {
+            const auto it = by_pixel.find((int64_t)py * W + px);
+            if (it != by_pixel.end()) return composite(sc, px, py, keep, it->second.first, it->second.second);
+        }
+        return composite(sc, px, py, keep);
+    }
+};
 
 // Per-Gaussian screen-space gradient: du, dv, da, db, dc (conic), d opacity, d r, d g, d b.
 struct G2 {
@@ -675,6 +779,16 @@ extern "C" {
 
 float oracle_det_expf(float x) { return det_expf(x); }
 
+// Threads of the parallel loops (pixel rows, pixels, Gaussians); n <= 0 leaves the default (all
+// cores).  Returns the count now in effect.
+int oracle_set_threads(int n) {
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
+
+// The bound EPS_OG on the kernel's o G relative to the oracle's decision-side o 2^p.
+double oracle_decision_bound(void) { return EPS_OG; }
+
 void oracle_sh_basis(const double* dir, double* out_y, double* out_dy) {
     double Y[16], dY[16][3];
     sh_basis(dir, Y, dY);
@@ -772,6 +886,7 @@ void oracle_render(const ogauss_t* G, const ocam_t* cam, int tile, double* image
                    int32_t* last, uint8_t* flag, int64_t* evals, int32_t* ncomp) {
     Scene sc(*G, *cam, tile);
     const int W = cam->width, H = cam->height;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
             const PixelResult r = composite(sc, px, py, false);
@@ -791,6 +906,7 @@ void oracle_render_pixels(const ogauss_t* G, const ocam_t* cam, int tile, int64_
                           const int32_t* pix, double* rgb, double* T_final, int32_t* last,
                           uint8_t* flag) {
     Scene sc(*G, *cam, tile);
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < npix; ++k) {
         const PixelResult r = composite(sc, pix[2 * k], pix[2 * k + 1], false);
         if (rgb)
@@ -798,6 +914,48 @@ void oracle_render_pixels(const ogauss_t* G, const ocam_t* cam, int tile, int64_
         if (T_final) T_final[k] = r.T;
         if (last) last[k] = r.last;
         if (flag) flag[k] = r.flag;
+    }
+}
+
+// Render a list of pixels (x, y pairs) following given decisions: pixel k's evaluated entries take
+// the codes codes[off[k] .. off[k + 1]) (0 skipped, 1 composited, 2 composited clamped at 0.99,
+// 3 stop), values stay FP64.  rgb [npix][3], T [npix], last [npix], ncomp [npix]; flips [npix]
+// counts the codes that differ from the oracle's own decisions and illegal [npix] those of them
+// whose own decision was not within the error bound of its threshold (or codes that end before
+// the list without a stop, or run past it).
+void oracle_render_forced(const ogauss_t* G, const ocam_t* cam, int tile, int64_t npix,
+                          const int32_t* pix, const int64_t* off, const uint8_t* codes, double* rgb,
+                          double* T_final, int32_t* last, int32_t* ncomp, int32_t* flips, int32_t* illegal) {
+    Scene sc(*G, *cam, tile);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < npix; ++k) {
+        const PixelResult r = composite(sc, pix[2 * k], pix[2 * k + 1], false, codes + off[k], off[k + 1] - off[k]);
+        for (int c = 0; c < 3; ++c) rgb[3 * k + c] = r.C[c];
+        T_final[k] = r.T;
+        last[k] = r.last;
+        ncomp[k] = r.ncomp;
+        flips[k] = r.flips;
+        illegal[k] = r.illegal;
+    }
+}
+
+// The oracle's own decisions for a list of pixels: for each evaluated entry (at most max_entries
+// per pixel) its decision-side o 2^p (FP64 opacity, exact 2^p of the fp32 exponent) into
+// og [npix][max_entries] and its code (as in oracle_render_forced) into code [npix][max_entries];
+// count [npix] = entries evaluated (-1 when more than max_entries).
+void oracle_decisions(const ogauss_t* G, const ocam_t* cam, int tile, int64_t npix, const int32_t* pix,
+                      int64_t max_entries, double* og, uint8_t* code, int64_t* count) {
+    Scene sc(*G, *cam, tile);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < npix; ++k) {
+        const int px = pix[2 * k], py = pix[2 * k + 1];
+        std::vector<std::pair<double, uint8_t>> dt;
+        const PixelResult r = composite(sc, px, py, false, nullptr, 0, &dt);
+        count[k] = r.evals <= max_entries ? r.evals : -1;
+        for (int64_t e = 0; e < (int64_t)dt.size() && e < max_entries; ++e) {
+            og[k * max_entries + e] = dt[e].first;
+            code[k * max_entries + e] = dt[e].second;
+        }
     }
 }
 
@@ -820,35 +978,63 @@ void oracle_render_eq7(const ogauss_t* G, const ocam_t* cam, int tile, double* i
         }
 }
 
+
 // Backward of the whole image for an upstream gradient dL/dimage [3][H][W].
 // grad2d [N][9] (du, dv, d conic a, b, c, d opacity, d rgb) and grads in the planar parameter
 // layout (means [3][N], log_scales [3][N], quats [4][N], logits [N], sh [3][K][N]); both are
 // overwritten.  mode 0 / 1 select the two derivations of dL/d(alpha, c).
-void oracle_backward(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
-                     int mode, double* grad2d, double* grads) {
+// Pixels listed in (nf, fpix, foff, fcodes) follow those decisions (as in oracle_render_forced).
+void oracle_backward_forced(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
+                            int mode, int64_t nf, const int32_t* fpix, const int64_t* foff,
+                            const uint8_t* fcodes, double* grad2d, double* grads) {
     Scene sc(*G, *cam, tile);
+    const Forced F(cam->width, nf, fpix, foff, fcodes);
     const int W = cam->width, H = cam->height;
+    // pixel rows split into one contiguous band per thread; each band sums into its own copy of the
+    // screen-space gradients, and the copies are added in band order
+    const int nt = omp_get_max_threads();
+    std::vector<std::vector<G2>> part((size_t)nt);
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = omp_get_thread_num(), nth = omp_get_num_threads();
+        std::vector<G2>& g2t = part[(size_t)t];
+        g2t.resize((size_t)G->n);
+        for (auto& e : g2t) std::fill(e.v, e.v + 9, 0.0);
+        const int y0 = (int)((int64_t)H * t / nth), y1 = (int)((int64_t)H * (t + 1) / nth);
+        for (int py = y0; py < y1; ++py)
+            for (int px = 0; px < W; ++px) {
+                const size_t p = (size_t)py * W + px;
+                const double dLdC[3] = {dL_dimage[p], dL_dimage[(size_t)W * H + p],
+                                        dL_dimage[2 * (size_t)W * H + p]};
+                const PixelResult r = F.composite_at(sc, px, py, true);
+                pixel_backward(sc, r, px, py, dLdC, mode, g2t);
+            }
+    }
     std::vector<G2> g2((size_t)G->n);
     for (auto& e : g2) std::fill(e.v, e.v + 9, 0.0);
-    for (int py = 0; py < H; ++py)
-        for (int px = 0; px < W; ++px) {
-            const size_t p = (size_t)py * W + px;
-            const double dLdC[3] = {dL_dimage[p], dL_dimage[(size_t)W * H + p],
-                                    dL_dimage[2 * (size_t)W * H + p]};
-            const PixelResult r = composite(sc, px, py, true);
-            pixel_backward(sc, r, px, py, dLdC, mode, g2);
-        }
+    for (const auto& g2t : part)
+        for (size_t i = 0; i < g2t.size(); ++i)
+            for (int k = 0; k < 9; ++k) g2[i].v[k] += g2t[i].v[k];
     const int PC = param_count(G->sh_degree);
     if (grads) std::fill(grads, grads + (size_t)PC * G->n, 0.0);
-    std::vector<double> tmp(PC);
-    for (int64_t i = 0; i < G->n; ++i) {
-        if (grad2d)
-            for (int k = 0; k < 9; ++k) grad2d[9 * i + k] = g2[i].v[k];
-        if (!grads || !sc.dec[i].visible) continue;
-        std::fill(tmp.begin(), tmp.end(), 0.0);
-        chain_to_params(sc, i, g2[i], tmp.data());
-        scatter_planar(*G, i, tmp.data(), grads);
+#pragma omp parallel
+    {
+        std::vector<double> tmp(PC);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < G->n; ++i) {
+            if (grad2d)
+                for (int k = 0; k < 9; ++k) grad2d[9 * i + k] = g2[i].v[k];
+            if (!grads || !sc.dec[i].visible) continue;
+            std::fill(tmp.begin(), tmp.end(), 0.0);
+            chain_to_params(sc, i, g2[i], tmp.data());
+            scatter_planar(*G, i, tmp.data(), grads);
+        }
     }
+}
+
+void oracle_backward(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
+                     int mode, double* grad2d, double* grads) {
+    oracle_backward_forced(G, cam, tile, dL_dimage, mode, 0, nullptr, nullptr, nullptr, grad2d, grads);
 }
 
 // Parameter gradients of selected Gaussians only, for images too large to differentiate whole:
@@ -856,12 +1042,16 @@ void oracle_backward(const ogauss_t* G, const ocam_t* cam, int tile, const doubl
 // derivative (mode 0) of that pixel with respect to the selected Gaussian is accumulated.
 // grad2d [nsel][9]; grads [nsel][P] with P = 11 + 3K in the per-Gaussian layout
 // (mean 3, log-scale 3, quat 4, logit 1, sh [3][K]).
-void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
-                            const double* dL_dimage, int64_t nsel, const int64_t* sel,
-                            double* grad2d, double* grads) {
+// Pixels listed in (nf, fpix, foff, fcodes) follow those decisions (as in oracle_render_forced).
+void oracle_backward_subset_forced(const ogauss_t* G, const ocam_t* cam, int tile,
+                                   const double* dL_dimage, int64_t nsel, const int64_t* sel, int64_t nf,
+                                   const int32_t* fpix, const int64_t* foff, const uint8_t* fcodes,
+                                   double* grad2d, double* grads) {
     Scene sc(*G, *cam, tile);
+    const Forced F(cam->width, nf, fpix, foff, fcodes);
     const int W = cam->width, H = cam->height;
     const int PC = param_count(G->sh_degree);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int64_t s = 0; s < nsel; ++s) {
         const int64_t gi = sel[s];
         std::vector<G2> one(1);
@@ -873,7 +1063,7 @@ void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
                     const size_t p = (size_t)py * W + px;
                     const double dLdC[3] = {dL_dimage[p], dL_dimage[(size_t)W * H + p],
                                             dL_dimage[2 * (size_t)W * H + p]};
-                    const PixelResult r = composite(sc, px, py, true);
+                    const PixelResult r = F.composite_at(sc, px, py, true);
                     pixel_backward(sc, r, px, py, dLdC, 0, one, &gi);
                 }
         }
@@ -886,6 +1076,12 @@ void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
     }
 }
 
+void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
+                            const double* dL_dimage, int64_t nsel, const int64_t* sel,
+                            double* grad2d, double* grads) {
+    oracle_backward_subset_forced(G, cam, tile, dL_dimage, nsel, sel, 0, nullptr, nullptr, nullptr, grad2d, grads);
+}
+
 // FP64 central finite differences of L = sum_p <w_p, C_p> (w = dL_dimage [3][H][W]) with respect
 // to every parameter of the selected Gaussians.  Each perturbed evaluation changes one parameter
 // of one Gaussian by +-h (h = h_rel * max(1, |theta|), applied to the fp32 parameter), recomputes
@@ -893,9 +1089,12 @@ void oracle_backward_subset(const ogauss_t* G, const ocam_t* cam, int tile,
 // depends on it).  A coordinate whose perturbation changes a decision - the rectangle, the depth
 // order inside a tile, or any pixel's (last, composited count, evaluated count) - is reported as
 // NaN.  out [nsel][11 + 3K] in the per-Gaussian layout of oracle_backward_subset.
-void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
-                      int64_t nsel, const int64_t* sel, double h_rel, double* out) {
+// Pixels listed in (nf, fpix, foff, fcodes) keep those decisions in every evaluation.
+void oracle_fd_subset_forced(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
+                             int64_t nsel, const int64_t* sel, double h_rel, int64_t nf, const int32_t* fpix,
+                             const int64_t* foff, const uint8_t* fcodes, double* out) {
     Scene sc(*G, *cam, tile);
+    const Forced F(cam->width, nf, fpix, foff, fcodes);
     const int W = cam->width, H = cam->height;
     const int K = (G->sh_degree + 1) * (G->sh_degree + 1);
     const int PC = param_count(G->sh_degree);
@@ -933,8 +1132,8 @@ void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const doub
                 for (int px = d0.x0 * tile; px < std::min(W, d0.x1 * tile); ++px) pix.emplace_back(px, py);
         std::vector<int64_t> sig0;
         for (auto& pp : pix) {
-            const PixelResult r = composite(sc, pp.first, pp.second, false);
-            sig0.push_back(((int64_t)r.last << 40) ^ ((int64_t)r.ncomp << 20) ^ r.evals);
+            const PixelResult r = F.composite_at(sc, pp.first, pp.second, false);
+            sig0.push_back(signature(r));
         }
         auto loss_with = [&](const float* q, bool& ok) {
             ogauss_t g1 = one(q);
@@ -963,8 +1162,8 @@ void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const doub
             double L = 0.0;
             for (size_t k = 0; k < pix.size() && ok; ++k) {
                 const int px = pix[k].first, py = pix[k].second;
-                const PixelResult r = composite(sc, px, py, false);
-                if ((((int64_t)r.last << 40) ^ ((int64_t)r.ncomp << 20) ^ r.evals) != sig0[k]) ok = false;
+                const PixelResult r = F.composite_at(sc, px, py, false);
+                if (signature(r) != sig0[k] || r.illegal) ok = false;
                 const size_t p = (size_t)py * W + px;
                 for (int c = 0; c < 3; ++c) L += dL_dimage[(size_t)c * W * H + p] * r.C[c];
             }
@@ -991,6 +1190,11 @@ void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const doub
             o = (okp && okm) ? (Lp - Lm) / ((double)qp[k] - (double)qm[k]) : std::nan("");
         }
     }
+}
+
+void oracle_fd_subset(const ogauss_t* G, const ocam_t* cam, int tile, const double* dL_dimage,
+                      int64_t nsel, const int64_t* sel, double h_rel, double* out) {
+    oracle_fd_subset_forced(G, cam, tile, dL_dimage, nsel, sel, h_rel, 0, nullptr, nullptr, nullptr, out);
 }
 
 // Chain given screen-space gradients grad2d [N][9] to parameters (planar layout, overwritten).

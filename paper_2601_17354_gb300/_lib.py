@@ -55,7 +55,8 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_batch_steps", "pgs_batch_time_render", "pgs_set_replay_cache", "pgs_loss_dssim",
             "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times",
             "pgs_mvs_create", "pgs_mvs_destroy", "pgs_mvs_depth_range", "pgs_mvs_select_reference",
-            "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse", "pgs_mvs_stage_times"]
+            "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse", "pgs_mvs_stage_times",
+            "pgs_trace_pixels"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -127,6 +128,8 @@ def lib():
             L.pgs_status.restype = I
             L.pgs_read_buffer.argtypes = [P, I, P, I64, C.POINTER(I64)]
             L.pgs_read_buffer.restype = I
+            L.pgs_trace_pixels.argtypes = [P, P, I64, C.c_int32, P, P, P, P, P, P]
+            L.pgs_trace_pixels.restype = I
             L.pgs_profile.argtypes = [P, I]
             L.pgs_profile.restype = I
             L.pgs_stage_times.argtypes = [P, P, P]

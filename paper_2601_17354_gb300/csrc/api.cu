@@ -473,6 +473,17 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
     return PGS_OK;
 }
 
+int pgs_trace_pixels(pgs_ctx* ctx, const int32_t* pixels, int64_t npix, int32_t max_entries, float* og,
+                     uint8_t* code, int32_t* count, float* T_final, uint32_t* last, uint32_t* ncomp) {
+    if (!ctx || npix < 0 || max_entries < 0 || (npix > 0 && (!pixels || !count || !T_final || !last || !ncomp)) ||
+        (max_entries > 0 && npix > 0 && (!og || !code)))
+        return PGS_ERR_INVALID_ARG;
+    if (!ctx->has_render) return PGS_ERR_NO_RENDER;
+    ctx->launches += launch_trace_pixels(ctx->cam, ctx->TX, ctx->tile, ctx->buf, ctx->n, ctx->sc, pixels, npix,
+                                         max_entries, og, code, count, T_final, last, ncomp, ctx->stream);
+    return cuda_err(cudaGetLastError());
+}
+
 int pgs_profile(pgs_ctx* ctx, int enable) {
     if (!ctx) return PGS_ERR_INVALID_ARG;
     ctx->profiling = enable != 0;

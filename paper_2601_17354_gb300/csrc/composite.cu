@@ -1029,6 +1029,66 @@ k_composite_batch(const RenderDesc* __restrict__ renders, int R, int64_t total_t
     }
 }
 
+// Decision trace of listed pixels (one thread per pixel): walk the pixel's tile list front to back
+// with the forward kernels' own evaluation (entry_alpha, the same staging of the conic, dx, dy,
+// T (1 - alpha)), and record per evaluated entry o G before the clamp and the decision taken:
+// 0 skipped (alpha < 1/255), 1 composited, 2 composited clamped at 0.99, 3 stop (T (1 - alpha)
+// < 1e-4; the walk ends there).  count = entries evaluated (recorded up to max_entries);
+// T_out / last_out / ncomp_out = the fp32 transmittance, 1 + position of the last composited entry
+// and the composited count, which equal the forward's T_final, last and ncomp.  A pixel outside
+// the image gets count -1.
+__global__ void k_trace_pixels(int W, int H, int TX, int T, int64_t n, const uint32_t* __restrict__ vals,
+                               Scratch sc, const int32_t* __restrict__ pix, int64_t npix, int max_entries,
+                               float* __restrict__ og_out, uint8_t* __restrict__ code_out,
+                               int32_t* __restrict__ count_out, float* __restrict__ T_out,
+                               uint32_t* __restrict__ last_out, uint32_t* __restrict__ ncomp_out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix) return;
+    const int px = pix[2 * k], py = pix[2 * k + 1];
+    if (px < 0 || py < 0 || px >= W || py >= H) {
+        count_out[k] = -1;
+        return;
+    }
+    const uint2 range = sc.ranges[(py / T) * TX + px / T];
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    float Tr = 1.0f;
+    uint32_t last = 0, ncomp = 0;
+    int32_t count = 0;
+    for (uint32_t idx = range.x; idx < range.y; ++idx) {
+        const uint32_t id = checked_id(vals[idx], n, sc.status);
+        const float4 p = sc.xyo[id];
+        const float4 s2 = scaled_conic(sc.conic[id]);
+        const float dx = fx - p.x;
+        const float adx2 = __fmul_rn(s2.x, __fmul_rn(dx, dx));
+        float G, og;
+        const float alpha = entry_alpha(dx, fy - p.y, adx2, s2, p.z, G, og);
+        uint8_t code = 0;
+        bool stop = false;
+        if (alpha >= kAlphaMin) {
+            const float Tn = Tr * (1.0f - alpha);
+            if (Tn < kTMin) {
+                code = 3;
+                stop = true;
+            } else {
+                code = og > kAlphaMax ? 2 : 1;
+                Tr = Tn;
+                last = idx - range.x + 1;
+                ++ncomp;
+            }
+        }
+        if (count < max_entries) {
+            og_out[k * max_entries + count] = og;
+            code_out[k * max_entries + count] = code;
+        }
+        ++count;
+        if (stop) break;
+    }
+    count_out[k] = count;
+    T_out[k] = Tr;
+    last_out[k] = last;
+    ncomp_out[k] = ncomp;
+}
+
 }  // namespace
 
 // pixels per thread and staging depth (64, 128, 256 entries) of the compositing kernels; default
@@ -1142,6 +1202,18 @@ int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles
     PGS_VARIANTS(X)
 #undef X
     return 0;
+}
+
+
+int launch_trace_pixels(const pgs_camera& cam, int TX, int T, int buf, int64_t n, const Scratch& sc,
+                        const int32_t* pix, int64_t npix, int max_entries, float* og, uint8_t* code,
+                        int32_t* count, float* T_out, uint32_t* last, uint32_t* ncomp, cudaStream_t s) {
+    if (npix <= 0) return 0;
+    const int threads = 128;
+    k_trace_pixels<<<(unsigned)((npix + threads - 1) / threads), threads, 0, s>>>(
+        cam.width, cam.height, TX, T, n, sc.vals[buf], sc, pix, npix, max_entries, og, code, count, T_out, last,
+        ncomp);
+    return 1;
 }
 
 }  // namespace pgs

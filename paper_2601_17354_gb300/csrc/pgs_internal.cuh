@@ -209,6 +209,11 @@ int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, 
 int launch_composite_replay(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                             const Scratch& sc, float* image, const float* dL_dimage, float4* rec,
                             uint32_t* count, int K, bool backward, cudaStream_t s);
+// Decision trace of listed pixels (x, y pairs) of the last render: per evaluated entry o G and the
+// decision code, and per pixel the count, the fp32 transmittance, last and composited count.
+int launch_trace_pixels(const pgs_camera& cam, int TX, int T, int buf, int64_t n, const Scratch& sc,
+                        const int32_t* pix, int64_t npix, int max_entries, float* og, uint8_t* code,
+                        int32_t* count, float* T_out, uint32_t* last, uint32_t* ncomp, cudaStream_t s);
 // Batched compositing over every tile of every render in one persistent launch; `work` is a
 // zeroed device counter.
 int launch_composite_batch(const RenderDesc* renders, int R, int64_t total_tiles, int T, int buf,

@@ -247,6 +247,30 @@ class Rasterizer:
         keep = [i for i, t in enumerate(mf) if t >= 0]
         return ({L.VARIANTS[i]: float(mf[i]) for i in keep}, {L.VARIANTS[i]: float(mb[i]) for i in keep})
 
+    def trace_pixels(self, pixels, max_entries: int) -> dict:
+        """Decision trace of the last render at pixels [m][2] (x, y): per evaluated entry o G
+        (og [m][max_entries]) and the decision code (code [m][max_entries]: 0 skipped, 1
+        composited, 2 composited clamped, 3 stop), per pixel count, T_final, last, ncomp
+        (numpy arrays; synchronises)."""
+        host = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+        m, E = host.shape[0], int(max_entries)
+        dev = self.device
+        ptr = lambda t: C.c_void_p(t.data_ptr())
+        with torch.cuda.stream(self.stream):
+            pix = torch.as_tensor(host, device=dev)
+            og = torch.zeros((m, max(E, 1)), dtype=torch.float32, device=dev)
+            code = torch.full((m, max(E, 1)), 255, dtype=torch.uint8, device=dev)
+            count = torch.zeros(m, dtype=torch.int32, device=dev)
+            T = torch.zeros(m, dtype=torch.float32, device=dev)
+            last = torch.zeros(m, dtype=torch.int32, device=dev)
+            ncomp = torch.zeros(m, dtype=torch.int32, device=dev)
+            L.check(self._lib.pgs_trace_pixels(self._ctx, ptr(pix), m, E, ptr(og), ptr(code), ptr(count), ptr(T),
+                                               ptr(last), ptr(ncomp)), "pgs_trace_pixels")
+        self.stream.synchronize()
+        return dict(og=og[:, :E].cpu().numpy(), code=code[:, :E].cpu().numpy(), count=count.cpu().numpy(),
+                    T=T.cpu().numpy(), last=last.cpu().numpy().astype(np.uint32),
+                    ncomp=ncomp.cpu().numpy().astype(np.uint32))
+
     def launch_count(self) -> int:
         return int(self._lib.pgs_launch_count(self._ctx))
 

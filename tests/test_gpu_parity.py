@@ -61,7 +61,46 @@ def test_forward_keys_and_image(R, name):
     P = check_keys(rast, g, cam)
     assert pairs == P
     ora = oracle.render(g, cam)
-    compare_forward(img, T, last, ora)
+    compare_forward(img, T, last, ora, (rast, g, cam, 16))
+
+
+@pytest.mark.parametrize("name", ["tiny_2k_128", "dense_20k_64", "surface_sh3_200x120"])
+def test_decision_trace_against_oracle_decisions(R, name):
+    """The decision trace walks every pixel as the render did (T_final bit-exact, last and the
+    composited count equal), the kernel's o G of every evaluated entry (above the flush-to-zero
+    range of its 2^p) lies within the oracle's stated bound of its decision-side o 2^p, and on
+    unflagged pixels the two take the same decision at every entry."""
+    from paper_2601_17354_gb300 import _lib as L
+    from tests._parity import list_lengths
+    g, cam = SCENES[name]()
+    rast, _, img, T, last, code, pairs = render_gpu(R, g, cam)
+    ncomp = rast.read_buffer(L.PGS_BUF_NCOMP).reshape(cam.height, cam.width)
+    rng = np.random.default_rng(5)
+    pix = np.stack([rng.integers(0, cam.width, 2000), rng.integers(0, cam.height, 2000)], 1).astype(np.int32)
+    ora = oracle.render(g, cam)
+    flagged = np.argwhere(ora["flag"] != 0)[:, ::-1].astype(np.int32)
+    pix = np.concatenate([pix, flagged])
+    E = int(list_lengths(g, cam, pix).max())
+    tr = rast.trace_pixels(pix, E)
+    od = oracle.decisions(g, cam, pix, E)
+    xs, ys = pix[:, 0], pix[:, 1]
+    assert np.array_equal(tr["T"].view(np.uint32), T[ys, xs].view(np.uint32))
+    assert np.array_equal(tr["last"], last[ys, xs])
+    assert np.array_equal(tr["ncomp"], ncomp[ys, xs])
+    eps = oracle.decision_bound()
+    worst = 0.0
+    for k in range(len(pix)):
+        n = min(tr["count"][k], od["count"][k])
+        # o G of an entry does not depend on the walk before it: compare every entry both evaluated
+        a, b = tr["og"][k, :n].astype(np.float64), od["og"][k, :n]
+        nz = b > 2.0 ** -100  # the kernel's 2^p flushes below 2^-126 to zero (skipped either way)
+        if nz.any():
+            worst = max(worst, float(np.max(np.abs(a[nz] / b[nz] - 1.0))))
+        if ora["flag"][ys[k], xs[k]] == 0:
+            assert tr["count"][k] == od["count"][k], (xs[k], ys[k])
+            assert np.array_equal(tr["code"][k, :n], od["code"][k, :n]), (xs[k], ys[k])
+    print(f"largest relative deviation of the kernel's o G: {worst:.3g} (bound {eps:.3g})")
+    assert worst <= eps
 
 
 @pytest.mark.parametrize("tile", [8, 32])
@@ -77,13 +116,12 @@ def test_other_tile_edges(R, name, tile):
     assert code == 0
     assert pairs == check_keys(rast, g, cam, tile)
     ora = oracle.render(g, cam, tile)
-    compare_forward(img, T, last, ora)
+    _, forced = compare_forward(img, T, last, ora, (rast, g, cam, tile))
     dL = S.random_image(13, cam.width, cam.height)
-    dL[:, ora["flag"] != 0] = 0.0
     grads = buf.zeros_like()
     rast.backward(torch.from_numpy(dL).cuda(), grads)
     torch.cuda.synchronize()
-    _, og = oracle.backward(g, cam, dL, tile)
+    _, og = oracle.backward(g, cam, dL, tile, forced=forced)
     compare_grads(grads.numpy(), og, oracle.gaussian_flags(g, cam, tile) == 0)
     for pix, depth in L.VARIANTS:
         if (tile == 8 and pix == 4) or (tile == 32 and pix == 1):
@@ -100,12 +138,12 @@ def test_backward_grads(R, name):
     cam.bg = (0.1, 0.3, 0.2)
     rast, buf, img, T, last, code, _ = render_gpu(R, g, cam)
     ora = oracle.render(g, cam)
+    _, forced = compare_forward(img, T, last, ora, (rast, g, cam, 16))
     dL = S.random_image(11, cam.width, cam.height)
-    dL[:, ora["flag"] != 0] = 0.0
     grads = buf.zeros_like()
     rast.backward(torch.from_numpy(dL).cuda(), grads)
     torch.cuda.synchronize()
-    o2, og = oracle.backward(g, cam, dL)
+    o2, og = oracle.backward(g, cam, dL, forced=forced)
     keep = oracle.gaussian_flags(g, cam) == 0
     from paper_2601_17354_gb300 import _lib as L
     g2 = rast.read_buffer(L.PGS_BUF_GRAD2D).reshape(9, g.n)
@@ -121,16 +159,15 @@ def test_separate_forward_and_backward_variants(R):
     cam.bg = (0.1, 0.3, 0.2)
     ora = oracle.render(g, cam)
     dL = S.random_image(13, cam.width, cam.height)
-    dL[:, ora["flag"] != 0] = 0.0
     keep = oracle.gaussian_flags(g, cam) == 0
-    _, og = oracle.backward(g, cam, dL)
+    og = None
     for fwd, bwd in (((1, 64), (4, 256)), ((4, 128), (2, 64))):
         rast = R.Rasterizer()
         rast.set_variants(fwd, bwd)
-        buf = R.GaussianBuffer.from_arrays(g)
-        img = rast.render(buf, cam).cpu().numpy()
-        ok = ora["flag"] == 0
-        assert np.abs(img[:, ok] - ora["image"][:, ok]).max() <= 1e-4
+        rast, buf, img, T, last, _, _ = render_gpu(R, g, cam, rast)
+        _, forced = compare_forward(img, T, last, ora, (rast, g, cam, 16))
+        if og is None:
+            _, og = oracle.backward(g, cam, dL, forced=forced)
         grads = buf.zeros_like()
         rast.backward(torch.from_numpy(dL).cuda(), grads)
         torch.cuda.synchronize()
@@ -140,17 +177,22 @@ def test_separate_forward_and_backward_variants(R):
 def test_fused_backward_step_matches_oracle_and_separate_calls(R):
     """pgs_backward_step == pgs_backward + pgs_step; its first-step moment m = (1 - b1) g
     exposes the in-register parameter gradient, checked against the oracle."""
+    from paper_2601_17354_gb300 import _lib as L
     g, cam = SCENES["surface_sh3_200x120"]()
     cam.bg = (0.1, 0.3, 0.2)
     ora = oracle.render(g, cam)
     dL = S.random_image(12, cam.width, cam.height)
-    dL[:, ora["flag"] != 0] = 0.0
     dLt = torch.from_numpy(dL).cuda()
     ra, rb = R.Rasterizer(), R.Rasterizer()
     pa, pb = R.GaussianBuffer.from_arrays(g), R.GaussianBuffer.from_arrays(g)
     ga, ma, va = pa.zeros_like(), pa.zeros_like(), pa.zeros_like()
     mb, vb = pb.zeros_like(), pb.zeros_like()
     ra.render(pa, cam)
+    torch.cuda.synchronize()
+    T = ra.read_buffer(L.PGS_BUF_T_FINAL).reshape(cam.height, cam.width)
+    last = ra.read_buffer(L.PGS_BUF_LAST).reshape(cam.height, cam.width)
+    img = ra.render(pa, cam).cpu().numpy()
+    _, forced = compare_forward(img, T, last, ora, (ra, g, cam, 16))
     ra.backward(dLt, ga)
     ra.step(pa, ga, ma, va, 1)
     rb.render(pb, cam)
@@ -162,7 +204,7 @@ def test_fused_backward_step_matches_oracle_and_separate_calls(R):
     # t = 1: the step is lr * g / (|g| + eps), so parameters agree wherever g is not at noise level
     dp = np.abs(pb.data.cpu().numpy() - pa.data.cpu().numpy())
     assert np.mean(dp > 1e-6) < 1e-3
-    _, og = oracle.backward(g, cam, dL)
+    _, og = oracle.backward(g, cam, dL, forced=forced)
     keep = oracle.gaussian_flags(g, cam) == 0
     grads = {k: v / (1 - np.float32(0.9)) for k, v in mb.numpy().items()}
     compare_grads(grads, og, keep)
@@ -219,7 +261,7 @@ def test_single_gaussian_covering_every_tile(R):
     TX, TY = oracle.tiles(cam)
     assert pairs == TX * TY
     check_keys(rast, g, cam)
-    compare_forward(img, T, last, oracle.render(g, cam))
+    compare_forward(img, T, last, oracle.render(g, cam), (rast, g, cam, 16))
 
 
 def test_one_pixel_image(R):
@@ -228,7 +270,7 @@ def test_one_pixel_image(R):
     rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam1)
     assert code == 0
     check_keys(rast, g, cam1)
-    compare_forward(img, T, last, oracle.render(g, cam1))
+    compare_forward(img, T, last, oracle.render(g, cam1), (rast, g, cam1, 16))
 
 
 def test_equal_depth_ties_are_stable(R):
@@ -236,7 +278,7 @@ def test_equal_depth_ties_are_stable(R):
     g.means[2, 1::5] = g.means[2, 0:-1:5][: len(g.means[2, 1::5])]
     rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
     check_keys(rast, g, cam)
-    compare_forward(img, T, last, oracle.render(g, cam))
+    compare_forward(img, T, last, oracle.render(g, cam), (rast, g, cam, 16))
 
 
 def _lengths(g, cam, tile=16):
@@ -294,7 +336,7 @@ def test_short_equal_depth_runs(R):
     rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam)
     assert code == 0
     assert pairs == check_keys(rast, g, cam)
-    compare_forward(img, T, last, oracle.render(g, cam))
+    compare_forward(img, T, last, oracle.render(g, cam), (rast, g, cam, 16))
 
 
 def test_nonfinite_parameter_is_reported_and_culled(R):
@@ -321,7 +363,7 @@ def test_capacity_overflow_is_reported_then_fits(R):
     exact = R.Rasterizer(pair_capacity=P)
     _, _, img, T, last, code, pairs = render_gpu(R, g, cam, exact)
     assert code == 0 and pairs == P
-    compare_forward(img, T, last, oracle.render(g, cam))
+    compare_forward(img, T, last, oracle.render(g, cam), (exact, g, cam, 16))
 
 
 def test_backward_without_render_is_an_error(R):

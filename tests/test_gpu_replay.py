@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2601_17354_gb300 import synthetic as S
-from tests._parity import compare_grads, rel_l2
+from tests._parity import check_render, compare_grads, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -40,9 +40,7 @@ def backward(R, rast, g, cam, dL):
 def test_replay_matches_oracle_and_recompute(R, name, k_max):
     g, cam = scene(name)
     cam.bg = (0.1, 0.3, 0.2)
-    ora = oracle.render(g, cam)
     dL = S.random_image(21, cam.width, cam.height)
-    dL[:, ora["flag"] != 0] = 0.0
     rec = R.Rasterizer()
     rec.set_variant(1, 256)
     img0, g0 = backward(R, rec, g, cam, dL)
@@ -50,7 +48,8 @@ def test_replay_matches_oracle_and_recompute(R, name, k_max):
     rep.set_replay_cache(k_max)
     img1, g1 = backward(R, rep, g, cam, dL)
     assert np.array_equal(img1, img0)  # recording does not change the forward
-    _, og = oracle.backward(g, cam, dL)
+    _, forced = check_render(rep, g, cam, img1)
+    _, og = oracle.backward(g, cam, dL, forced=forced)
     compare_grads(g1, og, oracle.gaussian_flags(g, cam) == 0)
     for k in g0:
         assert rel_l2(g1[k], g0[k]) < 1e-4, k
