@@ -909,7 +909,8 @@ __device__ __forceinline__ void bwd_tile_sorted(const TileJob& J, int64_t n, con
 // entries, each warp on its own pixels.
 //
 // Phase 1 (per pixel, back to front, as Eq. 8 orders it): each thread carries its pixels' state
-// and, for every entry of the round, writes two scalars per pixel to the warp's shared memory:
+// and, for every entry some pixel of the warp composites, writes two scalars per pixel to a row of
+// the warp's round in shared memory:
 // dpow = dL/dalpha alpha (zero through the 0.99 clamp) and wgt = alpha T (the weight of the entry's
 // colour).  The state is the transmittance T in front of the current entry and S = <C_behind,
 // dL/dC>, the colour behind the entry (Eq. 7's C_in) projected on the pixel's upstream gradient:
@@ -950,8 +951,9 @@ struct Bwd2Smem {
     float4 gg0[kWarps * kPW]; // dL/dC (r, r, g, g)
     float2 gg1[kWarps * kPW]; // (b, b)
     uint32_t wmax[32];
+    int rowj[kWarps][kBwdRound];  // staged entry of each row of a warp's round
     union {
-        float4 D[kWarps][kBwdRound][kRow];  // per warp, entry of the round and pixel pair: (dpow x2, wgt x2)
+        float4 D[kWarps][kBwdRound][kRow];  // per warp, row of the round and pixel pair: (dpow x2, wgt x2)
         struct {
             uint32_t order[kT * kT];  // tile pixels (row-major index) in the order of their `last`
             uint32_t count[256];
@@ -1091,51 +1093,58 @@ __device__ __forceinline__ void bwd_tile_2p(const TileJob& J, int64_t n, const u
             }
         }
         __syncthreads();
-        // this warp's entries: positions below its deepest `last`, in rounds from the back
+        // this warp's entries: positions below its deepest `last`, back to front; the entries some
+        // pixel of the warp composites fill rounds of kE rows, each summed by phase 2 when full
         const int jtop = (int)min((uint32_t)cnt, wmax > start ? wmax - start : 0u);
-        for (int hi = jtop; hi > 0; hi -= kE) {
-            const int lo = hi > kE ? hi - kE : 0;
-            // ---- phase 1: entries hi - 1 .. lo, back to front (two at a time: the alpha of the next
-            // entry does not wait for this one's transmittance)
-#pragma unroll 2
-            for (int j = hi - 1; j >= lo; --j) {
-                const uint32_t pos = start + j;
-                float4* __restrict__ Drow = Dw[j - lo];
-                const float4 xy = S.xy[j], ab = S.ab[j], co = S.co[j], rg = S.rg[j], bz = S.bz[j];
-                const F2 X2 = f2(xy.x, xy.y), Y2 = f2(xy.z, xy.w);
-                const F2 A2 = f2(ab.x, ab.y), B2 = f2(ab.z, ab.w), C2 = f2(co.x, co.y), O2 = f2(co.z, co.w);
-                const F2 Cr = f2(rg.x, rg.y), Cg = f2(rg.z, rg.w), Cb = f2(bz.x, bz.y);
+        int nrow = 0;
+        for (int j = jtop - 1; j >= 0; --j) {
+            // ---- phase 1: entry j for this thread's pixels
+            const uint32_t pos = start + j;
+            const float4 xy = S.xy[j], ab = S.ab[j], co = S.co[j], rg = S.rg[j], bz = S.bz[j];
+            const F2 X2 = f2(xy.x, xy.y), Y2 = f2(xy.z, xy.w);
+            const F2 A2 = f2(ab.x, ab.y), B2 = f2(ab.z, ab.w), C2 = f2(co.x, co.y), O2 = f2(co.z, co.w);
+            const F2 Cr = f2(rg.x, rg.y), Cg = f2(rg.z, rg.w), Cb = f2(bz.x, bz.y);
+            float4 out1[NP];
+            bool mine = false;
 #pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const F2 DX = sub2(FX[q], X2), DY = sub2(FY[q], Y2);
-                    // the forward's exponent, term for term: A dx^2 + B dx dy + C dy^2
-                    const float2 p = un(fma2(C2, mul2(DY, DY), fma2(B2, mul2(DX, DY), mul2(A2, mul2(DX, DX)))));
-                    const float2 og = un(mul2(O2, f2(ex2_approx(p.x), ex2_approx(p.y))));
-                    const float ax = fminf(kAlphaMax, og.x), ay = fminf(kAlphaMax, og.y);
-                    const bool p0 = pos < my_last[2 * q] && ax >= kAlphaMin;
-                    const bool p1 = pos < my_last[2 * q + 1] && ay >= kAlphaMin;
-                    // a pixel that does not composite the entry takes alpha = 0
-                    const F2 A = f2(p0 ? ax : 0.0f, p1 ? ay : 0.0f);
-                    // alpha through which the gradient flows: zero at the 0.99 clamp
-                    const F2 AQ = f2(p0 && og.x <= kAlphaMax ? ax : 0.0f, p1 && og.y <= kAlphaMax ? ay : 0.0f);
-                    const float2 om = un(sub2(ONE, A));
-                    float rx, ry;
-                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(om.x));
-                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(om.y));
-                    const F2 Tb = mul2(T[q], f2(p0 ? rx : 1.0f, p1 ? ry : 1.0f));  // transmittance in front
-                    const F2 cg = fma2(Cb, g2[q], fma2(Cg, g1[q], mul2(Cr, g0[q])));
-                    const F2 r = sub2(cg, Sb[q]);
-                    const float2 dpow = un(mul2(mul2(Tb, r), AQ));
-                    const float2 wgt = un(mul2(A, Tb));
-                    Sb[q] = fma2(A, r, Sb[q]);
-                    T[q] = Tb;
-                    Drow[q * 32 + lane] = make_float4(dpow.x, dpow.y, wgt.x, wgt.y);
-                }
+            for (int q = 0; q < NP; ++q) {
+                const F2 DX = sub2(FX[q], X2), DY = sub2(FY[q], Y2);
+                // the forward's exponent, term for term: A dx^2 + B dx dy + C dy^2
+                const float2 p = un(fma2(C2, mul2(DY, DY), fma2(B2, mul2(DX, DY), mul2(A2, mul2(DX, DX)))));
+                const float2 og = un(mul2(O2, f2(ex2_approx(p.x), ex2_approx(p.y))));
+                const float ax = fminf(kAlphaMax, og.x), ay = fminf(kAlphaMax, og.y);
+                const bool p0 = pos < my_last[2 * q] && ax >= kAlphaMin;
+                const bool p1 = pos < my_last[2 * q + 1] && ay >= kAlphaMin;
+                mine = mine || p0 || p1;
+                // a pixel that does not composite the entry takes alpha = 0
+                const F2 A = f2(p0 ? ax : 0.0f, p1 ? ay : 0.0f);
+                // alpha through which the gradient flows: zero at the 0.99 clamp
+                const F2 AQ = f2(p0 && og.x <= kAlphaMax ? ax : 0.0f, p1 && og.y <= kAlphaMax ? ay : 0.0f);
+                const float2 om = un(sub2(ONE, A));
+                float rx, ry;
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(om.x));
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(om.y));
+                const F2 Tb = mul2(T[q], f2(p0 ? rx : 1.0f, p1 ? ry : 1.0f));  // transmittance in front
+                const F2 cg = fma2(Cb, g2[q], fma2(Cg, g1[q], mul2(Cr, g0[q])));
+                const F2 r = sub2(cg, Sb[q]);
+                const float2 dpow = un(mul2(mul2(Tb, r), AQ));
+                const float2 wgt = un(mul2(A, Tb));
+                Sb[q] = fma2(A, r, Sb[q]);
+                T[q] = Tb;
+                out1[q] = make_float4(dpow.x, dpow.y, wgt.x, wgt.y);
             }
+            if (__any_sync(kFull, mine)) {  // warp-uniform: the entry gets a row of the round
+#pragma unroll
+                for (int q = 0; q < NP; ++q) Dw[nrow][q * 32 + lane] = out1[q];
+                if (lane == 0) S.rowj[warp][nrow] = j;
+                ++nrow;
+            }
+            if (nrow < kE && j > 0) continue;
+            if (nrow == 0) break;
             __syncwarp();
-            // ---- phase 2: entry lo + pe, summed over the warp's pairs pl, pl + L, ... (consecutive
-            // lanes read consecutive pairs: no bank conflict)
-            if (pe < hi - lo) {
+            // ---- phase 2: row pe (entry rowj[pe]), summed over the warp's pairs pl, pl + L, ...
+            // (consecutive lanes read consecutive pairs: no bank conflict)
+            if (pe < nrow) {
                 const float4* __restrict__ Drow = Dw[pe];
                 F2 acc[9];
 #pragma unroll
@@ -1169,32 +1178,28 @@ __device__ __forceinline__ void bwd_tile_2p(const TileJob& J, int64_t n, const u
                 for (int o = 1; o < L; o <<= 1)
 #pragma unroll
                     for (int k = 0; k < 9; ++k) v[k] += __shfl_xor_sync(gmask, v[k], o);
-                const int j = lo + pe;
+                const int je = S.rowj[warp][pe];
                 const float M0 = v[0], Mx = v[1], My = v[2], Mxx = v[3], Mxy = v[4], Myy = v[5];
-                const float u = S.xy[j].x - cxt, vv = S.xy[j].z - cyt;  // mean relative to the tile centre
+                const float u = S.xy[je].x - cxt, vv = S.xy[je].z - cyt;  // mean relative to the tile centre
                 const float sdx = fmaf(-u, M0, Mx), sdy = fmaf(-vv, M0, My);  // sum dpow dx, sum dpow dy
                 float out[9];
-                const float ca = S.bz[j].z, cc = S.bz[j].w, cb = S.bi[j].x;
+                const float ca = S.bz[je].z, cc = S.bz[je].w, cb = S.bi[je].x;
                 out[0] = fmaf(ca, sdx, cb * sdy);
                 out[1] = fmaf(cc, sdy, cb * sdx);
                 out[2] = -0.5f * fmaf(-u, sdx, fmaf(-u, Mx, Mxx));    // sum dpow dx^2
                 out[3] = -fmaf(-vv, sdx, fmaf(-u, My, Mxy));          // sum dpow dx dy
                 out[4] = -0.5f * fmaf(-vv, sdy, fmaf(-vv, My, Myy));  // sum dpow dy^2
-                out[5] = __fdividef(M0, S.co[j].z);
+                out[5] = __fdividef(M0, S.co[je].z);
                 out[6] = v[6];
                 out[7] = v[7];
                 out[8] = v[8];
-                bool any = false;
+                const uint32_t id = __float_as_uint(S.bi[je].y);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) any = any || out[k] != 0.0f;
-                if (any) {
-                    const uint32_t id = __float_as_uint(S.bi[j].y);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k)
-                        if (k % L == pl) atomicAdd(&sc.grad2d[(size_t)k * n + id], out[k]);
-                }
+                for (int k = 0; k < 9; ++k)
+                    if (k % L == pl) atomicAdd(&sc.grad2d[(size_t)k * n + id], out[k]);
             }
             __syncwarp();
+            nrow = 0;
         }
         end = start;
     }
