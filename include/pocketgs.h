@@ -223,10 +223,11 @@ int64_t pgs_launch_count(const pgs_ctx* ctx);
    another allocator (a framework's caching pool or an arena reserved at start-up, where a direct
    cudaMalloc can fail or fragment the reservation) or latency-critical loops in which
    cudaMalloc / cudaFree would synchronise the device.  It runs the radix sort of pgs_render
-   (stable, least-significant-digit first, 8-bit digits) over the low key_bits bits of count
-   (key, value) pairs: keys_in/vals_in (device, read only) -> keys_out/vals_out (device, caller
+   (stable, least-significant-digit first, 8-bit digits, the last digit masked) by the low key_bits
+   bits of count (key, value) pairs (higher key bits never take part in the order; keys_out keeps
+   them as they were): keys_in/vals_in (device, read only) -> keys_out/vals_out (device, caller
    owned, not overlapping the inputs).  It allocates nothing: its scratch is one file-scope device
-   array of about 3.1 MB, held by every GPU that loads the library until the process exits.
+   array of 3.2 MB, held by every GPU that loads the library until the process exits.
    count must be at most 262144 (PGS_ERR_TOO_LARGE otherwise); key_bits in 1..64.  The first call
    on a device looks the scratch address up (cudaGetSymbolAddress) with that device current; make
    that first call before any stream capture.  Every call shares the one scratch array, which
@@ -235,6 +236,12 @@ int64_t pgs_launch_count(const pgs_ctx* ctx);
    cuda_stream (NULL = legacy default stream). */
 int pgs_sort_pairs_static(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                           uint32_t* vals_out, int64_t count, int32_t key_bits, void* cuda_stream);
+/* The device-side check of pgs_sort_pairs_static (the sort's scatter checks every destination
+   index against the pair count and skips an access that fails, recording it in a status word of the
+   same static scratch, which stays set across sorts).  Synchronises cuda_stream, returns
+   PGS_ERR_INTERNAL if a check failed since the previous call of this function (else PGS_OK) and
+   clears the word.  No paper counterpart; allocates nothing. */
+int pgs_sort_pairs_static_status(void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------------
    Batched training: many views of many scenes (uneven Gaussian counts and resolutions) in one
@@ -271,6 +278,23 @@ void pgs_batch_destroy(pgs_batch* b);
    pgs_batch_status has reported PGS_ERR_CAPACITY (with the pairs needed) and cleared the flag;
    pgs_batch_reserve then grows the capacity. */
 int pgs_batch_step(pgs_batch* b);
+/* The two halves of a step as separate calls, for losses other than the built-in L1 (e.g. the
+   L1 + D-SSIM of pgs_loss_dssim) or renders for evaluation.
+   pgs_render_batch: the forward of every render (Eq. 7 front to back, as pgs_render: projection,
+   one depth sort, pair emission and sort, one persistent compositing launch) into each render's
+   image buffer; parameters, moments and the step count are not touched.  The batch keeps the
+   projected Gaussians, pairs, T_final and last of every render for pgs_backward_batch.
+   pgs_backward_batch: the backward of the last pgs_render_batch for the upstream gradients the
+   caller has written into each render's dL_dimage buffer (device [3][H][W]): Eq. 8 per pixel back
+   to front from `last`, scattered to the canonical indices (Eq. 10), chained to the parameters and
+   summed over each scene's renders; ADDED to grads[scene] (host array of n_scenes descriptors of
+   device buffers with the scene's n and sh_degree; the caller zeroes them).  PGS_ERR_NO_RENDER
+   without a pgs_render_batch since the last pgs_batch_step (which changes the parameters).  An
+   optimizer step on the gradients is the caller's (pgs_step per scene, with a context on the same
+   stream).  Both are asynchronous on the batch's stream; a pair overflow is reported by
+   pgs_batch_status and then the backward adds nothing. */
+int pgs_render_batch(pgs_batch* b);
+int pgs_backward_batch(pgs_batch* b, const pgs_gaussians* grads);
 /* Capture one step into a CUDA graph (nothing runs during capture); later steps replay it. */
 int pgs_batch_capture(pgs_batch* b);
 /* Point every render at a new view before the next step (cameras[n_renders], targets[n_renders]

@@ -56,7 +56,7 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times",
             "pgs_mvs_create", "pgs_mvs_destroy", "pgs_mvs_depth_range", "pgs_mvs_select_reference",
             "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse", "pgs_mvs_stage_times",
-            "pgs_trace_pixels"]
+            "pgs_trace_pixels", "pgs_sort_pairs_static_status", "pgs_render_batch", "pgs_backward_batch"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -138,6 +138,8 @@ def lib():
             L.pgs_launch_count.restype = I64
             L.pgs_sort_pairs_static.argtypes = [P, P, P, P, I64, C.c_int32, P]
             L.pgs_sort_pairs_static.restype = I
+            L.pgs_sort_pairs_static_status.argtypes = [P]
+            L.pgs_sort_pairs_static_status.restype = I
             L.pgs_batch_create.argtypes = [C.POINTER(P), C.POINTER(PgsConfig), C.c_int32,
                                            C.POINTER(PgsGaussians), C.POINTER(PgsGaussians),
                                            C.POINTER(PgsGaussians), C.c_int32,
@@ -145,6 +147,10 @@ def lib():
             L.pgs_batch_create.restype = I
             L.pgs_batch_destroy.argtypes = [P]
             L.pgs_batch_destroy.restype = None
+            L.pgs_render_batch.argtypes = [P]
+            L.pgs_render_batch.restype = I
+            L.pgs_backward_batch.argtypes = [P, C.POINTER(PgsGaussians)]
+            L.pgs_backward_batch.restype = I
             for name in ("pgs_batch_step", "pgs_batch_capture"):
                 getattr(L, name).argtypes = [P]
                 getattr(L, name).restype = I

@@ -15,8 +15,9 @@
 // the overflow), so no host synchronisation sits between projection and compositing.
 //
 // The radix sort is least-significant-digit first, 8-bit digits, over the bits that can be
-// non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; 64-bit
-// keys for the allocation-free entry point).  Each pass: per-CTA digit histogram,
+// non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; the
+// caller's low key bits of the 64-bit keys of the allocation-free entry point); the last digit is
+// masked to what is left of the bit range.  Each pass: per-CTA digit histogram,
 // per-digit scan across CTAs (digit totals come from one up-front histogram of all passes),
 // and a stable scatter that ranks keys inside a CTA with warp ballots (no inter-CTA waiting).
 #include "pgs_internal.cuh"
@@ -215,7 +216,8 @@ __device__ __forceinline__ uint64_t kept_pairs(const Scratch& sc, int64_t capaci
 // the partial copy of the CTA
 template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
-k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __restrict__ keys, Scratch sc) {
+k_digit_totals(int64_t capacity, int first_shift, int passes, uint32_t last_mask, const KeyT* __restrict__ keys,
+               Scratch sc) {
     __shared__ uint32_t h[kMaxPasses][kRadix];
     for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
@@ -224,7 +226,7 @@ k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __rest
          k += (uint64_t)gridDim.x * kSortThreads) {
         const unsigned long long key = keys[k];
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&h[p][(key >> (first_shift + p * kRadixBits)) & (kRadix - 1)], 1u);
+            atomicAdd(&h[p][(key >> (first_shift + p * kRadixBits)) & (p == passes - 1 ? last_mask : kRadix - 1)], 1u);
     }
     __syncthreads();
     uint32_t* copy = sc.digit_totals + (blockIdx.x % kTotalCopies) * (kMaxPasses * kRadix);
@@ -237,7 +239,7 @@ k_digit_totals(int64_t capacity, int first_shift, int passes, const KeyT* __rest
 // per-CTA histogram of one digit (CTA tiles of kSortThreads x kItems keys)
 template <typename KeyT, int kItems>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_hist(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ keys, Scratch sc) {
+k_sort_hist(int64_t capacity, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ keys, Scratch sc) {
     constexpr int kTile = kSortThreads * kItems;
     const uint32_t nblk = *sc.sort_blocks;
     if (blockIdx.x >= nblk) return;
@@ -248,7 +250,7 @@ k_sort_hist(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ ke
     const uint64_t begin = (uint64_t)blockIdx.x * kTile;
     const uint64_t end = begin + kTile < P ? begin + kTile : P;
     for (uint64_t k = begin + threadIdx.x; k < end; k += kSortThreads)
-        atomicAdd(&h[(uint32_t)(keys[k] >> shift) & (kRadix - 1)], 1u);
+        atomicAdd(&h[(uint32_t)(keys[k] >> shift) & dmask], 1u);
     __syncthreads();
     sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x] = h[threadIdx.x];
 }
@@ -328,7 +330,7 @@ constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSo
 
 template <typename KeyT, int kItems>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__ kin,
+k_sort_scatter(int64_t capacity, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ kin,
                const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
                Scratch sc) {
     constexpr int kTile = kSortThreads * kItems;        // keys per CTA
@@ -360,7 +362,7 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
         const bool valid = idx < P;
         key[r] = valid ? kin[idx] : (KeyT)0;
         val[r] = valid ? vin[idx] : 0u;
-        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRadix - 1) : 0u;
+        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & dmask : 0u;
         // lanes holding the same digit: one ballot per digit bit (and one for validity)
         unsigned peers = __ballot_sync(0xffffffffu, valid);
         if (!valid) peers = ~peers;
@@ -419,7 +421,7 @@ k_sort_scatter(int64_t capacity, int shift, int sb_max, const KeyT* __restrict__
     const uint32_t count = (uint32_t)min((uint64_t)kTile, P - cbase);
     for (uint32_t p = threadIdx.x; p < count; p += kSortThreads) {
         const KeyT k = s_keys[p];
-        const uint32_t d = (uint32_t)(k >> shift) & (kRadix - 1);
+        const uint32_t d = (uint32_t)(k >> shift) & dmask;
         const uint64_t dst = (uint64_t)s_gofs[d] + (p - s_bstart[d]);
         if (dst < P) {
             kout[dst] = k;
@@ -537,12 +539,15 @@ void enable_scatter_smem() {
     (void)done;
 }
 
-// LSD passes over the keys in keys[0] / keys[1] (viewed as KeyT) starting at bit first_shift, CTA
-// tiles of kSortThreads x kItems keys; returns the launches and leaves the sorted buffer's index
-// in *out_buf
+// LSD passes over bits [first_shift, first_shift + bits) of the keys in keys[0] / keys[1] (viewed
+// as KeyT), 8 bits a pass (the last pass takes what is left: bits above the range never take part),
+// CTA tiles of kSortThreads x kItems keys; returns the launches and leaves the sorted buffer's
+// index in *out_buf
 template <typename KeyT, int kItems>
-int sort_passes(int64_t capacity, int first_shift, int passes, const Scratch& sc, cudaStream_t s, int* out_buf) {
+int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf) {
     constexpr int kTile = kSortThreads * kItems;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
     const int sb_max = (int)((capacity + kTile - 1) / kTile);
     // the totals read every key once: one CTA per 1024 keys, at most 8 per SM
     const int64_t want = (capacity + 1023) / 1024;
@@ -553,13 +558,14 @@ int sort_passes(int64_t capacity, int first_shift, int passes, const Scratch& sc
     enable_scatter_smem<KeyT, kItems>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
     cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
-    k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, k[0], sc);
+    k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
-        k_sort_hist<KeyT, kItems><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, sb_max, k[buf], sc);
+        const uint32_t dmask = p == passes - 1 ? last_mask : (uint32_t)(kRadix - 1);
+        k_sort_hist<KeyT, kItems><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, dmask, sb_max, k[buf], sc);
         k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
         k_sort_scatter<KeyT, kItems><<<sb_max, kSortThreads, scatter_smem<KeyT, kItems>(), s>>>(
-            capacity, shift, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
+            capacity, shift, dmask, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }
     *out_buf = buf;
@@ -582,7 +588,7 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     d.pair_count = sc.dcount;
     d.sort_blocks = sc.dblocks;
     int buf = 0;
-    const int launched = sort_passes<uint32_t, kDepthItems>(n, 0, 32 / kRadixBits, d, s, &buf);
+    const int launched = sort_passes<uint32_t, kDepthItems>(n, 0, 32, d, s, &buf);
     *perm = sc.dvals[buf];
     return launched;
 }
@@ -601,9 +607,8 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)tiles) ++tile_bits;
     // the pairs arrive in depth order: a stable sort of their 32-bit tile keys completes it
-    const int passes = (tile_bits + kRadixBits - 1) / kRadixBits;
     int buf = 0;
-    int launched = sort_passes<uint32_t, kSortItems>(capacity, 0, passes, sc, s, &buf);
+    int launched = sort_passes<uint32_t, kSortItems>(capacity, 0, tile_bits, sc, s, &buf);
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (capacity > 0) {
         k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)tiles, reinterpret_cast<const uint32_t*>(sc.keys[buf]), sc);
@@ -622,8 +627,7 @@ int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t 
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf) {
-    return sort_passes<unsigned long long, kSortItems>(capacity, 0, (key_bits + kRadixBits - 1) / kRadixBits, sc,
-                                                       s, out_buf);
+    return sort_passes<unsigned long long, kSortItems>(capacity, 0, key_bits, sc, s, out_buf);
 }
 
 }  // namespace pgs

@@ -154,6 +154,10 @@ int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, in
                           int64_t gauss_total, int64_t items, const Scratch& sc, const float lr[6],
                           float b1, float b2, float eps, const int64_t* step, cudaStream_t s);
 int launch_step_tick(int64_t* step, const int32_t* status, cudaStream_t s);
+// The batched projection backward alone: each scene's parameter gradient, summed over its renders,
+// added to grads[scene] (a device table of S pgs_gaussians).
+int launch_bwd_batch(const RenderDesc* renders, const SceneDesc* scenes, int S, int deg, int64_t gauss_total,
+                     int64_t items, const Scratch& sc, const pgs_gaussians* grads, cudaStream_t s);
 int launch_loss_batch(const RenderDesc* renders, int R, int64_t values, double* losses, cudaStream_t s);
 
 // Initializer path (K13 kNN, K14 features + paper initializer, K15 MLP).
@@ -187,9 +191,9 @@ int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStrea
 // the sorted pairs' full 64-bit keys (tile << 32 | depth bits) into keys[buf ^ 1]
 int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t s);
 
-// K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting the
-// low key_bits bits (the pair count is read from sc.pair_count, at most `capacity`); the digit
-// totals must be zero on entry.
+// K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting by the
+// low key_bits bits only (higher bits never take part; the pair count is read from sc.pair_count,
+// at most `capacity`); the digit totals must be zero on entry.
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf);
 

@@ -27,17 +27,18 @@ constexpr size_t kOffBlocks = kOffCount + sizeof(unsigned long long);
 constexpr size_t kOffStatus = kOffBlocks + sizeof(uint32_t);
 constexpr size_t kScratchBytes = (kOffStatus + sizeof(int32_t) + 255) & ~size_t(255);
 
-// Held by every GPU that loads the library until the process exits (about 3.2 MB).
+// Held by every GPU that loads the library until the process exits (3.2 MB).
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-// Per-call set-up on the device: pair count, active sort CTAs, cleared totals and status.
+// Per-call set-up on the device: pair count, active sort CTAs, cleared totals.  The status word
+// is not cleared here: a failed check stays recorded until pgs_sort_pairs_static_status reads it
+// (the array starts zeroed).
 __global__ void k_static_sort_init(unsigned char* base, int64_t count) {
     uint32_t* totals = reinterpret_cast<uint32_t*>(base + kOffTotals);
     for (int k = threadIdx.x; k < kTotalWords; k += blockDim.x) totals[k] = 0;
     if (threadIdx.x == 0) {
         *reinterpret_cast<unsigned long long*>(base + kOffCount) = (unsigned long long)count;
         *reinterpret_cast<uint32_t*>(base + kOffBlocks) = (uint32_t)((count + kSortTile - 1) / kSortTile);
-        *reinterpret_cast<int32_t*>(base + kOffStatus) = 0;
     }
 }
 
@@ -103,4 +104,17 @@ extern "C" int pgs_sort_pairs_static(const uint64_t* keys_in, const uint32_t* va
         if (e != cudaSuccess) return PGS_ERR_CUDA;
     }
     return cudaGetLastError() == cudaSuccess ? PGS_OK : PGS_ERR_CUDA;
+}
+
+extern "C" int pgs_sort_pairs_static_status(void* cuda_stream) {
+    unsigned char* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != PGS_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, base + kOffStatus, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffStatus, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return PGS_ERR_CUDA;
+    return (st & kStatusInternal) ? PGS_ERR_INTERNAL : PGS_OK;
 }

@@ -33,6 +33,11 @@ def _render_pairs(g, cam):
     return keys, vals, 32 + max(1, int(np.ceil(np.log2(tiles))))
 
 
+def _status():
+    from paper_2601_17354_gb300 import _lib as L
+    return L.lib().pgs_sort_pairs_static_status(C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
 def _static_sort(keys_in, vals_in, key_bits):
     from paper_2601_17354_gb300 import _lib as L
     lib = L.lib()
@@ -64,6 +69,31 @@ def test_static_sort_matches_render_sort_twice():
         sk, sv = _static_sort(ek, ev, bits)
         assert np.array_equal(sk, keys)
         assert np.array_equal(sv, vals)
+        assert _status() == 0
+
+
+@pytest.mark.parametrize("key_bits", [40, 48, 64, 5])
+def test_static_sort_key_bits_and_pass_parity(key_bits):
+    """Odd (40 bits: 5 passes; 5 bits: 1 pass) and even (48 bits: 6 passes; 64 bits: 8 passes)
+    pass counts, with key bits above key_bits set at random: they take no part in the order (a
+    stable sort by the low key_bits bits, checked against numpy's stable argsort), and keys_out
+    keeps them."""
+    rng = np.random.default_rng(key_bits)
+    n = 70_001
+    keys = rng.integers(0, 2 ** 63, n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64)
+    mask = np.uint64((1 << key_bits) - 1) if key_bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    low = keys & mask
+    m = n // 3
+    low[0:3 * m:3] = low[1:3 * m:3]  # every third key repeats its neighbour's low bits: ties
+    keys = (keys & ~mask) | low
+    sort_key = keys & mask
+    vals = np.arange(n, dtype=np.uint32)[::-1].copy()
+    order = np.argsort(sort_key, kind="stable")
+    for _ in range(2):  # twice: the shared scratch keeps the first call's contents
+        sk, sv = _static_sort(keys, vals, key_bits)
+        assert np.array_equal(sv, vals[order])
+        assert np.array_equal(sk, keys[order])
+        assert _status() == 0
 
 
 def test_static_sort_rejects_sizes_beyond_its_scratch():
