@@ -1,6 +1,8 @@
 """Batched training over many views of many scenes: one planned batch per set of (scene, view,
 target) renders, one training step = render + L1 + backward + Adam of every render, optionally
-captured once in a CUDA graph and replayed.  Thin marshalling over pgs_batch_* of the C ABI."""
+captured once in a CUDA graph and replayed; or its halves apart (render(), then backward() of the
+caller's upstream gradients, e.g. L1 + D-SSIM).  Thin marshalling over pgs_batch_*,
+pgs_render_batch and pgs_backward_batch of the C ABI."""
 from __future__ import annotations
 
 import ctypes as C
@@ -74,6 +76,22 @@ class BatchTrainer:
     def step(self):
         self._enter()
         L.check(self._lib.pgs_batch_step(self._b), "pgs_batch_step")
+        self._leave()
+
+    def render(self):
+        """The forward of every render into self.images (no loss, no parameter change)."""
+        self._enter()
+        L.check(self._lib.pgs_render_batch(self._b), "pgs_render_batch")
+        self._leave()
+
+    def backward(self, grads: list):
+        """The backward of the last render() for the upstream gradients in self.dls (written by the
+        caller), added to grads (one GaussianBuffer per scene)."""
+        if len(grads) != len(self.scenes):
+            raise ValueError("one gradient buffer per scene")
+        G = (L.PgsGaussians * len(grads))(*[g.struct() for g in grads])
+        self._enter()
+        L.check(self._lib.pgs_backward_batch(self._b, G), "pgs_backward_batch")
         self._leave()
 
     def capture(self):

@@ -664,6 +664,8 @@ struct pgs_batch {
     double* d_losses = nullptr;
     uint32_t* d_work = nullptr;  // forward and backward work counters
     int64_t* d_step = nullptr;
+    pgs_gaussians* d_grads = nullptr;  // gradient buffers of pgs_backward_batch, one per scene
+    bool rendered = false;             // pgs_render_batch ran since the last parameter change
     int buf = 0;
     CompositeVariant variant = default_variant();
     cudaGraph_t graph = nullptr;
@@ -795,7 +797,8 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
     if (e != cudaSuccess) return fail(cuda_err(e));
     carve_g(b->sc, static_cast<char*>(b->arena_g), b->items, b->pixels, b->tiles);
     const size_t tbytes = align256(sizeof(SceneDesc) * n_scenes) + align256(sizeof(RenderDesc) * n_renders) +
-                          align256(sizeof(double) * 2 * n_renders) + 256 + 256;
+                          align256(sizeof(double) * 2 * n_renders) + 256 + 256 +
+                          align256(sizeof(pgs_gaussians) * n_scenes);
     e = cudaMalloc(&b->arena_t, tbytes);
     if (e != cudaSuccess) return fail(cuda_err(e));
     {
@@ -805,6 +808,7 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         b->d_losses = c.take<double>(2 * n_renders);
         b->d_work = c.take<uint32_t>(2);
         b->d_step = c.take<int64_t>(1);
+        b->d_grads = c.take<pgs_gaussians>(n_scenes);
     }
     cudaStream_t s = b->stream;
     e = cudaMemsetAsync(b->arena_g, 0, gbytes, s);
@@ -849,8 +853,41 @@ void pgs_batch_destroy(pgs_batch* b) {
     delete b;
 }
 
+int pgs_render_batch(pgs_batch* b) {
+    if (!b) return PGS_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream;
+    b->launches += enqueue_render(b);
+    cudaMemsetAsync(b->d_work, 0, sizeof(uint32_t), s);
+    b->launches += launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc,
+                                          b->d_work, false, s, b->variant);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e);
+    b->rendered = true;
+    return PGS_OK;
+}
+
+int pgs_backward_batch(pgs_batch* b, const pgs_gaussians* grads) {
+    if (!b || !grads) return PGS_ERR_INVALID_ARG;
+    for (int k = 0; k < b->S; ++k) {
+        const pgs_gaussians& p = b->scenes[k].params;
+        if (!valid_gaussians(&grads[k]) || grads[k].n != p.n || grads[k].sh_degree != p.sh_degree)
+            return PGS_ERR_INVALID_ARG;
+    }
+    if (!b->rendered) return PGS_ERR_NO_RENDER;
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_grads, grads, sizeof(pgs_gaussians) * b->S, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sc.grad2d, 0, sizeof(float) * 9 * (size_t)b->items, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_work + 1, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_err(e);
+    b->launches += launch_composite_batch(b->d_renders, b->R, b->tiles, b->cfg.tile, b->buf, b->items, b->sc,
+                                          b->d_work + 1, true, s, b->variant);
+    b->launches += launch_bwd_batch(b->d_renders, b->d_scenes, b->S, b->deg, b->gauss, b->items, b->sc, b->d_grads, s);
+    return cuda_err(cudaGetLastError());
+}
+
 int pgs_batch_step(pgs_batch* b) {
     if (!b) return PGS_ERR_INVALID_ARG;
+    b->rendered = false;  // the step changes the parameters
     if (b->exec) {
         const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
         if (e != cudaSuccess) return cuda_err(e);

@@ -785,6 +785,49 @@ k_bwd_adam_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __rest
     }
 }
 
+// Batched projection backward without Adam: one thread per Gaussian of every scene; the
+// Gaussian's parameter gradient is summed over the scene's renders (views) in shared memory, row
+// by row, and added to the scene's gradient buffer grads[scene] (Eq. 10's scatter of every view
+// into the canonical parameter buffer).  Nothing is written when the pairs overflowed the capacity.
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock, 2)
+k_bwd_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __restrict__ scenes, int S,
+            int64_t gauss_total, int64_t items, Scratch sc, const pgs_gaussians* __restrict__ grads) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int ROWS = 11 + 3 * K;
+    extern __shared__ float s_acc[];  // [ROWS][kProjBlock]
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (*sc.status & kStatusCapacity) != 0;
+    const int64_t k = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    float* acc = s_acc + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] = 0.f;
+    __syncthreads();
+    if (k >= gauss_total || s_skip) return;
+    const int si = scene_of(scenes, S, k);
+    const SceneDesc& sd = scenes[si];
+    const int64_t i = k - sd.gauss_base;
+    const int64_t n = sd.params.n;
+    bool any = false;
+    for (int rr = 0; rr < sd.n_renders; ++rr) {
+        const RenderDesc& rd = renders[sd.first_render + rr];
+        const int64_t j = rd.item_base + i;
+        if (sc.touched[j] == 0) continue;
+        any = true;
+        GradParts gp;
+        chain<DEG>(sd.params, rd.cam, sc.grad2d, items, j, i, gp);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) acc[r * kProjBlock] += grad_row<DEG>(gp, r);
+    }
+    if (!any) return;
+    const Rows Gg = rows_of(grads[si]);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int64_t idx = (int64_t)row_sub(r) * n + i;
+        Gg.g[row_group(r)][idx] += acc[r * kProjBlock];
+    }
+}
+
 }  // namespace
 
 int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY, int T,
@@ -887,6 +930,36 @@ int launch_bwd_adam_batch(const RenderDesc* renders, const SceneDesc* scenes, in
         case 1: return launch_bwd_adam_batch_deg<1>(renders, scenes, S, gauss_total, items, sc, a, step, s);
         case 2: return launch_bwd_adam_batch_deg<2>(renders, scenes, S, gauss_total, items, sc, a, step, s);
         default: return launch_bwd_adam_batch_deg<3>(renders, scenes, S, gauss_total, items, sc, a, step, s);
+    }
+}
+
+}  // namespace pgs
+
+namespace pgs {
+
+template <int DEG>
+static int launch_bwd_batch_deg(const RenderDesc* renders, const SceneDesc* scenes, int S, int64_t gauss_total,
+                                int64_t items, const Scratch& sc, const pgs_gaussians* grads, cudaStream_t s) {
+    constexpr int ROWS = 11 + 3 * (DEG + 1) * (DEG + 1);
+    const size_t smem = sizeof(float) * ROWS * kProjBlock;
+    static bool attr = [&] {
+        cudaFuncSetAttribute(k_bwd_batch<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return true;
+    }();
+    (void)attr;
+    const int64_t blocks = (gauss_total + kProjBlock - 1) / kProjBlock;
+    k_bwd_batch<DEG><<<(unsigned)blocks, kProjBlock, smem, s>>>(renders, scenes, S, gauss_total, items, sc, grads);
+    return 1;
+}
+
+int launch_bwd_batch(const RenderDesc* renders, const SceneDesc* scenes, int S, int deg, int64_t gauss_total,
+                     int64_t items, const Scratch& sc, const pgs_gaussians* grads, cudaStream_t s) {
+    if (gauss_total == 0) return 0;
+    switch (deg) {
+        case 0: return launch_bwd_batch_deg<0>(renders, scenes, S, gauss_total, items, sc, grads, s);
+        case 1: return launch_bwd_batch_deg<1>(renders, scenes, S, gauss_total, items, sc, grads, s);
+        case 2: return launch_bwd_batch_deg<2>(renders, scenes, S, gauss_total, items, sc, grads, s);
+        default: return launch_bwd_batch_deg<3>(renders, scenes, S, gauss_total, items, sc, grads, s);
     }
 }
 

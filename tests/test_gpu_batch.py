@@ -150,6 +150,57 @@ def test_batch_sh3_uneven_against_oracle(mods):
         assert np.all(np.abs(dp_gpu - dp_ora)[clear] <= 1e-6 + 1e-3 * np.abs(dp_ora)[clear])
 
 
+def test_split_batch_calls_dssim_against_oracle(mods):
+    """pgs_render_batch, the caller's L1 + D-SSIM gradient of every render (pgs_loss_dssim), and
+    pgs_backward_batch at SH3 over uneven scenes: every render against the oracle (every pixel),
+    each scene's gradient (summed over its views, Eq. 10's scatter) against the sum of the oracle's
+    backward of the oracle's own D-SSIM gradient of its image; the two calls change no parameter."""
+    R, B, _, L = mods
+    from oracle import ssim as OS
+    scenes, views = uneven_sh3_batch()
+    bt, bufs = make_trainer(mods, scenes, views)
+    p0 = [b.data.clone() for b in bufs]
+    bt.render()
+    lossr = R.Rasterizer()
+    for k in range(len(views)):
+        lossr.loss_dssim(bt.images[k], bt.targets[k], 0.2, grad=bt.dls[k])
+    grads = [b.zeros_like() for b in bufs]
+    bt.backward(grads)
+    torch.cuda.synchronize()
+    assert bt.status()[0] == 0
+    for x, y in zip(p0, bufs):
+        assert torch.equal(x, y.data)
+    for s, sc in enumerate(scenes):
+        g = sc.init
+        total, keep = None, np.ones(g.n, bool)
+        rast = R.Rasterizer()
+        for k, (vs, cam, tgt) in enumerate(views):
+            if vs != s:
+                continue
+            img = bt.images[k].cpu().numpy()
+            assert np.array_equal(rast.render(R.GaussianBuffer.from_arrays(g), cam).cpu().numpy(), img)
+            ora, forced = check_render(rast, g, cam, img)
+            _, _, dl = OS.loss_and_grad(ora["image"], np.asarray(tgt, np.float64), 0.2)
+            _, og = oracle.backward(g, cam, dl, forced=forced)
+            total = og if total is None else {q: total[q] + og[q] for q in og}
+            keep &= oracle.gaussian_flags(g, cam) == 0
+        compare_grads(grads[s].numpy(), total, keep)
+
+
+def test_backward_batch_needs_a_render(mods):
+    R, B, _, L = mods
+    scenes, views = small_batch(7)
+    bt, bufs = make_trainer(mods, scenes, views)
+    with pytest.raises(L.PgsError) as e:
+        bt.backward([b.zeros_like() for b in bufs])
+    assert e.value.code == L.PGS_ERR_NO_RENDER
+    bt.render()
+    bt.step()  # a step changes the parameters: the render is stale
+    with pytest.raises(L.PgsError) as e:
+        bt.backward([b.zeros_like() for b in bufs])
+    assert e.value.code == L.PGS_ERR_NO_RENDER
+
+
 def test_graph_replay_equals_eager_steps(mods):
     scenes, views = small_batch(2)
     a, pa = make_trainer(mods, scenes, views)
