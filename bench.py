@@ -78,8 +78,8 @@ def parse():
                     help="skip the batched 16-scene x 4-view, initializer, replay-cache and D-SSIM measurements")
     ap.add_argument("--batched-steps", type=int, default=60)
     ap.add_argument("--profile-run", action="store_true",
-                    help="short run for a profiler: one capacity probe, random targets, --steps "
-                         "steps, few launches before them; prints no bench line")
+                    help="short run for a profiler: the autotuner's configuration, one capacity probe, "
+                         "random targets, --steps steps; prints no bench line")
     return ap.parse_args()
 
 
@@ -752,22 +752,27 @@ def run_ours(args):
 
 def run_profile(args):
     import torch
+    from paper_2601_17354_gb300 import autotune as A
     from paper_2601_17354_gb300 import rasterizer as R
     torch.cuda.set_device(0)
     sc, cams = make_workload()
     params = R.GaussianBuffer.from_arrays(sc.init)
-    probe = R.Rasterizer()
+    # the benchmark's launch configuration: the autotuner's tile edge and variants
+    cand, tile, tuned = A.tune_rasterizer_tile(params, cams[0], torch.ones(3, HEIGHT, WIDTH, device="cuda") * 1e-6)
+    cand.close()
+    probe = R.Rasterizer(tile=tile)
     probe.render(params, cams[0])
     cap = int(probe.check_status() * 1.5) + 4096
     del probe
-    rast = R.Rasterizer(pair_capacity=cap)
+    rast = R.Rasterizer(pair_capacity=cap, tile=tile)
+    tuned.apply(rast)
     tr = R.Trainer(params, rast)
     target = torch.rand(3, HEIGHT, WIDTH, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
     for k in range(args.steps):
         tr.step(cams[0], target)
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": True, "steps": args.steps, "status": rast.status()[0],
-                      "launches": rast.launch_count()}))
+                      "launches": rast.launch_count(), "tile": tile, "forward": tuned.fwd, "backward": tuned.bwd}))
 
 
 def main():

@@ -43,6 +43,7 @@ extern "C" {
 #define PGS_ERR_INTERNAL (-8)    /* a device-side consistency check failed (access skipped) */
 #define PGS_ERR_TOO_LARGE (-9)   /* size beyond the fixed scratch of pgs_sort_pairs_static */
 #define PGS_ERR_NOT_PD (-10)     /* bundle adjustment: damped reduced system not positive definite */
+#define PGS_ERR_TIMEOUT (-11)    /* a bounded device-side wait ran out (the sort's look-back): results undefined */
 
 typedef struct pgs_ctx pgs_ctx;
 
@@ -227,7 +228,7 @@ int64_t pgs_launch_count(const pgs_ctx* ctx);
    bits of count (key, value) pairs (higher key bits never take part in the order; keys_out keeps
    them as they were): keys_in/vals_in (device, read only) -> keys_out/vals_out (device, caller
    owned, not overlapping the inputs).  It allocates nothing: its scratch is one file-scope device
-   array of 3.2 MB, held by every GPU that loads the library until the process exits.
+   array of 3.8 MB, held by every GPU that loads the library until the process exits.
    count must be at most 262144 (PGS_ERR_TOO_LARGE otherwise); key_bits in 1..64.  The first call
    on a device looks the scratch address up (cudaGetSymbolAddress) with that device current; make
    that first call before any stream capture.  Every call shares the one scratch array, which
@@ -501,6 +502,14 @@ int pgs_mvs_read(pgs_mvs* mvs, int32_t what, void* dst, int64_t bytes);
    PGS_ERR_CAPACITY when that exceeds capacity (the first `capacity` are written).  Synchronises. */
 int pgs_mvs_fuse(pgs_mvs* mvs, const pgs_camera* target, const float* depth, float* points, int32_t* pixels,
                  int64_t capacity, int64_t* count);
+
+/* Failure-detection self-test of the sort's bounded waits: one pass of the pair sort runs on the
+   context's scratch with the first tile's look-back words never published, so the next tile's wait
+   runs out (about a second), records the timeout in the device status word and abandons the pass
+   without writing.  Synchronises; returns what pgs_status then reads (PGS_ERR_TIMEOUT when the
+   detection works) and clears it.  The context stays usable; its last render is invalidated.
+   No paper counterpart. */
+int pgs_selftest_timeout(pgs_ctx* ctx);
 
 /* Static description of an error code. */
 const char* pgs_strerror(int code);

@@ -23,6 +23,7 @@ PGS_ERR_OOM = -7
 PGS_ERR_INTERNAL = -8
 PGS_ERR_TOO_LARGE = -9
 PGS_ERR_NOT_PD = -10
+PGS_ERR_TIMEOUT = -11
 
 PGS_MVS_CENSUS_TARGET = 0
 PGS_MVS_CENSUS_REFERENCE = 1
@@ -56,7 +57,8 @@ EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_
             "pgs_ba_create", "pgs_ba_destroy", "pgs_ba_project", "pgs_ba_step", "pgs_ba_solve", "pgs_ba_stage_times",
             "pgs_mvs_create", "pgs_mvs_destroy", "pgs_mvs_depth_range", "pgs_mvs_select_reference",
             "pgs_mvs_depth", "pgs_mvs_read", "pgs_mvs_fuse", "pgs_mvs_stage_times",
-            "pgs_trace_pixels", "pgs_sort_pairs_static_status", "pgs_render_batch", "pgs_backward_batch"]
+            "pgs_trace_pixels", "pgs_sort_pairs_static_status", "pgs_render_batch", "pgs_backward_batch",
+            "pgs_selftest_timeout"]
 
 VARIANTS = [(p, d) for p in (1, 2, 4) for d in (64, 128, 256)]
 
@@ -147,6 +149,8 @@ def lib():
             L.pgs_batch_create.restype = I
             L.pgs_batch_destroy.argtypes = [P]
             L.pgs_batch_destroy.restype = None
+            L.pgs_selftest_timeout.argtypes = [P]
+            L.pgs_selftest_timeout.restype = I
             L.pgs_render_batch.argtypes = [P]
             L.pgs_render_batch.restype = I
             L.pgs_backward_batch.argtypes = [P, C.POINTER(PgsGaussians)]

@@ -81,7 +81,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.dkeys[1] = c.take<unsigned long long>(n);
     sc.dvals[0] = c.take<uint32_t>(n);
     sc.dvals[1] = c.take<uint32_t>(n);
-    sc.dhist = c.take<uint32_t>((size_t)kRadix * ((n + kDepthTile - 1) / kDepthTile));
+    sc.dhist = c.take<uint32_t>(lookback_words(32 / kRadixBits, (n + kDepthTile - 1) / kDepthTile));
     sc.dtotals = c.take<uint32_t>(kTotalWords);
     sc.dcount = c.take<unsigned long long>(1);
     sc.dblocks = c.take<uint32_t>(1);
@@ -106,7 +106,7 @@ size_t carve_p(Scratch& sc, char* base, int64_t pairs) {
     sc.keys[1] = c.take<unsigned long long>(pairs);
     sc.vals[0] = c.take<uint32_t>(pairs);
     sc.vals[1] = c.take<uint32_t>(pairs);
-    sc.sort_hist = c.take<uint32_t>((size_t)kRadix * (sb ? sb : 1));
+    sc.sort_hist = c.take<uint32_t>(lookback_words(32 / kRadixBits, sb ? sb : 1));  // tile ids: at most 4 passes
     return c.off;
 }
 
@@ -233,6 +233,7 @@ const char* pgs_strerror(int code) {
         case PGS_ERR_INTERNAL: return "device-side consistency check failed";
         case PGS_ERR_NOT_PD: return "bundle adjustment: damped reduced camera system not positive definite";
         case PGS_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free sort (262144 pairs)";
+        case PGS_ERR_TIMEOUT: return "a bounded wait on the device ran out; the work it guarded was abandoned";
         default: return "unknown error";
     }
 }
@@ -468,6 +469,7 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
     if (e != cudaSuccess) return cuda_err(e);
     if (pairs_needed) *pairs_needed = (int64_t)P;
     if (st & kStatusInternal) return PGS_ERR_INTERNAL;
+    if (st & kStatusTimeout) return PGS_ERR_TIMEOUT;
     if (st & kStatusCapacity) return PGS_ERR_CAPACITY;
     if (st & kStatusNonfinite) return PGS_ERR_NONFINITE;
     return PGS_OK;
@@ -482,6 +484,17 @@ int pgs_trace_pixels(pgs_ctx* ctx, const int32_t* pixels, int64_t npix, int32_t 
     ctx->launches += launch_trace_pixels(ctx->cam, ctx->TX, ctx->tile, ctx->buf, ctx->n, ctx->sc, pixels, npix,
                                          max_entries, og, code, count, T_final, last, ncomp, ctx->stream);
     return cuda_err(cudaGetLastError());
+}
+
+int pgs_selftest_timeout(pgs_ctx* ctx) {
+    if (!ctx) return PGS_ERR_INVALID_ARG;
+    int rc = reserve_p(ctx, 3 * (int64_t)kSortTile > ctx->cap_pairs ? 3 * (int64_t)kSortTile : ctx->cap_pairs);
+    if (rc != PGS_OK) return rc;
+    ctx->has_render = false;
+    ctx->launches += launch_timeout_selftest(ctx->cap_pairs, ctx->sc, ctx->stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e);
+    return pgs_status(ctx, nullptr);
 }
 
 int pgs_profile(pgs_ctx* ctx, int enable) {
@@ -991,6 +1004,7 @@ int pgs_batch_status(pgs_batch* b, int64_t* pairs) {
     if (e != cudaSuccess) return cuda_err(e);
     if (pairs) *pairs = (int64_t)P;
     if (st & kStatusInternal) return PGS_ERR_INTERNAL;
+    if (st & kStatusTimeout) return PGS_ERR_TIMEOUT;
     if (st & kStatusCapacity) return PGS_ERR_CAPACITY;
     if (st & kStatusNonfinite) return PGS_ERR_NONFINITE;
     return PGS_OK;

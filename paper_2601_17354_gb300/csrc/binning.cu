@@ -17,9 +17,9 @@
 // The radix sort is least-significant-digit first, 8-bit digits, over the bits that can be
 // non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; the
 // caller's low key bits of the 64-bit keys of the allocation-free entry point); the last digit is
-// masked to what is left of the bit range.  Each pass: per-CTA digit histogram,
-// per-digit scan across CTAs (digit totals come from one up-front histogram of all passes),
-// and a stable scatter that ranks keys inside a CTA with warp ballots (no inter-CTA waiting).
+// masked to what is left of the bit range.  The digit totals of every pass come from one up-front
+// histogram; each pass is then one launch that ranks a tile's keys with warp ballots and finds the
+// tile's place by decoupled look-back over the tiles before it (bounded waits, see k_onesweep).
 #include "pgs_internal.cuh"
 
 namespace pgs {
@@ -236,121 +236,66 @@ k_digit_totals(int64_t capacity, int first_shift, int passes, uint32_t last_mask
     }
 }
 
-// per-CTA histogram of one digit (CTA tiles of kSortThreads x kItems keys)
-template <typename KeyT, int kItems>
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_hist(int64_t capacity, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ keys, Scratch sc) {
-    constexpr int kTile = kSortThreads * kItems;
-    const uint32_t nblk = *sc.sort_blocks;
-    if (blockIdx.x >= nblk) return;
-    __shared__ uint32_t h[kRadix];
-    h[threadIdx.x] = 0;  // kSortThreads == kRadix
-    __syncthreads();
-    const uint64_t P = kept_pairs(sc, capacity);
-    const uint64_t begin = (uint64_t)blockIdx.x * kTile;
-    const uint64_t end = begin + kTile < P ? begin + kTile : P;
-    for (uint64_t k = begin + threadIdx.x; k < end; k += kSortThreads)
-        atomicAdd(&h[(uint32_t)(keys[k] >> shift) & dmask], 1u);
-    __syncthreads();
-    sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x] = h[threadIdx.x];
-}
-
-// one CTA per digit: exclusive scan of that digit's per-CTA counts, offset by the total of all
-// smaller digits (summed over the partial copies of the totals); in place (counts -> scatter
-// offsets); each thread scans kRowItems consecutive counts per round
-constexpr int kRowItems = 8;
-
-__global__ void __launch_bounds__(kSortThreads)
-k_sort_rowscan(int pass, int sb_max, Scratch sc) {
-    const int d = blockIdx.x;
-    const uint32_t nblk = *sc.sort_blocks;
-    __shared__ uint32_t s_warp[kSortThreads / 32];
-    __shared__ uint32_t s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {   // total of digits < d: thread t sums copy t mod 16 over digits t / 16, t / 16 + 16, ...
-        static_assert(kSortThreads % kTotalCopies == 0, "copies per thread stride");
-        constexpr int kStep = kSortThreads / kTotalCopies;
-        const uint32_t* tot = sc.digit_totals + (threadIdx.x % kTotalCopies) * (kMaxPasses * kRadix) + pass * kRadix;
-        uint32_t acc = 0;
-        for (int k = threadIdx.x / kTotalCopies; k < d; k += kStep) acc += tot[k];
-        acc = __reduce_add_sync(kFull, acc);
-        if (lane == 0) s_warp[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) c += s_warp[w];
-            s_carry = c;
-        }
-        __syncthreads();
-    }
-    uint32_t* row = sc.sort_hist + (size_t)d * sb_max;
-    for (uint32_t base = 0; base < nblk; base += kSortThreads * kRowItems) {
-        const uint32_t i0 = base + threadIdx.x * kRowItems;
-        uint32_t v[kRowItems], mine = 0;
-#pragma unroll
-        for (int j = 0; j < kRowItems; ++j) {
-            v[j] = i0 + j < nblk ? row[i0 + j] : 0u;
-            mine += v[j];
-        }
-        uint32_t incl = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        uint32_t wpre = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) {
-            wpre += w < warp ? s_warp[w] : 0u;
-            total += s_warp[w];
-        }
-        uint32_t run = s_carry + wpre + incl - mine;
-#pragma unroll
-        for (int j = 0; j < kRowItems; ++j) {
-            if (i0 + j < nblk) row[i0 + j] = run;
-            run += v[j];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += total;
-        __syncthreads();
-    }
-}
-
-// stable scatter of one CTA's keys by one digit: rank each key among the CTA's keys of its
+// One pass of the sort in one launch (decoupled look-back): a CTA takes the next tile of
+// kSortThreads x kItems keys from a ticket (so every tile before it belongs to a CTA already
+// running), counts its keys per digit in shared memory and publishes those counts at once, so the
+// tiles after it can add them up before it has finished.  It then ranks its keys by the pass's
 // digit (per 32 consecutive keys the lanes of equal digit from one ballot per digit bit, warp
-// prefixes per digit), reorder the CTA's
-// keys by digit in shared memory, then write each digit's run to its global offset, so the
-// global writes are contiguous runs instead of one scattered store per key.
+// prefixes per digit) and adds up the counts of the tiles before it by walking back until a tile
+// that has published its inclusive prefix.  Each wait on a tile that has not published yet is
+// bounded: past kSpinLimit polls (about a second) the CTA records kStatusTimeout, raises the sort's
+// abort word, which ends every other wait at once, and leaves its keys unwritten.  The keys are
+// then reordered by digit in shared memory and each digit's run written to its global offset
+// (digits of smaller value from the pass's totals + the run of the tiles before), so the global
+// writes are contiguous runs.
+//
+// Look-back words: value | flag << 30, flag 1 = the tile's own count, 2 = inclusive prefix of the
+// tiles up to it; 0 = not yet published (the region is cleared before every sort).
+constexpr uint32_t kLbCount = 1u << 30, kLbPrefix = 2u << 30, kLbValue = (1u << 30) - 1u;
+constexpr int kSpinLimit = 1 << 20;  // with the back-off below, about half a second
+constexpr int kLbWindow = 8;
 constexpr int kSortWarps = kSortThreads / 32;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <typename KeyT, int kItems>
 constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSortThreads * kItems; }
 
 template <typename KeyT, int kItems>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_scatter(int64_t capacity, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ kin,
-               const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
-               Scratch sc) {
+k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ kin,
+           const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout, Scratch sc) {
     constexpr int kTile = kSortThreads * kItems;        // keys per CTA
     constexpr int kWarpItems = kTile / kSortWarps;      // contiguous keys per warp
     constexpr int kRounds = kWarpItems / 32;            // == kItems
-    const uint32_t nblk = *sc.sort_blocks;
-    if (blockIdx.x >= nblk) return;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     KeyT* s_keys = reinterpret_cast<KeyT*>(s_dyn);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KeyT) * kTile);
     __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
-    __shared__ uint32_t s_gofs[kRadix];            // global offset of this CTA's run of digit d
+    __shared__ uint32_t s_gofs[kRadix];            // global offset of this tile's run of digit d
     __shared__ uint32_t s_bstart[kRadix];          // start of digit d inside the CTA's reordering
     __shared__ uint32_t s_part[kSortWarps];
+    __shared__ uint32_t s_hist[kRadix];            // the tile's count of digit d
+    __shared__ uint32_t s_tile;
+    uint32_t* head = sc.sort_hist;  // [0] abort word, [1 + pass] ticket of the pass, then the look-back
+    uint32_t* lb = sc.sort_hist + kLookbackHead + (size_t)pass * kRadix * sb_max;
+    const uint32_t nblk = *sc.sort_blocks;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&head[1 + pass], 1u);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
-    s_gofs[threadIdx.x] = sc.sort_hist[(size_t)threadIdx.x * sb_max + blockIdx.x];
+    s_hist[threadIdx.x] = 0;
     __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= nblk) return;
     const uint64_t P = kept_pairs(sc, capacity);
-    const uint64_t cbase = (uint64_t)blockIdx.x * kTile;
+    const uint64_t cbase = (uint64_t)tile * kTile;
     const uint64_t wbase = cbase + (uint64_t)warp * kWarpItems;
     const unsigned lt = (1u << lane) - 1u;
     KeyT key[kRounds];
@@ -362,14 +307,28 @@ k_sort_scatter(int64_t capacity, int shift, uint32_t dmask, int sb_max, const Ke
         const bool valid = idx < P;
         key[r] = valid ? kin[idx] : (KeyT)0;
         val[r] = valid ? vin[idx] : 0u;
+    }
+    // the tile's digit counts, published before the ranking
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r)
+        if (wbase + (uint64_t)r * 32 + lane < P) atomicAdd(&s_hist[(uint32_t)(key[r] >> shift) & dmask], 1u);
+    __syncthreads();
+    uint32_t* const mine = lb + (size_t)tile * kRadix + threadIdx.x;
+    st_relaxed(mine, (tile == 0 ? kLbPrefix : kLbCount) | s_hist[threadIdx.x]);
+    const int nbits = __popc(dmask);  // dmask = 2^bits - 1: higher digit bits are zero
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
+        const bool valid = idx < P;
         const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & dmask : 0u;
         // lanes holding the same digit: one ballot per digit bit (and one for validity)
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
+        unsigned peers = __ballot_sync(kFull, valid);
         if (!valid) peers = ~peers;
 #pragma unroll
         for (int b = 0; b < kRadixBits; ++b) {
+            if (b >= nbits) break;  // warp-uniform
             const bool bit = (d >> b) & 1u;
-            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            const unsigned bal = __ballot_sync(kFull, bit);
             peers &= bit ? bal : ~bal;
         }
         uint32_t before = 0;
@@ -380,30 +339,84 @@ k_sort_scatter(int64_t capacity, int shift, uint32_t dmask, int sb_max, const Ke
         dr[r] = valid ? (d | ((before + __popc(peers & lt)) << 8)) : 0xffffffffu;
     }
     __syncthreads();
-    {   // thread = digit: warp prefixes and the CTA total of the digit
+    {   // thread = digit: warp prefixes, the tile's count of the digit, its look-back
         const int d = threadIdx.x;
         uint32_t acc = 0;
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = s_wh[w][d];
+            const uint32_t cnt = s_wh[w][d];
             s_wh[w][d] = acc;
-            acc += c;
+            acc += cnt;
         }
-        // exclusive scan of the digit totals across the CTA
-        uint32_t incl = acc;
+        uint32_t before = 0;  // keys of digit d in the tiles before this one
+        if (tile != 0) {
+            // kLbWindow predecessors per round, loaded together: the walk over tiles that have
+            // published only their count costs one memory latency per window, not per tile
+            int spins = 0;
+            int64_t t = (int64_t)tile - 1;
+            while (t >= 0) {
+                uint32_t w[kLbWindow];
+#pragma unroll
+                for (int k = 0; k < kLbWindow; ++k) w[k] = t - k >= 0 ? ld_relaxed(lb + (size_t)(t - k) * kRadix + d) : kLbPrefix;
+                int k = 0;
+                bool found = false;
+#pragma unroll
+                for (; k < kLbWindow; ++k) {
+                    const uint32_t flag = w[k] & ~kLbValue;
+                    if (flag == 0u) break;  // tile t - k has not published yet
+                    before += w[k] & kLbValue;
+                    if (flag == kLbPrefix) {
+                        found = true;
+                        break;
+                    }
+                }
+                if (found) break;
+                t -= k;
+                if (k == kLbWindow) continue;
+                // wait (bounded) for tile t, then take the next window from it
+                while ((ld_relaxed(lb + (size_t)t * kRadix + d) & ~kLbValue) == 0u) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(sc.status, kStatusTimeout);
+                        st_relaxed(head, 1u);
+                        break;
+                    }
+                    if ((spins & 63) == 0 && ld_relaxed(head) != 0u) break;  // another wait ran out
+                    __nanosleep(64);
+                }
+                if (ld_relaxed(head) != 0u) break;
+            }
+            st_relaxed(mine, kLbPrefix | (before + acc));
+        }
+        // offset of digit d in the pass's output: all keys of smaller digits + the tiles before
+        const uint32_t* tot = sc.digit_totals + pass * kRadix;
+        uint32_t all = 0;
+#pragma unroll
+        for (int cpy = 0; cpy < kTotalCopies; ++cpy) all += tot[(size_t)cpy * kMaxPasses * kRadix + d];
+        uint32_t incl_all = all, incl = acc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            const uint32_t ta = __shfl_up_sync(kFull, incl_all, o), tb = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) {
+                incl_all += ta;
+                incl += tb;
+            }
         }
-        if (lane == 31) s_part[warp] = incl;
+        if (lane == 31) s_part[warp] = incl_all;
         __syncthreads();
         uint32_t wpre = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
+        s_gofs[d] = wpre + incl_all - all + before;
+        __syncthreads();
+        if (lane == 31) s_part[warp] = incl;  // the tile's own digit counts, for its reordering
+        __syncthreads();
+        wpre = 0;
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
         s_bstart[d] = wpre + incl - acc;
     }
     __syncthreads();
+    if (ld_relaxed(head) != 0u) return;  // a wait ran out: the pass is abandoned (status recorded)
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         if (dr[r] != 0xffffffffu) {
@@ -527,12 +540,12 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch
 
 }  // namespace
 
-// the scatter reorders a whole CTA tile of keys in dynamic shared memory (32 KB with 4096 32-bit
-// keys, 48 KB with 4096 64-bit keys)
+// a pass reorders a whole CTA tile of keys in dynamic shared memory (32 KB with 4096 32-bit keys,
+// 48 KB with 4096 64-bit keys)
 template <typename KeyT, int kItems>
 void enable_scatter_smem() {
     static bool done = [] {
-        cudaFuncSetAttribute(k_sort_scatter<KeyT, kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_onesweep<KeyT, kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scatter_smem<KeyT, kItems>());
         return true;
     }();
@@ -541,8 +554,8 @@ void enable_scatter_smem() {
 
 // LSD passes over bits [first_shift, first_shift + bits) of the keys in keys[0] / keys[1] (viewed
 // as KeyT), 8 bits a pass (the last pass takes what is left: bits above the range never take part),
-// CTA tiles of kSortThreads x kItems keys; returns the launches and leaves the sorted buffer's
-// index in *out_buf
+// CTA tiles of kSortThreads x kItems keys: the digit totals of every pass in one read of the keys,
+// then one launch per pass.  Returns the launches and leaves the sorted buffer's index in *out_buf.
 template <typename KeyT, int kItems>
 int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf) {
     constexpr int kTile = kSortThreads * kItems;
@@ -558,18 +571,40 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     enable_scatter_smem<KeyT, kItems>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
     cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+    // abort word, tickets and the look-back words of every pass start cleared
+    cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * (kLookbackHead + (size_t)passes * kRadix * sb_max), s);
     k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
         const uint32_t dmask = p == passes - 1 ? last_mask : (uint32_t)(kRadix - 1);
-        k_sort_hist<KeyT, kItems><<<sb_max, kSortThreads, 0, s>>>(capacity, shift, dmask, sb_max, k[buf], sc);
-        k_sort_rowscan<<<kRadix, kSortThreads, 0, s>>>(p, sb_max, sc);
-        k_sort_scatter<KeyT, kItems><<<sb_max, kSortThreads, scatter_smem<KeyT, kItems>(), s>>>(
-            capacity, shift, dmask, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
+        k_onesweep<KeyT, kItems><<<sb_max, kSortThreads, scatter_smem<KeyT, kItems>(), s>>>(
+            capacity, p, shift, dmask, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }
     *out_buf = buf;
-    return 1 + 3 * passes;
+    return 1 + passes;
+}
+
+// One pass of the pair sort over three tiles whose first is never published: the ticket starts at
+// 1, so tile 1 waits on tile 0 until its bound runs out (failure-detection self-test).
+__global__ void k_selftest_setup(Scratch sc) {
+    *sc.pair_count = 3ull * kSortTile;
+    *sc.sort_blocks = 3u;
+    sc.sort_hist[1] = 1u;  // the pass's ticket: tile 0 is never taken
+}
+
+int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s) {
+    if (capacity < 3 * (int64_t)kSortTile) return 0;
+    enable_scatter_smem<uint32_t, kSortItems>();
+    const int sb_max = (int)((capacity + kSortTile - 1) / kSortTile);
+    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+    cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * lookback_words(1, sb_max), s);
+    k_selftest_setup<<<1, 1, 0, s>>>(sc);
+    uint32_t* k0 = reinterpret_cast<uint32_t*>(sc.keys[0]);
+    uint32_t* k1 = reinterpret_cast<uint32_t*>(sc.keys[1]);
+    k_onesweep<uint32_t, kSortItems><<<2, kSortThreads, scatter_smem<uint32_t, kSortItems>(), s>>>(
+        capacity, 0, 0, kRadix - 1, sb_max, k0, sc.vals[0], k1, sc.vals[1], sc);
+    return 2;
 }
 
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {

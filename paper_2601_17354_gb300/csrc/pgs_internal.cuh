@@ -15,7 +15,7 @@ constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kern
 constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
 constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels of the pairs
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort CTA
-constexpr int kDepthItems = 4;       // keys per thread in the depth sort (more, shorter CTAs)
+constexpr int kDepthItems = 8;       // keys per thread in the depth sort (more, shorter CTAs)
 constexpr int kDepthTile = kSortThreads * kDepthItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -29,6 +29,11 @@ constexpr int kTotalWords = kTotalCopies * kMaxPasses * kRadix;
 constexpr int32_t kStatusCapacity = 1;
 constexpr int32_t kStatusNonfinite = 2;
 constexpr int32_t kStatusInternal = 4;  // an index failed its bounds check; the access was skipped
+constexpr int32_t kStatusTimeout = 8;   // a bounded wait on another CTA ran out; its work was abandoned
+// words before the look-back region of a sort's scratch: an abort word and one ticket per pass
+constexpr int kLookbackHead = 16;
+// scratch words of a sort's look-back for `passes` passes over `tiles` CTA tiles
+constexpr size_t lookback_words(int passes, int64_t tiles) { return kLookbackHead + (size_t)passes * 256 * tiles; }
 
 // Per-Gaussian projected record read by the compositing kernels (gathered by canonical index).
 //   xyo   = (u, v, opacity, unused)   screen-space mean and opacity
@@ -64,14 +69,14 @@ struct Scratch {
     // its pair count / CTA count words and histograms, separate from the pair sort's
     unsigned long long* dkeys[2] = {nullptr, nullptr};
     uint32_t* dvals[2] = {nullptr, nullptr};
-    uint32_t* dhist = nullptr;
+    uint32_t* dhist = nullptr;  // the depth sort's look-back
     uint32_t* dtotals = nullptr;
     unsigned long long* dcount = nullptr;
     uint32_t* dblocks = nullptr;
     // per pair (separate allocation, grows independently)
     unsigned long long* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
-    uint32_t* sort_hist = nullptr;  // [kRadix][sort_blocks_max]
+    uint32_t* sort_hist = nullptr;  // the sort's look-back: head words, then [passes][tiles][kRadix]
 };
 
 constexpr int kLossBlocks = 1024;
@@ -196,6 +201,10 @@ int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t 
 // at most `capacity`); the digit totals must be zero on entry.
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,
                            int* out_buf);
+
+// Failure-detection self-test: one sort pass whose first tile is never published (the next tile's
+// bounded wait runs out and records kStatusTimeout); needs a pair capacity of three sort tiles.
+int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s);
 
 // Order the tiles by decreasing list length (quarter-octave buckets), so the compositing grids
 // start the heaviest tiles first.

@@ -16,18 +16,18 @@ constexpr int64_t kStaticMaxPairs = int64_t(1) << 18;  // 262,144 pairs
 constexpr int64_t kStaticSortBlocks = kStaticMaxPairs / kSortTile;
 constexpr int kMaxDevices = 64;
 
-// scratch layout (bytes): other ping-pong keys, other ping-pong values, per-CTA digit counts,
-// digit totals of every pass, pair count, sort CTA count, status word
+// scratch layout (bytes): other ping-pong keys, other ping-pong values, the sort's look-back
+// words (8 passes of 64-bit keys), digit totals of every pass, pair count, sort CTA count, status word
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + sizeof(unsigned long long) * kStaticMaxPairs;
 constexpr size_t kOffHist = kOffVals + sizeof(uint32_t) * kStaticMaxPairs;
-constexpr size_t kOffTotals = kOffHist + sizeof(uint32_t) * kRadix * kStaticSortBlocks;
+constexpr size_t kOffTotals = kOffHist + sizeof(uint32_t) * lookback_words(kMaxPasses, kStaticSortBlocks);
 constexpr size_t kOffCount = kOffTotals + sizeof(uint32_t) * kTotalWords;
 constexpr size_t kOffBlocks = kOffCount + sizeof(unsigned long long);
 constexpr size_t kOffStatus = kOffBlocks + sizeof(uint32_t);
 constexpr size_t kScratchBytes = (kOffStatus + sizeof(int32_t) + 255) & ~size_t(255);
 
-// Held by every GPU that loads the library until the process exits (3.2 MB).
+// Held by every GPU that loads the library until the process exits (3.8 MB).
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
 // Per-call set-up on the device: pair count, active sort CTAs, cleared totals.  The status word

@@ -271,6 +271,11 @@ class Rasterizer:
                     T=T.cpu().numpy(), last=last.cpu().numpy().astype(np.uint32),
                     ncomp=ncomp.cpu().numpy().astype(np.uint32))
 
+    def selftest_timeout(self) -> int:
+        """Failure-detection self-test of the sort's bounded waits (about a second); returns the
+        status code it reads (PGS_ERR_TIMEOUT when the detection works)."""
+        return int(self._lib.pgs_selftest_timeout(self._ctx))
+
     def launch_count(self) -> int:
         return int(self._lib.pgs_launch_count(self._ctx))
 

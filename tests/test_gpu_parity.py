@@ -366,6 +366,21 @@ def test_capacity_overflow_is_reported_then_fits(R):
     compare_forward(img, T, last, oracle.render(g, cam), (exact, g, cam, 16))
 
 
+def test_sort_wait_that_runs_out_is_reported_and_the_context_recovers(R):
+    """The sort's look-back waits are bounded: a pass whose first tile is never published (the
+    self-test withholds it) ends with PGS_ERR_TIMEOUT instead of hanging, and the same context then
+    renders the tiny scene with keys, values and ranges bit-exact."""
+    from paper_2601_17354_gb300 import _lib as L
+    g, cam = SCENES["tiny_2k_128"]()
+    rast = R.Rasterizer()
+    assert rast.selftest_timeout() == L.PGS_ERR_TIMEOUT
+    assert rast.status()[0] == 0  # read and cleared by the self-test
+    rast, _, img, T, last, code, pairs = render_gpu(R, g, cam, rast)
+    assert code == 0
+    assert pairs == check_keys(rast, g, cam)
+    compare_forward(img, T, last, oracle.render(g, cam), (rast, g, cam, 16))
+
+
 def test_backward_without_render_is_an_error(R):
     from paper_2601_17354_gb300 import _lib as L
     rast = R.Rasterizer()
