@@ -99,9 +99,13 @@ int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t 
    transmittance below 1e-4), and write image_out [3][H][W] = colour + T_final * bg.
    The context keeps, for pgs_backward, the projected Gaussians, the sorted pairs, the tile
    ranges, T_final [H][W] and last [H][W] (1 + list position of the last composited entry).
-   If the pair count exceeds the capacity the image is undefined and pgs_status reports
-   PGS_ERR_CAPACITY with the count needed; with pair_capacity = 0 the context instead reads the
-   count back (one synchronisation) and grows before compositing. */
+   The lists are built in two levels (Gaussians to super-tiles of 8 x 4 tiles, then to tiles), so
+   besides the P pairs the pair buffers also hold the coarse stage's entries and counters; the
+   capacity a render needs is max(P, its coarse entries, 32 counters per block of 256 of them),
+   which is P on every scene but ones with very few pairs per super-tile.  If the capacity is too
+   small the image is undefined and pgs_status reports PGS_ERR_CAPACITY with the capacity needed;
+   with pair_capacity = 0 the context instead reads that back (one synchronisation) and grows
+   before compositing. */
 int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out);
 
 /* L1 photometric loss of Sec. IV's training loop (the paper names no loss): for n = 3 H W values,
@@ -145,7 +149,7 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
 
 /* Synchronise the context's stream, return the first error recorded on the device since the
    last call (PGS_OK if none) and clear it.  *pairs_needed (optional) receives the pair count of
-   the last render. */
+   the last render, or with PGS_ERR_CAPACITY the pair capacity it needs. */
 int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
 
 /* The paper's replay cache (Sec. III-C, Eq. 9: the per-pixel record S of the forward, with its
@@ -161,10 +165,11 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed);
 int pgs_set_replay_cache(pgs_ctx* ctx, int32_t k_max);
 
 /* Internal buffers of the last render/backward, copied to `dst` (host or device) for inspection.
-   which: PGS_BUF_KEYS (uint64 [P], sorted keys (tile << 32) | depth bits, assembled from the
-   sorted tile ids and the Gaussians' depths), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
-   (uint32 [tiles][2]), PGS_BUF_T_FINAL (float [H][W]), PGS_BUF_LAST (uint32 [H][W]),
-   PGS_BUF_GRAD2D (float [9][n]: du, dv, d conic a, b, c, d opacity, d r, g, b),
+   which: PGS_BUF_KEYS (uint64 [P], sorted keys (tile << 32) | depth bits, assembled on the host
+   from the lists and the Gaussians' depths), PGS_BUF_VALUES (uint32 [P]), PGS_BUF_RANGES
+   (uint32 [tiles][2]) -- these three in the order of the stable sort of the pairs by key (tiles
+   row-major, an empty tile (0, 0)), whatever layout the render's buffers use --
+   PGS_BUF_T_FINAL (float [H][W]), PGS_BUF_LAST (uint32 [H][W]), PGS_BUF_GRAD2D (float [9][n]: du, dv, d conic a, b, c, d opacity, d r, g, b),
    PGS_BUF_TILES_TOUCHED (uint32 [n]), PGS_BUF_NCOMP (uint32 [H][W], entries composited per
    pixel).  Copies min(max_bytes, size) bytes, stores the full size in
    *bytes, synchronises. */
@@ -199,8 +204,8 @@ int pgs_trace_pixels(pgs_ctx* ctx, const int32_t* pixels, int64_t npix, int32_t 
    events on the context's stream at its stage boundaries; pgs_stage_times synchronises, writes
    the total milliseconds and the number of timed executions of each stage since the previous
    read into ms[PGS_NUM_STAGES] and counts[PGS_NUM_STAGES], and resets the accumulators.
-   Stages: projection (K1), binning = scan + key emission (K2, K3), sort = radix sort + tile
-   ranges (K4, K5), compositing forward (K6), loss (K7), compositing backward (K8), projection
+   Stages: projection (K1), binning = depth sort + pair count (K2), sort = coarse entries, their
+   radix sort by super-tile and the tile lists + ranges (K3-K5), compositing forward (K6), loss (K7), compositing backward (K8), projection
    backward (K9), Adam (K10), fused projection backward + Adam (pgs_backward_step).
    pgs_profile(ctx, 0) stops recording. */
 #define PGS_STAGE_PROJECT 0

@@ -3,6 +3,7 @@
 // Scratch lives in two device arenas owned by the context: one sized by (Gaussians, pixels,
 // tiles) and one by the pair capacity, so growing the pair buffers never disturbs projected
 // Gaussians of the render in flight.  Buffers are carved at 256-byte alignment.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -18,7 +19,7 @@ struct pgs_ctx {
     Scratch sc;
     void* arena_g = nullptr;
     void* arena_p = nullptr;
-    int64_t cap_n = -1, cap_pixels = -1, cap_tiles = -1, cap_pairs = 0;
+    int64_t cap_n = -1, cap_pixels = -1, cap_tiles = -1, cap_supers = -1, cap_pairs = 0;
     bool grow_pairs = false;
     // last render
     bool has_render = false;
@@ -64,7 +65,7 @@ struct Carver {
 };
 
 // Layout of the (Gaussians, pixels, tiles) arena; with base == nullptr only measures.
-size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles) {
+size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles, int64_t supers) {
     Carver c{base};
     const int64_t nb = (n + kProjBlock - 1) / kProjBlock;
     sc.xyo = c.take<float4>(n);
@@ -76,6 +77,11 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.touched = c.take<uint32_t>(n);
     sc.block_sums = c.take<uint32_t>(nb);
     sc.block_offsets = c.take<unsigned long long>(nb);
+    sc.crange = c.take<uint2>(supers);
+    sc.vbase = c.take<uint32_t>(supers + 1);
+    sc.stt = c.take<uint32_t>(32 * supers);
+    sc.ssum = c.take<uint32_t>(supers);
+    sc.sbase = c.take<uint32_t>(supers + 1);
     sc.grad2d = c.take<float>(9 * n);
     sc.dkeys[0] = c.take<unsigned long long>(n);
     sc.dkeys[1] = c.take<unsigned long long>(n);
@@ -92,6 +98,8 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.ncomp = c.take<uint32_t>(pixels);
     sc.status = c.take<int32_t>(1);
     sc.pair_count = c.take<unsigned long long>(1);
+    sc.pair_need = c.take<unsigned long long>(1);
+    sc.coarse_count = c.take<unsigned long long>(1);
     sc.sort_blocks = c.take<uint32_t>(1);
     sc.digit_totals = c.take<uint32_t>(kTotalWords);
     sc.loss_partials = c.take<float>(2 * kLossBlocks);
@@ -106,7 +114,8 @@ size_t carve_p(Scratch& sc, char* base, int64_t pairs) {
     sc.keys[1] = c.take<unsigned long long>(pairs);
     sc.vals[0] = c.take<uint32_t>(pairs);
     sc.vals[1] = c.take<uint32_t>(pairs);
-    sc.sort_hist = c.take<uint32_t>(lookback_words(32 / kRadixBits, sb ? sb : 1));  // tile ids: at most 4 passes
+    sc.sort_hist = c.take<uint32_t>(lookback_words(32 / kRadixBits, sb ? sb : 1));  // 32-bit keys: at most 4 passes
+    sc.vseg = c.take<uint32_t>(pairs / 32 + 1);
     return c.off;
 }
 
@@ -135,29 +144,32 @@ int cuda_err(cudaError_t e) {
     return PGS_ERR_CUDA;
 }
 
-int reserve_g(pgs_ctx* ctx, int64_t n, int64_t pixels, int64_t tiles) {
-    if (n <= ctx->cap_n && pixels <= ctx->cap_pixels && tiles <= ctx->cap_tiles) return PGS_OK;
+int reserve_g(pgs_ctx* ctx, int64_t n, int64_t pixels, int64_t tiles, int64_t supers) {
+    if (n <= ctx->cap_n && pixels <= ctx->cap_pixels && tiles <= ctx->cap_tiles && supers <= ctx->cap_supers)
+        return PGS_OK;
     n = n > ctx->cap_n ? n : ctx->cap_n;
     pixels = pixels > ctx->cap_pixels ? pixels : ctx->cap_pixels;
     tiles = tiles > ctx->cap_tiles ? tiles : ctx->cap_tiles;
+    supers = supers > ctx->cap_supers ? supers : ctx->cap_supers;
     Scratch tmp = ctx->sc;
-    const size_t bytes = carve_g(tmp, nullptr, n, pixels, tiles);
+    const size_t bytes = carve_g(tmp, nullptr, n, pixels, tiles, supers);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_err(e);
     if (ctx->arena_g) cudaFree(ctx->arena_g);
     ctx->arena_g = nullptr;
-    ctx->cap_n = ctx->cap_pixels = ctx->cap_tiles = -1;
+    ctx->cap_n = ctx->cap_pixels = ctx->cap_tiles = ctx->cap_supers = -1;
     e = cudaMalloc(&ctx->arena_g, bytes);
     if (e != cudaSuccess) {
         ctx->arena_g = nullptr;
         return cuda_err(e);
     }
-    carve_g(ctx->sc, static_cast<char*>(ctx->arena_g), n, pixels, tiles);
+    carve_g(ctx->sc, static_cast<char*>(ctx->arena_g), n, pixels, tiles, supers);
     e = cudaMemsetAsync(ctx->arena_g, 0, bytes, ctx->stream);
     if (e != cudaSuccess) return cuda_err(e);
     ctx->cap_n = n;
     ctx->cap_pixels = pixels;
     ctx->cap_tiles = tiles;
+    ctx->cap_supers = supers;
     ctx->has_render = false;
     return PGS_OK;
 }
@@ -248,7 +260,7 @@ int pgs_create(pgs_ctx** out, const pgs_config* cfg, void* cuda_stream) {
     ctx->tile = cfg->tile;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     ctx->grow_pairs = cfg->pair_capacity == 0;
-    int rc = reserve_g(ctx, 1, 1, 1);
+    int rc = reserve_g(ctx, 1, 1, 1, 1);
     if (rc == PGS_OK) rc = reserve_p(ctx, cfg->pair_capacity > 0 ? cfg->pair_capacity : (1 << 20));
     if (rc != PGS_OK) {
         pgs_destroy(ctx);
@@ -272,7 +284,7 @@ void pgs_destroy(pgs_ctx* ctx) {
 int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t pair_capacity) {
     if (!ctx || n < 0 || width < 0 || height < 0 || pair_capacity < 0) return PGS_ERR_INVALID_ARG;
     const int64_t T = ctx->tile, TX = (width + T - 1) / T, TY = (height + T - 1) / T;
-    int rc = reserve_g(ctx, n, (int64_t)width * height, TX * TY);
+    int rc = reserve_g(ctx, n, (int64_t)width * height, TX * TY, super_tiles(TX, TY));
     if (rc == PGS_OK) rc = reserve_p(ctx, pair_capacity);
     return rc;
 }
@@ -281,7 +293,8 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     if (!ctx || !valid_gaussians(params) || !valid_camera(cam) || !image_out) return PGS_ERR_INVALID_ARG;
     const int T = ctx->tile, TX = (cam->width + T - 1) / T, TY = (cam->height + T - 1) / T;
     const int64_t tiles = (int64_t)TX * TY, pixels = (int64_t)cam->width * cam->height;
-    int rc = reserve_g(ctx, params->n, pixels, tiles);
+    const int64_t supers = super_tiles(TX, TY);
+    int rc = reserve_g(ctx, params->n, pixels, tiles, supers);
     if (rc != PGS_OK) return rc;
     cudaStream_t s = ctx->stream;
     ctx->has_render = false;
@@ -290,15 +303,16 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     const size_t e1 = mark(ctx);
     const uint32_t* perm = nullptr;
     if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm);
-    ctx->launches += launch_scan_emit(params->n, TX, T, ctx->cap_pairs, perm, ctx->sc, s);
+    ctx->launches += launch_bin_count(params->n, supers, ctx->cap_pairs, perm, ctx->sc, s);
     if (ctx->grow_pairs) {
-        unsigned long long P = 0;
-        cudaError_t e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+        unsigned long long need = 0;
+        cudaError_t e = cudaMemcpyAsync(&need, ctx->sc.pair_need, sizeof(need), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_err(e);
-        if ((int64_t)P > ctx->cap_pairs) {
-            // grow with headroom, clear the overflow flag, and emit again
-            rc = reserve_p(ctx, (int64_t)(P + P / 4 + 1024));
+        if ((int64_t)need > ctx->cap_pairs) {
+            // grow with headroom, clear the overflow flag, and count again (the coarse sort's CTA
+            // count depends on the capacity)
+            rc = reserve_p(ctx, (int64_t)(need + need / 4 + 1024));
             if (rc != PGS_OK) return rc;
             int32_t st = 0;
             e = cudaMemcpyAsync(&st, ctx->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
@@ -308,11 +322,11 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
             e = cudaMemcpyAsync(ctx->sc.status, &st, sizeof(st), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_err(e);
-            ctx->launches += launch_scan_emit(params->n, TX, T, ctx->cap_pairs, perm, ctx->sc, s);
+            ctx->launches += launch_bin_count(params->n, supers, ctx->cap_pairs, perm, ctx->sc, s);
         }
     }
     const size_t e2 = mark(ctx);
-    ctx->launches += launch_sort_ranges(ctx->cap_pairs, (int)tiles, ctx->sc, s, &ctx->buf);
+    ctx->launches += launch_bin_lists(params->n, TX, TY, T, tiles, supers, ctx->cap_pairs, perm, ctx->sc, s, &ctx->buf);
     ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
     ctx->recorded = false;
@@ -463,10 +477,13 @@ int pgs_status(pgs_ctx* ctx, int64_t* pairs_needed) {
     unsigned long long P = 0;
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMemcpyAsync(&st, ctx->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    unsigned long long need = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&P, ctx->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&need, ctx->sc.pair_need, sizeof(need), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sc.status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(e);
+    if (st & kStatusCapacity) P = need;  // the capacity to grow to (the pairs, or more for the coarse stage)
     if (pairs_needed) *pairs_needed = (int64_t)P;
     if (st & kStatusInternal) return PGS_ERR_INTERNAL;
     if (st & kStatusTimeout) return PGS_ERR_TIMEOUT;
@@ -629,12 +646,13 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
     if (e != cudaSuccess) return cuda_err(e);
     const int64_t kept = (int64_t)P < ctx->cap_pairs ? (int64_t)P : ctx->cap_pairs;
     const int64_t pixels = (int64_t)ctx->cam.width * ctx->cam.height;
+    const int64_t tiles = (int64_t)ctx->TX * ctx->TY;
     const void* src = nullptr;
     int64_t size = 0;
     switch (which) {
-        case PGS_BUF_KEYS: src = ctx->sc.keys[ctx->buf ^ 1]; size = 8 * kept; break;
-        case PGS_BUF_VALUES: src = ctx->sc.vals[ctx->buf]; size = 4 * kept; break;
-        case PGS_BUF_RANGES: src = ctx->sc.ranges; size = 8 * (int64_t)ctx->TX * ctx->TY; break;
+        case PGS_BUF_KEYS: size = 8 * kept; break;
+        case PGS_BUF_VALUES: size = 4 * kept; break;
+        case PGS_BUF_RANGES: size = 8 * tiles; break;
         case PGS_BUF_T_FINAL: src = ctx->sc.T_final; size = 4 * pixels; break;
         case PGS_BUF_LAST: src = ctx->sc.last; size = 4 * pixels; break;
         case PGS_BUF_GRAD2D: src = ctx->sc.grad2d; size = 36 * ctx->n; break;
@@ -643,15 +661,54 @@ int pgs_read_buffer(pgs_ctx* ctx, int which, void* dst, int64_t max_bytes, int64
         default: return PGS_ERR_INVALID_ARG;
     }
     if (!ctx->has_render) return PGS_ERR_NO_RENDER;
-    // the sorted pair buffer holds tile ids: join each pair's depth bits into the free ping-pong
-    // key buffer (the backward reads only the values and ranges)
-    if (which == PGS_BUF_KEYS) launch_join_keys(ctx->cap_pairs, ctx->buf, ctx->sc, s);
     if (bytes) *bytes = size;
     const int64_t cp = size < max_bytes ? size : max_bytes;
-    if (cp > 0 && dst) {
+    if (cp <= 0 || !dst) return PGS_OK;
+    if (src) {
         e = cudaMemcpyAsync(dst, src, (size_t)cp, cudaMemcpyDefault, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_err(e);
+        return e == cudaSuccess ? PGS_OK : cuda_err(e);
+    }
+    // Pair lists, ranges and keys in the order of the stable sort of (tile << 32 | depth bits)
+    // pairs: tiles row-major, each tile's list as the render holds it (the render lays the lists
+    // out super-tile by super-tile; this read-back only reorders whole lists).
+    std::vector<uint2> rng((size_t)tiles);
+    std::vector<uint32_t> vals((size_t)kept);
+    e = cudaMemcpyAsync(rng.data(), ctx->sc.ranges, sizeof(uint2) * (size_t)tiles, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && kept > 0)
+        e = cudaMemcpyAsync(vals.data(), ctx->sc.vals[ctx->buf], 4 * (size_t)kept, cudaMemcpyDeviceToHost, s);
+    std::vector<uint32_t> depth;
+    if (which == PGS_BUF_KEYS && ctx->n > 0) {
+        depth.resize((size_t)ctx->n);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(depth.data(), ctx->sc.depth_bits, 4 * (size_t)ctx->n, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (which == PGS_BUF_RANGES) {
+        std::vector<uint2> out((size_t)tiles);
+        uint32_t at = 0;
+        for (int64_t t = 0; t < tiles; ++t) {
+            const uint32_t len = rng[t].y - rng[t].x;
+            out[t] = len ? make_uint2(at, at + len) : make_uint2(0u, 0u);  // an empty tile reads (0, 0)
+            at += len;
+        }
+        std::memcpy(dst, out.data(), (size_t)cp);
+        return PGS_OK;
+    }
+    std::vector<uint64_t> out;
+    out.reserve((size_t)kept);
+    for (int64_t t = 0; t < tiles; ++t)
+        for (uint32_t k = rng[t].x; k < rng[t].y && (int64_t)k < kept; ++k) {
+            const uint32_t g = vals[k];
+            if (which == PGS_BUF_VALUES) out.push_back(g);
+            else out.push_back(((uint64_t)t << 32) | (g < depth.size() ? depth[g] : 0xffffffffu));
+        }
+    if (which == PGS_BUF_VALUES) {
+        std::vector<uint32_t> v32(out.begin(), out.end());
+        std::memcpy(dst, v32.data(), (size_t)std::min<int64_t>(cp, 4 * (int64_t)v32.size()));
+    } else {
+        std::memcpy(dst, out.data(), (size_t)std::min<int64_t>(cp, 8 * (int64_t)out.size()));
     }
     return PGS_OK;
 }
@@ -667,7 +724,7 @@ struct pgs_batch {
     int S = 0, R = 0, deg = 0;
     std::vector<SceneDesc> scenes;
     std::vector<RenderDesc> renders;
-    int64_t items = 0, gauss = 0, tiles = 0, pixels = 0, values = 0, cap_pairs = 0;
+    int64_t items = 0, gauss = 0, tiles = 0, supers = 0, pixels = 0, values = 0, cap_pairs = 0;
     Scratch sc;
     void* arena_g = nullptr;
     void* arena_p = nullptr;
@@ -703,8 +760,9 @@ int64_t enqueue_render(pgs_batch* b) {
     k += launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
     const uint32_t* perm = nullptr;
     if (b->items > 0) k += launch_depth_sort(b->items, b->sc, s, &perm);
-    k += launch_scan_emit(b->items, 0, b->cfg.tile, b->cap_pairs, perm, b->sc, s, b->d_renders, b->R);
-    k += launch_sort_ranges(b->cap_pairs, (int)b->tiles, b->sc, s, &b->buf);
+    k += launch_bin_count(b->items, b->supers, b->cap_pairs, perm, b->sc, s);
+    k += launch_bin_lists(b->items, 0, 0, b->cfg.tile, b->tiles, b->supers, b->cap_pairs, perm, b->sc, s, &b->buf,
+                          b->d_renders, b->R);
     k += launch_tile_order((int)b->tiles, b->sc, s);
     return k;
 }
@@ -785,6 +843,8 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         rd.item_base = b->items;
         rd.n = params[d.scene].n;
         rd.tile_base = b->tiles;
+        rd.SX = (rd.TX + kSuperW - 1) / kSuperW;
+        rd.super_base = b->supers;
         rd.pixel_base = b->pixels;
         rd.value_base = b->values;
         rd.image = d.image;
@@ -792,6 +852,7 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         rd.dL = d.dL_dimage;
         b->items += rd.n;
         b->tiles += (int64_t)rd.TX * rd.TY;
+        b->supers += super_tiles(rd.TX, rd.TY);
         b->pixels += (int64_t)d.cam.width * d.cam.height;
         b->values += 3ll * d.cam.width * d.cam.height;
         SceneDesc& sd = b->scenes[d.scene];
@@ -805,10 +866,10 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
     if (b->items >= (int64_t(1) << 32) || b->tiles >= (int64_t(1) << 32)) return fail(PGS_ERR_INVALID_ARG);
     // arenas
     Scratch tmp;
-    const size_t gbytes = carve_g(tmp, nullptr, b->items, b->pixels, b->tiles);
+    const size_t gbytes = carve_g(tmp, nullptr, b->items, b->pixels, b->tiles, b->supers);
     cudaError_t e = cudaMalloc(&b->arena_g, gbytes);
     if (e != cudaSuccess) return fail(cuda_err(e));
-    carve_g(b->sc, static_cast<char*>(b->arena_g), b->items, b->pixels, b->tiles);
+    carve_g(b->sc, static_cast<char*>(b->arena_g), b->items, b->pixels, b->tiles, b->supers);
     const size_t tbytes = align256(sizeof(SceneDesc) * n_scenes) + align256(sizeof(RenderDesc) * n_renders) +
                           align256(sizeof(double) * 2 * n_renders) + 256 + 256 +
                           align256(sizeof(pgs_gaussians) * n_scenes);
@@ -838,10 +899,10 @@ int pgs_batch_create(pgs_batch** out, const pgs_config* cfg, int32_t n_scenes,
         launch_project_fwd_batch(b->d_renders, b->R, b->d_scenes, b->deg, b->items, b->sc, s);
         const uint32_t* perm = nullptr;
         launch_depth_sort(b->items, b->sc, s, &perm);
-        launch_scan_emit(b->items, 0, b->cfg.tile, 0, perm, b->sc, s, b->d_renders, b->R);
+        launch_bin_count(b->items, b->supers, 0, perm, b->sc, s);
         unsigned long long P = 0;
         int32_t zero = 0;
-        e = cudaMemcpyAsync(&P, b->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(&P, b->sc.pair_need, sizeof(P), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->sc.status, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(cuda_err(e));
@@ -998,10 +1059,13 @@ int pgs_batch_status(pgs_batch* b, int64_t* pairs) {
     unsigned long long P = 0;
     cudaStream_t s = b->stream;
     cudaError_t e = cudaMemcpyAsync(&st, b->sc.status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    unsigned long long need = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&P, b->sc.pair_count, sizeof(P), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&need, b->sc.pair_need, sizeof(need), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->sc.status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(e);
+    if (st & kStatusCapacity) P = need;  // the capacity to grow to (the pairs, or more for the coarse stage)
     if (pairs) *pairs = (int64_t)P;
     if (st & kStatusInternal) return PGS_ERR_INTERNAL;
     if (st & kStatusTimeout) return PGS_ERR_TIMEOUT;

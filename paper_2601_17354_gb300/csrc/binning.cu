@@ -1,25 +1,31 @@
-// K2 scan, K3 key emission, K4 radix sort, K5 tile ranges.
+// K2 counts, K3 coarse entries, K4 radix sort, K5 tile lists and ranges.
 //
-// The sorted (tile | depth) keys carry the canonical index as their value: this is the
-// permutation pi of Eq. 10 ("a GPU sort yields a permutation mapping sorted index i to canonical
-// index pi(i)").  Parameters are never reordered; the compositing kernels gather by pi and the
-// backward scatters gradients to pi (index-mapped gradient scattering).
+// The pair lists carry the canonical index of each Gaussian: this is the permutation pi of Eq. 10
+// ("a GPU sort yields a permutation mapping sorted index i to canonical index pi(i)").  Parameters
+// are never reordered; the compositing kernels gather by pi and the backward scatters gradients to
+// pi (index-mapped gradient scattering).
 //
-// key = (tile << 32) | float bits of the camera depth (depth > near > 0, so the bits order like
-// the depths); equal keys keep emission order (canonical order), so the sort is the stable sort
-// of the pairs.  The Gaussians are first sorted by depth (32-bit depth keys) and the pairs are
-// emitted in that order, so the pair sort only has to order the 32-bit tile part stably: the
-// pair buffers hold tile ids (uint32), and the full 64-bit key of a sorted pair is
-// (tile << 32) | depth bits of its Gaussian.  The number of pairs is known only on the device: every kernel reads it from the
-// context's pair counter, and pairs beyond the capacity are not written (the status word records
-// the overflow), so no host synchronisation sits between projection and compositing.
+// Every tile's list holds the Gaussians that reach it in depth order, ties in canonical order: the
+// order of the stable sort of (tile << 32 | depth bits) pairs.  It is built in two levels.  The
+// Gaussians are sorted by depth (32-bit keys, ties kept in canonical order); each then emits one
+// coarse entry per super-tile (kSuperW x kSuperH tiles) its tile rectangle overlaps, in depth
+// order; a stable radix sort by super-tile id groups the entries by super-tile, still in depth
+// order inside each group.  The fine stage gives each entry a 32-bit mask of the super-tile's tiles
+// the Gaussian reaches (the projection's reach test), counts each tile's entries per block of
+// kFineBlock with one warp ballot per tile, scans those counts, and writes each entry's canonical
+// index at its tile's first pair + the entries of the tile before it.  The pair buffer is laid out
+// super-tile by super-tile, tiles row-major inside; a tile's list is [ranges[t].x, ranges[t].y).
+// The pair count is the sum of the projection's reached-tile counts, known before any list is
+// built; pairs beyond the capacity are not written (the status word records the overflow and the
+// capacity needed), so no host synchronisation sits between projection and compositing.
 //
 // The radix sort is least-significant-digit first, 8-bit digits, over the bits that can be
-// non-zero (32 depth bits for the Gaussians, ceil(log2 tiles) tile bits for the pairs; the
-// caller's low key bits of the 64-bit keys of the allocation-free entry point); the last digit is
-// masked to what is left of the bit range.  The digit totals of every pass come from one up-front
-// histogram; each pass is then one launch that ranks a tile's keys with warp ballots and finds the
-// tile's place by decoupled look-back over the tiles before it (bounded waits, see k_onesweep).
+// non-zero (32 depth bits for the Gaussians, ceil(log2 super-tiles) bits for the coarse entries;
+// the caller's low key bits of the 64-bit keys of the allocation-free entry point); the last digit
+// is masked to what is left of the bit range.  The digit totals of every pass come from one
+// up-front histogram; each pass is then one launch that ranks a tile's keys with warp ballots and
+// finds the tile's place by decoupled look-back over the tiles before it (bounded waits, see
+// k_onesweep).
 #include "pgs_internal.cuh"
 
 namespace pgs {
@@ -29,12 +35,56 @@ constexpr unsigned kFull = 0xffffffffu;
 static_assert(kSortThreads == kRadix, "one thread per digit in the sort kernels");
 
 // ---------------------------------------------------------------------------------------------
-// K2: exclusive scan of the per-CTA tile counts -> pair offsets, total pair count, capacity check
+// K2: pair count and coarse entry counts
 // ---------------------------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 
+// super-tile rectangle [sx0, sx1) x [sy0, sy1) of a tile rectangle (x0 | y0 << 16, x1 | y1 << 16)
+__device__ __forceinline__ void super_rect(uint2 r, uint32_t& sx0, uint32_t& sy0, uint32_t& sx1, uint32_t& sy1) {
+    sx0 = (r.x & 0xffffu) / kSuperW;
+    sy0 = (r.x >> 16) / kSuperH;
+    sx1 = ((r.y & 0xffffu) + kSuperW - 1) / kSuperW;
+    sy1 = ((r.y >> 16) + kSuperH - 1) / kSuperH;
+}
+
+// Per CTA of depth-ordered Gaussians: coarse entries (super-tiles of the rectangle) into
+// block_sums; reached tiles added into pair_count (zeroed before).
+__global__ void __launch_bounds__(kProjBlock)
+k_coarse_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
+    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
+    uint32_t area = 0, reached = 0;
+    if (i < n) {
+        const uint32_t g = perm[i];
+        reached = sc.touched[g];
+        if (reached) {
+            uint32_t sx0, sy0, sx1, sy1;
+            super_rect(sc.rect[g], sx0, sy0, sx1, sy1);
+            area = (sx1 - sx0) * (sy1 - sy0);
+        }
+    }
+    const uint32_t wa = __reduce_add_sync(kFull, area), wr = __reduce_add_sync(kFull, reached);
+    __shared__ uint32_t s_a[kProjBlock / 32], s_r[kProjBlock / 32];
+    if ((threadIdx.x & 31) == 0) {
+        s_a[threadIdx.x >> 5] = wa;
+        s_r[threadIdx.x >> 5] = wr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < kProjBlock / 32;
+        const uint32_t a = __reduce_add_sync(kFull, in ? s_a[threadIdx.x] : 0u);
+        const unsigned long long r = __reduce_add_sync(kFull, in ? s_r[threadIdx.x] : 0u);
+        if (threadIdx.x == 0) {
+            sc.block_sums[blockIdx.x] = a;
+            if (r) atomicAdd(sc.pair_count, r);
+        }
+    }
+}
+
+// Exclusive scan of the per-CTA coarse counts -> their offsets; coarse total, the coarse sort's CTA
+// count, the capacity the render needs (pairs, and the coarse stage's entries and counters) and
+// the capacity check.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
+k_coarse_scan(int nb, int64_t capacity, int64_t supers, Scratch sc) {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -42,7 +92,7 @@ k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = 0; base < nb; base += kScanThreads) {
         const int idx = base + threadIdx.x;
-        unsigned long long v = idx < nb ? sc.block_sums[idx] : 0ull;
+        const unsigned long long v = idx < nb ? sc.block_sums[idx] : 0ull;
         unsigned long long incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -52,14 +102,14 @@ k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
         if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            unsigned long long w = s_warp[lane];
+            const unsigned long long w = s_warp[lane];
             unsigned long long wi = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long t = __shfl_up_sync(kFull, wi, o);
                 if (lane >= o) wi += t;
             }
-            s_warp[lane] = wi - w;  // exclusive prefix of warp totals
+            s_warp[lane] = wi - w;
         }
         __syncthreads();
         const unsigned long long carry = s_carry;
@@ -69,72 +119,44 @@ k_scan_blocks(int nb, int64_t capacity, Scratch sc) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const unsigned long long P = s_carry;
-        *sc.pair_count = P;
-        const unsigned long long kept = P < (unsigned long long)capacity ? P : (unsigned long long)capacity;
+        const unsigned long long Ce = s_carry, P = *sc.pair_count;
+        *sc.coarse_count = Ce;
+        const unsigned long long kept = Ce < (unsigned long long)capacity ? Ce : (unsigned long long)capacity;
         *sc.sort_blocks = (uint32_t)((kept + kSortTile - 1) / kSortTile);
-        if (P > (unsigned long long)capacity) atomicOr(sc.status, kStatusCapacity);
-    }
-}
-
-// per-CTA sums of tiles touched, Gaussians taken in depth order
-__global__ void __launch_bounds__(kProjBlock)
-k_perm_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
-    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    const uint32_t count = i < n ? sc.touched[perm[i]] : 0u;
-    const uint32_t warp_sum = __reduce_add_sync(kFull, count);
-    __shared__ uint32_t s_part[kProjBlock / 32];
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = warp_sum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < kProjBlock / 32 ? s_part[threadIdx.x] : 0u;
-        v = __reduce_add_sync(kFull, v);
-        if (threadIdx.x == 0) sc.block_sums[blockIdx.x] = v;
+        const unsigned long long c = coarse_need(Ce, (unsigned long long)supers);
+        const unsigned long long need = P > c ? P : c;
+        *sc.pair_need = need;
+        if (need > (unsigned long long)capacity) atomicOr(sc.status, kStatusCapacity);
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// K3: emit the pairs of one CTA's Gaussians in depth order (ties: canonical order), tiles
-// row-major inside each rectangle.  Each warp walks the candidate tiles of its own 32 Gaussians,
-// 32 per round (candidate k by lane k mod 32; its Gaussian found by a shuffle binary search over
-// the lanes' inclusive rectangle areas), and compacts the reached ones in order with one ballot.
-// A warp's output starts after the pairs of the warps before it, known from the Gaussians'
-// reached-tile counts, so warps never wait for one another inside the walk.
+// K3: coarse entries (super-tile id, canonical index) of one CTA's Gaussians in depth order,
+// super-tiles row-major inside each Gaussian's super-tile rectangle.  Each warp walks the entries
+// of its own 32 Gaussians, 32 per round (entry k by lane k mod 32; its Gaussian found by a shuffle
+// binary search over the lanes' inclusive entry counts).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
-k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
-       const RenderDesc* __restrict__ renders, int R) {
-    __shared__ uint32_t s_x0[kProjBlock], s_y0[kProjBlock], s_w[kProjBlock];
-    __shared__ uint32_t s_tx[kProjBlock], s_tbase[kProjBlock];
-    __shared__ float s_u[kProjBlock], s_v[kProjBlock], s_ca[kProjBlock], s_cb[kProjBlock], s_cc[kProjBlock];
-    __shared__ float s_sx[kProjBlock], s_sy[kProjBlock];
-    __shared__ uint32_t s_mask[kProjBlock];
+k_coarse_emit(int64_t n, int SX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
+              const RenderDesc* __restrict__ renders, int R) {
+    __shared__ uint32_t s_sx0[kProjBlock], s_sy0[kProjBlock], s_sw[kProjBlock];
+    __shared__ uint32_t s_SX[kProjBlock], s_base[kProjBlock], s_gid[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
-    __shared__ uint32_t s_gid[kProjBlock];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
-    uint32_t cnt = 0, reached = 0;  // rectangle area, reached tiles
+    uint32_t cnt = 0;
     if (i < n) {
         const uint32_t g = perm[i];
         s_gid[t] = g;
-        reached = sc.touched[g];
-        if (reached) {
-            const uint2 r = sc.rect[g];
-            s_x0[t] = r.x & 0xffffu;
-            s_y0[t] = r.x >> 16;
-            s_w[t] = (r.y & 0xffffu) - (r.x & 0xffffu);
-            cnt = s_w[t] * ((r.y >> 16) - (r.x >> 16));
-            const float4 p = sc.xyo[g], q = sc.conic[g];
-            s_u[t] = p.x;
-            s_v[t] = p.y;
-            s_ca[t] = q.x;
-            s_cb[t] = q.y;
-            s_cc[t] = q.z;
-            s_sx[t] = __fdiv_rn(q.y, q.x);
-            s_sy[t] = __fdiv_rn(q.y, q.z);
-            s_mask[t] = sc.hitmask[g];
-            s_tx[t] = (uint32_t)TX;
-            s_tbase[t] = 0;
+        if (sc.touched[g]) {
+            uint32_t sx0, sy0, sx1, sy1;
+            super_rect(sc.rect[g], sx0, sy0, sx1, sy1);
+            s_sx0[t] = sx0;
+            s_sy0[t] = sy0;
+            s_sw[t] = sx1 - sx0;
+            cnt = (sx1 - sx0) * (sy1 - sy0);
+            s_SX[t] = (uint32_t)SX;
+            s_base[t] = 0;
             if (renders) {  // batch: item g belongs to the last render whose first item is <= g
                 int lo = 0, hi = R - 1;
                 while (lo < hi) {
@@ -142,8 +164,8 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
                     if (renders[mid].item_base <= (int64_t)g) lo = mid;
                     else hi = mid - 1;
                 }
-                s_tx[t] = (uint32_t)renders[lo].TX;
-                s_tbase[t] = (uint32_t)renders[lo].tile_base;
+                s_SX[t] = (uint32_t)renders[lo].SX;
+                s_base[t] = (uint32_t)renders[lo].super_base;
             }
         }
     }
@@ -153,20 +175,18 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
         const uint32_t v = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += v;
     }
-    const uint32_t first = incl - cnt;  // this lane's first candidate in the warp's walk
+    const uint32_t first = incl - cnt;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t wpairs = __reduce_add_sync(kFull, reached);
-    if (lane == 0) s_warp[warp] = wpairs;
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();  // also publishes the lanes' records in shared memory
     uint32_t before = 0;
 #pragma unroll
     for (int w = 0; w < kProjBlock / 32; ++w) before += w < warp ? s_warp[w] : 0u;
     const unsigned long long out = sc.block_offsets[blockIdx.x] + before;
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t written = 0;
+    uint32_t* ck = reinterpret_cast<uint32_t*>(sc.keys[0]);
     for (uint32_t b = 0; b < total; b += 32) {  // warp-uniform
         const uint32_t k = b + (uint32_t)lane;
-        int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive area exceeds k
+        int lo = 0, hi = 31;  // owner of entry k: the first lane whose inclusive count exceeds k
 #pragma unroll
         for (int step = 0; step < 5; ++step) {
             const int mid = (lo + hi) >> 1;
@@ -176,30 +196,17 @@ k_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* __restrict__ 
                 else lo = mid + 1;
             }
         }
-        const uint32_t ofirst = __shfl_sync(kFull, first, lo), oarea = __shfl_sync(kFull, cnt, lo);
-        bool hit = false;
-        uint32_t tile = 0, gid = 0;
-        if (k < total) {  // then the owner's rectangle is not empty
+        const uint32_t ofirst = __shfl_sync(kFull, first, lo);
+        if (k < total) {
             const int o = warp * 32 + lo;
-            const uint32_t local = k - ofirst;
-            const uint32_t w = s_w[o];
+            const uint32_t local = k - ofirst, w = s_sw[o];
             const uint32_t dy = local / w, dx = local - dy * w;
-            const uint32_t tx = s_x0[o] + dx, ty = s_y0[o] + dy;
-            hit = oarea <= 32u ? ((s_mask[o] >> local) & 1u) != 0u
-                               : tile_hit(s_u[o], s_v[o], s_ca[o], s_cb[o], s_cc[o], s_sx[o], s_sy[o], (int)tx,
-                                          (int)ty, T);
-            tile = s_tbase[o] + ty * s_tx[o] + tx;
-            gid = s_gid[o];
-        }
-        const unsigned bal = __ballot_sync(kFull, hit);
-        if (hit) {
-            const unsigned long long pos = out + written + __popc(bal & lt);
+            const unsigned long long pos = out + k;
             if (pos < (unsigned long long)capacity) {
-                reinterpret_cast<uint32_t*>(sc.keys[0])[pos] = tile;
-                sc.vals[0][pos] = gid;
+                ck[pos] = s_base[o] + (s_sy0[o] + dy) * s_SX[o] + s_sx0[o] + dx;
+                sc.vals[0][pos] = s_gid[o];
             }
         }
-        written += __popc(bal);
     }
 }
 
@@ -480,13 +487,356 @@ k_ranges(int64_t capacity, uint32_t tiles, const uint32_t* __restrict__ keys, Sc
     }
 }
 
-// the full keys of the sorted pairs, (tile << 32) | depth bits of the pair's Gaussian
+// ---------------------------------------------------------------------------------------------
+// K5: fine stage.  The coarse entries of a super-tile, in depth order, are cut into blocks of
+// kFineBlock; a block computes each entry's 32-bit mask of reached tiles of the super-tile and its
+// per-tile counts; a scan over each super-tile's blocks and one over the super-tiles give every
+// (block, tile) its first pair, and the block writes its pairs: entry e of tile x goes after the
+// entries of x in earlier blocks, earlier warps and earlier lanes, i.e. in depth order.
+// ---------------------------------------------------------------------------------------------
+constexpr int kFineWarps = kFineBlock / 32;
+constexpr int kFineGrid = 152 * 8;  // grid-stride over the blocks
+
+// tile grid of super-tile s: its position and the render it belongs to
+struct SuperCell {
+    uint32_t sx, sy;
+    int TX, TY;
+    uint32_t tile_base;
+};
+
+__device__ __forceinline__ SuperCell super_cell(uint32_t s, int TX, int TY, const RenderDesc* __restrict__ renders,
+                                                int R) {
+    SuperCell c;
+    uint32_t local = s, SX = (uint32_t)((TX + kSuperW - 1) / kSuperW);
+    c.TX = TX;
+    c.TY = TY;
+    c.tile_base = 0;
+    if (renders) {  // the last render whose first super-tile is <= s
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (renders[mid].super_base <= (int64_t)s) lo = mid;
+            else hi = mid - 1;
+        }
+        local = s - (uint32_t)renders[lo].super_base;
+        SX = (uint32_t)renders[lo].SX;
+        c.TX = renders[lo].TX;
+        c.TY = renders[lo].TY;
+        c.tile_base = (uint32_t)renders[lo].tile_base;
+    }
+    c.sy = local / SX;
+    c.sx = local - c.sy * SX;
+    return c;
+}
+
+// One CTA: blocks per super-tile (ceil(entries / kFineBlock)), their exclusive scan into vbase
+// (vbase[S] = all blocks) and each block's super-tile into vseg.
+__global__ void __launch_bounds__(kScanThreads)
+k_block_prefix(int S, int64_t capacity, Scratch sc) {
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < S; base += kScanThreads) {
+        const int s = base + threadIdx.x;
+        uint32_t nb = 0;
+        if (s < S) {
+            const uint2 cr = sc.crange[s];
+            nb = (cr.y - cr.x + kFineBlock - 1) / kFineBlock;
+        }
+        uint32_t incl = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_warp[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        const uint32_t first = carry + s_warp[warp] + incl - nb;
+        if (s < S) {
+            sc.vbase[s] = first;
+            for (uint32_t v = first; v < first + nb; ++v)
+                if (v < (uint64_t)capacity / 32) sc.vseg[v] = (uint32_t)s;
+        }
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sc.vbase[S] = s_carry;
+}
+
+// Transpose of the warp's 32 x 32 bit matrix (lane l holds row l): lane x returns column x, whose
+// bit l is bit x of lane l's word.  Five stages; at stage j the lanes l and l ^ j swap the block of
+// bits b with b & j set (upper lane l) against the block with b & j clear (lower lane l ^ j).
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
+    constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t m = kMask[k];
+        const uint32_t o = __shfl_xor_sync(kFull, x, j);
+        x = (lane & j) ? ((x & ~m) | ((o & ~m) >> j)) : ((x & m) | ((o & m) << j));
+    }
+    return x;
+}
+
+// Masks of every coarse entry (into masks[e]) and each block's per-tile counts (wc[32 v + x]).
+// A mask holds the tiles of super-tile (sx, sy) the entry's Gaussian reaches (bit (ty mod kSuperH)
+// kSuperW + tx mod kSuperW): read row by row from the projection's reach mask for rectangles of
+// <= 32 tiles; for larger ones the warp runs the projection's reach test over all such entries'
+// candidate tiles together, 32 per round (candidate k by lane k mod 32, its entry found by a
+// shuffle binary search over the lanes' inclusive candidate counts), so one large Gaussian does
+// not hold its warp for 32 tests.
+__global__ void __launch_bounds__(kFineBlock)
+k_fine_count(int64_t capacity, int T, int TX, int TY, const uint32_t* __restrict__ cv, uint32_t* __restrict__ masks,
+             uint32_t* __restrict__ wc, const uint32_t* __restrict__ vseg, int S, Scratch sc,
+             const RenderDesc* __restrict__ renders, int R) {
+    __shared__ uint32_t s_cw[kFineWarps][32];
+    __shared__ uint32_t s_big[kFineWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t VB = sc.vbase[S];
+    for (uint32_t v = blockIdx.x; v < VB; v += gridDim.x) {
+        if ((uint64_t)v >= (uint64_t)capacity / 32) break;  // no slot for the block (capacity status raised)
+        const uint32_t s = vseg[v];
+        const uint2 cr = sc.crange[s];
+        const uint64_t e = (uint64_t)cr.x + (uint64_t)(v - sc.vbase[s]) * kFineBlock + threadIdx.x;
+        const bool valid = e < cr.y;
+        const SuperCell c = super_cell(s, TX, TY, renders, R);
+        const uint32_t bx = c.sx * kSuperW, by = c.sy * kSuperH;
+        uint32_t mask = 0, ncand = 0, X0 = 0, Y0 = 0, wX = 1;
+        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, ssx = 0.f, ssy = 0.f;
+        if (valid) {
+            const uint32_t g = cv[e];
+            const uint2 r = sc.rect[g];
+            const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
+            X0 = max(x0, bx);
+            Y0 = max(y0, by);
+            const uint32_t X1 = min(x1, bx + kSuperW), Y1 = min(y1, by + kSuperH);
+            const uint32_t w = x1 - x0;
+            wX = X1 - X0;  // >= 1: the super-tile lies in the Gaussian's super-tile rectangle
+            if (w * (y1 - y0) <= 32u) {
+                const uint32_t hm = sc.hitmask[g], row = (1u << wX) - 1u;
+                for (uint32_t ty = Y0; ty < Y1; ++ty)
+                    mask |= ((hm >> ((ty - y0) * w + (X0 - x0))) & row) << ((ty - by) * kSuperW + (X0 - bx));
+            } else {
+                ncand = wX * (Y1 - Y0);
+                const float4 p = sc.xyo[g], q = sc.conic[g];
+                u = p.x;
+                vv = p.y;
+                ca = q.x;
+                cb = q.y;
+                cc = q.z;
+                ssx = __fdiv_rn(q.y, q.x);
+                ssy = __fdiv_rn(q.y, q.z);
+            }
+        }
+        uint32_t incl = ncand;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31), first = incl - ncand;
+        if (total) {  // warp-uniform
+            s_big[warp][lane] = 0u;
+            __syncwarp();
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t k = b + (uint32_t)lane;
+                int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive count exceeds k
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t im = __shfl_sync(kFull, incl, mid);
+                    if (lo < hi) {
+                        if (im > k) hi = mid;
+                        else lo = mid + 1;
+                    }
+                }
+                const uint32_t of = __shfl_sync(kFull, first, lo), ow = __shfl_sync(kFull, wX, lo);
+                const uint32_t ox = __shfl_sync(kFull, X0, lo), oy = __shfl_sync(kFull, Y0, lo);
+                const float ou = __shfl_sync(kFull, u, lo), ov = __shfl_sync(kFull, vv, lo);
+                const float oa = __shfl_sync(kFull, ca, lo), ob = __shfl_sync(kFull, cb, lo), oc = __shfl_sync(kFull, cc, lo);
+                const float osx = __shfl_sync(kFull, ssx, lo), osy = __shfl_sync(kFull, ssy, lo);
+                if (k < total) {
+                    const uint32_t local = k - of, dy = local / ow, dx = local - dy * ow;
+                    const uint32_t tx = ox + dx, ty = oy + dy;
+                    if (tile_hit(ou, ov, oa, ob, oc, osx, osy, (int)tx, (int)ty, T))
+                        atomicOr(&s_big[warp][lo], 1u << ((ty - by) * kSuperW + (tx - bx)));
+                }
+            }
+            __syncwarp();
+            mask |= s_big[warp][lane];
+        }
+        if (valid) masks[e] = mask;
+        s_cw[warp][lane] = __popc(warp_transpose(mask, lane));
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int w = 0; w < kFineWarps; ++w) sum += s_cw[w][lane];
+            wc[32ull * v + lane] = sum;  // 32 v + 31 < capacity
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per super-tile: exclusive scan of its blocks' per-tile counts (in place), the tiles'
+// pair counts stt[32 s + x] and the super-tile's pairs ssum[s].
 __global__ void __launch_bounds__(256)
-k_join_keys(int64_t capacity, const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
-            unsigned long long* __restrict__ out, Scratch sc) {
-    const uint64_t P = kept_pairs(sc, capacity);
-    for (uint64_t k = (uint64_t)blockIdx.x * 256 + threadIdx.x; k < P; k += (uint64_t)gridDim.x * 256)
-        out[k] = ((unsigned long long)tiles[k] << 32) | sc.depth_bits[vals[k]];
+k_seg_scan(int64_t capacity, uint32_t* __restrict__ wc, Scratch sc) {
+    __shared__ uint32_t s_part[8][32];
+    const int s = blockIdx.x, x = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t v0 = sc.vbase[s], nb = sc.vbase[s + 1] - v0;
+    const uint32_t q = (nb + 7) / 8, r0 = min(nb, w * q), r1 = min(nb, r0 + q);
+    uint32_t sum = 0;
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint64_t idx = 32ull * (v0 + r) + x;
+        if (idx < (uint64_t)capacity) sum += wc[idx];
+    }
+    s_part[w][x] = sum;
+    __syncthreads();
+    uint32_t run = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t p = s_part[k][x];
+        run += k < w ? p : 0u;
+        total += p;
+    }
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint64_t idx = 32ull * (v0 + r) + x;
+        if (idx < (uint64_t)capacity) {
+            const uint32_t c = wc[idx];
+            wc[idx] = run;
+            run += c;
+        }
+    }
+    if (w == 0) {
+        sc.stt[32 * s + x] = total;
+        const uint32_t all = __reduce_add_sync(kFull, total);
+        if (x == 0) sc.ssum[s] = all;
+    }
+}
+
+// One CTA: exclusive scan of the super-tiles' pairs -> their first pair sbase[s]; the pair count.
+__global__ void __launch_bounds__(kScanThreads)
+k_super_scan(int S, int64_t capacity, Scratch sc) {
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < S; base += kScanThreads) {
+        const int s = base + threadIdx.x;
+        const unsigned long long v = s < S ? sc.ssum[s] : 0ull;
+        unsigned long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long w = s_warp[lane];
+            unsigned long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        if (s < S) sc.sbase[s] = (uint32_t)(carry + s_warp[warp] + incl - v);
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long P = s_carry;
+        *sc.pair_count = P;
+        if (P > *sc.pair_need) *sc.pair_need = P;
+        if (P > (unsigned long long)capacity) atomicOr(sc.status, kStatusCapacity);
+    }
+}
+
+// The pairs of every block (values = canonical indices into out), and the ranges of a super-tile's
+// tiles from its first block.  Per warp the 32 masks are transposed, so lane x holds the set of
+// lanes reaching tile x: its count is one popcount and an entry's rank among them another.
+__global__ void __launch_bounds__(kFineBlock)
+k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ masks,
+            const uint32_t* __restrict__ wc, const uint32_t* __restrict__ vseg, int S, uint32_t* __restrict__ out,
+            Scratch sc, const RenderDesc* __restrict__ renders, int R) {
+    __shared__ uint32_t s_cw[kFineWarps][32];
+    __shared__ uint32_t s_off[kFineWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t VB = sc.vbase[S];
+    for (uint32_t v = blockIdx.x; v < VB; v += gridDim.x) {
+        if ((uint64_t)v >= (uint64_t)capacity / 32) break;
+        const uint32_t s = vseg[v];
+        const uint2 cr = sc.crange[s];
+        const uint32_t j = v - sc.vbase[s];
+        const uint64_t e = (uint64_t)cr.x + (uint64_t)j * kFineBlock + threadIdx.x;
+        const bool valid = e < cr.y;
+        const uint32_t g = valid ? cv[e] : 0u, mask = valid ? masks[e] : 0u;
+        const uint32_t col = warp_transpose(mask, lane);  // lanes whose entry reaches tile `lane`
+        s_cw[warp][lane] = __popc(col);
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t tt = sc.stt[32 * s + lane];
+            uint32_t incl = tt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t ts = sc.sbase[s] + incl - tt;  // the tile's first pair
+            const uint64_t idx = 32ull * v + lane;
+            uint32_t base = ts + (idx < (uint64_t)capacity ? wc[idx] : 0u);
+#pragma unroll
+            for (int w = 0; w < kFineWarps; ++w) {
+                s_off[w][lane] = base;
+                base += s_cw[w][lane];
+            }
+            if (j == 0) {
+                const SuperCell c = super_cell(s, TX, TY, renders, R);
+                const uint32_t tx = c.sx * kSuperW + (lane % kSuperW), ty = c.sy * kSuperH + (lane / kSuperW);
+                if ((int)tx < c.TX && (int)ty < c.TY) {
+                    const uint32_t cap = capacity < 0xffffffffll ? (uint32_t)capacity : 0xffffffffu;
+                    sc.ranges[c.tile_base + ty * (uint32_t)c.TX + tx] = make_uint2(min(ts, cap), min(ts + tt, cap));
+                }
+            }
+        }
+        __syncthreads();
+        // each lane writes its entry's pairs: tile x after the warp's earlier lanes that reach x
+        uint32_t m = mask;
+        const int rounds = __reduce_max_sync(kFull, (uint32_t)__popc(mask));
+        for (int it = 0; it < rounds; ++it) {  // warp-uniform
+            const int x = m ? __ffs(m) - 1 : 0;
+            const uint32_t cx = __shfl_sync(kFull, col, x);
+            if (m) {
+                const uint64_t pos = (uint64_t)s_off[warp][x] + __popc(cx & lt);
+                if (pos < (uint64_t)capacity) out[pos] = g;
+                m &= m - 1u;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // One CTA: counting sort of the tiles into 128 quarter-octave buckets of their list length,
@@ -628,36 +978,51 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     return launched;
 }
 
-int launch_scan_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s, const RenderDesc* renders, int R) {
+int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+                     cudaStream_t s) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
-    if (nb > 0) k_perm_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
-    k_scan_blocks<<<1, kScanThreads, 0, s>>>(nb, capacity, sc);
-    if (nb == 0) return 1;
-    k_emit<<<nb, kProjBlock, 0, s>>>(n, TX, T, capacity, perm, sc, renders, R);
-    return 3;
+    cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
+    if (nb > 0) k_coarse_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
+    k_coarse_scan<<<1, kScanThreads, 0, s>>>(nb, capacity, supers, sc);
+    return nb > 0 ? 2 : 1;
 }
 
-int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* out_buf) {
-    int tile_bits = 0;
-    while ((1ll << tile_bits) < (long long)tiles) ++tile_bits;
-    // the pairs arrive in depth order: a stable sort of their 32-bit tile keys completes it
-    int buf = 0;
-    int launched = sort_passes<uint32_t, kSortItems>(capacity, 0, tile_bits, sc, s, &buf);
+int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t supers, int64_t capacity,
+                     const uint32_t* perm, const Scratch& sc, cudaStream_t s, int* out_buf, const RenderDesc* renders,
+                     int R) {
+    const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
+    int launched = 0;
+    *out_buf = 1;
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
-    if (capacity > 0) {
-        k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)tiles, reinterpret_cast<const uint32_t*>(sc.keys[buf]), sc);
+    if (capacity <= 0 || supers <= 0) return 0;
+    if (nb > 0) {
+        k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, capacity, perm, sc, renders, R);
         ++launched;
     }
-    *out_buf = buf;
-    return launched;
-}
-
-int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t s) {
-    if (capacity <= 0) return 0;
-    k_join_keys<<<152 * 8, 256, 0, s>>>(capacity, reinterpret_cast<const uint32_t*>(sc.keys[buf]),
-                                         sc.vals[buf], sc.keys[buf ^ 1], sc);
-    return 1;
+    // the coarse entries arrive in depth order: a stable sort by super-tile keeps it in each
+    // super-tile (its count and CTA count are the coarse stage's)
+    Scratch cs = sc;
+    cs.pair_count = sc.coarse_count;
+    int bits = 0;
+    while ((1ll << bits) < (long long)supers) ++bits;
+    int cb = 0;
+    launched += sort_passes<uint32_t, kSortItems>(capacity, 0, bits, cs, s, &cb);
+    cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
+    cs.ranges = sc.crange;
+    k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
+    k_block_prefix<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
+    // masks in the first half of the free key buffer (as 32-bit words), block counts in the second
+    uint32_t* masks = reinterpret_cast<uint32_t*>(sc.keys[cb ^ 1]);
+    uint32_t* wc = masks + capacity;
+    const uint32_t* cv = sc.vals[cb];
+    k_fine_count<<<kFineGrid, kFineBlock, 0, s>>>(capacity, T, TX, TY, cv, masks, wc, sc.vseg, (int)supers, sc,
+                                                   renders, R);
+    k_seg_scan<<<(unsigned)supers, 256, 0, s>>>(capacity, wc, sc);
+    k_super_scan<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
+    k_fine_emit<<<kFineGrid, kFineBlock, 0, s>>>(capacity, TX, TY, cv, masks, wc, sc.vseg, (int)supers,
+                                                  sc.vals[cb ^ 1], sc, renders, R);
+    *out_buf = cb ^ 1;
+    return launched + 6;
 }
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,

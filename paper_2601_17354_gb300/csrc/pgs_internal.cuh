@@ -35,6 +35,23 @@ constexpr int kLookbackHead = 16;
 // scratch words of a sort's look-back for `passes` passes over `tiles` CTA tiles
 constexpr size_t lookback_words(int passes, int64_t tiles) { return kLookbackHead + (size_t)passes * 256 * tiles; }
 
+// Two-level binning: screen tiles are grouped into super-tiles of kSuperW x kSuperH tiles (one bit
+// each in a 32-bit mask); the pair lists are laid out super-tile by super-tile, tiles row-major
+// inside a super-tile.  Coarse entries (one per Gaussian and super-tile its rectangle overlaps)
+// are processed in blocks of kFineBlock.
+constexpr int kSuperW = 8, kSuperH = 4;
+constexpr int kFineBlock = 256;
+inline int64_t super_tiles(int64_t TX, int64_t TY) {
+    return ((TX + kSuperW - 1) / kSuperW) * ((TY + kSuperH - 1) / kSuperH);
+}
+// pair-buffer capacity the coarse stage needs besides the pairs themselves: its Ce entries, and 32
+// counters per block of kFineBlock entries of a super-tile (at most floor(Ce / kFineBlock) + the
+// non-empty super-tiles, at most min(S, Ce), blocks)
+__host__ __device__ inline unsigned long long coarse_need(unsigned long long Ce, unsigned long long S) {
+    const unsigned long long w = 32ull * (Ce / kFineBlock + (S < Ce ? S : Ce));
+    return Ce > w ? Ce : w;
+}
+
 // Per-Gaussian projected record read by the compositing kernels (gathered by canonical index).
 //   xyo   = (u, v, opacity, unused)   screen-space mean and opacity
 //   conic = (a, b, c, unused)         inverse 2-D covariance; power = -(a dx^2 + c dy^2)/2 - b dx dy
@@ -51,6 +68,13 @@ struct Scratch {
     uint32_t* touched = nullptr;
     uint32_t* block_sums = nullptr;
     unsigned long long* block_offsets = nullptr;
+    // per super-tile: coarse entry range, first fine block (S + 1), pair count per tile (32 S),
+    // pairs, first pair (S + 1)
+    uint2* crange = nullptr;
+    uint32_t* vbase = nullptr;
+    uint32_t* stt = nullptr;
+    uint32_t* ssum = nullptr;
+    uint32_t* sbase = nullptr;
     float* grad2d = nullptr;  // [9][n]
     // per tile / pixel
     uint2* ranges = nullptr;
@@ -61,6 +85,8 @@ struct Scratch {
     // small words
     int32_t* status = nullptr;
     unsigned long long* pair_count = nullptr;
+    unsigned long long* pair_need = nullptr;  // pair capacity the render needs (>= pair_count)
+    unsigned long long* coarse_count = nullptr;
     uint32_t* sort_blocks = nullptr;  // sort CTAs with work in the current render
     uint32_t* digit_totals = nullptr; // [kTotalCopies][kMaxPasses][kRadix]
     float* loss_partials = nullptr;   // [2][kLossBlocks]
@@ -77,6 +103,7 @@ struct Scratch {
     unsigned long long* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
     uint32_t* sort_hist = nullptr;  // the sort's look-back: head words, then [passes][tiles][kRadix]
+    uint32_t* vseg = nullptr;       // super-tile of each fine block (pairs / 32 + 1 slots)
 };
 
 constexpr int kLossBlocks = 1024;
@@ -88,9 +115,11 @@ struct RenderDesc {
     int32_t scene;
     int32_t TX, TY;
     int32_t tile;        // tile edge T
+    int32_t SX;          // super-tiles per row
     int64_t item_base;   // first item: item j of the render = Gaussian j - item_base of the scene
     int64_t n;           // Gaussians of the scene
     int64_t tile_base;   // first batch-wide tile
+    int64_t super_base;  // first batch-wide super-tile
     int64_t pixel_base;  // first pixel of the batch-wide per-pixel planes
     int64_t value_base;  // first value of the batch-wide image buffers (3 H W per render)
     float* image;        // [3][H][W]
@@ -186,15 +215,19 @@ int launch_mlp_adam(float* master, float* grad, float* m, float* v, float lr, fl
                     float eps, int64_t t, void* W1, void* W2, void* W3, cudaStream_t s);
 int launch_mlp_pack(const float* master, void* W1, void* W2, void* W3, cudaStream_t s);
 
-// K2/K3: per-CTA tile counts in depth order, their scan, pair count + capacity check, and key
-// emission in depth order (so a stable sort by tile alone orders the pairs by tile, then depth).
-int launch_scan_emit(int64_t n, int TX, int T, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s, const RenderDesc* renders = nullptr, int R = 0);
-// K4/K5: stable radix sort of the pairs by the tile bits (returns which ping-pong buffer holds
-// the result) and ranges.
-int launch_sort_ranges(int64_t capacity, int tiles, const Scratch& sc, cudaStream_t s, int* buf);
-// the sorted pairs' full 64-bit keys (tile << 32 | depth bits) into keys[buf ^ 1]
-int launch_join_keys(int64_t capacity, int buf, const Scratch& sc, cudaStream_t s);
+// K2: pair count (the Gaussians' reached tiles, exact) and the coarse entries' per-CTA counts in
+// depth order with their scan; writes pair_count, pair_need and coarse_count and raises the
+// capacity status when pair_need exceeds `capacity`.  `supers` = super-tiles of the render (batch:
+// of all renders).
+int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t* perm, const Scratch& sc,
+                     cudaStream_t s);
+// K3-K5 after launch_bin_count: coarse entries in depth order, their stable sort by super-tile, the
+// reached-tile masks and pair lists of every tile in depth order (values = canonical indices in
+// vals[*out_buf], laid out super-tile by super-tile), and the tile ranges.  TX, TY: the tile grid
+// of a single render (renders == nullptr); a batch reads each render's grid from `renders`.
+int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t supers, int64_t capacity,
+                     const uint32_t* perm, const Scratch& sc, cudaStream_t s, int* out_buf,
+                     const RenderDesc* renders = nullptr, int R = 0);
 
 // K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting by the
 // low key_bits bits only (higher bits never take part; the pair count is read from sc.pair_count,
