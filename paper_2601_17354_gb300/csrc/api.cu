@@ -74,6 +74,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.depth_bits = c.take<uint32_t>(n);
     sc.rect = c.take<uint2>(n);
     sc.hitmask = c.take<uint32_t>(n);
+    sc.smask = c.take<uint4>(n);
     sc.touched = c.take<uint32_t>(n);
     sc.block_sums = c.take<uint32_t>(nb);
     sc.block_offsets = c.take<unsigned long long>(nb);
@@ -115,7 +116,7 @@ size_t carve_p(Scratch& sc, char* base, int64_t pairs) {
     sc.vals[0] = c.take<uint32_t>(pairs);
     sc.vals[1] = c.take<uint32_t>(pairs);
     sc.sort_hist = c.take<uint32_t>(lookback_words(32 / kRadixBits, sb ? sb : 1));  // 32-bit keys: at most 4 passes
-    sc.vseg = c.take<uint32_t>(pairs / 32 + 1);
+    sc.binfo = c.take<uint4>(pairs / 32 + 1);
     return c.off;
 }
 

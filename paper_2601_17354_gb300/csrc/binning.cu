@@ -130,18 +130,115 @@ k_coarse_scan(int nb, int64_t capacity, int64_t supers, Scratch sc) {
     }
 }
 
+// Transpose of the warp's 32 x 32 bit matrix (lane l holds row l): lane x returns column x, whose
+// bit l is bit x of lane l's word.  Five stages; at stage j the lanes l and l ^ j swap the block of
+// bits b with b & j set (upper lane l) against the block with b & j clear (lower lane l ^ j).
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
+    constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t m = kMask[k];
+        const uint32_t o = __shfl_xor_sync(kFull, x, j);
+        x = (lane & j) ? ((x & ~m) | ((o & ~m) >> j)) : ((x & m) | ((o & m) << j));
+    }
+    return x;
+}
+
+// Reach mask of one entry per lane (warp-collective): tiles of the super-tile at tile (bx, by) (each
+// lane its own) that Gaussian g reaches, bit (ty - by) kSuperW + tx - bx.  Rectangles of <= 32 tiles: read row by row
+// from the projection's reach mask.  Larger ones: the warp runs the projection's reach test over
+// all such lanes' candidate tiles together, 32 per round (candidate k by lane k mod 32, its lane
+// found by a shuffle binary search over the lanes' inclusive candidate counts), so one large
+// Gaussian does not hold its warp for 32 tests.
+__device__ __forceinline__ uint32_t entry_mask(bool valid, uint32_t g, uint2 r, uint32_t hm, uint32_t bx, uint32_t by,
+                                               int T, const Scratch& sc, int lane, uint32_t* s_big) {
+    uint32_t mask = 0, ncand = 0, X0 = 0, Y0 = 0, wX = 1;
+    float u = 0.f, v = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, ssx = 0.f, ssy = 0.f;
+    if (valid) {
+        const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
+        X0 = max(x0, bx);
+        Y0 = max(y0, by);
+        const uint32_t X1 = min(x1, bx + kSuperW), Y1 = min(y1, by + kSuperH);
+        const uint32_t w = x1 - x0;
+        wX = X1 - X0;  // >= 1: the super-tile lies in the Gaussian's super-tile rectangle
+        if (w * (y1 - y0) <= 32u) {
+            const uint32_t row = (1u << wX) - 1u;
+            for (uint32_t ty = Y0; ty < Y1; ++ty)
+                mask |= ((hm >> ((ty - y0) * w + (X0 - x0))) & row) << ((ty - by) * kSuperW + (X0 - bx));
+        } else {
+            ncand = wX * (Y1 - Y0);
+            const float4 p = sc.xyo[g], q = sc.conic[g];
+            u = p.x;
+            v = p.y;
+            ca = q.x;
+            cb = q.y;
+            cc = q.z;
+            ssx = __fdiv_rn(q.y, q.x);
+            ssy = __fdiv_rn(q.y, q.z);
+        }
+    }
+    uint32_t incl = ncand;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31), first = incl - ncand;
+    if (total) {  // warp-uniform
+        s_big[lane] = 0u;
+        __syncwarp();
+        for (uint32_t b = 0; b < total; b += 32) {
+            const uint32_t k = b + (uint32_t)lane;
+            int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive count exceeds k
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const uint32_t im = __shfl_sync(kFull, incl, mid);
+                if (lo < hi) {
+                    if (im > k) hi = mid;
+                    else lo = mid + 1;
+                }
+            }
+            const uint32_t of = __shfl_sync(kFull, first, lo), ow = __shfl_sync(kFull, wX, lo);
+            const uint32_t ox = __shfl_sync(kFull, X0, lo), oy = __shfl_sync(kFull, Y0, lo);
+            const float ou = __shfl_sync(kFull, u, lo), ov = __shfl_sync(kFull, v, lo);
+            const float oa = __shfl_sync(kFull, ca, lo), ob = __shfl_sync(kFull, cb, lo), oc = __shfl_sync(kFull, cc, lo);
+            const float osx = __shfl_sync(kFull, ssx, lo), osy = __shfl_sync(kFull, ssy, lo);
+            const uint32_t obx = __shfl_sync(kFull, bx, lo), oby = __shfl_sync(kFull, by, lo);  // owner's super-tile
+            if (k < total) {
+                const uint32_t local = k - of, dy = local / ow, dx = local - dy * ow;
+                const uint32_t tx = ox + dx, ty = oy + dy;
+                if (tile_hit(ou, ov, oa, ob, oc, osx, osy, (int)tx, (int)ty, T))
+                    atomicOr(&s_big[lo], 1u << ((ty - oby) * kSuperW + (tx - obx)));
+            }
+        }
+        __syncwarp();
+        mask |= s_big[lane];
+        __syncwarp();
+    }
+    return mask;
+}
+
 // ---------------------------------------------------------------------------------------------
-// K3: coarse entries (super-tile id, canonical index) of one CTA's Gaussians in depth order,
-// super-tiles row-major inside each Gaussian's super-tile rectangle.  Each warp walks the entries
-// of its own 32 Gaussians, 32 per round (entry k by lane k mod 32; its Gaussian found by a shuffle
-// binary search over the lanes' inclusive entry counts).
+// K3: coarse entries of one CTA's Gaussians in depth order, super-tiles row-major inside each
+// Gaussian's super-tile rectangle: key = super-tile id, value = the entry's own position e0, and at
+// e0 the Gaussian's canonical index and its reach mask of the super-tile (rectangles of <= 32
+// tiles: read from their reach bits; larger ones whose super-tile rectangle spans at most 2 x 2:
+// the projection's masks; the rest: entry_mask).  Each warp walks
+// the entries of its own 32 Gaussians, 32 per round (entry k by lane k mod 32; its Gaussian found
+// by a shuffle binary search over the lanes' inclusive entry counts).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
-k_coarse_emit(int64_t n, int SX, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
-              const RenderDesc* __restrict__ renders, int R) {
+k_coarse_emit(int64_t n, int SX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
+              uint32_t* __restrict__ gidx, uint32_t* __restrict__ gmask, const RenderDesc* __restrict__ renders,
+              int R) {
     __shared__ uint32_t s_sx0[kProjBlock], s_sy0[kProjBlock], s_sw[kProjBlock];
-    __shared__ uint32_t s_SX[kProjBlock], s_base[kProjBlock], s_gid[kProjBlock];
+    __shared__ uint32_t s_SX[kProjBlock], s_base[kProjBlock], s_gid[kProjBlock], s_hm[kProjBlock];
+    __shared__ uint2 s_rect[kProjBlock];
+    __shared__ uint4 s_sm[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
+    __shared__ uint32_t s_big[kProjBlock / 32][32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
     uint32_t cnt = 0;
@@ -149,12 +246,19 @@ k_coarse_emit(int64_t n, int SX, int64_t capacity, const uint32_t* __restrict__ 
         const uint32_t g = perm[i];
         s_gid[t] = g;
         if (sc.touched[g]) {
+            const uint2 r = sc.rect[g];
             uint32_t sx0, sy0, sx1, sy1;
-            super_rect(sc.rect[g], sx0, sy0, sx1, sy1);
+            super_rect(r, sx0, sy0, sx1, sy1);
             s_sx0[t] = sx0;
             s_sy0[t] = sy0;
             s_sw[t] = sx1 - sx0;
             cnt = (sx1 - sx0) * (sy1 - sy0);
+            s_rect[t] = r;
+            const uint32_t area = ((r.y & 0xffffu) - (r.x & 0xffffu)) * ((r.y >> 16) - (r.x >> 16));
+            s_hm[t] = area <= 32u ? sc.hitmask[g] : 0u;
+            if (area <= 32u) s_sw[t] |= 0x40000000u;                          // masks from hitmask
+            else if (sx1 - sx0 <= 2u && sy1 - sy0 <= 2u) s_sm[t] = sc.smask[g];  // projection's masks
+            else s_sw[t] |= 0x80000000u;                                      // entry_mask
             s_SX[t] = (uint32_t)SX;
             s_base[t] = 0;
             if (renders) {  // batch: item g belongs to the last render whose first item is <= g
@@ -197,15 +301,33 @@ k_coarse_emit(int64_t n, int SX, int64_t capacity, const uint32_t* __restrict__ 
             }
         }
         const uint32_t ofirst = __shfl_sync(kFull, first, lo);
-        if (k < total) {
-            const int o = warp * 32 + lo;
-            const uint32_t local = k - ofirst, w = s_sw[o];
+        const bool valid = k < total;
+        const int o = warp * 32 + lo;
+        uint32_t sx = 0, sy = 0, slot = 0, g = 0, how = 0;
+        uint2 r = make_uint2(0u, 0u);
+        uint32_t hm = 0;
+        if (valid) {
+            const uint32_t local = k - ofirst, w = s_sw[o] & 0x3fffffffu;
             const uint32_t dy = local / w, dx = local - dy * w;
-            const unsigned long long pos = out + k;
-            if (pos < (unsigned long long)capacity) {
-                ck[pos] = s_base[o] + (s_sy0[o] + dy) * s_SX[o] + s_sx0[o] + dx;
-                sc.vals[0][pos] = s_gid[o];
-            }
+            sx = s_sx0[o] + dx;
+            sy = s_sy0[o] + dy;
+            slot = 2u * dy + dx;
+            g = s_gid[o];
+            how = s_sw[o] >> 30;  // 1: hitmask, 0: projection's masks, 2: entry_mask
+            r = s_rect[o];
+            hm = s_hm[o];
+        }
+        uint32_t mask = entry_mask(valid && how == 2u, g, r, hm, sx * kSuperW, sy * kSuperH, T, sc, lane, s_big[warp]);
+        if (valid && how == 1u)
+            mask = super_mask_from_hits(hm, r.x & 0xffffu, r.x >> 16, r.y & 0xffffu, r.y >> 16, sx, sy);
+        else if (valid && how == 0u)
+            mask = smask_slot(s_sm[o], slot);
+        const unsigned long long pos = out + k;
+        if (valid && pos < (unsigned long long)capacity) {
+            ck[pos] = s_base[o] + sy * s_SX[o] + sx;
+            sc.vals[0][pos] = (uint32_t)pos;
+            gidx[pos] = g;
+            gmask[pos] = mask;
         }
     }
 }
@@ -494,7 +616,10 @@ k_ranges(int64_t capacity, uint32_t tiles, const uint32_t* __restrict__ keys, Sc
 // (block, tile) its first pair, and the block writes its pairs: entry e of tile x goes after the
 // entries of x in earlier blocks, earlier warps and earlier lanes, i.e. in depth order.
 // ---------------------------------------------------------------------------------------------
-constexpr int kFineWarps = kFineBlock / 32;
+constexpr int kFineThreads = 256;
+constexpr int kFineWarps = kFineThreads / 32;
+constexpr int kFineRounds = kFineBlock / kFineThreads;  // entries per thread: warp w takes the
+                                                        // block's entries [64 w, 64 w + 64), 32 a round
 constexpr int kFineGrid = 152 * 8;  // grid-stride over the blocks
 
 // tile grid of super-tile s: its position and the render it belongs to
@@ -530,7 +655,8 @@ __device__ __forceinline__ SuperCell super_cell(uint32_t s, int TX, int TY, cons
 }
 
 // One CTA: blocks per super-tile (ceil(entries / kFineBlock)), their exclusive scan into vbase
-// (vbase[S] = all blocks) and each block's super-tile into vseg.
+// (vbase[S] = all blocks) and each block's record binfo[v] = (super-tile, first entry, end entry,
+// block index inside the super-tile).
 __global__ void __launch_bounds__(kScanThreads)
 k_block_prefix(int S, int64_t capacity, Scratch sc) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -568,8 +694,11 @@ k_block_prefix(int S, int64_t capacity, Scratch sc) {
         const uint32_t first = carry + s_warp[warp] + incl - nb;
         if (s < S) {
             sc.vbase[s] = first;
-            for (uint32_t v = first; v < first + nb; ++v)
-                if (v < (uint64_t)capacity / 32) sc.vseg[v] = (uint32_t)s;
+            const uint2 cr = sc.crange[s];
+            for (uint32_t k = 0; k < nb; ++k)
+                if (first + k < (uint64_t)capacity / 32)
+                    sc.binfo[first + k] = make_uint4((uint32_t)s, cr.x + k * kFineBlock,
+                                                     min(cr.x + (k + 1) * kFineBlock, cr.y), k);
         }
         __syncthreads();
         if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
@@ -578,110 +707,26 @@ k_block_prefix(int S, int64_t capacity, Scratch sc) {
     if (threadIdx.x == 0) sc.vbase[S] = s_carry;
 }
 
-// Transpose of the warp's 32 x 32 bit matrix (lane l holds row l): lane x returns column x, whose
-// bit l is bit x of lane l's word.  Five stages; at stage j the lanes l and l ^ j swap the block of
-// bits b with b & j set (upper lane l) against the block with b & j clear (lower lane l ^ j).
-__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane) {
-    constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int j = 16 >> k;
-        const uint32_t m = kMask[k];
-        const uint32_t o = __shfl_xor_sync(kFull, x, j);
-        x = (lane & j) ? ((x & ~m) | ((o & ~m) >> j)) : ((x & m) | ((o & m) << j));
-    }
-    return x;
-}
-
-// Masks of every coarse entry (into masks[e]) and each block's per-tile counts (wc[32 v + x]).
-// A mask holds the tiles of super-tile (sx, sy) the entry's Gaussian reaches (bit (ty mod kSuperH)
-// kSuperW + tx mod kSuperW): read row by row from the projection's reach mask for rectangles of
-// <= 32 tiles; for larger ones the warp runs the projection's reach test over all such entries'
-// candidate tiles together, 32 per round (candidate k by lane k mod 32, its entry found by a
-// shuffle binary search over the lanes' inclusive candidate counts), so one large Gaussian does
-// not hold its warp for 32 tests.
-__global__ void __launch_bounds__(kFineBlock)
-k_fine_count(int64_t capacity, int T, int TX, int TY, const uint32_t* __restrict__ cv, uint32_t* __restrict__ masks,
-             uint32_t* __restrict__ wc, const uint32_t* __restrict__ vseg, int S, Scratch sc,
-             const RenderDesc* __restrict__ renders, int R) {
+// Each block's per-tile counts wc[32 v + x] from its entries' masks.
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_count(int64_t capacity, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ gmask,
+             uint32_t* __restrict__ wc, int S, Scratch sc) {
     __shared__ uint32_t s_cw[kFineWarps][32];
-    __shared__ uint32_t s_big[kFineWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t VB = sc.vbase[S];
     for (uint32_t v = blockIdx.x; v < VB; v += gridDim.x) {
         if ((uint64_t)v >= (uint64_t)capacity / 32) break;  // no slot for the block (capacity status raised)
-        const uint32_t s = vseg[v];
-        const uint2 cr = sc.crange[s];
-        const uint64_t e = (uint64_t)cr.x + (uint64_t)(v - sc.vbase[s]) * kFineBlock + threadIdx.x;
-        const bool valid = e < cr.y;
-        const SuperCell c = super_cell(s, TX, TY, renders, R);
-        const uint32_t bx = c.sx * kSuperW, by = c.sy * kSuperH;
-        uint32_t mask = 0, ncand = 0, X0 = 0, Y0 = 0, wX = 1;
-        float u = 0.f, vv = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, ssx = 0.f, ssy = 0.f;
-        if (valid) {
-            const uint32_t g = cv[e];
-            const uint2 r = sc.rect[g];
-            const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu, y1 = r.y >> 16;
-            X0 = max(x0, bx);
-            Y0 = max(y0, by);
-            const uint32_t X1 = min(x1, bx + kSuperW), Y1 = min(y1, by + kSuperH);
-            const uint32_t w = x1 - x0;
-            wX = X1 - X0;  // >= 1: the super-tile lies in the Gaussian's super-tile rectangle
-            if (w * (y1 - y0) <= 32u) {
-                const uint32_t hm = sc.hitmask[g], row = (1u << wX) - 1u;
-                for (uint32_t ty = Y0; ty < Y1; ++ty)
-                    mask |= ((hm >> ((ty - y0) * w + (X0 - x0))) & row) << ((ty - by) * kSuperW + (X0 - bx));
-            } else {
-                ncand = wX * (Y1 - Y0);
-                const float4 p = sc.xyo[g], q = sc.conic[g];
-                u = p.x;
-                vv = p.y;
-                ca = q.x;
-                cb = q.y;
-                cc = q.z;
-                ssx = __fdiv_rn(q.y, q.x);
-                ssy = __fdiv_rn(q.y, q.z);
-            }
-        }
-        uint32_t incl = ncand;
+        const uint4 bi = sc.binfo[v];  // super-tile, first entry, end entry, block of the super-tile
+        uint32_t m[kFineRounds];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
+        for (int r = 0; r < kFineRounds; ++r) {
+            const uint64_t e = (uint64_t)bi.y + warp * (32 * kFineRounds) + r * 32 + lane;
+            m[r] = e < bi.z ? gmask[cv[e]] : 0u;
         }
-        const uint32_t total = __shfl_sync(kFull, incl, 31), first = incl - ncand;
-        if (total) {  // warp-uniform
-            s_big[warp][lane] = 0u;
-            __syncwarp();
-            for (uint32_t b = 0; b < total; b += 32) {
-                const uint32_t k = b + (uint32_t)lane;
-                int lo = 0, hi = 31;  // owner of candidate k: the first lane whose inclusive count exceeds k
+        uint32_t cnt = 0;
 #pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo + hi) >> 1;
-                    const uint32_t im = __shfl_sync(kFull, incl, mid);
-                    if (lo < hi) {
-                        if (im > k) hi = mid;
-                        else lo = mid + 1;
-                    }
-                }
-                const uint32_t of = __shfl_sync(kFull, first, lo), ow = __shfl_sync(kFull, wX, lo);
-                const uint32_t ox = __shfl_sync(kFull, X0, lo), oy = __shfl_sync(kFull, Y0, lo);
-                const float ou = __shfl_sync(kFull, u, lo), ov = __shfl_sync(kFull, vv, lo);
-                const float oa = __shfl_sync(kFull, ca, lo), ob = __shfl_sync(kFull, cb, lo), oc = __shfl_sync(kFull, cc, lo);
-                const float osx = __shfl_sync(kFull, ssx, lo), osy = __shfl_sync(kFull, ssy, lo);
-                if (k < total) {
-                    const uint32_t local = k - of, dy = local / ow, dx = local - dy * ow;
-                    const uint32_t tx = ox + dx, ty = oy + dy;
-                    if (tile_hit(ou, ov, oa, ob, oc, osx, osy, (int)tx, (int)ty, T))
-                        atomicOr(&s_big[warp][lo], 1u << ((ty - by) * kSuperW + (tx - bx)));
-                }
-            }
-            __syncwarp();
-            mask |= s_big[warp][lane];
-        }
-        if (valid) masks[e] = mask;
-        s_cw[warp][lane] = __popc(warp_transpose(mask, lane));
+        for (int r = 0; r < kFineRounds; ++r) cnt += __popc(warp_transpose(m[r], lane));
+        s_cw[warp][lane] = cnt;
         __syncthreads();
         if (warp == 0) {
             uint32_t sum = 0;
@@ -775,11 +820,11 @@ k_super_scan(int S, int64_t capacity, Scratch sc) {
 }
 
 // The pairs of every block (values = canonical indices into out), and the ranges of a super-tile's
-// tiles from its first block.  Per warp the 32 masks are transposed, so lane x holds the set of
-// lanes reaching tile x: its count is one popcount and an entry's rank among them another.
-__global__ void __launch_bounds__(kFineBlock)
-k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ masks,
-            const uint32_t* __restrict__ wc, const uint32_t* __restrict__ vseg, int S, uint32_t* __restrict__ out,
+// tiles from its first block.  Per warp and round the 32 masks are transposed, so lane x holds the
+// set of lanes reaching tile x: its count is one popcount and an entry's rank among them another.
+__global__ void __launch_bounds__(kFineThreads)
+k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ gidx,
+            const uint32_t* __restrict__ gmask, const uint32_t* __restrict__ wc, int S, uint32_t* __restrict__ out,
             Scratch sc, const RenderDesc* __restrict__ renders, int R) {
     __shared__ uint32_t s_cw[kFineWarps][32];
     __shared__ uint32_t s_off[kFineWarps][32];
@@ -788,14 +833,24 @@ k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, c
     const uint32_t VB = sc.vbase[S];
     for (uint32_t v = blockIdx.x; v < VB; v += gridDim.x) {
         if ((uint64_t)v >= (uint64_t)capacity / 32) break;
-        const uint32_t s = vseg[v];
-        const uint2 cr = sc.crange[s];
-        const uint32_t j = v - sc.vbase[s];
-        const uint64_t e = (uint64_t)cr.x + (uint64_t)j * kFineBlock + threadIdx.x;
-        const bool valid = e < cr.y;
-        const uint32_t g = valid ? cv[e] : 0u, mask = valid ? masks[e] : 0u;
-        const uint32_t col = warp_transpose(mask, lane);  // lanes whose entry reaches tile `lane`
-        s_cw[warp][lane] = __popc(col);
+        const uint4 bi = sc.binfo[v];
+        const uint32_t s = bi.x;
+        uint32_t g[kFineRounds], m[kFineRounds], col[kFineRounds];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int r = 0; r < kFineRounds; ++r) {
+            const uint64_t e = (uint64_t)bi.y + warp * (32 * kFineRounds) + r * 32 + lane;
+            const bool valid = e < bi.z;
+            const uint32_t e0 = valid ? cv[e] : 0u;
+            g[r] = valid ? gidx[e0] : 0u;
+            m[r] = valid ? gmask[e0] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kFineRounds; ++r) {
+            col[r] = warp_transpose(m[r], lane);  // lanes whose entry of round r reaches tile `lane`
+            cnt += __popc(col[r]);
+        }
+        s_cw[warp][lane] = cnt;
         __syncthreads();
         if (warp == 0) {
             const uint32_t tt = sc.stt[32 * s + lane];
@@ -806,14 +861,13 @@ k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, c
                 if (lane >= o) incl += t;
             }
             const uint32_t ts = sc.sbase[s] + incl - tt;  // the tile's first pair
-            const uint64_t idx = 32ull * v + lane;
-            uint32_t base = ts + (idx < (uint64_t)capacity ? wc[idx] : 0u);
+            uint32_t base = ts + wc[32ull * v + lane];
 #pragma unroll
             for (int w = 0; w < kFineWarps; ++w) {
                 s_off[w][lane] = base;
                 base += s_cw[w][lane];
             }
-            if (j == 0) {
+            if (bi.w == 0) {
                 const SuperCell c = super_cell(s, TX, TY, renders, R);
                 const uint32_t tx = c.sx * kSuperW + (lane % kSuperW), ty = c.sy * kSuperH + (lane / kSuperW);
                 if ((int)tx < c.TX && (int)ty < c.TY) {
@@ -823,16 +877,22 @@ k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, c
             }
         }
         __syncthreads();
-        // each lane writes its entry's pairs: tile x after the warp's earlier lanes that reach x
-        uint32_t m = mask;
-        const int rounds = __reduce_max_sync(kFull, (uint32_t)__popc(mask));
-        for (int it = 0; it < rounds; ++it) {  // warp-uniform
-            const int x = m ? __ffs(m) - 1 : 0;
-            const uint32_t cx = __shfl_sync(kFull, col, x);
-            if (m) {
-                const uint64_t pos = (uint64_t)s_off[warp][x] + __popc(cx & lt);
-                if (pos < (uint64_t)capacity) out[pos] = g;
-                m &= m - 1u;
+        // each lane writes its entries' pairs: tile x after the warp's earlier entries that reach x
+#pragma unroll
+        for (int r = 0; r < kFineRounds; ++r) {
+            uint32_t mm = m[r];
+            const int rounds = __reduce_max_sync(kFull, (uint32_t)__popc(mm));
+            for (int it = 0; it < rounds; ++it) {  // warp-uniform
+                const int x = mm ? __ffs(mm) - 1 : 0;
+                uint32_t earlier = 0;
+#pragma unroll
+                for (int q = 0; q < r; ++q) earlier += __popc(__shfl_sync(kFull, col[q], x));
+                const uint32_t cx = __shfl_sync(kFull, col[r], x);
+                if (mm) {
+                    const uint64_t pos = (uint64_t)s_off[warp][x] + earlier + __popc(cx & lt);
+                    if (pos < (uint64_t)capacity) out[pos] = g[r];
+                    mm &= mm - 1u;
+                }
             }
         }
         __syncthreads();
@@ -993,10 +1053,15 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
     int launched = 0;
     *out_buf = 1;
+    // canonical index and reach mask of coarse entry e0 in the upper halves of the key buffers (the
+    // coarse keys are 32-bit: the sort uses the lower halves)
+    uint32_t* gidx = reinterpret_cast<uint32_t*>(sc.keys[0]) + capacity;
+    uint32_t* gmask = reinterpret_cast<uint32_t*>(sc.keys[1]) + capacity;
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (capacity <= 0 || supers <= 0) return 0;
     if (nb > 0) {
-        k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, capacity, perm, sc, renders, R);
+        k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, T, capacity, perm, sc, gidx, gmask,
+                                                renders, R);
         ++launched;
     }
     // the coarse entries arrive in depth order: a stable sort by super-tile keeps it in each
@@ -1011,16 +1076,14 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     cs.ranges = sc.crange;
     k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
     k_block_prefix<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
-    // masks in the first half of the free key buffer (as 32-bit words), block counts in the second
-    uint32_t* masks = reinterpret_cast<uint32_t*>(sc.keys[cb ^ 1]);
-    uint32_t* wc = masks + capacity;
+    // block counts over the sorted coarse keys (read by k_ranges before)
+    uint32_t* wc = reinterpret_cast<uint32_t*>(sc.keys[cb]);
     const uint32_t* cv = sc.vals[cb];
-    k_fine_count<<<kFineGrid, kFineBlock, 0, s>>>(capacity, T, TX, TY, cv, masks, wc, sc.vseg, (int)supers, sc,
-                                                   renders, R);
+    k_fine_count<<<kFineGrid, kFineThreads, 0, s>>>(capacity, cv, gmask, wc, (int)supers, sc);
     k_seg_scan<<<(unsigned)supers, 256, 0, s>>>(capacity, wc, sc);
     k_super_scan<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
-    k_fine_emit<<<kFineGrid, kFineBlock, 0, s>>>(capacity, TX, TY, cv, masks, wc, sc.vseg, (int)supers,
-                                                  sc.vals[cb ^ 1], sc, renders, R);
+    k_fine_emit<<<kFineGrid, kFineThreads, 0, s>>>(capacity, TX, TY, cv, gidx, gmask, wc, (int)supers, sc.vals[cb ^ 1],
+                                                    sc, renders, R);
     *out_buf = cb ^ 1;
     return launched + 6;
 }

@@ -40,7 +40,7 @@ constexpr size_t lookback_words(int passes, int64_t tiles) { return kLookbackHea
 // inside a super-tile.  Coarse entries (one per Gaussian and super-tile its rectangle overlaps)
 // are processed in blocks of kFineBlock.
 constexpr int kSuperW = 8, kSuperH = 4;
-constexpr int kFineBlock = 256;
+constexpr int kFineBlock = 512;
 inline int64_t super_tiles(int64_t TX, int64_t TY) {
     return ((TX + kSuperW - 1) / kSuperW) * ((TY + kSuperH - 1) / kSuperH);
 }
@@ -65,6 +65,7 @@ struct Scratch {
     uint32_t* depth_bits = nullptr;
     uint2* rect = nullptr;  // (x0 | y0 << 16, x1 | y1 << 16), tiles, half-open
     uint32_t* hitmask = nullptr;  // rectangles of <= 32 tiles: bit k (row-major in the rectangle) = tile k reached
+    uint4* smask = nullptr;       // > 32 tiles, super-tile rectangles of <= 2 x 2: mask per super-tile (smask_slot)
     uint32_t* touched = nullptr;
     uint32_t* block_sums = nullptr;
     unsigned long long* block_offsets = nullptr;
@@ -103,7 +104,8 @@ struct Scratch {
     unsigned long long* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
     uint32_t* sort_hist = nullptr;  // the sort's look-back: head words, then [passes][tiles][kRadix]
-    uint32_t* vseg = nullptr;       // super-tile of each fine block (pairs / 32 + 1 slots)
+    uint4* binfo = nullptr;         // fine blocks: super-tile, first entry, end entry, block of the
+                                    // super-tile (pairs / 32 + 1 slots)
 };
 
 constexpr int kLossBlocks = 1024;
@@ -294,6 +296,40 @@ __device__ __forceinline__ bool tile_hit(float u, float v, float ca, float cb, f
     if (hit_q(fminf(fmaxf(__fadd_rn(u, -__fmul_rn(sx, __fadd_rn(yl, -v))), xl), xh), yl, u, v, ca, cb, cc) <= 9.0f)
         return true;
     return hit_q(fminf(fmaxf(__fadd_rn(u, -__fmul_rn(sx, __fadd_rn(yh, -v))), xl), xh), yh, u, v, ca, cb, cc) <= 9.0f;
+}
+
+// Reach masks of super-tiles (bit (ty mod kSuperH) kSuperW + tx mod kSuperW = tile (tx, ty)).
+// A Gaussian of more than 32 tiles whose super-tile rectangle is at most 2 x 2 keeps its masks in
+// one uint4, slot 2 (sy - sy0) + (sx - sx0) (x, y, z, w); smaller ones keep their reach bits in the
+// rectangle's hitmask, larger ones have none (the binning computes theirs).
+__device__ __forceinline__ bool small_super_rect(uint2 rect) {
+    const uint32_t sx0 = (rect.x & 0xffffu) / kSuperW, sy0 = (rect.x >> 16) / kSuperH;
+    const uint32_t sx1 = ((rect.y & 0xffffu) + kSuperW - 1) / kSuperW, sy1 = ((rect.y >> 16) + kSuperH - 1) / kSuperH;
+    return sx1 - sx0 <= 2u && sy1 - sy0 <= 2u;
+}
+__device__ __forceinline__ uint32_t smask_slot(const uint4& m, uint32_t slot) {
+    return slot == 0 ? m.x : slot == 1 ? m.y : slot == 2 ? m.z : m.w;
+}
+// add tile (tx, ty) to the masks of a Gaussian whose super-tile rectangle starts at (sx0, sy0)
+__device__ __forceinline__ void smask_add(uint4& m, uint32_t tx, uint32_t ty, uint32_t sx0, uint32_t sy0) {
+    const uint32_t slot = 2u * (ty / kSuperH - sy0) + (tx / kSuperW - sx0);
+    const uint32_t bit = 1u << ((ty % kSuperH) * kSuperW + (tx % kSuperW));
+    if (slot == 0) m.x |= bit;
+    else if (slot == 1) m.y |= bit;
+    else if (slot == 2) m.z |= bit;
+    else m.w |= bit;
+}
+// Mask of super-tile (sx, sy), which overlaps the tile rectangle [x0, x1) x [y0, y1) of at most 32
+// tiles, from the rectangle's reach bits `hits` (row-major in the rectangle).
+__device__ __forceinline__ uint32_t super_mask_from_hits(uint32_t hits, uint32_t x0, uint32_t y0, uint32_t x1,
+                                                         uint32_t y1, uint32_t sx, uint32_t sy) {
+    const uint32_t bx = sx * kSuperW, by = sy * kSuperH;
+    const uint32_t X0 = max(x0, bx), X1 = min(x1, bx + kSuperW), Y0 = max(y0, by), Y1 = min(y1, by + kSuperH);
+    const uint32_t w = x1 - x0, row = (1u << (X1 - X0)) - 1u;
+    uint32_t mask = 0;
+    for (uint32_t ty = Y0; ty < Y1; ++ty)
+        mask |= ((hits >> ((ty - y0) * w + (X0 - x0))) & row) << ((ty - by) * kSuperW + (X0 - bx));
+    return mask;
 }
 
 // Bundle adjustment (Sec. III-A, Eq. 2-3): problem shape and chunking, index check, per-point

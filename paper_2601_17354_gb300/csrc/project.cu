@@ -211,10 +211,14 @@ __device__ __forceinline__ void camera_centre(const pgs_camera& cam, float c[3])
 // round, candidate k by lane k mod 32 with its owner's parameters (found by a binary search over
 // the lanes' inclusive counts); a lane's count and bit mask of reached tiles (rectangles of <= 32
 // tiles) come from the round ballots over its own candidates.  Every lane of the warp calls it;
-// the warp's rectangles hold at most 32 x 1024 candidates.
+// the warp's rectangles hold at most 32 x 1024 candidates.  For a lane with `super` set (a rectangle
+// of more than 32 tiles whose super-tile rectangle starts at (sx0, sy0) and spans at most 2 x 2)
+// the lane that evaluates a reached candidate also sets its bit in the owner's super-tile masks,
+// s_sm[4 owner + slot] (the warp's 32 x 4 words of shared memory, cleared by the owners before).
 __device__ __forceinline__ void warp_reach(uint32_t area, uint32_t w, uint32_t x0, uint32_t y0, float u, float v,
                                            float ca, float cb, float cc, float sx, float sy, int T, uint32_t& count,
-                                           uint32_t& hits) {
+                                           uint32_t& hits, bool super, uint32_t sx0, uint32_t sy0,
+                                           uint32_t* s_sm) {
     constexpr unsigned kAll = 0xffffffffu;
     const uint32_t lane = threadIdx.x & 31;
     uint32_t incl = area;
@@ -245,11 +249,17 @@ __device__ __forceinline__ void warp_reach(uint32_t area, uint32_t w, uint32_t x
         const float oca = __shfl_sync(kAll, ca, lo), ocb = __shfl_sync(kAll, cb, lo), occ = __shfl_sync(kAll, cc, lo);
         const float osx = __shfl_sync(kAll, sx, lo), osy = __shfl_sync(kAll, sy, lo);
         const int oT = __shfl_sync(kAll, T, lo);
+        const bool osuper = __shfl_sync(kAll, super, lo);
+        const uint32_t osx0 = __shfl_sync(kAll, sx0, lo), osy0 = __shfl_sync(kAll, sy0, lo);
         bool h = false;
         if (k < total) {  // then the owner's rectangle is not empty (ow >= 1)
             const uint32_t local = k - ofirst;
             const uint32_t dy = local / ow, dx = local - dy * ow;
-            h = tile_hit(ou, ov, oca, ocb, occ, osx, osy, (int)(ox0 + dx), (int)(oy0 + dy), oT);
+            const uint32_t tx = ox0 + dx, ty = oy0 + dy;
+            h = tile_hit(ou, ov, oca, ocb, occ, osx, osy, (int)tx, (int)ty, oT);
+            if (h && osuper)
+                atomicOr(&s_sm[4 * lo + 2u * (ty / kSuperH - osy0) + (tx / kSuperW - osx0)],
+                         1u << ((ty % kSuperH) * kSuperW + (tx % kSuperW)));
         }
         const uint32_t hb = __ballot_sync(kAll, h);
         // this lane's candidates in the round: [s0, s1), at lanes s0 - base ..
@@ -268,7 +278,8 @@ __device__ __forceinline__ void warp_reach(uint32_t area, uint32_t w, uint32_t x
 // active == false only take part in them.
 template <int DEG>
 __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
-                                             int TX, int TY, int T, int64_t j, const Scratch& sc, bool active) {
+                                             int TX, int TY, int T, int64_t j, const Scratch& sc, bool active,
+                                             uint32_t* s_sm) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     uint32_t count = 0;
@@ -316,6 +327,17 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
     }
     // of the rectangle's tiles, those whose pixel centres the 3-sigma ellipse reaches
     const uint32_t rw = vis ? x1 - x0 : 0u, area = vis ? rw * (y1 - y0) : 0u;  // at most 65535^2
+    // super-tile masks of rectangles of more than 32 tiles whose super-tile rectangle spans at most
+    // 2 x 2 (smaller rectangles keep their reach bits in hitmask)
+    const uint2 rect = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+    const bool super = area > 0u && small_super_rect(rect);
+    const uint32_t sx0 = x0 / kSuperW, sy0 = y0 / kSuperH;
+    uint4 sm = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t* const warp_sm = s_sm + 128 * (threadIdx.x >> 5);  // 32 lanes x 4 slots
+#pragma unroll
+    for (int k = 0; k < 4; ++k) warp_sm[4 * lane + k] = 0u;
+    __syncwarp();
     if (__any_sync(0xffffffffu, area > 1024u)) {
         // a large rectangle in the warp: each lane walks its own
         uint32_t k = 0;
@@ -324,9 +346,14 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
                 const bool h = tile_hit(G.u, G.v, con_a, con_b, con_c, sx, sy, (int)tx, (int)ty, T);
                 count += h;
                 if (area <= 32u && h) hits |= 1u << k;
+                if (super && area > 32u && h) smask_add(sm, tx, ty, sx0, sy0);
             }
     } else {
-        warp_reach(area, rw, x0, y0, vis ? G.u : 0.f, vis ? G.v : 0.f, con_a, con_b, con_c, sx, sy, T, count, hits);
+        warp_reach(area, rw, x0, y0, vis ? G.u : 0.f, vis ? G.v : 0.f, con_a, con_b, con_c, sx, sy, T, count, hits,
+                   super && area > 32u, sx0, sy0, warp_sm);
+        __syncwarp();
+        if (super && area > 32u)
+            sm = make_uint4(warp_sm[4 * lane], warp_sm[4 * lane + 1], warp_sm[4 * lane + 2], warp_sm[4 * lane + 3]);
     }
     if (!active) return;
     if (count > 0) {
@@ -357,8 +384,9 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
             sc.conic[j] = make_float4(con_a, con_b, con_c, 0.0f);
             sc.rgb[j] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
             sc.depth_bits[j] = __float_as_uint(G.zc);
-            sc.rect[j] = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+            sc.rect[j] = rect;
             sc.hitmask[j] = hits;
+            if (super && area > 32u) sc.smask[j] = sm;
         }
     }
     if (!finite) atomicOr(sc.status, kStatusNonfinite);
@@ -373,7 +401,8 @@ __global__ void __launch_bounds__(kProjBlock)
 k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc) {
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    project_item<DEG>(g, i < n ? i : 0, cam, TX, TY, T, i, sc, i < n);
+    __shared__ uint32_t s_sm[4 * kProjBlock];
+    project_item<DEG>(g, i < n ? i : 0, cam, TX, TY, T, i, sc, i < n, s_sm);
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
         *sc.dblocks = (uint32_t)((n + kDepthTile - 1) / kDepthTile);
@@ -399,8 +428,9 @@ k_project_fwd_batch(const RenderDesc* __restrict__ renders, int R, const SceneDe
     const int64_t j = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     const bool active = j < items;
     const RenderDesc& rd = renders[active ? render_of_item(renders, R, j) : 0];
+    __shared__ uint32_t s_sm[4 * kProjBlock];
     project_item<DEG>(scenes[rd.scene].params, active ? j - rd.item_base : 0, rd.cam, rd.TX, rd.TY, rd.tile, j, sc,
-                      active);
+                      active, s_sm);
     if (j == 0) {
         *sc.dcount = (unsigned long long)items;
         *sc.dblocks = (uint32_t)((items + kDepthTile - 1) / kDepthTile);
