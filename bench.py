@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 16-scene x 4-view, initializer, replay-cache and D-SSIM measurements")
     ap.add_argument("--batched-steps", type=int, default=60)
+    ap.add_argument("--no-learned-init", action="store_true",
+                    help="skip the learned-initializer experiment (32 scenes of 200k points, about 70 s)")
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: the autotuner's configuration, one capacity probe, "
                          "random targets, --steps steps; prints no bench line")
@@ -742,6 +744,9 @@ def run_ours(args):
         out["dssim"] = run_dssim(init, cams, targets, tile, tuned)
         out["bundle_adjustment"] = run_ba()
         out["mvs"] = run_mvs()
+    if not args.no_batched and not args.no_learned_init and rank == 0:
+        from paper_2601_17354_gb300 import evaluate as E
+        out["learned_init"] = E.learned_init_experiment()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, cams[0])
     if rank == 0:

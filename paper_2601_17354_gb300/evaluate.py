@@ -298,12 +298,37 @@ def prior_experiment(seed: int = 3, width: int = 320, height: int = 180, focal: 
     return out
 
 
+def learned_init_experiment(scenes: int = 32, held_out: int = 8, points: int = 200_000, width: int = 1280,
+                            height: int = 720, focal: float = 1000.0, fit_steps: int = 1000,
+                            views_per_step=(1, 2), check_every: int = 5, with_paper_batched: bool = True) -> dict:
+    """Learned-initializer experiment on surface scenes of `points` points: the network is fitted on
+    the converged Gaussians of plain 500-iteration runs of the training scenes (seeds 1000..) and
+    compared with the paper's initializer on the held-out views of the held-out scenes (seeds 2000..)
+    at 100/250/500 iterations; then the batched form is timed to the plain form's 500-iteration
+    PSNR on the held-out scenes, with the learned initializer (and, for reference, the paper's)."""
+    t0 = time.time()
+    train = list(range(1000, 1000 + scenes - held_out))
+    held = list(range(2000, 2000 + held_out))
+    res = compare_initializers(train, held, points, width, height, focal, fit_steps=fit_steps, keep_learned=True)
+    out = {"experiment": "learned initializer", "train_seeds": [train[0], train[-1]],
+           "held_out_seeds": [held[0], held[-1]], "points": points, "resolution": f"{width}x{height}",
+           "focal": focal, "psnr_paper_init": res.mean("paper"), "psnr_learned_init": res.mean("learned"),
+           "fit_steps": fit_steps, "fit_loss": res.fit_history[-1][1], "fallbacks": res.fallbacks,
+           "time_to_plain_psnr": []}
+    for vps in views_per_step:
+        for learned in ((res.learned_init, None) if with_paper_batched else (res.learned_init,)):
+            tt = time_to_target(held, points, width, height, focal, views_per_step=vps, learned=learned,
+                                adam=batched_adam(vps) if vps > 1 else None, check_every=check_every)
+            out["time_to_plain_psnr"].append(
+                {"views_per_step": vps, "learned": learned is not None,
+                 **{k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps", "all_reached", "ratio")}})
+    out["wall_s"] = time.time() - t0
+    return out
+
+
 def main(argv=None):
-    """Learned-initializer experiment on 32 surface scenes of 200k points (1280x720, fx = 1000):
-    the network is fitted on the converged Gaussians of plain 500-iteration runs of the training
-    scenes and compared with the paper's initializer on the held-out views of the held-out scenes
-    at 100/250/500 iterations; then the batched learned-init form is timed to the plain form's
-    500-iteration PSNR on the held-out scenes.  Prints one JSON line."""
+    """Runs learned_init_experiment (default: 32 surface scenes of 200k points, 1280x720, fx = 1000,
+    8 held out) and prints one JSON line."""
     import argparse
     import json
     ap = argparse.ArgumentParser()
@@ -317,25 +342,9 @@ def main(argv=None):
     ap.add_argument("--views-per-step", type=int, nargs="+", default=[1, 2])
     ap.add_argument("--check-every", type=int, default=5, help="batched steps between PSNR checks")
     args = ap.parse_args(argv)
-    t0 = time.time()
-    train = list(range(1000, 1000 + args.scenes - args.held_out))
-    held = list(range(2000, 2000 + args.held_out))
-    res = compare_initializers(train, held, args.points, args.width, args.height, args.focal,
-                               fit_steps=args.fit_steps, keep_learned=True)
-    out = {"experiment": "learned initializer", "train_scenes": len(train), "held_out_scenes": len(held),
-           "points": args.points, "resolution": f"{args.width}x{args.height}",
-           "psnr_paper_init": res.mean("paper"), "psnr_learned_init": res.mean("learned"),
-           "fit_loss": res.fit_history[-1][1], "fallbacks": res.fallbacks, "time_to_plain_psnr": []}
-    for vps in args.views_per_step:
-        for learned in (res.learned_init, None):
-            tt = time_to_target(held, args.points, args.width, args.height, args.focal, views_per_step=vps,
-                                learned=learned, adam=batched_adam(vps) if vps > 1 else None,
-                                check_every=args.check_every)
-            out["time_to_plain_psnr"].append(
-                {"views_per_step": vps, "learned": learned is not None,
-                 **{k: tt[k] for k in ("plain_gpu_s", "batched_gpu_s", "steps", "all_reached", "ratio")}})
-    out["wall_s"] = time.time() - t0
-    print(json.dumps(out))
+    print(json.dumps(learned_init_experiment(args.scenes, args.held_out, args.points, args.width, args.height,
+                                             args.focal, args.fit_steps, tuple(args.views_per_step),
+                                             args.check_every)))
 
 
 if __name__ == "__main__":
