@@ -48,7 +48,7 @@ FLOPS_BWD_COMP = 38     # Eq. 8 + chain to the nine screen-space gradients of a 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel on this workload, with a
 # digest of the sources it was taken on: reported only while those sources are unchanged.
 NCU_TRAFFIC = {
-    "composite_bwd": (85_359_872 + 2_602_240, "d90cea0f0524273a", ("paper_2601_17354_gb300/csrc/composite.cu",)),
+    "composite_bwd": (85_355_520 + 2_803_456, "a2c482101db273ab", ("paper_2601_17354_gb300/csrc/composite.cu",)),
 }
 
 
@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: the autotuner's configuration, one capacity probe, "
                          "random targets, --steps steps; prints no bench line")
+    ap.add_argument("--profile-mlp", action="store_true",
+                    help="short run for a profiler: --steps MLP forwards over the 6.4 M feature rows of "
+                         "32 scenes of 200k points; prints no bench line")
     return ap.parse_args()
 
 
@@ -780,10 +783,29 @@ def run_profile(args):
                       "launches": rast.launch_count(), "tile": tile, "forward": tuned.fwd, "backward": tuned.bwd}))
 
 
+def run_profile_mlp(args):
+    import torch
+    from paper_2601_17354_gb300 import initializer as I
+    from paper_2601_17354_gb300 import synthetic as S
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    pts = torch.from_numpy(np.ascontiguousarray(
+        S.sample_surface_points(rng, S.random_surfaces(rng), 200_000).astype(np.float32))).cuda()
+    init = I.Initializer()
+    x = init.paper_init(pts, 3).features_bf16.repeat(32, 1).contiguous()
+    mlp = I.MLP(init, seed=1)
+    for _ in range(args.steps):
+        mlp.forward(x)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_mlp": True, "rows": int(x.shape[0]), "steps": args.steps}))
+
+
 def main():
     args = parse()
     if args.profile_run:
         run_profile(args)
+    elif args.profile_mlp:
+        run_profile_mlp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
