@@ -231,16 +231,18 @@ __device__ __forceinline__ uint32_t entry_mask(bool valid, uint32_t g, uint2 r, 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock)
 k_coarse_emit(int64_t n, int SX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
-              uint32_t* __restrict__ gidx, uint32_t* __restrict__ gmask, const RenderDesc* __restrict__ renders,
-              int R) {
+              uint32_t* __restrict__ gidx, uint32_t* __restrict__ gmask, int passes, uint32_t last_mask,
+              const RenderDesc* __restrict__ renders, int R) {
     __shared__ uint32_t s_sx0[kProjBlock], s_sy0[kProjBlock], s_sw[kProjBlock];
     __shared__ uint32_t s_SX[kProjBlock], s_base[kProjBlock], s_gid[kProjBlock], s_hm[kProjBlock];
     __shared__ uint2 s_rect[kProjBlock];
     __shared__ uint4 s_sm[kProjBlock];
     __shared__ uint32_t s_warp[kProjBlock / 32];
     __shared__ uint32_t s_big[kProjBlock / 32][32];
+    __shared__ uint32_t s_hist[4][kRadix];  // digit counts of the written keys, pass by pass
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + t;
+    for (int k = t; k < 4 * kRadix; k += kProjBlock) (&s_hist[0][0])[k] = 0u;
     uint32_t cnt = 0;
     if (i < n) {
         const uint32_t g = perm[i];
@@ -324,11 +326,21 @@ k_coarse_emit(int64_t n, int SX, int T, int64_t capacity, const uint32_t* __rest
             mask = smask_slot(s_sm[o], slot);
         const unsigned long long pos = out + k;
         if (valid && pos < (unsigned long long)capacity) {
-            ck[pos] = s_base[o] + sy * s_SX[o] + sx;
+            const uint32_t key = s_base[o] + sy * s_SX[o] + sx;
+            ck[pos] = key;
             sc.vals[0][pos] = (uint32_t)pos;
             gidx[pos] = g;
             gmask[pos] = mask;
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(key >> (p * kRadixBits)) & (p == passes - 1 ? last_mask : kRadix - 1)], 1u);
         }
+    }
+    // the sort's digit totals: this CTA's counts added into its partial copy (zeroed before)
+    __syncthreads();
+    uint32_t* copy = sc.digit_totals + (blockIdx.x % kTotalCopies) * (kMaxPasses * kRadix);
+    for (int k = t; k < passes * kRadix; k += kProjBlock) {
+        const uint32_t v = (&s_hist[0][0])[k];
+        if (v) atomicAdd(&copy[k], v);
     }
 }
 
@@ -657,13 +669,40 @@ __device__ __forceinline__ SuperCell super_cell(uint32_t s, int TX, int TY, cons
 // One CTA: blocks per super-tile (ceil(entries / kFineBlock)), their exclusive scan into vbase
 // (vbase[S] = all blocks) and each block's record binfo[v] = (super-tile, first entry, end entry,
 // block index inside the super-tile).
+// crange_from: 0 = crange is already filled (k_ranges over the sorted keys); 1 = the sort was one
+// pass of the whole super-tile id (S <= 256): crange is the exclusive scan of its digit totals;
+// 2 = one super-tile: crange[0] = all kept entries.
 __global__ void __launch_bounds__(kScanThreads)
-k_block_prefix(int S, int64_t capacity, Scratch sc) {
+k_block_prefix(int S, int64_t capacity, Scratch sc, int crange_from) {
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (crange_from == 1) {  // S <= 256 (the parameter is the same for every thread)
+        const int s = threadIdx.x;
+        uint32_t c = 0;
+        if (s < kRadix) {
+#pragma unroll
+            for (int cpy = 0; cpy < kTotalCopies; ++cpy) c += sc.digit_totals[(size_t)cpy * kMaxPasses * kRadix + s];
+        }
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        if (s < S) sc.crange[s] = make_uint2(before + incl - c, before + incl);
+        __syncthreads();  // s_warp is reused below; crange is read below
+    }
+    if (crange_from == 2 && threadIdx.x == 0) {
+        const unsigned long long Ce = *sc.coarse_count;
+        sc.crange[0] = make_uint2(0u, (uint32_t)(Ce < (unsigned long long)capacity ? Ce : (unsigned long long)capacity));
+    }
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = 0; base < S; base += kScanThreads) {
         const int s = base + threadIdx.x;
         uint32_t nb = 0;
@@ -967,7 +1006,8 @@ void enable_scatter_smem() {
 // CTA tiles of kSortThreads x kItems keys: the digit totals of every pass in one read of the keys,
 // then one launch per pass.  Returns the launches and leaves the sorted buffer's index in *out_buf.
 template <typename KeyT, int kItems>
-int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf) {
+int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf,
+                bool totals_ready = false) {
     constexpr int kTile = kSortThreads * kItems;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
     const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
@@ -980,10 +1020,12 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     if (sb_max <= 0 || passes <= 0) return 0;
     enable_scatter_smem<KeyT, kItems>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
-    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
     // abort word, tickets and the look-back words of every pass start cleared
     cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * (kLookbackHead + (size_t)passes * kRadix * sb_max), s);
-    k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
+    if (!totals_ready) {  // else the kernel that wrote the keys counted their digits
+        cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+        k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
+    }
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
         const uint32_t dmask = p == passes - 1 ? last_mask : (uint32_t)(kRadix - 1);
@@ -992,7 +1034,7 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
         buf ^= 1;
     }
     *out_buf = buf;
-    return 1 + passes;
+    return (totals_ready ? 0 : 1) + passes;
 }
 
 // One pass of the pair sort over three tiles whose first is never published: the ticket starts at
@@ -1059,23 +1101,31 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     uint32_t* gmask = reinterpret_cast<uint32_t*>(sc.keys[1]) + capacity;
     cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (capacity <= 0 || supers <= 0) return 0;
+    int bits = 0;
+    while ((1ll << bits) < (long long)supers) ++bits;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
+    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
     if (nb > 0) {
         k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, T, capacity, perm, sc, gidx, gmask,
-                                                renders, R);
+                                                passes, last_mask, renders, R);
         ++launched;
     }
     // the coarse entries arrive in depth order: a stable sort by super-tile keeps it in each
-    // super-tile (its count and CTA count are the coarse stage's)
+    // super-tile (its count and CTA count are the coarse stage's, its digit totals the emission's)
     Scratch cs = sc;
     cs.pair_count = sc.coarse_count;
-    int bits = 0;
-    while ((1ll << bits) < (long long)supers) ++bits;
     int cb = 0;
-    launched += sort_passes<uint32_t, kSortItems>(capacity, 0, bits, cs, s, &cb);
-    cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
-    cs.ranges = sc.crange;
-    k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
-    k_block_prefix<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
+    launched += sort_passes<uint32_t, kSortItems>(capacity, 0, bits, cs, s, &cb, true);
+    int crange_from = passes == 0 ? 2 : 1;
+    if (passes > 1) {  // the super-tiles' ranges from the sorted keys
+        cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
+        cs.ranges = sc.crange;
+        k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
+        ++launched;
+        crange_from = 0;
+    }
+    k_block_prefix<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc, crange_from);
     // block counts over the sorted coarse keys (read by k_ranges before)
     uint32_t* wc = reinterpret_cast<uint32_t*>(sc.keys[cb]);
     const uint32_t* cv = sc.vals[cb];
@@ -1085,7 +1135,7 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     k_fine_emit<<<kFineGrid, kFineThreads, 0, s>>>(capacity, TX, TY, cv, gidx, gmask, wc, (int)supers, sc.vals[cb ^ 1],
                                                     sc, renders, R);
     *out_buf = cb ^ 1;
-    return launched + 6;
+    return launched + 5;
 }
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,

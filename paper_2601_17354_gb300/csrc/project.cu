@@ -277,9 +277,9 @@ __device__ __forceinline__ void warp_reach(uint32_t area, uint32_t w, uint32_t x
 // item j.  Every lane of the warp calls it (the reach tests are warp-collective); lanes with
 // active == false only take part in them.
 template <int DEG>
-__device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
-                                             int TX, int TY, int T, int64_t j, const Scratch& sc, bool active,
-                                             uint32_t* s_sm) {
+__device__ __forceinline__ uint32_t project_item(const pgs_gaussians& g, int64_t i, const pgs_camera& cam,
+                                                 int TX, int TY, int T, int64_t j, const Scratch& sc, bool active,
+                                                 uint32_t* s_sm) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t n = g.n;
     uint32_t count = 0;
@@ -355,7 +355,7 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
         if (super && area > 32u)
             sm = make_uint4(warp_sm[4 * lane], warp_sm[4 * lane + 1], warp_sm[4 * lane + 2], warp_sm[4 * lane + 3]);
     }
-    if (!active) return;
+    if (!active) return 0xffffffffu;
     if (count > 0) {
         // value path: opacity, colour (the conic is the decision path's)
         const float opacity = 1.0f / (1.0f + expf(-logit));
@@ -392,8 +392,10 @@ __device__ __forceinline__ void project_item(const pgs_gaussians& g, int64_t i, 
     if (!finite) atomicOr(sc.status, kStatusNonfinite);
     sc.touched[j] = count;
     // depth-sort input: visible Gaussians by depth bits, culled ones last
-    reinterpret_cast<uint32_t*>(sc.dkeys[0])[j] = count > 0 ? sc.depth_bits[j] : 0xffffffffu;
+    const uint32_t key = count > 0 ? sc.depth_bits[j] : 0xffffffffu;
+    reinterpret_cast<uint32_t*>(sc.dkeys[0])[j] = key;
     sc.dvals[0][j] = (uint32_t)j;
+    return key;
 }
 
 template <int DEG>
