@@ -47,10 +47,70 @@ __device__ __forceinline__ void super_rect(uint2 r, uint32_t& sx0, uint32_t& sy0
     sy1 = ((r.y >> 16) + kSuperH - 1) / kSuperH;
 }
 
+// Exclusive scan of `count` values by one CTA (a whole number of warps, at most 1024 threads):
+// load(i) gives value i, store(i, prefix) receives its exclusive prefix; returns the total to every
+// thread.  Every thread of the CTA calls it.
+template <class Load, class Store>
+__device__ unsigned long long cta_scan(int count, Load load, Store store) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < count; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const unsigned long long v = idx < count ? load(idx) : 0ull;
+        unsigned long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long w = lane < nw ? s_warp[lane] : 0ull;
+            unsigned long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long t = __shfl_up_sync(kFull, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < nw) s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        if (idx < count) store(idx, carry + s_warp[warp] + incl - v);
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = carry + s_warp[warp] + incl;
+        __syncthreads();
+    }
+    return s_carry;
+}
+
+// Is this CTA the last of the grid to get here?  Each CTA's writes before the call are visible to
+// the last one (fence before the ticket, fence after); the last CTA resets the ticket.  No CTA
+// waits for another.
+__device__ __forceinline__ bool last_cta(uint32_t* ticket) {
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (s_last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
 // Per CTA of depth-ordered Gaussians: coarse entries (super-tiles of the rectangle) into
-// block_sums; reached tiles added into pair_count (zeroed before).
+// block_sums; reached tiles added into pair_count (zeroed before).  The last CTA then scans the
+// per-CTA counts into their offsets and sets the coarse total, the coarse sort's CTA count, the
+// capacity the render needs (pairs, and the coarse stage's entries and counters) and the capacity
+// check.
 __global__ void __launch_bounds__(kProjBlock)
-k_coarse_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
+k_coarse_counts(int64_t n, int64_t capacity, int64_t supers, const uint32_t* __restrict__ perm, Scratch sc) {
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     uint32_t area = 0, reached = 0;
     if (i < n) {
@@ -78,48 +138,12 @@ k_coarse_counts(int64_t n, const uint32_t* __restrict__ perm, Scratch sc) {
             if (r) atomicAdd(sc.pair_count, r);
         }
     }
-}
-
-// Exclusive scan of the per-CTA coarse counts -> their offsets; coarse total, the coarse sort's CTA
-// count, the capacity the render needs (pairs, and the coarse stage's entries and counters) and
-// the capacity check.
-__global__ void __launch_bounds__(kScanThreads)
-k_coarse_scan(int nb, int64_t capacity, int64_t supers, Scratch sc) {
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    __shared__ unsigned long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < nb; base += kScanThreads) {
-        const int idx = base + threadIdx.x;
-        const unsigned long long v = idx < nb ? sc.block_sums[idx] : 0ull;
-        unsigned long long incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned long long w = s_warp[lane];
-            unsigned long long wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long t = __shfl_up_sync(kFull, wi, o);
-                if (lane >= o) wi += t;
-            }
-            s_warp[lane] = wi - w;
-        }
-        __syncthreads();
-        const unsigned long long carry = s_carry;
-        if (idx < nb) sc.block_offsets[idx] = carry + s_warp[warp] + incl - v;
-        __syncthreads();
-        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
-        __syncthreads();
-    }
+    if (!last_cta(&sc.bin_ticket[0])) return;
+    const unsigned long long Ce = cta_scan(
+        (int)gridDim.x, [&](int k) { return (unsigned long long)__ldcg(&sc.block_sums[k]); },
+        [&](int k, unsigned long long v) { sc.block_offsets[k] = v; });
     if (threadIdx.x == 0) {
-        const unsigned long long Ce = s_carry, P = *sc.pair_count;
+        const unsigned long long P = atomicAdd(sc.pair_count, 0ull);
         *sc.coarse_count = Ce;
         const unsigned long long kept = Ce < (unsigned long long)capacity ? Ce : (unsigned long long)capacity;
         *sc.sort_blocks = (uint32_t)((kept + kSortTile - 1) / kSortTile);
@@ -778,7 +802,8 @@ k_fine_count(int64_t capacity, const uint32_t* __restrict__ cv, const uint32_t* 
 }
 
 // One CTA per super-tile: exclusive scan of its blocks' per-tile counts (in place), the tiles'
-// pair counts stt[32 s + x] and the super-tile's pairs ssum[s].
+// pair counts stt[32 s + x] and the super-tile's pairs ssum[s].  The last CTA then scans the
+// super-tiles' pairs into their first pair sbase[s] and sets the pair count.
 __global__ void __launch_bounds__(256)
 k_seg_scan(int64_t capacity, uint32_t* __restrict__ wc, Scratch sc) {
     __shared__ uint32_t s_part[8][32];
@@ -812,46 +837,11 @@ k_seg_scan(int64_t capacity, uint32_t* __restrict__ wc, Scratch sc) {
         const uint32_t all = __reduce_add_sync(kFull, total);
         if (x == 0) sc.ssum[s] = all;
     }
-}
-
-// One CTA: exclusive scan of the super-tiles' pairs -> their first pair sbase[s]; the pair count.
-__global__ void __launch_bounds__(kScanThreads)
-k_super_scan(int S, int64_t capacity, Scratch sc) {
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    __shared__ unsigned long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < S; base += kScanThreads) {
-        const int s = base + threadIdx.x;
-        const unsigned long long v = s < S ? sc.ssum[s] : 0ull;
-        unsigned long long incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned long long w = s_warp[lane];
-            unsigned long long wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long t = __shfl_up_sync(kFull, wi, o);
-                if (lane >= o) wi += t;
-            }
-            s_warp[lane] = wi - w;
-        }
-        __syncthreads();
-        const unsigned long long carry = s_carry;
-        if (s < S) sc.sbase[s] = (uint32_t)(carry + s_warp[warp] + incl - v);
-        __syncthreads();
-        if (threadIdx.x == kScanThreads - 1) s_carry = carry + s_warp[warp] + incl;
-        __syncthreads();
-    }
+    if (!last_cta(&sc.bin_ticket[1])) return;
+    const unsigned long long P = cta_scan(
+        (int)gridDim.x, [&](int k) { return (unsigned long long)__ldcg(&sc.ssum[k]); },
+        [&](int k, unsigned long long v) { sc.sbase[k] = (uint32_t)v; });
     if (threadIdx.x == 0) {
-        const unsigned long long P = s_carry;
         *sc.pair_count = P;
         if (P > *sc.pair_need) *sc.pair_need = P;
         if (P > (unsigned long long)capacity) atomicOr(sc.status, kStatusCapacity);
@@ -1084,9 +1074,8 @@ int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t
                      cudaStream_t s) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
     cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
-    if (nb > 0) k_coarse_counts<<<nb, kProjBlock, 0, s>>>(n, perm, sc);
-    k_coarse_scan<<<1, kScanThreads, 0, s>>>(nb, capacity, supers, sc);
-    return nb > 0 ? 2 : 1;
+    k_coarse_counts<<<nb > 0 ? nb : 1, kProjBlock, 0, s>>>(n, capacity, supers, perm, sc);
+    return 1;
 }
 
 int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t supers, int64_t capacity,
@@ -1131,11 +1120,10 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     const uint32_t* cv = sc.vals[cb];
     k_fine_count<<<kFineGrid, kFineThreads, 0, s>>>(capacity, cv, gmask, wc, (int)supers, sc);
     k_seg_scan<<<(unsigned)supers, 256, 0, s>>>(capacity, wc, sc);
-    k_super_scan<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc);
     k_fine_emit<<<kFineGrid, kFineThreads, 0, s>>>(capacity, TX, TY, cv, gidx, gmask, wc, (int)supers, sc.vals[cb ^ 1],
                                                     sc, renders, R);
     *out_buf = cb ^ 1;
-    return launched + 5;
+    return launched + 4;
 }
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,

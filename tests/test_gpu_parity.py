@@ -264,6 +264,22 @@ def test_single_gaussian_covering_every_tile(R):
     compare_forward(img, T, last, oracle.render(g, cam), (rast, g, cam, 16))
 
 
+def test_many_super_tiles_take_two_grouping_passes(R):
+    """1280x720 with 8x8 tiles: 160 x 90 tiles in 20 x 23 = 460 super-tiles of 8 x 4 tiles, so the
+    coarse entries are grouped by a two-pass sort over 9-bit super-tile ids and the super-tiles'
+    ranges come from the sorted keys: keys, values and ranges bit-exact against the oracle, image
+    and `last` checked on every pixel."""
+    sc = S.surface_scene(4, 20000, 1, 1280, 720, 1000.0, n_cameras=8)
+    g, cam = sc.gt, sc.cameras[2]
+    TX, TY = -(-cam.width // 8), -(-cam.height // 8)
+    assert -(-TX // 8) * -(-TY // 4) > 256
+    rast = R.Rasterizer(tile=8)
+    rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam, rast)
+    assert code == 0
+    assert pairs == check_keys(rast, g, cam, 8)
+    compare_forward(img, T, last, oracle.render(g, cam, 8), (rast, g, cam, 8))
+
+
 def test_one_pixel_image(R):
     g, cam = SCENES["tiny_2k_128"]()
     cam1 = S.Camera(1, 1, cam.fx, cam.fy, 0.5, 0.5, cam.viewmat)
