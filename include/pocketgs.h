@@ -228,8 +228,9 @@ int64_t pgs_launch_count(const pgs_ctx* ctx);
    that may not allocate device memory themselves, such as code whose device memory is owned by
    another allocator (a framework's caching pool or an arena reserved at start-up, where a direct
    cudaMalloc can fail or fragment the reservation) or latency-critical loops in which
-   cudaMalloc / cudaFree would synchronise the device.  It runs the radix sort of pgs_render
-   (stable, least-significant-digit first, 8-bit digits, the last digit masked) by the low key_bits
+   cudaMalloc / cudaFree would synchronise the device.  It runs the radix sort pgs_render uses for
+   its depth keys and coarse entries (stable, least-significant-digit first, 8-bit digits, one
+   launch per pass with decoupled look-back, the last digit masked) by the low key_bits
    bits of count (key, value) pairs (higher key bits never take part in the order; keys_out keeps
    them as they were): keys_in/vals_in (device, read only) -> keys_out/vals_out (device, caller
    owned, not overlapping the inputs).  It allocates nothing: its scratch is one file-scope device
@@ -251,7 +252,8 @@ int pgs_sort_pairs_static_status(void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------------
    Batched training: many views of many scenes (uneven Gaussian counts and resolutions) in one
-   step.  All renders of a step share one projection launch, one depth sort, one pair sort, one
+   step.  All renders of a step share one projection launch, one depth sort, one binning (coarse
+   entries of every render's super-tiles, one grouping sort, one fine stage), one
    persistent compositing launch forward and one backward (CTAs take tiles of every render,
    heaviest first, from a device work counter), one loss launch and one fused backward + Adam
    launch that sums each Gaussian's gradient over its scene's views.  The step can be captured
@@ -508,8 +510,8 @@ int pgs_mvs_read(pgs_mvs* mvs, int32_t what, void* dst, int64_t bytes);
 int pgs_mvs_fuse(pgs_mvs* mvs, const pgs_camera* target, const float* depth, float* points, int32_t* pixels,
                  int64_t capacity, int64_t* count);
 
-/* Failure-detection self-test of the sort's bounded waits: one pass of the pair sort runs on the
-   context's scratch with the first tile's look-back words never published, so the next tile's wait
+/* Failure-detection self-test of the sort's bounded waits: one pass of the radix sort runs on the
+   context's pair scratch with the first tile's look-back words never published, so the next tile's wait
    runs out (about a second), records the timeout in the device status word and abandons the pass
    without writing.  Synchronises; returns what pgs_status then reads (PGS_ERR_TIMEOUT when the
    detection works) and clears it.  The context stays usable; its last render is invalidated.

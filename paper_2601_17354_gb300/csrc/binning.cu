@@ -1027,7 +1027,7 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     return (totals_ready ? 0 : 1) + passes;
 }
 
-// One pass of the pair sort over three tiles whose first is never published: the ticket starts at
+// One radix-sort pass over three tiles of the pair buffers, the first never published: the ticket starts at
 // 1, so tile 1 waits on tile 0 until its bound runs out (failure-detection self-test).
 __global__ void k_selftest_setup(Scratch sc) {
     *sc.pair_count = 3ull * kSortTile;

@@ -94,7 +94,7 @@ struct Scratch {
     float* loss_partials = nullptr;   // [2][kLossBlocks]
     uint32_t* loss_ticket = nullptr;
     // depth sort of the Gaussians: keys = depth bits (culled: all ones), values = canonical index;
-    // its pair count / CTA count words and histograms, separate from the pair sort's
+    // its key count / CTA count words and histograms, separate from those of the coarse entries' sort
     unsigned long long* dkeys[2] = {nullptr, nullptr};
     uint32_t* dvals[2] = {nullptr, nullptr};
     uint32_t* dhist = nullptr;  // the depth sort's look-back

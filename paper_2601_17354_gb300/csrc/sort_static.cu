@@ -1,4 +1,4 @@
-// Allocation-free variant of the pair sort (K4): the same least-significant-digit radix sort,
+// Allocation-free (key, value) sort: the least-significant-digit radix sort of K4,
 // with all of its scratch in one file-scope device array instead of context memory.
 //
 // For callers that may not call cudaMalloc: code whose device memory is owned by another

@@ -1,11 +1,11 @@
-"""The allocation-free pair sort (pgs_sort_pairs_static), called through the C ABI, against the
-sort inside pgs_render.
+"""The allocation-free (key, value) sort (pgs_sort_pairs_static), called through the C ABI,
+against the tile lists of pgs_render and against numpy's stable sort.
 
 Some callers cannot allocate device memory themselves (their memory belongs to another
 allocator's pool, or a cudaMalloc would synchronise a latency-critical loop); this entry point
-keeps its scratch in a fixed device array instead.  The test feeds it the render's pairs in their
-emission order (canonical index, then tile) and expects the render's sorted keys and values bit
-for bit, on two calls in a row with different inputs, so the second call also checks that what
+keeps its scratch in a fixed device array instead.  The test feeds it the render's pairs in
+canonical order (canonical index, then tile) and expects the render's lists (the stable sort of
+the pairs by tile and depth) bit for bit, on two calls in a row with different inputs, so the second call also checks that what
 the first left in the shared scratch does not leak into the result.
 
 This file is collected last on purpose.
