@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--profile-run", action="store_true",
                     help="short run for a profiler: the autotuner's configuration, one capacity probe, "
                          "random targets, --steps steps; prints no bench line")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="short run for a profiler: the batched 16-scene x 4-view workload at tile 16, strips "
+                         "(2, 64), captured, --steps steps; prints no bench line")
     ap.add_argument("--profile-mlp", action="store_true",
                     help="short run for a profiler: --steps MLP forwards over the 6.4 M feature rows of "
                          "32 scenes of 200k points; prints no bench line")
@@ -783,6 +786,32 @@ def run_profile(args):
                       "launches": rast.launch_count(), "tile": tile, "forward": tuned.fwd, "backward": tuned.bwd}))
 
 
+def run_profile_batched(args):
+    import torch
+    from paper_2601_17354_gb300 import batch as B
+    from paper_2601_17354_gb300 import rasterizer as R
+    from paper_2601_17354_gb300 import synthetic as S
+    torch.cuda.set_device(0)
+    scenes = S.batched_scenes(11, BATCH_SCENES, BATCH_VIEWS, sh_degree=SH_DEGREE)
+    rast = R.Rasterizer()
+    bufs, views = [], []
+    for s, sc in enumerate(scenes):
+        gt = R.GaussianBuffer.from_arrays(sc.gt)
+        for c in sc.cameras:
+            views.append((s, c, rast.render(gt, c).clone()))
+        bufs.append(R.GaussianBuffer.from_arrays(sc.init))
+    del rast
+    torch.cuda.synchronize()
+    bt = B.BatchTrainer(bufs, views, tile=16)
+    bt.set_variant(2, 64)
+    bt.capture()
+    for _ in range(args.steps):
+        bt.step()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batched": True, "steps": args.steps, "status": bt.status()[0],
+                      "launches_per_step": bt.launch_count() // max(1, args.steps)}))
+
+
 def run_profile_mlp(args):
     import torch
     from paper_2601_17354_gb300 import initializer as I
@@ -806,6 +835,8 @@ def main():
         run_profile(args)
     elif args.profile_mlp:
         run_profile_mlp(args)
+    elif args.profile_batched:
+        run_profile_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -101,7 +101,8 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.pair_count = c.take<unsigned long long>(1);
     sc.pair_need = c.take<unsigned long long>(1);
     sc.coarse_count = c.take<unsigned long long>(1);
-    sc.bin_ticket = c.take<uint32_t>(2);
+    sc.bin_ticket = c.take<uint32_t>(3);
+    sc.tile_buckets = c.take<uint32_t>(256);
     sc.sort_blocks = c.take<uint32_t>(1);
     sc.digit_totals = c.take<uint32_t>(kTotalWords);
     sc.loss_partials = c.take<float>(2 * kLossBlocks);

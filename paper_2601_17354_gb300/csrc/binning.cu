@@ -47,20 +47,26 @@ __device__ __forceinline__ void super_rect(uint2 r, uint32_t& sx0, uint32_t& sy0
     sy1 = ((r.y >> 16) + kSuperH - 1) / kSuperH;
 }
 
-// Exclusive scan of `count` values by one CTA (a whole number of warps, at most 1024 threads):
-// load(i) gives value i, store(i, prefix) receives its exclusive prefix; returns the total to every
-// thread.  Every thread of the CTA calls it.
+// Exclusive scan of `count` values by one CTA (a whole number of warps, at most 1024 threads),
+// kV consecutive values per thread and step: load(i) gives value i, store(i, prefix) receives its
+// exclusive prefix; returns the total to every thread.  Every thread of the CTA calls it.
 template <class Load, class Store>
 __device__ unsigned long long cta_scan(int count, Load load, Store store) {
+    constexpr int kV = 8;
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < count; base += blockDim.x) {
-        const int idx = base + threadIdx.x;
-        const unsigned long long v = idx < count ? load(idx) : 0ull;
-        unsigned long long incl = v;
+    for (int base = 0; base < count; base += blockDim.x * kV) {
+        const int first = base + threadIdx.x * kV;
+        unsigned long long v[kV], tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            v[k] = first + k < count ? load(first + k) : 0ull;
+            tsum += v[k];
+        }
+        unsigned long long incl = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long t = __shfl_up_sync(kFull, incl, o);
@@ -80,9 +86,14 @@ __device__ unsigned long long cta_scan(int count, Load load, Store store) {
         }
         __syncthreads();
         const unsigned long long carry = s_carry;
-        if (idx < count) store(idx, carry + s_warp[warp] + incl - v);
+        unsigned long long run = carry + s_warp[warp] + incl - tsum;
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            if (first + k < count) store(first + k, run);
+            run += v[k];
+        }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = carry + s_warp[warp] + incl;
+        if (threadIdx.x == blockDim.x - 1) s_carry = run;
         __syncthreads();
     }
     return s_carry;
@@ -928,53 +939,92 @@ k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, c
     }
 }
 
-// One CTA: counting sort of the tiles into 128 quarter-octave buckets of their list length,
-// heaviest bucket first.  Only the schedule depends on it, never a result.
-constexpr int kOrderThreads = 1024;
+// Counting sort of the tiles into 128 quarter-octave buckets of their list length, heaviest
+// bucket first (only the schedule depends on it, never a result; the order inside a bucket is
+// arbitrary).  Above kOrderSmall tiles, two launches over CTAs of kOrderThreads x kOrderItems
+// tiles: per-CTA bucket counts
+// added into the global counts, whose exclusive scan the last CTA writes as the buckets' cursors;
+// then each CTA reserves one range per bucket it holds and scatters its tiles into it.
+constexpr int kOrderThreads = 256;
+constexpr int kOrderItems = 8;
 constexpr int kOrderBuckets = 128;
 
-__global__ void __launch_bounds__(kOrderThreads) k_tile_order(int tiles, Scratch sc) {
+__device__ __forceinline__ int order_slot(const Scratch& sc, int t) {
+    const uint2 r = sc.ranges[t];
+    const uint32_t len = r.y - r.x;
+    // lengths 0..3 are their own buckets; from 4 on, 4 (l - 1) + the two bits after the leading
+    // one (l = floor(log2 len)): monotone in the length, at most 123
+    int b = (int)len;
+    if (len >= 4) {
+        const int l = 31 - __clz(len);
+        b = 4 * (l - 1) + (int)((len >> (l - 2)) & 3u);
+    }
+    return kOrderBuckets - 1 - b;
+}
+
+// up to kOrderSmall tiles: both steps in one CTA of 1024 threads (one launch)
+constexpr int kOrderSmall = 16384;
+__global__ void __launch_bounds__(1024) k_tile_order_small(int tiles, Scratch sc) {
     __shared__ uint32_t hist[kOrderBuckets], cursor[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
     __syncthreads();
-    auto slot_of = [&](int t) {
-        const uint2 r = sc.ranges[t];
-        const uint32_t len = r.y - r.x;
-        // lengths 0..3 are their own buckets; from 4 on, 4 (l - 1) + the two bits after the
-        // leading one (l = floor(log2 len)): monotone in the length, at most 123
-        int b = (int)len;
-        if (len >= 4) {
-            const int l = 31 - __clz(len);
-            b = 4 * (l - 1) + (int)((len >> (l - 2)) & 3u);
-        }
-        return kOrderBuckets - 1 - b;
-    };
-    for (int t = threadIdx.x; t < tiles; t += kOrderThreads) atomicAdd(&hist[slot_of(t)], 1u);
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&hist[order_slot(sc, t)], 1u);
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan, 4 buckets per lane
-        const int lane = threadIdx.x;
-        uint32_t h[4], s = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            h[k] = hist[4 * lane + k];
-            s += h[k];
-        }
-        uint32_t incl = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        uint32_t run = incl - s;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            cursor[4 * lane + k] = run;
-            run += h[k];
-        }
+    cta_scan(kOrderBuckets, [&](int k) { return (unsigned long long)hist[k]; },
+             [&](int k, unsigned long long v) { cursor[k] = (uint32_t)v; });
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint32_t pos = atomicAdd(&cursor[order_slot(sc, t)], 1u);
+        if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)t;
+        else atomicOr(sc.status, kStatusInternal);
+    }
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_hist(int tiles, Scratch sc) {
+    __shared__ uint32_t hist[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int t0 = blockIdx.x * kOrderThreads * kOrderItems;
+    for (int k = 0; k < kOrderItems; ++k) {
+        const int t = t0 + k * kOrderThreads + threadIdx.x;
+        if (t < tiles) atomicAdd(&hist[order_slot(sc, t)], 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += kOrderThreads)
-        sc.tile_order[atomicAdd(&cursor[slot_of(t)], 1u)] = (uint32_t)t;
+    uint32_t* counts = sc.tile_buckets;  // [0, 128): counts, [128, 256): cursors
+    if (threadIdx.x < kOrderBuckets && hist[threadIdx.x]) atomicAdd(&counts[threadIdx.x], hist[threadIdx.x]);
+    if (!last_cta(&sc.bin_ticket[2])) return;
+    cta_scan(kOrderBuckets, [&](int k) { return (unsigned long long)__ldcg(&counts[k]); },
+             [&](int k, unsigned long long v) { counts[kOrderBuckets + k] = (uint32_t)v; });
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets) counts[threadIdx.x] = 0u;  // zero for the next render
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_scatter(int tiles, Scratch sc) {
+    __shared__ uint32_t hist[kOrderBuckets], base[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int t0 = blockIdx.x * kOrderThreads * kOrderItems;
+    int slot[kOrderItems];
+    uint32_t rank[kOrderItems];
+#pragma unroll
+    for (int k = 0; k < kOrderItems; ++k) {
+        const int t = t0 + k * kOrderThreads + threadIdx.x;
+        slot[k] = t < tiles ? order_slot(sc, t) : -1;
+        rank[k] = slot[k] >= 0 ? atomicAdd(&hist[slot[k]], 1u) : 0u;
+    }
+    __syncthreads();
+    uint32_t* cursor = sc.tile_buckets + kOrderBuckets;
+    if (threadIdx.x < kOrderBuckets && hist[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], hist[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kOrderItems; ++k) {
+        const int t = t0 + k * kOrderThreads + threadIdx.x;
+        if (slot[k] >= 0) {
+            const uint32_t pos = base[slot[k]] + rank[k];
+            if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)t;
+            else atomicOr(sc.status, kStatusInternal);
+        }
+    }
 }
 
 }  // namespace
@@ -1050,8 +1100,15 @@ int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s)
 }
 
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
-    k_tile_order<<<1, kOrderThreads, 0, s>>>(tiles, sc);
-    return 1;
+    if (tiles <= 0) return 0;
+    if (tiles <= kOrderSmall) {
+        k_tile_order_small<<<1, 1024, 0, s>>>(tiles, sc);
+        return 1;
+    }
+    const int blocks = (tiles + kOrderThreads * kOrderItems - 1) / (kOrderThreads * kOrderItems);
+    k_tile_hist<<<blocks, kOrderThreads, 0, s>>>(tiles, sc);
+    k_tile_scatter<<<blocks, kOrderThreads, 0, s>>>(tiles, sc);
+    return 2;
 }
 
 int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm) {

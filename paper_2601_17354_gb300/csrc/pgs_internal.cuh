@@ -88,7 +88,8 @@ struct Scratch {
     unsigned long long* pair_count = nullptr;
     unsigned long long* pair_need = nullptr;  // pair capacity the render needs (>= pair_count)
     unsigned long long* coarse_count = nullptr;
-    uint32_t* bin_ticket = nullptr;  // [2] arrival counters of the binning's last-CTA steps (reset by it)
+    uint32_t* bin_ticket = nullptr;  // [3] arrival counters of the binning's last-CTA steps (reset by it)
+    uint32_t* tile_buckets = nullptr;  // [256] tile-order bucket counts (kept zero between renders), cursors
     uint32_t* sort_blocks = nullptr;  // sort CTAs with work in the current render
     uint32_t* digit_totals = nullptr; // [kTotalCopies][kMaxPasses][kRadix]
     float* loss_partials = nullptr;   // [2][kLossBlocks]
