@@ -624,6 +624,9 @@ def run_ours(args):
         step(k)
     torch.cuda.synchronize()
     L.check(rast.status()[0], "warm-up")
+    # the training state after warm-up: the end-to-end leg restarts from it, so both legs time the
+    # same steps (the cost of a step drifts as training changes the Gaussians)
+    snapshot = (tr.params.data.clone(), tr.m.data.clone(), tr.v.data.clone(), tr.t)
     # per-pixel evaluation counts of one view, for the compositing rooflines
     rast.render(params, cams[0])
     last = rast.read_buffer(L.PGS_BUF_LAST).astype(np.int64)
@@ -667,12 +670,18 @@ def run_ours(args):
     feed = R.ImageFeed(targets[0].shape, dev)
     loss_host = torch.zeros(2, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
+    tr.params.data.copy_(snapshot[0])
+    tr.m.data.copy_(snapshot[1])
+    tr.v.data.copy_(snapshot[2])
+    tr.t = snapshot[3]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    feed.put(0, host_targets[0])
+    w0 = args.warmup  # the same views as the timed region's steps
+    feed.put(0, host_targets[w0 % len(host_targets)])
     for k in range(args.steps):
         if k + 1 < args.steps:
-            feed.put(k + 1, host_targets[(k + 1) % len(host_targets)])
-        loss = tr.step(cams[k % len(cams)], feed.take(k, stream))
+            feed.put(k + 1, host_targets[(w0 + k + 1) % len(host_targets)])
+        loss = tr.step(cams[(w0 + k) % len(cams)], feed.take(k, stream))
         feed.release(k, stream)
         loss_host.copy_(loss, non_blocking=True)
     torch.cuda.synchronize()
