@@ -265,14 +265,15 @@ def test_single_gaussian_covering_every_tile(R):
 
 
 def test_many_super_tiles_take_two_grouping_passes(R):
-    """1280x720 with 8x8 tiles: 160 x 90 tiles in 20 x 23 = 460 super-tiles of 8 x 4 tiles, so the
-    coarse entries are grouped by a two-pass sort over 9-bit super-tile ids and the super-tiles'
-    ranges come from the sorted keys: keys, values and ranges bit-exact against the oracle, image
-    and `last` checked on every pixel."""
-    sc = S.surface_scene(4, 20000, 1, 1280, 720, 1000.0, n_cameras=8)
+    """1920x1080 with 8x8 tiles: 240 x 135 = 32,400 tiles in 30 x 34 = 1,020 super-tiles of 8 x 4
+    tiles, so the coarse entries are grouped by a two-pass sort over 10-bit super-tile ids, the
+    super-tiles' ranges come from the sorted keys, and the heaviest-first tile order takes its
+    multi-CTA form (more than 16,384 tiles): keys, values and ranges bit-exact against the oracle,
+    image and `last` checked on every pixel."""
+    sc = S.surface_scene(4, 20000, 1, 1920, 1080, 1500.0, n_cameras=8)
     g, cam = sc.gt, sc.cameras[2]
     TX, TY = -(-cam.width // 8), -(-cam.height // 8)
-    assert -(-TX // 8) * -(-TY // 4) > 256
+    assert -(-TX // 8) * -(-TY // 4) > 256 and TX * TY > 16384
     rast = R.Rasterizer(tile=8)
     rast, buf, img, T, last, code, pairs = render_gpu(R, g, cam, rast)
     assert code == 0
