@@ -321,3 +321,24 @@ def test_tile_edge_8_batch_matches_single_view_and_tuner_picks_an_edge(mods, tmp
     tuned.step()
     torch.cuda.synchronize()
     assert tuned.status()[0] == 0
+
+
+def test_many_super_tiles_batch_renders_like_single_views(mods):
+    """Four 1920x1080 renders with 8x8 tiles in one batch: 4 x 1,020 super-tiles (two grouping
+    passes over 12-bit ids, ranges from the sorted keys) and 129,600 tiles (the multi-CTA tile
+    order); every image equals the single-view render bit for bit."""
+    R, B, _, _ = mods
+    scenes, views = [], []
+    for s in range(2):
+        sc = S.surface_scene(40 + s, 20000, 1, 1920, 1080, 1500.0, n_cameras=4)
+        scenes.append(sc)
+        for v in (0, 1):
+            views.append((s, sc.cameras[v], S.random_image(7 * s + v, 1920, 1080, 0.0, 1.0)))
+    bt, bufs = make_trainer(mods, scenes, views, tile=8)
+    bt.render()
+    torch.cuda.synchronize()
+    assert bt.status()[0] == 0
+    rast = R.Rasterizer(tile=8)
+    for k, (s, cam, _) in enumerate(views):
+        img = rast.render(R.GaussianBuffer.from_arrays(scenes[s].init), cam)
+        assert torch.equal(img, bt.images[k]), k
