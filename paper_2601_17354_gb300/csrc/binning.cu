@@ -430,7 +430,10 @@ k_digit_totals(int64_t capacity, int first_shift, int passes, uint32_t last_mask
 constexpr uint32_t kLbCount = 1u << 30, kLbPrefix = 2u << 30, kLbValue = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 20;  // with the back-off below, about half a second
 constexpr int kLbWindow = 8;
-constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kDigitWarps = kRadix / 32;  // the warps whose threads own one digit each
+
+// named barrier of the digit warps (the first kRadix threads); barrier 0 is __syncthreads
+__device__ __forceinline__ void digit_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kRadix) : "memory"); }
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -441,23 +444,27 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename KeyT, int kItems>
-constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kSortThreads * kItems; }
+template <typename KeyT, int kItems, int kThreads = kSortThreads>
+constexpr size_t scatter_smem() { return (sizeof(KeyT) + sizeof(uint32_t)) * kThreads * kItems; }
 
-template <typename KeyT, int kItems>
-__global__ void __launch_bounds__(kSortThreads)
+// kThreads = kRadix or a multiple of it: with more threads than digits each warp ranks fewer keys
+// and only the first kRadix threads take the per-digit steps (their own named barrier)
+template <typename KeyT, int kItems, int kThreads = kSortThreads>
+__global__ void __launch_bounds__(kThreads)
 k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ kin,
            const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout, Scratch sc) {
-    constexpr int kTile = kSortThreads * kItems;        // keys per CTA
-    constexpr int kWarpItems = kTile / kSortWarps;      // contiguous keys per warp
+    static_assert(kThreads % kRadix == 0, "whole digit warps");
+    constexpr int kWarps = kThreads / 32;
+    constexpr int kTile = kThreads * kItems;            // keys per CTA
+    constexpr int kWarpItems = kTile / kWarps;          // contiguous keys per warp
     constexpr int kRounds = kWarpItems / 32;            // == kItems
     extern __shared__ __align__(16) unsigned char s_dyn[];
     KeyT* s_keys = reinterpret_cast<KeyT*>(s_dyn);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_dyn + sizeof(KeyT) * kTile);
-    __shared__ uint32_t s_wh[kSortWarps][kRadix];  // per-warp digit counts, then warp prefixes
+    __shared__ uint32_t s_wh[kWarps][kRadix];      // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_gofs[kRadix];            // global offset of this tile's run of digit d
     __shared__ uint32_t s_bstart[kRadix];          // start of digit d inside the CTA's reordering
-    __shared__ uint32_t s_part[kSortWarps];
+    __shared__ uint32_t s_part[kDigitWarps];
     __shared__ uint32_t s_hist[kRadix];            // the tile's count of digit d
     __shared__ uint32_t s_tile;
     uint32_t* head = sc.sort_hist;  // [0] abort word, [1 + pass] ticket of the pass, then the look-back
@@ -465,8 +472,8 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
     const uint32_t nblk = *sc.sort_blocks;
     if (threadIdx.x == 0) s_tile = atomicAdd(&head[1 + pass], 1u);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kSortWarps * kRadix; k += kSortThreads) (&s_wh[0][0])[k] = 0;
-    s_hist[threadIdx.x] = 0;
+    for (int k = threadIdx.x; k < kWarps * kRadix; k += kThreads) (&s_wh[0][0])[k] = 0;
+    if (threadIdx.x < kRadix) s_hist[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= nblk) return;
@@ -489,8 +496,8 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
     for (int r = 0; r < kRounds; ++r)
         if (wbase + (uint64_t)r * 32 + lane < P) atomicAdd(&s_hist[(uint32_t)(key[r] >> shift) & dmask], 1u);
     __syncthreads();
-    uint32_t* const mine = lb + (size_t)tile * kRadix + threadIdx.x;
-    st_relaxed(mine, (tile == 0 ? kLbPrefix : kLbCount) | s_hist[threadIdx.x]);
+    uint32_t* const mine = lb + (size_t)tile * kRadix + (threadIdx.x & (kRadix - 1));
+    if (threadIdx.x < kRadix) st_relaxed(mine, (tile == 0 ? kLbPrefix : kLbCount) | s_hist[threadIdx.x]);
     const int nbits = __popc(dmask);  // dmask = 2^bits - 1: higher digit bits are zero
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
@@ -515,11 +522,11 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
         dr[r] = valid ? (d | ((before + __popc(peers & lt)) << 8)) : 0xffffffffu;
     }
     __syncthreads();
-    {   // thread = digit: warp prefixes, the tile's count of the digit, its look-back
+    if (threadIdx.x < kRadix) {  // thread = digit: warp prefixes, the tile's count of the digit, its look-back
         const int d = threadIdx.x;
         uint32_t acc = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
+        for (int w = 0; w < kWarps; ++w) {
             const uint32_t cnt = s_wh[w][d];
             s_wh[w][d] = acc;
             acc += cnt;
@@ -578,17 +585,17 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
             }
         }
         if (lane == 31) s_part[warp] = incl_all;
-        __syncthreads();
+        digit_sync();
         uint32_t wpre = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
+        for (int w = 0; w < kDigitWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
         s_gofs[d] = wpre + incl_all - all + before;
-        __syncthreads();
+        digit_sync();
         if (lane == 31) s_part[warp] = incl;  // the tile's own digit counts, for its reordering
-        __syncthreads();
+        digit_sync();
         wpre = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
+        for (int w = 0; w < kDigitWarps; ++w) wpre += w < warp ? s_part[w] : 0u;
         s_bstart[d] = wpre + incl - acc;
     }
     __syncthreads();
@@ -608,7 +615,7 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
     }
     __syncthreads();
     const uint32_t count = (uint32_t)min((uint64_t)kTile, P - cbase);
-    for (uint32_t p = threadIdx.x; p < count; p += kSortThreads) {
+    for (uint32_t p = threadIdx.x; p < count; p += kThreads) {
         const KeyT k = s_keys[p];
         const uint32_t d = (uint32_t)(k >> shift) & dmask;
         const uint64_t dst = (uint64_t)s_gofs[d] + (p - s_bstart[d]);
@@ -1031,11 +1038,11 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_scatter(int tiles, Scrat
 
 // a pass reorders a whole CTA tile of keys in dynamic shared memory (32 KB with 4096 32-bit keys,
 // 48 KB with 4096 64-bit keys)
-template <typename KeyT, int kItems>
+template <typename KeyT, int kItems, int kThreads = kSortThreads>
 void enable_scatter_smem() {
     static bool done = [] {
-        cudaFuncSetAttribute(k_onesweep<KeyT, kItems>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)scatter_smem<KeyT, kItems>());
+        cudaFuncSetAttribute(k_onesweep<KeyT, kItems, kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem<KeyT, kItems, kThreads>());
         return true;
     }();
     (void)done;
@@ -1043,12 +1050,12 @@ void enable_scatter_smem() {
 
 // LSD passes over bits [first_shift, first_shift + bits) of the keys in keys[0] / keys[1] (viewed
 // as KeyT), 8 bits a pass (the last pass takes what is left: bits above the range never take part),
-// CTA tiles of kSortThreads x kItems keys: the digit totals of every pass in one read of the keys,
+// CTA tiles of kThreads x kItems keys: the digit totals of every pass in one read of the keys,
 // then one launch per pass.  Returns the launches and leaves the sorted buffer's index in *out_buf.
-template <typename KeyT, int kItems>
+template <typename KeyT, int kItems, int kThreads = kSortThreads>
 int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf,
                 bool totals_ready = false) {
-    constexpr int kTile = kSortThreads * kItems;
+    constexpr int kTile = kThreads * kItems;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
     const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
     const int sb_max = (int)((capacity + kTile - 1) / kTile);
@@ -1058,7 +1065,7 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     int buf = 0;
     *out_buf = 0;
     if (sb_max <= 0 || passes <= 0) return 0;
-    enable_scatter_smem<KeyT, kItems>();
+    enable_scatter_smem<KeyT, kItems, kThreads>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
     // abort word, tickets and the look-back words of every pass start cleared
     cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * (kLookbackHead + (size_t)passes * kRadix * sb_max), s);
@@ -1069,7 +1076,7 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
         const uint32_t dmask = p == passes - 1 ? last_mask : (uint32_t)(kRadix - 1);
-        k_onesweep<KeyT, kItems><<<sb_max, kSortThreads, scatter_smem<KeyT, kItems>(), s>>>(
+        k_onesweep<KeyT, kItems, kThreads><<<sb_max, kThreads, scatter_smem<KeyT, kItems, kThreads>(), s>>>(
             capacity, p, shift, dmask, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }
@@ -1122,7 +1129,7 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     d.pair_count = sc.dcount;
     d.sort_blocks = sc.dblocks;
     int buf = 0;
-    const int launched = sort_passes<uint32_t, kDepthItems>(n, 0, 32, d, s, &buf);
+    const int launched = sort_passes<uint32_t, kDepthItems, kDepthThreads>(n, 0, 32, d, s, &buf);
     *perm = sc.dvals[buf];
     return launched;
 }

@@ -15,8 +15,9 @@ constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kern
 constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
 constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels of the pairs
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort CTA
-constexpr int kDepthItems = 8;       // keys per thread in the depth sort (more, shorter CTAs)
-constexpr int kDepthTile = kSortThreads * kDepthItems;
+constexpr int kDepthThreads = 512;   // threads per CTA of the depth sort's passes (more warps per key)
+constexpr int kDepthItems = 4;       // keys per thread in the depth sort (more, shorter CTAs)
+constexpr int kDepthTile = kDepthThreads * kDepthItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
