@@ -302,11 +302,14 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     cudaStream_t s = ctx->stream;
     ctx->has_render = false;
     const size_t e0 = mark(ctx);
-    ctx->launches += launch_project_fwd(*params, *cam, TX, TY, T, ctx->sc, s);
+    // the projection zeroes the binning's counters, look-back words and ranges on its way
+    ctx->launches += launch_project_fwd(*params, *cam, TX, TY, T, ctx->sc,
+                                        render_zero_plan(ctx->sc, params->n, tiles, supers, ctx->cap_pairs), s);
     const size_t e1 = mark(ctx);
     const uint32_t* perm = nullptr;
-    if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm);
-    ctx->launches += launch_bin_count(params->n, supers, ctx->cap_pairs, perm, ctx->sc, s);
+    if (params->n > 0) ctx->launches += launch_depth_sort(params->n, ctx->sc, s, &perm, true);
+    ctx->launches += launch_bin_count(params->n, supers, ctx->cap_pairs, perm, ctx->sc, s, true);
+    bool cleared = true;  // false once the pair arena has moved
     if (ctx->grow_pairs) {
         unsigned long long need = 0;
         cudaError_t e = cudaMemcpyAsync(&need, ctx->sc.pair_need, sizeof(need), cudaMemcpyDeviceToHost, s);
@@ -326,10 +329,12 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_err(e);
             ctx->launches += launch_bin_count(params->n, supers, ctx->cap_pairs, perm, ctx->sc, s);
+            cleared = false;
         }
     }
     const size_t e2 = mark(ctx);
-    ctx->launches += launch_bin_lists(params->n, TX, TY, T, tiles, supers, ctx->cap_pairs, perm, ctx->sc, s, &ctx->buf);
+    ctx->launches += launch_bin_lists(params->n, TX, TY, T, tiles, supers, ctx->cap_pairs, perm, ctx->sc, s, &ctx->buf,
+                                      nullptr, 0, cleared);
     ctx->launches += launch_tile_order((int)tiles, ctx->sc, s);
     const size_t e3 = mark(ctx);
     ctx->recorded = false;

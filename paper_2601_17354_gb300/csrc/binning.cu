@@ -1052,9 +1052,17 @@ void enable_scatter_smem() {
 // as KeyT), 8 bits a pass (the last pass takes what is left: bits above the range never take part),
 // CTA tiles of kThreads x kItems keys: the digit totals of every pass in one read of the keys,
 // then one launch per pass.  Returns the launches and leaves the sorted buffer's index in *out_buf.
+// bits of a super-tile id (the coarse sort's key width)
+static int super_bits(int64_t supers) {
+    int bits = 0;
+    while ((1ll << bits) < (long long)supers) ++bits;
+    return bits;
+}
+
+// cleared: the look-back words (and, unless totals_ready, the digit totals) are already zero.
 template <typename KeyT, int kItems, int kThreads = kSortThreads>
 int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, cudaStream_t s, int* out_buf,
-                bool totals_ready = false) {
+                bool totals_ready = false, bool cleared = false) {
     constexpr int kTile = kThreads * kItems;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
     const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
@@ -1068,9 +1076,9 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     enable_scatter_smem<KeyT, kItems, kThreads>();
     KeyT* k[2] = {reinterpret_cast<KeyT*>(sc.keys[0]), reinterpret_cast<KeyT*>(sc.keys[1])};
     // abort word, tickets and the look-back words of every pass start cleared
-    cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * (kLookbackHead + (size_t)passes * kRadix * sb_max), s);
+    if (!cleared) cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * lookback_words(passes, sb_max), s);
     if (!totals_ready) {  // else the kernel that wrote the keys counted their digits
-        cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+        if (!cleared) cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
         k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
     }
     for (int p = 0; p < passes; ++p) {
@@ -1118,7 +1126,7 @@ int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
     return 2;
 }
 
-int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm) {
+int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm, bool cleared) {
     Scratch d = sc;
     d.keys[0] = sc.dkeys[0];
     d.keys[1] = sc.dkeys[1];
@@ -1129,22 +1137,22 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
     d.pair_count = sc.dcount;
     d.sort_blocks = sc.dblocks;
     int buf = 0;
-    const int launched = sort_passes<uint32_t, kDepthItems, kDepthThreads>(n, 0, 32, d, s, &buf);
+    const int launched = sort_passes<uint32_t, kDepthItems, kDepthThreads>(n, 0, 32, d, s, &buf, false, cleared);
     *perm = sc.dvals[buf];
     return launched;
 }
 
 int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool cleared) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
-    cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
+    if (!cleared) cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
     k_coarse_counts<<<nb > 0 ? nb : 1, kProjBlock, 0, s>>>(n, capacity, supers, perm, sc);
     return 1;
 }
 
 int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t supers, int64_t capacity,
                      const uint32_t* perm, const Scratch& sc, cudaStream_t s, int* out_buf, const RenderDesc* renders,
-                     int R) {
+                     int R, bool cleared) {
     const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
     int launched = 0;
     *out_buf = 1;
@@ -1152,13 +1160,12 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     // coarse keys are 32-bit: the sort uses the lower halves)
     uint32_t* gidx = reinterpret_cast<uint32_t*>(sc.keys[0]) + capacity;
     uint32_t* gmask = reinterpret_cast<uint32_t*>(sc.keys[1]) + capacity;
-    cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
+    if (!cleared) cudaMemsetAsync(sc.ranges, 0, sizeof(uint2) * (size_t)tiles, s);
     if (capacity <= 0 || supers <= 0) return 0;
-    int bits = 0;
-    while ((1ll << bits) < (long long)supers) ++bits;
+    const int bits = super_bits(supers);
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
     const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
-    cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
+    if (!cleared) cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
     if (nb > 0) {
         k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, T, capacity, perm, sc, gidx, gmask,
                                                 passes, last_mask, renders, R);
@@ -1169,10 +1176,10 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     Scratch cs = sc;
     cs.pair_count = sc.coarse_count;
     int cb = 0;
-    launched += sort_passes<uint32_t, kSortItems>(capacity, 0, bits, cs, s, &cb, true);
+    launched += sort_passes<uint32_t, kCoarseItems, kCoarseThreads>(capacity, 0, bits, cs, s, &cb, true, cleared);
     int crange_from = passes == 0 ? 2 : 1;
     if (passes > 1) {  // the super-tiles' ranges from the sorted keys
-        cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
+        if (!cleared) cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
         cs.ranges = sc.crange;
         k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
         ++launched;
@@ -1188,6 +1195,34 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
                                                     sc, renders, R);
     *out_buf = cb ^ 1;
     return launched + 4;
+}
+
+ZeroPlan render_zero_plan(const Scratch& sc, int64_t n, int64_t tiles, int64_t supers, int64_t capacity) {
+    ZeroPlan z{};
+    auto add = [&](void* p, size_t words) {
+        if (p && words > 0 && z.count < kZeroRegions) {
+            z.p[z.count] = static_cast<uint32_t*>(p);
+            z.words[z.count] = (uint32_t)words;
+            ++z.count;
+        }
+    };
+    // depth sort: 4 passes over ceil(n / kDepthTile) tiles, its digit totals
+    add(sc.dhist, lookback_words(32 / kRadixBits, (n + kDepthTile - 1) / kDepthTile));
+    add(sc.dtotals, kTotalWords);
+    add(sc.pair_count, 2);
+    add(sc.ranges, 2 * (size_t)tiles);
+    // coarse stage: its digit totals, its sort's look-back words, the super-tiles' ranges
+    add(sc.digit_totals, kTotalWords);
+    if (capacity > 0 && supers > 0) {
+        const int passes = (super_bits(supers) + kRadixBits - 1) / kRadixBits;
+        add(sc.sort_hist, lookback_words(passes, (capacity + kSortTile - 1) / kSortTile));
+        if (passes > 1) add(sc.crange, 2 * (size_t)supers);
+    }
+    return z;
+}
+
+void clear_zero_plan(const ZeroPlan& z, cudaStream_t s) {
+    for (int r = 0; r < z.count; ++r) cudaMemsetAsync(z.p[r], 0, sizeof(uint32_t) * z.words[r], s);
 }
 
 int launch_radix_sort_only(int64_t capacity, int key_bits, const Scratch& sc, cudaStream_t s,

@@ -15,6 +15,10 @@ constexpr int kProjBlock = 256;      // threads per CTA of the per-Gaussian kern
 constexpr int kSortThreads = 256;    // threads per CTA of the radix-sort kernels
 constexpr int kSortItems = 16;       // keys per thread in the radix-sort kernels of the pairs
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort CTA
+// the coarse entries' sort: 512 threads x 8 keys, the pair sort's tile size
+constexpr int kCoarseThreads = 512;
+constexpr int kCoarseItems = 8;
+static_assert(kCoarseThreads * kCoarseItems == kSortTile, "coarse sort CTAs cover kSortTile keys");
 constexpr int kDepthThreads = 512;   // threads per CTA of the depth sort's passes (more warps per key)
 constexpr int kDepthItems = 4;       // keys per thread in the depth sort (more, shorter CTAs)
 constexpr int kDepthTile = kDepthThreads * kDepthItems;
@@ -169,17 +173,33 @@ CompositeVariant default_variant();
 // launchers (all asynchronous on `s`); each returns the number of kernels it launched
 // ---------------------------------------------------------------------------------------------
 
+// Word ranges of a render's scratch that must be zero before its binning (look-back words, digit
+// totals, counters, tile and super-tile ranges).  The projection clears them on its way, so the
+// binning launches no separate clears.
+constexpr int kZeroRegions = 8;
+struct ZeroPlan {
+    uint32_t* p[kZeroRegions];
+    uint32_t words[kZeroRegions];
+    int count;
+};
+// The ranges one render's depth sort, pair count and tile lists use (n Gaussians, `tiles` tiles
+// in `supers` super-tiles, pair capacity `capacity`).
+ZeroPlan render_zero_plan(const Scratch& sc, int64_t n, int64_t tiles, int64_t supers, int64_t capacity);
+// The same clears as separate memsets (after the scratch moved, e.g. a grown pair arena).
+void clear_zero_plan(const ZeroPlan& z, cudaStream_t s);
+
 // K1: project + cull + SH colour; writes the projected record, depth bits, tile rectangle,
-// tiles touched and the per-CTA sum of tiles touched.
+// tiles touched and the per-CTA sum of tiles touched, and zeroes the ranges of `zero`.
 int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY, int T,
-                        const Scratch& sc, cudaStream_t s);
+                        const Scratch& sc, const ZeroPlan& zero, cudaStream_t s);
 // K9: chain screen-space gradients (grad2d) to the parameters, added into grads.
 int launch_project_bwd(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
                         pgs_gaussians& grads, cudaStream_t s);
 
 // Depth sort of the Gaussians (LSD radix over the 32 depth bits of dkeys[0] / dvals[0]); returns
 // the kernels launched, *perm receives the buffer holding the depth-ordered canonical indices.
-int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm);
+// cleared: its look-back words and digit totals are already zero (render_zero_plan).
+int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32_t** perm, bool cleared = false);
 // K9 + K10 fused: chain the screen-space gradients to the parameters and apply one Adam step to
 // every Gaussian (culled ones with a zero gradient) without storing the gradient.
 int launch_project_bwd_adam(const pgs_gaussians& g, const pgs_camera& cam, const Scratch& sc,
@@ -224,15 +244,17 @@ int launch_mlp_pack(const float* master, void* W1, void* W2, void* W3, cudaStrea
 // depth order with their scan; writes pair_count, pair_need and coarse_count and raises the
 // capacity status when pair_need exceeds `capacity`.  `supers` = super-tiles of the render (batch:
 // of all renders).
+// cleared: pair_count is already zero.
 int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t* perm, const Scratch& sc,
-                     cudaStream_t s);
+                     cudaStream_t s, bool cleared = false);
 // K3-K5 after launch_bin_count: coarse entries in depth order, their stable sort by super-tile, the
 // reached-tile masks and pair lists of every tile in depth order (values = canonical indices in
 // vals[*out_buf], laid out super-tile by super-tile), and the tile ranges.  TX, TY: the tile grid
 // of a single render (renders == nullptr); a batch reads each render's grid from `renders`.
+// cleared: the ranges, the digit totals and the sort's look-back words are already zero.
 int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t supers, int64_t capacity,
                      const uint32_t* perm, const Scratch& sc, cudaStream_t s, int* out_buf,
-                     const RenderDesc* renders = nullptr, int R = 0);
+                     const RenderDesc* renders = nullptr, int R = 0, bool cleared = false);
 
 // K4 alone over keys[0]/vals[0] with keys[1]/vals[1] as the other ping-pong buffer, sorting by the
 // low key_bits bits only (higher bits never take part; the pair count is read from sc.pair_count,

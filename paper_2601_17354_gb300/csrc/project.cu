@@ -400,7 +400,7 @@ __device__ __forceinline__ uint32_t project_item(const pgs_gaussians& g, int64_t
 
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
-k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc) {
+k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc, ZeroPlan zero) {
     const int64_t n = g.n;
     const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
     __shared__ uint32_t s_sm[4 * kProjBlock];
@@ -408,6 +408,14 @@ k_project_fwd(pgs_gaussians g, pgs_camera cam, int TX, int TY, int T, Scratch sc
     if (i == 0) {
         *sc.dcount = (unsigned long long)n;
         *sc.dblocks = (uint32_t)((n + kDepthTile - 1) / kDepthTile);
+    }
+    // the binning's scratch, grid-stride (a few MB against the projection's reads)
+    const uint64_t stride = (uint64_t)gridDim.x * kProjBlock;
+#pragma unroll
+    for (int r = 0; r < kZeroRegions; ++r) {
+        if (r >= zero.count) break;
+        uint32_t* const dst = zero.p[r];
+        for (uint64_t w = (uint64_t)i; w < zero.words[r]; w += stride) dst[w] = 0u;
     }
 }
 
@@ -863,14 +871,17 @@ k_bwd_batch(const RenderDesc* __restrict__ renders, const SceneDesc* __restrict_
 }  // namespace
 
 int launch_project_fwd(const pgs_gaussians& g, const pgs_camera& cam, int TX, int TY, int T,
-                       const Scratch& sc, cudaStream_t s) {
+                       const Scratch& sc, const ZeroPlan& zero, cudaStream_t s) {
     const int64_t blocks = (g.n + kProjBlock - 1) / kProjBlock;
-    if (blocks == 0) return 0;
+    if (blocks == 0) {
+        clear_zero_plan(zero, s);
+        return 0;
+    }
     switch (g.sh_degree) {
-        case 0: k_project_fwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
-        case 1: k_project_fwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
-        case 2: k_project_fwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
-        default: k_project_fwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc); break;
+        case 0: k_project_fwd<0><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc, zero); break;
+        case 1: k_project_fwd<1><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc, zero); break;
+        case 2: k_project_fwd<2><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc, zero); break;
+        default: k_project_fwd<3><<<(unsigned)blocks, kProjBlock, 0, s>>>(g, cam, TX, TY, T, sc, zero); break;
     }
     return 1;
 }
