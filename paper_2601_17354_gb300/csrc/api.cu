@@ -29,6 +29,7 @@ struct pgs_ctx {
     // replay cache (pgs_set_replay_cache): K entries per pixel, off when 0
     int replay_k = 0;
     bool recorded = false;     // the last render recorded the cache
+    bool grad_clean = false;   // grad2d is zero (cleared by the last forward), no backward since
     void* arena_c = nullptr;
     int64_t cap_c = 0;         // pixels x K the cache arena holds
     float4* c_rec = nullptr;
@@ -301,6 +302,7 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     if (rc != PGS_OK) return rc;
     cudaStream_t s = ctx->stream;
     ctx->has_render = false;
+    ctx->grad_clean = false;
     const size_t e0 = mark(ctx);
     // the projection zeroes the binning's counters, look-back words and ranges on its way
     ctx->launches += launch_project_fwd(*params, *cam, TX, TY, T, ctx->sc,
@@ -345,7 +347,11 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
                                                  ctx->c_rec, ctx->c_count, ctx->replay_k, false, s);
         ctx->recorded = true;
     } else {
-        ctx->launches += launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant);
+        // the forward also clears the screen-space gradients its backward accumulates
+        const int k = launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant,
+                                           9 * params->n);
+        ctx->launches += k;
+        ctx->grad_clean = k > 0;
     }
     const size_t e4 = mark(ctx);
     span(ctx, PGS_STAGE_PROJECT, e0, e1);
@@ -429,7 +435,8 @@ int pgs_backward(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* grads) {
     if (!ctx->has_render) return PGS_ERR_NO_RENDER;
     if (grads->n != ctx->n || grads->sh_degree != ctx->params.sh_degree) return PGS_ERR_INVALID_ARG;
     cudaStream_t s = ctx->stream;
-    if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    if (ctx->n > 0 && !ctx->grad_clean) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    ctx->grad_clean = false;
     const size_t e0 = mark(ctx);
     ctx->launches += composite_backward(ctx, dL_dimage);
     const size_t e1 = mark(ctx);
@@ -467,7 +474,8 @@ int pgs_backward_step(pgs_ctx* ctx, const float* dL_dimage, pgs_gaussians* param
         if (q->n != ctx->n || q->sh_degree != ctx->params.sh_degree) return PGS_ERR_INVALID_ARG;
     if (params->means != ctx->params.means) return PGS_ERR_INVALID_ARG;
     cudaStream_t s = ctx->stream;
-    if (ctx->n > 0) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    if (ctx->n > 0 && !ctx->grad_clean) cudaMemsetAsync(ctx->sc.grad2d, 0, sizeof(float) * 9 * (size_t)ctx->n, s);
+    ctx->grad_clean = false;
     const size_t e0 = mark(ctx);
     ctx->launches += composite_backward(ctx, dL_dimage);
     const size_t e1 = mark(ctx);
@@ -604,7 +612,8 @@ int pgs_time_variants_split(pgs_ctx* ctx, float* image, const float* dL_dimage, 
             ms_bwd[idx] = bb;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    // the timing overwrote the screen-space gradients: the next backward recomputes them
+    // the timing overwrote the screen-space gradients: the next backward clears and recomputes them
+    ctx->grad_clean = false;
     return err == cudaSuccess ? PGS_OK : cuda_err(err);
 }
 
@@ -641,7 +650,8 @@ int pgs_time_variants(pgs_ctx* ctx, float* image, const float* dL_dimage, int32_
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // the timing overwrote the screen-space gradients: the next backward recomputes them
+    // the timing overwrote the screen-space gradients: the next backward clears and recomputes them
+    ctx->grad_clean = false;
     return err == cudaSuccess ? PGS_OK : cuda_err(err);
 }
 

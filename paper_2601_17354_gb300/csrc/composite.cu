@@ -1267,7 +1267,7 @@ __device__ __forceinline__ TileJob batch_job(const RenderDesc& rd, int64_t gt, c
 template <int kT, int kPix, int kDepth>
 __global__ void __launch_bounds__(kT * kT / kPix)
 k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
-                Scratch sc, float* __restrict__ image) {
+                Scratch sc, float* __restrict__ image, int64_t zero_grad) {
     __shared__ FwdSmem<kDepth> S;
     TileJob J;
     J.W = W;
@@ -1282,6 +1282,14 @@ k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     J.last = sc.last;
     J.ncomp = sc.ncomp;
     fwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
+    if (zero_grad > 0) {  // grad2d is 256-byte aligned: 16-byte stores, the tail by block 0
+        float4* g4 = reinterpret_cast<float4*>(sc.grad2d);
+        const int64_t n4 = zero_grad >> 2;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n4; w += stride)
+            g4[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (blockIdx.x == 0 && threadIdx.x < (zero_grad & 3)) sc.grad2d[(n4 << 2) + threadIdx.x] = 0.f;
+    }
 }
 
 template <int kT, int kPix, int kDepth>
@@ -1467,12 +1475,12 @@ bool valid_variant(CompositeVariant v, int T) {
     X(32, 2, 64) X(32, 2, 128) X(32, 2, 256) X(32, 4, 64) X(32, 4, 128) X(32, 4, 256)
 
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
-                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v) {
+                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v, int64_t zero_grad) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
 #define X(TT, P, D)                                                                               \
     if (T == TT && v.pix == P && v.depth == D) {                                                  \
         k_composite_fwd<TT, P, D><<<TX * TY, TT * TT / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
-                                                                  sc.vals[buf], sc, image);      \
+                                                                  sc.vals[buf], sc, image, zero_grad); \
         return 1;                                                                                 \
     }
     PGS_VARIANTS(X)

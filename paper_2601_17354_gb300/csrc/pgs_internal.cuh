@@ -271,8 +271,11 @@ int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s)
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
+// zero_grad: also zero the first zero_grad floats of sc.grad2d (the coming backward's screen-space
+// gradients), spread over the CTAs, in place of a separate clear.
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
-                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v);
+                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v,
+                         int64_t zero_grad = 0);
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v);
 // Replay-cache compositing (one pixel per thread): the forward records, per pixel, the first K

@@ -211,6 +211,9 @@ def test_fused_backward_step_matches_oracle_and_separate_calls(R):
 
 
 def test_backward_accumulates(R):
+    """The first backward after a render reads the screen-space gradients its forward cleared;
+    every later one (or one after a variant timing, which runs backwards of its own) clears them
+    itself: repeated calls add the same gradient each time."""
     g, cam = SCENES["tiny_2k_128"]()
     rast, buf, *_ = render_gpu(R, g, cam)
     dL = torch.from_numpy(S.random_image(4, cam.width, cam.height)).cuda()
@@ -219,9 +222,13 @@ def test_backward_accumulates(R):
     g2 = buf.zeros_like()
     rast.backward(dL, g2)
     rast.backward(dL, g2)
+    rast.time_variants(dL, reps=1)
+    g3 = buf.zeros_like()
+    rast.backward(dL, g3)
     torch.cuda.synchronize()
     # float atomics add in a scheduling-dependent order: equal up to rounding
     assert rel_l2(g2.data.cpu().numpy(), 2 * g1.data.cpu().numpy()) < 1e-5
+    assert rel_l2(g3.data.cpu().numpy(), g1.data.cpu().numpy()) < 1e-5
     assert torch.count_nonzero(g1.data) > 0
 
 
