@@ -114,6 +114,15 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
    loss_out is a device pointer to 2 floats. */
 int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,
                 float* loss_out);
+/* pgs_render followed by pgs_loss_l1 on its image (n = 3 H W), in one pass: the compositing
+   forward also reads target [3][H][W] (device), writes dL_dimage [3][H][W] (device) and adds its
+   CTAs' sums into the loss, so no separate loss kernel reads the image back.  image_out, T_final,
+   last and dL_dimage are bit for bit those of the two calls; loss_out (device, 2 floats) holds the
+   same sums added in another order (per CTA, then in double), so they agree to rounding.  With the
+   replay cache on, the recording forward is followed by the loss kernel instead.  Errors as
+   pgs_render; PGS_ERR_INVALID_ARG for a null target, dL_dimage or loss_out. */
+int pgs_render_l1(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, const float* target,
+                  float* image_out, float* dL_dimage, float* loss_out);
 /* L1 + D-SSIM loss (the paper reports SSIM, Sec. IV, and names no training loss): per colour
    plane of [3][height][width] images, SSIM with the 11 x 11 Gaussian window (sigma 1.5, taps
    normalised to 1), zero padding, C1 = 0.01^2, C2 = 0.03^2; loss = (1 - lambda) mean|image -

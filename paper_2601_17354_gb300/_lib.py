@@ -43,7 +43,7 @@ PGS_BUF_NCOMP = 7
 PGS_STAGES = ["project", "bin", "sort", "composite_fwd", "loss", "composite_bwd", "project_bwd",
               "adam", "project_bwd_adam"]
 
-EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_loss_l1",
+EXPORTED = ["pgs_create", "pgs_destroy", "pgs_reserve", "pgs_render", "pgs_render_l1", "pgs_loss_l1",
             "pgs_backward", "pgs_step", "pgs_status", "pgs_read_buffer", "pgs_strerror",
             "pgs_profile", "pgs_stage_times", "pgs_launch_count", "pgs_backward_step",
             "pgs_batch_create", "pgs_batch_destroy", "pgs_batch_step", "pgs_batch_capture",
@@ -120,6 +120,8 @@ def lib():
             L.pgs_render.restype = I
             L.pgs_loss_l1.argtypes = [P, P, P, I64, P, P]
             L.pgs_loss_l1.restype = I
+            L.pgs_render_l1.argtypes = [P, C.POINTER(PgsGaussians), C.POINTER(PgsCamera), P, P, P, P]
+            L.pgs_render_l1.restype = I
             L.pgs_backward.argtypes = [P, P, C.POINTER(PgsGaussians)]
             L.pgs_backward.restype = I
             L.pgs_step.argtypes = [P] + [C.POINTER(PgsGaussians)] * 4 + [I64]

@@ -108,6 +108,7 @@ size_t carve_g(Scratch& sc, char* base, int64_t n, int64_t pixels, int64_t tiles
     sc.digit_totals = c.take<uint32_t>(kTotalWords);
     sc.loss_partials = c.take<float>(2 * kLossBlocks);
     sc.loss_ticket = c.take<uint32_t>(1);
+    sc.l1_acc = c.take<double>(3);
     return c.off;
 }
 
@@ -293,8 +294,11 @@ int pgs_reserve(pgs_ctx* ctx, int64_t n, int32_t width, int32_t height, int64_t 
     return rc;
 }
 
-int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out) {
+// pgs_render, and with target != nullptr pgs_render_l1 (the L1 loss in the compositing forward)
+static int render_impl(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out,
+                       const float* target, float* dL_dimage, float* loss_out) {
     if (!ctx || !valid_gaussians(params) || !valid_camera(cam) || !image_out) return PGS_ERR_INVALID_ARG;
+    if (target && (!dL_dimage || !loss_out)) return PGS_ERR_INVALID_ARG;
     const int T = ctx->tile, TX = (cam->width + T - 1) / T, TY = (cam->height + T - 1) / T;
     const int64_t tiles = (int64_t)TX * TY, pixels = (int64_t)cam->width * cam->height;
     const int64_t supers = super_tiles(TX, TY);
@@ -348,8 +352,18 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
         ctx->recorded = true;
     } else {
         // the forward also clears the screen-space gradients its backward accumulates
+        L1Fused l1f;
+        if (target) {
+            l1f.target = target;
+            l1f.dL = dL_dimage;
+            l1f.n = 3 * pixels;
+            l1f.inv_n = 1.0f / (float)l1f.n;
+            l1f.acc = ctx->sc.l1_acc;  // zeroed by the projection
+            l1f.ticket = reinterpret_cast<uint32_t*>(ctx->sc.l1_acc + 2);
+            l1f.out = loss_out;
+        }
         const int k = launch_composite_fwd(*cam, TX, TY, T, ctx->buf, params->n, ctx->sc, image_out, s, ctx->variant,
-                                           9 * params->n);
+                                           9 * params->n, l1f);
         ctx->launches += k;
         ctx->grad_clean = k > 0;
     }
@@ -358,6 +372,11 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     span(ctx, PGS_STAGE_BIN, e1, e2);
     span(ctx, PGS_STAGE_SORT, e2, e3);
     span(ctx, PGS_STAGE_COMPOSITE_FWD, e3, e4);
+    if (target && ctx->recorded) {  // the recording forward has no fused loss: the loss kernel
+        const size_t e5 = mark(ctx);
+        ctx->launches += launch_loss_l1(image_out, target, 3 * pixels, dL_dimage, loss_out, ctx->sc, s);
+        span(ctx, PGS_STAGE_LOSS, e5, mark(ctx));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e);
     ctx->has_render = true;
@@ -367,6 +386,16 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
     ctx->cam = *cam;
     ctx->params = *params;
     return PGS_OK;
+}
+
+int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, float* image_out) {
+    return render_impl(ctx, params, cam, image_out, nullptr, nullptr, nullptr);
+}
+
+int pgs_render_l1(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam, const float* target,
+                  float* image_out, float* dL_dimage, float* loss_out) {
+    if (!target) return PGS_ERR_INVALID_ARG;
+    return render_impl(ctx, params, cam, image_out, target, dL_dimage, loss_out);
 }
 
 int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,

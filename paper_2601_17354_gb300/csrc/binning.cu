@@ -969,20 +969,34 @@ __device__ __forceinline__ int order_slot(const Scratch& sc, int t) {
     return kOrderBuckets - 1 - b;
 }
 
-// up to kOrderSmall tiles: both steps in one CTA of 1024 threads (one launch)
+// up to kOrderSmall tiles: both steps in one CTA of 1024 threads (one launch); each thread loads
+// the ranges of its (at most 16) tiles up front, so the loads overlap instead of costing one
+// memory latency per round, and keeps their buckets for the scatter
+constexpr int kOrderSmallThreads = 1024;
 constexpr int kOrderSmall = 16384;
-__global__ void __launch_bounds__(1024) k_tile_order_small(int tiles, Scratch sc) {
+constexpr int kOrderSmallItems = kOrderSmall / kOrderSmallThreads;
+__global__ void __launch_bounds__(kOrderSmallThreads) k_tile_order_small(int tiles, Scratch sc) {
     __shared__ uint32_t hist[kOrderBuckets], cursor[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
+    int slot[kOrderSmallItems];
+#pragma unroll
+    for (int k = 0; k < kOrderSmallItems; ++k) {
+        const int t = k * kOrderSmallThreads + (int)threadIdx.x;
+        slot[k] = t < tiles ? order_slot(sc, t) : -1;
+    }
     __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&hist[order_slot(sc, t)], 1u);
+#pragma unroll
+    for (int k = 0; k < kOrderSmallItems; ++k)
+        if (slot[k] >= 0) atomicAdd(&hist[slot[k]], 1u);
     __syncthreads();
     cta_scan(kOrderBuckets, [&](int k) { return (unsigned long long)hist[k]; },
              [&](int k, unsigned long long v) { cursor[k] = (uint32_t)v; });
     __syncthreads();
-    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
-        const uint32_t pos = atomicAdd(&cursor[order_slot(sc, t)], 1u);
-        if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)t;
+#pragma unroll
+    for (int k = 0; k < kOrderSmallItems; ++k) {
+        if (slot[k] < 0) continue;
+        const uint32_t pos = atomicAdd(&cursor[slot[k]], 1u);
+        if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)(k * kOrderSmallThreads + (int)threadIdx.x);
         else atomicOr(sc.status, kStatusInternal);
     }
 }
@@ -1117,7 +1131,7 @@ int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s)
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
     if (tiles <= 0) return 0;
     if (tiles <= kOrderSmall) {
-        k_tile_order_small<<<1, 1024, 0, s>>>(tiles, sc);
+        k_tile_order_small<<<1, kOrderSmallThreads, 0, s>>>(tiles, sc);
         return 1;
     }
     const int blocks = (tiles + kOrderThreads * kOrderItems - 1) / (kOrderThreads * kOrderItems);
@@ -1218,6 +1232,7 @@ ZeroPlan render_zero_plan(const Scratch& sc, int64_t n, int64_t tiles, int64_t s
         add(sc.sort_hist, lookback_words(passes, (capacity + kSortTile - 1) / kSortTile));
         if (passes > 1) add(sc.crange, 2 * (size_t)supers);
     }
+    add(sc.l1_acc, 6);  // the forward's fused L1 sums and ticket
     return z;
 }
 

@@ -80,7 +80,25 @@ struct TileJob {
     float* T_final;
     uint32_t* last;
     uint32_t* ncomp;
+    // forward with the L1 loss fused (target != nullptr): dL_out = sign(image - target) * inv_n
+    const float* target = nullptr;
+    float* dL_out = nullptr;
+    float inv_n = 0.f;
 };
+
+// L1 terms of one pixel's three values (the loss kernel's arithmetic): gradient written, |d| and
+// d^2 added to the thread's sums
+__device__ __forceinline__ void l1_pixel(const TileJob& J, size_t p, size_t plane, float r, float g, float b,
+                                         float& l1, float& l2) {
+    const float v[3] = {r, g, b};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float d = v[c] - J.target[c * plane + p];
+        l1 += fabsf(d);
+        l2 = fmaf(d, d, l2);
+        J.dL_out[c * plane + p] = d > 0.f ? J.inv_n : (d < 0.f ? -J.inv_n : 0.f);
+    }
+}
 
 // Replay cache of the paper's training operator (the per-pixel record S = {id, C_in, alpha} of
 // Eq. 9 with a per-pixel count reset every render), in front-to-back form: for each pixel the
@@ -115,8 +133,9 @@ struct FwdSmem {
 
 // One tile of the forward.  kPix: pixels per thread (vertical strip); kDepth: entries staged per
 // batch.  Every thread of the CTA calls it with the same job.
+// Returns the thread's L1 sums (|d|, d^2) when J.target is set, else zeros.
 template <int kT, int kPix, int kDepth, bool kRecord = false>
-__device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+__device__ __forceinline__ float2 fwd_tile_scalar(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
                                          const Scratch& sc, FwdSmem<kDepth>& S, ReplayCache rc = {}) {
     static_assert(!kRecord || kPix == 1, "the replay cache records one pixel per thread");
     constexpr int kThreads = kT * kT / kPix;
@@ -197,20 +216,24 @@ __device__ __forceinline__ void fwd_tile_scalar(const TileJob& J, int64_t n, con
             }
         }
     }
+    float l1 = 0.f, l2 = 0.f;
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
         const int py = py0 + k;
         if (px < W && py < H) {
             const size_t p = (size_t)py * W + px, plane = (size_t)W * H;
-            J.image[p] = fmaf(T[k], bg.x, C0[k]);
-            J.image[plane + p] = fmaf(T[k], bg.y, C1[k]);
-            J.image[2 * plane + p] = fmaf(T[k], bg.z, C2[k]);
+            const float r = fmaf(T[k], bg.x, C0[k]), g = fmaf(T[k], bg.y, C1[k]), b = fmaf(T[k], bg.z, C2[k]);
+            J.image[p] = r;
+            J.image[plane + p] = g;
+            J.image[2 * plane + p] = b;
             J.T_final[p] = T[k];
             J.last[p] = last[k];
             J.ncomp[p] = ncomp[k];
             if constexpr (kRecord) rc.count[p] = ncomp[k] > (uint32_t)rc.K ? (uint32_t)rc.K + 1 : ncomp[k];
+            if (J.target) l1_pixel(J, p, plane, r, g, b, l1, l2);
         }
     }
+    return make_float2(l1, l2);
 }
 
 // Sum v[0..8] over the warp.  Afterwards lane l with l % 4 == 0 holds the sum of v[l >> 2]
@@ -520,8 +543,8 @@ __device__ __forceinline__ void pair_alpha(F2 dy, F2 DX, F2 ADX2, F2 S2Y, F2 S2Z
 }
 
 template <int kT, int kPix, int kDepth>
-__device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
-                                               const Scratch& sc, FwdSmem<kDepth>& S) {
+__device__ __forceinline__ float2 fwd_tile_pairs(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                                 const Scratch& sc, FwdSmem<kDepth>& S) {
     constexpr int kThreads = kT * kT / kPix;
     constexpr int kBatch = kDepth;
     constexpr int NP = kPix / 2;
@@ -605,6 +628,7 @@ __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, cons
             }
         }
     }
+    float l1 = 0.f, l2 = 0.f;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const float2 t = un(T[q]), c0 = un(C0[q]), c1 = un(C1[q]), c2 = un(C2[q]);
@@ -615,15 +639,18 @@ __device__ __forceinline__ void fwd_tile_pairs(const TileJob& J, int64_t n, cons
             const int py = py0 + k;
             if (px < W && py < H) {
                 const size_t pp = (size_t)py * W + px, plane = (size_t)W * H;
-                J.image[pp] = fmaf(tk[h], bg.x, r[h]);
-                J.image[plane + pp] = fmaf(tk[h], bg.y, g[h]);
-                J.image[2 * plane + pp] = fmaf(tk[h], bg.z, b[h]);
+                const float ir = fmaf(tk[h], bg.x, r[h]), ig = fmaf(tk[h], bg.y, g[h]), ib = fmaf(tk[h], bg.z, b[h]);
+                J.image[pp] = ir;
+                J.image[plane + pp] = ig;
+                J.image[2 * plane + pp] = ib;
                 J.T_final[pp] = tk[h];
                 J.last[pp] = last[k];
                 J.ncomp[pp] = ncomp[k];
+                if (J.target) l1_pixel(J, pp, plane, ir, ig, ib, l1, l2);
             }
         }
     }
+    return make_float2(l1, l2);
 }
 
 // Backward tiles of 32 x 32 pixels with two or four pixels per thread (the two-phase routine
@@ -1206,10 +1233,10 @@ __device__ __forceinline__ void bwd_tile_2p(const TileJob& J, int64_t n, const u
 }
 
 template <int kT, int kPix, int kDepth>
-__device__ __forceinline__ void fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
-                                         const Scratch& sc, FwdSmem<kDepth>& S) {
-    if constexpr (kPix == 1) fwd_tile_scalar<kT, kPix, kDepth>(J, n, vals, sc, S);
-    else fwd_tile_pairs<kT, kPix, kDepth>(J, n, vals, sc, S);
+__device__ __forceinline__ float2 fwd_tile(const TileJob& J, int64_t n, const uint32_t* __restrict__ vals,
+                                           const Scratch& sc, FwdSmem<kDepth>& S) {
+    if constexpr (kPix == 1) return fwd_tile_scalar<kT, kPix, kDepth>(J, n, vals, sc, S);
+    else return fwd_tile_pairs<kT, kPix, kDepth>(J, n, vals, sc, S);
 }
 
 // shared memory of a backward tile: one pixel per thread stages plain records, pairs the packed ones
@@ -1267,7 +1294,7 @@ __device__ __forceinline__ TileJob batch_job(const RenderDesc& rd, int64_t gt, c
 template <int kT, int kPix, int kDepth>
 __global__ void __launch_bounds__(kT * kT / kPix)
 k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __restrict__ vals,
-                Scratch sc, float* __restrict__ image, int64_t zero_grad) {
+                Scratch sc, float* __restrict__ image, int64_t zero_grad, L1Fused l1f) {
     __shared__ FwdSmem<kDepth> S;
     TileJob J;
     J.W = W;
@@ -1281,7 +1308,42 @@ k_composite_fwd(int W, int H, int TX, float3 bg, int64_t n, const uint32_t* __re
     J.T_final = sc.T_final;
     J.last = sc.last;
     J.ncomp = sc.ncomp;
-    fwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
+    J.target = l1f.target;
+    J.dL_out = l1f.dL;
+    J.inv_n = l1f.inv_n;
+    const float2 l = fwd_tile<kT, kPix, kDepth>(J, n, vals, sc, S);
+    if (l1f.target) {  // the tile's L1 sums into the render's double accumulators; the last CTA reports
+        constexpr int kWarps = kT * kT / kPix / 32;
+        __shared__ float s_l1[kWarps], s_l2[kWarps];
+        __shared__ bool s_last;
+        float a = l.x, b = l.y;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(kFull, a, o);
+            b += __shfl_xor_sync(kFull, b, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_l1[threadIdx.x >> 5] = a;
+            s_l2[threadIdx.x >> 5] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ta = 0.0, tb = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                ta += (double)s_l1[w];
+                tb += (double)s_l2[w];
+            }
+            atomicAdd(&l1f.acc[0], ta);
+            atomicAdd(&l1f.acc[1], tb);
+            __threadfence();
+            s_last = atomicAdd(l1f.ticket, 1u) == gridDim.x - 1;
+            if (s_last) {
+                __threadfence();
+                l1f.out[0] = (float)(atomicAdd(&l1f.acc[0], 0.0) / (double)l1f.n);
+                l1f.out[1] = (float)atomicAdd(&l1f.acc[1], 0.0);
+            }
+        }
+    }
     if (zero_grad > 0) {  // grad2d is 256-byte aligned: 16-byte stores, the tail by block 0
         float4* g4 = reinterpret_cast<float4*>(sc.grad2d);
         const int64_t n4 = zero_grad >> 2;
@@ -1475,12 +1537,13 @@ bool valid_variant(CompositeVariant v, int T) {
     X(32, 2, 64) X(32, 2, 128) X(32, 2, 256) X(32, 4, 64) X(32, 4, 128) X(32, 4, 256)
 
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
-                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v, int64_t zero_grad) {
+                         const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v, int64_t zero_grad,
+                         const L1Fused& l1f) {
     const float3 bg = make_float3(cam.bg[0], cam.bg[1], cam.bg[2]);
 #define X(TT, P, D)                                                                               \
     if (T == TT && v.pix == P && v.depth == D) {                                                  \
         k_composite_fwd<TT, P, D><<<TX * TY, TT * TT / P, 0, s>>>(cam.width, cam.height, TX, bg, n, \
-                                                                  sc.vals[buf], sc, image, zero_grad); \
+                                                                  sc.vals[buf], sc, image, zero_grad, l1f); \
         return 1;                                                                                 \
     }
     PGS_VARIANTS(X)

@@ -99,6 +99,7 @@ struct Scratch {
     uint32_t* digit_totals = nullptr; // [kTotalCopies][kMaxPasses][kRadix]
     float* loss_partials = nullptr;   // [2][kLossBlocks]
     uint32_t* loss_ticket = nullptr;
+    double* l1_acc = nullptr;         // [3]: the fused L1's sums of |d| and d^2, then its CTA ticket
     // depth sort of the Gaussians: keys = depth bits (culled: all ones), values = canonical index;
     // its key count / CTA count words and histograms, separate from those of the coarse entries' sort
     unsigned long long* dkeys[2] = {nullptr, nullptr};
@@ -176,7 +177,7 @@ CompositeVariant default_variant();
 // Word ranges of a render's scratch that must be zero before its binning (look-back words, digit
 // totals, counters, tile and super-tile ranges).  The projection clears them on its way, so the
 // binning launches no separate clears.
-constexpr int kZeroRegions = 8;
+constexpr int kZeroRegions = 10;  // render_zero_plan adds at most 8
 struct ZeroPlan {
     uint32_t* p[kZeroRegions];
     uint32_t words[kZeroRegions];
@@ -271,11 +272,24 @@ int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s)
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s);
 
 // K6/K8: compositing forward and backward (sorted values in buffer `buf`).
+// The L1 loss fused into the compositing forward (target == nullptr: off): with n = 3 H W values,
+// dL[k] = sign(image[k] - target[k]) * inv_n; the CTAs add their sums of |d| and d^2 into acc[0],
+// acc[1] (zero on entry) and the last CTA (ticket, zero on entry) writes out[0] = acc[0] / n,
+// out[1] = acc[1].
+struct L1Fused {
+    const float* target = nullptr;
+    float* dL = nullptr;
+    float inv_n = 0.f;
+    int64_t n = 0;
+    double* acc = nullptr;
+    uint32_t* ticket = nullptr;
+    float* out = nullptr;
+};
 // zero_grad: also zero the first zero_grad floats of sc.grad2d (the coming backward's screen-space
 // gradients), spread over the CTAs, in place of a separate clear.
 int launch_composite_fwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, float* image, cudaStream_t s, CompositeVariant v,
-                         int64_t zero_grad = 0);
+                         int64_t zero_grad = 0, const L1Fused& l1f = L1Fused{});
 int launch_composite_bwd(const pgs_camera& cam, int TX, int TY, int T, int buf, int64_t n,
                          const Scratch& sc, const float* dL_dimage, cudaStream_t s, CompositeVariant v);
 // Replay-cache compositing (one pixel per thread): the forward records, per pixel, the first K

@@ -145,6 +145,23 @@ class Rasterizer:
     def render(self, params: GaussianBuffer, cam, out: torch.Tensor | None = None) -> torch.Tensor:
         return self.render_struct(params.struct(), cam, out)
 
+    def render_l1(self, params: GaussianBuffer, cam, target: torch.Tensor, out: torch.Tensor | None = None,
+                  grad: torch.Tensor | None = None, loss: torch.Tensor | None = None):
+        """render + loss_l1 in one pass (pgs_render_l1): (image, dL/dimage, device tensor [l1, sse])."""
+        cs = cam if isinstance(cam, L.PgsCamera) else camera_struct(cam)
+        shape = (3, cs.height, cs.width)
+        assert target.is_contiguous() and tuple(target.shape) == shape and target.dtype == torch.float32
+        out = torch.empty(shape, dtype=torch.float32, device=self.device) if out is None else out
+        grad = torch.empty(shape, dtype=torch.float32, device=self.device) if grad is None else grad
+        loss = torch.empty(2, dtype=torch.float32, device=self.device) if loss is None else loss
+        g = params.struct()
+        L.check(self._lib.pgs_render_l1(self._ctx, C.byref(g), C.byref(cs), C.c_void_p(target.data_ptr()),
+                                        C.c_void_p(out.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                        C.c_void_p(loss.data_ptr())), "pgs_render_l1")
+        self.render_id += 1
+        self._last_shape = (cs.height, cs.width)
+        return out, grad, loss
+
     def loss_l1(self, image: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None,
                 out: torch.Tensor | None = None):
         """(dL/dimage, device tensor [l1, sse])."""
@@ -310,14 +327,15 @@ class Trainer:
         self.loss = torch.zeros(2, dtype=torch.float32, device=params.data.device)
 
     def step(self, cam, target: torch.Tensor) -> torch.Tensor:
-        self.image = self.r.render(self.params, cam, self.image if self.image is not None and
-                                   self.image.shape[1:] == (cam.height, cam.width) else None)
-        if self.dl is None or self.dl.shape != self.image.shape:
+        shape = (3, cam.height, cam.width)
+        if self.image is None or tuple(self.image.shape) != shape:
+            self.image = torch.empty(shape, dtype=torch.float32, device=self.params.data.device)
             self.dl = torch.empty_like(self.image)
         if self.dssim > 0.0:
+            self.r.render(self.params, cam, self.image)
             self.r.loss_dssim(self.image, target, self.dssim, self.dl, self.loss)
-        else:
-            self.r.loss_l1(self.image, target, self.dl, self.loss)
+        else:  # the L1 loss and its gradient come out of the compositing forward
+            self.r.render_l1(self.params, cam, target, self.image, self.dl, self.loss)
         self.t += 1
         if self.fused:
             self.r.backward_step(self.dl, self.params, self.m, self.v, self.t)
