@@ -969,9 +969,11 @@ __device__ __forceinline__ int order_slot(const Scratch& sc, int t) {
     return kOrderBuckets - 1 - b;
 }
 
-// up to kOrderSmall tiles: both steps in one CTA of 1024 threads (one launch); each thread loads
-// the ranges of its (at most 16) tiles up front, so the loads overlap instead of costing one
-// memory latency per round, and keeps their buckets for the scatter
+// up to kOrderSmall tiles: both steps in one CTA of 1024 threads (one launch); each thread takes
+// a run of (at most 16) consecutive tiles, loads their ranges up front and keeps their buckets
+// for the scatter.  Runs, not a stride of 1024: the 32 tiles one warp instruction touches are then
+// 16 tiles apart instead of neighbours of similar list length, so fewer of its shared-memory
+// atomics fall on the same bucket and serialise
 constexpr int kOrderSmallThreads = 1024;
 constexpr int kOrderSmall = 16384;
 constexpr int kOrderSmallItems = kOrderSmall / kOrderSmallThreads;
@@ -981,7 +983,7 @@ __global__ void __launch_bounds__(kOrderSmallThreads) k_tile_order_small(int til
     int slot[kOrderSmallItems];
 #pragma unroll
     for (int k = 0; k < kOrderSmallItems; ++k) {
-        const int t = k * kOrderSmallThreads + (int)threadIdx.x;
+        const int t = (int)threadIdx.x * kOrderSmallItems + k;
         slot[k] = t < tiles ? order_slot(sc, t) : -1;
     }
     __syncthreads();
@@ -996,7 +998,7 @@ __global__ void __launch_bounds__(kOrderSmallThreads) k_tile_order_small(int til
     for (int k = 0; k < kOrderSmallItems; ++k) {
         if (slot[k] < 0) continue;
         const uint32_t pos = atomicAdd(&cursor[slot[k]], 1u);
-        if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)(k * kOrderSmallThreads + (int)threadIdx.x);
+        if (pos < (uint32_t)tiles) sc.tile_order[pos] = (uint32_t)((int)threadIdx.x * kOrderSmallItems + k);
         else atomicOr(sc.status, kStatusInternal);
     }
 }
