@@ -115,43 +115,61 @@ __device__ __forceinline__ bool last_cta(uint32_t* ticket) {
     return s_last;
 }
 
-// Per CTA of depth-ordered Gaussians: coarse entries (super-tiles of the rectangle) into
-// block_sums; reached tiles added into pair_count (zeroed before).  The last CTA then scans the
-// per-CTA counts into their offsets and sets the coarse total, the coarse sort's CTA count, the
-// capacity the render needs (pairs, and the coarse stage's entries and counters) and the capacity
-// check.
+// Per block of kProjBlock depth-ordered Gaussians (the coarse emission's CTAs): coarse entries
+// (super-tiles of the rectangle) into block_sums; reached tiles added into pair_count (zeroed
+// before).  A CTA takes kCountItems such blocks, one Gaussian of each per thread, so each thread
+// has that many independent gathers in flight.  The last CTA then scans the per-block counts into
+// their offsets and sets the coarse total, the coarse sort's CTA count, the capacity the render
+// needs (pairs, and the coarse stage's entries and counters) and the capacity check.
+constexpr int kCountItems = 4;
 __global__ void __launch_bounds__(kProjBlock)
 k_coarse_counts(int64_t n, int64_t capacity, int64_t supers, const uint32_t* __restrict__ perm, Scratch sc) {
-    const int64_t i = (int64_t)blockIdx.x * kProjBlock + threadIdx.x;
-    uint32_t area = 0, reached = 0;
-    if (i < n) {
-        const uint32_t g = perm[i];
-        reached = sc.touched[g];
-        if (reached) {
+    const int64_t nbk = (n + kProjBlock - 1) / kProjBlock;  // blocks of the emission
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t g[kCountItems], reached[kCountItems], area[kCountItems];
+    uint2 rect[kCountItems];
+#pragma unroll
+    for (int k = 0; k < kCountItems; ++k) {
+        const int64_t i = ((int64_t)blockIdx.x * kCountItems + k) * kProjBlock + threadIdx.x;
+        g[k] = i < n ? perm[i] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int k = 0; k < kCountItems; ++k) {
+        const bool valid = g[k] != 0xffffffffu;
+        reached[k] = valid ? sc.touched[g[k]] : 0u;
+        rect[k] = valid ? sc.rect[g[k]] : make_uint2(0u, 0u);
+    }
+    __shared__ uint32_t s_a[kCountItems][kProjBlock / 32], s_r[kProjBlock / 32];
+    uint32_t rsum = 0;
+#pragma unroll
+    for (int k = 0; k < kCountItems; ++k) {
+        area[k] = 0;
+        if (reached[k]) {
             uint32_t sx0, sy0, sx1, sy1;
-            super_rect(sc.rect[g], sx0, sy0, sx1, sy1);
-            area = (sx1 - sx0) * (sy1 - sy0);
+            super_rect(rect[k], sx0, sy0, sx1, sy1);
+            area[k] = (sx1 - sx0) * (sy1 - sy0);
         }
+        const uint32_t wa = __reduce_add_sync(kFull, area[k]);
+        if (lane == 0) s_a[k][warp] = wa;
+        rsum += reached[k];
     }
-    const uint32_t wa = __reduce_add_sync(kFull, area), wr = __reduce_add_sync(kFull, reached);
-    __shared__ uint32_t s_a[kProjBlock / 32], s_r[kProjBlock / 32];
-    if ((threadIdx.x & 31) == 0) {
-        s_a[threadIdx.x >> 5] = wa;
-        s_r[threadIdx.x >> 5] = wr;
-    }
+    const uint32_t wr = __reduce_add_sync(kFull, rsum);
+    if (lane == 0) s_r[warp] = wr;
     __syncthreads();
     if (threadIdx.x < 32) {
         const bool in = threadIdx.x < kProjBlock / 32;
-        const uint32_t a = __reduce_add_sync(kFull, in ? s_a[threadIdx.x] : 0u);
-        const unsigned long long r = __reduce_add_sync(kFull, in ? s_r[threadIdx.x] : 0u);
-        if (threadIdx.x == 0) {
-            sc.block_sums[blockIdx.x] = a;
-            if (r) atomicAdd(sc.pair_count, r);
+#pragma unroll
+        for (int k = 0; k < kCountItems; ++k) {
+            const uint32_t a = __reduce_add_sync(kFull, in ? s_a[k][threadIdx.x] : 0u);
+            const int64_t b = (int64_t)blockIdx.x * kCountItems + k;
+            if (threadIdx.x == 0 && b < nbk) sc.block_sums[b] = a;
         }
+        const unsigned long long r = __reduce_add_sync(kFull, in ? s_r[threadIdx.x] : 0u);
+        if (threadIdx.x == 0 && r) atomicAdd(sc.pair_count, r);
     }
     if (!last_cta(&sc.bin_ticket[0])) return;
     const unsigned long long Ce = cta_scan(
-        (int)gridDim.x, [&](int k) { return (unsigned long long)__ldcg(&sc.block_sums[k]); },
+        (int)nbk, [&](int k) { return (unsigned long long)__ldcg(&sc.block_sums[k]); },
         [&](int k, unsigned long long v) { sc.block_offsets[k] = v; });
     if (threadIdx.x == 0) {
         const unsigned long long P = atomicAdd(sc.pair_count, 0ull);
@@ -1160,7 +1178,8 @@ int launch_depth_sort(int64_t n, const Scratch& sc, cudaStream_t s, const uint32
 
 int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t* perm, const Scratch& sc,
                      cudaStream_t s, bool cleared) {
-    const int nb = (int)((n + kProjBlock - 1) / kProjBlock);
+    const int64_t nbk = (n + kProjBlock - 1) / kProjBlock;
+    const int nb = (int)((nbk + kCountItems - 1) / kCountItems);
     if (!cleared) cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
     k_coarse_counts<<<nb > 0 ? nb : 1, kProjBlock, 0, s>>>(n, capacity, supers, perm, sc);
     return 1;
