@@ -124,6 +124,7 @@ __device__ __forceinline__ bool last_cta(uint32_t* ticket) {
 constexpr int kCountItems = 4;
 __global__ void __launch_bounds__(kProjBlock)
 k_coarse_counts(int64_t n, int64_t capacity, int64_t supers, const uint32_t* __restrict__ perm, Scratch sc) {
+    pdl_begin();
     const int64_t nbk = (n + kProjBlock - 1) / kProjBlock;  // blocks of the emission
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t g[kCountItems], reached[kCountItems], area[kCountItems];
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(kProjBlock)
 k_coarse_emit(int64_t n, int SX, int T, int64_t capacity, const uint32_t* __restrict__ perm, Scratch sc,
               uint32_t* __restrict__ gidx, uint32_t* __restrict__ gmask, int passes, uint32_t last_mask,
               const RenderDesc* __restrict__ renders, int R) {
+    pdl_begin();
     __shared__ uint32_t s_sx0[kProjBlock], s_sy0[kProjBlock], s_sw[kProjBlock];
     __shared__ uint32_t s_SX[kProjBlock], s_base[kProjBlock], s_gid[kProjBlock], s_hm[kProjBlock];
     __shared__ uint2 s_rect[kProjBlock];
@@ -412,6 +414,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kSortThreads)
 k_digit_totals(int64_t capacity, int first_shift, int passes, uint32_t last_mask, const KeyT* __restrict__ keys,
                Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t h[kMaxPasses][kRadix];
     for (int k = threadIdx.x; k < kMaxPasses * kRadix; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
@@ -471,6 +474,7 @@ template <typename KeyT, int kItems, int kThreads = kSortThreads>
 __global__ void __launch_bounds__(kThreads)
 k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, const KeyT* __restrict__ kin,
            const uint32_t* __restrict__ vin, KeyT* __restrict__ kout, uint32_t* __restrict__ vout, Scratch sc) {
+    pdl_begin();
     static_assert(kThreads % kRadix == 0, "whole digit warps");
     constexpr int kWarps = kThreads / 32;
     constexpr int kTile = kThreads * kItems;            // keys per CTA
@@ -651,6 +655,7 @@ k_onesweep(int64_t capacity, int pass, int shift, uint32_t dmask, int sb_max, co
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_ranges(int64_t capacity, uint32_t tiles, const uint32_t* __restrict__ keys, Scratch sc) {
+    pdl_begin();
     const uint64_t P = kept_pairs(sc, capacity);
     // four consecutive keys per thread step (one 16-byte load), with the neighbours either side
     for (uint64_t k0 = ((uint64_t)blockIdx.x * 256 + threadIdx.x) * 4; k0 < P; k0 += (uint64_t)gridDim.x * 1024) {
@@ -734,6 +739,7 @@ __device__ __forceinline__ SuperCell super_cell(uint32_t s, int TX, int TY, cons
 // 2 = one super-tile: crange[0] = all kept entries.
 __global__ void __launch_bounds__(kScanThreads)
 k_block_prefix(int S, int64_t capacity, Scratch sc, int crange_from) {
+    pdl_begin();
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ uint32_t s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -810,6 +816,7 @@ k_block_prefix(int S, int64_t capacity, Scratch sc, int crange_from) {
 __global__ void __launch_bounds__(kFineThreads)
 k_fine_count(int64_t capacity, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ gmask,
              uint32_t* __restrict__ wc, int S, Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t s_cw[kFineWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t VB = sc.vbase[S];
@@ -842,6 +849,7 @@ k_fine_count(int64_t capacity, const uint32_t* __restrict__ cv, const uint32_t* 
 // super-tiles' pairs into their first pair sbase[s] and sets the pair count.
 __global__ void __launch_bounds__(256)
 k_seg_scan(int64_t capacity, uint32_t* __restrict__ wc, Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t s_part[8][32];
     const int s = blockIdx.x, x = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t v0 = sc.vbase[s], nb = sc.vbase[s + 1] - v0;
@@ -891,6 +899,7 @@ __global__ void __launch_bounds__(kFineThreads)
 k_fine_emit(int64_t capacity, int TX, int TY, const uint32_t* __restrict__ cv, const uint32_t* __restrict__ gidx,
             const uint32_t* __restrict__ gmask, const uint32_t* __restrict__ wc, int S, uint32_t* __restrict__ out,
             Scratch sc, const RenderDesc* __restrict__ renders, int R) {
+    pdl_begin();
     __shared__ uint32_t s_cw[kFineWarps][32];
     __shared__ uint32_t s_off[kFineWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -996,6 +1005,7 @@ constexpr int kOrderSmallThreads = 1024;
 constexpr int kOrderSmall = 16384;
 constexpr int kOrderSmallItems = kOrderSmall / kOrderSmallThreads;
 __global__ void __launch_bounds__(kOrderSmallThreads) k_tile_order_small(int tiles, Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t hist[kOrderBuckets], cursor[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
     int slot[kOrderSmallItems];
@@ -1022,6 +1032,7 @@ __global__ void __launch_bounds__(kOrderSmallThreads) k_tile_order_small(int til
 }
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_hist(int tiles, Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t hist[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
     __syncthreads();
@@ -1041,6 +1052,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_hist(int tiles, Scratch 
 }
 
 __global__ void __launch_bounds__(kOrderThreads) k_tile_scatter(int tiles, Scratch sc) {
+    pdl_begin();
     __shared__ uint32_t hist[kOrderBuckets], base[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0;
     __syncthreads();
@@ -1113,13 +1125,15 @@ int sort_passes(int64_t capacity, int first_shift, int bits, const Scratch& sc, 
     if (!cleared) cudaMemsetAsync(sc.sort_hist, 0, sizeof(uint32_t) * lookback_words(passes, sb_max), s);
     if (!totals_ready) {  // else the kernel that wrote the keys counted their digits
         if (!cleared) cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
-        k_digit_totals<KeyT><<<total_blocks, kSortThreads, 0, s>>>(capacity, first_shift, passes, last_mask, k[0], sc);
+        launch_pdl(k_digit_totals<KeyT>, dim3(total_blocks), dim3(kSortThreads), 0, s, capacity, first_shift, passes,
+                   last_mask, (const KeyT*)k[0], sc);
     }
     for (int p = 0; p < passes; ++p) {
         const int shift = first_shift + p * kRadixBits;
         const uint32_t dmask = p == passes - 1 ? last_mask : (uint32_t)(kRadix - 1);
-        k_onesweep<KeyT, kItems, kThreads><<<sb_max, kThreads, scatter_smem<KeyT, kItems, kThreads>(), s>>>(
-            capacity, p, shift, dmask, sb_max, k[buf], sc.vals[buf], k[buf ^ 1], sc.vals[buf ^ 1], sc);
+        launch_pdl(k_onesweep<KeyT, kItems, kThreads>, dim3(sb_max), dim3(kThreads), scatter_smem<KeyT, kItems, kThreads>(),
+                   s, capacity, p, shift, dmask, sb_max, (const KeyT*)k[buf], (const uint32_t*)sc.vals[buf], k[buf ^ 1],
+                   sc.vals[buf ^ 1], sc);
         buf ^= 1;
     }
     *out_buf = buf;
@@ -1151,12 +1165,12 @@ int launch_timeout_selftest(int64_t capacity, const Scratch& sc, cudaStream_t s)
 int launch_tile_order(int tiles, const Scratch& sc, cudaStream_t s) {
     if (tiles <= 0) return 0;
     if (tiles <= kOrderSmall) {
-        k_tile_order_small<<<1, kOrderSmallThreads, 0, s>>>(tiles, sc);
+        launch_pdl(k_tile_order_small, dim3(1), dim3(kOrderSmallThreads), 0, s, tiles, sc);
         return 1;
     }
     const int blocks = (tiles + kOrderThreads * kOrderItems - 1) / (kOrderThreads * kOrderItems);
-    k_tile_hist<<<blocks, kOrderThreads, 0, s>>>(tiles, sc);
-    k_tile_scatter<<<blocks, kOrderThreads, 0, s>>>(tiles, sc);
+    launch_pdl(k_tile_hist, dim3(blocks), dim3(kOrderThreads), 0, s, tiles, sc);
+    launch_pdl(k_tile_scatter, dim3(blocks), dim3(kOrderThreads), 0, s, tiles, sc);
     return 2;
 }
 
@@ -1181,7 +1195,7 @@ int launch_bin_count(int64_t n, int64_t supers, int64_t capacity, const uint32_t
     const int64_t nbk = (n + kProjBlock - 1) / kProjBlock;
     const int nb = (int)((nbk + kCountItems - 1) / kCountItems);
     if (!cleared) cudaMemsetAsync(sc.pair_count, 0, sizeof(unsigned long long), s);
-    k_coarse_counts<<<nb > 0 ? nb : 1, kProjBlock, 0, s>>>(n, capacity, supers, perm, sc);
+    launch_pdl(k_coarse_counts, dim3(nb > 0 ? nb : 1), dim3(kProjBlock), 0, s, n, capacity, supers, perm, sc);
     return 1;
 }
 
@@ -1202,8 +1216,8 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     const uint32_t last_mask = passes > 0 ? (uint32_t)((1u << (bits - kRadixBits * (passes - 1))) - 1u) : 0u;
     if (!cleared) cudaMemsetAsync(sc.digit_totals, 0, sizeof(uint32_t) * kTotalWords, s);
     if (nb > 0) {
-        k_coarse_emit<<<nb, kProjBlock, 0, s>>>(n, (TX + kSuperW - 1) / kSuperW, T, capacity, perm, sc, gidx, gmask,
-                                                passes, last_mask, renders, R);
+        launch_pdl(k_coarse_emit, dim3(nb), dim3(kProjBlock), 0, s, n, (TX + kSuperW - 1) / kSuperW, T, capacity, perm,
+                   sc, gidx, gmask, passes, last_mask, renders, R);
         ++launched;
     }
     // the coarse entries arrive in depth order: a stable sort by super-tile keeps it in each
@@ -1216,18 +1230,19 @@ int launch_bin_lists(int64_t n, int TX, int TY, int T, int64_t tiles, int64_t su
     if (passes > 1) {  // the super-tiles' ranges from the sorted keys
         if (!cleared) cudaMemsetAsync(sc.crange, 0, sizeof(uint2) * (size_t)supers, s);
         cs.ranges = sc.crange;
-        k_ranges<<<152 * 8, 256, 0, s>>>(capacity, (uint32_t)supers, reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
+        launch_pdl(k_ranges, dim3(152 * 8), dim3(256), 0, s, capacity, (uint32_t)supers,
+                   reinterpret_cast<const uint32_t*>(sc.keys[cb]), cs);
         ++launched;
         crange_from = 0;
     }
-    k_block_prefix<<<1, kScanThreads, 0, s>>>((int)supers, capacity, sc, crange_from);
+    launch_pdl(k_block_prefix, dim3(1), dim3(kScanThreads), 0, s, (int)supers, capacity, sc, crange_from);
     // block counts over the sorted coarse keys (read by k_ranges before)
     uint32_t* wc = reinterpret_cast<uint32_t*>(sc.keys[cb]);
     const uint32_t* cv = sc.vals[cb];
-    k_fine_count<<<kFineGrid, kFineThreads, 0, s>>>(capacity, cv, gmask, wc, (int)supers, sc);
-    k_seg_scan<<<(unsigned)supers, 256, 0, s>>>(capacity, wc, sc);
-    k_fine_emit<<<kFineGrid, kFineThreads, 0, s>>>(capacity, TX, TY, cv, gidx, gmask, wc, (int)supers, sc.vals[cb ^ 1],
-                                                    sc, renders, R);
+    launch_pdl(k_fine_count, dim3(kFineGrid), dim3(kFineThreads), 0, s, capacity, cv, gmask, wc, (int)supers, sc);
+    launch_pdl(k_seg_scan, dim3((unsigned)supers), dim3(256), 0, s, capacity, wc, sc);
+    launch_pdl(k_fine_emit, dim3(kFineGrid), dim3(kFineThreads), 0, s, capacity, TX, TY, cv, gidx, gmask, wc, (int)supers,
+               sc.vals[cb ^ 1], sc, renders, R);
     *out_buf = cb ^ 1;
     return launched + 4;
 }

@@ -4,9 +4,37 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "pocketgs.h"
 
 namespace pgs {
+
+// Programmatic dependent launch between the short binning kernels. A kernel launched by
+// launch_pdl may be scheduled while the kernel before it on the stream is finishing; it calls
+// pdl_begin() first, which waits until that kernel has completed with its writes visible (a no-op
+// for a plain launch) and then lets the kernel after it be scheduled early in turn. Nothing is
+// read or written before the wait, so every kernel still sees all earlier kernels' results.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // screen tile edge T (pixels): 8, 16 (the default) or 32, one tile per compositing CTA
 constexpr int kTileDefault = 16;
