@@ -12,8 +12,9 @@
 // order; a stable radix sort by super-tile id groups the entries by super-tile, still in depth
 // order inside each group.  The fine stage gives each entry a 32-bit mask of the super-tile's tiles
 // the Gaussian reaches (the projection's reach test), counts each tile's entries per block of
-// kFineBlock with one warp ballot per tile, scans those counts, and writes each entry's canonical
-// index at its tile's first pair + the entries of the tile before it.  The pair buffer is laid out
+// kFineBlock (a warp's 32 masks transposed in five shuffle stages, so lane x holds the lanes that
+// reach tile x), scans those counts, and writes each entry's canonical index at its tile's first
+// pair + the entries of the tile before it.  The pair buffer is laid out
 // super-tile by super-tile, tiles row-major inside; a tile's list is [ranges[t].x, ranges[t].y).
 // The pair count is the sum of the projection's reached-tile counts, known before any list is
 // built; pairs beyond the capacity are not written (the status word records the overflow and the
@@ -26,6 +27,11 @@
 // up-front histogram; each pass is then one launch that ranks a tile's keys with warp ballots and
 // finds the tile's place by decoupled look-back over the tiles before it (bounded waits, see
 // k_onesweep).
+//
+// Every kernel here starts with pdl_begin() and is launched by launch_pdl: the next one is
+// scheduled while the current one's last CTAs run and waits for them before it touches memory.
+// The scratch these kernels expect zeroed (look-back words, digit totals, counters, ranges) is
+// cleared by the projection before them (render_zero_plan), or by memsets when the caller says so.
 #include "pgs_internal.cuh"
 
 namespace pgs {
