@@ -28,8 +28,9 @@
 // finds the tile's place by decoupled look-back over the tiles before it (bounded waits, see
 // k_onesweep).
 //
-// Every kernel here starts with pdl_begin() and is launched by launch_pdl: the next one is
-// scheduled while the current one's last CTAs run and waits for them before it touches memory.
+// The kernels of a render's binning start with pdl_begin() and are launched by launch_pdl (the
+// timeout self-test launches plainly): the next one is scheduled while the current one's last
+// CTAs run and waits for them before it touches memory.
 // The scratch these kernels expect zeroed (look-back words, digit totals, counters, ranges) is
 // cleared by the projection before them (render_zero_plan), or by memsets when the caller says so.
 #include "pgs_internal.cuh"
