@@ -114,7 +114,8 @@ int pgs_render(pgs_ctx* ctx, const pgs_gaussians* params, const pgs_camera* cam,
    loss_out is a device pointer to 2 floats. */
 int pgs_loss_l1(pgs_ctx* ctx, const float* image, const float* target, int64_t n, float* dL_dimage,
                 float* loss_out);
-/* pgs_render followed by pgs_loss_l1 on its image (n = 3 H W), in one pass: the compositing
+/* pgs_render (Eq. 7, Sec. III-C) followed by pgs_loss_l1 (the L1 loss of Sec. IV's training loop)
+   on its image (n = 3 H W), in one pass: the compositing
    forward also reads target [3][H][W] (device), writes dL_dimage [3][H][W] (device) and adds its
    CTAs' sums into the loss, so no separate loss kernel reads the image back.  image_out, T_final,
    last and dL_dimage are bit for bit those of the two calls; loss_out (device, 2 floats) holds the
